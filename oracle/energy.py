@@ -1,0 +1,78 @@
+"""Stray field, demag energy and its gradient (oracle; test infrastructure only).
+
+h_d = -grad phi (Sec. 1, the line introducing Eq. poisson).  The paper's
+energy study (Alg. 2 and the text after Fig. 2) discretises the stray field
+and the energy "second order" without giving the stencil; the reading used
+here is:
+
+* d/dx_p by central differences (phi[i+1] - phi[i-1]) / (2 h_p) in the
+  interior and the 3-point one-sided formulas
+  (-3 phi[0] + 4 phi[1] - phi[2]) / (2 h_p),
+  ( 3 phi[n-1] - 4 phi[n-2] + phi[n-3]) / (2 h_p) at the two end cells,
+  all second-order accurate (n_p >= 3; n_p = 2 uses the two-point
+  difference, n_p = 1 gives 0);
+* E = -1/2 * V_cell * sum_i m_i . h_d(xi_i) (midpoint rule, V_cell = h1 h2 h3).
+
+With phi = P m linear, E = 1/2 V m^T D P m and
+grad_m E = 1/2 V (D P m + P^T D^T m).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from .full import mode_product, apply_full, apply_adjoint
+
+
+def fd_matrix(n: int, hp: float) -> np.ndarray:
+    """1D derivative matrix D (n x n) of the stencils in the module docstring."""
+    D = np.zeros((n, n))
+    if n == 1:
+        return D
+    if n == 2:
+        D[:, 0], D[:, 1] = -1.0 / hp, 1.0 / hp
+        return D
+    for i in range(1, n - 1):
+        D[i, i - 1], D[i, i + 1] = -0.5 / hp, 0.5 / hp
+    D[0, 0:3] = np.array([-3.0, 4.0, -1.0]) / (2.0 * hp)
+    D[n - 1, n - 3:n] = np.array([1.0, -4.0, 3.0]) / (2.0 * hp)
+    return D
+
+
+def gradient(phi: np.ndarray, h) -> np.ndarray:
+    """D phi: [3, n3, n2, n1], component p = d/dx_{p+1}."""
+    phi = np.asarray(phi, dtype=np.float64)
+    n3, n2, n1 = phi.shape
+    n = (n1, n2, n3)
+    return np.stack([mode_product(phi, fd_matrix(n[p], float(h[p])), p + 1) for p in range(3)])
+
+
+def gradient_adjoint(g: np.ndarray, h) -> np.ndarray:
+    """D^T g = sum_p D_p^T g_p for a vector field g [3, n3, n2, n1]."""
+    g = np.asarray(g, dtype=np.float64)
+    _, n3, n2, n1 = g.shape
+    n = (n1, n2, n3)
+    return sum(mode_product(g[p], fd_matrix(n[p], float(h[p])).T, p + 1) for p in range(3))
+
+
+def stray_field(phi: np.ndarray, h) -> np.ndarray:
+    return -gradient(phi, h)
+
+
+def energy(m: np.ndarray, phi: np.ndarray, h) -> float:
+    """E = -1/2 V_cell sum m . h_d."""
+    V = float(h[0]) * float(h[1]) * float(h[2])
+    hd = stray_field(phi, h)
+    return -0.5 * V * float((np.asarray(m, dtype=np.float64) * hd).sum())
+
+
+def energy_from_m(m, n, h, R: int, c0: float = 2.15) -> float:
+    return energy(m, apply_full(m, n, h, R, c0), h)
+
+
+def energy_gradient(m, n, h, R: int, c0: float = 2.15) -> np.ndarray:
+    """grad_m E = 1/2 V (D P m + P^T D^T m), [3, n3, n2, n1]."""
+    V = float(h[0]) * float(h[1]) * float(h[2])
+    m = np.asarray(m, dtype=np.float64)
+    DPm = gradient(apply_full(m, n, h, R, c0), h)
+    PtDtm = apply_adjoint(gradient_adjoint(m, h), n, h, R, c0)
+    return 0.5 * V * (DPm + PtDtm)
