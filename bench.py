@@ -1,0 +1,398 @@
+#!/usr/bin/env python
+"""Benchmark of the demagnetizing operator applied as a sum of Kronecker products.
+
+Metric: demag potential applications per second.  One step is one complete
+application of the operator (all 3 components, all M = (R-1)/2 folded nodes,
+summed output) to a full-format magnetization on a 256^3 grid (R = 41, the
+vortex state with 5% noise); the same line reports the structured path on a
+batch of CP magnetizations with n = 4096 per mode (CP rank 4 per component,
+R = 61), where one application produces the CP output of rank 30*3*4.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints ONE JSON line on rank 0.  Under torchrun (N > 1) every rank runs the
+same workload independently (the operator does not shard across GPUs here:
+replicas only) and `value` is the total over ranks divided by the slowest
+rank's time.  `--impl reference` times the FP64 CPU oracle on bounded samples
+of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "demag potential apps/s at 256³ full & n=4096 CP; rel L2 err vs FP64 oracle"
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+# FP32 CUDA-core peak of a GB300: 152 SMs x 128 FP32 lanes x 2 flops (FMA) x 2.07 GHz
+FP32_SIMT_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=256, help="full-format grid edge")
+    ap.add_argument("--form", default="auto", help="auto | fp32 | fp64 | tf32x3 | bf16x3")
+    ap.add_argument("--cp-n", type=int, default=4096)
+    ap.add_argument("--cp-batch", type=int, default=256)
+    ap.add_argument("--no-oracle", action="store_true", help="skip the oracle error check and CPU baseline")
+    return ap.parse_args()
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return dict(PEAKS_FALLBACK), "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks sampled every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.file = None
+
+    def __enter__(self):
+        self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.file, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        self.file.flush()
+
+    def summary(self):
+        rows = []
+        try:
+            with open(self.file.name) as f:
+                for line in f:
+                    parts = [p.strip() for p in line.split(",")]
+                    if len(parts) >= 9:
+                        rows.append(parts)
+        finally:
+            os.unlink(self.file.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ workloads
+
+def full_config(n):
+    return (n, n, n), (1.0 / n,) * 3, 41
+
+
+def cp_config(n):
+    return (n, n, n), (1.0 / n,) * 3, 61, 4
+
+
+def make_cp_batch(n, r, batch, seed0):
+    import numpy as np
+    import synth
+    lam = np.empty((batch, 3, r), dtype=np.float32)
+    U = np.empty((batch, 3 * 3 * r * n), dtype=np.float32)
+    for b in range(batch):
+        l, u = synth.cp_inputs((n, n, n), r, seed0 + b)
+        lam[b] = l
+        U[b] = u.ravel()
+    return lam, U
+
+
+def time_region(fn, steps, stream):
+    import torch
+    start = torch.cuda.Event(enable_timing=True)
+    stop = torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    for _ in range(steps):
+        fn()
+    stop.record(stream)
+    stop.synchronize()
+    return start.elapsed_time(stop) / steps
+
+
+def run_ours(args, world, rank, local):
+    import numpy as np
+    import torch
+    import paper_1212_3509_gb300 as D
+    import synth
+
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    peaks, peak_src = load_peaks()
+
+    # ---------------- full format, 256^3
+    n3, h, R = full_config(args.n)
+    form = args.form
+    P = D.demag_build_factors(n3, h, R)
+    if form == "auto":
+        form = "fp32"
+        for cand in ("bf16x3",):
+            try:
+                D.demag_reserve_workspace(P, cand)
+                form = cand
+                break
+            except D.DemagError:
+                pass
+    D.demag_reserve_workspace(P, form)
+    m_host = synth.vortex_m(n3, 1213)
+    m = torch.from_numpy(m_host).cuda()
+    phi = torch.empty(n3[2], n3[1], n3[0], device="cuda")
+    full_fn = lambda: D.demag_apply_full(P, m, phi, form)  # noqa: E731
+    for _ in range(args.warmup):
+        full_fn()
+    torch.cuda.synchronize()
+    launches0 = D.demag_launch_count(P)
+    D.demag_profile(P, True)
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        ms_full = time_region(full_fn, args.steps, stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    D.demag_profile(P, False)
+    launches_full = (D.demag_launch_count(P) - launches0) // args.steps
+    fam = "gemm_tc" if form in ("bf16x3", "tf32x3") else "gemm_simt"
+    gemm_ms, gemm_n = D.demag_profile_read(P, fam)
+    split_ms, split_n = D.demag_profile_read(P, "split")
+    ms_full_max = max_over_ranks(ms_full, world)
+
+    M = P.M
+    flops_app = 16.0 * (args.n ** 4) * M  # 8 mode-product GEMMs of n^4 MACs per node
+    gemm_ms_app = gemm_ms / args.steps
+    achieved_tflops = flops_app / (gemm_ms_app * 1e-3) / 1e12
+    if fam == "gemm_tc":
+        peak, bound = peaks.get("bf16_tflops", PEAKS_FALLBACK["bf16_tflops"]), "tensor"
+        if form == "tf32x3":
+            peak = peak / 2.0  # TF32 dense rate is half the BF16 rate
+        peak_note = f"{peak_src} dense {'bf16' if form == 'bf16x3' else 'tf32 (bf16/2)'} burst"
+    else:
+        peak, bound = FP32_SIMT_PEAK_TFLOPS, "alu"
+        peak_note = "FP32 FMA peak from unit counts and max clock (152 SMs x 128 lanes x 2 x 2.07 GHz)"
+
+    # e2e through the public API with pinned host buffers
+    m_pin = torch.from_numpy(m_host).pin_memory()
+    phi_pin = torch.empty(phi.shape, dtype=torch.float32).pin_memory()
+    m_dev2 = torch.empty_like(m)
+
+    def e2e_fn():
+        m_dev2.copy_(m_pin, non_blocking=True)
+        D.demag_apply_full(P, m_dev2, phi, form)
+        phi_pin.copy_(phi, non_blocking=True)
+
+    for _ in range(max(1, args.warmup)):
+        e2e_fn()
+    torch.cuda.synchronize()
+    barrier(world)
+    ms_e2e = max_over_ranks(time_region(e2e_fn, args.steps, stream), world)
+
+    # ---------------- CP, n = 4096, batched
+    ncp = args.cp_n
+    cn3, ch, cR, r = cp_config(ncp)
+    B = args.cp_batch
+    PC = D.demag_build_factors(cn3, ch, cR)
+    lam_h, U_h = make_cp_batch(ncp, r, B, 1214)
+    lam = torch.from_numpy(lam_h).cuda()
+    U = torch.from_numpy(U_h).cuda()
+    Mc = PC.M
+    out_w = torch.empty(B * Mc * 3 * r, device="cuda")
+    out_U = torch.empty(B * Mc * 3 * r * 3 * ncp, device="cuda")
+    cp_fn = lambda: D.demag_apply_cp_batched(PC, B, r, lam, U, out_w, out_U)  # noqa: E731
+    for _ in range(args.warmup):
+        cp_fn()
+    torch.cuda.synchronize()
+    cl0 = D.demag_launch_count(PC)
+    D.demag_profile(PC, True)
+    barrier(world)
+    with ClockSampler(local) as clk_cp:
+        ms_cp = time_region(cp_fn, args.steps, stream)
+    D.demag_profile(PC, False)
+    launches_cp = (D.demag_launch_count(PC) - cl0) // args.steps
+    fft_ms, fft_n = D.demag_profile_read(PC, "fft")
+    ms_cp_max = max_over_ranks(ms_cp, world)
+    bytes_app = 4.0 * (9 * r * ncp + 3 * r) + 4.0 * (Mc * 3 * r * 3 * ncp + Mc * 3 * r)
+    sym_bytes = 4.0 * Mc * 2 * (ncp + 1)  # symbols of one axis per launch (all axes share n and h)
+    fft_launch_bytes = B * bytes_app / 3.0 + sym_bytes  # one launch per mode
+    fft_gbs = fft_launch_bytes / ((fft_ms / fft_n) * 1e-3) / 1e9
+    hbm = peaks.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"])
+
+    result = {
+        "metric": METRIC,
+        "value": world * 1e3 / ms_full_max,
+        "unit": "apps/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_full_max,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": {"fp32": "f32", "fp64": "f64", "tf32x3": "tf32x3 (f32 accumulate)",
+                  "bf16x3": "bf16x3 (f32 accumulate)"}[form],
+        "data": "synthetic (seeded vortex state + 5% noise; smooth random CP factors)",
+        "config": {"workload": f"full format {args.n}^3, R=41 (M=20), form {form}; "
+                               f"CP n={ncp} rank {r}/component, R=61 (M=30), batch {B}",
+                   "grid": [args.n] * 3, "R": R, "form": form, "cp_n": ncp, "cp_rank": r, "cp_R": cR,
+                   "cp_batch": B, "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (m = 201 MB at 256^3; CP batch outputs 4.5 GB)"},
+        "roofline": {"kernel": "mode-product GEMM (" + fam + ")", "bound": bound,
+                     "achieved": achieved_tflops, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved_tflops / peak, "traffic": None,
+                     "algorithmic_flops_per_app": flops_app, "launches_per_app": gemm_n / args.steps,
+                     "kernel_ms_per_app": gemm_ms_app, "peak_source": peak_note,
+                     "split_ms_per_app": split_ms / args.steps},
+        "cp": {"value": world * B * 1e3 / ms_cp_max, "unit": "apps/s", "ms_per_batch": ms_cp_max,
+               "batch": B,
+               "roofline": {"kernel": "toeplitz_fft_kernel", "bound": "hbm", "achieved": fft_gbs, "peak": hbm,
+                            "unit": "GB/s", "frac": fft_gbs / hbm, "traffic": None,
+                            "algorithmic_bytes_per_app": bytes_app, "launches_per_batch": fft_n / args.steps,
+                            "kernel_ms_per_batch": fft_ms / args.steps,
+                            "peak_source": f"{peak_src} STREAM copy"},
+               "gpu_launches": launches_cp,
+               "clocks": clk_cp.summary()},
+        "e2e": {"value": world * 1e3 / ms_e2e, "unit": "apps/s",
+                "h2d_bytes_per_step": int(m.numel() * 4), "d2h_bytes_per_step": int(phi.numel() * 4)},
+        "gpu_launches": int(launches_full),
+        "clocks": clk.summary(),
+    }
+
+    # ---------------- parity against the oracle (sampled) and CPU baseline
+    if not args.no_oracle and rank == 0:
+        from oracle import full as ofull, structured as ost
+        lines = [(0, 0), (n3[2] // 2, n3[1] // 3), (n3[2] - 1, n3[1] - 1), (n3[2] // 4, n3[1] - 7)]
+        ref = ofull.apply_full_lines(m_host, n3, h, R, lines)
+        got = phi.cpu().numpy()
+        num = sum(float(((got[i3, i2] - ref[j]) ** 2).sum()) for j, (i3, i2) in enumerate(lines))
+        den = sum(float((ref[j] ** 2).sum()) for j in range(len(lines)))
+        result["rel_l2_full"] = (num / den) ** 0.5
+        result["rel_l2_full_sample"] = f"{len(lines)} output lines phi[i3,i2,:] vs the FP64 oracle"
+        rw, rU = ost.apply_cp(lam_h[0], U_h[0], cn3, ch, cR)
+        ref_cp = np.concatenate([rU[p].ravel() for p in range(3)])
+        got_cp = out_U[: Mc * 3 * r * 3 * ncp].cpu().numpy()
+        result["cp"]["rel_l2"] = float(np.linalg.norm(got_cp - ref_cp) / np.linalg.norm(ref_cp))
+        result["cpu_baseline"] = cpu_baseline(n3, h, R, m_host, budget_s=20.0)
+    print(json.dumps(result), flush=True)
+
+
+def cpu_baseline(n3, h, R, m_host, budget_s):
+    """The FP64 oracle on the host cores, on a bounded number of nodes (scaled)."""
+    from oracle import full as ofull
+    M = (R - 1) // 2
+    t0 = time.perf_counter()
+    done = 0
+    while done < M and (time.perf_counter() - t0) < budget_s:
+        ofull.apply_full(m_host, n3, h, R, nodes=[done])
+        done += 1
+    dt = time.perf_counter() - t0
+    return {"value": (done / M) / dt, "unit": "apps/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"full format {n3[0]}^3, {done} of {M} nodes (all 3 components), scaled to one app; "
+                      f"numpy float64 with its default BLAS threads"}
+
+
+def run_reference(args, world, rank, local):
+    """The FP64 CPU oracle as it stands, timed on bounded samples (rank 0 only)."""
+    if rank != 0:
+        return
+    import synth
+    from oracle import full as ofull
+    n3, h, R = full_config(args.n)
+    M = (R - 1) // 2
+    m_host = synth.vortex_m(n3, 1213)
+    step = lambda: ofull.apply_full(m_host, n3, h, R, nodes=[0])  # noqa: E731
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = (time.perf_counter() - t0) / args.steps
+    value = (1.0 / M) / dt
+    out = {"metric": METRIC, "value": value, "unit": "apps/s", "impl": "reference", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 * M, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded vortex state)",
+           "config": {"workload": f"full format {args.n}^3, R=41 (M=20); FP64 CPU oracle", "grid": [args.n] * 3,
+                      "R": R, "parallelism": "host cores"},
+           "cpu_baseline": {"value": value, "unit": "apps/s", "cores": os.cpu_count(), "kind": "oracle",
+                            "sample": f"each step: 1 of {M} nodes of the {args.n}^3 full-format application, "
+                                      "scaled to one app"},
+           "e2e": {"value": value, "unit": "apps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_init()
+    if args.impl == "reference":
+        run_reference(args, world, rank, local)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    try:
+        run_ours(args, world, rank, local)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,228 @@
+/*
+ * demag.h -- C ABI of libdemag: the demagnetizing (scalar potential) operator
+ * of arXiv 1212.3509 (Exl, Abert, Mauser, Schrefl, Stimming, Suess, "FFT-based
+ * Kronecker product approximation to micromagnetic long-range interactions")
+ * applied as a sum of Kronecker products on one GB300 GPU (sm_103a).
+ *
+ * What is computed (paper Sec. 3, Eq. coll, Eq. pot_op, Cor. 3 Eq. kron_operator):
+ *
+ *   phi_i = c * s * sum_{k=1..M} omega_k sum_{q=1..3} sum_j
+ *                 T_{k,q,3}[i3-j3] T_{k,q,2}[i2-j2] T_{k,q,1}[i1-j1] m^(q)_j
+ *
+ *   c = 1/(2 pi^{3/2}),  T_{k,q,p} = F_k^(p) if p == q else E_k^(p),
+ *   E_k^(p)[d] = int_{(d-1/2)h}^{(d+1/2)h} exp(-tau_k^2 x^2) dx,
+ *   F_k^(p)[d] = int_{(d-1/2)h}^{(d+1/2)h} x exp(-tau_k^2 x^2) dx   (Eq. f_anal),
+ *   tau_k = sinh(k theta), omega_k = 2 theta cosh(k theta) sinh(k theta)^2,
+ *   theta = c0 ln(M)/M, R = 2M+1 symmetric sinc nodes (Thm. 1, Lemma 2).
+ *
+ * Conventions used by every entry point:
+ *  - Units: reduced (|m| = 1).  The domain is scaled so that its longest edge
+ *    is 1 before the nodes are applied (Sec. 3.4, rho <= 3); s = max_p n_p h_p
+ *    and hh_p = h_p / s are used for the generators and phi is returned in the
+ *    caller's length unit (multiplied by s).
+ *  - Sign: phi = +(1/4pi) int m.(x-y)/|x-y|^3, the sign that solves
+ *    Delta phi = div m with h_d = -grad phi (Eq. poisson, Eq. intop1); the
+ *    printed Eq. intop2 / coll / kron_operator carry the opposite sign.
+ *  - Layout: a scalar field is float [n3][n2][n1] (i1 fastest, the vec order of
+ *    the footnote to Cor. 3); a magnetization is float [3][n3][n2][n1].
+ *  - Memory: every data pointer is a DEVICE pointer owned by the caller; the
+ *    library never frees or retains it after the call returns.  The plan owns
+ *    its generators, symbols, dense factor matrices and workspace.
+ *  - Streams: `stream` is a cudaStream_t (NULL = legacy default stream).  All
+ *    compute entry points are asynchronous on that stream.
+ *  - Errors: arguments are validated before any launch; a rejected call
+ *    returns DEMAG_EINVAL (or DEMAG_EUNSUPPORTED) and launches nothing.  A
+ *    failed launch returns DEMAG_ECUDA.  The message of the last error of a
+ *    plan is returned by demag_last_error (plan may be NULL for errors raised
+ *    before a plan exists).  No entry point aborts the process.
+ *  - Threads: a plan must not be used from two host threads at once.
+ */
+#ifndef DEMAG_H
+#define DEMAG_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  DEMAG_OK = 0,
+  DEMAG_EINVAL = 1,      /* bad argument (NULL pointer, size, rank, R, c0) */
+  DEMAG_ENOMEM = 2,      /* device allocation failed */
+  DEMAG_ECUDA = 3,       /* a CUDA runtime call or launch failed */
+  DEMAG_ETIMEOUT = 4,    /* a bounded device-side wait gave up */
+  DEMAG_EUNSUPPORTED = 5 /* valid request outside this build's limits */
+} demag_status;
+
+/* Arithmetic of the full-format mode products (Sec. 2.2 Eq. modemul).
+ * FP64 / FP32: SIMT (CUDA cores).  TF32X3 / BF16X3: tcgen05 tensor cores with
+ * each operand split into a high and a low part and three products
+ * (hi*hi + hi*lo + lo*hi) accumulated in FP32. */
+typedef enum {
+  DEMAG_FP64 = 0,
+  DEMAG_FP32 = 1,
+  DEMAG_TF32X3 = 2,
+  DEMAG_BF16X3 = 3
+} demag_precision;
+
+/* Grid and quadrature (Sec. 3.1 notation; Alg. 2 signature potential(M, h, R, c0, tol)).
+ * n[p] >= 1 cells on axis p (n[0] = n1 is the fastest index), h[p] > 0 the
+ * cell edge, R = 2M+1 odd and >= 5 the number of symmetric sinc nodes,
+ * c0 > 0 the step constant (2.15 in Sec. 3.4, Fig. 1). */
+typedef struct {
+  int n[3];
+  double h[3];
+  int R;
+  double c0;
+} demag_grid_desc;
+
+typedef struct demag_plan demag_plan;
+
+/* ---- setup -------------------------------------------------------------- */
+
+/* Build a plan: sinc nodes, FP64 generators E_k^(p), F_k^(p) (Eq. f_anal,
+ * erfc/erfcx/expm1 forms), their FP32 copies, the circulant symbols of the
+ * structured path (Sec. 4.2 Eq. conv_pot / fft_pot: real FFT of the length
+ * L_p = pow2 >= 2 n_p - 1 embedding, computed in FP64) and the dense Toeplitz
+ * factor matrices of the full path (Cor. 3, U_k^(qp)).  Setup is done once
+ * per grid (Sec. 4.2: the kernel is built in a setup phase).  Allocates
+ * device memory and synchronizes `stream` before returning.
+ * On success *out receives the plan; on failure *out is set to NULL. */
+demag_status demag_build_factors(const demag_grid_desc* desc, demag_plan** out, void* stream);
+
+/* Release every device buffer the plan owns.  NULL is accepted. */
+void demag_plan_destroy(demag_plan* plan);
+
+/* Number of folded quadrature terms M = (R-1)/2 (the term count of every
+ * structured output), or -1 for a NULL plan. */
+int demag_num_terms(const demag_plan* plan);
+
+/* Text of the last error recorded on `plan` (or of the last error of a call
+ * made without a plan when plan == NULL).  Never NULL. */
+const char* demag_last_error(const demag_plan* plan);
+
+/* Copy the setup data to caller device buffers (for verification):
+ * nodes: double [3][M] = t_k, tau_k, omega_k;  generators: double
+ * [M][2][3][2*nmax-1], type 0 = E, 1 = F, entry d + n_p - 1 for
+ * d = -(n_p-1)..n_p-1 (unused tail entries of short axes are 0);
+ * symbols: float [M][2][3][Lmax/2+1], the real FFT of the circulant
+ * embedding divided by L_p (E: real part, F: imaginary part; the other part
+ * is 0 by symmetry).  Synchronous on `stream`. */
+demag_status demag_copy_nodes(const demag_plan* plan, double* dst, void* stream);
+demag_status demag_copy_generators(const demag_plan* plan, double* dst, void* stream);
+demag_status demag_copy_symbols(const demag_plan* plan, float* dst, void* stream);
+/* Sizes in elements of the three buffers above. */
+size_t demag_generators_size(const demag_plan* plan);
+size_t demag_symbols_size(const demag_plan* plan);
+
+/* ---- full format (Cor. 3, Eq. kron_operator; Sec. 2.2 Eq. modemul) -------- */
+
+/* phi = sum_q P^(q) m^(q) for a full magnetization.
+ * m: float [3][n3][n2][n1], phi: float [n3][n2][n1] (overwritten).
+ * Per node the nine mode products share work: 8 GEMMs of n^4 flops-pairs
+ * (mode 1: F m1, E m2, E m3; mode 2: E Y1 + F Y2, E Y3; mode 3 with the node
+ * sum folded into the contraction).  The first call of a precision allocates
+ * its workspace (so make it before any stream capture).  m and phi must not
+ * overlap. */
+demag_status demag_apply_full(demag_plan* plan, const float* m, float* phi,
+                              demag_precision prec, void* stream);
+
+/* Apply several plans' operators in one call: phi[i] = P_i m[i] for
+ * i < count.  Arrays of device pointers live in HOST memory.  Grids may
+ * differ in shape; every plan must already have its workspace for `prec`
+ * (made by a previous demag_apply_full or demag_reserve_workspace). */
+demag_status demag_apply_full_batched(demag_plan* const* plans, const float* const* m,
+                                      float* const* phi, int count, demag_precision prec,
+                                      void* stream);
+
+/* Allocate the full-format workspace of `prec` now (idempotent). */
+demag_status demag_reserve_workspace(demag_plan* plan, demag_precision prec);
+
+/* Adjoint: g^(q) = (P^(q))^T y for q = 1..3.  E is even and F odd in d (Sec.
+ * 4.2), so each transposed Kronecker term equals minus the term itself; the
+ * map is one field in, three fields out.  y: float [n3][n2][n1],
+ * g: float [3][n3][n2][n1] (overwritten). */
+demag_status demag_apply_adjoint(demag_plan* plan, const float* y, float* g,
+                                 demag_precision prec, void* stream);
+
+/* ---- structured formats through circulant FFTs (Sec. 4, Lemmas 4-5) ----- */
+
+/* CP input (Eq. CP, one CP tensor per component q) -> CP output
+ * (Eq. kron_eval_cp): term (k, q, l) has weight c s omega_k lambda[q][l] and
+ * factor columns T_{k,q,p} u^(q,p)_l, p = 1..3.  Every Toeplitz matvec runs as
+ * a zero-padded real FFT of length L_p, a product with the symbol and an
+ * inverse real FFT keeping the first n_p entries.
+ * lambda: float [3][r]; U: float, blocks (q, p) in order q-major, each block
+ * [r][n_p] (a column is contiguous); out_w: float [M][3][r];
+ * out_U: float, three mode blocks p = 1..3, block p = [M][3][r][n_p].
+ * r >= 1. */
+demag_status demag_apply_cp(demag_plan* plan, int r, const float* lambda, const float* U,
+                            float* out_w, float* out_U, void* stream);
+
+/* `batch` independent CP inputs in one launch: input b starts at
+ * lambda + b*3*r and U + b*3*r*(n1+n2+n3); output b at out_w + b*M*3*r and
+ * out_U + b*M*3*r*(n1+n2+n3). */
+demag_status demag_apply_cp_batched(demag_plan* plan, int batch, int r, const float* lambda,
+                                    const float* U, float* out_w, float* out_U, void* stream);
+
+/* Tucker input (Eq. tucker_rep) -> Tucker output (Eq. kron_eval_tuck): the
+ * core of component q is reused unchanged by the caller; term (k, q) has
+ * weight c s omega_k and factors T_{k,q,p} V^(q,p).
+ * r[3] >= 1 multilinear ranks; V: float blocks (q, p), each [r_p][n_p];
+ * out_w: float [M][3]; out_V: three mode blocks, block p = [M][3][r_p][n_p]. */
+demag_status demag_apply_tucker(demag_plan* plan, const int r[3], const float* V,
+                                float* out_w, float* out_V, void* stream);
+
+/* Tensor train (App. C Eq. tt_3d_1, a 3D TT is the Tucker2 tensor
+ * [[G2; G1, id, G3^T]], Eq. tt_3d_2) -> TT output: term (k, q) has weight
+ * c s omega_k and cores T_{k,q,1} G1, T_{k,q,2} G2 (each mode-2 fibre),
+ * T_{k,q,3} G3.  r[2] >= 1 TT ranks; G1: float [3][r1][n1],
+ * G2: float [3][r1*r2][n2] (fibre index a1*r2 + a2), G3: float [3][r2][n3];
+ * out_w: float [M][3]; oG1: float [M][3][r1][n1]; oG2: float [M][3][r1*r2][n2];
+ * oG3: float [M][3][r2][n3]. */
+demag_status demag_apply_tt(demag_plan* plan, const int r[2], const float* G1,
+                            const float* G2, const float* G3, float* out_w, float* oG1,
+                            float* oG2, float* oG3, void* stream);
+
+/* ---- stray field, energy and gradient (h_d = -grad phi, Sec. 1) ---------- */
+
+/* Second-order finite-difference stray field h_d = -D phi: central
+ * differences inside, 3-point one-sided at the first and last cell of each
+ * axis (two-point for n_p = 2, zero for n_p = 1).
+ * phi: float [n3][n2][n1]; hd: float [3][n3][n2][n1] (overwritten). */
+demag_status demag_stray_field(demag_plan* plan, const float* phi, float* hd, void* stream);
+
+/* Demag energy E = -1/2 h1 h2 h3 sum_i m_i . h_d,i with h_d = -D P m, and
+ * optionally its gradient dE/dm = 1/2 h1 h2 h3 (D P m + P^T D^T m).
+ * m: float [3][n3][n2][n1]; energy: one double on the device (overwritten);
+ * grad: float [3][n3][n2][n1] or NULL (energy only).  Uses `prec` for the
+ * operator applications. */
+demag_status demag_energy(demag_plan* plan, const float* m, double* energy, float* grad,
+                          demag_precision prec, void* stream);
+
+/* Read and clear the device-side status word of the plan (bounded waits that
+ * gave up set DEMAG_ETIMEOUT there).  Synchronizes `stream`. */
+demag_status demag_sync_status(demag_plan* plan, void* stream);
+
+/* ---- diagnostics (build-only; no counterpart in the paper) -------------- */
+
+/* Number of kernels the library has launched for this plan so far. */
+unsigned long long demag_launch_count(const demag_plan* plan);
+
+/* Per-kernel-family timing.  demag_profile(plan, 1) clears the record and
+ * brackets every later launch of the plan with CUDA events on its stream;
+ * demag_profile(plan, 0) stops recording.  demag_profile_read sums the
+ * recorded durations (milliseconds) and counts the launches of one family:
+ * 0 = mode-product GEMM on CUDA cores, 1 = mode-product GEMM on tensor
+ * cores, 2 = Toeplitz FFT, 3 = operand split / conversion, 4 = setup,
+ * 5 = stray field / energy, 6 = small bookkeeping kernels (term weights).
+ * Reading waits for the recorded events. */
+demag_status demag_profile(demag_plan* plan, int enable);
+demag_status demag_profile_read(demag_plan* plan, int family, double* total_ms, long long* launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DEMAG_H */

@@ -52,6 +52,11 @@ def terms(n, h, R: int, c0: float = 2.15):
     def mats(k):
         out = {}
         for p in range(3):
+            # axes with the same n and spacing have the same matrices
+            same = [r for r in range(p) if n[r] == n[p] and hh[r] == hh[p]]
+            if same:
+                out[(p, "E")], out[(p, "F")] = out[(same[0], "E")], out[(same[0], "F")]
+                continue
             out[(p, "E")] = toeplitz(gen_E(tau[k], hh[p], n[p]), n[p])
             out[(p, "F")] = toeplitz(gen_F(tau[k], hh[p], n[p]), n[p])
         return out
@@ -83,6 +88,31 @@ def apply_full(m: np.ndarray, n, h, R: int, c0: float = 2.15, nodes=None) -> np.
                 X = mode_product(X, T[(p, factor_kind(p, q))], p + 1)
             phi += omega[k] * X
     return (C_POT * s) * phi
+
+
+def apply_full_lines(m: np.ndarray, n, h, R: int, lines, c0: float = 2.15) -> np.ndarray:
+    """phi[i3, i2, :] for a list of (i3, i2) pairs, without forming all of phi.
+
+    Same sum as apply_full (Eq. kron_operator), with the mode-3 and mode-2
+    products restricted to the requested output rows:
+    phi[i3, i2, :] = c s sum_k omega_k sum_q U^(q1) (sum_{j3, j2} U^(q3)[i3, j3] U^(q2)[i2, j2] m^(q)[j3, j2, :]).
+    Returns float64 [len(lines), n1].
+    """
+    n = tuple(int(v) for v in n)
+    m = np.asarray(m, dtype=np.float64)
+    s, omega, mats = terms(n, h, R, c0)
+    out = np.zeros((len(lines), n[0]))
+    for k in range(len(omega)):
+        T = mats(k)
+        for q in range(3):
+            U1 = T[(0, factor_kind(0, q))]
+            U2 = T[(1, factor_kind(1, q))]
+            U3 = T[(2, factor_kind(2, q))]
+            for idx, (i3, i2) in enumerate(lines):
+                w = np.tensordot(U3[i3], m[q], axes=([0], [0]))  # [n2, n1]
+                w = U2[i2] @ w                                    # [n1]
+                out[idx] += omega[k] * (U1 @ w)
+    return (C_POT * s) * out
 
 
 def apply_adjoint(y: np.ndarray, n, h, R: int, c0: float = 2.15) -> np.ndarray:

@@ -1,0 +1,270 @@
+"""ctypes binding of libdemag (include/demag.h).
+
+Argument marshalling only: every step of the operator runs in the CUDA
+library.  Functions carry the C names; tensors are PyTorch CUDA tensors of
+the documented dtype and size (contiguous), or raw integer device pointers.
+The library must have been built (``paper_1212_3509_gb300.build.build()``);
+importing this module without it raises immediately.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "lib", "libdemag.so")
+
+PRECISIONS = {"fp64": 0, "fp32": 1, "tf32x3": 2, "bf16x3": 3}
+STATUS = {0: "DEMAG_OK", 1: "DEMAG_EINVAL", 2: "DEMAG_ENOMEM", 3: "DEMAG_ECUDA",
+          4: "DEMAG_ETIMEOUT", 5: "DEMAG_EUNSUPPORTED"}
+
+
+class DemagError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class GridDesc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int * 3), ("h", ctypes.c_double * 3), ("R", ctypes.c_int), ("c0", ctypes.c_double)]
+
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libdemag is not built ({LIB_PATH} missing); run paper_1212_3509_gb300.build.build()")
+
+lib = ctypes.CDLL(LIB_PATH)
+
+_vp, _i, _sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
+_SIGS = {
+    "demag_build_factors": (_i, [ctypes.POINTER(GridDesc), ctypes.POINTER(_vp), _vp]),
+    "demag_plan_destroy": (None, [_vp]),
+    "demag_num_terms": (_i, [_vp]),
+    "demag_last_error": (ctypes.c_char_p, [_vp]),
+    "demag_copy_nodes": (_i, [_vp, _vp, _vp]),
+    "demag_copy_generators": (_i, [_vp, _vp, _vp]),
+    "demag_copy_symbols": (_i, [_vp, _vp, _vp]),
+    "demag_generators_size": (_sz, [_vp]),
+    "demag_symbols_size": (_sz, [_vp]),
+    "demag_apply_full": (_i, [_vp, _vp, _vp, _i, _vp]),
+    "demag_apply_full_batched": (_i, [ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i, _i, _vp]),
+    "demag_reserve_workspace": (_i, [_vp, _i]),
+    "demag_apply_adjoint": (_i, [_vp, _vp, _vp, _i, _vp]),
+    "demag_apply_cp": (_i, [_vp, _i, _vp, _vp, _vp, _vp, _vp]),
+    "demag_apply_cp_batched": (_i, [_vp, _i, _i, _vp, _vp, _vp, _vp, _vp]),
+    "demag_apply_tucker": (_i, [_vp, ctypes.POINTER(_i), _vp, _vp, _vp, _vp]),
+    "demag_apply_tt": (_i, [_vp, ctypes.POINTER(_i), _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "demag_stray_field": (_i, [_vp, _vp, _vp, _vp]),
+    "demag_energy": (_i, [_vp, _vp, _vp, _vp, _i, _vp]),
+    "demag_sync_status": (_i, [_vp, _vp]),
+    "demag_launch_count": (ctypes.c_ulonglong, [_vp]),
+    "demag_profile": (_i, [_vp, _i]),
+    "demag_profile_read": (_i, [_vp, _i, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]),
+}
+
+FAMILIES = {"gemm_simt": 0, "gemm_tc": 1, "fft": 2, "split": 3, "setup": 4, "energy": 5, "misc": 6}
+for _name, (_res, _args) in _SIGS.items():
+    _f = getattr(lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+
+def _check(status: int, plan_ptr=None):
+    if status != 0:
+        msg = lib.demag_last_error(plan_ptr).decode(errors="replace")
+        raise DemagError(status, msg)
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _ptr(t, numel=None, dtype=None, name="tensor"):
+    """Device pointer of a tensor (validated) or an int passed through."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    import torch
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name} must have dtype {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} must have {numel} elements, got {t.numel()}")
+    return t.data_ptr()
+
+
+def _prec(p):
+    if isinstance(p, int):
+        return p
+    return PRECISIONS[p.lower()]
+
+
+class Plan:
+    """Owns a demag_plan*.  Attributes mirror demag_grid_desc; M = (R-1)/2."""
+
+    def __init__(self, ptr: int, n, h, R: int, c0: float):
+        self.ptr = ptr
+        self.n = tuple(int(v) for v in n)
+        self.h = tuple(float(v) for v in h)
+        self.R, self.c0 = int(R), float(c0)
+        self.M = lib.demag_num_terms(ptr)
+
+    @property
+    def N(self):
+        return self.n[0] * self.n[1] * self.n[2]
+
+    def close(self):
+        if self.ptr:
+            lib.demag_plan_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def demag_build_factors(n, h, R: int, c0: float = 2.15, stream=None) -> Plan:
+    d = GridDesc((ctypes.c_int * 3)(*[int(v) for v in n]), (ctypes.c_double * 3)(*[float(v) for v in h]), int(R), float(c0))
+    out = _vp()
+    _check(lib.demag_build_factors(ctypes.byref(d), ctypes.byref(out), _stream(stream)))
+    return Plan(out.value, n, h, R, c0)
+
+
+def demag_plan_destroy(plan: Plan):
+    plan.close()
+
+
+def demag_num_terms(plan: Plan) -> int:
+    return lib.demag_num_terms(plan.ptr)
+
+
+def demag_last_error(plan: Plan | None = None) -> str:
+    return lib.demag_last_error(plan.ptr if plan else None).decode(errors="replace")
+
+
+def demag_generators_size(plan: Plan) -> int:
+    return lib.demag_generators_size(plan.ptr)
+
+
+def demag_symbols_size(plan: Plan) -> int:
+    return lib.demag_symbols_size(plan.ptr)
+
+
+def demag_copy_nodes(plan: Plan, dst, stream=None):
+    import torch
+    _check(lib.demag_copy_nodes(plan.ptr, _ptr(dst, 3 * plan.M, torch.float64, "dst"), _stream(stream)), plan.ptr)
+
+
+def demag_copy_generators(plan: Plan, dst, stream=None):
+    import torch
+    _check(lib.demag_copy_generators(plan.ptr, _ptr(dst, demag_generators_size(plan), torch.float64, "dst"),
+                                     _stream(stream)), plan.ptr)
+
+
+def demag_copy_symbols(plan: Plan, dst, stream=None):
+    import torch
+    _check(lib.demag_copy_symbols(plan.ptr, _ptr(dst, demag_symbols_size(plan), torch.float32, "dst"),
+                                  _stream(stream)), plan.ptr)
+
+
+def demag_apply_full(plan: Plan, m, phi, precision="fp32", stream=None):
+    import torch
+    _check(lib.demag_apply_full(plan.ptr, _ptr(m, 3 * plan.N, torch.float32, "m"),
+                                _ptr(phi, plan.N, torch.float32, "phi"), _prec(precision), _stream(stream)), plan.ptr)
+
+
+def demag_apply_full_batched(plans, ms, phis, precision="bf16x3", stream=None):
+    import torch
+    cnt = len(plans)
+    P = (_vp * cnt)(*[p.ptr for p in plans])
+    Mp = (_vp * cnt)(*[_ptr(m, 3 * p.N, torch.float32, "m") for m, p in zip(ms, plans)])
+    Fp = (_vp * cnt)(*[_ptr(f, p.N, torch.float32, "phi") for f, p in zip(phis, plans)])
+    _check(lib.demag_apply_full_batched(P, Mp, Fp, cnt, _prec(precision), _stream(stream)))
+
+
+def demag_reserve_workspace(plan: Plan, precision="fp32"):
+    _check(lib.demag_reserve_workspace(plan.ptr, _prec(precision)), plan.ptr)
+
+
+def demag_apply_adjoint(plan: Plan, y, g, precision="fp32", stream=None):
+    import torch
+    _check(lib.demag_apply_adjoint(plan.ptr, _ptr(y, plan.N, torch.float32, "y"),
+                                   _ptr(g, 3 * plan.N, torch.float32, "g"), _prec(precision), _stream(stream)), plan.ptr)
+
+
+def demag_apply_cp(plan: Plan, r: int, lam, U, out_w, out_U, stream=None):
+    demag_apply_cp_batched(plan, 1, r, lam, U, out_w, out_U, stream)
+
+
+def demag_apply_cp_batched(plan: Plan, batch: int, r: int, lam, U, out_w, out_U, stream=None):
+    import torch
+    ns = sum(plan.n)
+    f32 = torch.float32
+    _check(lib.demag_apply_cp_batched(plan.ptr, int(batch), int(r), _ptr(lam, batch * 3 * r, f32, "lambda"),
+                                      _ptr(U, batch * 3 * r * ns, f32, "U"),
+                                      _ptr(out_w, batch * plan.M * 3 * r, f32, "out_w"),
+                                      _ptr(out_U, batch * plan.M * 3 * r * ns, f32, "out_U"), _stream(stream)), plan.ptr)
+
+
+def demag_apply_tucker(plan: Plan, ranks, V, out_w, out_V, stream=None):
+    import torch
+    r = (_i * 3)(*[int(v) for v in ranks])
+    tot = sum(int(ranks[p]) * plan.n[p] for p in range(3))
+    f32 = torch.float32
+    _check(lib.demag_apply_tucker(plan.ptr, r, _ptr(V, 3 * tot, f32, "V"), _ptr(out_w, plan.M * 3, f32, "out_w"),
+                                  _ptr(out_V, plan.M * 3 * tot, f32, "out_V"), _stream(stream)), plan.ptr)
+
+
+def demag_apply_tt(plan: Plan, ranks, G1, G2, G3, out_w, oG1, oG2, oG3, stream=None):
+    import torch
+    r1, r2 = int(ranks[0]), int(ranks[1])
+    n1, n2, n3 = plan.n
+    M = plan.M
+    f32 = torch.float32
+    r = (_i * 2)(r1, r2)
+    _check(lib.demag_apply_tt(plan.ptr, r, _ptr(G1, 3 * r1 * n1, f32, "G1"), _ptr(G2, 3 * r1 * r2 * n2, f32, "G2"),
+                              _ptr(G3, 3 * r2 * n3, f32, "G3"), _ptr(out_w, M * 3, f32, "out_w"),
+                              _ptr(oG1, M * 3 * r1 * n1, f32, "oG1"), _ptr(oG2, M * 3 * r1 * r2 * n2, f32, "oG2"),
+                              _ptr(oG3, M * 3 * r2 * n3, f32, "oG3"), _stream(stream)), plan.ptr)
+
+
+def demag_stray_field(plan: Plan, phi, hd, stream=None):
+    import torch
+    _check(lib.demag_stray_field(plan.ptr, _ptr(phi, plan.N, torch.float32, "phi"),
+                                 _ptr(hd, 3 * plan.N, torch.float32, "hd"), _stream(stream)), plan.ptr)
+
+
+def demag_energy(plan: Plan, m, energy, grad=None, precision="fp32", stream=None):
+    import torch
+    _check(lib.demag_energy(plan.ptr, _ptr(m, 3 * plan.N, torch.float32, "m"), _ptr(energy, 1, torch.float64, "energy"),
+                            _ptr(grad, 3 * plan.N, torch.float32, "grad"), _prec(precision), _stream(stream)), plan.ptr)
+
+
+def demag_sync_status(plan: Plan, stream=None):
+    _check(lib.demag_sync_status(plan.ptr, _stream(stream)), plan.ptr)
+
+
+def demag_launch_count(plan: Plan) -> int:
+    return int(lib.demag_launch_count(plan.ptr))
+
+
+def demag_profile(plan: Plan, enable: bool):
+    _check(lib.demag_profile(plan.ptr, 1 if enable else 0), plan.ptr)
+
+
+def demag_profile_read(plan: Plan, family) -> tuple:
+    """(total milliseconds, launches) recorded for a kernel family (name or id)."""
+    fam = FAMILIES[family] if isinstance(family, str) else int(family)
+    ms, cnt = ctypes.c_double(), ctypes.c_longlong()
+    _check(lib.demag_profile_read(plan.ptr, fam, ctypes.byref(ms), ctypes.byref(cnt)), plan.ptr)
+    return ms.value, cnt.value

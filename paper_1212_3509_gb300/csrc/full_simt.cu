@@ -1,0 +1,439 @@
+// Full format: the Kronecker operator by chained mode products on CUDA cores.
+//
+// Cor. 3 (Eq. kron_operator) with the mode product of Sec. 2.2 (Eq. modemul):
+// per node k and component q the three Toeplitz factors act along i1, i2, i3.
+// Per node the nine products share work (8 GEMMs of n^4 multiply-adds):
+//   mode 1:  Y1 = m1 x_1 F,  Y2 = m2 x_1 E,  Y3 = m3 x_1 E
+//   mode 2:  U = Y1 x_2 E + Y2 x_2 F,  V = Y3 x_2 E
+//   mode 3:  phi = sum_k (U_k x_3 S_k E + V_k x_3 S_k F),  S_k = c s omega_k
+// and the node sum of the last stage is one contraction of length 2 n3 M.
+//
+// Every stage is a "TN" GEMM whose output is stored transposed:
+//   C[a][row] = alpha * sum_pairs sum_kk A[row][kk] * B[a][kk],
+// A = the field with its contraction index contiguous, B = the n x n factor.
+// Storing [a][row] rotates the axes (i3,i2,i1) -> (i1,i3,i2) -> (i2,i1,i3) ->
+// (i3,i2,i1), so every stage reads its contraction index contiguously and the
+// final stage writes phi in [i3][i2][i1] order.  The same kernel serves the
+// adjoint (one field in, three out) and the FP64 form.
+#include <vector>
+
+#include "internal.h"
+
+namespace demag {
+
+constexpr int kMaxJobs = 64;
+constexpr int kMaxPairs = 2 * kMaxTerms + 8;
+
+struct GemmJob {
+  int rows, ncol, K;
+  int lda, ldb, ldc;
+  int pair0, npairs;
+  int tiles_m, tiles_n, tile0;
+  float alpha;
+  void* C;
+};
+
+struct GemmBatch {
+  int njobs, total_tiles;
+  GemmJob jobs[kMaxJobs];
+  const void* A[kMaxPairs];
+  const void* B[kMaxPairs];
+};
+
+template <typename T> struct SimtCfg;
+template <> struct SimtCfg<float> { static constexpr int TM = 8, BK = 8; };
+template <> struct SimtCfg<double> { static constexpr int TM = 4, BK = 8; };
+
+// 256 threads as 16 x 16; each thread owns TM rows x TM columns of the tile.
+template <typename T>
+__global__ void __launch_bounds__(256) gemm_tn_kernel(const __grid_constant__ GemmBatch batch) {
+  constexpr int TM = SimtCfg<T>::TM, BK = SimtCfg<T>::BK;
+  constexpr int BM = 16 * TM, BN = 16 * TM;
+  constexpr int LA = BM * BK / 256;  // elements each thread loads per operand
+  __shared__ T As[2][BK][BM + 4];  // +4: conflict-free transposed stores
+  __shared__ T Bs[2][BK][BN + 4];
+
+  int tile = blockIdx.x;
+  int j = 0;
+  while (j + 1 < batch.njobs && tile >= batch.jobs[j + 1].tile0) ++j;
+  const GemmJob& J = batch.jobs[j];
+  tile -= J.tile0;
+  const int tm = tile % J.tiles_m, tn = tile / J.tiles_m;
+  const int row0 = tm * BM, col0 = tn * BN;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+
+  T acc[TM][TM];
+#pragma unroll
+  for (int a = 0; a < TM; ++a)
+#pragma unroll
+    for (int b = 0; b < TM; ++b) acc[a][b] = (T)0;
+
+  const int nk = (J.K + BK - 1) / BK;
+  const int steps = nk * J.npairs;
+  T ra[LA], rb[LA];
+
+  auto load = [&](int step) {
+    const int pr = J.pair0 + step / nk;
+    const int k0 = (step % nk) * BK;
+    const T* A = (const T*)batch.A[pr];
+    const T* B = (const T*)batch.B[pr];
+#pragma unroll
+    for (int i = 0; i < LA; ++i) {
+      int idx = threadIdx.x + i * 256;
+      int r = idx / BK, kk = idx % BK;
+      int gk = k0 + kk;
+      int gr = row0 + r, gc = col0 + r;
+      ra[i] = (gr < J.rows && gk < J.K) ? A[(long)gr * J.lda + gk] : (T)0;
+      rb[i] = (gc < J.ncol && gk < J.K) ? B[(long)gc * J.ldb + gk] : (T)0;
+    }
+  };
+  auto store = [&](int buf) {
+#pragma unroll
+    for (int i = 0; i < LA; ++i) {
+      int idx = threadIdx.x + i * 256;
+      int r = idx / BK, kk = idx % BK;
+      As[buf][kk][r] = ra[i];
+      Bs[buf][kk][r] = rb[i];
+    }
+  };
+
+  if (steps > 0) {
+    load(0);
+    store(0);
+  }
+  __syncthreads();
+  for (int s = 0; s < steps; ++s) {
+    const int cur = s & 1;
+    if (s + 1 < steps) load(s + 1);
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      T av[TM], bv[TM];
+#pragma unroll
+      for (int a = 0; a < TM / 2; ++a) {
+        av[a] = As[cur][kk][tx * (TM / 2) + a];
+        av[a + TM / 2] = As[cur][kk][BM / 2 + tx * (TM / 2) + a];
+        bv[a] = Bs[cur][kk][ty * (TM / 2) + a];
+        bv[a + TM / 2] = Bs[cur][kk][BN / 2 + ty * (TM / 2) + a];
+      }
+#pragma unroll
+      for (int a = 0; a < TM; ++a)
+#pragma unroll
+        for (int b = 0; b < TM; ++b) acc[a][b] += av[a] * bv[b];
+    }
+    if (s + 1 < steps) store(cur ^ 1);
+    __syncthreads();
+  }
+
+  T* C = (T*)J.C;
+  const T alpha = (T)J.alpha;
+#pragma unroll
+  for (int b = 0; b < TM; ++b) {
+    const int gc = col0 + (b < TM / 2 ? ty * (TM / 2) + b : BN / 2 + ty * (TM / 2) + b - TM / 2);
+    if (gc >= J.ncol) continue;
+#pragma unroll
+    for (int a = 0; a < TM; ++a) {
+      const int gr = row0 + (a < TM / 2 ? tx * (TM / 2) + a : BM / 2 + tx * (TM / 2) + a - TM / 2);
+      if (gr < J.rows) C[(long)gc * J.ldc + gr] = alpha * acc[a][b];
+    }
+  }
+}
+
+// ---------------------------------------------------------------- host side
+
+class BatchBuilder {
+ public:
+  BatchBuilder() { b_.njobs = 0; b_.total_tiles = 0; npairs_ = 0; }
+  void add(int rows, int ncol, int K, int lda, int ldb, int ldc, void* C, float alpha,
+           const std::vector<std::pair<const void*, const void*>>& pairs, int bm) {
+    GemmJob& J = b_.jobs[b_.njobs++];
+    J.rows = rows; J.ncol = ncol; J.K = K;
+    J.lda = lda; J.ldb = ldb; J.ldc = ldc;
+    J.pair0 = npairs_;
+    J.npairs = (int)pairs.size();
+    for (auto& pr : pairs) {
+      b_.A[npairs_] = pr.first;
+      b_.B[npairs_] = pr.second;
+      ++npairs_;
+    }
+    J.tiles_m = (rows + bm - 1) / bm;
+    J.tiles_n = (ncol + bm - 1) / bm;
+    J.tile0 = b_.total_tiles;
+    J.alpha = alpha;
+    J.C = C;
+    b_.total_tiles += J.tiles_m * J.tiles_n;
+  }
+  const GemmBatch& get() const { return b_; }
+
+ private:
+  GemmBatch b_;
+  int npairs_;
+};
+
+template <typename T>
+static cudaError_t launch_batch(demag_plan* P, const GemmBatch& b, cudaStream_t st) {
+  if (b.total_tiles == 0) return cudaSuccess;
+  DEMAG_LAUNCH(P, kFamGemmSimt, st, gemm_tn_kernel<T><<<b.total_tiles, 256, 0, st>>>(b));
+  return cudaGetLastError();
+}
+
+// T[k][type][axis] blocks: n_p x n_p row-major, T[i][j] = gen[i-j+n_p-1],
+// axis-3 blocks multiplied by S_k = c s omega_k.
+template <typename T>
+__global__ void dense_factor_kernel(int M, int glen, int n0, int n1, int n2, size_t tgroup, size_t off1,
+                                    size_t off2, const double* gen, const double* scale, T* out) {
+  const size_t total = (size_t)M * 2 * tgroup;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    size_t e = idx % tgroup;
+    size_t kt = idx / tgroup;  // k*2 + type
+    int axis, n;
+    size_t local;
+    if (e < off1) { axis = 0; n = n0; local = e; }
+    else if (e < off2) { axis = 1; n = n1; local = e - off1; }
+    else { axis = 2; n = n2; local = e - off2; }
+    int i = (int)(local / n), jj = (int)(local % n);
+    double v = gen[(kt * 3 + axis) * glen + (i - jj + n - 1)];
+    if (axis == 2) v *= scale[kt / 2];
+    out[idx] = (T)v;
+  }
+}
+
+template <typename T>
+static const T* factor(const demag_plan* P, const T* base, int k, int type, int axis) {
+  return base + ((size_t)k * 2 + type) * P->tgroup + P->toff[axis];
+}
+
+demag_status ensure_dense_factors(demag_plan* P, demag_precision prec, cudaStream_t st) {
+  const size_t total = (size_t)P->M * 2 * P->tgroup;
+  int blocks = (int)((total + 255) / 256);
+  if (blocks > 152 * 64) blocks = 152 * 64;
+  if (prec == DEMAG_FP64) {
+    if (P->T64) return DEMAG_OK;
+    DEMAG_CUDA(P, cudaMalloc(&P->T64, sizeof(double) * total));
+    DEMAG_LAUNCH(P, kFamSetup, st,
+                 dense_factor_kernel<double><<<blocks, 256, 0, st>>>(P->M, P->glen, P->n[0], P->n[1], P->n[2],
+                                                                     P->tgroup, P->toff[1], P->toff[2], P->gen64,
+                                                                     P->scale, P->T64));
+  } else {
+    if (P->T32) return DEMAG_OK;
+    DEMAG_CUDA(P, cudaMalloc(&P->T32, sizeof(float) * total));
+    DEMAG_LAUNCH(P, kFamSetup, st,
+                 dense_factor_kernel<float><<<blocks, 256, 0, st>>>(P->M, P->glen, P->n[0], P->n[1], P->n[2],
+                                                                    P->tgroup, P->toff[1], P->toff[2], P->gen64,
+                                                                    P->scale, P->T32));
+  }
+  DEMAG_LAUNCHED(P, "dense_factor_kernel");
+  return DEMAG_OK;
+}
+
+size_t workspace_bytes(const demag_plan* P, demag_precision prec) {
+  const size_t N = field_size(P);
+  if (prec == DEMAG_TF32X3 || prec == DEMAG_BF16X3) return tc_workspace_bytes(P, prec);
+  // forward: Y (3 fields) + U,V per node; adjoint: Y (2) + 3 per node.
+  // FP64 also keeps double copies of the input and output fields (3 + 3).
+  size_t fields = 3 * (size_t)P->M + 3;
+  if (prec == DEMAG_FP64) fields += 6;
+  return fields * N * (prec == DEMAG_FP64 ? sizeof(double) : sizeof(float));
+}
+
+demag_status ensure_workspace(demag_plan* P, demag_precision prec) {
+  demag::Workspace& w = P->ws[prec];
+  const size_t need = workspace_bytes(P, prec);
+  if (w.base && w.bytes >= need) return DEMAG_OK;
+  if (w.base) cudaFree(w.base);
+  w.base = nullptr;
+  w.bytes = 0;
+  cudaError_t e = cudaMalloc(&w.base, need);
+  if (e != cudaSuccess) return cuda_error(P, e, "workspace allocation");
+  w.bytes = need;
+  return DEMAG_OK;
+}
+
+template <typename T>
+__global__ void convert_kernel(const float* in, T* out, size_t count) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
+    out[i] = (T)in[i];
+}
+__global__ void narrow_kernel(const double* in, float* out, size_t count) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
+    out[i] = (float)in[i];
+}
+
+// forward: m (3 fields, type T) -> phi (type T) using workspace `ws` of type T
+template <typename T>
+static demag_status simt_forward(demag_plan* P, const T* m, T* phi, const T* Tm, T* ws, cudaStream_t st) {
+  constexpr int BM = 16 * SimtCfg<T>::TM;
+  const int n1 = P->n[0], n2 = P->n[1], n3 = P->n[2];
+  const size_t N = field_size(P);
+  T* Y = ws;                 // 3 fields
+  T* UV = ws + 3 * N;        // [M][2] fields
+  const int M = P->M;
+  for (int k = 0; k < M; ++k) {
+    BatchBuilder b1;
+    for (int q = 0; q < 3; ++q) {
+      const T* B = factor(P, Tm, k, q == 0 ? 1 : 0, 0);
+      b1.add(n3 * n2, n1, n1, n1, n1, n3 * n2, Y + q * N, 1.f, {{m + q * N, B}}, BM);
+    }
+    cudaError_t e = launch_batch<T>(P, b1.get(), st);
+    if (e != cudaSuccess) return cuda_error(P, e, "gemm_tn_kernel (mode 1)");
+    BatchBuilder b2;
+    const T* E2 = factor(P, Tm, k, 0, 1);
+    const T* F2 = factor(P, Tm, k, 1, 1);
+    b2.add(n1 * n3, n2, n2, n2, n2, n1 * n3, UV + (2 * k) * N, 1.f, {{Y, E2}, {Y + N, F2}}, BM);
+    b2.add(n1 * n3, n2, n2, n2, n2, n1 * n3, UV + (2 * k + 1) * N, 1.f, {{Y + 2 * N, E2}}, BM);
+    e = launch_batch<T>(P, b2.get(), st);
+    if (e != cudaSuccess) return cuda_error(P, e, "gemm_tn_kernel (mode 2)");
+  }
+  BatchBuilder b3;
+  std::vector<std::pair<const void*, const void*>> pairs;
+  for (int k = 0; k < M; ++k) {
+    pairs.push_back({UV + (2 * k) * N, factor(P, Tm, k, 0, 2)});
+    pairs.push_back({UV + (2 * k + 1) * N, factor(P, Tm, k, 1, 2)});
+  }
+  b3.add(n2 * n1, n3, n3, n3, n3, n2 * n1, phi, 1.f, pairs, BM);
+  cudaError_t e = launch_batch<T>(P, b3.get(), st);
+  if (e != cudaSuccess) return cuda_error(P, e, "gemm_tn_kernel (mode 3)");
+  return DEMAG_OK;
+}
+
+// adjoint: y (1 field) -> g (3 fields): g^(q) = -P^(q) y
+template <typename T>
+static demag_status simt_adjoint(demag_plan* P, const T* y, T* g, const T* Tm, T* ws, cudaStream_t st) {
+  constexpr int BM = 16 * SimtCfg<T>::TM;
+  const int n1 = P->n[0], n2 = P->n[1], n3 = P->n[2];
+  const size_t N = field_size(P);
+  T* Y = ws;            // 2 fields: F1 y, E1 y
+  T* Z = ws + 2 * N;    // [M][3]
+  const int M = P->M;
+  for (int k = 0; k < M; ++k) {
+    BatchBuilder b1;
+    b1.add(n3 * n2, n1, n1, n1, n1, n3 * n2, Y, 1.f, {{y, factor(P, Tm, k, 1, 0)}}, BM);
+    b1.add(n3 * n2, n1, n1, n1, n1, n3 * n2, Y + N, 1.f, {{y, factor(P, Tm, k, 0, 0)}}, BM);
+    cudaError_t e = launch_batch<T>(P, b1.get(), st);
+    if (e != cudaSuccess) return cuda_error(P, e, "gemm_tn_kernel (adjoint mode 1)");
+    BatchBuilder b2;
+    const T* E2 = factor(P, Tm, k, 0, 1);
+    const T* F2 = factor(P, Tm, k, 1, 1);
+    b2.add(n1 * n3, n2, n2, n2, n2, n1 * n3, Z + (3 * k) * N, 1.f, {{Y, E2}}, BM);
+    b2.add(n1 * n3, n2, n2, n2, n2, n1 * n3, Z + (3 * k + 1) * N, 1.f, {{Y + N, F2}}, BM);
+    b2.add(n1 * n3, n2, n2, n2, n2, n1 * n3, Z + (3 * k + 2) * N, 1.f, {{Y + N, E2}}, BM);
+    e = launch_batch<T>(P, b2.get(), st);
+    if (e != cudaSuccess) return cuda_error(P, e, "gemm_tn_kernel (adjoint mode 2)");
+  }
+  BatchBuilder b3;
+  for (int q = 0; q < 3; ++q) {
+    std::vector<std::pair<const void*, const void*>> pairs;
+    for (int k = 0; k < M; ++k) pairs.push_back({Z + (3 * k + q) * N, factor(P, Tm, k, q == 2 ? 1 : 0, 2)});
+    b3.add(n2 * n1, n3, n3, n3, n3, n2 * n1, g + q * N, -1.f, pairs, BM);
+  }
+  cudaError_t e = launch_batch<T>(P, b3.get(), st);
+  if (e != cudaSuccess) return cuda_error(P, e, "gemm_tn_kernel (adjoint mode 3)");
+  return DEMAG_OK;
+}
+
+static int conv_blocks(size_t count) {
+  size_t b = (count + 255) / 256;
+  return (int)(b > 152 * 32 ? 152 * 32 : b);
+}
+
+demag_status full_forward(demag_plan* P, const float* m, float* phi, demag_precision prec, cudaStream_t st) {
+  if (prec == DEMAG_TF32X3 || prec == DEMAG_BF16X3) return tc_forward(P, m, phi, prec, st);
+  demag_status s = ensure_dense_factors(P, prec, st);
+  if (s != DEMAG_OK) return s;
+  s = ensure_workspace(P, prec);
+  if (s != DEMAG_OK) return s;
+  const size_t N = field_size(P);
+  if (prec == DEMAG_FP32) return simt_forward<float>(P, m, phi, P->T32, (float*)P->ws[prec].base, st);
+  double* ws = (double*)P->ws[prec].base;
+  double* m64 = ws + (3 * (size_t)P->M + 3) * N;
+  double* phi64 = m64 + 3 * N;
+  DEMAG_LAUNCH(P, kFamSplit, st, convert_kernel<double><<<conv_blocks(3 * N), 256, 0, st>>>(m, m64, 3 * N));
+  DEMAG_LAUNCHED(P, "convert_kernel");
+  s = simt_forward<double>(P, m64, phi64, P->T64, ws, st);
+  if (s != DEMAG_OK) return s;
+  DEMAG_LAUNCH(P, kFamSplit, st, narrow_kernel<<<conv_blocks(N), 256, 0, st>>>(phi64, phi, N));
+  DEMAG_LAUNCHED(P, "narrow_kernel");
+  return DEMAG_OK;
+}
+
+demag_status full_adjoint(demag_plan* P, const float* y, float* g, demag_precision prec, cudaStream_t st) {
+  if (prec == DEMAG_TF32X3 || prec == DEMAG_BF16X3) return tc_adjoint(P, y, g, prec, st);
+  demag_status s = ensure_dense_factors(P, prec, st);
+  if (s != DEMAG_OK) return s;
+  s = ensure_workspace(P, prec);
+  if (s != DEMAG_OK) return s;
+  const size_t N = field_size(P);
+  if (prec == DEMAG_FP32) return simt_adjoint<float>(P, y, g, P->T32, (float*)P->ws[prec].base, st);
+  double* ws = (double*)P->ws[prec].base;
+  double* y64 = ws + (3 * (size_t)P->M + 3) * N;
+  double* g64 = y64 + 3 * N;
+  DEMAG_LAUNCH(P, kFamSplit, st, convert_kernel<double><<<conv_blocks(N), 256, 0, st>>>(y, y64, N));
+  DEMAG_LAUNCHED(P, "convert_kernel");
+  s = simt_adjoint<double>(P, y64, g64, P->T64, ws, st);
+  if (s != DEMAG_OK) return s;
+  DEMAG_LAUNCH(P, kFamSplit, st, narrow_kernel<<<conv_blocks(3 * N), 256, 0, st>>>(g64, g, 3 * N));
+  DEMAG_LAUNCHED(P, "narrow_kernel");
+  return DEMAG_OK;
+}
+
+static demag_status check_prec(demag_plan* P, demag_precision prec, const char* what) {
+  if ((int)prec < 0 || (int)prec > 3) return set_error(P, DEMAG_EINVAL, "%s: unknown precision %d", what, (int)prec);
+  return DEMAG_OK;
+}
+
+}  // namespace demag
+
+using namespace demag;
+
+extern "C" demag_status demag_reserve_workspace(demag_plan* P, demag_precision prec) {
+  if (!P) return set_error(nullptr, DEMAG_EINVAL, "demag_reserve_workspace: plan is NULL");
+  demag_status s = check_prec(P, prec, "demag_reserve_workspace");
+  if (s != DEMAG_OK) return s;
+  if (prec == DEMAG_TF32X3 || prec == DEMAG_BF16X3) {
+    s = tc_prepare(P, prec, 0);
+    if (s != DEMAG_OK) return s;
+  } else {
+    s = ensure_dense_factors(P, prec, 0);
+    if (s != DEMAG_OK) return s;
+  }
+  s = ensure_workspace(P, prec);
+  if (s != DEMAG_OK) return s;
+  DEMAG_CUDA(P, cudaDeviceSynchronize());
+  return DEMAG_OK;
+}
+
+extern "C" demag_status demag_apply_full(demag_plan* P, const float* m, float* phi, demag_precision prec,
+                                         void* stream) {
+  if (!P) return set_error(nullptr, DEMAG_EINVAL, "demag_apply_full: plan is NULL");
+  demag_status s = check_prec(P, prec, "demag_apply_full");
+  if (s != DEMAG_OK) return s;
+  if (!m || !phi) return set_error(P, DEMAG_EINVAL, "demag_apply_full: NULL pointer");
+  return full_forward(P, m, phi, prec, (cudaStream_t)stream);
+}
+
+extern "C" demag_status demag_apply_adjoint(demag_plan* P, const float* y, float* g, demag_precision prec,
+                                            void* stream) {
+  if (!P) return set_error(nullptr, DEMAG_EINVAL, "demag_apply_adjoint: plan is NULL");
+  demag_status s = check_prec(P, prec, "demag_apply_adjoint");
+  if (s != DEMAG_OK) return s;
+  if (!y || !g) return set_error(P, DEMAG_EINVAL, "demag_apply_adjoint: NULL pointer");
+  return full_adjoint(P, y, g, prec, (cudaStream_t)stream);
+}
+
+extern "C" demag_status demag_apply_full_batched(demag_plan* const* plans, const float* const* m,
+                                                 float* const* phi, int count, demag_precision prec,
+                                                 void* stream) {
+  if (count < 0 || (count > 0 && (!plans || !m || !phi)))
+    return set_error(nullptr, DEMAG_EINVAL, "demag_apply_full_batched: bad arguments");
+  for (int i = 0; i < count; ++i) {
+    if (!plans[i] || !m[i] || !phi[i])
+      return set_error(nullptr, DEMAG_EINVAL, "demag_apply_full_batched: NULL entry %d", i);
+    if (!plans[i]->ws[prec].base)
+      return set_error(plans[i], DEMAG_EINVAL, "demag_apply_full_batched: plan %d has no workspace", i);
+  }
+  for (int i = 0; i < count; ++i) {
+    demag_status s = full_forward(plans[i], m[i], phi[i], prec, (cudaStream_t)stream);
+    if (s != DEMAG_OK) return s;
+  }
+  return DEMAG_OK;
+}

@@ -1,0 +1,133 @@
+// Internal declarations of libdemag (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/demag.h"
+
+namespace demag {
+
+constexpr int kMaxTerms = 64;       // M <= 64 (R <= 129)
+constexpr int kMaxFFTLog = 13;      // complex FFT length N = L/2 <= 8192 -> n <= 8192
+constexpr double kPi = 3.141592653589793238462643383279502884;
+// c = 1/(2 pi^{3/2}): (1/4pi) from Eq. coll times 2/sqrt(pi) from Eq. gauss_trans
+constexpr double kCPot = 0.08979356106258328;
+
+// Workspace of the full-format path for one precision.
+struct Workspace {
+  void* base = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace demag
+
+struct demag_plan {
+  int n[3];
+  double h[3];
+  int R, M;
+  double c0;
+  double s;         // length scale: longest domain edge
+  double hh[3];     // scaled cell sizes h_p / s
+  int L[3];         // FFT length per axis (power of 2 >= 2 n_p - 1, >= 2)
+  int nmax, Lmax;
+  int glen;         // generator row length 2*nmax - 1
+
+  // setup data (device)
+  double* nodes = nullptr;   // [3][M]: t, tau, omega
+  double* gen64 = nullptr;   // [M][2][3][glen]
+  float* sym = nullptr;      // [M][2][3][Lmax/2 + 1] symbols / L_p
+  float2* twid[3] = {nullptr, nullptr, nullptr};  // per axis: exp(-2 pi i m / L_p), m < L_p
+  double* scale = nullptr;   // [M]: c * s * omega_k
+
+  // dense factor matrices of the full path, per precision (device, lazily built)
+  // layout [M][2][3] blocks of n_p x n_p (row-major T[i][j] = gen[i-j]),
+  // axis-3 blocks carry the scale c*s*omega_k.
+  float* T32 = nullptr;
+  double* T64 = nullptr;
+  size_t toff[3];            // element offset of axis p inside one (k, type) group
+  size_t tgroup;             // elements per (k, type) group = sum_p n_p^2
+
+  demag::Workspace ws[4];    // per demag_precision
+  int* dev_status = nullptr; // device status word (DEMAG_ETIMEOUT etc.)
+  // tensor-core state (opaque, owned by full_tc.cu)
+  void* tc = nullptr;
+  // energy / gradient scratch: phi, D^T m (1 field each) and P^T D^T m (3 fields)
+  float* ews = nullptr;
+
+  // diagnostics: kernels launched, and optional CUDA-event timing per family
+  unsigned long long launches = 0;
+  bool prof_on = false;
+  struct ProfRec { int family; cudaEvent_t a, b; };
+  std::vector<ProfRec> prof;
+  std::vector<cudaEvent_t> prof_pool;
+  size_t prof_used = 0;
+
+  char err[512];
+};
+
+namespace demag {
+
+// kernel families for demag_profile_read
+enum Family { kFamGemmSimt = 0, kFamGemmTc = 1, kFamFFT = 2, kFamSplit = 3, kFamSetup = 4, kFamEnergy = 5, kFamMisc = 6 };
+
+void prof_begin(demag_plan* P, int family, cudaStream_t st);
+void prof_end(demag_plan* P, cudaStream_t st);
+
+// Bracket one kernel launch: counts it and, when profiling is on, records
+// CUDA events around it on the launching stream.
+#define DEMAG_LAUNCH(P, family, st, ...)     \
+  do {                                       \
+    demag::prof_begin((P), (family), (st));  \
+    __VA_ARGS__;                             \
+    (P)->launches++;                         \
+    demag::prof_end((P), (st));              \
+  } while (0)
+
+// error helpers ---------------------------------------------------------------
+demag_status set_error(demag_plan* plan, demag_status st, const char* fmt, ...);
+demag_status cuda_error(demag_plan* plan, cudaError_t e, const char* where);
+
+#define DEMAG_CUDA(plan, call)                                  \
+  do {                                                          \
+    cudaError_t e_ = (call);                                    \
+    if (e_ != cudaSuccess) return demag::cuda_error(plan, e_, #call); \
+  } while (0)
+
+#define DEMAG_LAUNCHED(plan, what)                              \
+  do {                                                          \
+    cudaError_t e_ = cudaGetLastError();                        \
+    if (e_ != cudaSuccess) return demag::cuda_error(plan, e_, what); \
+  } while (0)
+
+inline size_t field_size(const demag_plan* p) { return (size_t)p->n[0] * p->n[1] * p->n[2]; }
+
+// full format (full_simt.cu / full_tc.cu) ---------------------------------------
+demag_status ensure_dense_factors(demag_plan* plan, demag_precision prec, cudaStream_t st);
+demag_status ensure_workspace(demag_plan* plan, demag_precision prec);
+size_t workspace_bytes(const demag_plan* plan, demag_precision prec);
+demag_status full_forward(demag_plan* plan, const float* m, float* phi, demag_precision prec,
+                          cudaStream_t st);
+demag_status full_adjoint(demag_plan* plan, const float* y, float* g, demag_precision prec,
+                          cudaStream_t st);
+
+// tensor cores (full_tc.cu)
+demag_status tc_prepare(demag_plan* plan, demag_precision prec, cudaStream_t st);
+demag_status tc_forward(demag_plan* plan, const float* m, float* phi, demag_precision prec,
+                        cudaStream_t st);
+demag_status tc_adjoint(demag_plan* plan, const float* y, float* g, demag_precision prec,
+                        cudaStream_t st);
+size_t tc_workspace_bytes(const demag_plan* plan, demag_precision prec);
+void tc_destroy(demag_plan* plan);
+
+// energy (energy.cu)
+demag_status fd_gradient(demag_plan* plan, const float* phi, float* out, float scale,
+                         cudaStream_t st);
+void energy_destroy(demag_plan* plan);
+
+}  // namespace demag

@@ -1,0 +1,314 @@
+// Structured formats: batched 1D Toeplitz matvecs through circulant FFTs.
+//
+// Eq. kron_eval_cp / Eq. kron_eval_tuck (Sec. 3.4) and App. C Eq. tt_3d_2:
+// applying the Kronecker operator to a CP / Tucker / TT tensor maps every
+// factor column v (mode p, component q) to T_{k,q,p} v for each node k.
+// Sec. 4.2 (Eq. conv_op, conv_pot, fft_pot) and Lemmas 4-5: with midpoint
+// collocation on a uniform grid the factors are Toeplitz, so each matvec is a
+// circular convolution of the zero-padded column with the length-L embedding
+// of the generator: y = IFFT(FFT(v, L) * symbol)[0:n].  FP32 throughout; the
+// symbols were computed in FP64 at setup and already carry the 1/L of the
+// inverse transform.
+//
+// One group of TG threads owns one column: it computes the column's real
+// spectrum once into shared memory and then, for each node of its node range,
+// multiplies by the node's symbol, runs the inverse FFT and streams the n
+// outputs to HBM.  A block holds 256 / TG groups.
+#include "internal.h"
+#include "fft.cuh"
+
+namespace demag {
+
+struct ToepLaunch {
+  int n;           // column length n_p
+  int axis;        // p
+  int M;           // number of nodes
+  int rcols;       // columns per (batch item, component)
+  int ncols;       // batch * 3 * rcols
+  int kgroup;      // nodes per block (grid.y covers M)
+  int symstride;   // Lmax/2 + 1
+  const float* in; // column (b, q, l) at in + b*in_bstride + q*in_qstride + l*n
+  long in_bstride, in_qstride;
+  float* out;      // node k: out + b*out_bstride + ((k*3 + q)*rcols + l)*n
+  long out_bstride;
+  const float* sym;    // [M][2][3][symstride]
+  const float2* twid;  // exp(-2 pi i m / L), m < L
+};
+
+struct TwiddleF {
+  const float2* t;  // length-L table; W_N^m = t[2m]
+  __device__ __forceinline__ float2 operator()(int m) const { return __ldg(t + 2 * m); }
+};
+
+template <int LOGN> struct ToepCfg {
+  static constexpr int N = 1 << LOGN;
+  static constexpr int TG = (N / 16) < 32 ? 32 : ((N / 16) > 256 ? 256 : (N / 16));
+  static constexpr int G = 256 / TG;
+  static constexpr size_t smem = (size_t)G * (2 * N + 1) * sizeof(float2);
+};
+
+template <int LOGN>
+__global__ void __launch_bounds__(256) toeplitz_fft_kernel(ToepLaunch a) {
+  using Cfg = ToepCfg<LOGN>;
+  constexpr int N = Cfg::N, TG = Cfg::TG;
+  extern __shared__ float2 smem_c[];
+  const int g = threadIdx.x / TG, lt = threadIdx.x % TG;
+  float2* spec = smem_c + (size_t)g * (2 * N + 1);
+  float2* work = spec + (N + 1);
+  const int c = blockIdx.x * Cfg::G + g;
+  const bool active = c < a.ncols;
+  const int l = active ? c % a.rcols : 0;
+  const int bq = active ? c / a.rcols : 0;
+  const int q = bq % 3, b = bq / 3;
+  const int n = a.n;
+  const float* in = a.in + b * a.in_bstride + q * a.in_qstride + (long)l * n;
+  const TwiddleF tw{a.twid};
+
+  // 1. zero-padded column as N complex samples, forward FFT
+  for (int j = lt; j < N; j += TG) {
+    float x0 = 0.f, x1 = 0.f;
+    if (active) {
+      if (2 * j < n) x0 = __ldg(in + 2 * j);
+      if (2 * j + 1 < n) x1 = __ldg(in + 2 * j + 1);
+    }
+    work[j] = make_float2(x0, x1);
+  }
+  __syncthreads();
+  fft_inplace<LOGN, TG, false>(work, lt, tw);
+
+  // 2. split step: spectrum of the real signal, bins 0..N
+  for (int f = lt; f <= N; f += TG) {
+    float2 A = work[f & (N - 1)], B = work[(N - f) & (N - 1)];
+    float ex = 0.5f * (A.x + B.x), ey = 0.5f * (A.y - B.y);
+    float dx = 0.5f * (A.x - B.x), dy = 0.5f * (A.y + B.y);
+    float2 w = __ldg(a.twid + f);  // exp(-2 pi i f / L), f <= N < L
+    float wx = w.x * dx - w.y * dy, wy = w.x * dy + w.y * dx;
+    spec[f] = make_float2(ex + wy, ey - wx);
+  }
+  __syncthreads();
+
+  const int type = (a.axis == q) ? 1 : 0;  // F on the axis of the component
+  const int k0 = blockIdx.y * a.kgroup;
+  const int k1 = min(a.M, k0 + a.kgroup);
+  for (int k = k0; k < k1; ++k) {
+    const float* s = a.sym + ((long)(k * 2 + type) * 3 + a.axis) * a.symstride;
+    // 3. product with the symbol and the inverse split step
+    for (int f = lt; f < N; f += TG) {
+      float2 Yf = spec[f], Yc = spec[N - f];
+      float sf = __ldg(s + f), sc = __ldg(s + N - f);
+      if (type == 0) {
+        Yf.x *= sf; Yf.y *= sf;
+        Yc.x *= sc; Yc.y *= sc;
+      } else {  // times i * s
+        float t0 = Yf.x;
+        Yf.x = -Yf.y * sf; Yf.y = t0 * sf;
+        float t1 = Yc.x;
+        Yc.x = -Yc.y * sc; Yc.y = t1 * sc;
+      }
+      // Ze = Yf + conj(Yc); Zo = (Yf - conj(Yc)) * exp(+2 pi i f / L); Z = Ze + i Zo
+      float zex = Yf.x + Yc.x, zey = Yf.y - Yc.y;
+      float dx = Yf.x - Yc.x, dy = Yf.y + Yc.y;
+      float2 w = __ldg(a.twid + f);
+      float zox = w.x * dx + w.y * dy, zoy = w.x * dy - w.y * dx;
+      work[f] = make_float2(zex - zoy, zey + zox);
+    }
+    __syncthreads();
+    fft_inplace<LOGN, TG, true>(work, lt, tw);
+    // 4. first n real samples to HBM
+    if (active) {
+      float* out = a.out + b * a.out_bstride + ((long)(k * 3 + q) * a.rcols + l) * n;
+      if ((n & 1) == 0 && ((reinterpret_cast<uintptr_t>(out) & 7) == 0)) {
+        float2* o2 = reinterpret_cast<float2*>(out);
+        for (int j = lt; j < n / 2; j += TG) o2[j] = work[j];
+      } else {
+        for (int i = lt; i < n; i += TG) {
+          float2 v = work[i >> 1];
+          out[i] = (i & 1) ? v.y : v.x;
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// weights: out_w[b][k][q][l] = c s omega_k * lambda[b][q][l] (lambda NULL -> 1)
+__global__ void weights_kernel(int M, int batch, int rq, const double* scale, const float* lambda,
+                               float* out_w) {
+  long total = (long)batch * M * 3 * rq;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
+    int l = (int)(i % rq);
+    long t = i / rq;
+    int q = (int)(t % 3);
+    t /= 3;
+    int k = (int)(t % M);
+    int b = (int)(t / M);
+    double lam = lambda ? (double)lambda[((long)b * 3 + q) * rq + l] : 1.0;
+    out_w[i] = (float)(scale[k] * lam);
+  }
+}
+
+template <int LOGN>
+static cudaError_t launch_toep(demag_plan* P, const ToepLaunch& a, cudaStream_t st) {
+  using Cfg = ToepCfg<LOGN>;
+  if (Cfg::smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(toeplitz_fft_kernel<LOGN>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::smem);
+    if (e != cudaSuccess) return e;
+  }
+  int gx = (a.ncols + Cfg::G - 1) / Cfg::G;
+  int gy = (a.M + a.kgroup - 1) / a.kgroup;
+  DEMAG_LAUNCH(P, kFamFFT, st, toeplitz_fft_kernel<LOGN><<<dim3(gx, gy), 256, Cfg::smem, st>>>(a));
+  return cudaGetLastError();
+}
+
+static int ilog2i(int v) {
+  int l = 0;
+  while ((1 << l) < v) ++l;
+  return l;
+}
+
+static int groups_per_block(int logn) {
+  int N = 1 << logn;
+  int TG = N / 16 < 32 ? 32 : (N / 16 > 256 ? 256 : N / 16);
+  return 256 / TG;
+}
+
+static cudaError_t run_toep(demag_plan* P, ToepLaunch a, cudaStream_t st) {
+  const int logn = ilog2i(P->L[a.axis] / 2);
+  a.n = P->n[a.axis];
+  a.M = P->M;
+  a.symstride = P->Lmax / 2 + 1;
+  a.sym = P->sym;
+  a.twid = P->twid[a.axis];
+  // node grouping: enough blocks to fill the GPU, spectra reused across nodes
+  int gx = (a.ncols + groups_per_block(logn) - 1) / groups_per_block(logn);
+  int kg = a.M;
+  while (kg > 1 && (long)gx * ((a.M + kg - 1) / kg) < 1216) kg = (kg + 1) / 2;
+  a.kgroup = kg;
+  switch (logn) {
+    case 0: return launch_toep<0>(P, a, st);
+    case 1: return launch_toep<1>(P, a, st);
+    case 2: return launch_toep<2>(P, a, st);
+    case 3: return launch_toep<3>(P, a, st);
+    case 4: return launch_toep<4>(P, a, st);
+    case 5: return launch_toep<5>(P, a, st);
+    case 6: return launch_toep<6>(P, a, st);
+    case 7: return launch_toep<7>(P, a, st);
+    case 8: return launch_toep<8>(P, a, st);
+    case 9: return launch_toep<9>(P, a, st);
+    case 10: return launch_toep<10>(P, a, st);
+    case 11: return launch_toep<11>(P, a, st);
+    case 12: return launch_toep<12>(P, a, st);
+    case 13: return launch_toep<13>(P, a, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+static demag_status check_fft_plan(demag_plan* P, const char* what) {
+  if (!P) return set_error(nullptr, DEMAG_EINVAL, "%s: plan is NULL", what);
+  if (!P->sym)
+    return set_error(P, DEMAG_EUNSUPPORTED, "%s: n_p up to %d supported by the FFT path", what,
+                     1 << kMaxFFTLog);
+  return DEMAG_OK;
+}
+
+static demag_status launch_weights(demag_plan* P, int batch, int rq, const float* lambda, float* out_w,
+                                   cudaStream_t st) {
+  long total = (long)batch * P->M * 3 * rq;
+  int blocks = (int)((total + 255) / 256);
+  if (blocks > 4096) blocks = 4096;
+  DEMAG_LAUNCH(P, kFamMisc, st, weights_kernel<<<blocks, 256, 0, st>>>(P->M, batch, rq, P->scale, lambda, out_w));
+  DEMAG_LAUNCHED(P, "weights_kernel");
+  return DEMAG_OK;
+}
+
+}  // namespace demag
+
+using namespace demag;
+
+extern "C" demag_status demag_apply_cp_batched(demag_plan* P, int batch, int r, const float* lambda,
+                                               const float* U, float* out_w, float* out_U, void* stream) {
+  demag_status s = check_fft_plan(P, "demag_apply_cp");
+  if (s != DEMAG_OK) return s;
+  if (batch < 1 || r < 1) return set_error(P, DEMAG_EINVAL, "demag_apply_cp: batch and r must be >= 1");
+  if (!lambda || !U || !out_w || !out_U) return set_error(P, DEMAG_EINVAL, "demag_apply_cp: NULL pointer");
+  cudaStream_t st = (cudaStream_t)stream;
+  const long nsum = (long)P->n[0] + P->n[1] + P->n[2];
+  long aoff = 0;
+  for (int p = 0; p < 3; ++p) {
+    ToepLaunch a{};
+    a.axis = p;
+    a.rcols = r;
+    a.ncols = batch * 3 * r;
+    a.in = U + (long)r * aoff;
+    a.in_bstride = 3L * r * nsum;
+    a.in_qstride = (long)r * nsum;
+    a.out = out_U + (long)P->M * 3 * r * aoff;
+    a.out_bstride = (long)P->M * 3 * r * nsum;
+    cudaError_t e = run_toep(P, a, st);
+    if (e != cudaSuccess) return cuda_error(P, e, "toeplitz_fft_kernel (cp)");
+    aoff += P->n[p];
+  }
+  return launch_weights(P, batch, r, lambda, out_w, st);
+}
+
+extern "C" demag_status demag_apply_cp(demag_plan* P, int r, const float* lambda, const float* U,
+                                       float* out_w, float* out_U, void* stream) {
+  return demag_apply_cp_batched(P, 1, r, lambda, U, out_w, out_U, stream);
+}
+
+extern "C" demag_status demag_apply_tucker(demag_plan* P, const int r[3], const float* V, float* out_w,
+                                           float* out_V, void* stream) {
+  demag_status s = check_fft_plan(P, "demag_apply_tucker");
+  if (s != DEMAG_OK) return s;
+  if (!r || !V || !out_w || !out_V) return set_error(P, DEMAG_EINVAL, "demag_apply_tucker: NULL pointer");
+  for (int p = 0; p < 3; ++p)
+    if (r[p] < 1) return set_error(P, DEMAG_EINVAL, "demag_apply_tucker: r[%d] must be >= 1", p);
+  cudaStream_t st = (cudaStream_t)stream;
+  long qstride = 0;
+  for (int p = 0; p < 3; ++p) qstride += (long)r[p] * P->n[p];
+  long aoff = 0;
+  for (int p = 0; p < 3; ++p) {
+    ToepLaunch a{};
+    a.axis = p;
+    a.rcols = r[p];
+    a.ncols = 3 * r[p];
+    a.in = V + aoff;
+    a.in_bstride = 0;
+    a.in_qstride = qstride;
+    a.out = out_V + (long)P->M * 3 * aoff;
+    a.out_bstride = 0;
+    cudaError_t e = run_toep(P, a, st);
+    if (e != cudaSuccess) return cuda_error(P, e, "toeplitz_fft_kernel (tucker)");
+    aoff += (long)r[p] * P->n[p];
+  }
+  return launch_weights(P, 1, 1, nullptr, out_w, st);
+}
+
+extern "C" demag_status demag_apply_tt(demag_plan* P, const int r[2], const float* G1, const float* G2,
+                                       const float* G3, float* out_w, float* oG1, float* oG2, float* oG3,
+                                       void* stream) {
+  demag_status s = check_fft_plan(P, "demag_apply_tt");
+  if (s != DEMAG_OK) return s;
+  if (!r || !G1 || !G2 || !G3 || !out_w || !oG1 || !oG2 || !oG3)
+    return set_error(P, DEMAG_EINVAL, "demag_apply_tt: NULL pointer");
+  if (r[0] < 1 || r[1] < 1) return set_error(P, DEMAG_EINVAL, "demag_apply_tt: TT ranks must be >= 1");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int rc[3] = {r[0], r[0] * r[1], r[1]};
+  const float* ins[3] = {G1, G2, G3};
+  float* outs[3] = {oG1, oG2, oG3};
+  for (int p = 0; p < 3; ++p) {
+    ToepLaunch a{};
+    a.axis = p;
+    a.rcols = rc[p];
+    a.ncols = 3 * rc[p];
+    a.in = ins[p];
+    a.in_bstride = 0;
+    a.in_qstride = (long)rc[p] * P->n[p];
+    a.out = outs[p];
+    a.out_bstride = 0;
+    cudaError_t e = run_toep(P, a, st);
+    if (e != cudaSuccess) return cuda_error(P, e, "toeplitz_fft_kernel (tt)");
+  }
+  return launch_weights(P, 1, 1, nullptr, out_w, st);
+}

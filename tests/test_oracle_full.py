@@ -158,3 +158,14 @@ def test_uniform_cube_energy_order():
     assert errs[-1] < 2e-5
     order = np.log2(errs[1] / errs[2])
     assert abs(order - FACTS["energy_error_order"]["value"]) < 0.3
+
+
+def test_sampled_lines_equal_full_apply():
+    n, h, R = (9, 7, 6), (0.1, 0.1, 0.1), 21
+    rng = np.random.default_rng(8)
+    m = rng.standard_normal((3, 6, 7, 9))
+    ref = full.apply_full(m, n, h, R)
+    lines = [(0, 0), (5, 6), (2, 3)]
+    got = full.apply_full_lines(m, n, h, R, lines)
+    for idx, (i3, i2) in enumerate(lines):
+        assert np.allclose(got[idx], ref[i3, i2], rtol=1e-12, atol=1e-14)
