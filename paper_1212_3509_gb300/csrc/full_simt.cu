@@ -237,6 +237,7 @@ size_t workspace_bytes(const demag_plan* P, demag_precision prec) {
 }
 
 demag_status ensure_workspace(demag_plan* P, demag_precision prec) {
+  if (prec == DEMAG_TF32X3 || prec == DEMAG_BF16X3) return tc_prepare(P, prec, 0);  // owns its buffers
   demag::Workspace& w = P->ws[prec];
   const size_t need = workspace_bytes(P, prec);
   if (w.base && w.bytes >= need) return DEMAG_OK;
@@ -389,10 +390,7 @@ extern "C" demag_status demag_reserve_workspace(demag_plan* P, demag_precision p
   if (!P) return set_error(nullptr, DEMAG_EINVAL, "demag_reserve_workspace: plan is NULL");
   demag_status s = check_prec(P, prec, "demag_reserve_workspace");
   if (s != DEMAG_OK) return s;
-  if (prec == DEMAG_TF32X3 || prec == DEMAG_BF16X3) {
-    s = tc_prepare(P, prec, 0);
-    if (s != DEMAG_OK) return s;
-  } else {
+  if (prec != DEMAG_TF32X3 && prec != DEMAG_BF16X3) {
     s = ensure_dense_factors(P, prec, 0);
     if (s != DEMAG_OK) return s;
   }
@@ -428,7 +426,8 @@ extern "C" demag_status demag_apply_full_batched(demag_plan* const* plans, const
   for (int i = 0; i < count; ++i) {
     if (!plans[i] || !m[i] || !phi[i])
       return set_error(nullptr, DEMAG_EINVAL, "demag_apply_full_batched: NULL entry %d", i);
-    if (!plans[i]->ws[prec].base)
+    const bool tc = prec == DEMAG_TF32X3 || prec == DEMAG_BF16X3;
+    if (tc ? !plans[i]->tc : !plans[i]->ws[prec].base)
       return set_error(plans[i], DEMAG_EINVAL, "demag_apply_full_batched: plan %d has no workspace", i);
   }
   for (int i = 0; i < count; ++i) {

@@ -123,6 +123,7 @@ demag_status tc_forward(demag_plan* plan, const float* m, float* phi, demag_prec
 demag_status tc_adjoint(demag_plan* plan, const float* y, float* g, demag_precision prec,
                         cudaStream_t st);
 size_t tc_workspace_bytes(const demag_plan* plan, demag_precision prec);
+demag_status tc_sync_status(demag_plan* plan, cudaStream_t st);
 void tc_destroy(demag_plan* plan);
 
 // energy (energy.cu)

@@ -399,7 +399,7 @@ extern "C" demag_status demag_sync_status(demag_plan* plan, void* stream) {
     DEMAG_CUDA(plan, cudaStreamSynchronize(st));
     return set_error(plan, (demag_status)h, "device reported status %d (a bounded wait gave up)", h);
   }
-  return DEMAG_OK;
+  return tc_sync_status(plan, st);
 }
 
 extern "C" unsigned long long demag_launch_count(const demag_plan* plan) { return plan ? plan->launches : 0ULL; }
@@ -407,8 +407,10 @@ extern "C" unsigned long long demag_launch_count(const demag_plan* plan) { retur
 extern "C" demag_status demag_profile(demag_plan* plan, int enable) {
   if (!plan) return set_error(nullptr, DEMAG_EINVAL, "demag_profile: plan is NULL");
   plan->prof_on = enable != 0;
-  plan->prof.clear();
-  plan->prof_used = 0;
+  if (enable) {  // a new record; disabling keeps the record for demag_profile_read
+    plan->prof.clear();
+    plan->prof_used = 0;
+  }
   return DEMAG_OK;
 }
 

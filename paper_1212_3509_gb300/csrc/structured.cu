@@ -7,13 +7,21 @@
 // collocation on a uniform grid the factors are Toeplitz, so each matvec is a
 // circular convolution of the zero-padded column with the length-L embedding
 // of the generator: y = IFFT(FFT(v, L) * symbol)[0:n].  FP32 throughout; the
-// symbols were computed in FP64 at setup and already carry the 1/L of the
-// inverse transform.
+// symbols were computed in FP64 at setup and carry the 1/L of the inverse.
 //
-// One group of TG threads owns one column: it computes the column's real
-// spectrum once into shared memory and then, for each node of its node range,
-// multiplies by the node's symbol, runs the inverse FFT and streams the n
-// outputs to HBM.  A block holds 256 / TG groups.
+// A group of TG threads owns one column.  It computes the column's real
+// spectrum once (shared memory) and then, for each node of its node range:
+//   pass 1  (registers)  symbol product and inverse split step for the bins
+//                        this thread's first radix pass reads, then the
+//                        first radix-R DFT, written to shared memory;
+//   middle  (shared)     radix-16 Stockham passes (ping-pong buffers padded
+//                        by one element per 16 so strided writes do not
+//                        collide in banks);
+//   last    (registers)  final radix-16 pass; only the outputs of the first
+//                        half of the complex signal (the n real samples we
+//                        keep) are computed into registers and stored to HBM.
+// Twiddles come from a two-level table in shared memory:
+// W_L^m = T1[m >> 7] * T0[m & 127].
 #include "internal.h"
 #include "fft.cuh"
 
@@ -35,26 +43,82 @@ struct ToepLaunch {
   const float2* twid;  // exp(-2 pi i m / L), m < L
 };
 
-struct TwiddleF {
-  const float2* t;  // length-L table; W_N^m = t[2m]
-  __device__ __forceinline__ float2 operator()(int m) const { return __ldg(t + 2 * m); }
-};
+__device__ __forceinline__ int pad16(int i) { return i + (i >> 4); }
 
 template <int LOGN> struct ToepCfg {
   static constexpr int N = 1 << LOGN;
+  static constexpr int L = 2 * N;
   static constexpr int TG = (N / 16) < 32 ? 32 : ((N / 16) > 256 ? 256 : (N / 16));
   static constexpr int G = 256 / TG;
-  static constexpr size_t smem = (size_t)G * (2 * N + 1) * sizeof(float2);
+  static constexpr int NP = N + N / 16;            // padded buffer length
+  static constexpr int T0 = L < 128 ? L : 128;     // fine twiddle table
+  static constexpr int T1 = L / T0;                // coarse twiddle table
+  static constexpr int R1 = (LOGN % 4) ? (1 << (LOGN % 4)) : (LOGN >= 4 ? 16 : 1);
+  static constexpr int NPASS = LOGN / 4 + ((LOGN % 4) ? 1 : 0);
+  // per group: spectrum (N+1) and two padded buffers
+  static constexpr size_t group_floats2 = (size_t)(N + 1) + 2 * NP;
+  static constexpr size_t smem = ((size_t)T0 + T1 + G * group_floats2) * sizeof(float2);
 };
+
+struct TwSmem {
+  const float2* t0;
+  const float2* t1;
+  // W_L^m
+  __device__ __forceinline__ float2 L(int m) const { return cmul(t1[m >> 7], t0[m & 127]); }
+};
+
+// forward-FFT twiddle W_N^m = W_L^(2m) for the generic in-place routine
+struct TwN {
+  TwSmem s;
+  __device__ __forceinline__ float2 operator()(int m) const { return s.L(2 * m); }
+};
+
+// Pass with radix R reading src (padded) and writing dst (padded), Ns = size
+// of the sub-transforms already done.  Inverse direction.
+template <int R, int N, int TG>
+__device__ __forceinline__ void mid_pass(const float2* src, float2* dst, int Ns, int lt, const TwSmem& tw) {
+  constexpr int items = N / R;
+  constexpr int ipt = (items + TG - 1) / TG;
+#pragma unroll
+  for (int it = 0; it < ipt; ++it) {
+    const int j = lt + it * TG;
+    if (items % TG == 0 || j < items) {
+      float2 v[R];
+      const int k = j % Ns;
+      const int tstep = k * (N / (Ns * R));  // in units of W_N
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        float2 x = src[pad16(j + r * items)];
+        if (r > 0) {
+          float2 w = tw.L(2 * r * tstep);
+          w.y = -w.y;  // inverse
+          x = cmul(x, w);
+        }
+        v[r] = x;
+      }
+      dft_reg<R, true>(v);
+      const int base = (j / Ns) * Ns * R + k;
+#pragma unroll
+      for (int r = 0; r < R; ++r) dst[pad16(base + r * Ns)] = v[r];
+    }
+  }
+}
 
 template <int LOGN>
 __global__ void __launch_bounds__(256) toeplitz_fft_kernel(ToepLaunch a) {
   using Cfg = ToepCfg<LOGN>;
-  constexpr int N = Cfg::N, TG = Cfg::TG;
+  constexpr int N = Cfg::N, TG = Cfg::TG, R1 = Cfg::R1, NPASS = Cfg::NPASS;
   extern __shared__ float2 smem_c[];
+  float2* t0 = smem_c;
+  float2* t1 = t0 + Cfg::T0;
   const int g = threadIdx.x / TG, lt = threadIdx.x % TG;
-  float2* spec = smem_c + (size_t)g * (2 * N + 1);
-  float2* work = spec + (N + 1);
+  float2* spec = t1 + Cfg::T1 + (size_t)g * Cfg::group_floats2;
+  float2* bufA = spec + (N + 1);
+  float2* bufB = bufA + Cfg::NP;
+  for (int i = threadIdx.x; i < Cfg::T0; i += blockDim.x) t0[i] = __ldg(a.twid + i);
+  for (int i = threadIdx.x; i < Cfg::T1; i += blockDim.x) t1[i] = __ldg(a.twid + i * Cfg::T0);
+  const TwSmem tw{t0, t1};
+
   const int c = blockIdx.x * Cfg::G + g;
   const bool active = c < a.ncols;
   const int l = active ? c % a.rcols : 0;
@@ -62,26 +126,25 @@ __global__ void __launch_bounds__(256) toeplitz_fft_kernel(ToepLaunch a) {
   const int q = bq % 3, b = bq / 3;
   const int n = a.n;
   const float* in = a.in + b * a.in_bstride + q * a.in_qstride + (long)l * n;
-  const TwiddleF tw{a.twid};
 
-  // 1. zero-padded column as N complex samples, forward FFT
+  // 1. zero-padded column as N complex samples, forward FFT (once per column)
   for (int j = lt; j < N; j += TG) {
     float x0 = 0.f, x1 = 0.f;
     if (active) {
       if (2 * j < n) x0 = __ldg(in + 2 * j);
       if (2 * j + 1 < n) x1 = __ldg(in + 2 * j + 1);
     }
-    work[j] = make_float2(x0, x1);
+    bufA[j] = make_float2(x0, x1);
   }
   __syncthreads();
-  fft_inplace<LOGN, TG, false>(work, lt, tw);
+  fft_inplace<LOGN, TG, false>(bufA, lt, TwN{tw});
 
   // 2. split step: spectrum of the real signal, bins 0..N
   for (int f = lt; f <= N; f += TG) {
-    float2 A = work[f & (N - 1)], B = work[(N - f) & (N - 1)];
+    float2 A = bufA[f & (N - 1)], B = bufA[(N - f) & (N - 1)];
     float ex = 0.5f * (A.x + B.x), ey = 0.5f * (A.y - B.y);
     float dx = 0.5f * (A.x - B.x), dy = 0.5f * (A.y + B.y);
-    float2 w = __ldg(a.twid + f);  // exp(-2 pi i f / L), f <= N < L
+    float2 w = tw.L(f);  // exp(-2 pi i f / L)
     float wx = w.x * dx - w.y * dy, wy = w.x * dy + w.y * dx;
     spec[f] = make_float2(ex + wy, ey - wx);
   }
@@ -90,40 +153,112 @@ __global__ void __launch_bounds__(256) toeplitz_fft_kernel(ToepLaunch a) {
   const int type = (a.axis == q) ? 1 : 0;  // F on the axis of the component
   const int k0 = blockIdx.y * a.kgroup;
   const int k1 = min(a.M, k0 + a.kgroup);
+  float* outbase = a.out + b * a.out_bstride + (long)l * n;
+  // paired stores need an even length and an 8-byte aligned column start
+  // (every (k, q) offset is a multiple of n, so one check per column)
+  const bool vec = ((n & 1) == 0) && ((reinterpret_cast<uintptr_t>(outbase) & 7) == 0);
   for (int k = k0; k < k1; ++k) {
     const float* s = a.sym + ((long)(k * 2 + type) * 3 + a.axis) * a.symstride;
-    // 3. product with the symbol and the inverse split step
-    for (int f = lt; f < N; f += TG) {
-      float2 Yf = spec[f], Yc = spec[N - f];
-      float sf = __ldg(s + f), sc = __ldg(s + N - f);
-      if (type == 0) {
-        Yf.x *= sf; Yf.y *= sf;
-        Yc.x *= sc; Yc.y *= sc;
-      } else {  // times i * s
-        float t0 = Yf.x;
-        Yf.x = -Yf.y * sf; Yf.y = t0 * sf;
-        float t1 = Yc.x;
-        Yc.x = -Yc.y * sc; Yc.y = t1 * sc;
+    // 3. first pass in registers: symbol product + inverse split step feed
+    //    the radix-R1 DFT of the items j = lt + it*TG (bins j + r N/R1)
+    constexpr int items1 = N / R1;
+    constexpr int ipt1 = (items1 + TG - 1) / TG;
+    float2* dst1 = (NPASS <= 1) ? nullptr : bufA;
+#pragma unroll
+    for (int it = 0; it < ipt1; ++it) {
+      const int j = lt + it * TG;
+      if (items1 % TG == 0 || j < items1) {
+        float2 v[R1];
+#pragma unroll
+        for (int r = 0; r < R1; ++r) {
+          const int f = j + r * items1;
+          float2 Yf = spec[f], Yc = spec[N - f];
+          const float sf = __ldg(s + f), sc = __ldg(s + N - f);
+          if (type == 0) {
+            Yf.x *= sf; Yf.y *= sf;
+            Yc.x *= sc; Yc.y *= sc;
+          } else {  // times i * s
+            const float t0v = Yf.x;
+            Yf.x = -Yf.y * sf; Yf.y = t0v * sf;
+            const float t1v = Yc.x;
+            Yc.x = -Yc.y * sc; Yc.y = t1v * sc;
+          }
+          // Ze = Yf + conj(Yc); Zo = (Yf - conj(Yc)) exp(+2 pi i f / L); Z = Ze + i Zo
+          const float zex = Yf.x + Yc.x, zey = Yf.y - Yc.y;
+          const float dx = Yf.x - Yc.x, dy = Yf.y + Yc.y;
+          const float2 w = tw.L(f);
+          const float zox = w.x * dx + w.y * dy, zoy = w.x * dy - w.y * dx;
+          v[r] = make_float2(zex - zoy, zey + zox);
+        }
+        dft_reg<R1, true>(v);
+        if constexpr (NPASS <= 1) {
+          // single pass: outputs j + r*items1, keep the first half
+#pragma unroll
+          for (int r = 0; r < R1; ++r) {
+            const int i = j + r * items1;
+            if (active && 2 * i < n) {
+              float* o = outbase + (long)(k * 3 + q) * a.rcols * n;
+              o[2 * i] = v[r].x;
+              if (2 * i + 1 < n) o[2 * i + 1] = v[r].y;
+            }
+          }
+        } else {
+#pragma unroll
+          for (int r = 0; r < R1; ++r) dst1[pad16(j * R1 + r)] = v[r];
+        }
       }
-      // Ze = Yf + conj(Yc); Zo = (Yf - conj(Yc)) * exp(+2 pi i f / L); Z = Ze + i Zo
-      float zex = Yf.x + Yc.x, zey = Yf.y - Yc.y;
-      float dx = Yf.x - Yc.x, dy = Yf.y + Yc.y;
-      float2 w = __ldg(a.twid + f);
-      float zox = w.x * dx + w.y * dy, zoy = w.x * dy - w.y * dx;
-      work[f] = make_float2(zex - zoy, zey + zox);
     }
-    __syncthreads();
-    fft_inplace<LOGN, TG, true>(work, lt, tw);
-    // 4. first n real samples to HBM
-    if (active) {
-      float* out = a.out + b * a.out_bstride + ((long)(k * 3 + q) * a.rcols + l) * n;
-      if ((n & 1) == 0 && ((reinterpret_cast<uintptr_t>(out) & 7) == 0)) {
-        float2* o2 = reinterpret_cast<float2*>(out);
-        for (int j = lt; j < n / 2; j += TG) o2[j] = work[j];
-      } else {
-        for (int i = lt; i < n; i += TG) {
-          float2 v = work[i >> 1];
-          out[i] = (i & 1) ? v.y : v.x;
+    if constexpr (NPASS > 1) {
+      __syncthreads();
+      // 4. middle radix-16 passes, ping-pong A -> B -> A ...
+      float2* src = bufA;
+      float2* dst = bufB;
+      int Ns = R1;
+#pragma unroll
+      for (int ps = 1; ps < NPASS - 1; ++ps) {
+        mid_pass<16, N, TG>(src, dst, Ns, lt, tw);
+        __syncthreads();
+        float2* t = src;
+        src = dst;
+        dst = t;
+        Ns *= 16;
+      }
+      // 5. last radix-16 pass (Ns = N/16): outputs j + r N/16, keep r < 8
+      constexpr int items = N / 16;
+      constexpr int ipt = (items + TG - 1) / TG;
+#pragma unroll
+      for (int it = 0; it < ipt; ++it) {
+        const int j = lt + it * TG;
+        if (items % TG == 0 || j < items) {
+          float2 v[16];
+#pragma unroll
+          for (int r = 0; r < 16; ++r) {
+            float2 x = src[pad16(j + r * items)];
+            if (r > 0) {
+              float2 w = tw.L(2 * r * j);  // W_N^(r j), Ns = N/16 so k = j
+              w.y = -w.y;
+              x = cmul(x, w);
+            }
+            v[r] = x;
+          }
+          dft_reg<16, true>(v);
+          if (active) {
+            float* o = outbase + (long)(k * 3 + q) * a.rcols * n;
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+              const int i = j + r * items;
+              if (2 * i + 1 < n) {
+                if (vec)
+                  reinterpret_cast<float2*>(o)[i] = v[r];
+                else {
+                  o[2 * i] = v[r].x;
+                  o[2 * i + 1] = v[r].y;
+                }
+              } else if (2 * i < n) {
+                o[2 * i] = v[r].x;
+              }
+            }
+          }
         }
       }
     }
