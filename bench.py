@@ -313,21 +313,44 @@ def run_ours(args, world, rank, local):
         "clocks": clk.summary(),
     }
 
+    # ---------------- every full-format form on the same input (C2: error per form)
+    phis = {}
+    forms = {}
+    for f in ("fp32", "tf32x3", "bf16x3"):
+        try:
+            D.demag_reserve_workspace(P, f)
+        except D.DemagError:
+            continue
+        out = torch.empty_like(phi)
+        fn = lambda: D.demag_apply_full(P, m, out, f)  # noqa: E731
+        fn()
+        torch.cuda.synchronize()
+        ms_f = time_region(fn, max(2, args.steps // 3), stream)
+        forms[f] = {"apps_per_s": 1e3 / ms_f, "ms_per_app": ms_f}
+        phis[f] = out
+
     # ---------------- parity against the oracle (sampled) and CPU baseline
     if not args.no_oracle and rank == 0:
         from oracle import full as ofull, structured as ost
         lines = [(0, 0), (n3[2] // 2, n3[1] // 3), (n3[2] - 1, n3[1] - 1), (n3[2] // 4, n3[1] - 7)]
         ref = ofull.apply_full_lines(m_host, n3, h, R, lines)
-        got = phi.cpu().numpy()
-        num = sum(float(((got[i3, i2] - ref[j]) ** 2).sum()) for j, (i3, i2) in enumerate(lines))
-        den = sum(float((ref[j] ** 2).sum()) for j in range(len(lines)))
-        result["rel_l2_full"] = (num / den) ** 0.5
+
+        def sampled_err(field):
+            got = field.cpu().numpy()
+            num = sum(float(((got[i3, i2] - ref[j]) ** 2).sum()) for j, (i3, i2) in enumerate(lines))
+            den = sum(float((ref[j] ** 2).sum()) for j in range(len(lines)))
+            return (num / den) ** 0.5
+
+        result["rel_l2_full"] = sampled_err(phi)
         result["rel_l2_full_sample"] = f"{len(lines)} output lines phi[i3,i2,:] vs the FP64 oracle"
+        for f, field in phis.items():
+            forms[f]["rel_l2"] = sampled_err(field)
         rw, rU = ost.apply_cp(lam_h[0], U_h[0], cn3, ch, cR)
         ref_cp = np.concatenate([rU[p].ravel() for p in range(3)])
         got_cp = out_U[: Mc * 3 * r * 3 * ncp].cpu().numpy()
         result["cp"]["rel_l2"] = float(np.linalg.norm(got_cp - ref_cp) / np.linalg.norm(ref_cp))
         result["cpu_baseline"] = cpu_baseline(n3, h, R, m_host, budget_s=20.0)
+    result["forms_full"] = forms
     print(json.dumps(result), flush=True)
 
 

@@ -427,7 +427,7 @@ extern "C" demag_status demag_apply_full_batched(demag_plan* const* plans, const
     if (!plans[i] || !m[i] || !phi[i])
       return set_error(nullptr, DEMAG_EINVAL, "demag_apply_full_batched: NULL entry %d", i);
     const bool tc = prec == DEMAG_TF32X3 || prec == DEMAG_BF16X3;
-    if (tc ? !plans[i]->tc : !plans[i]->ws[prec].base)
+    if (tc ? !tc_ready(plans[i], prec) : !plans[i]->ws[prec].base)
       return set_error(plans[i], DEMAG_EINVAL, "demag_apply_full_batched: plan %d has no workspace", i);
   }
   for (int i = 0; i < count; ++i) {

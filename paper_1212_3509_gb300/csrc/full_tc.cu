@@ -1,17 +1,19 @@
-// Full format on tcgen05 tensor cores: split-precision (BF16x3) mode products.
+// Full format on tcgen05 tensor cores: split-precision mode products
+// (BF16x3 and TF32x3).
 //
 // The same chain as full_simt.cu (Cor. 3, Eq. kron_operator, as mode products
 // of Eq. modemul; 8 GEMMs per node; node sum folded into the last
 // contraction; transposed stores rotate the axes), with every GEMM operand x
-// carried as x_hi = bf16(x), x_lo = bf16(x - x_hi) and each product formed as
-// A_hi B_hi + A_hi B_lo + A_lo B_hi with FP32 accumulation in tensor memory.
+// carried as x_hi = round(x), x_lo = round(x - x_hi) in BF16 or TF32 and each
+// product formed as A_hi B_hi + A_hi B_lo + A_lo B_hi with FP32 accumulation
+// in tensor memory.
 //
 // Kernel: persistent, one CTA (192 threads) per SM, warp-specialised:
-//   warp 0      TMA producer: loads A_hi, A_lo (128 x 32) and B_hi, B_lo
-//               (BN x 32) k-blocks into a 4-stage shared-memory ring,
-//   warp 1      MMA issuer: 2 k-steps x 3 tcgen05.mma (M = 128, N = BN,
-//               K = 16) per stage into one of two TMEM accumulators
-//               (2 x 256 columns),
+//   warp 0      TMA producer: loads A_hi, A_lo (128 rows) and B_hi, B_lo
+//               (BN rows) k-blocks of 64-byte rows (32 BF16 or 16 TF32
+//               elements) into a 4-stage shared-memory ring,
+//   warp 1      MMA issuer: 2 k-steps x 3 tcgen05.mma (M = 128, N = BN) per
+//               stage into one of two TMEM accumulators (2 x 256 columns),
 //   warps 2..5  epilogue: tcgen05.ld of the accumulator (one TMEM lane per
 //               thread = one output row), then either the hi/lo split of the
 //               next stage's operand or the final FP32 field, stored
@@ -27,10 +29,11 @@
 
 namespace demag {
 
-constexpr int kBM = 128, kBN = 256, kBK = 32;     // k-block: 32 bf16 = one 64-byte swizzled row
+constexpr int kBM = 128, kBN = 256;
+constexpr int kRowBytes = 64;                      // one 64-byte swizzled row per k-block
 constexpr int kStages = 4;
-constexpr int kTileA = kBM * kBK * 2;              // 8 KB
-constexpr int kTileB = kBN * kBK * 2;              // 16 KB
+constexpr int kTileA = kBM * kRowBytes;            // 8 KB
+constexpr int kTileB = kBN * kRowBytes;            // 16 KB
 constexpr int kStageBytes = 2 * kTileA + 2 * kTileB;  // 48 KB
 constexpr int kBarBytes = 256;
 constexpr int kSmemBytes = kStages * kStageBytes + kBarBytes + 1024;
@@ -39,9 +42,43 @@ constexpr int kMaxTcJobs = 3 * kMaxTerms + 8;
 constexpr int kMaxTcPairs = 4 * kMaxTerms + 8;
 constexpr uint64_t kWaitNs = 2000000000ull;        // 2 s bound on every wait
 constexpr uint32_t kSwizzle64 = 4;                 // descriptor code of SWIZZLE_64B
-constexpr uint32_t kSBO = 8 * 64;                  // 8 rows x 64 bytes per swizzle atom
+constexpr uint32_t kSBO = 8 * kRowBytes;           // 8 rows x 64 bytes per swizzle atom
 
 enum TcOut { kOutSplit = 0, kOutF32 = 1 };
+
+// Element traits of the two split forms.
+struct Bf16Form {
+  using T = __nv_bfloat16;
+  static constexpr int kElem = 2;
+  static constexpr int kBK = kRowBytes / kElem;    // 32 elements per k-block
+  static constexpr uint32_t kFormat = 1;           // instruction-descriptor code of BF16
+  __device__ static void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    ptx::mma_bf16(d, a, b, idesc, acc);
+  }
+  __device__ static void split(float x, T& hi, T& lo) {
+    hi = __float2bfloat16_rn(x);
+    lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+  }
+};
+
+struct Tf32Form {
+  using T = float;                                 // TF32 values in 32-bit containers
+  static constexpr int kElem = 4;
+  static constexpr int kBK = kRowBytes / kElem;    // 16 elements per k-block
+  static constexpr uint32_t kFormat = 2;           // instruction-descriptor code of TF32
+  __device__ static void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    ptx::mma_tf32(d, a, b, idesc, acc);
+  }
+  __device__ static float to_tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+  }
+  __device__ static void split(float x, T& hi, T& lo) {
+    hi = to_tf32(x);
+    lo = to_tf32(x - hi);
+  }
+};
 
 struct TcJob {
   int pair0, npairs, out_field, pad;
@@ -49,8 +86,8 @@ struct TcJob {
 
 struct TcParams {
   CUtensorMap a_hi, a_lo, b_hi, b_lo;  // 3D maps: (K, rows, field | matrix)
-  void* out_hi;                        // split: bf16 hi plane base; f32: float base
-  void* out_lo;                        // split: bf16 lo plane base
+  void* out_hi;                        // split: hi plane base; f32: float base
+  void* out_lo;                        // split: lo plane base
   long long field_elems;               // elements per output field
   long long s_a;                       // output stride of the column index a
   int ldC, n_inner;                    // output row stride and row split (outer, inner)
@@ -75,7 +112,9 @@ __device__ __forceinline__ void tc_fail(volatile int* abort, int* status) {
   atomicExch(status, (int)DEMAG_ETIMEOUT);
 }
 
+template <class F>
 __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const __grid_constant__ TcParams p) {
+  using T = typename F::T;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * kStageBytes);
@@ -116,7 +155,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const __grid_con
       ptx::prefetch_tmap(&p.a_lo);
       ptx::prefetch_tmap(&p.b_hi);
       ptx::prefetch_tmap(&p.b_lo);
-      const uint32_t bytes = 2 * kTileA + 2 * (uint32_t)p.bn * kBK * 2;
+      const uint32_t bytes = 2 * kTileA + 2 * (uint32_t)p.bn * kRowBytes;
       int s = 0;
       uint32_t ph = 0;
       for (int tile = blockIdx.x; tile < p.total_tiles && !*abort; tile += gridDim.x) {
@@ -132,10 +171,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const __grid_con
             }
             uint8_t* st = smem + s * kStageBytes;
             ptx::mbar_arrive_expect_tx(&full[s], bytes);
-            ptx::tma_load_3d(st, &p.a_hi, &full[s], kb * kBK, mt * kBM, pr.x);
-            ptx::tma_load_3d(st + kTileA, &p.a_lo, &full[s], kb * kBK, mt * kBM, pr.x);
-            ptx::tma_load_3d(st + 2 * kTileA, &p.b_hi, &full[s], kb * kBK, nt * kBN, pr.y);
-            ptx::tma_load_3d(st + 2 * kTileA + kTileB, &p.b_lo, &full[s], kb * kBK, nt * kBN, pr.y);
+            ptx::tma_load_3d(st, &p.a_hi, &full[s], kb * F::kBK, mt * kBM, pr.x);
+            ptx::tma_load_3d(st + kTileA, &p.a_lo, &full[s], kb * F::kBK, mt * kBM, pr.x);
+            ptx::tma_load_3d(st + 2 * kTileA, &p.b_hi, &full[s], kb * F::kBK, nt * kBN, pr.y);
+            ptx::tma_load_3d(st + 2 * kTileA + kTileB, &p.b_lo, &full[s], kb * F::kBK, nt * kBN, pr.y);
             if (++s == kStages) { s = 0; ph ^= 1; }
           }
         }
@@ -143,7 +182,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const __grid_con
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      const uint32_t idesc = ptx::instr_desc(1, kBM, (uint32_t)p.bn);
+      const uint32_t idesc = ptx::instr_desc(F::kFormat, kBM, (uint32_t)p.bn);
       int s = 0;
       uint32_t ph = 0, tph = 0;
       int buf = 0;
@@ -169,15 +208,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const __grid_con
             ptx::tc_fence_after();
             const uint32_t st = ptx::smem_u32(smem + s * kStageBytes);
 #pragma unroll
-            for (int kk = 0; kk < kBK / 16; ++kk) {
-              const uint32_t off = kk * 32;  // 16 bf16 along K
+            for (int kk = 0; kk < 2; ++kk) {
+              const uint32_t off = kk * 32;  // one MMA consumes 32 bytes of K
               const uint64_t ah = ptx::smem_desc(st + off, kSBO, kSwizzle64);
               const uint64_t al = ptx::smem_desc(st + kTileA + off, kSBO, kSwizzle64);
               const uint64_t bh = ptx::smem_desc(st + 2 * kTileA + off, kSBO, kSwizzle64);
               const uint64_t bl = ptx::smem_desc(st + 2 * kTileA + kTileB + off, kSBO, kSwizzle64);
-              ptx::mma_bf16(d, ah, bh, idesc, acc);
-              ptx::mma_bf16(d, ah, bl, idesc, 1u);
-              ptx::mma_bf16(d, al, bh, idesc, 1u);
+              F::mma(d, ah, bh, idesc, acc);
+              F::mma(d, ah, bl, idesc, 1u);
+              F::mma(d, al, bh, idesc, 1u);
               acc = 1u;
             }
             issued_mma = true;
@@ -210,25 +249,33 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const __grid_con
       const int outer = row / p.n_inner, inner = row - outer * p.n_inner;
       const long long rbase = (long long)J.out_field * p.field_elems + (long long)outer * p.ldC + inner;
       const uint32_t taddr = tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * kBN);
+      const int a0 = nt * kBN;
+      const int acount = min(p.bn, p.n_a - a0);  // columns of this tile that exist
       for (int c0 = 0; c0 < p.bn; c0 += 32) {
         uint32_t r[32];
         ptx::tmem_ld32(taddr + (uint32_t)c0, r);
         ptx::tmem_ld_wait();
         if (valid) {
+          if (p.mode == kOutSplit) {
+            T* hp = reinterpret_cast<T*>(p.out_hi) + rbase + (long long)(a0 + c0) * p.s_a;
+            T* lp = reinterpret_cast<T*>(p.out_lo) + rbase + (long long)(a0 + c0) * p.s_a;
 #pragma unroll
-          for (int jj = 0; jj < 32; ++jj) {
-            const int a = nt * kBN + c0 + jj;
-            if (a < p.n_a) {
-              const float x = p.alpha * __uint_as_float(r[jj]);
-              const long long idx = rbase + (long long)a * p.s_a;
-              if (p.mode == kOutSplit) {
-                const __nv_bfloat16 hi = __float2bfloat16_rn(x);
-                const __nv_bfloat16 lo = __float2bfloat16_rn(x - __bfloat162float(hi));
-                reinterpret_cast<__nv_bfloat16*>(p.out_hi)[idx] = hi;
-                reinterpret_cast<__nv_bfloat16*>(p.out_lo)[idx] = lo;
-              } else {
-                reinterpret_cast<float*>(p.out_hi)[idx] = x;
+            for (int jj = 0; jj < 32; ++jj) {
+              if (c0 + jj < acount) {
+                T hi, lo;
+                F::split(__uint_as_float(r[jj]), hi, lo);
+                *hp = hi;
+                *lp = lo;
               }
+              hp += p.s_a;
+              lp += p.s_a;
+            }
+          } else {
+            float* op = reinterpret_cast<float*>(p.out_hi) + rbase + (long long)(a0 + c0) * p.s_a;
+#pragma unroll
+            for (int jj = 0; jj < 32; ++jj) {
+              if (c0 + jj < acount) *op = p.alpha * __uint_as_float(r[jj]);
+              op += p.s_a;
             }
           }
         }
@@ -264,26 +311,28 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const __grid_con
 
 // ---------------------------------------------------------------- operand preparation
 
-// hi/lo split of a [fields][rows][n] FP32 tensor into [fields][rows][ld] BF16 planes
+// hi/lo split of a [fields][rows][n] FP32 tensor into [fields][rows][ld] planes
+template <class F>
 __global__ void split_rows_kernel(const float* __restrict__ x, long long nrows, int n, int ld,
-                                  __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo) {
+                                  typename F::T* __restrict__ hi, typename F::T* __restrict__ lo) {
   const long long total = nrows * n;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
     const long long r = i / n;
     const int c = (int)(i - r * n);
-    const float v = x[i];
-    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    typename F::T h, l;
+    F::split(x[i], h, l);
     const long long o = r * ld + c;
     hi[o] = h;
-    lo[o] = __float2bfloat16_rn(v - __bfloat162float(h));
+    lo[o] = l;
   }
 }
 
 // Dense Toeplitz factors of one axis, hi/lo, [M][2][n][ld]; the third axis
 // carries the scale c s omega_k.
+template <class F>
 __global__ void tc_factor_kernel(int M, int glen, int axis, int n, int ld, const double* gen, const double* scale,
-                                 __nv_bfloat16* hi, __nv_bfloat16* lo) {
+                                 typename F::T* hi, typename F::T* lo) {
   const long long total = (long long)M * 2 * n * n;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
@@ -293,11 +342,11 @@ __global__ void tc_factor_kernel(int M, int glen, int axis, int n, int ld, const
     const int kt = (int)(t / n);  // k*2 + type
     double v = gen[((long long)kt * 3 + axis) * glen + (ii - jj + n - 1)];
     if (axis == 2) v *= scale[kt / 2];
-    const float f = (float)v;
-    const __nv_bfloat16 h = __float2bfloat16_rn(f);
+    typename F::T h, l;
+    F::split((float)v, h, l);
     const long long o = ((long long)kt * n + ii) * ld + jj;
     hi[o] = h;
-    lo[o] = __float2bfloat16_rn(f - __bfloat162float(h));
+    lo[o] = l;
   }
 }
 
@@ -320,53 +369,63 @@ static EncodeTiledFn encode_fn() {
   return fn;
 }
 
-// 3D BF16 map over [dim2][dim1][ld] with logical inner extent dim0 <= ld; box (32, box1, 1), 64B swizzle.
-static bool make_map(CUtensorMap* m, void* base, uint64_t dim0, uint64_t dim1, uint64_t dim2, uint64_t ld,
-                     uint32_t box1) {
+// 3D map over [dim2][dim1][ld] with logical inner extent dim0 <= ld; box (64 bytes, box1, 1), 64B swizzle.
+static bool make_map(CUtensorMap* m, void* base, int elem_bytes, uint64_t dim0, uint64_t dim1, uint64_t dim2,
+                     uint64_t ld, uint32_t box1) {
   EncodeTiledFn enc = encode_fn();
   if (!enc) return false;
   cuuint64_t dims[3] = {dim0, dim1, dim2};
-  cuuint64_t strides[2] = {ld * 2, ld * dim1 * 2};
-  cuuint32_t box[3] = {(cuuint32_t)kBK, box1, 1};
+  cuuint64_t strides[2] = {ld * elem_bytes, ld * dim1 * elem_bytes};
+  cuuint32_t box[3] = {(cuuint32_t)(kRowBytes / elem_bytes), box1, 1};
   cuuint32_t estr[3] = {1, 1, 1};
-  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box, estr,
-                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  const CUtensorMapDataType dt = elem_bytes == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  CUresult r = enc(m, dt, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
 
 static int round_up(int v, int m) { return (v + m - 1) / m * m; }
 
-// Per-plan tensor-core state (BF16x3).
+// Per-plan, per-form tensor-core state.
 struct TcState {
-  int ld[3];              // padded row lengths (multiples of 8 bf16 = 16 bytes)
+  int elem;               // bytes per element (2 BF16, 4 TF32)
+  int ld[3];              // padded row lengths (16-byte multiples)
   int bn[3];              // N tile width per axis
-  __nv_bfloat16* B[3][2];  // per axis: hi / lo factors [M][2][n][ld]
-  __nv_bfloat16* X[2];     // split input: [3][n3 n2][ld1]
-  __nv_bfloat16* buf1[2];  // [3M][n1 n3][ld2]
-  __nv_bfloat16* buf2[2];  // [3M][n2 n1][ld3]
+  void* B[3][2];          // per axis: hi / lo factors [M][2][n][ld]
+  void* X[2];             // split input: [3][n3 n2][ld1]
+  void* buf1[2];          // [3M][n1 n3][ld2]
+  void* buf2[2];          // [3M][n2 n1][ld3]
   CUtensorMap mapB[3][2];
   CUtensorMap mapX[2], map1[2], map2[2];
   int* status;
   size_t bytes;
 };
 
-static TcState* state(demag_plan* P) { return reinterpret_cast<TcState*>(P->tc); }
+struct TcHolder {
+  TcState* s[2] = {nullptr, nullptr};  // [0] BF16x3, [1] TF32x3
+};
+
+static int form_index(demag_precision prec) { return prec == DEMAG_TF32X3 ? 1 : 0; }
+
+static TcState* state(demag_plan* P, demag_precision prec) {
+  TcHolder* H = reinterpret_cast<TcHolder*>(P->tc);
+  return H ? H->s[form_index(prec)] : nullptr;
+}
 
 size_t tc_workspace_bytes(const demag_plan* P, demag_precision prec) {
-  (void)prec;
+  const size_t e = prec == DEMAG_TF32X3 ? 4 : 2;
+  const int al = (int)(16 / e);
   size_t b = 0;
   const int n1 = P->n[0], n2 = P->n[1], n3 = P->n[2];
-  const size_t l1 = round_up(n1, 8), l2 = round_up(n2, 8), l3 = round_up(n3, 8);
-  for (int p = 0; p < 3; ++p) b += 2 * (size_t)P->M * 2 * P->n[p] * round_up(P->n[p], 8) * 2;
-  b += 2 * 3 * (size_t)n3 * n2 * l1 * 2;
-  b += 2 * 3 * (size_t)P->M * n1 * n3 * l2 * 2;
-  b += 2 * 3 * (size_t)P->M * n2 * n1 * l3 * 2;
+  const size_t l1 = round_up(n1, al), l2 = round_up(n2, al), l3 = round_up(n3, al);
+  for (int p = 0; p < 3; ++p) b += 2 * (size_t)P->M * 2 * P->n[p] * round_up(P->n[p], al) * e;
+  b += 2 * 3 * (size_t)n3 * n2 * l1 * e;
+  b += 2 * 3 * (size_t)P->M * n1 * n3 * l2 * e;
+  b += 2 * 3 * (size_t)P->M * n2 * n1 * l3 * e;
   return b;
 }
 
-void tc_destroy(demag_plan* P) {
-  TcState* S = state(P);
+static void free_state(TcState* S) {
   if (!S) return;
   for (int p = 0; p < 3; ++p)
     for (int h = 0; h < 2; ++h) cudaFree(S->B[p][h]);
@@ -377,6 +436,16 @@ void tc_destroy(demag_plan* P) {
   }
   cudaFree(S->status);
   delete S;
+}
+
+void tc_destroy(demag_plan* P) {
+  TcHolder* H = reinterpret_cast<TcHolder*>(P->tc);
+  if (!H) return;
+  for (auto*& s : H->s) {
+    free_state(s);
+    s = nullptr;
+  }
+  delete H;
   P->tc = nullptr;
 }
 
@@ -385,16 +454,39 @@ static int grid_blocks(long long count) {
   return (int)(b > 152 * 16 ? 152 * 16 : (b < 1 ? 1 : b));
 }
 
+template <class F>
+static demag_status prepare_form(demag_plan* P, TcState* S, cudaStream_t st) {
+  const int M = P->M;
+  for (int p = 0; p < 3; ++p) {
+    long long total = (long long)M * 2 * P->n[p] * P->n[p];
+    DEMAG_LAUNCH(P, kFamSetup, st,
+                 tc_factor_kernel<F><<<grid_blocks(total), 256, 0, st>>>(
+                     M, P->glen, p, P->n[p], S->ld[p], P->gen64, P->scale, (typename F::T*)S->B[p][0],
+                     (typename F::T*)S->B[p][1]));
+    DEMAG_LAUNCHED(P, "tc_factor_kernel");
+  }
+  static bool attr = false;
+  if (!attr) {
+    DEMAG_CUDA(P, cudaFuncSetAttribute(tc_gemm_kernel<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
+    attr = true;
+  }
+  return DEMAG_OK;
+}
+
 demag_status tc_prepare(demag_plan* P, demag_precision prec, cudaStream_t st) {
-  if (prec != DEMAG_BF16X3) return set_error(P, DEMAG_EUNSUPPORTED, "tensor-core form %d is not built", (int)prec);
-  if (P->tc) return DEMAG_OK;
+  if (prec != DEMAG_BF16X3 && prec != DEMAG_TF32X3)
+    return set_error(P, DEMAG_EUNSUPPORTED, "tensor-core form %d is not built", (int)prec);
+  if (state(P, prec)) return DEMAG_OK;
   if (!encode_fn()) return set_error(P, DEMAG_ECUDA, "cuTensorMapEncodeTiled is unavailable");
+  if (!P->tc) P->tc = new TcHolder();
+  TcHolder* H = reinterpret_cast<TcHolder*>(P->tc);
   const int n1 = P->n[0], n2 = P->n[1], n3 = P->n[2], M = P->M;
   TcState* S = new TcState();
   memset(S, 0, sizeof(*S));
-  P->tc = S;
+  S->elem = prec == DEMAG_TF32X3 ? 4 : 2;
+  const int al = 16 / S->elem;
   for (int p = 0; p < 3; ++p) {
-    S->ld[p] = round_up(P->n[p], 8);
+    S->ld[p] = round_up(P->n[p], al);
     S->bn[p] = P->n[p] >= kBN ? kBN : round_up(P->n[p], 16);
   }
   auto alloc = [&](void** ptr, size_t bytes) -> bool {
@@ -402,43 +494,37 @@ demag_status tc_prepare(demag_plan* P, demag_precision prec, cudaStream_t st) {
     S->bytes += bytes;
     return cudaMemsetAsync(*ptr, 0, bytes, st) == cudaSuccess;
   };
+  const size_t e = S->elem;
   bool ok = true;
   for (int p = 0; p < 3 && ok; ++p)
-    for (int h = 0; h < 2 && ok; ++h)
-      ok = alloc((void**)&S->B[p][h], (size_t)M * 2 * P->n[p] * S->ld[p] * 2);
+    for (int h = 0; h < 2 && ok; ++h) ok = alloc(&S->B[p][h], (size_t)M * 2 * P->n[p] * S->ld[p] * e);
   for (int h = 0; h < 2 && ok; ++h) {
-    ok = ok && alloc((void**)&S->X[h], 3 * (size_t)n3 * n2 * S->ld[0] * 2);
-    ok = ok && alloc((void**)&S->buf1[h], 3 * (size_t)M * n1 * n3 * S->ld[1] * 2);
-    ok = ok && alloc((void**)&S->buf2[h], 3 * (size_t)M * n2 * n1 * S->ld[2] * 2);
+    ok = ok && alloc(&S->X[h], 3 * (size_t)n3 * n2 * S->ld[0] * e);
+    ok = ok && alloc(&S->buf1[h], 3 * (size_t)M * n1 * n3 * S->ld[1] * e);
+    ok = ok && alloc(&S->buf2[h], 3 * (size_t)M * n2 * n1 * S->ld[2] * e);
   }
   ok = ok && alloc((void**)&S->status, sizeof(int));
   if (!ok) {
-    tc_destroy(P);
+    free_state(S);
     return set_error(P, DEMAG_ENOMEM, "tensor-core workspace allocation failed");
-  }
-  for (int p = 0; p < 3; ++p) {
-    long long total = (long long)M * 2 * P->n[p] * P->n[p];
-    DEMAG_LAUNCH(P, kFamSetup, st,
-                 tc_factor_kernel<<<grid_blocks(total), 256, 0, st>>>(M, P->glen, p, P->n[p], S->ld[p], P->gen64,
-                                                                      P->scale, S->B[p][0], S->B[p][1]));
-    DEMAG_LAUNCHED(P, "tc_factor_kernel");
   }
   for (int h = 0; h < 2; ++h) {
     for (int p = 0; p < 3; ++p)
-      ok = ok && make_map(&S->mapB[p][h], S->B[p][h], P->n[p], P->n[p], 2 * M, S->ld[p], S->bn[p]);
-    ok = ok && make_map(&S->mapX[h], S->X[h], n1, (uint64_t)n3 * n2, 3, S->ld[0], kBM);
-    ok = ok && make_map(&S->map1[h], S->buf1[h], n2, (uint64_t)n1 * n3, 3 * M, S->ld[1], kBM);
-    ok = ok && make_map(&S->map2[h], S->buf2[h], n3, (uint64_t)n2 * n1, 3 * M, S->ld[2], kBM);
+      ok = ok && make_map(&S->mapB[p][h], S->B[p][h], S->elem, P->n[p], P->n[p], 2 * M, S->ld[p], S->bn[p]);
+    ok = ok && make_map(&S->mapX[h], S->X[h], S->elem, n1, (uint64_t)n3 * n2, 3, S->ld[0], kBM);
+    ok = ok && make_map(&S->map1[h], S->buf1[h], S->elem, n2, (uint64_t)n1 * n3, 3 * M, S->ld[1], kBM);
+    ok = ok && make_map(&S->map2[h], S->buf2[h], S->elem, n3, (uint64_t)n2 * n1, 3 * M, S->ld[2], kBM);
   }
   if (!ok) {
-    tc_destroy(P);
+    free_state(S);
     return set_error(P, DEMAG_ECUDA, "tensor map encoding failed");
   }
-  static bool attr = false;
-  if (!attr) {
-    DEMAG_CUDA(P, cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
-    attr = true;
+  demag_status s = prec == DEMAG_TF32X3 ? prepare_form<Tf32Form>(P, S, st) : prepare_form<Bf16Form>(P, S, st);
+  if (s != DEMAG_OK) {
+    free_state(S);
+    return s;
   }
+  H->s[form_index(prec)] = S;
   return DEMAG_OK;
 }
 
@@ -454,9 +540,9 @@ struct StageDesc {
   float alpha;
 };
 
-static demag_status launch_stage(demag_plan* P, const StageDesc& d, const std::vector<TcJob>& jobs,
+template <class F>
+static demag_status launch_stage(demag_plan* P, TcState* S, const StageDesc& d, const std::vector<TcJob>& jobs,
                                  const std::vector<short2>& pairs, cudaStream_t st) {
-  TcState* S = state(P);
   thread_local static TcParams prm;  // host staging; the launch copies the parameters at enqueue
   if ((int)jobs.size() > kMaxTcJobs || (int)pairs.size() > kMaxTcPairs)
     return set_error(P, DEMAG_EUNSUPPORTED, "too many GEMM jobs for one launch");
@@ -472,7 +558,7 @@ static demag_status launch_stage(demag_plan* P, const StageDesc& d, const std::v
   prm.n_inner = d.n_inner;
   prm.rows = d.rows;
   prm.n_a = d.n_a;
-  prm.kblocks = (d.K + kBK - 1) / kBK;
+  prm.kblocks = (d.K + F::kBK - 1) / F::kBK;
   prm.bn = d.bn;
   prm.mode = d.mode;
   prm.alpha = d.alpha;
@@ -487,7 +573,7 @@ static demag_status launch_stage(demag_plan* P, const StageDesc& d, const std::v
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int grid = prm.total_tiles < sms ? prm.total_tiles : sms;
-  DEMAG_LAUNCH(P, kFamGemmTc, st, tc_gemm_kernel<<<grid, kTcThreads, kSmemBytes, st>>>(prm));
+  DEMAG_LAUNCH(P, kFamGemmTc, st, tc_gemm_kernel<F><<<grid, kTcThreads, kSmemBytes, st>>>(prm));
   DEMAG_LAUNCHED(P, "tc_gemm_kernel");
   return DEMAG_OK;
 }
@@ -501,12 +587,12 @@ static TcJob job(int pair0, int npairs, int out_field) {
   return j;
 }
 
-static demag_status split_input(demag_plan* P, const float* x, int fields, cudaStream_t st) {
-  TcState* S = state(P);
+template <class F>
+static demag_status split_input(demag_plan* P, TcState* S, const float* x, int fields, cudaStream_t st) {
   const long long nrows = (long long)fields * P->n[2] * P->n[1];
   DEMAG_LAUNCH(P, kFamSplit, st,
-               split_rows_kernel<<<grid_blocks(nrows * P->n[0]), 256, 0, st>>>(x, nrows, P->n[0], S->ld[0],
-                                                                                 S->X[0], S->X[1]));
+               split_rows_kernel<F><<<grid_blocks(nrows * P->n[0]), 256, 0, st>>>(
+                   x, nrows, P->n[0], S->ld[0], (typename F::T*)S->X[0], (typename F::T*)S->X[1]));
   DEMAG_LAUNCHED(P, "split_rows_kernel");
   return DEMAG_OK;
 }
@@ -514,12 +600,10 @@ static demag_status split_input(demag_plan* P, const float* x, int fields, cudaS
 // matrix index of (node k, type) in the per-axis factor maps
 static short mat(int k, int type) { return (short)(2 * k + type); }
 
-demag_status tc_forward(demag_plan* P, const float* m, float* phi, demag_precision prec, cudaStream_t st) {
-  demag_status s = tc_prepare(P, prec, st);
-  if (s != DEMAG_OK) return s;
-  TcState* S = state(P);
+template <class F>
+static demag_status forward_chain(demag_plan* P, TcState* S, const float* m, float* phi, cudaStream_t st) {
   const int n1 = P->n[0], n2 = P->n[1], n3 = P->n[2], M = P->M;
-  s = split_input(P, m, 3, st);
+  demag_status s = split_input<F>(P, S, m, 3, st);
   if (s != DEMAG_OK) return s;
   // mode 1: Y[k][q] = m_q x_1 T_{k,q,1}; rows (i3, i2), contraction i1 -> Y [i1'][i3][i2]
   {
@@ -533,7 +617,7 @@ demag_status tc_forward(demag_plan* P, const float* m, float* phi, demag_precisi
     StageDesc d{{&S->mapX[0], &S->mapX[1]}, {&S->mapB[0][0], &S->mapB[0][1]}, n3 * n2, n1, n1, S->bn[0],
                 S->buf1[0], S->buf1[1], (long long)n1 * n3 * S->ld[1], (long long)n3 * S->ld[1], S->ld[1], n2,
                 kOutSplit, 1.f};
-    s = launch_stage(P, d, jobs, pairs, st);
+    s = launch_stage<F>(P, S, d, jobs, pairs, st);
     if (s != DEMAG_OK) return s;
   }
   // mode 2: U_k = Y_k1 x_2 E + Y_k2 x_2 F, V_k = Y_k3 x_2 E; rows (i1', i3) -> [i2'][i1'][i3]
@@ -550,7 +634,7 @@ demag_status tc_forward(demag_plan* P, const float* m, float* phi, demag_precisi
     StageDesc d{{&S->map1[0], &S->map1[1]}, {&S->mapB[1][0], &S->mapB[1][1]}, n1 * n3, n2, n2, S->bn[1],
                 S->buf2[0], S->buf2[1], (long long)n2 * n1 * S->ld[2], (long long)n1 * S->ld[2], S->ld[2], n3,
                 kOutSplit, 1.f};
-    s = launch_stage(P, d, jobs, pairs, st);
+    s = launch_stage<F>(P, S, d, jobs, pairs, st);
     if (s != DEMAG_OK) return s;
   }
   // mode 3 with the node sum: phi = sum_k U_k x_3 S E + V_k x_3 S F; rows (i2', i1') -> [i3'][i2'][i1']
@@ -564,18 +648,16 @@ demag_status tc_forward(demag_plan* P, const float* m, float* phi, demag_precisi
     }
     StageDesc d{{&S->map2[0], &S->map2[1]}, {&S->mapB[2][0], &S->mapB[2][1]}, n2 * n1, n3, n3, S->bn[2],
                 phi, nullptr, (long long)n3 * n2 * n1, (long long)n2 * n1, n1, n1, kOutF32, 1.f};
-    s = launch_stage(P, d, jobs, pairs, st);
+    s = launch_stage<F>(P, S, d, jobs, pairs, st);
     if (s != DEMAG_OK) return s;
   }
   return DEMAG_OK;
 }
 
-demag_status tc_adjoint(demag_plan* P, const float* y, float* g, demag_precision prec, cudaStream_t st) {
-  demag_status s = tc_prepare(P, prec, st);
-  if (s != DEMAG_OK) return s;
-  TcState* S = state(P);
+template <class F>
+static demag_status adjoint_chain(demag_plan* P, TcState* S, const float* y, float* g, cudaStream_t st) {
   const int n1 = P->n[0], n2 = P->n[1], n3 = P->n[2], M = P->M;
-  s = split_input(P, y, 1, st);
+  demag_status s = split_input<F>(P, S, y, 1, st);
   if (s != DEMAG_OK) return s;
   // mode 1: Ya_k = y x_1 F, Yb_k = y x_1 E  (fields 2k, 2k+1 of buf1)
   {
@@ -589,7 +671,7 @@ demag_status tc_adjoint(demag_plan* P, const float* y, float* g, demag_precision
     StageDesc d{{&S->mapX[0], &S->mapX[1]}, {&S->mapB[0][0], &S->mapB[0][1]}, n3 * n2, n1, n1, S->bn[0],
                 S->buf1[0], S->buf1[1], (long long)n1 * n3 * S->ld[1], (long long)n3 * S->ld[1], S->ld[1], n2,
                 kOutSplit, 1.f};
-    s = launch_stage(P, d, jobs, pairs, st);
+    s = launch_stage<F>(P, S, d, jobs, pairs, st);
     if (s != DEMAG_OK) return s;
   }
   // mode 2: Za = Ya x_2 E (g1), Zb = Yb x_2 F (g2), Zc = Yb x_2 E (g3)  (fields 3k+q of buf2)
@@ -607,7 +689,7 @@ demag_status tc_adjoint(demag_plan* P, const float* y, float* g, demag_precision
     StageDesc d{{&S->map1[0], &S->map1[1]}, {&S->mapB[1][0], &S->mapB[1][1]}, n1 * n3, n2, n2, S->bn[1],
                 S->buf2[0], S->buf2[1], (long long)n2 * n1 * S->ld[2], (long long)n1 * S->ld[2], S->ld[2], n3,
                 kOutSplit, 1.f};
-    s = launch_stage(P, d, jobs, pairs, st);
+    s = launch_stage<F>(P, S, d, jobs, pairs, st);
     if (s != DEMAG_OK) return s;
   }
   // mode 3 with the node sum: g_q = -sum_k Z_kq x_3 S T_{k,q,3}
@@ -620,23 +702,42 @@ demag_status tc_adjoint(demag_plan* P, const float* y, float* g, demag_precision
     }
     StageDesc d{{&S->map2[0], &S->map2[1]}, {&S->mapB[2][0], &S->mapB[2][1]}, n2 * n1, n3, n3, S->bn[2],
                 g, nullptr, (long long)n3 * n2 * n1, (long long)n2 * n1, n1, n1, kOutF32, -1.f};
-    s = launch_stage(P, d, jobs, pairs, st);
+    s = launch_stage<F>(P, S, d, jobs, pairs, st);
     if (s != DEMAG_OK) return s;
   }
   return DEMAG_OK;
 }
 
+demag_status tc_forward(demag_plan* P, const float* m, float* phi, demag_precision prec, cudaStream_t st) {
+  demag_status s = tc_prepare(P, prec, st);
+  if (s != DEMAG_OK) return s;
+  TcState* S = state(P, prec);
+  return prec == DEMAG_TF32X3 ? forward_chain<Tf32Form>(P, S, m, phi, st) : forward_chain<Bf16Form>(P, S, m, phi, st);
+}
+
+demag_status tc_adjoint(demag_plan* P, const float* y, float* g, demag_precision prec, cudaStream_t st) {
+  demag_status s = tc_prepare(P, prec, st);
+  if (s != DEMAG_OK) return s;
+  TcState* S = state(P, prec);
+  return prec == DEMAG_TF32X3 ? adjoint_chain<Tf32Form>(P, S, y, g, st) : adjoint_chain<Bf16Form>(P, S, y, g, st);
+}
+
 demag_status tc_sync_status(demag_plan* P, cudaStream_t st) {
-  TcState* S = state(P);
-  if (!S) return DEMAG_OK;
-  int h = 0;
-  DEMAG_CUDA(P, cudaMemcpyAsync(&h, S->status, sizeof(int), cudaMemcpyDeviceToHost, st));
-  DEMAG_CUDA(P, cudaStreamSynchronize(st));
-  if (h) {
-    DEMAG_CUDA(P, cudaMemsetAsync(S->status, 0, sizeof(int), st));
-    return set_error(P, (demag_status)h, "tensor-core kernel reported status %d (a bounded wait gave up)", h);
+  TcHolder* H = reinterpret_cast<TcHolder*>(P->tc);
+  if (!H) return DEMAG_OK;
+  for (TcState* S : H->s) {
+    if (!S) continue;
+    int h = 0;
+    DEMAG_CUDA(P, cudaMemcpyAsync(&h, S->status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    DEMAG_CUDA(P, cudaStreamSynchronize(st));
+    if (h) {
+      DEMAG_CUDA(P, cudaMemsetAsync(S->status, 0, sizeof(int), st));
+      return set_error(P, (demag_status)h, "tensor-core kernel reported status %d (a bounded wait gave up)", h);
+    }
   }
   return DEMAG_OK;
 }
+
+bool tc_ready(const demag_plan* P, demag_precision prec) { return state(const_cast<demag_plan*>(P), prec) != nullptr; }
 
 }  // namespace demag

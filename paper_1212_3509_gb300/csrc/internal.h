@@ -124,6 +124,7 @@ demag_status tc_adjoint(demag_plan* plan, const float* y, float* g, demag_precis
                         cudaStream_t st);
 size_t tc_workspace_bytes(const demag_plan* plan, demag_precision prec);
 demag_status tc_sync_status(demag_plan* plan, cudaStream_t st);
+bool tc_ready(const demag_plan* plan, demag_precision prec);
 void tc_destroy(demag_plan* plan);
 
 // energy (energy.cu)

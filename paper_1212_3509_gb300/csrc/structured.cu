@@ -67,11 +67,42 @@ struct TwSmem {
   __device__ __forceinline__ float2 L(int m) const { return cmul(t1[m >> 7], t0[m & 127]); }
 };
 
+// exp(-2 pi i j / 32): cos(pi j / 16) and -sin(pi j / 16), j < 32
+__device__ __forceinline__ constexpr double w32_re(int j) {
+  return j == 0 ? 1.0 : j == 1 ? 0.98078528040323044913 : j == 2 ? 0.92387953251128675613
+       : j == 3 ? 0.83146961230254523708 : j == 4 ? 0.70710678118654752440 : j == 5 ? 0.55557023301960222474
+       : j == 6 ? 0.38268343236508977173 : j == 7 ? 0.19509032201612826785 : j == 8 ? 0.0
+       : j < 16 ? -w32_re(16 - j) : -w32_re(j - 16);
+}
+__device__ __forceinline__ constexpr double w32_im(int j) { return -w32_re((j + 24) & 31); }
+
 // forward-FFT twiddle W_N^m = W_L^(2m) for the generic in-place routine
 struct TwN {
   TwSmem s;
   __device__ __forceinline__ float2 operator()(int m) const { return s.L(2 * m); }
 };
+
+// pw[r] = w^r for r < R by a product tree of depth <= 4 (w^2, w^4, w^8 by
+// squaring, the rest as one product of those), so each power carries only a
+// few roundings of the table value w.
+template <int R>
+__device__ __forceinline__ void powers(float2 w, float2 (&pw)[R]) {
+  pw[0] = make_float2(1.f, 0.f);
+  if constexpr (R > 1) pw[1] = w;
+  if constexpr (R > 2) pw[2] = cmul(w, w);
+  if constexpr (R > 3) pw[3] = cmul(pw[2], w);
+  if constexpr (R > 4) {
+    pw[4] = cmul(pw[2], pw[2]);
+    pw[5] = cmul(pw[4], w);
+    pw[6] = cmul(pw[4], pw[2]);
+    pw[7] = cmul(pw[4], pw[3]);
+  }
+  if constexpr (R > 8) {
+    pw[8] = cmul(pw[4], pw[4]);
+#pragma unroll
+    for (int r = 9; r < R; ++r) pw[r] = cmul(pw[8], pw[r - 8]);
+  }
+}
 
 // Pass with radix R reading src (padded) and writing dst (padded), Ns = size
 // of the sub-transforms already done.  Inverse direction.
@@ -86,15 +117,14 @@ __device__ __forceinline__ void mid_pass(const float2* src, float2* dst, int Ns,
       float2 v[R];
       const int k = j % Ns;
       const int tstep = k * (N / (Ns * R));  // in units of W_N
+      float2 w = tw.L(2 * tstep);
+      w.y = -w.y;  // inverse
+      float2 pw[R];
+      powers<R>(w, pw);
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         float2 x = src[pad16(j + r * items)];
-        if (r > 0) {
-          float2 w = tw.L(2 * r * tstep);
-          w.y = -w.y;  // inverse
-          x = cmul(x, w);
-        }
-        v[r] = x;
+        v[r] = r > 0 ? cmul(x, pw[r]) : x;
       }
       dft_reg<R, true>(v);
       const int base = (j / Ns) * Ns * R + k;
@@ -105,7 +135,7 @@ __device__ __forceinline__ void mid_pass(const float2* src, float2* dst, int Ns,
 }
 
 template <int LOGN>
-__global__ void __launch_bounds__(256) toeplitz_fft_kernel(ToepLaunch a) {
+__global__ void __launch_bounds__(256, 2) toeplitz_fft_kernel(ToepLaunch a) {
   using Cfg = ToepCfg<LOGN>;
   constexpr int N = Cfg::N, TG = Cfg::TG, R1 = Cfg::R1, NPASS = Cfg::NPASS;
   extern __shared__ float2 smem_c[];
@@ -169,6 +199,8 @@ __global__ void __launch_bounds__(256) toeplitz_fft_kernel(ToepLaunch a) {
       const int j = lt + it * TG;
       if (items1 % TG == 0 || j < items1) {
         float2 v[R1];
+        // exp(-2 pi i f / L) for f = j + r N/R1 is W_L^j times the 2 R1-th root W^r
+        const float2 wj = tw.L(j);
 #pragma unroll
         for (int r = 0; r < R1; ++r) {
           const int f = j + r * items1;
@@ -186,7 +218,8 @@ __global__ void __launch_bounds__(256) toeplitz_fft_kernel(ToepLaunch a) {
           // Ze = Yf + conj(Yc); Zo = (Yf - conj(Yc)) exp(+2 pi i f / L); Z = Ze + i Zo
           const float zex = Yf.x + Yc.x, zey = Yf.y - Yc.y;
           const float dx = Yf.x - Yc.x, dy = Yf.y + Yc.y;
-          const float2 w = tw.L(f);
+          const float2 cr = make_float2((float)w32_re((r * 16 / R1) & 31), (float)w32_im((r * 16 / R1) & 31));
+          const float2 w = r == 0 ? wj : cmul(wj, cr);
           const float zox = w.x * dx + w.y * dy, zoy = w.x * dy - w.y * dx;
           v[r] = make_float2(zex - zoy, zey + zox);
         }
@@ -231,15 +264,14 @@ __global__ void __launch_bounds__(256) toeplitz_fft_kernel(ToepLaunch a) {
         const int j = lt + it * TG;
         if (items % TG == 0 || j < items) {
           float2 v[16];
+          float2 w = tw.L(2 * j);  // W_N^j (Ns = N/16, so k = j), inverse: conjugate
+          w.y = -w.y;
+          float2 pw[16];
+          powers<16>(w, pw);
 #pragma unroll
           for (int r = 0; r < 16; ++r) {
-            float2 x = src[pad16(j + r * items)];
-            if (r > 0) {
-              float2 w = tw.L(2 * r * j);  // W_N^(r j), Ns = N/16 so k = j
-              w.y = -w.y;
-              x = cmul(x, w);
-            }
-            v[r] = x;
+            const float2 x = src[pad16(j + r * items)];
+            v[r] = r > 0 ? cmul(x, pw[r]) : x;
           }
           dft_reg<16, true>(v);
           if (active) {

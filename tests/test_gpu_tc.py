@@ -34,31 +34,33 @@ def D():
     return D
 
 
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32x3"])
 @pytest.mark.parametrize("n,h,R", TC_SHAPES)
-def test_bf16x3_full_vs_oracle(D, n, h, R):
+def test_split_full_vs_oracle(D, n, h, R, prec):
     m = synth.random_unit_m(n, 1212 + sum(n))
     P = D.demag_build_factors(n, h, R)
     phi = torch.empty(n[2], n[1], n[0], device="cuda")
-    D.demag_apply_full(P, dev(m), phi, "bf16x3")
+    D.demag_apply_full(P, dev(m), phi, prec)
     torch.cuda.synchronize()
     D.demag_sync_status(P)
     err = rel_l2(host(phi), ofull.apply_full(m, n, h, R))
-    print(f"bf16x3 {n}: rel L2 {err:.3e}")
-    assert err <= TOL["bf16x3"], err
+    print(f"{prec} {n}: rel L2 {err:.3e}")
+    assert err <= TOL[prec], err
 
 
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32x3"])
 @pytest.mark.parametrize("n,h,R", [TC_SHAPES[1], TC_SHAPES[3], TC_SHAPES[6]])
-def test_bf16x3_adjoint_vs_oracle(D, n, h, R):
+def test_split_adjoint_vs_oracle(D, n, h, R, prec):
     rng = np.random.default_rng(11)
     y = rng.standard_normal((n[2], n[1], n[0])).astype(np.float32)
     P = D.demag_build_factors(n, h, R)
     g = torch.empty(3, n[2], n[1], n[0], device="cuda")
-    D.demag_apply_adjoint(P, dev(y), g, "bf16x3")
+    D.demag_apply_adjoint(P, dev(y), g, prec)
     torch.cuda.synchronize()
     D.demag_sync_status(P)
     err = rel_l2(host(g), ofull.apply_adjoint(y, n, h, R))
-    print(f"bf16x3 adjoint {n}: rel L2 {err:.3e}")
-    assert err <= TOL["bf16x3"], err
+    print(f"{prec} adjoint {n}: rel L2 {err:.3e}")
+    assert err <= TOL[prec], err
 
 
 def test_bf16x3_repeated_calls_are_identical(D):
