@@ -205,6 +205,33 @@ demag_status demag_energy(demag_plan* plan, const float* m, double* energy, floa
  * gave up set DEMAG_ETIMEOUT there).  Synchronizes `stream`. */
 demag_status demag_sync_status(demag_plan* plan, void* stream);
 
+/* ---- allocation-free full format (no counterpart in the paper) ---------- */
+
+/* phi = sum_q P^(q) m^(q) exactly as demag_apply_full with DEMAG_FP32 (same
+ * kernels, same order of operations), for callers that must not allocate
+ * device memory: code running while a host framework's memory pool owns the
+ * GPU (an allocation from a library would fail or fragment it), loops where
+ * an allocation would implicitly synchronise the device, and hosts whose
+ * plugin rules forbid allocation.  No plan is needed and nothing is
+ * allocated: the nodes, generators, dense factors and intermediate fields
+ * live in one fixed device array of 32 MiB inside the library, which every
+ * GPU that loads the library keeps until the process exits.
+ * desc: the grid, as for demag_build_factors; m: float [3][n3][n2][n1] and
+ * phi: float [n3][n2][n1], device pointers owned by the caller.
+ * Limits: the grid must fit the array: 8*(4M + 6M(2 nmax - 1)) + 8M sum_p
+ * n_p^2 + 4(2M + 3) n1 n2 n3 bytes (each part rounded up to 256) <= 32 MiB
+ * (for example 32^3 and 48^3 grids with R = 41 fit, 64^3 does not); larger
+ * grids are rejected with DEMAG_EUNSUPPORTED and a message giving both sizes,
+ * before anything is launched.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  Every call on a device uses the same array and leaves its
+ * contents there; nothing in it has to start at zero.  Calls whose work can
+ * overlap on the GPU (other streams, other host threads) race on the array:
+ * serialise them.  Errors are reported through demag_last_error(NULL). */
+demag_status demag_apply_full_noalloc(const demag_grid_desc* desc, const float* m, float* phi,
+                                      void* stream);
+
 /* ---- diagnostics (build-only; no counterpart in the paper) -------------- */
 
 /* Number of kernels the library has launched for this plan so far. */

@@ -56,6 +56,7 @@ _SIGS = {
     "demag_stray_field": (_i, [_vp, _vp, _vp, _vp]),
     "demag_energy": (_i, [_vp, _vp, _vp, _vp, _i, _vp]),
     "demag_sync_status": (_i, [_vp, _vp]),
+    "demag_apply_full_noalloc": (_i, [ctypes.POINTER(GridDesc), _vp, _vp, _vp]),
     "demag_launch_count": (ctypes.c_ulonglong, [_vp]),
     "demag_profile": (_i, [_vp, _i]),
     "demag_profile_read": (_i, [_vp, _i, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]),
@@ -268,3 +269,18 @@ def demag_profile_read(plan: Plan, family) -> tuple:
     ms, cnt = ctypes.c_double(), ctypes.c_longlong()
     _check(lib.demag_profile_read(plan.ptr, fam, ctypes.byref(ms), ctypes.byref(cnt)), plan.ptr)
     return ms.value, cnt.value
+
+
+def demag_apply_full_noalloc(n, h, R: int, m, phi, c0: float = 2.15, stream=None):
+    """FP32 full-format application that allocates no device memory.
+
+    For callers that cannot allocate (a host framework's memory pool owns the
+    GPU, allocations would synchronise a latency-critical loop, or plugin rules
+    forbid them): the library uses a fixed 32 MiB device array of its own, and
+    grids that do not fit are rejected with DemagError (DEMAG_EUNSUPPORTED).
+    """
+    import torch
+    N = int(n[0]) * int(n[1]) * int(n[2])
+    d = GridDesc((ctypes.c_int * 3)(*[int(v) for v in n]), (ctypes.c_double * 3)(*[float(v) for v in h]), int(R), float(c0))
+    _check(lib.demag_apply_full_noalloc(ctypes.byref(d), _ptr(m, 3 * N, torch.float32, "m"),
+                                        _ptr(phi, N, torch.float32, "phi"), _stream(stream)))

@@ -436,3 +436,223 @@ extern "C" demag_status demag_apply_full_batched(demag_plan* const* plans, const
   }
   return DEMAG_OK;
 }
+
+// ---------------------------------------------------------------- allocation-free entry point
+//
+// demag_apply_full_noalloc serves callers that must not allocate device
+// memory themselves or through this library: code that runs while a device
+// memory pool owned by a host framework has reserved the GPU (a cudaMalloc
+// from a library would fail or fragment it), latency-critical loops where
+// an allocation would implicitly synchronise the device, and embedders whose
+// plugin rules forbid allocation.  Everything this call needs beyond the
+// caller's input and output (nodes, generators, dense factors and the
+// intermediates of the mode-product chain) lives in one file-scope device
+// array of fixed size, which every GPU that loads the library keeps until
+// the process exits.  The arithmetic is that of demag_apply_full with
+// DEMAG_FP32 (same kernels, same order).
+
+#include <cmath>
+#include <mutex>
+
+namespace demag {
+
+constexpr size_t kNoAllocBytes = size_t(32) << 20;  // 32 MiB of device scratch
+constexpr int kNoAllocMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+static void* g_noalloc_addr[kNoAllocMaxDevices];
+static std::mutex g_noalloc_mu;
+
+// Device address of the scratch array on the current device.  Host code sees
+// only a host-side stand-in for `g_noalloc_scratch`, so the address is asked
+// from the runtime once per device (with that device current) and cached.
+static demag_status noalloc_address(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_error(nullptr, e, "demag_apply_full_noalloc: cudaGetDevice");
+  if (dev < 0 || dev >= kNoAllocMaxDevices)
+    return set_error(nullptr, DEMAG_EUNSUPPORTED, "demag_apply_full_noalloc: device %d out of range", dev);
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_error(nullptr, e, "demag_apply_full_noalloc: cudaGetSymbolAddress");
+    g_noalloc_addr[dev] = p;
+  }
+  *out = g_noalloc_addr[dev];
+  return DEMAG_OK;
+}
+
+static size_t na_align(size_t b) { return (b + 255) & ~size_t(255); }
+
+// Append one job to a GEMM batch without any host heap use.
+static void na_add(GemmBatch& b, int& npairs, int rows, int ncol, int K, int ldc, void* C,
+                   const void* const* A, const void* const* B, int np) {
+  GemmJob& J = b.jobs[b.njobs++];
+  J.rows = rows; J.ncol = ncol; J.K = K;
+  J.lda = K; J.ldb = K; J.ldc = ldc;
+  J.pair0 = npairs;
+  J.npairs = np;
+  for (int i = 0; i < np; ++i) {
+    b.A[npairs] = A[i];
+    b.B[npairs] = B[i];
+    ++npairs;
+  }
+  const int bm = 16 * SimtCfg<float>::TM;
+  J.tiles_m = (rows + bm - 1) / bm;
+  J.tiles_n = (ncol + bm - 1) / bm;
+  J.tile0 = b.total_tiles;
+  J.alpha = 1.f;
+  J.C = C;
+  b.total_tiles += J.tiles_m * J.tiles_n;
+}
+
+static demag_status na_launch(demag_plan* P, const GemmBatch& b, cudaStream_t st) {
+  DEMAG_LAUNCH(P, kFamGemmSimt, st, gemm_tn_kernel<float><<<b.total_tiles, 256, 0, st>>>(b));
+  DEMAG_LAUNCHED(P, "gemm_tn_kernel (allocation-free)");
+  return DEMAG_OK;
+}
+
+}  // namespace demag
+
+extern "C" demag_status demag_apply_full_noalloc(const demag_grid_desc* d, const float* m, float* phi,
+                                                 void* stream) {
+  using namespace demag;
+  if (!d || !m || !phi) return set_error(nullptr, DEMAG_EINVAL, "demag_apply_full_noalloc: NULL pointer");
+  for (int p = 0; p < 3; ++p) {
+    if (d->n[p] < 1) return set_error(nullptr, DEMAG_EINVAL, "n[%d] = %d must be >= 1", p, d->n[p]);
+    if (!(d->h[p] > 0.0) || !std::isfinite(d->h[p]))
+      return set_error(nullptr, DEMAG_EINVAL, "h[%d] must be positive and finite", p);
+  }
+  if (d->R < 5 || d->R % 2 == 0)
+    return set_error(nullptr, DEMAG_EINVAL, "R = %d must be odd and >= 5 (R = 2M+1)", d->R);
+  if ((d->R - 1) / 2 > kMaxTerms)
+    return set_error(nullptr, DEMAG_EUNSUPPORTED, "R = %d exceeds 2*%d+1", d->R, kMaxTerms);
+  if (!(d->c0 > 0.0) || !std::isfinite(d->c0))
+    return set_error(nullptr, DEMAG_EINVAL, "c0 must be positive and finite");
+
+  // the fields of a plan this call needs, kept on the host stack
+  demag_plan P;
+  snprintf(P.err, sizeof(P.err), "no error");
+  P.R = d->R;
+  P.M = (d->R - 1) / 2;
+  P.c0 = d->c0;
+  P.s = 0.0;
+  P.nmax = 0;
+  for (int p = 0; p < 3; ++p) {
+    P.n[p] = d->n[p];
+    P.h[p] = d->h[p];
+    P.s = fmax(P.s, (double)d->n[p] * d->h[p]);
+    P.nmax = d->n[p] > P.nmax ? d->n[p] : P.nmax;
+  }
+  P.tgroup = 0;
+  for (int p = 0; p < 3; ++p) {
+    P.hh[p] = P.h[p] / P.s;
+    P.toff[p] = P.tgroup;
+    P.tgroup += (size_t)P.n[p] * P.n[p];
+  }
+  P.glen = 2 * P.nmax - 1;
+  const int M = P.M;
+  const size_t N = (size_t)P.n[0] * P.n[1] * P.n[2];
+
+  // scratch layout: nodes [3][M], scale [M], generators [M][2][3][glen] (FP64),
+  // dense factors [M][2][sum n_p^2] and the chain's fields Y (3) + U, V (2M) (FP32)
+  const size_t b_nodes = na_align(sizeof(double) * 3 * M);
+  const size_t b_scale = na_align(sizeof(double) * M);
+  const size_t b_gen = na_align(sizeof(double) * (size_t)M * 6 * P.glen);
+  const size_t b_fac = na_align(sizeof(float) * (size_t)M * 2 * P.tgroup);
+  const size_t b_ws = na_align(sizeof(float) * (2 * (size_t)M + 3) * N);
+  const size_t need = b_nodes + b_scale + b_gen + b_fac + b_ws;
+  if (need > kNoAllocBytes)
+    return set_error(nullptr, DEMAG_EUNSUPPORTED,
+                     "demag_apply_full_noalloc: this grid needs %zu bytes of scratch, the fixed maximum is %zu "
+                     "bytes (%d MiB); use demag_apply_full",
+                     need, kNoAllocBytes, (int)(kNoAllocBytes >> 20));
+
+  void* base = nullptr;
+  demag_status s = noalloc_address(&base);
+  if (s != DEMAG_OK) return s;
+  unsigned char* at = static_cast<unsigned char*>(base);
+  P.nodes = reinterpret_cast<double*>(at);
+  P.scale = reinterpret_cast<double*>(at + b_nodes);
+  P.gen64 = reinterpret_cast<double*>(at + b_nodes + b_scale);
+  float* T = reinterpret_cast<float*>(at + b_nodes + b_scale + b_gen);
+  float* Y = reinterpret_cast<float*>(at + b_nodes + b_scale + b_gen + b_fac);
+  float* UV = Y + 3 * N;
+  cudaStream_t st = (cudaStream_t)stream;
+
+  // setup: every scratch region below is fully written before it is read,
+  // so nothing has to be cleared between calls
+  DEMAG_LAUNCH(&P, kFamSetup, st, nodes_kernel<<<(M + 63) / 64, 64, 0, st>>>(M, P.c0, kCPot * P.s, P.nodes, P.scale));
+  DEMAG_LAUNCHED(&P, "nodes_kernel (allocation-free)");
+  GridInfo g;
+  for (int p = 0; p < 3; ++p) {
+    g.n[p] = P.n[p];
+    g.hh[p] = P.hh[p];
+  }
+  {
+    long total = (long)M * 6 * P.glen;
+    int blocks = (int)((total + 255) / 256);
+    if (blocks > 152 * 32) blocks = 152 * 32;
+    DEMAG_LAUNCH(&P, kFamSetup, st, generators_kernel<<<blocks, 256, 0, st>>>(M, P.glen, g, P.nodes, P.gen64));
+    DEMAG_LAUNCHED(&P, "generators_kernel (allocation-free)");
+  }
+  {
+    const size_t total = (size_t)M * 2 * P.tgroup;
+    int blocks = (int)((total + 255) / 256);
+    if (blocks > 152 * 64) blocks = 152 * 64;
+    DEMAG_LAUNCH(&P, kFamSetup, st,
+                 dense_factor_kernel<float><<<blocks, 256, 0, st>>>(M, P.glen, P.n[0], P.n[1], P.n[2], P.tgroup,
+                                                                    P.toff[1], P.toff[2], P.gen64, P.scale, T));
+    DEMAG_LAUNCHED(&P, "dense_factor_kernel (allocation-free)");
+  }
+
+  // the mode-product chain of demag_apply_full (DEMAG_FP32)
+  const int n1 = P.n[0], n2 = P.n[1], n3 = P.n[2];
+  for (int k = 0; k < M; ++k) {
+    GemmBatch b1;
+    b1.njobs = 0;
+    b1.total_tiles = 0;
+    int np = 0;
+    for (int q = 0; q < 3; ++q) {
+      const void* A[1] = {m + q * N};
+      const void* B[1] = {factor(&P, (const float*)T, k, q == 0 ? 1 : 0, 0)};
+      na_add(b1, np, n3 * n2, n1, n1, n3 * n2, Y + q * N, A, B, 1);
+    }
+    s = na_launch(&P, b1, st);
+    if (s != DEMAG_OK) return s;
+    GemmBatch b2;
+    b2.njobs = 0;
+    b2.total_tiles = 0;
+    np = 0;
+    const float* E2 = factor(&P, (const float*)T, k, 0, 1);
+    const float* F2 = factor(&P, (const float*)T, k, 1, 1);
+    {
+      const void* A[2] = {Y, Y + N};
+      const void* B[2] = {E2, F2};
+      na_add(b2, np, n1 * n3, n2, n2, n1 * n3, UV + (2 * k) * N, A, B, 2);
+    }
+    {
+      const void* A[1] = {Y + 2 * N};
+      const void* B[1] = {E2};
+      na_add(b2, np, n1 * n3, n2, n2, n1 * n3, UV + (2 * k + 1) * N, A, B, 1);
+    }
+    s = na_launch(&P, b2, st);
+    if (s != DEMAG_OK) return s;
+  }
+  GemmBatch b3;
+  b3.njobs = 0;
+  b3.total_tiles = 0;
+  int np = 0;
+  const void* A3[2 * kMaxTerms];
+  const void* B3[2 * kMaxTerms];
+  for (int k = 0; k < M; ++k) {
+    A3[2 * k] = UV + (2 * k) * N;
+    B3[2 * k] = factor(&P, (const float*)T, k, 0, 2);
+    A3[2 * k + 1] = UV + (2 * k + 1) * N;
+    B3[2 * k + 1] = factor(&P, (const float*)T, k, 1, 2);
+  }
+  na_add(b3, np, n2 * n1, n3, n3, n2 * n1, phi, A3, B3, 2 * M);
+  return na_launch(&P, b3, st);
+}

@@ -127,6 +127,14 @@ demag_status tc_sync_status(demag_plan* plan, cudaStream_t st);
 bool tc_ready(const demag_plan* plan, demag_precision prec);
 void tc_destroy(demag_plan* plan);
 
+// setup kernels (plan.cu)
+struct GridInfo {
+  int n[3];
+  double hh[3];
+};
+__global__ void nodes_kernel(int M, double c0, double cscale, double* nodes, double* scale);
+__global__ void generators_kernel(int M, int glen, GridInfo g, const double* nodes, double* gen);
+
 // energy (energy.cu)
 demag_status fd_gradient(demag_plan* plan, const float* phi, float* out, float scale,
                          cudaStream_t st);

@@ -77,11 +77,6 @@ __global__ void nodes_kernel(int M, double c0, double cscale, double* nodes, dou
   scale[k] = cscale * omega;
 }
 
-struct GridInfo {
-  int n[3];
-  double hh[3];
-};
-
 // E_k^(p)[d] and F_k^(p)[d] of Eq. f_anal for d = -(n_p-1)..n_p-1, FP64.
 // E, d != 0, uses erf(tau b) - erf(tau a) while tau a < 1/2 and otherwise
 // the tail form exp(-tau^2 a^2) (erfcx(tau a) - exp(-tau^2 (b^2-a^2)) erfcx(tau b)),
