@@ -95,9 +95,12 @@ struct TcParams {
   float alpha;
   int njobs, m_tiles, n_tiles, total_tiles;
   int* status;
+  int* tile_counter;                   // zeroed before the launch; tiles are taken in order
   TcJob jobs[kMaxTcJobs];
   short2 pairs[kMaxTcPairs];           // (A field, B matrix)
 };
+
+constexpr int kRing = 4;               // tile ids handed from the producer to the other roles
 
 __device__ __forceinline__ void tile_coords(const TcParams& p, int tile, int& j, int& mt, int& nt) {
   // job fastest: consecutive tiles share the A row block (L2 reuse across nodes)
@@ -122,7 +125,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const __grid_con
   uint64_t* tfull = empty + kStages;   // [2]
   uint64_t* tempty = tfull + 2;        // [2]
   uint64_t* drain = tempty + 2;        // [1]
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+  uint64_t* sfull = drain + 1;         // [kRing] a tile id is in the ring slot
+  uint64_t* sempty = sfull + kRing;    // [kRing] the MMA thread and the 4 epilogue warps read it
+  volatile int* ring = reinterpret_cast<volatile int*>(sempty + kRing);  // [kRing]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sempty + kRing) + kRing;
   volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -134,6 +140,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const __grid_con
     for (int b = 0; b < 2; ++b) {
       ptx::mbar_init(&tfull[b], 1);
       ptx::mbar_init(&tempty[b], 4);
+    }
+    for (int i = 0; i < kRing; ++i) {
+      ptx::mbar_init(&sfull[i], 1);
+      ptx::mbar_init(&sempty[i], 5);
     }
     ptx::mbar_init(drain, 1);
     *abort = 0;
@@ -158,7 +168,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const __grid_con
       const uint32_t bytes = 2 * kTileA + 2 * (uint32_t)p.bn * kRowBytes;
       int s = 0;
       uint32_t ph = 0;
-      for (int tile = blockIdx.x; tile < p.total_tiles && !*abort; tile += gridDim.x) {
+      int rs = 0;
+      uint32_t rph = 0;
+      while (!*abort) {
+        // take the next tile and hand its id to the MMA and epilogue roles
+        if (!ptx::mbar_wait(&sempty[rs], rph ^ 1, abort, kWaitNs)) {
+          tc_fail(abort, p.status);
+          break;
+        }
+        const int tile = atomicAdd(p.tile_counter, 1);
+        ring[rs] = tile < p.total_tiles ? tile : -1;
+        ptx::mbar_arrive(&sfull[rs]);
+        if (++rs == kRing) { rs = 0; rph ^= 1; }
+        if (tile >= p.total_tiles) break;
         int j, mt, nt;
         tile_coords(p, tile, j, mt, nt);
         const TcJob& J = p.jobs[j];
@@ -186,7 +208,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const __grid_con
       int s = 0;
       uint32_t ph = 0, tph = 0;
       int buf = 0;
-      for (int tile = blockIdx.x; tile < p.total_tiles && !*abort; tile += gridDim.x) {
+      int rs = 0;
+      uint32_t rph = 0;
+      while (!*abort) {
+        if (!ptx::mbar_wait(&sfull[rs], rph, abort, kWaitNs)) {
+          tc_fail(abort, p.status);
+          break;
+        }
+        const int tile = ring[rs];
+        ptx::mbar_arrive(&sempty[rs]);
+        if (++rs == kRing) { rs = 0; rph ^= 1; }
+        if (tile < 0) break;
         int j, mt, nt;
         tile_coords(p, tile, j, mt, nt);
         const TcJob& J = p.jobs[j];
@@ -235,7 +267,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const __grid_con
     const int rloc = quad * 32 + lane;
     int buf = 0;
     uint32_t tph = 0;
-    for (int tile = blockIdx.x; tile < p.total_tiles && !*abort; tile += gridDim.x) {
+    int rs = 0;
+    uint32_t rph = 0;
+    while (!*abort) {
+      if (!ptx::mbar_wait(&sfull[rs], rph, abort, kWaitNs)) {
+        tc_fail(abort, p.status);
+        break;
+      }
+      const int tile = ring[rs];
+      __syncwarp();
+      if (lane == 0) ptx::mbar_arrive(&sempty[rs]);
+      if (++rs == kRing) { rs = 0; rph ^= 1; }
+      if (tile < 0) break;
       int j, mt, nt;
       tile_coords(p, tile, j, mt, nt);
       const TcJob& J = p.jobs[j];
@@ -398,8 +441,36 @@ struct TcState {
   CUtensorMap mapB[3][2];
   CUtensorMap mapX[2], map1[2], map2[2];
   int* status;
+  int* counter;           // dynamic tile counter of the running launch
+  float* part;            // split node-sum partial fields
+  int pp3;                // (A, B) pairs per accumulator in the node-sum stage
   size_t bytes;
 };
+
+// The tensor cores accumulate into TMEM with FP32 additions that do not round
+// to nearest, so the error of a long contraction grows with the number of
+// MMAs accumulated into one accumulator.  The node-sum stage (2M pairs of
+// length n3) is therefore split into groups of at most ~400 accumulations,
+// whose FP32 partial fields are summed on CUDA cores in FP64.
+static int pairs_per_split(int kblocks) {
+  const int per_pair = kblocks * 6;  // 2 k-steps x 3 products per k-block
+  const int pp = 400 / (per_pair > 0 ? per_pair : 1);
+  return pp < 1 ? 1 : pp;
+}
+
+// out[q][i] = alpha * sum_g part[q*groups + g][i], accumulated in FP64
+__global__ void reduce_parts_kernel(const float* __restrict__ part, int groups, long long N, int nout, float alpha,
+                                    float* __restrict__ out) {
+  const long long total = (long long)nout * N;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const long long q = idx / N, i = idx - q * N;
+    const float* src = part + q * groups * N + i;
+    double acc = 0.0;
+    for (int g = 0; g < groups; ++g) acc += (double)src[g * N];
+    out[idx] = (float)(alpha * acc);
+  }
+}
 
 struct TcHolder {
   TcState* s[2] = {nullptr, nullptr};  // [0] BF16x3, [1] TF32x3
@@ -435,6 +506,8 @@ static void free_state(TcState* S) {
     cudaFree(S->buf2[h]);
   }
   cudaFree(S->status);
+  cudaFree(S->counter);
+  cudaFree(S->part);
   delete S;
 }
 
@@ -504,6 +577,15 @@ demag_status tc_prepare(demag_plan* P, demag_precision prec, cudaStream_t st) {
     ok = ok && alloc(&S->buf2[h], 3 * (size_t)M * n2 * n1 * S->ld[2] * e);
   }
   ok = ok && alloc((void**)&S->status, sizeof(int));
+  ok = ok && alloc((void**)&S->counter, sizeof(int));
+  {
+    const int kb3 = (n3 + kRowBytes / S->elem - 1) / (kRowBytes / S->elem);
+    S->pp3 = pairs_per_split(kb3);
+    const int gf = (2 * M + S->pp3 - 1) / S->pp3;   // forward: 2M pairs in one sum
+    const int ga = (M + S->pp3 - 1) / S->pp3;       // adjoint: M pairs per component
+    const int fields = gf > 3 * ga ? gf : 3 * ga;
+    ok = ok && alloc((void**)&S->part, sizeof(float) * (size_t)fields * n1 * n2 * n3);
+  }
   if (!ok) {
     free_state(S);
     return set_error(P, DEMAG_ENOMEM, "tensor-core workspace allocation failed");
@@ -567,12 +649,14 @@ static demag_status launch_stage(demag_plan* P, TcState* S, const StageDesc& d, 
   prm.n_tiles = (d.n_a + kBN - 1) / kBN;
   prm.total_tiles = prm.njobs * prm.m_tiles * prm.n_tiles;
   prm.status = S->status;
+  prm.tile_counter = S->counter;
   for (size_t i = 0; i < jobs.size(); ++i) prm.jobs[i] = jobs[i];
   for (size_t i = 0; i < pairs.size(); ++i) prm.pairs[i] = pairs[i];
   int sms = 0, dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int grid = prm.total_tiles < sms ? prm.total_tiles : sms;
+  DEMAG_CUDA(P, cudaMemsetAsync(S->counter, 0, sizeof(int), st));
   DEMAG_LAUNCH(P, kFamGemmTc, st, tc_gemm_kernel<F><<<grid, kTcThreads, kSmemBytes, st>>>(prm));
   DEMAG_LAUNCHED(P, "tc_gemm_kernel");
   return DEMAG_OK;
@@ -641,15 +725,22 @@ static demag_status forward_chain(demag_plan* P, TcState* S, const float* m, flo
   {
     std::vector<TcJob> jobs;
     std::vector<short2> pairs;
-    jobs.push_back(job(0, 2 * M, 0));
     for (int k = 0; k < M; ++k) {
       pairs.push_back(make_short2((short)(2 * k), mat(k, 0)));
       pairs.push_back(make_short2((short)(2 * k + 1), mat(k, 1)));
     }
+    const int groups = (2 * M + S->pp3 - 1) / S->pp3;
+    for (int g = 0; g < groups; ++g) {
+      const int p0 = g * S->pp3;
+      jobs.push_back(job(p0, (2 * M - p0) < S->pp3 ? (2 * M - p0) : S->pp3, g));
+    }
+    const long long N = (long long)n3 * n2 * n1;
     StageDesc d{{&S->map2[0], &S->map2[1]}, {&S->mapB[2][0], &S->mapB[2][1]}, n2 * n1, n3, n3, S->bn[2],
-                phi, nullptr, (long long)n3 * n2 * n1, (long long)n2 * n1, n1, n1, kOutF32, 1.f};
+                S->part, nullptr, N, (long long)n2 * n1, n1, n1, kOutF32, 1.f};
     s = launch_stage<F>(P, S, d, jobs, pairs, st);
     if (s != DEMAG_OK) return s;
+    DEMAG_LAUNCH(P, kFamMisc, st, reduce_parts_kernel<<<grid_blocks(N), 256, 0, st>>>(S->part, groups, N, 1, 1.f, phi));
+    DEMAG_LAUNCHED(P, "reduce_parts_kernel");
   }
   return DEMAG_OK;
 }
@@ -696,14 +787,23 @@ static demag_status adjoint_chain(demag_plan* P, TcState* S, const float* y, flo
   {
     std::vector<TcJob> jobs;
     std::vector<short2> pairs;
+    const int groups = (M + S->pp3 - 1) / S->pp3;
     for (int q = 0; q < 3; ++q) {
-      jobs.push_back(job((int)pairs.size(), M, q));
+      const int base = (int)pairs.size();
       for (int k = 0; k < M; ++k) pairs.push_back(make_short2((short)(3 * k + q), mat(k, q == 2 ? 1 : 0)));
+      for (int gi = 0; gi < groups; ++gi) {
+        const int p0 = gi * S->pp3;
+        jobs.push_back(job(base + p0, (M - p0) < S->pp3 ? (M - p0) : S->pp3, q * groups + gi));
+      }
     }
+    const long long N = (long long)n3 * n2 * n1;
     StageDesc d{{&S->map2[0], &S->map2[1]}, {&S->mapB[2][0], &S->mapB[2][1]}, n2 * n1, n3, n3, S->bn[2],
-                g, nullptr, (long long)n3 * n2 * n1, (long long)n2 * n1, n1, n1, kOutF32, -1.f};
+                S->part, nullptr, N, (long long)n2 * n1, n1, n1, kOutF32, 1.f};
     s = launch_stage<F>(P, S, d, jobs, pairs, st);
     if (s != DEMAG_OK) return s;
+    DEMAG_LAUNCH(P, kFamMisc, st,
+                 reduce_parts_kernel<<<grid_blocks(3 * N), 256, 0, st>>>(S->part, groups, N, 3, -1.f, g));
+    DEMAG_LAUNCHED(P, "reduce_parts_kernel");
   }
   return DEMAG_OK;
 }

@@ -43,6 +43,7 @@ struct demag_plan {
   double* gen64 = nullptr;   // [M][2][3][glen]
   float* sym = nullptr;      // [M][2][3][Lmax/2 + 1] symbols / L_p
   float2* twid[3] = {nullptr, nullptr, nullptr};  // per axis: exp(-2 pi i m / L_p), m < L_p
+  float2* sympair = nullptr; // [M][2][3][Lmax/2]: (symbol[f], symbol[L_p/2 - f]) for f < L_p/2
   double* scale = nullptr;   // [M]: c * s * omega_k
 
   // dense factor matrices of the full path, per precision (device, lazily built)

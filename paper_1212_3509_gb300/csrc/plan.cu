@@ -169,6 +169,18 @@ __global__ void __launch_bounds__(256) symbol_kernel(int M, int glen, int axis, 
   }
 }
 
+// (s[f], s[N - f]) pairs of one axis for the structured kernels, f < N = L_p/2
+__global__ void sympair_kernel(int M, int axis, int N, int symstride, int pairstride, const float* sym,
+                               float2* pair) {
+  const long total = (long)M * 2 * N;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
+    const int f = (int)(i % N);
+    const long kt = i / N;  // k*2 + type
+    const float* s = sym + (kt * 3 + axis) * symstride;
+    pair[(kt * 3 + axis) * pairstride + f] = make_float2(s[f], s[N - f]);
+  }
+}
+
 __global__ void twiddle_kernel(int L, float2* tw) {
   int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= L) return;
@@ -217,6 +229,7 @@ static void free_plan_buffers(demag_plan* P) {
   cudaFree(P->nodes);
   cudaFree(P->gen64);
   cudaFree(P->sym);
+  cudaFree(P->sympair);
   cudaFree(P->scale);
   for (int p = 0; p < 3; ++p) {
     bool dup = false;
@@ -328,6 +341,17 @@ extern "C" demag_status demag_build_factors(const demag_grid_desc* d, demag_plan
         TRY_CUDA(cudaGetLastError());
       }
       dispatch_symbol(P, p, st);
+      TRY_CUDA(cudaGetLastError());
+    }
+    TRY_CUDA(cudaMalloc(&P->sympair, sizeof(float2) * (size_t)M * 6 * (P->Lmax / 2)));
+    for (int p = 0; p < 3; ++p) {
+      const int N = P->L[p] / 2;
+      const long total = (long)M * 2 * N;
+      int blocks = (int)((total + 255) / 256);
+      if (blocks > 152 * 16) blocks = 152 * 16;
+      DEMAG_LAUNCH(P, kFamSetup, st,
+                   sympair_kernel<<<blocks, 256, 0, st>>>(M, p, N, P->Lmax / 2 + 1, P->Lmax / 2, P->sym,
+                                                          P->sympair));
       TRY_CUDA(cudaGetLastError());
     }
   }

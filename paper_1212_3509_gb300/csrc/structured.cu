@@ -9,19 +9,26 @@
 // of the generator: y = IFFT(FFT(v, L) * symbol)[0:n].  FP32 throughout; the
 // symbols were computed in FP64 at setup and carry the 1/L of the inverse.
 //
-// A group of TG threads owns one column.  It computes the column's real
-// spectrum once (shared memory) and then, for each node of its node range:
-//   pass 1  (registers)  symbol product and inverse split step for the bins
-//                        this thread's first radix pass reads, then the
-//                        first radix-R DFT, written to shared memory;
-//   middle  (shared)     radix-16 Stockham passes (ping-pong buffers padded
+// The real inverse transform of length L = 2N runs as a complex one of
+// length N on Z[f] = Y_f (1 + i conj(w_f)) + conj(Y_{N-f}) (1 - i conj(w_f)),
+// w_f = exp(-2 pi i f / L), Y = symbol * X.  With the per-column constants
+// P[f] = X_f (1 + i conj(w_f)) and Q[f] = conj(X_{N-f}) (1 - i conj(w_f)) this is
+//   E (real symbol s):        Z[f] = s_f P[f] + s_{N-f} Q[f]
+//   F (imaginary symbol i s): Z[f] = i (s_f P[f] - s_{N-f} Q[f]),
+// four multiply-adds per bin.
+//
+// A group of TG threads owns one column.  It computes P and Q once (shared
+// memory) and then, for each node of its node range:
+//   pass 1  (registers)  Z for the bins of this thread's first radix pass,
+//                        the first radix-R DFT, written to shared memory;
+//   middle  (shared)     radix-16 Stockham passes in place (one buffer padded
 //                        by one element per 16 so strided writes do not
 //                        collide in banks);
 //   last    (registers)  final radix-16 pass; only the outputs of the first
 //                        half of the complex signal (the n real samples we
-//                        keep) are computed into registers and stored to HBM.
-// Twiddles come from a two-level table in shared memory:
-// W_L^m = T1[m >> 7] * T0[m & 127].
+//                        keep) are computed and stored to HBM.
+// Twiddles: one value per item from a two-level shared table
+// (W_L^m = T1[m >> 7] * T0[m & 127]) and its powers by a product tree.
 #include "internal.h"
 #include "fft.cuh"
 
@@ -34,13 +41,13 @@ struct ToepLaunch {
   int rcols;       // columns per (batch item, component)
   int ncols;       // batch * 3 * rcols
   int kgroup;      // nodes per block (grid.y covers M)
-  int symstride;   // Lmax/2 + 1
+  int pairstride;  // Lmax/2
   const float* in; // column (b, q, l) at in + b*in_bstride + q*in_qstride + l*n
   long in_bstride, in_qstride;
   float* out;      // node k: out + b*out_bstride + ((k*3 + q)*rcols + l)*n
   long out_bstride;
-  const float* sym;    // [M][2][3][symstride]
-  const float2* twid;  // exp(-2 pi i m / L), m < L
+  const float2* sympair;  // [M][2][3][pairstride]: (s_f, s_{N-f})
+  const float2* twid;     // exp(-2 pi i m / L), m < L
 };
 
 __device__ __forceinline__ int pad16(int i) { return i + (i >> 4); }
@@ -55,9 +62,10 @@ template <int LOGN> struct ToepCfg {
   static constexpr int T1 = L / T0;                // coarse twiddle table
   static constexpr int R1 = (LOGN % 4) ? (1 << (LOGN % 4)) : (LOGN >= 4 ? 16 : 1);
   static constexpr int NPASS = LOGN / 4 + ((LOGN % 4) ? 1 : 0);
-  // per group: spectrum (N+1) and two padded buffers
-  static constexpr size_t group_floats2 = (size_t)(N + 1) + 2 * NP;
+  // per group: P, Q (N each) and one padded work buffer
+  static constexpr size_t group_floats2 = 2 * (size_t)N + NP;
   static constexpr size_t smem = ((size_t)T0 + T1 + G * group_floats2) * sizeof(float2);
+  static constexpr int minblocks = smem * 2 <= 220 * 1024 ? 2 : 1;
 };
 
 struct TwSmem {
@@ -66,15 +74,6 @@ struct TwSmem {
   // W_L^m
   __device__ __forceinline__ float2 L(int m) const { return cmul(t1[m >> 7], t0[m & 127]); }
 };
-
-// exp(-2 pi i j / 32): cos(pi j / 16) and -sin(pi j / 16), j < 32
-__device__ __forceinline__ constexpr double w32_re(int j) {
-  return j == 0 ? 1.0 : j == 1 ? 0.98078528040323044913 : j == 2 ? 0.92387953251128675613
-       : j == 3 ? 0.83146961230254523708 : j == 4 ? 0.70710678118654752440 : j == 5 ? 0.55557023301960222474
-       : j == 6 ? 0.38268343236508977173 : j == 7 ? 0.19509032201612826785 : j == 8 ? 0.0
-       : j < 16 ? -w32_re(16 - j) : -w32_re(j - 16);
-}
-__device__ __forceinline__ constexpr double w32_im(int j) { return -w32_re((j + 24) & 31); }
 
 // forward-FFT twiddle W_N^m = W_L^(2m) for the generic in-place routine
 struct TwN {
@@ -104,47 +103,55 @@ __device__ __forceinline__ void powers(float2 w, float2 (&pw)[R]) {
   }
 }
 
-// Pass with radix R reading src (padded) and writing dst (padded), Ns = size
-// of the sub-transforms already done.  Inverse direction.
+// In-place middle pass of radix R on the padded buffer (inverse direction):
+// every item is read into registers, the block synchronises, then writes.
 template <int R, int N, int TG>
-__device__ __forceinline__ void mid_pass(const float2* src, float2* dst, int Ns, int lt, const TwSmem& tw) {
+__device__ __forceinline__ void mid_pass(float2* buf, int Ns, int lt, const TwSmem& tw) {
   constexpr int items = N / R;
   constexpr int ipt = (items + TG - 1) / TG;
+  float2 v[ipt][R];
 #pragma unroll
   for (int it = 0; it < ipt; ++it) {
     const int j = lt + it * TG;
     if (items % TG == 0 || j < items) {
-      float2 v[R];
       const int k = j % Ns;
-      const int tstep = k * (N / (Ns * R));  // in units of W_N
-      float2 w = tw.L(2 * tstep);
-      w.y = -w.y;  // inverse
+      float2 w = tw.L(2 * k * (N / (Ns * R)));
+      w.y = -w.y;
       float2 pw[R];
       powers<R>(w, pw);
 #pragma unroll
       for (int r = 0; r < R; ++r) {
-        float2 x = src[pad16(j + r * items)];
-        v[r] = r > 0 ? cmul(x, pw[r]) : x;
+        const float2 x = buf[pad16(j + r * items)];
+        v[it][r] = r > 0 ? cmul(x, pw[r]) : x;
       }
-      dft_reg<R, true>(v);
-      const int base = (j / Ns) * Ns * R + k;
-#pragma unroll
-      for (int r = 0; r < R; ++r) dst[pad16(base + r * Ns)] = v[r];
+      dft_reg<R, true>(v[it]);
     }
   }
+  __syncthreads();
+#pragma unroll
+  for (int it = 0; it < ipt; ++it) {
+    const int j = lt + it * TG;
+    if (items % TG == 0 || j < items) {
+      const int k = j % Ns;
+      const int base = (j / Ns) * Ns * R + k;
+#pragma unroll
+      for (int r = 0; r < R; ++r) buf[pad16(base + r * Ns)] = v[it][r];
+    }
+  }
+  __syncthreads();
 }
 
 template <int LOGN>
-__global__ void __launch_bounds__(256, 2) toeplitz_fft_kernel(ToepLaunch a) {
+__global__ void __launch_bounds__(256, ToepCfg<LOGN>::minblocks) toeplitz_fft_kernel(ToepLaunch a) {
   using Cfg = ToepCfg<LOGN>;
   constexpr int N = Cfg::N, TG = Cfg::TG, R1 = Cfg::R1, NPASS = Cfg::NPASS;
   extern __shared__ float2 smem_c[];
   float2* t0 = smem_c;
   float2* t1 = t0 + Cfg::T0;
   const int g = threadIdx.x / TG, lt = threadIdx.x % TG;
-  float2* spec = t1 + Cfg::T1 + (size_t)g * Cfg::group_floats2;
-  float2* bufA = spec + (N + 1);
-  float2* bufB = bufA + Cfg::NP;
+  float2* Pm = t1 + Cfg::T1 + (size_t)g * Cfg::group_floats2;
+  float2* Qm = Pm + N;
+  float2* buf = Qm + N;
   for (int i = threadIdx.x; i < Cfg::T0; i += blockDim.x) t0[i] = __ldg(a.twid + i);
   for (int i = threadIdx.x; i < Cfg::T1; i += blockDim.x) t1[i] = __ldg(a.twid + i * Cfg::T0);
   const TwSmem tw{t0, t1};
@@ -164,23 +171,38 @@ __global__ void __launch_bounds__(256, 2) toeplitz_fft_kernel(ToepLaunch a) {
       if (2 * j < n) x0 = __ldg(in + 2 * j);
       if (2 * j + 1 < n) x1 = __ldg(in + 2 * j + 1);
     }
-    bufA[j] = make_float2(x0, x1);
+    buf[j] = make_float2(x0, x1);
   }
   __syncthreads();
-  fft_inplace<LOGN, TG, false>(bufA, lt, TwN{tw});
+  fft_inplace<LOGN, TG, false>(buf, lt, TwN{tw});
 
-  // 2. split step: spectrum of the real signal, bins 0..N
-  for (int f = lt; f <= N; f += TG) {
-    float2 A = bufA[f & (N - 1)], B = bufA[(N - f) & (N - 1)];
+  // 2. split step to the real spectrum X and the per-column constants P, Q
+  for (int f = lt; f < N; f += TG) {
+    const int fc = (N - f) & (N - 1);
+    const float2 A = buf[f], B = buf[fc];
+    const float2 w = tw.L(f);                  // w_f
+    const float2 wc = make_float2(-w.x, w.y);  // w_{N-f} = -conj(w_f)
+    // X_f = (A + conj B)/2 - i/2 w_f (A - conj B); X_{N-f} with A, B swapped
     float ex = 0.5f * (A.x + B.x), ey = 0.5f * (A.y - B.y);
     float dx = 0.5f * (A.x - B.x), dy = 0.5f * (A.y + B.y);
-    float2 w = tw.L(f);  // exp(-2 pi i f / L)
     float wx = w.x * dx - w.y * dy, wy = w.x * dy + w.y * dx;
-    spec[f] = make_float2(ex + wy, ey - wx);
+    const float2 Xf = make_float2(ex + wy, ey - wx);
+    ex = 0.5f * (B.x + A.x);
+    ey = 0.5f * (B.y - A.y);
+    dx = 0.5f * (B.x - A.x);
+    dy = 0.5f * (B.y + A.y);
+    wx = wc.x * dx - wc.y * dy;
+    wy = wc.x * dy + wc.y * dx;
+    const float2 Xc = make_float2(ex + wy, ey - wx);
+    // 1 + i conj(w) and 1 - i conj(w)
+    const float2 up = make_float2(1.f + w.y, w.x), um = make_float2(1.f - w.y, -w.x);
+    Pm[f] = cmul(Xf, up);
+    Qm[f] = cmul(make_float2(Xc.x, -Xc.y), um);
   }
   __syncthreads();
 
   const int type = (a.axis == q) ? 1 : 0;  // F on the axis of the component
+  const float fsign = type ? -1.f : 1.f;
   const int k0 = blockIdx.y * a.kgroup;
   const int k1 = min(a.M, k0 + a.kgroup);
   float* outbase = a.out + b * a.out_bstride + (long)l * n;
@@ -188,40 +210,25 @@ __global__ void __launch_bounds__(256, 2) toeplitz_fft_kernel(ToepLaunch a) {
   // (every (k, q) offset is a multiple of n, so one check per column)
   const bool vec = ((n & 1) == 0) && ((reinterpret_cast<uintptr_t>(outbase) & 7) == 0);
   for (int k = k0; k < k1; ++k) {
-    const float* s = a.sym + ((long)(k * 2 + type) * 3 + a.axis) * a.symstride;
-    // 3. first pass in registers: symbol product + inverse split step feed
-    //    the radix-R1 DFT of the items j = lt + it*TG (bins j + r N/R1)
+    const float2* sp = a.sympair + ((long)(k * 2 + type) * 3 + a.axis) * a.pairstride;
+    // 3. first pass in registers on the bins j + r N/R1 of item j
     constexpr int items1 = N / R1;
     constexpr int ipt1 = (items1 + TG - 1) / TG;
-    float2* dst1 = (NPASS <= 1) ? nullptr : bufA;
 #pragma unroll
     for (int it = 0; it < ipt1; ++it) {
       const int j = lt + it * TG;
       if (items1 % TG == 0 || j < items1) {
         float2 v[R1];
-        // exp(-2 pi i f / L) for f = j + r N/R1 is W_L^j times the 2 R1-th root W^r
-        const float2 wj = tw.L(j);
 #pragma unroll
         for (int r = 0; r < R1; ++r) {
           const int f = j + r * items1;
-          float2 Yf = spec[f], Yc = spec[N - f];
-          const float sf = __ldg(s + f), sc = __ldg(s + N - f);
-          if (type == 0) {
-            Yf.x *= sf; Yf.y *= sf;
-            Yc.x *= sc; Yc.y *= sc;
-          } else {  // times i * s
-            const float t0v = Yf.x;
-            Yf.x = -Yf.y * sf; Yf.y = t0v * sf;
-            const float t1v = Yc.x;
-            Yc.x = -Yc.y * sc; Yc.y = t1v * sc;
-          }
-          // Ze = Yf + conj(Yc); Zo = (Yf - conj(Yc)) exp(+2 pi i f / L); Z = Ze + i Zo
-          const float zex = Yf.x + Yc.x, zey = Yf.y - Yc.y;
-          const float dx = Yf.x - Yc.x, dy = Yf.y + Yc.y;
-          const float2 cr = make_float2((float)w32_re((r * 16 / R1) & 31), (float)w32_im((r * 16 / R1) & 31));
-          const float2 w = r == 0 ? wj : cmul(wj, cr);
-          const float zox = w.x * dx + w.y * dy, zoy = w.x * dy - w.y * dx;
-          v[r] = make_float2(zex - zoy, zey + zox);
+          const float2 s2 = __ldg(sp + f);
+          const float2 P = Pm[f], Q = Qm[f];
+          // E: s_f P + s_c Q ;  F: i (s_f P - s_c Q)
+          const float sc = fsign * s2.y;
+          const float zx = fmaf(s2.x, P.x, sc * Q.x);
+          const float zy = fmaf(s2.x, P.y, sc * Q.y);
+          v[r] = type ? make_float2(-zy, zx) : make_float2(zx, zy);
         }
         dft_reg<R1, true>(v);
         if constexpr (NPASS <= 1) {
@@ -237,23 +244,17 @@ __global__ void __launch_bounds__(256, 2) toeplitz_fft_kernel(ToepLaunch a) {
           }
         } else {
 #pragma unroll
-          for (int r = 0; r < R1; ++r) dst1[pad16(j * R1 + r)] = v[r];
+          for (int r = 0; r < R1; ++r) buf[pad16(j * R1 + r)] = v[r];
         }
       }
     }
     if constexpr (NPASS > 1) {
       __syncthreads();
-      // 4. middle radix-16 passes, ping-pong A -> B -> A ...
-      float2* src = bufA;
-      float2* dst = bufB;
+      // 4. middle radix-16 passes in place
       int Ns = R1;
 #pragma unroll
       for (int ps = 1; ps < NPASS - 1; ++ps) {
-        mid_pass<16, N, TG>(src, dst, Ns, lt, tw);
-        __syncthreads();
-        float2* t = src;
-        src = dst;
-        dst = t;
+        mid_pass<16, N, TG>(buf, Ns, lt, tw);
         Ns *= 16;
       }
       // 5. last radix-16 pass (Ns = N/16): outputs j + r N/16, keep r < 8
@@ -270,7 +271,7 @@ __global__ void __launch_bounds__(256, 2) toeplitz_fft_kernel(ToepLaunch a) {
           powers<16>(w, pw);
 #pragma unroll
           for (int r = 0; r < 16; ++r) {
-            const float2 x = src[pad16(j + r * items)];
+            const float2 x = buf[pad16(j + r * items)];
             v[r] = r > 0 ? cmul(x, pw[r]) : x;
           }
           dft_reg<16, true>(v);
@@ -344,8 +345,8 @@ static cudaError_t run_toep(demag_plan* P, ToepLaunch a, cudaStream_t st) {
   const int logn = ilog2i(P->L[a.axis] / 2);
   a.n = P->n[a.axis];
   a.M = P->M;
-  a.symstride = P->Lmax / 2 + 1;
-  a.sym = P->sym;
+  a.pairstride = P->Lmax / 2;
+  a.sympair = P->sympair;
   a.twid = P->twid[a.axis];
   // node grouping: enough blocks to fill the GPU, spectra reused across nodes
   int gx = (a.ncols + groups_per_block(logn) - 1) / groups_per_block(logn);
@@ -373,7 +374,7 @@ static cudaError_t run_toep(demag_plan* P, ToepLaunch a, cudaStream_t st) {
 
 static demag_status check_fft_plan(demag_plan* P, const char* what) {
   if (!P) return set_error(nullptr, DEMAG_EINVAL, "%s: plan is NULL", what);
-  if (!P->sym)
+  if (!P->sym || !P->sympair)
     return set_error(P, DEMAG_EUNSUPPORTED, "%s: n_p up to %d supported by the FFT path", what,
                      1 << kMaxFFTLog);
   return DEMAG_OK;
