@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--form", default="auto", help="auto | fp32 | fp64 | tf32x3 | bf16x3")
     ap.add_argument("--cp-n", type=int, default=4096)
     ap.add_argument("--cp-batch", type=int, default=256)
+    ap.add_argument("--batch-grids", type=int, default=64, help="uneven full-format batch size (0: skip)")
     ap.add_argument("--no-oracle", action="store_true", help="skip the oracle error check and CPU baseline")
     return ap.parse_args()
 
@@ -227,21 +228,51 @@ def run_ours(args, world, rank, local):
         peak, bound = FP32_SIMT_PEAK_TFLOPS, "alu"
         peak_note = "FP32 FMA peak from unit counts and max clock (152 SMs x 128 lanes x 2 x 2.07 GHz)"
 
-    # e2e through the public API with pinned host buffers
-    m_pin = torch.from_numpy(m_host).pin_memory()
-    phi_pin = torch.empty(phi.shape, dtype=torch.float32).pin_memory()
-    m_dev2 = torch.empty_like(m)
+    # e2e through the public API with pinned host buffers: every step copies its
+    # m from pinned host memory, applies the operator and reads phi back; steps
+    # are double-buffered so step i+1's upload overlaps step i's compute
+    m_pin = [torch.from_numpy(m_host).pin_memory() for _ in range(2)]
+    phi_pin = [torch.empty(phi.shape, dtype=torch.float32).pin_memory() for _ in range(2)]
+    m_dev = [torch.empty_like(m) for _ in range(2)]
+    phi_dev = [torch.empty_like(phi) for _ in range(2)]
+    up = torch.cuda.Stream()
+    down = torch.cuda.Stream()
+    ev_up = [torch.cuda.Event() for _ in range(2)]
+    ev_done = [torch.cuda.Event() for _ in range(2)]
+    ev_free = [torch.cuda.Event() for _ in range(2)]
+    ev_read = [torch.cuda.Event() for _ in range(2)]
 
-    def e2e_fn():
-        m_dev2.copy_(m_pin, non_blocking=True)
-        D.demag_apply_full(P, m_dev2, phi, form)
-        phi_pin.copy_(phi, non_blocking=True)
+    def e2e_run(steps):
+        for i in range(steps):
+            b = i % 2
+            with torch.cuda.stream(up):
+                up.wait_event(ev_free[b])            # compute of step i-2 has consumed m_dev[b]
+                m_dev[b].copy_(m_pin[b], non_blocking=True)
+                ev_up[b].record(up)
+            stream.wait_event(ev_up[b])
+            stream.wait_event(ev_read[b])            # phi of step i-2 has been read back
+            D.demag_apply_full(P, m_dev[b], phi_dev[b], form, stream=stream)
+            ev_free[b].record(stream)
+            ev_done[b].record(stream)
+            with torch.cuda.stream(down):
+                down.wait_event(ev_done[b])
+                phi_pin[b].copy_(phi_dev[b], non_blocking=True)
+                ev_read[b].record(down)
 
-    for _ in range(max(1, args.warmup)):
-        e2e_fn()
+    e2e_run(max(2, args.warmup))
     torch.cuda.synchronize()
     barrier(world)
-    ms_e2e = max_over_ranks(time_region(e2e_fn, args.steps, stream), world)
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_stop = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    up.wait_stream(stream)
+    down.wait_stream(stream)
+    e2e_run(args.steps)
+    stream.wait_stream(up)
+    stream.wait_stream(down)
+    t_stop.record(stream)
+    t_stop.synchronize()
+    ms_e2e = max_over_ranks(t_start.elapsed_time(t_stop) / args.steps, world)
 
     # ---------------- CP, n = 4096, batched
     ncp = args.cp_n
@@ -268,10 +299,23 @@ def run_ours(args, world, rank, local):
     fft_ms, fft_n = D.demag_profile_read(PC, "fft")
     ms_cp_max = max_over_ranks(ms_cp, world)
     bytes_app = 4.0 * (9 * r * ncp + 3 * r) + 4.0 * (Mc * 3 * r * 3 * ncp + Mc * 3 * r)
-    sym_bytes = 4.0 * Mc * 2 * (ncp + 1)  # symbols of one axis per launch (all axes share n and h)
-    fft_launch_bytes = B * bytes_app / 3.0 + sym_bytes  # one launch per mode
-    fft_gbs = fft_launch_bytes / ((fft_ms / fft_n) * 1e-3) / 1e9
+    sym_bytes = 4.0 * Mc * 2 * (ncp + 1)  # symbol pairs of one axis (read once per axis)
+    # all three modes run in one launch per batch (they share the FFT length)
+    fft_batch_ms = fft_ms / args.steps
+    fft_batch_bytes = B * bytes_app + 3 * sym_bytes
+    fft_gbs = fft_batch_bytes / (fft_batch_ms * 1e-3) / 1e9
     hbm = peaks.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"])
+    # algorithmic FFT flops per application: 2.5 L log2 L per real transform of
+    # length L = 2n (36 forward, 30*36 inverse), plus 2 flops per symbol product bin
+    import math
+    Lc = 2 * ncp
+    fft_flops_app = (9 * r + Mc * 9 * r) * 2.5 * Lc * math.log2(Lc) + Mc * 9 * r * 2 * (Lc // 2 + 1)
+    fft_tflops = B * fft_flops_app / (fft_batch_ms * 1e-3) / 1e12
+
+    # ---------------- uneven batch: 64 grids of mixed shape, BF16x3, CUDA graph
+    batch = None
+    if args.batch_grids > 0:
+        batch = run_uneven_batch(args, D, world, local, stream, form="bf16x3")
 
     result = {
         "metric": METRIC,
@@ -297,14 +341,21 @@ def run_ours(args, world, rank, local):
                      "frac": achieved_tflops / peak, "traffic": None,
                      "algorithmic_flops_per_app": flops_app, "launches_per_app": gemm_n / args.steps,
                      "kernel_ms_per_app": gemm_ms_app, "peak_source": peak_note,
-                     "split_ms_per_app": split_ms / args.steps},
+                     "split_ms_per_app": split_ms / args.steps,
+                     # the split forms issue 3 tensor-core products per algorithmic product
+                     "tensor_pipe_issued_tflops": achieved_tflops * (3 if fam == "gemm_tc" else 1),
+                     "tensor_pipe_issued_frac": achieved_tflops * (3 if fam == "gemm_tc" else 1) / peak},
         "cp": {"value": world * B * 1e3 / ms_cp_max, "unit": "apps/s", "ms_per_batch": ms_cp_max,
                "batch": B,
-               "roofline": {"kernel": "toeplitz_fft_kernel", "bound": "hbm", "achieved": fft_gbs, "peak": hbm,
-                            "unit": "GB/s", "frac": fft_gbs / hbm, "traffic": None,
+               "roofline": {"kernel": "toeplitz_fft_kernel", "bound": "alu", "achieved": fft_tflops,
+                            "peak": FP32_SIMT_PEAK_TFLOPS, "unit": "TFLOP/s",
+                            "frac": fft_tflops / FP32_SIMT_PEAK_TFLOPS, "traffic": None,
+                            "algorithmic_flops_per_app": fft_flops_app,
+                            "hbm_achieved_gbs": fft_gbs, "hbm_peak_gbs": hbm, "hbm_frac": fft_gbs / hbm,
                             "algorithmic_bytes_per_app": bytes_app, "launches_per_batch": fft_n / args.steps,
                             "kernel_ms_per_batch": fft_ms / args.steps,
-                            "peak_source": f"{peak_src} STREAM copy"},
+                            "peak_source": "FP32 FMA peak from unit counts and max clock; HBM: "
+                                           f"{peak_src} STREAM copy"},
                "gpu_launches": launches_cp,
                "clocks": clk_cp.summary()},
         "e2e": {"value": world * 1e3 / ms_e2e, "unit": "apps/s",
@@ -351,7 +402,73 @@ def run_ours(args, world, rank, local):
         result["cp"]["rel_l2"] = float(np.linalg.norm(got_cp - ref_cp) / np.linalg.norm(ref_cp))
         result["cpu_baseline"] = cpu_baseline(n3, h, R, m_host, budget_s=20.0)
     result["forms_full"] = forms
+    if batch is not None:
+        if not args.no_oracle and rank == 0:
+            from oracle import full as ofull
+            errs = []
+            for i in batch.pop("_check"):
+                sn, sh, sR = batch["_shapes"][i], batch["_h"][i], 41
+                lines = [(0, 0), (sn[2] // 2, sn[1] - 1)]
+                ref = ofull.apply_full_lines(batch["_m"][i], sn, sh, sR, lines)
+                g = batch["_phi"][i].cpu().numpy()
+                got = np.stack([g[i3, i2] for i3, i2 in lines])
+                errs.append(float(np.linalg.norm(got - ref) / np.linalg.norm(ref)))
+            batch["rel_l2_sampled_max"] = max(errs)
+            batch["rel_l2_sample"] = "2 output lines of the first cube and the first 512x512x4 film vs the FP64 oracle"
+        for k in [k for k in batch if k.startswith("_")]:
+            del batch[k]
+        result["uneven_batch"] = batch
     print(json.dumps(result), flush=True)
+
+
+def run_uneven_batch(args, D, world, local, stream, form):
+    """64 full-format grids of mixed shape (cubes 32^3..192^3, 512x512x4 and
+    256x64x8 films), R = 41, one grouped tensor-core launch per mode-product
+    stage, replayed as a CUDA graph; compared with one call per grid."""
+    import numpy as np
+    import torch
+    import synth
+    shapes = synth.uneven_batch_shapes(args.batch_grids, 1215)
+    plans, ms, phis, ms_host, hs = [], [], [], [], []
+    for i, sn in enumerate(shapes):
+        sh = (1.0 / max(sn),) * 3
+        P = D.demag_build_factors(sn, sh, 41)
+        D.demag_reserve_workspace(P, form)
+        mh = synth.random_unit_m(sn, 1216 + i)
+        plans.append(P)
+        ms_host.append(mh)
+        hs.append(sh)
+        ms.append(torch.from_numpy(mh).cuda())
+        phis.append(torch.empty(sn[2], sn[1], sn[0], device="cuda"))
+    M = plans[0].M
+    flops = sum(2.0 * M * (a * b * c) * (3 * a + 3 * b + 2 * c) for a, b, c in shapes)
+    G = D.demag_graph_create_batched(plans, ms, phis, form)
+    graph_fn = lambda: G.launch(stream)  # noqa: E731
+    seq_fn = lambda: [D.demag_apply_full(P, m, f, form) for P, m, f in zip(plans, ms, phis)]  # noqa: E731
+    for _ in range(args.warmup):
+        graph_fn()
+        seq_fn()
+    torch.cuda.synchronize()
+    steps = max(3, args.steps)
+    l0 = D.demag_launch_count(plans[0])
+    barrier(world)
+    with ClockSampler(local) as clk:
+        ms_graph = time_region(graph_fn, steps, stream)
+    launches = (D.demag_launch_count(plans[0]) - l0) // steps
+    ms_seq = time_region(seq_fn, steps, stream)
+    graph_fn()
+    torch.cuda.synchronize()
+    for P in plans:
+        D.demag_sync_status(P)
+    ms_graph = max_over_ranks(ms_graph, world)
+    check = [0, next(i for i, s in enumerate(shapes) if s == (512, 512, 4))]
+    return {"grids": len(shapes), "form": form, "value": world * len(shapes) * 1e3 / ms_graph,
+            "unit": "grids/s", "ms_per_batch": ms_graph, "ms_per_batch_one_call_per_grid": ms_seq,
+            "algorithmic_tflops": flops / (ms_graph * 1e-3) / 1e12, "algorithmic_flops_per_batch": flops,
+            "cells": int(sum(a * b * c for a, b, c in shapes)),
+            "shapes": {f"{a}x{b}x{c}": shapes.count((a, b, c)) for a, b, c in sorted(set(shapes))},
+            "gpu_launches": int(launches), "graph_kernels": G.kernels, "clocks": clk.summary(),
+            "_check": check, "_shapes": shapes, "_h": hs, "_m": ms_host, "_phi": phis}
 
 
 def cpu_baseline(n3, h, R, m_host, budget_s):

@@ -131,10 +131,36 @@ demag_status demag_apply_full(demag_plan* plan, const float* m, float* phi,
 /* Apply several plans' operators in one call: phi[i] = P_i m[i] for
  * i < count.  Arrays of device pointers live in HOST memory.  Grids may
  * differ in shape; every plan must already have its workspace for `prec`
- * (made by a previous demag_apply_full or demag_reserve_workspace). */
+ * (made by a previous demag_apply_full or demag_reserve_workspace).
+ * With DEMAG_TF32X3 / DEMAG_BF16X3 each of the three mode-product stages of
+ * all listed grids is ONE persistent tensor-core launch (tiles of every grid
+ * drawn from one work counter); a plan listed twice starts a second such
+ * group after the first.  Device-side errors of a group are reported on its
+ * first plan (demag_sync_status).  The grouped descriptors are cached on the
+ * first plan for the last list seen; the first call with a new list
+ * allocates them. */
 demag_status demag_apply_full_batched(demag_plan* const* plans, const float* const* m,
                                       float* const* phi, int count, demag_precision prec,
                                       void* stream);
+
+/* ---- CUDA-graph form of the batched apply --------------------------------
+ * demag_graph_create_batched records everything demag_apply_full_batched
+ * would launch for these plans and pointers into a CUDA graph (captured on a
+ * stream of the library's own, nothing runs), instantiates it and returns a
+ * handle; demag_graph_launch replays it on `stream`.  The plans must be
+ * distinct, have their workspace for `prec`, and outlive the graph; the
+ * pointers m[i], phi[i] are baked in (update the buffers, not the pointers).
+ * Replays of one graph, and calls on the same plans, must not overlap in
+ * time (they share the plans' intermediates).  Kernel-family profiling
+ * (demag_profile) does not see graph replays. */
+typedef struct demag_graph demag_graph;
+demag_status demag_graph_create_batched(demag_plan* const* plans, const float* const* m,
+                                        float* const* phi, int count, demag_precision prec,
+                                        demag_graph** out);
+demag_status demag_graph_launch(demag_graph* graph, void* stream);
+/* Kernels one replay launches (the graph's kernel nodes). */
+int demag_graph_kernel_count(const demag_graph* graph);
+void demag_graph_destroy(demag_graph* graph);
 
 /* Allocate the full-format workspace of `prec` now (idempotent). */
 demag_status demag_reserve_workspace(demag_plan* plan, demag_precision prec);
@@ -247,6 +273,28 @@ unsigned long long demag_launch_count(const demag_plan* plan);
  * Reading waits for the recorded events. */
 demag_status demag_profile(demag_plan* plan, int enable);
 demag_status demag_profile_read(demag_plan* plan, int family, double* total_ms, long long* launches);
+
+/* ---- autotuning (build-only; no counterpart in the paper) --------------- */
+
+/* demag_autotune(plan, 1) turns tuning on for this plan: from then on
+ *  - the first Toeplitz-FFT launch of each shape (FFT length, number of column
+ *    blocks, M) times every node-group size M, M/2, ..., 1 (one warm-up and
+ *    three timed launches each, on the call's stream, which is synchronised)
+ *    and keeps the fastest for later launches of that shape;
+ *  - tensor-core state created afterwards (first DEMAG_TF32X3 / DEMAG_BF16X3
+ *    use) times, per mode-product stage, the output-column tile widths
+ *    {default, 128, 64} below the default (zero operands, stage timed alone)
+ *    and keeps the fastest.
+ * The tuning launches write the call's own outputs, so results are those of
+ * an untuned call.  No tuning happens while the stream is being captured.
+ * demag_autotune(plan, 0) stops tuning and keeps what was chosen. */
+demag_status demag_autotune(demag_plan* plan, int enable);
+/* Number of tuned shapes, and entry i of them: kind (0 FFT node group, 1 BF16x3
+ * tile width, 2 TF32x3 tile width), key (FFT: log2 of the complex FFT length,
+ * column blocks, M; tensor core: stage program 0..5, default width, 0), the
+ * chosen value and its time per launch in ms. */
+int demag_autotune_count(const demag_plan* plan);
+demag_status demag_autotune_entry(const demag_plan* plan, int i, int* kind, int key[3], int* value, float* ms);
 
 #ifdef __cplusplus
 }

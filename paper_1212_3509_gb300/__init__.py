@@ -9,6 +9,7 @@ There is no CPU fallback: importing the package requires the built library
 """
 from ._abi import (  # noqa: F401
     DemagError,
+    Graph,
     Plan,
     PRECISIONS,
     LIB_PATH,
@@ -19,12 +20,19 @@ from ._abi import (  # noqa: F401
     demag_apply_full_batched,
     demag_apply_tt,
     demag_apply_tucker,
+    demag_autotune,
+    demag_autotune_count,
+    demag_autotune_entry,
     demag_build_factors,
     demag_copy_generators,
     demag_copy_nodes,
     demag_copy_symbols,
     demag_energy,
     demag_generators_size,
+    demag_graph_create_batched,
+    demag_graph_destroy,
+    demag_graph_kernel_count,
+    demag_graph_launch,
     demag_last_error,
     demag_num_terms,
     demag_plan_destroy,

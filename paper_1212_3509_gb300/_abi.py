@@ -47,6 +47,11 @@ _SIGS = {
     "demag_symbols_size": (_sz, [_vp]),
     "demag_apply_full": (_i, [_vp, _vp, _vp, _i, _vp]),
     "demag_apply_full_batched": (_i, [ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i, _i, _vp]),
+    "demag_graph_create_batched": (_i, [ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i, _i,
+                                        ctypes.POINTER(_vp)]),
+    "demag_graph_launch": (_i, [_vp, _vp]),
+    "demag_graph_kernel_count": (_i, [_vp]),
+    "demag_graph_destroy": (None, [_vp]),
     "demag_reserve_workspace": (_i, [_vp, _i]),
     "demag_apply_adjoint": (_i, [_vp, _vp, _vp, _i, _vp]),
     "demag_apply_cp": (_i, [_vp, _i, _vp, _vp, _vp, _vp, _vp]),
@@ -58,6 +63,10 @@ _SIGS = {
     "demag_sync_status": (_i, [_vp, _vp]),
     "demag_apply_full_noalloc": (_i, [ctypes.POINTER(GridDesc), _vp, _vp, _vp]),
     "demag_launch_count": (ctypes.c_ulonglong, [_vp]),
+    "demag_autotune": (_i, [_vp, _i]),
+    "demag_autotune_count": (_i, [_vp]),
+    "demag_autotune_entry": (_i, [_vp, _i, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i),
+                                  ctypes.POINTER(ctypes.c_float)]),
     "demag_profile": (_i, [_vp, _i]),
     "demag_profile_read": (_i, [_vp, _i, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]),
 }
@@ -185,12 +194,60 @@ def demag_apply_full(plan: Plan, m, phi, precision="fp32", stream=None):
 
 
 def demag_apply_full_batched(plans, ms, phis, precision="bf16x3", stream=None):
+    cnt, P, Mp, Fp = _batch_arrays(plans, ms, phis)
+    _check(lib.demag_apply_full_batched(P, Mp, Fp, cnt, _prec(precision), _stream(stream)))
+
+
+def _batch_arrays(plans, ms, phis):
     import torch
     cnt = len(plans)
     P = (_vp * cnt)(*[p.ptr for p in plans])
     Mp = (_vp * cnt)(*[_ptr(m, 3 * p.N, torch.float32, "m") for m, p in zip(ms, plans)])
     Fp = (_vp * cnt)(*[_ptr(f, p.N, torch.float32, "phi") for f, p in zip(phis, plans)])
-    _check(lib.demag_apply_full_batched(P, Mp, Fp, cnt, _prec(precision), _stream(stream)))
+    return cnt, P, Mp, Fp
+
+
+class Graph:
+    """Owns a demag_graph* (a captured batched apply).  Keeps the plans and
+    tensors it was recorded with alive while it exists."""
+
+    def __init__(self, ptr: int, plans, ms, phis):
+        self.ptr = ptr
+        self._keep = (list(plans), list(ms), list(phis))
+        self.kernels = lib.demag_graph_kernel_count(ptr)
+
+    def launch(self, stream=None):
+        demag_graph_launch(self, stream)
+
+    def close(self):
+        if self.ptr:
+            lib.demag_graph_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def demag_graph_create_batched(plans, ms, phis, precision="bf16x3") -> Graph:
+    cnt, P, Mp, Fp = _batch_arrays(plans, ms, phis)
+    out = _vp()
+    _check(lib.demag_graph_create_batched(P, Mp, Fp, cnt, _prec(precision), ctypes.byref(out)))
+    return Graph(out.value, plans, ms, phis)
+
+
+def demag_graph_launch(graph: Graph, stream=None):
+    _check(lib.demag_graph_launch(graph.ptr, _stream(stream)))
+
+
+def demag_graph_kernel_count(graph: Graph) -> int:
+    return lib.demag_graph_kernel_count(graph.ptr)
+
+
+def demag_graph_destroy(graph: Graph):
+    graph.close()
 
 
 def demag_reserve_workspace(plan: Plan, precision="fp32"):
@@ -253,6 +310,27 @@ def demag_energy(plan: Plan, m, energy, grad=None, precision="fp32", stream=None
 
 def demag_sync_status(plan: Plan, stream=None):
     _check(lib.demag_sync_status(plan.ptr, _stream(stream)), plan.ptr)
+
+
+def demag_autotune(plan: Plan, enable: bool = True):
+    _check(lib.demag_autotune(plan.ptr, int(bool(enable))), plan.ptr)
+
+
+def demag_autotune_count(plan: Plan) -> int:
+    return lib.demag_autotune_count(plan.ptr)
+
+
+TUNE_KINDS = {0: "fft_node_group", 1: "bf16x3_tile_width", 2: "tf32x3_tile_width"}
+
+
+def demag_autotune_entry(plan: Plan, i: int) -> dict:
+    kind, value = _i(), _i()
+    key = (_i * 3)()
+    ms = ctypes.c_float()
+    _check(lib.demag_autotune_entry(plan.ptr, int(i), ctypes.byref(kind), key, ctypes.byref(value),
+                                    ctypes.byref(ms)), plan.ptr)
+    return {"kind": TUNE_KINDS.get(kind.value, kind.value), "key": list(key), "value": value.value,
+            "ms": ms.value}
 
 
 def demag_launch_count(plan: Plan) -> int:

@@ -418,17 +418,41 @@ extern "C" demag_status demag_apply_adjoint(demag_plan* P, const float* y, float
   return full_adjoint(P, y, g, prec, (cudaStream_t)stream);
 }
 
+static demag_status check_batch(demag_plan* const* plans, const float* const* m, float* const* phi, int count,
+                                demag_precision prec, const char* what) {
+  if (count < 0 || (count > 0 && (!plans || !m || !phi)))
+    return set_error(nullptr, DEMAG_EINVAL, "%s: bad arguments", what);
+  if ((int)prec < 0 || (int)prec > (int)DEMAG_BF16X3)
+    return set_error(nullptr, DEMAG_EINVAL, "%s: unknown precision %d", what, (int)prec);
+  for (int i = 0; i < count; ++i) {
+    if (!plans[i] || !m[i] || !phi[i]) return set_error(nullptr, DEMAG_EINVAL, "%s: NULL entry %d", what, i);
+    const bool tc = prec == DEMAG_TF32X3 || prec == DEMAG_BF16X3;
+    if (tc ? !tc_ready(plans[i], prec) : !plans[i]->ws[prec].base)
+      return set_error(plans[i], DEMAG_EINVAL, "%s: plan %d has no workspace", what, i);
+  }
+  return DEMAG_OK;
+}
+
 extern "C" demag_status demag_apply_full_batched(demag_plan* const* plans, const float* const* m,
                                                  float* const* phi, int count, demag_precision prec,
                                                  void* stream) {
-  if (count < 0 || (count > 0 && (!plans || !m || !phi)))
-    return set_error(nullptr, DEMAG_EINVAL, "demag_apply_full_batched: bad arguments");
-  for (int i = 0; i < count; ++i) {
-    if (!plans[i] || !m[i] || !phi[i])
-      return set_error(nullptr, DEMAG_EINVAL, "demag_apply_full_batched: NULL entry %d", i);
-    const bool tc = prec == DEMAG_TF32X3 || prec == DEMAG_BF16X3;
-    if (tc ? !tc_ready(plans[i], prec) : !plans[i]->ws[prec].base)
-      return set_error(plans[i], DEMAG_EINVAL, "demag_apply_full_batched: plan %d has no workspace", i);
+  demag_status cs = check_batch(plans, m, phi, count, prec, "demag_apply_full_batched");
+  if (cs != DEMAG_OK) return cs;
+  if (prec == DEMAG_TF32X3 || prec == DEMAG_BF16X3) {
+    // each stage of a run of distinct plans is one grouped persistent launch;
+    // a plan that repeats (it owns one set of intermediates) starts a new run
+    int first = 0;
+    for (int i = 1; i <= count; ++i) {
+      bool repeat = false;
+      for (int j = first; j < i && i < count; ++j) repeat = repeat || plans[j] == plans[i];
+      if (i == count || repeat) {
+        demag_status s = tc_forward_batched(plans + first, m + first, phi + first, i - first, prec,
+                                            (cudaStream_t)stream);
+        if (s != DEMAG_OK) return s;
+        first = i;
+      }
+    }
+    return DEMAG_OK;
   }
   for (int i = 0; i < count; ++i) {
     demag_status s = full_forward(plans[i], m[i], phi[i], prec, (cudaStream_t)stream);
@@ -436,6 +460,105 @@ extern "C" demag_status demag_apply_full_batched(demag_plan* const* plans, const
   }
   return DEMAG_OK;
 }
+
+// ---------------------------------------------------------------- CUDA-graph form of the batched apply
+
+struct demag_graph {
+  std::vector<demag_plan*> plans;
+  demag::TcBatch* batch = nullptr;  // grouped descriptors owned by this graph (tensor-core forms)
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int kernels = 0;
+};
+
+extern "C" void demag_graph_destroy(demag_graph* g) {
+  if (!g) return;
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (g->graph) cudaGraphDestroy(g->graph);
+  tc_batch_destroy(g->batch);
+  delete g;
+}
+
+extern "C" demag_status demag_graph_create_batched(demag_plan* const* plans, const float* const* m,
+                                                   float* const* phi, int count, demag_precision prec,
+                                                   demag_graph** out) {
+  if (!out) return set_error(nullptr, DEMAG_EINVAL, "demag_graph_create_batched: out is NULL");
+  *out = nullptr;
+  demag_status s = check_batch(plans, m, phi, count, prec, "demag_graph_create_batched");
+  if (s != DEMAG_OK) return s;
+  if (count == 0) return set_error(nullptr, DEMAG_EINVAL, "demag_graph_create_batched: empty batch");
+  for (int i = 0; i < count; ++i)
+    for (int j = 0; j < i; ++j)
+      if (plans[i] == plans[j])
+        return set_error(plans[i], DEMAG_EINVAL, "demag_graph_create_batched: plan %d repeats plan %d", i, j);
+  const bool tc = prec == DEMAG_TF32X3 || prec == DEMAG_BF16X3;
+  demag_graph* g = new demag_graph();
+  g->plans.assign(plans, plans + count);
+  if (tc) {
+    s = tc_batch_create(plans, count, prec, &g->batch);
+    if (s != DEMAG_OK) {
+      demag_graph_destroy(g);
+      return s;
+    }
+  }
+  cudaStream_t cs = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    demag_graph_destroy(g);
+    return cuda_error(plans[0], e, "demag_graph_create_batched: stream");
+  }
+  // event timing would record into the graph: off while capturing
+  std::vector<char> prof(count);
+  std::vector<unsigned long long> before(count);
+  for (int i = 0; i < count; ++i) {
+    prof[i] = plans[i]->prof_on;
+    plans[i]->prof_on = false;
+    before[i] = plans[i]->launches;
+  }
+  e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    if (tc) {
+      s = tc_batch_run(g->batch, m, phi, cs);
+    } else {
+      for (int i = 0; i < count && s == DEMAG_OK; ++i) s = full_forward(plans[i], m[i], phi[i], prec, cs);
+    }
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+    g->graph = graph;
+    if (s == DEMAG_OK && e2 != cudaSuccess) s = cuda_error(plans[0], e2, "demag_graph_create_batched: capture");
+  } else {
+    s = cuda_error(plans[0], e, "demag_graph_create_batched: begin capture");
+  }
+  // the capture launched nothing: move the recorded kernels out of the counters
+  unsigned long long recorded = 0;
+  for (int i = 0; i < count; ++i) {
+    plans[i]->prof_on = prof[i];
+    recorded += plans[i]->launches - before[i];
+    plans[i]->launches = before[i];
+  }
+  g->kernels = (int)recorded;
+  cudaStreamDestroy(cs);
+  if (s == DEMAG_OK && g->graph) {
+    e = cudaGraphInstantiate(&g->exec, g->graph, 0);
+    if (e != cudaSuccess) s = cuda_error(plans[0], e, "demag_graph_create_batched: instantiate");
+  }
+  if (s != DEMAG_OK) {
+    demag_graph_destroy(g);
+    return s;
+  }
+  *out = g;
+  return DEMAG_OK;
+}
+
+extern "C" demag_status demag_graph_launch(demag_graph* g, void* stream) {
+  if (!g || !g->exec) return set_error(nullptr, DEMAG_EINVAL, "demag_graph_launch: graph is NULL");
+  cudaError_t e = cudaGraphLaunch(g->exec, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_error(g->plans[0], e, "demag_graph_launch");
+  g->plans[0]->launches += (unsigned long long)g->kernels;
+  return DEMAG_OK;
+}
+
+extern "C" int demag_graph_kernel_count(const demag_graph* g) { return g ? g->kernels : 0; }
 
 // ---------------------------------------------------------------- allocation-free entry point
 //

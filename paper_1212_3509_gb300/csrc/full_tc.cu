@@ -9,17 +9,25 @@
 // in tensor memory.
 //
 // Kernel: persistent, one CTA (192 threads) per SM, warp-specialised:
-//   warp 0      TMA producer: loads A_hi, A_lo (128 rows) and B_hi, B_lo
-//               (BN rows) k-blocks of 64-byte rows (32 BF16 or 16 TF32
-//               elements) into a 4-stage shared-memory ring,
+//   warp 0      TMA producer: takes tiles from an atomic counter, hands their
+//               ids to the other roles through a shared ring, and loads
+//               A_hi, A_lo (128 rows) and B_hi, B_lo (BN rows) k-blocks of
+//               64-byte rows (32 BF16 or 16 TF32 elements) into a 4-stage
+//               shared-memory ring,
 //   warp 1      MMA issuer: 2 k-steps x 3 tcgen05.mma (M = 128, N = BN) per
 //               stage into one of two TMEM accumulators (2 x 256 columns),
 //   warps 2..5  epilogue: tcgen05.ld of the accumulator (one TMEM lane per
-//               thread = one output row), then either the hi/lo split of the
-//               next stage's operand or the final FP32 field, stored
-//               transposed (consecutive threads write consecutive addresses).
-// Tiles are (job, 128-row block, BN-column block); a job is one output field
-// with a list of (A field, B matrix) pairs whose contractions it sums.
+//               thread = one output row), then the hi/lo split of the next
+//               stage's operand or an FP32 field, stored transposed, through
+//               shared memory and TMA bulk stores where a warp's 32 rows share
+//               one outer index, else directly (consecutive threads write
+//               consecutive addresses).
+// A launch runs one or several "groups": a group is one GEMM stage of one
+// grid (tensor maps, shapes, a job table and a pair table in device memory,
+// built once per plan).  A tile is (group, job, 128-row block, BN-column
+// block); a job is one output field with a list of (A field, B matrix) pairs
+// whose contractions it sums.  Several grids of different shapes therefore run
+// a stage in one persistent launch.
 #include <cuda_bf16.h>
 
 #include <vector>
@@ -36,10 +44,11 @@ constexpr int kTileA = kBM * kRowBytes;            // 8 KB
 constexpr int kTileB = kBN * kRowBytes;            // 16 KB
 constexpr int kStageBytes = 2 * kTileA + 2 * kTileB;  // 48 KB
 constexpr int kBarBytes = 256;
-constexpr int kSmemBytes = kStages * kStageBytes + kBarBytes + 1024;
+constexpr int kOutBuf = 4096;                      // one 32 x 32 output chunk (2 BF16 planes or 1 FP32)
+constexpr int kOutStaging = 4 * 2 * kOutBuf;       // 4 epilogue warps, double-buffered
+constexpr int kSmemBytes = kStages * kStageBytes + kOutStaging + kBarBytes + 1024;
 constexpr int kTcThreads = 192;
-constexpr int kMaxTcJobs = 3 * kMaxTerms + 8;
-constexpr int kMaxTcPairs = 4 * kMaxTerms + 8;
+constexpr int kRing = 4;                           // tile ids handed from the producer to the other roles
 constexpr uint64_t kWaitNs = 2000000000ull;        // 2 s bound on every wait
 constexpr uint32_t kSwizzle64 = 4;                 // descriptor code of SWIZZLE_64B
 constexpr uint32_t kSBO = 8 * kRowBytes;           // 8 rows x 64 bytes per swizzle atom
@@ -84,30 +93,44 @@ struct TcJob {
   int pair0, npairs, out_field, pad;
 };
 
-struct TcParams {
+// One GEMM stage of one grid, in device memory (64-byte aligned for the maps).
+struct alignas(64) TcGroup {
   CUtensorMap a_hi, a_lo, b_hi, b_lo;  // 3D maps: (K, rows, field | matrix)
+  CUtensorMap o_hi, o_lo;              // 4D output maps (inner, outer, a, field) when tma_out
+  const TcJob* jobs;
+  const short2* pairs;                 // (A field, B matrix)
   void* out_hi;                        // split: hi plane base; f32: float base
   void* out_lo;                        // split: lo plane base
   long long field_elems;               // elements per output field
   long long s_a;                       // output stride of the column index a
   int ldC, n_inner;                    // output row stride and row split (outer, inner)
-  int rows, n_a, kblocks, bn, mode;
+  int rows, n_a, kblocks, bn, mode, tma_out;
   float alpha;
-  int njobs, m_tiles, n_tiles, total_tiles;
-  int* status;
-  int* tile_counter;                   // zeroed before the launch; tiles are taken in order
-  TcJob jobs[kMaxTcJobs];
-  short2 pairs[kMaxTcPairs];           // (A field, B matrix)
+  int njobs, m_tiles, n_tiles, ntiles;
 };
 
-constexpr int kRing = 4;               // tile ids handed from the producer to the other roles
+struct TcLaunch {
+  const TcGroup* groups;               // device array
+  const int* tile0;                    // device prefix sums of group tiles, [ngroups + 1]
+  int ngroups, total_tiles;
+  int* tile_counter;                   // zeroed before the launch
+  int* status;
+};
 
-__device__ __forceinline__ void tile_coords(const TcParams& p, int tile, int& j, int& mt, int& nt) {
+__device__ __forceinline__ void tile_coords(const TcLaunch& L, int tile, int& g, int& j, int& mt, int& nt) {
+  int lo = 0, hi = L.ngroups - 1;
+  while (lo < hi) {  // last group whose first tile <= tile
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(L.tile0 + mid) <= tile) lo = mid; else hi = mid - 1;
+  }
+  g = lo;
+  const TcGroup& G = L.groups[g];
+  int t = tile - __ldg(L.tile0 + g);
   // job fastest: consecutive tiles share the A row block (L2 reuse across nodes)
-  j = tile % p.njobs;
-  int rest = tile / p.njobs;
-  nt = rest % p.n_tiles;
-  mt = rest / p.n_tiles;
+  j = t % G.njobs;
+  t /= G.njobs;
+  nt = t % G.n_tiles;
+  mt = t / G.n_tiles;
 }
 
 __device__ __forceinline__ void tc_fail(volatile int* abort, int* status) {
@@ -116,11 +139,12 @@ __device__ __forceinline__ void tc_fail(volatile int* abort, int* status) {
 }
 
 template <class F>
-__global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const __grid_constant__ TcParams p) {
+__global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const __grid_constant__ TcLaunch L) {
   using T = typename F::T;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * kStageBytes);
+  uint8_t* ostage = smem + kStages * kStageBytes;  // epilogue staging (1024-aligned)
+  uint64_t* full = reinterpret_cast<uint64_t*>(ostage + kOutStaging);
   uint64_t* empty = full + kStages;
   uint64_t* tfull = empty + kStages;   // [2]
   uint64_t* tempty = tfull + 2;        // [2]
@@ -161,11 +185,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const __grid_con
 
   if (warp == 0) {
     if (lane == 0) {
-      ptx::prefetch_tmap(&p.a_hi);
-      ptx::prefetch_tmap(&p.a_lo);
-      ptx::prefetch_tmap(&p.b_hi);
-      ptx::prefetch_tmap(&p.b_lo);
-      const uint32_t bytes = 2 * kTileA + 2 * (uint32_t)p.bn * kRowBytes;
       int s = 0;
       uint32_t ph = 0;
       int rs = 0;
@@ -173,30 +192,32 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const __grid_con
       while (!*abort) {
         // take the next tile and hand its id to the MMA and epilogue roles
         if (!ptx::mbar_wait(&sempty[rs], rph ^ 1, abort, kWaitNs)) {
-          tc_fail(abort, p.status);
+          tc_fail(abort, L.status);
           break;
         }
-        const int tile = atomicAdd(p.tile_counter, 1);
-        ring[rs] = tile < p.total_tiles ? tile : -1;
+        const int tile = atomicAdd(L.tile_counter, 1);
+        ring[rs] = tile < L.total_tiles ? tile : -1;
         ptx::mbar_arrive(&sfull[rs]);
         if (++rs == kRing) { rs = 0; rph ^= 1; }
-        if (tile >= p.total_tiles) break;
-        int j, mt, nt;
-        tile_coords(p, tile, j, mt, nt);
-        const TcJob& J = p.jobs[j];
+        if (tile >= L.total_tiles) break;
+        int g, j, mt, nt;
+        tile_coords(L, tile, g, j, mt, nt);
+        const TcGroup& G = L.groups[g];
+        const TcJob J = G.jobs[j];
+        const uint32_t bytes = 2 * kTileA + 2 * (uint32_t)G.bn * kRowBytes;
         for (int pi = 0; pi < J.npairs && !*abort; ++pi) {
-          const short2 pr = p.pairs[J.pair0 + pi];
-          for (int kb = 0; kb < p.kblocks; ++kb) {
+          const short2 pr = G.pairs[J.pair0 + pi];
+          for (int kb = 0; kb < G.kblocks; ++kb) {
             if (!ptx::mbar_wait(&empty[s], ph ^ 1, abort, kWaitNs)) {
-              tc_fail(abort, p.status);
+              tc_fail(abort, L.status);
               break;
             }
             uint8_t* st = smem + s * kStageBytes;
             ptx::mbar_arrive_expect_tx(&full[s], bytes);
-            ptx::tma_load_3d(st, &p.a_hi, &full[s], kb * F::kBK, mt * kBM, pr.x);
-            ptx::tma_load_3d(st + kTileA, &p.a_lo, &full[s], kb * F::kBK, mt * kBM, pr.x);
-            ptx::tma_load_3d(st + 2 * kTileA, &p.b_hi, &full[s], kb * F::kBK, nt * kBN, pr.y);
-            ptx::tma_load_3d(st + 2 * kTileA + kTileB, &p.b_lo, &full[s], kb * F::kBK, nt * kBN, pr.y);
+            ptx::tma_load_3d(st, &G.a_hi, &full[s], kb * F::kBK, mt * kBM, pr.x);
+            ptx::tma_load_3d(st + kTileA, &G.a_lo, &full[s], kb * F::kBK, mt * kBM, pr.x);
+            ptx::tma_load_3d(st + 2 * kTileA, &G.b_hi, &full[s], kb * F::kBK, nt * G.bn, pr.y);
+            ptx::tma_load_3d(st + 2 * kTileA + kTileB, &G.b_lo, &full[s], kb * F::kBK, nt * G.bn, pr.y);
             if (++s == kStages) { s = 0; ph ^= 1; }
           }
         }
@@ -204,7 +225,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const __grid_con
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      const uint32_t idesc = ptx::instr_desc(F::kFormat, kBM, (uint32_t)p.bn);
       int s = 0;
       uint32_t ph = 0, tph = 0;
       int buf = 0;
@@ -212,18 +232,21 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const __grid_con
       uint32_t rph = 0;
       while (!*abort) {
         if (!ptx::mbar_wait(&sfull[rs], rph, abort, kWaitNs)) {
-          tc_fail(abort, p.status);
+          tc_fail(abort, L.status);
           break;
         }
         const int tile = ring[rs];
         ptx::mbar_arrive(&sempty[rs]);
         if (++rs == kRing) { rs = 0; rph ^= 1; }
         if (tile < 0) break;
-        int j, mt, nt;
-        tile_coords(p, tile, j, mt, nt);
-        const TcJob& J = p.jobs[j];
+        int g, j, mt, nt;
+        tile_coords(L, tile, g, j, mt, nt);
+        const TcGroup& G = L.groups[g];
+        const TcJob J = G.jobs[j];
+        const uint32_t idesc = ptx::instr_desc(F::kFormat, kBM, (uint32_t)G.bn);
+        const int kblocks = G.kblocks;
         if (!ptx::mbar_wait(&tempty[buf], tph ^ 1, abort, kWaitNs)) {
-          tc_fail(abort, p.status);
+          tc_fail(abort, L.status);
           break;
         }
         ptx::tc_fence_after();
@@ -231,9 +254,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const __grid_con
         uint32_t acc = 0;
         bool ok = true;
         for (int pi = 0; pi < J.npairs && ok; ++pi) {
-          for (int kb = 0; kb < p.kblocks; ++kb) {
+          for (int kb = 0; kb < kblocks; ++kb) {
             if (!ptx::mbar_wait(&full[s], ph, abort, kWaitNs)) {
-              tc_fail(abort, p.status);
+              tc_fail(abort, L.status);
               ok = false;
               break;
             }
@@ -269,9 +292,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const __grid_con
     uint32_t tph = 0;
     int rs = 0;
     uint32_t rph = 0;
+    uint32_t chunk = 0;  // staged chunks of this warp so far: selects the staging buffer
     while (!*abort) {
       if (!ptx::mbar_wait(&sfull[rs], rph, abort, kWaitNs)) {
-        tc_fail(abort, p.status);
+        tc_fail(abort, L.status);
         break;
       }
       const int tile = ring[rs];
@@ -279,29 +303,79 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const __grid_con
       if (lane == 0) ptx::mbar_arrive(&sempty[rs]);
       if (++rs == kRing) { rs = 0; rph ^= 1; }
       if (tile < 0) break;
-      int j, mt, nt;
-      tile_coords(p, tile, j, mt, nt);
-      const TcJob& J = p.jobs[j];
+      int g, j, mt, nt;
+      tile_coords(L, tile, g, j, mt, nt);
+      const TcGroup& G = L.groups[g];
+      const int out_field = G.jobs[j].out_field;
       if (!ptx::mbar_wait(&tfull[buf], tph, abort, kWaitNs)) {
-        tc_fail(abort, p.status);
+        tc_fail(abort, L.status);
         break;
       }
       ptx::tc_fence_after();
-      const int row = mt * kBM + rloc;
-      const bool valid = row < p.rows;
-      const int outer = row / p.n_inner, inner = row - outer * p.n_inner;
-      const long long rbase = (long long)J.out_field * p.field_elems + (long long)outer * p.ldC + inner;
       const uint32_t taddr = tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * kBN);
-      const int a0 = nt * kBN;
-      const int acount = min(p.bn, p.n_a - a0);  // columns of this tile that exist
-      for (int c0 = 0; c0 < p.bn; c0 += 32) {
-        uint32_t r[32];
-        ptx::tmem_ld32(taddr + (uint32_t)c0, r);
-        ptx::tmem_ld_wait();
-        if (valid) {
-          if (p.mode == kOutSplit) {
-            T* hp = reinterpret_cast<T*>(p.out_hi) + rbase + (long long)(a0 + c0) * p.s_a;
-            T* lp = reinterpret_cast<T*>(p.out_lo) + rbase + (long long)(a0 + c0) * p.s_a;
+      const int a0 = nt * G.bn;
+      const int bn = G.bn;
+      const int n_inner = G.n_inner;
+      const int mode = G.mode;
+      const float alpha = G.alpha;
+      if (G.tma_out) {
+        // A warp's 32 rows lie in one `outer` (n_inner % 32 == 0), so each
+        // 32-column chunk is one TMA box per plane: stage it in shared memory
+        // as [column][row] and store it with the async copy engine.
+        const int rw = mt * kBM + quad * 32;
+        const int outer_w = rw / n_inner, inner_w = rw - outer_w * n_inner;
+        const bool warp_valid = rw < G.rows;
+        uint8_t* stg = ostage + quad * (2 * kOutBuf);
+        for (int c0 = 0; c0 < bn; c0 += 32) {
+          uint32_t r[32];
+          ptx::tmem_ld32(taddr + (uint32_t)c0, r);
+          ptx::tmem_ld_wait();
+          if (!warp_valid) continue;
+          // buffers alternate over the warp's whole chunk sequence (across
+          // tiles), so at most the other buffer's store can still be reading
+          uint8_t* sb = stg + (chunk & 1) * kOutBuf;
+          ++chunk;
+          if (lane == 0) ptx::bulk_wait_read_1();  // the store that used this buffer has read it
+          __syncwarp();
+          if (mode == kOutSplit) {
+            T* sh = reinterpret_cast<T*>(sb);
+            T* sl = sh + 32 * 32;
+#pragma unroll
+            for (int jj = 0; jj < 32; ++jj) {
+              T hi, lo;
+              F::split(__uint_as_float(r[jj]), hi, lo);
+              sh[jj * 32 + lane] = hi;
+              sl[jj * 32 + lane] = lo;
+            }
+          } else {
+            float* sf = reinterpret_cast<float*>(sb);
+#pragma unroll
+            for (int jj = 0; jj < 32; ++jj) sf[jj * 32 + lane] = alpha * __uint_as_float(r[jj]);
+          }
+          ptx::fence_proxy_async_smem();
+          __syncwarp();
+          if (lane == 0) {
+            ptx::tma_store_4d(&G.o_hi, sb, inner_w, outer_w, a0 + c0, out_field);
+            if (mode == kOutSplit)
+              ptx::tma_store_4d(&G.o_lo, sb + 32 * 32 * sizeof(T), inner_w, outer_w, a0 + c0, out_field);
+            ptx::bulk_commit();
+          }
+        }
+      } else {
+        const int row = mt * kBM + rloc;
+        const bool valid = row < G.rows;
+        const int outer = row / n_inner, inner = row - outer * n_inner;
+        const long long s_a = G.s_a;
+        const long long rbase = (long long)out_field * G.field_elems + (long long)outer * G.ldC + inner;
+        const int acount = min(bn, G.n_a - a0);  // columns of this tile that exist
+        for (int c0 = 0; c0 < bn; c0 += 32) {
+          uint32_t r[32];
+          ptx::tmem_ld32(taddr + (uint32_t)c0, r);
+          ptx::tmem_ld_wait();
+          if (!valid) continue;
+          if (mode == kOutSplit) {
+            T* hp = reinterpret_cast<T*>(G.out_hi) + rbase + (long long)(a0 + c0) * s_a;
+            T* lp = reinterpret_cast<T*>(G.out_lo) + rbase + (long long)(a0 + c0) * s_a;
 #pragma unroll
             for (int jj = 0; jj < 32; ++jj) {
               if (c0 + jj < acount) {
@@ -310,15 +384,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const __grid_con
                 *hp = hi;
                 *lp = lo;
               }
-              hp += p.s_a;
-              lp += p.s_a;
+              hp += s_a;
+              lp += s_a;
             }
           } else {
-            float* op = reinterpret_cast<float*>(p.out_hi) + rbase + (long long)(a0 + c0) * p.s_a;
+            float* op = reinterpret_cast<float*>(G.out_hi) + rbase + (long long)(a0 + c0) * s_a;
 #pragma unroll
             for (int jj = 0; jj < 32; ++jj) {
-              if (c0 + jj < acount) *op = p.alpha * __uint_as_float(r[jj]);
-              op += p.s_a;
+              if (c0 + jj < acount) *op = alpha * __uint_as_float(r[jj]);
+              op += s_a;
             }
           }
         }
@@ -329,6 +403,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const __grid_con
       buf ^= 1;
       if (buf == 0) tph ^= 1;
     }
+    if (lane == 0) ptx::bulk_wait_all();  // staged stores finished before the block exits
   }
 
   // teardown: after an abort let in-flight MMAs and copies land (bounded)
@@ -393,6 +468,31 @@ __global__ void tc_factor_kernel(int M, int glen, int axis, int n, int ld, const
   }
 }
 
+// The tensor cores accumulate into TMEM with FP32 additions that do not round
+// to nearest, so the error of a long contraction grows with the number of
+// MMAs accumulated into one accumulator.  The node-sum stage (2M pairs of
+// length n3) is therefore split into groups of at most ~400 accumulations
+// (~200 for TF32x3), whose FP32 partial fields are summed on CUDA cores in FP64.
+static int pairs_per_split(int kblocks, int budget) {
+  const int per_pair = kblocks * 6;  // 2 k-steps x 3 products per k-block
+  const int pp = budget / (per_pair > 0 ? per_pair : 1);
+  return pp < 1 ? 1 : pp;
+}
+
+// out[q][i] = alpha * sum_g part[q*groups + g][i], accumulated in FP64
+__global__ void reduce_parts_kernel(const float* __restrict__ part, int groups, long long N, int nout, float alpha,
+                                    float* __restrict__ out) {
+  const long long total = (long long)nout * N;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const long long q = idx / N, i = idx - q * N;
+    const float* src = part + q * groups * N + i;
+    double acc = 0.0;
+    for (int g = 0; g < groups; ++g) acc += (double)src[g * N];
+    out[idx] = (float)(alpha * acc);
+  }
+}
+
 // ---------------------------------------------------------------- host side
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -427,7 +527,27 @@ static bool make_map(CUtensorMap* m, void* base, int elem_bytes, uint64_t dim0, 
   return r == CUDA_SUCCESS;
 }
 
+// 4D map over an output field set: (inner, outer, a, field) with the given
+// strides in elements; box (32, 1, 32, 1) = one epilogue warp's 32 rows x 32
+// output columns, no swizzle.
+static bool make_out_map(CUtensorMap* m, void* base, int elem_bytes, uint64_t inner, uint64_t outer, uint64_t na,
+                         uint64_t fields, uint64_t ld, uint64_t s_a, uint64_t field_elems) {
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return false;
+  cuuint64_t dims[4] = {inner, outer, na, fields};
+  cuuint64_t strides[3] = {ld * elem_bytes, s_a * elem_bytes, field_elems * elem_bytes};
+  cuuint32_t box[4] = {32, 1, 32, 1};
+  cuuint32_t estr[4] = {1, 1, 1, 1};
+  const CUtensorMapDataType dt = elem_bytes == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  CUresult r = enc(m, dt, 4, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
 static int round_up(int v, int m) { return (v + m - 1) / m * m; }
+
+// Stage programs of a plan: forward stages 0-2, adjoint stages 3-5.
+enum { kFwd1 = 0, kFwd2, kFwd3, kAdj1, kAdj2, kAdj3, kPrograms };
 
 // Per-plan, per-form tensor-core state.
 struct TcState {
@@ -438,42 +558,36 @@ struct TcState {
   void* X[2];             // split input: [3][n3 n2][ld1]
   void* buf1[2];          // [3M][n1 n3][ld2]
   void* buf2[2];          // [3M][n2 n1][ld3]
-  CUtensorMap mapB[3][2];
-  CUtensorMap mapX[2], map1[2], map2[2];
   int* status;
   int* counter;           // dynamic tile counter of the running launch
   float* part;            // split node-sum partial fields
   int pp3;                // (A, B) pairs per accumulator in the node-sum stage
+  int part_fields;        // partial fields allocated
+  int groups_fwd, groups_adj;  // partial fields used by the forward / adjoint node sum
+  int tma[3];             // stage epilogue stores through TMA
+  // stage programs: the group descriptors (device) and their job / pair tables
+  TcGroup* prog;          // device [kPrograms]
+  TcJob* jobs;            // device, all programs
+  short2* pairs;          // device, all programs
+  int* tile0;             // device [kPrograms][2]: {0, ntiles} for single-group launches
+  TcGroup host_prog[kPrograms];
   size_t bytes;
 };
 
-// The tensor cores accumulate into TMEM with FP32 additions that do not round
-// to nearest, so the error of a long contraction grows with the number of
-// MMAs accumulated into one accumulator.  The node-sum stage (2M pairs of
-// length n3) is therefore split into groups of at most ~400 accumulations,
-// whose FP32 partial fields are summed on CUDA cores in FP64.
-static int pairs_per_split(int kblocks) {
-  const int per_pair = kblocks * 6;  // 2 k-steps x 3 products per k-block
-  const int pp = 400 / (per_pair > 0 ? per_pair : 1);
-  return pp < 1 ? 1 : pp;
-}
-
-// out[q][i] = alpha * sum_g part[q*groups + g][i], accumulated in FP64
-__global__ void reduce_parts_kernel(const float* __restrict__ part, int groups, long long N, int nout, float alpha,
-                                    float* __restrict__ out) {
-  const long long total = (long long)nout * N;
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const long long q = idx / N, i = idx - q * N;
-    const float* src = part + q * groups * N + i;
-    double acc = 0.0;
-    for (int g = 0; g < groups; ++g) acc += (double)src[g * N];
-    out[idx] = (float)(alpha * acc);
-  }
-}
+// Grouped descriptors of the forward stages of several plans (one launch per
+// stage over all of them); owned by a plan's cache or by a captured graph.
+struct TcBatch {
+  std::vector<demag_plan*> plans;
+  std::vector<unsigned long long> serials;  // with the pointers, the cache key
+  int prec = -1;
+  TcGroup* groups = nullptr;           // device [3][count]
+  int* tile0 = nullptr;                // device [3][count + 1]
+  int total[3] = {0, 0, 0};
+};
 
 struct TcHolder {
   TcState* s[2] = {nullptr, nullptr};  // [0] BF16x3, [1] TF32x3
+  TcBatch* cache = nullptr;            // last plan list given to demag_apply_full_batched
 };
 
 static int form_index(demag_precision prec) { return prec == DEMAG_TF32X3 ? 1 : 0; }
@@ -508,6 +622,10 @@ static void free_state(TcState* S) {
   cudaFree(S->status);
   cudaFree(S->counter);
   cudaFree(S->part);
+  cudaFree(S->prog);
+  cudaFree(S->jobs);
+  cudaFree(S->pairs);
+  cudaFree(S->tile0);
   delete S;
 }
 
@@ -518,6 +636,7 @@ void tc_destroy(demag_plan* P) {
     free_state(s);
     s = nullptr;
   }
+  tc_batch_destroy(H->cache);
   delete H;
   P->tc = nullptr;
 }
@@ -525,6 +644,168 @@ void tc_destroy(demag_plan* P) {
 static int grid_blocks(long long count) {
   long long b = (count + 255) / 256;
   return (int)(b > 152 * 16 ? 152 * 16 : (b < 1 ? 1 : b));
+}
+
+static TcJob job(int pair0, int npairs, int out_field) {
+  TcJob j;
+  j.pair0 = pair0;
+  j.npairs = npairs;
+  j.out_field = out_field;
+  j.pad = 0;
+  return j;
+}
+
+// matrix index of (node k, type) in the per-axis factor maps
+static short mat(int k, int type) { return (short)(2 * k + type); }
+
+// Build the six stage programs of a plan (host descriptors, job and pair tables).
+struct ProgramBuild {
+  std::vector<TcJob> jobs;
+  std::vector<short2> pairs;
+  int job0[kPrograms], pair0[kPrograms];
+};
+
+static void set_stage(TcGroup& G, const CUtensorMap& ahi, const CUtensorMap& alo, const CUtensorMap& bhi,
+                      const CUtensorMap& blo, int rows, int n_a, int K, int bk, int bn, void* out_hi, void* out_lo,
+                      long long field_elems, long long s_a, int ldC, int n_inner, int mode, float alpha) {
+  G.a_hi = ahi;
+  G.a_lo = alo;
+  G.b_hi = bhi;
+  G.b_lo = blo;
+  G.rows = rows;
+  G.n_a = n_a;
+  G.kblocks = (K + bk - 1) / bk;
+  G.bn = bn;
+  G.out_hi = out_hi;
+  G.out_lo = out_lo;
+  G.field_elems = field_elems;
+  G.s_a = s_a;
+  G.ldC = ldC;
+  G.n_inner = n_inner;
+  G.mode = mode;
+  G.alpha = alpha;
+  G.m_tiles = (rows + kBM - 1) / kBM;
+  G.n_tiles = (n_a + bn - 1) / bn;
+}
+
+static demag_status build_programs(demag_plan* P, TcState* S, const CUtensorMap (&mapX)[2],
+                                   const CUtensorMap (&map1)[2], const CUtensorMap (&map2)[2],
+                                   const CUtensorMap (&mapB)[3][2], const CUtensorMap (&out1)[2],
+                                   const CUtensorMap (&out2)[2], const CUtensorMap& out3, int bk,
+                                   cudaStream_t st) {
+  const int n1 = P->n[0], n2 = P->n[1], n3 = P->n[2], M = P->M;
+  const long long N = (long long)n1 * n2 * n3;
+  ProgramBuild b;
+  auto begin = [&](int prog) {
+    b.job0[prog] = (int)b.jobs.size();
+    b.pair0[prog] = (int)b.pairs.size();
+  };
+  auto add_job = [&](int prog, int npairs, int out_field) {
+    b.jobs.push_back(job((int)b.pairs.size() - b.pair0[prog] - npairs, npairs, out_field));
+  };
+  // forward mode 1: Y[k][q] = m_q x_1 T_{k,q,1}; rows (i3, i2), contraction i1 -> Y [i1'][i3][i2]
+  begin(kFwd1);
+  for (int q = 0; q < 3; ++q)
+    for (int k = 0; k < M; ++k) {
+      b.pairs.push_back(make_short2((short)q, mat(k, q == 0 ? 1 : 0)));
+      add_job(kFwd1, 1, 3 * k + q);
+    }
+  // forward mode 2: U_k = Y_k1 x_2 E + Y_k2 x_2 F, V_k = Y_k3 x_2 E; rows (i1', i3) -> [i2'][i1'][i3]
+  begin(kFwd2);
+  for (int k = 0; k < M; ++k) {
+    b.pairs.push_back(make_short2((short)(3 * k + 0), mat(k, 0)));
+    b.pairs.push_back(make_short2((short)(3 * k + 1), mat(k, 1)));
+    add_job(kFwd2, 2, 2 * k);
+    b.pairs.push_back(make_short2((short)(3 * k + 2), mat(k, 0)));
+    add_job(kFwd2, 1, 2 * k + 1);
+  }
+  // forward mode 3, node sum split in groups of pp3 pairs: part_g = sum U_k x_3 S E + V_k x_3 S F
+  begin(kFwd3);
+  for (int k = 0; k < M; ++k) {
+    b.pairs.push_back(make_short2((short)(2 * k), mat(k, 0)));
+    b.pairs.push_back(make_short2((short)(2 * k + 1), mat(k, 1)));
+  }
+  S->groups_fwd = (2 * M + S->pp3 - 1) / S->pp3;
+  for (int g = 0; g < S->groups_fwd; ++g) {
+    const int p0 = g * S->pp3;
+    const int np = (2 * M - p0) < S->pp3 ? (2 * M - p0) : S->pp3;
+    b.jobs.push_back(job(p0, np, g));
+  }
+  // adjoint mode 1: Ya_k = y x_1 F, Yb_k = y x_1 E  (fields 2k, 2k+1 of buf1)
+  begin(kAdj1);
+  for (int k = 0; k < M; ++k)
+    for (int t = 0; t < 2; ++t) {
+      b.pairs.push_back(make_short2((short)0, mat(k, t == 0 ? 1 : 0)));
+      add_job(kAdj1, 1, 2 * k + t);
+    }
+  // adjoint mode 2: Za = Ya x_2 E (g1), Zb = Yb x_2 F (g2), Zc = Yb x_2 E (g3)  (fields 3k+q of buf2)
+  begin(kAdj2);
+  for (int k = 0; k < M; ++k) {
+    const short src[3] = {(short)(2 * k), (short)(2 * k + 1), (short)(2 * k + 1)};
+    const int typ[3] = {0, 1, 0};
+    for (int q = 0; q < 3; ++q) {
+      b.pairs.push_back(make_short2(src[q], mat(k, typ[q])));
+      add_job(kAdj2, 1, 3 * k + q);
+    }
+  }
+  // adjoint mode 3 with the node sum split: part_{q,g} = sum_k Z_kq x_3 S T_{k,q,3}
+  begin(kAdj3);
+  S->groups_adj = (M + S->pp3 - 1) / S->pp3;
+  for (int q = 0; q < 3; ++q) {
+    const int base = (int)b.pairs.size() - b.pair0[kAdj3];
+    for (int k = 0; k < M; ++k) b.pairs.push_back(make_short2((short)(3 * k + q), mat(k, q == 2 ? 1 : 0)));
+    for (int gi = 0; gi < S->groups_adj; ++gi) {
+      const int p0 = gi * S->pp3;
+      const int np = (M - p0) < S->pp3 ? (M - p0) : S->pp3;
+      b.jobs.push_back(job(base + p0, np, q * S->groups_adj + gi));
+    }
+  }
+  const int job_end = (int)b.jobs.size();
+
+  const long long f1 = (long long)n1 * n3 * S->ld[1], f2 = (long long)n2 * n1 * S->ld[2];
+  TcGroup* H = S->host_prog;
+  memset(H, 0, sizeof(S->host_prog));
+  set_stage(H[kFwd1], mapX[0], mapX[1], mapB[0][0], mapB[0][1], n3 * n2, n1, n1, bk, S->bn[0], S->buf1[0],
+            S->buf1[1], f1, (long long)n3 * S->ld[1], S->ld[1], n2, kOutSplit, 1.f);
+  set_stage(H[kFwd2], map1[0], map1[1], mapB[1][0], mapB[1][1], n1 * n3, n2, n2, bk, S->bn[1], S->buf2[0],
+            S->buf2[1], f2, (long long)n1 * S->ld[2], S->ld[2], n3, kOutSplit, 1.f);
+  set_stage(H[kFwd3], map2[0], map2[1], mapB[2][0], mapB[2][1], n2 * n1, n3, n3, bk, S->bn[2], S->part, nullptr, N,
+            (long long)n2 * n1, n1, n1, kOutF32, 1.f);
+  H[kAdj1] = H[kFwd1];
+  H[kAdj2] = H[kFwd2];
+  H[kAdj3] = H[kFwd3];
+  for (int p = 0; p < kPrograms; ++p) {
+    const int stage = p % 3;
+    if (S->tma[stage]) {
+      H[p].tma_out = 1;
+      if (stage == 0) { H[p].o_hi = out1[0]; H[p].o_lo = out1[1]; }
+      if (stage == 1) { H[p].o_hi = out2[0]; H[p].o_lo = out2[1]; }
+      if (stage == 2) H[p].o_hi = out3;
+    }
+  }
+  // job and pair tables
+  DEMAG_CUDA(P, cudaMalloc(&S->jobs, sizeof(TcJob) * b.jobs.size()));
+  DEMAG_CUDA(P, cudaMalloc(&S->pairs, sizeof(short2) * b.pairs.size()));
+  DEMAG_CUDA(P, cudaMemcpy(S->jobs, b.jobs.data(), sizeof(TcJob) * b.jobs.size(), cudaMemcpyHostToDevice));
+  DEMAG_CUDA(P, cudaMemcpy(S->pairs, b.pairs.data(), sizeof(short2) * b.pairs.size(), cudaMemcpyHostToDevice));
+  for (int p = 0; p < kPrograms; ++p) {
+    const int jend = p + 1 < kPrograms ? b.job0[p + 1] : job_end;
+    H[p].jobs = S->jobs + b.job0[p];
+    H[p].pairs = S->pairs + b.pair0[p];
+    H[p].njobs = jend - b.job0[p];
+    H[p].ntiles = H[p].njobs * H[p].m_tiles * H[p].n_tiles;
+  }
+  DEMAG_CUDA(P, cudaMalloc(&S->prog, sizeof(TcGroup) * kPrograms));
+  DEMAG_CUDA(P, cudaMemcpy(S->prog, H, sizeof(TcGroup) * kPrograms, cudaMemcpyHostToDevice));
+  int t0[2 * kPrograms];
+  for (int p = 0; p < kPrograms; ++p) {
+    t0[2 * p] = 0;
+    t0[2 * p + 1] = H[p].ntiles;
+  }
+  DEMAG_CUDA(P, cudaMalloc(&S->tile0, sizeof(t0)));
+  DEMAG_CUDA(P, cudaMemcpy(S->tile0, t0, sizeof(t0), cudaMemcpyHostToDevice));
+  (void)st;
+  return DEMAG_OK;
 }
 
 template <class F>
@@ -546,13 +827,85 @@ static demag_status prepare_form(demag_plan* P, TcState* S, cudaStream_t st) {
   return DEMAG_OK;
 }
 
+template <class F>
+static demag_status run_program(demag_plan* P, TcState* S, int prog, cudaStream_t st);
+
+// Point stage program `prog` at output-column tile width bn (device copy included).
+static demag_status set_tile_width(demag_plan* P, TcState* S, int prog, int bn) {
+  TcGroup& G = S->host_prog[prog];
+  const int axis = prog % 3;
+  const int M = P->M;
+  for (int h = 0; h < 2; ++h)
+    if (!make_map(h ? &G.b_lo : &G.b_hi, S->B[axis][h], S->elem, P->n[axis], P->n[axis], 2 * M, S->ld[axis], bn))
+      return set_error(P, DEMAG_ECUDA, "tensor map encoding failed");
+  G.bn = bn;
+  G.n_tiles = (G.n_a + bn - 1) / bn;
+  G.ntiles = G.njobs * G.m_tiles * G.n_tiles;
+  const int t0[2] = {0, G.ntiles};
+  DEMAG_CUDA(P, cudaMemcpy(S->prog + prog, &G, sizeof(TcGroup), cudaMemcpyHostToDevice));
+  DEMAG_CUDA(P, cudaMemcpy(S->tile0 + 2 * prog, t0, sizeof(t0), cudaMemcpyHostToDevice));
+  return DEMAG_OK;
+}
+
+// Autotuning of the output-column tile width of every stage program: the
+// default (256, or the column count rounded up to 16) and 128 and 64 below it
+// are timed (one warm-up, three timed launches, operands as they are in the
+// workspace), and the fastest is kept.
+template <class F>
+static demag_status tune_tile_widths(demag_plan* P, TcState* S, cudaStream_t st) {
+  cudaEvent_t e0, e1;
+  DEMAG_CUDA(P, cudaEventCreate(&e0));
+  DEMAG_CUDA(P, cudaEventCreate(&e1));
+  demag_status s = DEMAG_OK;
+  for (int prog = 0; prog < kPrograms && s == DEMAG_OK; ++prog) {
+    const int def = S->host_prog[prog].bn;
+    std::vector<int> cands{def};
+    for (int c = 128; c >= 64; c /= 2)
+      if (c < def) cands.push_back(c);
+    if (cands.size() == 1) continue;
+    float best = 1e30f;
+    int best_bn = def;
+    for (int c : cands) {
+      s = set_tile_width(P, S, prog, c);
+      if (s == DEMAG_OK) s = run_program<F>(P, S, prog, st);
+      if (s != DEMAG_OK) break;
+      DEMAG_CUDA(P, cudaEventRecord(e0, st));
+      for (int r = 0; r < 3 && s == DEMAG_OK; ++r) s = run_program<F>(P, S, prog, st);
+      DEMAG_CUDA(P, cudaEventRecord(e1, st));
+      DEMAG_CUDA(P, cudaEventSynchronize(e1));
+      if (s != DEMAG_OK) break;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) {
+        best = ms;
+        best_bn = c;
+      }
+    }
+    if (s == DEMAG_OK) s = set_tile_width(P, S, prog, best_bn);
+    if (s == DEMAG_OK) {
+      demag_plan::Tuned t;
+      t.kind = S->elem == 2 ? 1 : 2;
+      t.key[0] = prog;
+      t.key[1] = def;
+      t.key[2] = 0;
+      t.value = best_bn;
+      t.ms = best / 3.f;
+      P->tuned.push_back(t);
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (s == DEMAG_OK) s = tc_sync_status(P, st);
+  return s;
+}
+
 demag_status tc_prepare(demag_plan* P, demag_precision prec, cudaStream_t st) {
   if (prec != DEMAG_BF16X3 && prec != DEMAG_TF32X3)
     return set_error(P, DEMAG_EUNSUPPORTED, "tensor-core form %d is not built", (int)prec);
   if (state(P, prec)) return DEMAG_OK;
   if (!encode_fn()) return set_error(P, DEMAG_ECUDA, "cuTensorMapEncodeTiled is unavailable");
   if (!P->tc) P->tc = new TcHolder();
-  TcHolder* H = reinterpret_cast<TcHolder*>(P->tc);
+  TcHolder* Hd = reinterpret_cast<TcHolder*>(P->tc);
   const int n1 = P->n[0], n2 = P->n[1], n3 = P->n[2], M = P->M;
   TcState* S = new TcState();
   memset(S, 0, sizeof(*S));
@@ -580,95 +933,97 @@ demag_status tc_prepare(demag_plan* P, demag_precision prec, cudaStream_t st) {
   ok = ok && alloc((void**)&S->counter, sizeof(int));
   {
     const int kb3 = (n3 + kRowBytes / S->elem - 1) / (kRowBytes / S->elem);
-    S->pp3 = pairs_per_split(kb3);
+    // TF32x3 issues twice the MMAs per K of BF16x3 in stages 1-2 as well, so its
+    // node sum gets half the accumulation budget
+    S->pp3 = pairs_per_split(kb3, S->elem == 4 ? 200 : 400);
     const int gf = (2 * M + S->pp3 - 1) / S->pp3;   // forward: 2M pairs in one sum
     const int ga = (M + S->pp3 - 1) / S->pp3;       // adjoint: M pairs per component
     const int fields = gf > 3 * ga ? gf : 3 * ga;
+    S->part_fields = fields;
     ok = ok && alloc((void**)&S->part, sizeof(float) * (size_t)fields * n1 * n2 * n3);
   }
   if (!ok) {
     free_state(S);
     return set_error(P, DEMAG_ENOMEM, "tensor-core workspace allocation failed");
   }
+  CUtensorMap mapB[3][2], mapX[2], map1[2], map2[2], out1[2], out2[2], out3;
+  memset(out1, 0, sizeof(out1));
+  memset(out2, 0, sizeof(out2));
+  memset(&out3, 0, sizeof(out3));
   for (int h = 0; h < 2; ++h) {
     for (int p = 0; p < 3; ++p)
-      ok = ok && make_map(&S->mapB[p][h], S->B[p][h], S->elem, P->n[p], P->n[p], 2 * M, S->ld[p], S->bn[p]);
-    ok = ok && make_map(&S->mapX[h], S->X[h], S->elem, n1, (uint64_t)n3 * n2, 3, S->ld[0], kBM);
-    ok = ok && make_map(&S->map1[h], S->buf1[h], S->elem, n2, (uint64_t)n1 * n3, 3 * M, S->ld[1], kBM);
-    ok = ok && make_map(&S->map2[h], S->buf2[h], S->elem, n3, (uint64_t)n2 * n1, 3 * M, S->ld[2], kBM);
+      ok = ok && make_map(&mapB[p][h], S->B[p][h], S->elem, P->n[p], P->n[p], 2 * M, S->ld[p], S->bn[p]);
+    ok = ok && make_map(&mapX[h], S->X[h], S->elem, n1, (uint64_t)n3 * n2, 3, S->ld[0], kBM);
+    ok = ok && make_map(&map1[h], S->buf1[h], S->elem, n2, (uint64_t)n1 * n3, 3 * M, S->ld[1], kBM);
+    ok = ok && make_map(&map2[h], S->buf2[h], S->elem, n3, (uint64_t)n2 * n1, 3 * M, S->ld[2], kBM);
   }
+  // epilogue stores through TMA where a warp's 32 output rows share one outer
+  // index (n_inner % 32 == 0) and a 32 x 32 chunk fits the staging buffer
+  // (BF16 planes, FP32 partials)
+  S->tma[0] = (n2 % 32 == 0) && S->elem == 2;
+  S->tma[1] = (n3 % 32 == 0) && S->elem == 2;
+  S->tma[2] = (n1 % 32 == 0);
+  for (int h = 0; h < 2; ++h) {
+    if (S->tma[0])
+      ok = ok && make_out_map(&out1[h], S->buf1[h], S->elem, n2, n3, n1, 3 * M, S->ld[1], (uint64_t)n3 * S->ld[1],
+                              (uint64_t)n1 * n3 * S->ld[1]);
+    if (S->tma[1])
+      ok = ok && make_out_map(&out2[h], S->buf2[h], S->elem, n3, n1, n2, 3 * M, S->ld[2], (uint64_t)n1 * S->ld[2],
+                              (uint64_t)n2 * n1 * S->ld[2]);
+  }
+  if (S->tma[2])
+    ok = ok && make_out_map(&out3, S->part, 4, n1, n2, n3, S->part_fields, n1, (uint64_t)n2 * n1,
+                            (uint64_t)n1 * n2 * n3);
   if (!ok) {
     free_state(S);
     return set_error(P, DEMAG_ECUDA, "tensor map encoding failed");
   }
-  demag_status s = prec == DEMAG_TF32X3 ? prepare_form<Tf32Form>(P, S, st) : prepare_form<Bf16Form>(P, S, st);
+  const int bk = kRowBytes / S->elem;
+  demag_status s = build_programs(P, S, mapX, map1, map2, mapB, out1, out2, out3, bk, st);
+  if (s == DEMAG_OK)
+    s = prec == DEMAG_TF32X3 ? prepare_form<Tf32Form>(P, S, st) : prepare_form<Bf16Form>(P, S, st);
+  if (s == DEMAG_OK && P->autotune) {
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(st, &cap);
+    if (cap == cudaStreamCaptureStatusNone) {
+      Hd->s[form_index(prec)] = S;  // tc_sync_status reads the state through the holder
+      s = prec == DEMAG_TF32X3 ? tune_tile_widths<Tf32Form>(P, S, st) : tune_tile_widths<Bf16Form>(P, S, st);
+      Hd->s[form_index(prec)] = nullptr;
+    }
+  }
   if (s != DEMAG_OK) {
     free_state(S);
     return s;
   }
-  H->s[form_index(prec)] = S;
+  Hd->s[form_index(prec)] = S;
   return DEMAG_OK;
 }
 
-// One GEMM stage: C = alpha * sum over the job's pairs of A[field] * B[matrix]^T.
-struct StageDesc {
-  const CUtensorMap* a[2];
-  const CUtensorMap* b[2];
-  int rows, n_a, K, bn;
-  void* out_hi;
-  void* out_lo;
-  long long field_elems, s_a;
-  int ldC, n_inner, mode;
-  float alpha;
-};
-
 template <class F>
-static demag_status launch_stage(demag_plan* P, TcState* S, const StageDesc& d, const std::vector<TcJob>& jobs,
-                                 const std::vector<short2>& pairs, cudaStream_t st) {
-  thread_local static TcParams prm;  // host staging; the launch copies the parameters at enqueue
-  if ((int)jobs.size() > kMaxTcJobs || (int)pairs.size() > kMaxTcPairs)
-    return set_error(P, DEMAG_EUNSUPPORTED, "too many GEMM jobs for one launch");
-  prm.a_hi = *d.a[0];
-  prm.a_lo = *d.a[1];
-  prm.b_hi = *d.b[0];
-  prm.b_lo = *d.b[1];
-  prm.out_hi = d.out_hi;
-  prm.out_lo = d.out_lo;
-  prm.field_elems = d.field_elems;
-  prm.s_a = d.s_a;
-  prm.ldC = d.ldC;
-  prm.n_inner = d.n_inner;
-  prm.rows = d.rows;
-  prm.n_a = d.n_a;
-  prm.kblocks = (d.K + F::kBK - 1) / F::kBK;
-  prm.bn = d.bn;
-  prm.mode = d.mode;
-  prm.alpha = d.alpha;
-  prm.njobs = (int)jobs.size();
-  prm.m_tiles = (d.rows + kBM - 1) / kBM;
-  prm.n_tiles = (d.n_a + kBN - 1) / kBN;
-  prm.total_tiles = prm.njobs * prm.m_tiles * prm.n_tiles;
-  prm.status = S->status;
-  prm.tile_counter = S->counter;
-  for (size_t i = 0; i < jobs.size(); ++i) prm.jobs[i] = jobs[i];
-  for (size_t i = 0; i < pairs.size(); ++i) prm.pairs[i] = pairs[i];
+static demag_status launch_groups(demag_plan* P, const TcGroup* groups, const int* tile0, int ngroups,
+                                  int total_tiles, int* counter, int* status, cudaStream_t st) {
+  if (total_tiles <= 0) return DEMAG_OK;
+  TcLaunch L;
+  L.groups = groups;
+  L.tile0 = tile0;
+  L.ngroups = ngroups;
+  L.total_tiles = total_tiles;
+  L.tile_counter = counter;
+  L.status = status;
   int sms = 0, dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int grid = prm.total_tiles < sms ? prm.total_tiles : sms;
-  DEMAG_CUDA(P, cudaMemsetAsync(S->counter, 0, sizeof(int), st));
-  DEMAG_LAUNCH(P, kFamGemmTc, st, tc_gemm_kernel<F><<<grid, kTcThreads, kSmemBytes, st>>>(prm));
+  const int grid = total_tiles < sms ? total_tiles : sms;
+  DEMAG_CUDA(P, cudaMemsetAsync(counter, 0, sizeof(int), st));
+  DEMAG_LAUNCH(P, kFamGemmTc, st, tc_gemm_kernel<F><<<grid, kTcThreads, kSmemBytes, st>>>(L));
   DEMAG_LAUNCHED(P, "tc_gemm_kernel");
   return DEMAG_OK;
 }
 
-static TcJob job(int pair0, int npairs, int out_field) {
-  TcJob j;
-  j.pair0 = pair0;
-  j.npairs = npairs;
-  j.out_field = out_field;
-  j.pad = 0;
-  return j;
+template <class F>
+static demag_status run_program(demag_plan* P, TcState* S, int prog, cudaStream_t st) {
+  return launch_groups<F>(P, S->prog + prog, S->tile0 + 2 * prog, 1, S->host_prog[prog].ntiles, S->counter,
+                          S->status, st);
 }
 
 template <class F>
@@ -681,131 +1036,29 @@ static demag_status split_input(demag_plan* P, TcState* S, const float* x, int f
   return DEMAG_OK;
 }
 
-// matrix index of (node k, type) in the per-axis factor maps
-static short mat(int k, int type) { return (short)(2 * k + type); }
-
-template <class F>
-static demag_status forward_chain(demag_plan* P, TcState* S, const float* m, float* phi, cudaStream_t st) {
-  const int n1 = P->n[0], n2 = P->n[1], n3 = P->n[2], M = P->M;
-  demag_status s = split_input<F>(P, S, m, 3, st);
-  if (s != DEMAG_OK) return s;
-  // mode 1: Y[k][q] = m_q x_1 T_{k,q,1}; rows (i3, i2), contraction i1 -> Y [i1'][i3][i2]
-  {
-    std::vector<TcJob> jobs;
-    std::vector<short2> pairs;
-    for (int q = 0; q < 3; ++q)
-      for (int k = 0; k < M; ++k) {
-        jobs.push_back(job((int)pairs.size(), 1, 3 * k + q));
-        pairs.push_back(make_short2((short)q, mat(k, q == 0 ? 1 : 0)));
-      }
-    StageDesc d{{&S->mapX[0], &S->mapX[1]}, {&S->mapB[0][0], &S->mapB[0][1]}, n3 * n2, n1, n1, S->bn[0],
-                S->buf1[0], S->buf1[1], (long long)n1 * n3 * S->ld[1], (long long)n3 * S->ld[1], S->ld[1], n2,
-                kOutSplit, 1.f};
-    s = launch_stage<F>(P, S, d, jobs, pairs, st);
-    if (s != DEMAG_OK) return s;
-  }
-  // mode 2: U_k = Y_k1 x_2 E + Y_k2 x_2 F, V_k = Y_k3 x_2 E; rows (i1', i3) -> [i2'][i1'][i3]
-  {
-    std::vector<TcJob> jobs;
-    std::vector<short2> pairs;
-    for (int k = 0; k < M; ++k) {
-      jobs.push_back(job((int)pairs.size(), 2, 2 * k));
-      pairs.push_back(make_short2((short)(3 * k + 0), mat(k, 0)));
-      pairs.push_back(make_short2((short)(3 * k + 1), mat(k, 1)));
-      jobs.push_back(job((int)pairs.size(), 1, 2 * k + 1));
-      pairs.push_back(make_short2((short)(3 * k + 2), mat(k, 0)));
-    }
-    StageDesc d{{&S->map1[0], &S->map1[1]}, {&S->mapB[1][0], &S->mapB[1][1]}, n1 * n3, n2, n2, S->bn[1],
-                S->buf2[0], S->buf2[1], (long long)n2 * n1 * S->ld[2], (long long)n1 * S->ld[2], S->ld[2], n3,
-                kOutSplit, 1.f};
-    s = launch_stage<F>(P, S, d, jobs, pairs, st);
-    if (s != DEMAG_OK) return s;
-  }
-  // mode 3 with the node sum: phi = sum_k U_k x_3 S E + V_k x_3 S F; rows (i2', i1') -> [i3'][i2'][i1']
-  {
-    std::vector<TcJob> jobs;
-    std::vector<short2> pairs;
-    for (int k = 0; k < M; ++k) {
-      pairs.push_back(make_short2((short)(2 * k), mat(k, 0)));
-      pairs.push_back(make_short2((short)(2 * k + 1), mat(k, 1)));
-    }
-    const int groups = (2 * M + S->pp3 - 1) / S->pp3;
-    for (int g = 0; g < groups; ++g) {
-      const int p0 = g * S->pp3;
-      jobs.push_back(job(p0, (2 * M - p0) < S->pp3 ? (2 * M - p0) : S->pp3, g));
-    }
-    const long long N = (long long)n3 * n2 * n1;
-    StageDesc d{{&S->map2[0], &S->map2[1]}, {&S->mapB[2][0], &S->mapB[2][1]}, n2 * n1, n3, n3, S->bn[2],
-                S->part, nullptr, N, (long long)n2 * n1, n1, n1, kOutF32, 1.f};
-    s = launch_stage<F>(P, S, d, jobs, pairs, st);
-    if (s != DEMAG_OK) return s;
-    DEMAG_LAUNCH(P, kFamMisc, st, reduce_parts_kernel<<<grid_blocks(N), 256, 0, st>>>(S->part, groups, N, 1, 1.f, phi));
-    DEMAG_LAUNCHED(P, "reduce_parts_kernel");
-  }
+static demag_status reduce_parts(demag_plan* P, TcState* S, int groups, int nout, float alpha, float* out,
+                                 cudaStream_t st) {
+  const long long N = (long long)P->n[0] * P->n[1] * P->n[2];
+  DEMAG_LAUNCH(P, kFamMisc, st,
+               reduce_parts_kernel<<<grid_blocks(nout * N), 256, 0, st>>>(S->part, groups, N, nout, alpha, out));
+  DEMAG_LAUNCHED(P, "reduce_parts_kernel");
   return DEMAG_OK;
 }
 
 template <class F>
-static demag_status adjoint_chain(demag_plan* P, TcState* S, const float* y, float* g, cudaStream_t st) {
-  const int n1 = P->n[0], n2 = P->n[1], n3 = P->n[2], M = P->M;
-  demag_status s = split_input<F>(P, S, y, 1, st);
+static demag_status forward_chain(demag_plan* P, TcState* S, const float* m, float* phi, cudaStream_t st) {
+  demag_status s = split_input<F>(P, S, m, 3, st);
+  for (int prog = kFwd1; prog <= kFwd3 && s == DEMAG_OK; ++prog) s = run_program<F>(P, S, prog, st);
   if (s != DEMAG_OK) return s;
-  // mode 1: Ya_k = y x_1 F, Yb_k = y x_1 E  (fields 2k, 2k+1 of buf1)
-  {
-    std::vector<TcJob> jobs;
-    std::vector<short2> pairs;
-    for (int k = 0; k < M; ++k)
-      for (int t = 0; t < 2; ++t) {
-        jobs.push_back(job((int)pairs.size(), 1, 2 * k + t));
-        pairs.push_back(make_short2((short)0, mat(k, t == 0 ? 1 : 0)));
-      }
-    StageDesc d{{&S->mapX[0], &S->mapX[1]}, {&S->mapB[0][0], &S->mapB[0][1]}, n3 * n2, n1, n1, S->bn[0],
-                S->buf1[0], S->buf1[1], (long long)n1 * n3 * S->ld[1], (long long)n3 * S->ld[1], S->ld[1], n2,
-                kOutSplit, 1.f};
-    s = launch_stage<F>(P, S, d, jobs, pairs, st);
-    if (s != DEMAG_OK) return s;
-  }
-  // mode 2: Za = Ya x_2 E (g1), Zb = Yb x_2 F (g2), Zc = Yb x_2 E (g3)  (fields 3k+q of buf2)
-  {
-    std::vector<TcJob> jobs;
-    std::vector<short2> pairs;
-    for (int k = 0; k < M; ++k) {
-      const short src[3] = {(short)(2 * k), (short)(2 * k + 1), (short)(2 * k + 1)};
-      const int typ[3] = {0, 1, 0};
-      for (int q = 0; q < 3; ++q) {
-        jobs.push_back(job((int)pairs.size(), 1, 3 * k + q));
-        pairs.push_back(make_short2(src[q], mat(k, typ[q])));
-      }
-    }
-    StageDesc d{{&S->map1[0], &S->map1[1]}, {&S->mapB[1][0], &S->mapB[1][1]}, n1 * n3, n2, n2, S->bn[1],
-                S->buf2[0], S->buf2[1], (long long)n2 * n1 * S->ld[2], (long long)n1 * S->ld[2], S->ld[2], n3,
-                kOutSplit, 1.f};
-    s = launch_stage<F>(P, S, d, jobs, pairs, st);
-    if (s != DEMAG_OK) return s;
-  }
-  // mode 3 with the node sum: g_q = -sum_k Z_kq x_3 S T_{k,q,3}
-  {
-    std::vector<TcJob> jobs;
-    std::vector<short2> pairs;
-    const int groups = (M + S->pp3 - 1) / S->pp3;
-    for (int q = 0; q < 3; ++q) {
-      const int base = (int)pairs.size();
-      for (int k = 0; k < M; ++k) pairs.push_back(make_short2((short)(3 * k + q), mat(k, q == 2 ? 1 : 0)));
-      for (int gi = 0; gi < groups; ++gi) {
-        const int p0 = gi * S->pp3;
-        jobs.push_back(job(base + p0, (M - p0) < S->pp3 ? (M - p0) : S->pp3, q * groups + gi));
-      }
-    }
-    const long long N = (long long)n3 * n2 * n1;
-    StageDesc d{{&S->map2[0], &S->map2[1]}, {&S->mapB[2][0], &S->mapB[2][1]}, n2 * n1, n3, n3, S->bn[2],
-                S->part, nullptr, N, (long long)n2 * n1, n1, n1, kOutF32, 1.f};
-    s = launch_stage<F>(P, S, d, jobs, pairs, st);
-    if (s != DEMAG_OK) return s;
-    DEMAG_LAUNCH(P, kFamMisc, st,
-                 reduce_parts_kernel<<<grid_blocks(3 * N), 256, 0, st>>>(S->part, groups, N, 3, -1.f, g));
-    DEMAG_LAUNCHED(P, "reduce_parts_kernel");
-  }
-  return DEMAG_OK;
+  return reduce_parts(P, S, S->groups_fwd, 1, 1.f, phi, st);
+}
+
+template <class F>
+static demag_status adjoint_chain(demag_plan* P, TcState* S, const float* y, float* g, cudaStream_t st) {
+  demag_status s = split_input<F>(P, S, y, 1, st);
+  for (int prog = kAdj1; prog <= kAdj3 && s == DEMAG_OK; ++prog) s = run_program<F>(P, S, prog, st);
+  if (s != DEMAG_OK) return s;
+  return reduce_parts(P, S, S->groups_adj, 3, -1.f, g, st);
 }
 
 demag_status tc_forward(demag_plan* P, const float* m, float* phi, demag_precision prec, cudaStream_t st) {
@@ -820,6 +1073,98 @@ demag_status tc_adjoint(demag_plan* P, const float* y, float* g, demag_precision
   if (s != DEMAG_OK) return s;
   TcState* S = state(P, prec);
   return prec == DEMAG_TF32X3 ? adjoint_chain<Tf32Form>(P, S, y, g, st) : adjoint_chain<Bf16Form>(P, S, y, g, st);
+}
+
+void tc_batch_destroy(TcBatch* B) {
+  if (!B) return;
+  cudaFree(B->groups);
+  cudaFree(B->tile0);
+  delete B;
+}
+
+// Concatenate the forward stage programs of `plans` (which must be distinct and
+// have their tensor-core state for `prec`) into per-stage group arrays.
+demag_status tc_batch_create(demag_plan* const* plans, int count, demag_precision prec, TcBatch** out) {
+  *out = nullptr;
+  demag_plan* P0 = plans[0];
+  TcBatch* B = new TcBatch();
+  B->plans.assign(plans, plans + count);
+  for (int i = 0; i < count; ++i) B->serials.push_back(plans[i]->serial);
+  B->prec = (int)prec;
+  std::vector<TcGroup> g(3 * (size_t)count);
+  std::vector<int> t0(3 * (size_t)(count + 1));
+  for (int st3 = 0; st3 < 3; ++st3) {
+    int acc = 0;
+    for (int i = 0; i < count; ++i) {
+      const TcState* S = state(plans[i], prec);
+      g[st3 * count + i] = S->host_prog[kFwd1 + st3];
+      t0[st3 * (count + 1) + i] = acc;
+      acc += S->host_prog[kFwd1 + st3].ntiles;
+    }
+    t0[st3 * (count + 1) + count] = acc;
+    B->total[st3] = acc;
+  }
+  if (cudaMalloc(&B->groups, sizeof(TcGroup) * g.size()) != cudaSuccess ||
+      cudaMalloc(&B->tile0, sizeof(int) * t0.size()) != cudaSuccess) {
+    tc_batch_destroy(B);
+    return set_error(P0, DEMAG_ENOMEM, "grouped launch descriptors: allocation failed");
+  }
+  cudaError_t e = cudaMemcpy(B->groups, g.data(), sizeof(TcGroup) * g.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(B->tile0, t0.data(), sizeof(int) * t0.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    tc_batch_destroy(B);
+    return cuda_error(P0, e, "grouped launch descriptors");
+  }
+  *out = B;
+  return DEMAG_OK;
+}
+
+// Several grids in one call: each plan's input is split, then every forward
+// stage of all grids runs as ONE persistent launch over the concatenated group
+// descriptors (tiles of all grids share the dynamic tile counter of the first
+// plan), then each plan's node-sum partials are reduced into its phi.
+template <class F>
+static demag_status batched_chain(const TcBatch* B, const float* const* m, float* const* phi, cudaStream_t st) {
+  const demag_precision prec = (demag_precision)B->prec;
+  const int count = (int)B->plans.size();
+  demag_plan* P0 = B->plans[0];
+  TcState* S0 = state(P0, prec);
+  for (int i = 0; i < count; ++i) {
+    demag_status s = split_input<F>(B->plans[i], state(B->plans[i], prec), m[i], 3, st);
+    if (s != DEMAG_OK) return s;
+  }
+  for (int st3 = 0; st3 < 3; ++st3) {
+    demag_status s = launch_groups<F>(P0, B->groups + (size_t)st3 * count, B->tile0 + (size_t)st3 * (count + 1),
+                                      count, B->total[st3], S0->counter, S0->status, st);
+    if (s != DEMAG_OK) return s;
+  }
+  for (int i = 0; i < count; ++i) {
+    TcState* S = state(B->plans[i], prec);
+    demag_status s = reduce_parts(B->plans[i], S, S->groups_fwd, 1, 1.f, phi[i], st);
+    if (s != DEMAG_OK) return s;
+  }
+  return DEMAG_OK;
+}
+
+demag_status tc_batch_run(const TcBatch* B, const float* const* m, float* const* phi, cudaStream_t st) {
+  return B->prec == DEMAG_TF32X3 ? batched_chain<Tf32Form>(B, m, phi, st) : batched_chain<Bf16Form>(B, m, phi, st);
+}
+
+demag_status tc_forward_batched(demag_plan* const* plans, const float* const* m, float* const* phi, int count,
+                                demag_precision prec, cudaStream_t st) {
+  if (count <= 0) return DEMAG_OK;
+  TcHolder* H = reinterpret_cast<TcHolder*>(plans[0]->tc);
+  TcBatch* B = H->cache;
+  bool hit = B && B->prec == (int)prec && (int)B->plans.size() == count;
+  for (int i = 0; hit && i < count; ++i) hit = B->plans[i] == plans[i] && B->serials[i] == plans[i]->serial;
+  if (!hit) {
+    tc_batch_destroy(H->cache);
+    H->cache = nullptr;
+    demag_status s = tc_batch_create(plans, count, prec, &H->cache);
+    if (s != DEMAG_OK) return s;
+    B = H->cache;
+  }
+  return tc_batch_run(B, m, phi, st);
 }
 
 demag_status tc_sync_status(demag_plan* P, cudaStream_t st) {

@@ -37,6 +37,7 @@ struct demag_plan {
   int L[3];         // FFT length per axis (power of 2 >= 2 n_p - 1, >= 2)
   int nmax, Lmax;
   int glen;         // generator row length 2*nmax - 1
+  unsigned long long serial = 0;  // unique per plan in the process (cache keys)
 
   // setup data (device)
   double* nodes = nullptr;   // [3][M]: t, tau, omega
@@ -60,6 +61,16 @@ struct demag_plan {
   void* tc = nullptr;
   // energy / gradient scratch: phi, D^T m (1 field each) and P^T D^T m (3 fields)
   float* ews = nullptr;
+
+  // autotuning: when on, launch shapes not yet tuned are timed on first use
+  bool autotune = false;
+  struct Tuned {
+    int kind;      // 0 FFT nodes per block; 1 / 2 tensor-core N tile (BF16x3 / TF32x3)
+    int key[3];    // FFT: log2 N, column blocks, M; tensor core: stage program, default tile, 0
+    int value;     // chosen setting
+    float ms;      // its time per launch
+  };
+  std::vector<Tuned> tuned;
 
   // diagnostics: kernels launched, and optional CUDA-event timing per family
   unsigned long long launches = 0;
@@ -123,6 +134,12 @@ demag_status tc_forward(demag_plan* plan, const float* m, float* phi, demag_prec
                         cudaStream_t st);
 demag_status tc_adjoint(demag_plan* plan, const float* y, float* g, demag_precision prec,
                         cudaStream_t st);
+struct TcBatch;
+demag_status tc_batch_create(demag_plan* const* plans, int count, demag_precision prec, TcBatch** out);
+demag_status tc_batch_run(const TcBatch* batch, const float* const* m, float* const* phi, cudaStream_t st);
+void tc_batch_destroy(TcBatch* batch);
+demag_status tc_forward_batched(demag_plan* const* plans, const float* const* m, float* const* phi, int count,
+                                demag_precision prec, cudaStream_t st);
 size_t tc_workspace_bytes(const demag_plan* plan, demag_precision prec);
 demag_status tc_sync_status(demag_plan* plan, cudaStream_t st);
 bool tc_ready(const demag_plan* plan, demag_precision prec);

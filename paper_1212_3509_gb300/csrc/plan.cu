@@ -4,6 +4,7 @@
 // (erf / exp differences), Sec. 4.2 (Eq. conv_op, conv_pot, fft_pot).
 #include <cstdarg>
 #include <cmath>
+#include <atomic>
 #include <new>
 
 #include "internal.h"
@@ -267,6 +268,8 @@ extern "C" demag_status demag_build_factors(const demag_grid_desc* d, demag_plan
   demag_plan* P = new (std::nothrow) demag_plan();
   if (!P) return set_error(nullptr, DEMAG_ENOMEM, "host allocation failed");
   snprintf(P->err, sizeof(P->err), "no error");
+  static std::atomic<unsigned long long> next_serial{1};
+  P->serial = next_serial.fetch_add(1);
   P->R = d->R;
   P->M = (d->R - 1) / 2;
   P->c0 = d->c0;
@@ -422,6 +425,27 @@ extern "C" demag_status demag_sync_status(demag_plan* plan, void* stream) {
 }
 
 extern "C" unsigned long long demag_launch_count(const demag_plan* plan) { return plan ? plan->launches : 0ULL; }
+
+extern "C" demag_status demag_autotune(demag_plan* plan, int enable) {
+  if (!plan) return set_error(nullptr, DEMAG_EINVAL, "demag_autotune: plan is NULL");
+  plan->autotune = enable != 0;
+  return DEMAG_OK;
+}
+
+extern "C" int demag_autotune_count(const demag_plan* plan) { return plan ? (int)plan->tuned.size() : 0; }
+
+extern "C" demag_status demag_autotune_entry(const demag_plan* plan, int i, int* kind, int key[3], int* value,
+                                             float* ms) {
+  if (!plan || i < 0 || i >= (int)plan->tuned.size())
+    return set_error(nullptr, DEMAG_EINVAL, "demag_autotune_entry: no entry %d", i);
+  const demag_plan::Tuned& t = plan->tuned[i];
+  if (kind) *kind = t.kind;
+  if (key)
+    for (int j = 0; j < 3; ++j) key[j] = t.key[j];
+  if (value) *value = t.value;
+  if (ms) *ms = t.ms;
+  return DEMAG_OK;
+}
 
 extern "C" demag_status demag_profile(demag_plan* plan, int enable) {
   if (!plan) return set_error(nullptr, DEMAG_EINVAL, "demag_profile: plan is NULL");

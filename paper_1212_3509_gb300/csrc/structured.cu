@@ -34,20 +34,29 @@
 
 namespace demag {
 
-struct ToepLaunch {
+// One axis of a launch: its columns, input and output layout.
+struct ToepAxis {
   int n;           // column length n_p
   int axis;        // p
-  int M;           // number of nodes
   int rcols;       // columns per (batch item, component)
   int ncols;       // batch * 3 * rcols
-  int kgroup;      // nodes per block (grid.y covers M)
-  int pairstride;  // Lmax/2
   const float* in; // column (b, q, l) at in + b*in_bstride + q*in_qstride + l*n
   long in_bstride, in_qstride;
   float* out;      // node k: out + b*out_bstride + ((k*3 + q)*rcols + l)*n
   long out_bstride;
-  const float2* sympair;  // [M][2][3][pairstride]: (s_f, s_{N-f})
   const float2* twid;     // exp(-2 pi i m / L), m < L
+};
+
+// Every axis whose FFT length is the same goes into one launch: blocks
+// [bx0[s], bx0[s+1]) of grid.x serve axis slot s, grid.y covers the nodes.
+struct ToepLaunch {
+  ToepAxis ax[3];
+  int naxes;
+  int bx0[4];
+  int M;           // number of nodes
+  int kgroup;      // nodes per block
+  int pairstride;  // Lmax/2
+  const float2* sympair;  // [M][2][3][pairstride]: (s_f, s_{N-f})
 };
 
 __device__ __forceinline__ int pad16(int i) { return i + (i >> 4); }
@@ -142,7 +151,8 @@ __device__ __forceinline__ void mid_pass(float2* buf, int Ns, int lt, const TwSm
 }
 
 template <int LOGN>
-__global__ void __launch_bounds__(256, ToepCfg<LOGN>::minblocks) toeplitz_fft_kernel(ToepLaunch a) {
+__global__ void __launch_bounds__(256, ToepCfg<LOGN>::minblocks)
+    toeplitz_fft_kernel(const __grid_constant__ ToepLaunch a) {
   using Cfg = ToepCfg<LOGN>;
   constexpr int N = Cfg::N, TG = Cfg::TG, R1 = Cfg::R1, NPASS = Cfg::NPASS;
   extern __shared__ float2 smem_c[];
@@ -152,17 +162,21 @@ __global__ void __launch_bounds__(256, ToepCfg<LOGN>::minblocks) toeplitz_fft_ke
   float2* Pm = t1 + Cfg::T1 + (size_t)g * Cfg::group_floats2;
   float2* Qm = Pm + N;
   float2* buf = Qm + N;
-  for (int i = threadIdx.x; i < Cfg::T0; i += blockDim.x) t0[i] = __ldg(a.twid + i);
-  for (int i = threadIdx.x; i < Cfg::T1; i += blockDim.x) t1[i] = __ldg(a.twid + i * Cfg::T0);
+  int slot = 0;
+  while (slot + 1 < a.naxes && (int)blockIdx.x >= a.bx0[slot + 1]) ++slot;
+  const ToepAxis& A = a.ax[slot];
+  for (int i = threadIdx.x; i < Cfg::T0; i += blockDim.x) t0[i] = __ldg(A.twid + i);
+  for (int i = threadIdx.x; i < Cfg::T1; i += blockDim.x) t1[i] = __ldg(A.twid + i * Cfg::T0);
   const TwSmem tw{t0, t1};
 
-  const int c = blockIdx.x * Cfg::G + g;
-  const bool active = c < a.ncols;
-  const int l = active ? c % a.rcols : 0;
-  const int bq = active ? c / a.rcols : 0;
+  const int c = ((int)blockIdx.x - a.bx0[slot]) * Cfg::G + g;
+  const bool active = c < A.ncols;
+  const int l = active ? c % A.rcols : 0;
+  const int bq = active ? c / A.rcols : 0;
   const int q = bq % 3, b = bq / 3;
-  const int n = a.n;
-  const float* in = a.in + b * a.in_bstride + q * a.in_qstride + (long)l * n;
+  const int n = A.n;
+  const int rcols = A.rcols;
+  const float* in = A.in + b * A.in_bstride + q * A.in_qstride + (long)l * n;
 
   // 1. zero-padded column as N complex samples, forward FFT (once per column)
   for (int j = lt; j < N; j += TG) {
@@ -201,16 +215,17 @@ __global__ void __launch_bounds__(256, ToepCfg<LOGN>::minblocks) toeplitz_fft_ke
   }
   __syncthreads();
 
-  const int type = (a.axis == q) ? 1 : 0;  // F on the axis of the component
+  const int axis = A.axis;
+  const int type = (axis == q) ? 1 : 0;  // F on the axis of the component
   const float fsign = type ? -1.f : 1.f;
   const int k0 = blockIdx.y * a.kgroup;
   const int k1 = min(a.M, k0 + a.kgroup);
-  float* outbase = a.out + b * a.out_bstride + (long)l * n;
+  float* outbase = A.out + b * A.out_bstride + (long)l * n;
   // paired stores need an even length and an 8-byte aligned column start
   // (every (k, q) offset is a multiple of n, so one check per column)
   const bool vec = ((n & 1) == 0) && ((reinterpret_cast<uintptr_t>(outbase) & 7) == 0);
   for (int k = k0; k < k1; ++k) {
-    const float2* sp = a.sympair + ((long)(k * 2 + type) * 3 + a.axis) * a.pairstride;
+    const float2* sp = a.sympair + ((long)(k * 2 + type) * 3 + axis) * a.pairstride;
     // 3. first pass in registers on the bins j + r N/R1 of item j
     constexpr int items1 = N / R1;
     constexpr int ipt1 = (items1 + TG - 1) / TG;
@@ -237,7 +252,7 @@ __global__ void __launch_bounds__(256, ToepCfg<LOGN>::minblocks) toeplitz_fft_ke
           for (int r = 0; r < R1; ++r) {
             const int i = j + r * items1;
             if (active && 2 * i < n) {
-              float* o = outbase + (long)(k * 3 + q) * a.rcols * n;
+              float* o = outbase + (long)(k * 3 + q) * rcols * n;
               o[2 * i] = v[r].x;
               if (2 * i + 1 < n) o[2 * i + 1] = v[r].y;
             }
@@ -276,7 +291,7 @@ __global__ void __launch_bounds__(256, ToepCfg<LOGN>::minblocks) toeplitz_fft_ke
           }
           dft_reg<16, true>(v);
           if (active) {
-            float* o = outbase + (long)(k * 3 + q) * a.rcols * n;
+            float* o = outbase + (long)(k * 3 + q) * rcols * n;
 #pragma unroll
             for (int r = 0; r < 8; ++r) {
               const int i = j + r * items;
@@ -316,14 +331,13 @@ __global__ void weights_kernel(int M, int batch, int rq, const double* scale, co
 }
 
 template <int LOGN>
-static cudaError_t launch_toep(demag_plan* P, const ToepLaunch& a, cudaStream_t st) {
+static cudaError_t launch_toep(demag_plan* P, const ToepLaunch& a, int gx, cudaStream_t st) {
   using Cfg = ToepCfg<LOGN>;
   if (Cfg::smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(toeplitz_fft_kernel<LOGN>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::smem);
     if (e != cudaSuccess) return e;
   }
-  int gx = (a.ncols + Cfg::G - 1) / Cfg::G;
   int gy = (a.M + a.kgroup - 1) / a.kgroup;
   DEMAG_LAUNCH(P, kFamFFT, st, toeplitz_fft_kernel<LOGN><<<dim3(gx, gy), 256, Cfg::smem, st>>>(a));
   return cudaGetLastError();
@@ -341,35 +355,115 @@ static int groups_per_block(int logn) {
   return 256 / TG;
 }
 
-static cudaError_t run_toep(demag_plan* P, ToepLaunch a, cudaStream_t st) {
-  const int logn = ilog2i(P->L[a.axis] / 2);
-  a.n = P->n[a.axis];
-  a.M = P->M;
-  a.pairstride = P->Lmax / 2;
-  a.sympair = P->sympair;
-  a.twid = P->twid[a.axis];
-  // node grouping: enough blocks to fill the GPU, spectra reused across nodes
-  int gx = (a.ncols + groups_per_block(logn) - 1) / groups_per_block(logn);
-  int kg = a.M;
-  while (kg > 1 && (long)gx * ((a.M + kg - 1) / kg) < 1216) kg = (kg + 1) / 2;
-  a.kgroup = kg;
+static cudaError_t launch_logn(demag_plan* P, int logn, const ToepLaunch& a, int gx, cudaStream_t st) {
   switch (logn) {
-    case 0: return launch_toep<0>(P, a, st);
-    case 1: return launch_toep<1>(P, a, st);
-    case 2: return launch_toep<2>(P, a, st);
-    case 3: return launch_toep<3>(P, a, st);
-    case 4: return launch_toep<4>(P, a, st);
-    case 5: return launch_toep<5>(P, a, st);
-    case 6: return launch_toep<6>(P, a, st);
-    case 7: return launch_toep<7>(P, a, st);
-    case 8: return launch_toep<8>(P, a, st);
-    case 9: return launch_toep<9>(P, a, st);
-    case 10: return launch_toep<10>(P, a, st);
-    case 11: return launch_toep<11>(P, a, st);
-    case 12: return launch_toep<12>(P, a, st);
-    case 13: return launch_toep<13>(P, a, st);
+    case 0: return launch_toep<0>(P, a, gx, st);
+    case 1: return launch_toep<1>(P, a, gx, st);
+    case 2: return launch_toep<2>(P, a, gx, st);
+    case 3: return launch_toep<3>(P, a, gx, st);
+    case 4: return launch_toep<4>(P, a, gx, st);
+    case 5: return launch_toep<5>(P, a, gx, st);
+    case 6: return launch_toep<6>(P, a, gx, st);
+    case 7: return launch_toep<7>(P, a, gx, st);
+    case 8: return launch_toep<8>(P, a, gx, st);
+    case 9: return launch_toep<9>(P, a, gx, st);
+    case 10: return launch_toep<10>(P, a, gx, st);
+    case 11: return launch_toep<11>(P, a, gx, st);
+    case 12: return launch_toep<12>(P, a, gx, st);
+    case 13: return launch_toep<13>(P, a, gx, st);
     default: return cudaErrorInvalidValue;
   }
+}
+
+// Nodes per block.  Each block transforms its columns once and reuses the
+// spectra for kgroup nodes, so large groups save forward FFTs, while small
+// groups give more blocks.  Default: the largest group that still yields
+// eight blocks per SM; with autotuning on, the candidates M, M/2, M/4, ..., 1
+// are timed once per (FFT length, column blocks, M) and the fastest is kept.
+static cudaError_t pick_kgroup(demag_plan* P, int logn, ToepLaunch& a, int gx, cudaStream_t st) {
+  const int M = a.M;
+  for (const demag_plan::Tuned& t : P->tuned)
+    if (t.kind == 0 && t.key[0] == logn && t.key[1] == gx && t.key[2] == M) {
+      a.kgroup = t.value;
+      return cudaSuccess;
+    }
+  int kg = M;
+  while (kg > 1 && (long)gx * ((M + kg - 1) / kg) < 1216) kg = (kg + 1) / 2;
+  a.kgroup = kg;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(st, &cap);
+  if (!P->autotune || cap != cudaStreamCaptureStatusNone) return cudaSuccess;
+  std::vector<int> cands;
+  for (int c = M;; c = (c + 1) / 2) {
+    if (cands.empty() || cands.back() != c) cands.push_back(c);
+    if (c == 1) break;
+  }
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  int best_kg = kg;
+  cudaError_t err = cudaSuccess;
+  for (int c : cands) {
+    a.kgroup = c;
+    err = launch_logn(P, logn, a, gx, st);  // warm-up
+    cudaEventRecord(e0, st);
+    for (int r = 0; r < 3 && err == cudaSuccess; ++r) err = launch_logn(P, logn, a, gx, st);
+    cudaEventRecord(e1, st);
+    if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+    if (err != cudaSuccess) break;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) {
+      best = ms;
+      best_kg = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (err != cudaSuccess) return err;
+  a.kgroup = best_kg;
+  demag_plan::Tuned t;
+  t.kind = 0;
+  t.key[0] = logn;
+  t.key[1] = gx;
+  t.key[2] = M;
+  t.value = best_kg;
+  t.ms = best / 3.f;
+  P->tuned.push_back(t);
+  return cudaSuccess;
+}
+
+// Toeplitz matvecs of the given axes: axes that share an FFT length run in
+// one launch (normally all three), each as its own range of blocks.
+static demag_status run_axes(demag_plan* P, ToepAxis* axes, int count, const char* what, cudaStream_t st) {
+  bool done[3] = {false, false, false};
+  for (int i = 0; i < count; ++i) {
+    if (done[i]) continue;
+    const int logn = ilog2i(P->L[axes[i].axis] / 2);
+    const int G = groups_per_block(logn);
+    ToepLaunch a{};
+    a.M = P->M;
+    a.pairstride = P->Lmax / 2;
+    a.sympair = P->sympair;
+    int gx = 0;
+    for (int j = i; j < count; ++j) {
+      if (done[j] || ilog2i(P->L[axes[j].axis] / 2) != logn) continue;
+      ToepAxis x = axes[j];
+      x.n = P->n[x.axis];
+      x.twid = P->twid[x.axis];
+      a.ax[a.naxes] = x;
+      a.bx0[a.naxes] = gx;
+      gx += (x.ncols + G - 1) / G;
+      ++a.naxes;
+      done[j] = true;
+    }
+    a.bx0[a.naxes] = gx;
+    cudaError_t e = pick_kgroup(P, logn, a, gx, st);
+    if (e == cudaSuccess) e = launch_logn(P, logn, a, gx, st);
+    if (e != cudaSuccess) return cuda_error(P, e, what);
+  }
+  return DEMAG_OK;
 }
 
 static demag_status check_fft_plan(demag_plan* P, const char* what) {
@@ -402,9 +496,11 @@ extern "C" demag_status demag_apply_cp_batched(demag_plan* P, int batch, int r, 
   if (!lambda || !U || !out_w || !out_U) return set_error(P, DEMAG_EINVAL, "demag_apply_cp: NULL pointer");
   cudaStream_t st = (cudaStream_t)stream;
   const long nsum = (long)P->n[0] + P->n[1] + P->n[2];
+  ToepAxis ax[3];
   long aoff = 0;
   for (int p = 0; p < 3; ++p) {
-    ToepLaunch a{};
+    ToepAxis& a = ax[p];
+    a = ToepAxis{};
     a.axis = p;
     a.rcols = r;
     a.ncols = batch * 3 * r;
@@ -413,10 +509,10 @@ extern "C" demag_status demag_apply_cp_batched(demag_plan* P, int batch, int r, 
     a.in_qstride = (long)r * nsum;
     a.out = out_U + (long)P->M * 3 * r * aoff;
     a.out_bstride = (long)P->M * 3 * r * nsum;
-    cudaError_t e = run_toep(P, a, st);
-    if (e != cudaSuccess) return cuda_error(P, e, "toeplitz_fft_kernel (cp)");
     aoff += P->n[p];
   }
+  s = run_axes(P, ax, 3, "toeplitz_fft_kernel (cp)", st);
+  if (s != DEMAG_OK) return s;
   return launch_weights(P, batch, r, lambda, out_w, st);
 }
 
@@ -435,9 +531,11 @@ extern "C" demag_status demag_apply_tucker(demag_plan* P, const int r[3], const 
   cudaStream_t st = (cudaStream_t)stream;
   long qstride = 0;
   for (int p = 0; p < 3; ++p) qstride += (long)r[p] * P->n[p];
+  ToepAxis ax[3];
   long aoff = 0;
   for (int p = 0; p < 3; ++p) {
-    ToepLaunch a{};
+    ToepAxis& a = ax[p];
+    a = ToepAxis{};
     a.axis = p;
     a.rcols = r[p];
     a.ncols = 3 * r[p];
@@ -446,10 +544,10 @@ extern "C" demag_status demag_apply_tucker(demag_plan* P, const int r[3], const 
     a.in_qstride = qstride;
     a.out = out_V + (long)P->M * 3 * aoff;
     a.out_bstride = 0;
-    cudaError_t e = run_toep(P, a, st);
-    if (e != cudaSuccess) return cuda_error(P, e, "toeplitz_fft_kernel (tucker)");
     aoff += (long)r[p] * P->n[p];
   }
+  s = run_axes(P, ax, 3, "toeplitz_fft_kernel (tucker)", st);
+  if (s != DEMAG_OK) return s;
   return launch_weights(P, 1, 1, nullptr, out_w, st);
 }
 
@@ -465,8 +563,10 @@ extern "C" demag_status demag_apply_tt(demag_plan* P, const int r[2], const floa
   const int rc[3] = {r[0], r[0] * r[1], r[1]};
   const float* ins[3] = {G1, G2, G3};
   float* outs[3] = {oG1, oG2, oG3};
+  ToepAxis ax[3];
   for (int p = 0; p < 3; ++p) {
-    ToepLaunch a{};
+    ToepAxis& a = ax[p];
+    a = ToepAxis{};
     a.axis = p;
     a.rcols = rc[p];
     a.ncols = 3 * rc[p];
@@ -475,8 +575,8 @@ extern "C" demag_status demag_apply_tt(demag_plan* P, const int r[2], const floa
     a.in_qstride = (long)rc[p] * P->n[p];
     a.out = outs[p];
     a.out_bstride = 0;
-    cudaError_t e = run_toep(P, a, st);
-    if (e != cudaSuccess) return cuda_error(P, e, "toeplitz_fft_kernel (tt)");
   }
+  s = run_axes(P, ax, 3, "toeplitz_fft_kernel (tt)", st);
+  if (s != DEMAG_OK) return s;
   return launch_weights(P, 1, 1, nullptr, out_w, st);
 }

@@ -23,6 +23,7 @@ TC_SHAPES = [
     ((64, 64, 4), (1 / 64, 1 / 64, 1 / 64), 41),
     ((300, 20, 10), (1 / 300,) * 3, 11),
     ((48, 40, 264), (1.0, 1.0, 1.0), 11),
+    ((64, 32, 96), (0.02, 0.02, 0.02), 21),
 ]
 
 
@@ -63,8 +64,11 @@ def test_split_adjoint_vs_oracle(D, n, h, R, prec):
     assert err <= TOL[prec], err
 
 
-def test_bf16x3_repeated_calls_are_identical(D):
-    n, h, R = (40, 24, 16), (0.05,) * 3, 21
+@pytest.mark.parametrize("n", [(40, 24, 16), (64, 32, 96), (96, 64, 32)])
+def test_bf16x3_repeated_calls_are_identical(D, n):
+    # (64, 32, 96) and (96, 64, 32) store every stage through TMA with an odd
+    # number of 32-column chunks per tile
+    h, R = (0.05,) * 3, 21
     m = dev(synth.random_unit_m(n, 99))
     P = D.demag_build_factors(n, h, R)
     a = torch.empty(n[2], n[1], n[0], device="cuda")
@@ -73,3 +77,73 @@ def test_bf16x3_repeated_calls_are_identical(D):
     D.demag_apply_full(P, m, b, "bf16x3")
     torch.cuda.synchronize()
     assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32x3"])
+def test_grouped_batch_equals_single_applies(D, prec):
+    """One grouped launch per stage over grids of different shapes (TMA-stored
+    and directly stored epilogues mixed, a plan listed twice) gives, bit for
+    bit, what separate calls give: every tile runs the same MMA sequence."""
+    cases = [TC_SHAPES[0], TC_SHAPES[1], TC_SHAPES[4], TC_SHAPES[7], TC_SHAPES[8]]
+    plans, ms, single = [], [], []
+    for i, (n, h, R) in enumerate(cases):
+        P = D.demag_build_factors(n, h, R)
+        m = dev(synth.random_unit_m(n, 4242 + i))
+        phi = torch.empty(n[2], n[1], n[0], device="cuda")
+        D.demag_apply_full(P, m, phi, prec)
+        plans.append(P)
+        ms.append(m)
+        single.append(phi)
+    # the first plan again, with another input, at the end of the list
+    n0 = cases[0][0]
+    m_extra = dev(synth.random_unit_m(n0, 777))
+    ref_extra = torch.empty(n0[2], n0[1], n0[0], device="cuda")
+    D.demag_apply_full(plans[0], m_extra, ref_extra, prec)
+    outs = [torch.full_like(p, float("nan")) for p in single] + [torch.full_like(ref_extra, float("nan"))]
+    D.demag_apply_full_batched(plans + [plans[0]], ms + [m_extra], outs, prec)
+    torch.cuda.synchronize()
+    for P in plans:
+        D.demag_sync_status(P)
+    for got, ref in zip(outs, single + [ref_extra]):
+        assert torch.equal(got, ref)
+    n, h, R = cases[3]
+    err = rel_l2(host(outs[3]), ofull.apply_full(host(ms[3]), n, h, R))
+    assert err <= TOL[prec], err
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "fp32"])
+def test_graph_replay_equals_batched_call(D, prec):
+    """The captured graph of a batched apply reproduces the direct call bit for
+    bit on replay, picks up new input values, and rejects a repeated plan."""
+    cases = [TC_SHAPES[0], TC_SHAPES[1], ((64, 32, 96), (0.02,) * 3, 21)]
+    plans, ms, ref, outs = [], [], [], []
+    for i, (n, h, R) in enumerate(cases):
+        P = D.demag_build_factors(n, h, R)
+        D.demag_reserve_workspace(P, prec)
+        plans.append(P)
+        ms.append(dev(synth.random_unit_m(n, 31 + i)))
+        ref.append(torch.empty(n[2], n[1], n[0], device="cuda"))
+        outs.append(torch.full_like(ref[-1], float("nan")))
+    D.demag_apply_full_batched(plans, ms, ref, prec)
+    G = D.demag_graph_create_batched(plans, ms, outs, prec)
+    assert G.kernels > 0
+    torch.cuda.synchronize()
+    assert all(torch.isnan(o).all() for o in outs)  # capture runs nothing
+    before = D.demag_launch_count(plans[0])
+    for _ in range(2):
+        G.launch()
+        torch.cuda.synchronize()
+        for got, want in zip(outs, ref):
+            assert torch.equal(got, want)
+    assert D.demag_launch_count(plans[0]) == before + 2 * G.kernels
+    # new values in the same buffers
+    ms[1].copy_(dev(synth.random_unit_m(cases[1][0], 555)))
+    D.demag_apply_full_batched(plans, ms, ref, prec)
+    G.launch()
+    torch.cuda.synchronize()
+    for P in plans:
+        D.demag_sync_status(P)
+    assert torch.equal(outs[1], ref[1])
+    with pytest.raises(D.DemagError):
+        D.demag_graph_create_batched([plans[0], plans[0]], [ms[0], ms[0]], [outs[0], outs[0]], prec)
+    G.close()
