@@ -213,6 +213,11 @@ def run_ours(args, world, rank, local):
     fam = "gemm_tc" if form in ("bf16x3", "tf32x3") else "gemm_simt"
     gemm_ms, gemm_n = D.demag_profile_read(P, fam)
     split_ms, split_n = D.demag_profile_read(P, "split")
+    misc_ms, _ = D.demag_profile_read(P, "misc")
+    recs = [D.demag_profile_launch(P, i) for i in range(D.demag_profile_count(P))]
+    gemm_recs = [t for f, t in recs if f == fam]
+    per_app = max(1, len(gemm_recs) // args.steps)
+    stage_ms = [sum(gemm_recs[j::per_app]) / args.steps for j in range(per_app)]
     ms_full_max = max_over_ranks(ms_full, world)
 
     M = P.M
@@ -342,6 +347,8 @@ def run_ours(args, world, rank, local):
                      "algorithmic_flops_per_app": flops_app, "launches_per_app": gemm_n / args.steps,
                      "kernel_ms_per_app": gemm_ms_app, "peak_source": peak_note,
                      "split_ms_per_app": split_ms / args.steps,
+                     "stage_ms_per_app": stage_ms,
+                     "reduce_ms_per_app": misc_ms / args.steps,
                      # the split forms issue 3 tensor-core products per algorithmic product
                      "tensor_pipe_issued_tflops": achieved_tflops * (3 if fam == "gemm_tc" else 1),
                      "tensor_pipe_issued_frac": achieved_tflops * (3 if fam == "gemm_tc" else 1) / peak},

@@ -273,6 +273,10 @@ unsigned long long demag_launch_count(const demag_plan* plan);
  * Reading waits for the recorded events. */
 demag_status demag_profile(demag_plan* plan, int enable);
 demag_status demag_profile_read(demag_plan* plan, int family, double* total_ms, long long* launches);
+/* The recorded launches one by one, in launch order: their number, and the
+ * family and duration (ms) of record i.  Reading waits for its events. */
+long long demag_profile_count(const demag_plan* plan);
+demag_status demag_profile_launch(demag_plan* plan, long long i, int* family, double* ms);
 
 /* ---- autotuning (build-only; no counterpart in the paper) --------------- */
 

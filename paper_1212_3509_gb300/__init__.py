@@ -42,6 +42,8 @@ from ._abi import (  # noqa: F401
     demag_sync_status,
     demag_launch_count,
     demag_profile,
+    demag_profile_count,
+    demag_profile_launch,
     demag_profile_read,
     FAMILIES,
 )

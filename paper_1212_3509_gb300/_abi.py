@@ -69,6 +69,8 @@ _SIGS = {
                                   ctypes.POINTER(ctypes.c_float)]),
     "demag_profile": (_i, [_vp, _i]),
     "demag_profile_read": (_i, [_vp, _i, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]),
+    "demag_profile_count": (ctypes.c_longlong, [_vp]),
+    "demag_profile_launch": (_i, [_vp, ctypes.c_longlong, ctypes.POINTER(_i), ctypes.POINTER(ctypes.c_double)]),
 }
 
 FAMILIES = {"gemm_simt": 0, "gemm_tc": 1, "fft": 2, "split": 3, "setup": 4, "energy": 5, "misc": 6}
@@ -347,6 +349,20 @@ def demag_profile_read(plan: Plan, family) -> tuple:
     ms, cnt = ctypes.c_double(), ctypes.c_longlong()
     _check(lib.demag_profile_read(plan.ptr, fam, ctypes.byref(ms), ctypes.byref(cnt)), plan.ptr)
     return ms.value, cnt.value
+
+
+def demag_profile_count(plan: Plan) -> int:
+    return lib.demag_profile_count(plan.ptr)
+
+
+_FAMILY_NAMES = {v: k for k, v in FAMILIES.items()}
+
+
+def demag_profile_launch(plan: Plan, i: int) -> tuple:
+    """(family name, milliseconds) of recorded launch i, in launch order."""
+    fam, ms = _i(), ctypes.c_double()
+    _check(lib.demag_profile_launch(plan.ptr, int(i), ctypes.byref(fam), ctypes.byref(ms)), plan.ptr)
+    return _FAMILY_NAMES.get(fam.value, fam.value), ms.value
 
 
 def demag_apply_full_noalloc(n, h, R: int, m, phi, c0: float = 2.15, stream=None):

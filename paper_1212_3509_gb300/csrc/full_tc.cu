@@ -44,11 +44,26 @@ constexpr int kTileA = kBM * kRowBytes;            // 8 KB
 constexpr int kTileB = kBN * kRowBytes;            // 16 KB
 constexpr int kStageBytes = 2 * kTileA + 2 * kTileB;  // 48 KB
 constexpr int kBarBytes = 256;
+// Epilogue warps: kEpiWarps / 4 warps share each TMEM lane quadrant and take
+// its 32-column chunks in turn.  Four (one per quadrant) measured as fast as
+// eight: the stage time is set by the output write traffic, not by epilogue
+// latency.
+#ifndef DEMAG_TC_EPI_WARPS
+#define DEMAG_TC_EPI_WARPS 4
+#endif
+constexpr int kEpiWarps = DEMAG_TC_EPI_WARPS;
+static_assert(kEpiWarps == 4 || kEpiWarps == 8, "4 or 8 epilogue warps");
+constexpr int kEpiSlices = kEpiWarps / 4;          // warps per TMEM lane quadrant
 constexpr int kOutBuf = 4096;                      // one 32 x 32 output chunk (2 BF16 planes or 1 FP32)
-constexpr int kOutStaging = 4 * 2 * kOutBuf;       // 4 epilogue warps, double-buffered
+constexpr int kOutStaging = 8 * kOutBuf;           // staging buffers shared out among the epilogue warps
+constexpr int kOutBufsPerWarp = kOutStaging / (kOutBuf * kEpiWarps);
 constexpr int kSmemBytes = kStages * kStageBytes + kOutStaging + kBarBytes + 1024;
-constexpr int kTcThreads = 192;
+constexpr int kTcThreads = 64 + 32 * kEpiWarps;
 constexpr int kRing = 4;                           // tile ids handed from the producer to the other roles
+#ifndef DEMAG_TC_ROW_GROUP
+#define DEMAG_TC_ROW_GROUP 1
+#endif
+constexpr int kRowGroup = DEMAG_TC_ROW_GROUP;      // default row blocks per super-block of the tile order
 constexpr uint64_t kWaitNs = 2000000000ull;        // 2 s bound on every wait
 constexpr uint32_t kSwizzle64 = 4;                 // descriptor code of SWIZZLE_64B
 constexpr uint32_t kSBO = 8 * kRowBytes;           // 8 rows x 64 bytes per swizzle atom
@@ -68,6 +83,13 @@ struct Bf16Form {
     hi = __float2bfloat16_rn(x);
     lo = __float2bfloat16_rn(x - __bfloat162float(hi));
   }
+  // four consecutive values to an 8-byte aligned address
+  __device__ static void store4(T* p, const T (&v)[4]) {
+    uint2 u;
+    u.x = (uint32_t)__bfloat16_as_ushort(v[0]) | ((uint32_t)__bfloat16_as_ushort(v[1]) << 16);
+    u.y = (uint32_t)__bfloat16_as_ushort(v[2]) | ((uint32_t)__bfloat16_as_ushort(v[3]) << 16);
+    *reinterpret_cast<uint2*>(p) = u;
+  }
 };
 
 struct Tf32Form {
@@ -86,6 +108,10 @@ struct Tf32Form {
   __device__ static void split(float x, T& hi, T& lo) {
     hi = to_tf32(x);
     lo = to_tf32(x - hi);
+  }
+  // four consecutive values to a 16-byte aligned address
+  __device__ static void store4(T* p, const T (&v)[4]) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
   }
 };
 
@@ -107,6 +133,7 @@ struct alignas(64) TcGroup {
   int rows, n_a, kblocks, bn, mode, tma_out;
   float alpha;
   int njobs, m_tiles, n_tiles, ntiles;
+  int rgroup;                          // row blocks per super-block of the tile order
 };
 
 struct TcLaunch {
@@ -126,11 +153,21 @@ __device__ __forceinline__ void tile_coords(const TcLaunch& L, int tile, int& g,
   g = lo;
   const TcGroup& G = L.groups[g];
   int t = tile - __ldg(L.tile0 + g);
-  // job fastest: consecutive tiles share the A row block (L2 reuse across nodes)
-  j = t % G.njobs;
-  t /= G.njobs;
+  // Tile order: super-blocks of `rgroup` row blocks; inside one, every job
+  // in turn over all of its row blocks (column tiles fastest).  rgroup = 1
+  // (the default) runs all jobs of one row block back to back, so the A rows
+  // they share are read from L2; larger groups make concurrently running
+  // tiles write neighbouring rows of one field instead (measured no faster on
+  // 160^3-256^3 grids, kept as a compile-time option).
+  const int per_sb = G.njobs * G.rgroup * G.n_tiles;
+  const int sb = t / per_sb;
+  t -= sb * per_sb;
+  const int rb0 = sb * G.rgroup;
+  const int gsb = min(G.rgroup, G.m_tiles - rb0);  // row blocks in this super-block
   nt = t % G.n_tiles;
-  mt = t / G.n_tiles;
+  t /= G.n_tiles;
+  mt = rb0 + t % gsb;
+  j = t / gsb;
 }
 
 __device__ __forceinline__ void tc_fail(volatile int* abort, int* status) {
@@ -163,11 +200,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const __grid_con
     }
     for (int b = 0; b < 2; ++b) {
       ptx::mbar_init(&tfull[b], 1);
-      ptx::mbar_init(&tempty[b], 4);
+      ptx::mbar_init(&tempty[b], kEpiWarps);
     }
     for (int i = 0; i < kRing; ++i) {
       ptx::mbar_init(&sfull[i], 1);
-      ptx::mbar_init(&sempty[i], 5);
+      ptx::mbar_init(&sempty[i], 1 + kEpiWarps);
     }
     ptx::mbar_init(drain, 1);
     *abort = 0;
@@ -286,7 +323,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const __grid_con
       }
     }
   } else {
-    const int quad = warp & 3;  // TMEM lane quadrant this warp may access
+    const int quad = warp & 3;                // TMEM lane quadrant this warp may access
+    const int slice = (warp - 2) / 4;         // which of the quadrant's chunks it takes
     const int rloc = quad * 32 + lane;
     int buf = 0;
     uint32_t tph = 0;
@@ -325,17 +363,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const __grid_con
         const int rw = mt * kBM + quad * 32;
         const int outer_w = rw / n_inner, inner_w = rw - outer_w * n_inner;
         const bool warp_valid = rw < G.rows;
-        uint8_t* stg = ostage + quad * (2 * kOutBuf);
-        for (int c0 = 0; c0 < bn; c0 += 32) {
+        uint8_t* stg = ostage + (warp - 2) * (kOutBufsPerWarp * kOutBuf);
+        for (int c0 = 32 * slice; c0 < bn; c0 += 32 * kEpiSlices) {
           uint32_t r[32];
           ptx::tmem_ld32(taddr + (uint32_t)c0, r);
           ptx::tmem_ld_wait();
           if (!warp_valid) continue;
-          // buffers alternate over the warp's whole chunk sequence (across
-          // tiles), so at most the other buffer's store can still be reading
-          uint8_t* sb = stg + (chunk & 1) * kOutBuf;
+          // a warp's buffers are used in turn over its whole chunk sequence
+          // (across tiles); before reuse, the store that last read a buffer
+          // must have finished reading it
+          uint8_t* sb = stg + (chunk % kOutBufsPerWarp) * kOutBuf;
           ++chunk;
-          if (lane == 0) ptx::bulk_wait_read_1();  // the store that used this buffer has read it
+          if (lane == 0) ptx::bulk_wait_read<kOutBufsPerWarp - 1>();
           __syncwarp();
           if (mode == kOutSplit) {
             T* sh = reinterpret_cast<T*>(sb);
@@ -368,7 +407,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const __grid_con
         const long long s_a = G.s_a;
         const long long rbase = (long long)out_field * G.field_elems + (long long)outer * G.ldC + inner;
         const int acount = min(bn, G.n_a - a0);  // columns of this tile that exist
-        for (int c0 = 0; c0 < bn; c0 += 32) {
+        for (int c0 = 32 * slice; c0 < bn; c0 += 32 * kEpiSlices) {
           uint32_t r[32];
           ptx::tmem_ld32(taddr + (uint32_t)c0, r);
           ptx::tmem_ld_wait();
@@ -429,20 +468,56 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const __grid_con
 
 // ---------------------------------------------------------------- operand preparation
 
-// hi/lo split of a [fields][rows][n] FP32 tensor into [fields][rows][ld] planes
+// Element-wise kernels over several grids in one launch: item i covers the
+// flat range [begin_i, begin_{i+1}) of the launch's index space; a thread's
+// indices only grow, so it finds its item by advancing from the last one.
+constexpr int kMaxItems = 128;
+
+struct SplitItem {
+  const float* x;      // [rows][n] FP32
+  void* hi;            // [rows][ld] planes
+  void* lo;
+  long long begin;     // first flat index of this item
+  int n, ld;
+  int vec;             // n % 4 == 0 and x 16-byte aligned
+};
+
+struct SplitList {
+  int count;
+  long long total;
+  SplitItem it[kMaxItems];
+};
+
+// hi/lo split of [rows][n] FP32 tensors into [rows][ld] planes.  The flat
+// index space counts groups of four consecutive elements of a row (rows are
+// padded to a multiple of four), so a row with n % 4 == 0 moves as 16-byte
+// loads and 4-element stores.
 template <class F>
-__global__ void split_rows_kernel(const float* __restrict__ x, long long nrows, int n, int ld,
-                                  typename F::T* __restrict__ hi, typename F::T* __restrict__ lo) {
-  const long long total = nrows * n;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+__global__ void split_rows_kernel(const __grid_constant__ SplitList L) {
+  using T = typename F::T;
+  int item = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < L.total;
        i += (long long)gridDim.x * blockDim.x) {
-    const long long r = i / n;
-    const int c = (int)(i - r * n);
-    typename F::T h, l;
-    F::split(x[i], h, l);
-    const long long o = r * ld + c;
-    hi[o] = h;
-    lo[o] = l;
+    while (item + 1 < L.count && i >= L.it[item + 1].begin) ++item;
+    const SplitItem& S = L.it[item];
+    const int quads = (S.n + 3) >> 2;
+    const long long e = i - S.begin;
+    const long long r = e / quads;
+    const int c = (int)(e - r * quads) * 4;
+    const float* src = S.x + r * S.n + c;
+    T* hi = reinterpret_cast<T*>(S.hi) + r * S.ld + c;
+    T* lo = reinterpret_cast<T*>(S.lo) + r * S.ld + c;
+    if (S.vec) {
+      const float4 v = *reinterpret_cast<const float4*>(src);
+      const float vv[4] = {v.x, v.y, v.z, v.w};
+      T h[4], l[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) F::split(vv[j], h[j], l[j]);
+      F::store4(hi, h);
+      F::store4(lo, l);
+    } else {
+      for (int j = 0; j < 4 && c + j < S.n; ++j) F::split(src[j], hi[j], lo[j]);
+    }
   }
 }
 
@@ -472,24 +547,74 @@ __global__ void tc_factor_kernel(int M, int glen, int axis, int n, int ld, const
 // to nearest, so the error of a long contraction grows with the number of
 // MMAs accumulated into one accumulator.  The node-sum stage (2M pairs of
 // length n3) is therefore split into groups of at most ~400 accumulations
-// (~200 for TF32x3), whose FP32 partial fields are summed on CUDA cores in FP64.
+// (~200 for TF32x3), whose FP32 partial fields are summed on CUDA cores with
+// a compensated sum.
 static int pairs_per_split(int kblocks, int budget) {
   const int per_pair = kblocks * 6;  // 2 k-steps x 3 products per k-block
   const int pp = budget / (per_pair > 0 ? per_pair : 1);
   return pp < 1 ? 1 : pp;
 }
 
-// out[q][i] = alpha * sum_g part[q*groups + g][i], accumulated in FP64
-__global__ void reduce_parts_kernel(const float* __restrict__ part, int groups, long long N, int nout, float alpha,
-                                    float* __restrict__ out) {
-  const long long total = (long long)nout * N;
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+struct ReduceItem {
+  const float* part;   // [nout][groups][N] partial fields
+  float* out;          // [nout][N]
+  long long begin;     // first flat index of this item
+  long long N;
+  int groups;
+  float alpha;
+  int vec;             // N % 4 == 0 and out 16-byte aligned: groups of four elements
+};
+
+struct ReduceList {
+  int count;
+  long long total;
+  ReduceItem it[kMaxItems];
+};
+
+// Neumaier's compensated sum: s + c carries the exact sum of the terms to a
+// few ulps for the handful of terms summed here, in round-to-nearest FP32
+// arithmetic (the FP64 units of this GPU are too slow to use at memory rate).
+struct Csum {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float y) {
+    const float t = s + y;
+    c += fabsf(s) >= fabsf(y) ? (s - t) + y : (y - t) + s;
+    s = t;
+  }
+  __device__ __forceinline__ float value() const { return s + c; }
+};
+
+// out[q][i] = alpha * sum_g part[q*groups + g][i], compensated; the flat index
+// space counts groups of four elements when N % 4 == 0 (16-byte accesses)
+__global__ void reduce_parts_kernel(const __grid_constant__ ReduceList L) {
+  int item = 0;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < L.total;
        idx += (long long)gridDim.x * blockDim.x) {
-    const long long q = idx / N, i = idx - q * N;
-    const float* src = part + q * groups * N + i;
-    double acc = 0.0;
-    for (int g = 0; g < groups; ++g) acc += (double)src[g * N];
-    out[idx] = (float)(alpha * acc);
+    while (item + 1 < L.count && idx >= L.it[item + 1].begin) ++item;
+    const ReduceItem& R = L.it[item];
+    const long long e = idx - R.begin;
+    if (R.vec) {
+      const long long nq = R.N >> 2;
+      const long long q = e / nq, i4 = e - q * nq;
+      const float4* src = reinterpret_cast<const float4*>(R.part + q * R.groups * R.N) + i4;
+      Csum a[4];
+      for (int g = 0; g < R.groups; ++g) {
+        const float4 v = src[g * nq];
+        a[0].add(v.x);
+        a[1].add(v.y);
+        a[2].add(v.z);
+        a[3].add(v.w);
+      }
+      reinterpret_cast<float4*>(R.out + q * R.N)[i4] =
+          make_float4(R.alpha * a[0].value(), R.alpha * a[1].value(), R.alpha * a[2].value(),
+                      R.alpha * a[3].value());
+    } else {
+      const long long q = e / R.N, i = e - q * R.N;
+      const float* src = R.part + q * R.groups * R.N + i;
+      Csum a;
+      for (int g = 0; g < R.groups; ++g) a.add(src[g * R.N]);
+      R.out[e] = R.alpha * a.value();
+    }
   }
 }
 
@@ -685,6 +810,7 @@ static void set_stage(TcGroup& G, const CUtensorMap& ahi, const CUtensorMap& alo
   G.mode = mode;
   G.alpha = alpha;
   G.m_tiles = (rows + kBM - 1) / kBM;
+  G.rgroup = kRowGroup < G.m_tiles ? kRowGroup : G.m_tiles;
   G.n_tiles = (n_a + bn - 1) / bn;
 }
 
@@ -1027,22 +1153,59 @@ static demag_status run_program(demag_plan* P, TcState* S, int prog, cudaStream_
 }
 
 template <class F>
-static demag_status split_input(demag_plan* P, TcState* S, const float* x, int fields, cudaStream_t st) {
-  const long long nrows = (long long)fields * P->n[2] * P->n[1];
-  DEMAG_LAUNCH(P, kFamSplit, st,
-               split_rows_kernel<F><<<grid_blocks(nrows * P->n[0]), 256, 0, st>>>(
-                   x, nrows, P->n[0], S->ld[0], (typename F::T*)S->X[0], (typename F::T*)S->X[1]));
+static demag_status launch_split(demag_plan* P, const SplitList& L, cudaStream_t st) {
+  DEMAG_LAUNCH(P, kFamSplit, st, split_rows_kernel<F><<<grid_blocks(L.total), 256, 0, st>>>(L));
   DEMAG_LAUNCHED(P, "split_rows_kernel");
   return DEMAG_OK;
 }
 
-static demag_status reduce_parts(demag_plan* P, TcState* S, int groups, int nout, float alpha, float* out,
-                                 cudaStream_t st) {
-  const long long N = (long long)P->n[0] * P->n[1] * P->n[2];
-  DEMAG_LAUNCH(P, kFamMisc, st,
-               reduce_parts_kernel<<<grid_blocks(nout * N), 256, 0, st>>>(S->part, groups, N, nout, alpha, out));
+static void add_split(SplitList& L, demag_plan* P, TcState* S, const float* x, int fields) {
+  SplitItem& it = L.it[L.count++];
+  it.x = x;
+  it.hi = S->X[0];
+  it.lo = S->X[1];
+  it.begin = L.total;
+  it.n = P->n[0];
+  it.ld = S->ld[0];
+  it.vec = (P->n[0] % 4 == 0) && (reinterpret_cast<uintptr_t>(x) % 16 == 0);
+  L.total += (long long)fields * P->n[2] * P->n[1] * ((P->n[0] + 3) / 4);
+}
+
+template <class F>
+static demag_status split_input(demag_plan* P, TcState* S, const float* x, int fields, cudaStream_t st) {
+  SplitList L;
+  L.count = 0;
+  L.total = 0;
+  add_split(L, P, S, x, fields);
+  return launch_split<F>(P, L, st);
+}
+
+static demag_status launch_reduce(demag_plan* P, const ReduceList& L, cudaStream_t st) {
+  DEMAG_LAUNCH(P, kFamMisc, st, reduce_parts_kernel<<<grid_blocks(L.total), 256, 0, st>>>(L));
   DEMAG_LAUNCHED(P, "reduce_parts_kernel");
   return DEMAG_OK;
+}
+
+static void add_reduce(ReduceList& L, demag_plan* P, TcState* S, int groups, int nout, float alpha, float* out) {
+  const long long N = (long long)P->n[0] * P->n[1] * P->n[2];
+  ReduceItem& it = L.it[L.count++];
+  it.part = S->part;
+  it.out = out;
+  it.begin = L.total;
+  it.N = N;
+  it.groups = groups;
+  it.alpha = alpha;
+  it.vec = (N % 4 == 0) && (reinterpret_cast<uintptr_t>(out) % 16 == 0);
+  L.total += it.vec ? nout * (N >> 2) : nout * N;
+}
+
+static demag_status reduce_parts(demag_plan* P, TcState* S, int groups, int nout, float alpha, float* out,
+                                 cudaStream_t st) {
+  ReduceList L;
+  L.count = 0;
+  L.total = 0;
+  add_reduce(L, P, S, groups, nout, alpha, out);
+  return launch_reduce(P, L, st);
 }
 
 template <class F>
@@ -1129,8 +1292,13 @@ static demag_status batched_chain(const TcBatch* B, const float* const* m, float
   const int count = (int)B->plans.size();
   demag_plan* P0 = B->plans[0];
   TcState* S0 = state(P0, prec);
-  for (int i = 0; i < count; ++i) {
-    demag_status s = split_input<F>(B->plans[i], state(B->plans[i], prec), m[i], 3, st);
+  // one split launch per kMaxItems grids
+  for (int i0 = 0; i0 < count; i0 += kMaxItems) {
+    SplitList L;
+    L.count = 0;
+    L.total = 0;
+    for (int i = i0; i < count && i < i0 + kMaxItems; ++i) add_split(L, B->plans[i], state(B->plans[i], prec), m[i], 3);
+    demag_status s = launch_split<F>(P0, L, st);
     if (s != DEMAG_OK) return s;
   }
   for (int st3 = 0; st3 < 3; ++st3) {
@@ -1138,9 +1306,15 @@ static demag_status batched_chain(const TcBatch* B, const float* const* m, float
                                       count, B->total[st3], S0->counter, S0->status, st);
     if (s != DEMAG_OK) return s;
   }
-  for (int i = 0; i < count; ++i) {
-    TcState* S = state(B->plans[i], prec);
-    demag_status s = reduce_parts(B->plans[i], S, S->groups_fwd, 1, 1.f, phi[i], st);
+  for (int i0 = 0; i0 < count; i0 += kMaxItems) {
+    ReduceList L;
+    L.count = 0;
+    L.total = 0;
+    for (int i = i0; i < count && i < i0 + kMaxItems; ++i) {
+      TcState* S = state(B->plans[i], prec);
+      add_reduce(L, B->plans[i], S, S->groups_fwd, 1, 1.f, phi[i]);
+    }
+    demag_status s = launch_reduce(P0, L, st);
     if (s != DEMAG_OK) return s;
   }
   return DEMAG_OK;

@@ -457,6 +457,20 @@ extern "C" demag_status demag_profile(demag_plan* plan, int enable) {
   return DEMAG_OK;
 }
 
+extern "C" long long demag_profile_count(const demag_plan* plan) { return plan ? (long long)plan->prof.size() : 0; }
+
+extern "C" demag_status demag_profile_launch(demag_plan* plan, long long i, int* family, double* ms) {
+  if (!plan || !family || !ms || i < 0 || i >= (long long)plan->prof.size())
+    return set_error(plan, DEMAG_EINVAL, "demag_profile_launch: no record %lld", i);
+  auto& r = plan->prof[(size_t)i];
+  DEMAG_CUDA(plan, cudaEventSynchronize(r.b));
+  float t = 0.f;
+  DEMAG_CUDA(plan, cudaEventElapsedTime(&t, r.a, r.b));
+  *family = r.family;
+  *ms = t;
+  return DEMAG_OK;
+}
+
 extern "C" demag_status demag_profile_read(demag_plan* plan, int family, double* total_ms, long long* launches) {
   if (!plan || !total_ms || !launches) return set_error(plan, DEMAG_EINVAL, "demag_profile_read: NULL argument");
   double t = 0.0;

@@ -60,6 +60,8 @@ struct ToepLaunch {
 };
 
 __device__ __forceinline__ int pad16(int i) { return i + (i >> 4); }
+// pad16(i + r * S) = pad16(i) + r * (S + S / 16) when S is a multiple of 16
+template <int S> struct PadStride { static constexpr int value = S + S / 16; };
 
 template <int LOGN> struct ToepCfg {
   static constexpr int N = 1 << LOGN;
@@ -130,7 +132,7 @@ __device__ __forceinline__ void mid_pass(float2* buf, int Ns, int lt, const TwSm
       powers<R>(w, pw);
 #pragma unroll
       for (int r = 0; r < R; ++r) {
-        const float2 x = buf[pad16(j + r * items)];
+        const float2 x = (items % 16 == 0) ? buf[pad16(j) + r * PadStride<items>::value] : buf[pad16(j + r * items)];
         v[it][r] = r > 0 ? cmul(x, pw[r]) : x;
       }
       dft_reg<R, true>(v[it]);
@@ -143,8 +145,14 @@ __device__ __forceinline__ void mid_pass(float2* buf, int Ns, int lt, const TwSm
     if (items % TG == 0 || j < items) {
       const int k = j % Ns;
       const int base = (j / Ns) * Ns * R + k;
+      if (Ns % 16 == 0) {
+        const int b0 = pad16(base), step = Ns + (Ns >> 4);
 #pragma unroll
-      for (int r = 0; r < R; ++r) buf[pad16(base + r * Ns)] = v[it][r];
+        for (int r = 0; r < R; ++r) buf[b0 + r * step] = v[it][r];
+      } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) buf[pad16(base + r * Ns)] = v[it][r];
+      }
     }
   }
   __syncthreads();
@@ -286,7 +294,8 @@ __global__ void __launch_bounds__(256, ToepCfg<LOGN>::minblocks)
           powers<16>(w, pw);
 #pragma unroll
           for (int r = 0; r < 16; ++r) {
-            const float2 x = buf[pad16(j + r * items)];
+            const float2 x =
+                (items % 16 == 0) ? buf[pad16(j) + r * PadStride<items>::value] : buf[pad16(j + r * items)];
             v[r] = r > 0 ? cmul(x, pw[r]) : x;
           }
           dft_reg<16, true>(v);

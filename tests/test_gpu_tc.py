@@ -147,3 +147,20 @@ def test_graph_replay_equals_batched_call(D, prec):
     with pytest.raises(D.DemagError):
         D.demag_graph_create_batched([plans[0], plans[0]], [ms[0], ms[0]], [outs[0], outs[0]], prec)
     G.close()
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32x3"])
+def test_unaligned_pointers_take_the_scalar_path(D, prec):
+    """m and phi that start 4 bytes past a 16-byte boundary give the same
+    result as aligned buffers (the vectorised split and reduce are skipped)."""
+    n, h, R = (32, 24, 40), (1 / 40,) * 3, 21
+    m = dev(synth.random_unit_m(n, 17))
+    P = D.demag_build_factors(n, h, R)
+    ref = torch.empty(n[2], n[1], n[0], device="cuda")
+    D.demag_apply_full(P, m, ref, prec)
+    m_buf = torch.empty(m.numel() + 1, device="cuda")
+    m_buf[1:].copy_(m.reshape(-1))
+    phi_buf = torch.full((ref.numel() + 1,), float("nan"), device="cuda")
+    D.demag_apply_full(P, m_buf[1:].data_ptr(), phi_buf[1:].data_ptr(), prec)
+    torch.cuda.synchronize()
+    assert torch.equal(phi_buf[1:].reshape(ref.shape), ref)
