@@ -27,6 +27,8 @@ from __future__ import annotations
 import numpy as np
 
 from .full import terms, factor_kind, C_POT
+from .generators import gen_E, gen_F, scaled_spacing
+from .quadrature import sinc_nodes
 
 
 def _split_blocks(flat, n, ranks):
@@ -61,6 +63,31 @@ def apply_cp(lam, U, n, h, R: int, c0: float = 2.15):
             for p in range(3):
                 outU[p][k, q] = (T[(p, factor_kind(p, q))] @ V[q][p].T).T
     return w, outU
+
+
+def apply_cp_entries(lam, U, n, h, R: int, p: int, idx, c0: float = 2.15) -> np.ndarray:
+    """Sampled entries outU[p][k, q, l, i] of apply_cp for i in idx (all k, q, l).
+
+    Each needed row of the Toeplitz factor is read off its generator,
+    T[i, j] = gen[i - j + n_p - 1] (Sec. 4.2), so long axes (n_p = 8192)
+    are checked without forming n_p x n_p matrices.  Returns [M][3][r][len(idx)].
+    """
+    n = tuple(int(v) for v in n)
+    lam = np.asarray(lam, dtype=np.float64)
+    r = lam.shape[1]
+    V = _split_blocks(U, n, (r, r, r))
+    M = (R - 1) // 2
+    _, hh = scaled_spacing(n, h)
+    _, _, tau, _ = sinc_nodes(M, c0)
+    idx = np.asarray(idx, dtype=np.int64)
+    j = np.arange(n[p])
+    out = np.zeros((M, 3, r, len(idx)))
+    for k in range(M):
+        gens = {"E": gen_E(tau[k], hh[p], n[p]), "F": gen_F(tau[k], hh[p], n[p])}
+        for q in range(3):
+            rows = gens[factor_kind(p, q)][(idx[:, None] - j[None, :]) + n[p] - 1]
+            out[k, q] = (rows @ V[q][p].T).T
+    return out
 
 
 def cp_to_full(lam, factors) -> np.ndarray:

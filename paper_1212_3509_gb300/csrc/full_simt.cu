@@ -22,7 +22,7 @@
 namespace demag {
 
 constexpr int kMaxJobs = 64;
-constexpr int kMaxPairs = 2 * kMaxTerms + 8;
+constexpr int kMaxPairs = 3 * kMaxTerms + 8;  // the adjoint node sum: 3 jobs of M pairs
 
 struct GemmJob {
   int rows, ncol, K;
@@ -142,9 +142,13 @@ __global__ void __launch_bounds__(256) gemm_tn_kernel(const __grid_constant__ Ge
 
 class BatchBuilder {
  public:
-  BatchBuilder() { b_.njobs = 0; b_.total_tiles = 0; npairs_ = 0; }
+  BatchBuilder() { b_.njobs = 0; b_.total_tiles = 0; npairs_ = 0; overflow_ = false; }
   void add(int rows, int ncol, int K, int lda, int ldb, int ldc, void* C, float alpha,
            const std::vector<std::pair<const void*, const void*>>& pairs, int bm) {
+    if (b_.njobs >= kMaxJobs || npairs_ + (int)pairs.size() > kMaxPairs) {
+      overflow_ = true;  // reported by launch_batch; nothing is written past the tables
+      return;
+    }
     GemmJob& J = b_.jobs[b_.njobs++];
     J.rows = rows; J.ncol = ncol; J.K = K;
     J.lda = lda; J.ldb = ldb; J.ldc = ldc;
@@ -163,14 +167,18 @@ class BatchBuilder {
     b_.total_tiles += J.tiles_m * J.tiles_n;
   }
   const GemmBatch& get() const { return b_; }
+  bool overflow() const { return overflow_; }
 
  private:
   GemmBatch b_;
   int npairs_;
+  bool overflow_;
 };
 
 template <typename T>
-static cudaError_t launch_batch(demag_plan* P, const GemmBatch& b, cudaStream_t st) {
+static cudaError_t launch_batch(demag_plan* P, const BatchBuilder& bb, cudaStream_t st) {
+  if (bb.overflow()) return cudaErrorInvalidValue;  // a job table exceeded its fixed capacity
+  const GemmBatch& b = bb.get();
   if (b.total_tiles == 0) return cudaSuccess;
   DEMAG_LAUNCH(P, kFamGemmSimt, st, gemm_tn_kernel<T><<<b.total_tiles, 256, 0, st>>>(b));
   return cudaGetLastError();
@@ -275,14 +283,14 @@ static demag_status simt_forward(demag_plan* P, const T* m, T* phi, const T* Tm,
       const T* B = factor(P, Tm, k, q == 0 ? 1 : 0, 0);
       b1.add(n3 * n2, n1, n1, n1, n1, n3 * n2, Y + q * N, 1.f, {{m + q * N, B}}, BM);
     }
-    cudaError_t e = launch_batch<T>(P, b1.get(), st);
+    cudaError_t e = launch_batch<T>(P, b1, st);
     if (e != cudaSuccess) return cuda_error(P, e, "gemm_tn_kernel (mode 1)");
     BatchBuilder b2;
     const T* E2 = factor(P, Tm, k, 0, 1);
     const T* F2 = factor(P, Tm, k, 1, 1);
     b2.add(n1 * n3, n2, n2, n2, n2, n1 * n3, UV + (2 * k) * N, 1.f, {{Y, E2}, {Y + N, F2}}, BM);
     b2.add(n1 * n3, n2, n2, n2, n2, n1 * n3, UV + (2 * k + 1) * N, 1.f, {{Y + 2 * N, E2}}, BM);
-    e = launch_batch<T>(P, b2.get(), st);
+    e = launch_batch<T>(P, b2, st);
     if (e != cudaSuccess) return cuda_error(P, e, "gemm_tn_kernel (mode 2)");
   }
   BatchBuilder b3;
@@ -292,7 +300,7 @@ static demag_status simt_forward(demag_plan* P, const T* m, T* phi, const T* Tm,
     pairs.push_back({UV + (2 * k + 1) * N, factor(P, Tm, k, 1, 2)});
   }
   b3.add(n2 * n1, n3, n3, n3, n3, n2 * n1, phi, 1.f, pairs, BM);
-  cudaError_t e = launch_batch<T>(P, b3.get(), st);
+  cudaError_t e = launch_batch<T>(P, b3, st);
   if (e != cudaSuccess) return cuda_error(P, e, "gemm_tn_kernel (mode 3)");
   return DEMAG_OK;
 }
@@ -310,7 +318,7 @@ static demag_status simt_adjoint(demag_plan* P, const T* y, T* g, const T* Tm, T
     BatchBuilder b1;
     b1.add(n3 * n2, n1, n1, n1, n1, n3 * n2, Y, 1.f, {{y, factor(P, Tm, k, 1, 0)}}, BM);
     b1.add(n3 * n2, n1, n1, n1, n1, n3 * n2, Y + N, 1.f, {{y, factor(P, Tm, k, 0, 0)}}, BM);
-    cudaError_t e = launch_batch<T>(P, b1.get(), st);
+    cudaError_t e = launch_batch<T>(P, b1, st);
     if (e != cudaSuccess) return cuda_error(P, e, "gemm_tn_kernel (adjoint mode 1)");
     BatchBuilder b2;
     const T* E2 = factor(P, Tm, k, 0, 1);
@@ -318,7 +326,7 @@ static demag_status simt_adjoint(demag_plan* P, const T* y, T* g, const T* Tm, T
     b2.add(n1 * n3, n2, n2, n2, n2, n1 * n3, Z + (3 * k) * N, 1.f, {{Y, E2}}, BM);
     b2.add(n1 * n3, n2, n2, n2, n2, n1 * n3, Z + (3 * k + 1) * N, 1.f, {{Y + N, F2}}, BM);
     b2.add(n1 * n3, n2, n2, n2, n2, n1 * n3, Z + (3 * k + 2) * N, 1.f, {{Y + N, E2}}, BM);
-    e = launch_batch<T>(P, b2.get(), st);
+    e = launch_batch<T>(P, b2, st);
     if (e != cudaSuccess) return cuda_error(P, e, "gemm_tn_kernel (adjoint mode 2)");
   }
   BatchBuilder b3;
@@ -327,7 +335,7 @@ static demag_status simt_adjoint(demag_plan* P, const T* y, T* g, const T* Tm, T
     for (int k = 0; k < M; ++k) pairs.push_back({Z + (3 * k + q) * N, factor(P, Tm, k, q == 2 ? 1 : 0, 2)});
     b3.add(n2 * n1, n3, n3, n3, n3, n2 * n1, g + q * N, -1.f, pairs, BM);
   }
-  cudaError_t e = launch_batch<T>(P, b3.get(), st);
+  cudaError_t e = launch_batch<T>(P, b3, st);
   if (e != cudaSuccess) return cuda_error(P, e, "gemm_tn_kernel (adjoint mode 3)");
   return DEMAG_OK;
 }

@@ -28,6 +28,18 @@ def test_cp_matches_full():
     assert S.cp_inner(w.ravel(), f, w.ravel(), f) == pytest.approx((got * got).sum(), rel=1e-11)
 
 
+def test_cp_entries_equal_apply_cp():
+    # sampled entries read off generator rows equal the dense-matrix products
+    r = 2
+    n = (12, 31, 9)
+    lam, U = synth.cp_inputs(n, r, 1219)
+    w, outU = S.apply_cp(lam, U, n, H, R)
+    for p, idx in ((0, [0, 5, 11]), (1, [0, 17, 30]), (2, [8])):
+        got = S.apply_cp_entries(lam, U, n, H, R, p, idx)
+        ref = outU[p][..., idx]
+        assert np.max(np.abs(got - ref)) <= 1e-13 * np.max(np.abs(ref))
+
+
 def test_tucker_matches_full():
     ranks = (3, 2, 4)
     core, V = synth.tucker_inputs(N, ranks, 1216)
