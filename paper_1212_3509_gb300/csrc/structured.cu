@@ -73,9 +73,9 @@ template <int LOGN> struct ToepCfg {
   static constexpr int T1 = L / T0;                // coarse twiddle table
   static constexpr int R1 = (LOGN % 4) ? (1 << (LOGN % 4)) : (LOGN >= 4 ? 16 : 1);
   static constexpr int NPASS = LOGN / 4 + ((LOGN % 4) ? 1 : 0);
-  // per group: P, Q (N each) and one padded work buffer
-  static constexpr size_t group_floats2 = 2 * (size_t)N + NP;
-  static constexpr size_t smem = ((size_t)T0 + T1 + G * group_floats2) * sizeof(float2);
+  // per group: P and Q interleaved (N float4) and one padded work buffer (NP float2);
+  // layout [G][N] float4 | T0 | T1 | [G][NP] float2
+  static constexpr size_t smem = (size_t)G * N * sizeof(float4) + ((size_t)T0 + T1 + (size_t)G * NP) * sizeof(float2);
   static constexpr int minblocks = smem * 2 <= 220 * 1024 ? 2 : 1;
 };
 
@@ -112,6 +112,29 @@ __device__ __forceinline__ void powers(float2 w, float2 (&pw)[R]) {
 #pragma unroll
     for (int r = 9; r < R; ++r) pw[r] = cmul(pw[8], pw[r - 8]);
   }
+}
+
+// The first 8 outputs of an inverse 16-point DFT (the kept half of the last
+// pass): two 8-point DFTs of the even and odd inputs and the "+" half of the
+// final butterflies.
+template <int K>
+__device__ __forceinline__ void combine_half16(float2 (&v)[16], float2 (&e)[8], float2 (&o)[8]) {
+  if constexpr (K < 8) {
+    v[K] = cadd(e[K], rot<16, K, true>(o[K]));
+    combine_half16<K + 1>(v, e, o);
+  }
+}
+
+__device__ __forceinline__ void idft16_first_half(float2 (&v)[16]) {
+  float2 e[8], o[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    e[i] = v[2 * i];
+    o[i] = v[2 * i + 1];
+  }
+  dft_reg<8, true>(e);
+  dft_reg<8, true>(o);
+  combine_half16<0>(v, e, o);
 }
 
 // In-place middle pass of radix R on the padded buffer (inverse direction):
@@ -163,13 +186,12 @@ __global__ void __launch_bounds__(256, ToepCfg<LOGN>::minblocks)
     toeplitz_fft_kernel(const __grid_constant__ ToepLaunch a) {
   using Cfg = ToepCfg<LOGN>;
   constexpr int N = Cfg::N, TG = Cfg::TG, R1 = Cfg::R1, NPASS = Cfg::NPASS;
-  extern __shared__ float2 smem_c[];
-  float2* t0 = smem_c;
-  float2* t1 = t0 + Cfg::T0;
+  extern __shared__ float4 smem_c[];
   const int g = threadIdx.x / TG, lt = threadIdx.x % TG;
-  float2* Pm = t1 + Cfg::T1 + (size_t)g * Cfg::group_floats2;
-  float2* Qm = Pm + N;
-  float2* buf = Qm + N;
+  float4* PQ = smem_c + (size_t)g * N;  // (P_f, Q_f) of this group's column
+  float2* t0 = reinterpret_cast<float2*>(smem_c + (size_t)Cfg::G * N);
+  float2* t1 = t0 + Cfg::T0;
+  float2* buf = t1 + Cfg::T1 + (size_t)g * Cfg::NP;
   int slot = 0;
   while (slot + 1 < a.naxes && (int)blockIdx.x >= a.bx0[slot + 1]) ++slot;
   const ToepAxis& A = a.ax[slot];
@@ -218,8 +240,8 @@ __global__ void __launch_bounds__(256, ToepCfg<LOGN>::minblocks)
     const float2 Xc = make_float2(ex + wy, ey - wx);
     // 1 + i conj(w) and 1 - i conj(w)
     const float2 up = make_float2(1.f + w.y, w.x), um = make_float2(1.f - w.y, -w.x);
-    Pm[f] = cmul(Xf, up);
-    Qm[f] = cmul(make_float2(Xc.x, -Xc.y), um);
+    const float2 Pf = cmul(Xf, up), Qf = cmul(make_float2(Xc.x, -Xc.y), um);
+    PQ[f] = make_float4(Pf.x, Pf.y, Qf.x, Qf.y);
   }
   __syncthreads();
 
@@ -232,6 +254,16 @@ __global__ void __launch_bounds__(256, ToepCfg<LOGN>::minblocks)
   // paired stores need an even length and an 8-byte aligned column start
   // (every (k, q) offset is a multiple of n, so one check per column)
   const bool vec = ((n & 1) == 0) && ((reinterpret_cast<uintptr_t>(outbase) & 7) == 0);
+  // The last pass's twiddles depend only on the thread's item: with one item
+  // per thread they are computed once here and reused for every node.
+  constexpr int items_last = N / 16;
+  constexpr bool keep_tw = NPASS > 1 && items_last == TG;
+  float2 pw_last[keep_tw ? 16 : 1];
+  if constexpr (keep_tw) {
+    float2 w = tw.L(2 * lt);  // W_N^j with j = lt, inverse: conjugate
+    w.y = -w.y;
+    powers<16>(w, pw_last);
+  }
   for (int k = k0; k < k1; ++k) {
     const float2* sp = a.sympair + ((long)(k * 2 + type) * 3 + axis) * a.pairstride;
     // 3. first pass in registers on the bins j + r N/R1 of item j
@@ -246,11 +278,11 @@ __global__ void __launch_bounds__(256, ToepCfg<LOGN>::minblocks)
         for (int r = 0; r < R1; ++r) {
           const int f = j + r * items1;
           const float2 s2 = __ldg(sp + f);
-          const float2 P = Pm[f], Q = Qm[f];
+          const float4 pq = PQ[f];  // (P, Q)
           // E: s_f P + s_c Q ;  F: i (s_f P - s_c Q)
           const float sc = fsign * s2.y;
-          const float zx = fmaf(s2.x, P.x, sc * Q.x);
-          const float zy = fmaf(s2.x, P.y, sc * Q.y);
+          const float zx = fmaf(s2.x, pq.x, sc * pq.z);
+          const float zy = fmaf(s2.x, pq.y, sc * pq.w);
           v[r] = type ? make_float2(-zy, zx) : make_float2(zx, zy);
         }
         dft_reg<R1, true>(v);
@@ -288,17 +320,22 @@ __global__ void __launch_bounds__(256, ToepCfg<LOGN>::minblocks)
         const int j = lt + it * TG;
         if (items % TG == 0 || j < items) {
           float2 v[16];
-          float2 w = tw.L(2 * j);  // W_N^j (Ns = N/16, so k = j), inverse: conjugate
-          w.y = -w.y;
           float2 pw[16];
-          powers<16>(w, pw);
+          if constexpr (keep_tw) {
+#pragma unroll
+            for (int r = 0; r < 16; ++r) pw[r] = pw_last[r];
+          } else {
+            float2 w = tw.L(2 * j);  // W_N^j (Ns = N/16, so k = j), inverse: conjugate
+            w.y = -w.y;
+            powers<16>(w, pw);
+          }
 #pragma unroll
           for (int r = 0; r < 16; ++r) {
             const float2 x =
                 (items % 16 == 0) ? buf[pad16(j) + r * PadStride<items>::value] : buf[pad16(j + r * items)];
             v[r] = r > 0 ? cmul(x, pw[r]) : x;
           }
-          dft_reg<16, true>(v);
+          idft16_first_half(v);
           if (active) {
             float* o = outbase + (long)(k * 3 + q) * rcols * n;
 #pragma unroll
