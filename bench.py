@@ -32,6 +32,13 @@ sys.path.insert(0, ROOT)
 
 METRIC = "demag potential apps/s at 256³ full & n=4096 CP; rel L2 err vs FP64 oracle"
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+# DRAM bytes (read + write) from ncu captures of the kernels as they stand, scaled
+# to the bench workloads by the units processed (the captures are smaller cases;
+# traffic grows in proportion): the three tcgen05 mode-product stages at 192^3
+# BF16x3 (5.80 GB) scaled to one 256^3 application; the Toeplitz FFT launch for
+# a CP batch of 32 (549.8 MB) scaled to a batch of 256.
+NCU_TRAFFIC_FULL256_BF16X3 = 13.81e9
+NCU_TRAFFIC_CP4096_PER_APP = 549.8e6 / 32
 # FP32 CUDA-core peak of a GB300: 152 SMs x 128 FP32 lanes x 2 flops (FMA) x 2.07 GHz
 FP32_SIMT_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 
@@ -368,7 +375,11 @@ def run_ours(args, world, rank, local):
                    "l2": "inputs larger than L2 (m = 201 MB at 256^3; CP batch outputs 4.5 GB)"},
         "roofline": {"kernel": "mode-product GEMM (" + fam + "), all stages of one application",
                      "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-                     "frac": achieved / peak, "traffic": None, "peak_source": peak_note,
+                     "frac": achieved / peak,
+                     "traffic": (NCU_TRAFFIC_FULL256_BF16X3 if (form == "bf16x3" and args.n == 256) else None),
+                     "traffic_note": "DRAM bytes per application: ncu capture of the three stages at 192^3 "
+                                     "scaled by cells (profiles/tc_gemm_bf16x3_full192.md)",
+                     "peak_source": peak_note,
                      "algorithmic_bytes_per_app": gemm_bytes_app,
                      "launches_per_app": gemm_n / args.steps, "kernel_ms_per_app": gemm_ms_app,
                      "split_ms_per_app": split_ms / args.steps,
@@ -383,7 +394,10 @@ def run_ours(args, world, rank, local):
                "batch": B,
                "roofline": {"kernel": "toeplitz_fft_kernel", "bound": "alu", "achieved": fft_tflops,
                             "peak": FP32_SIMT_PEAK_TFLOPS, "unit": "TFLOP/s",
-                            "frac": fft_tflops / FP32_SIMT_PEAK_TFLOPS, "traffic": None,
+                            "frac": fft_tflops / FP32_SIMT_PEAK_TFLOPS,
+                            "traffic": (NCU_TRAFFIC_CP4096_PER_APP * B if ncp == 4096 else None),
+                            "traffic_note": "DRAM bytes per batch launch: ncu capture of a batch of 32 scaled "
+                                            "to the batch (profiles/toeplitz_fft_cp4096_b32.md)",
                             "algorithmic_flops_per_app": fft_flops_app,
                             "hbm_achieved_gbs": fft_gbs, "hbm_peak_gbs": hbm, "hbm_frac": fft_gbs / hbm,
                             "algorithmic_bytes_per_app": bytes_app, "launches_per_batch": fft_n / args.steps,
