@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--cp-n", type=int, default=4096)
     ap.add_argument("--cp-batch", type=int, default=256)
     ap.add_argument("--batch-grids", type=int, default=64, help="uneven full-format batch size (0: skip)")
+    ap.add_argument("--c4-batch", type=int, default=128, help="Tucker / TT n=1024 batch (0: skip)")
     ap.add_argument("--no-oracle", action="store_true", help="skip the oracle error check and CPU baseline")
     return ap.parse_args()
 
@@ -349,6 +350,11 @@ def run_ours(args, world, rank, local):
     fft_flops_app = (9 * r + Mc * 9 * r) * 2.5 * Lc * math.log2(Lc) + Mc * 9 * r * 2 * (Lc // 2 + 1)
     fft_tflops = B * fft_flops_app / (fft_batch_ms * 1e-3) / 1e12
 
+    # ---------------- Tucker and TT, n = 1024, ranks 8, R = 61, batched, CUDA graph
+    c4 = None
+    if args.c4_batch > 0:
+        c4 = run_c4(args, D, world, local, stream, peaks)
+
     # ---------------- uneven batch: 64 grids of mixed shape, BF16x3, CUDA graph
     batch = None
     if args.batch_grids > 0:
@@ -450,6 +456,25 @@ def run_ours(args, world, rank, local):
         result["cp"]["rel_l2"] = float(np.linalg.norm(got_cp - ref_cp) / np.linalg.norm(ref_cp))
         result["cpu_baseline"] = cpu_baseline(n3, h, R, m_host, budget_s=20.0)
     result["forms_full"] = forms
+    if c4 is not None:
+        if not args.no_oracle and rank == 0:
+            from oracle import structured as ost
+            n3, h, R = c4.pop("_cfg")
+            core, Vh = c4.pop("_tucker_in")
+            rw, rV = ost.apply_tucker(core, Vh, n3, (8, 8, 8), h, R)
+            got = c4.pop("_tucker_out").cpu().numpy()
+            ref = np.concatenate([rV[p].ravel() for p in range(3)])
+            c4["tucker"]["rel_l2"] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+            G1, G2, G3 = c4.pop("_tt_in")
+            rw, r1, r2, r3 = ost.apply_tt(G1, G2, G3, n3, (8, 8), h, R)
+            outs = c4.pop("_tt_out")
+            num = sum(float(np.linalg.norm(o.cpu().numpy() - rr.ravel()) ** 2) for o, rr in zip(outs, (r1, r2, r3)))
+            den = sum(float(np.linalg.norm(rr) ** 2) for rr in (r1, r2, r3))
+            c4["tt"]["rel_l2"] = (num / den) ** 0.5
+            c4["rel_l2_sample"] = "the first batch item of each format in full vs the FP64 oracle"
+        for k in [k for k in c4 if k.startswith("_")]:
+            del c4[k]
+        result["tucker_tt"] = c4
     if batch is not None:
         if not args.no_oracle and rank == 0:
             from oracle import full as ofull
@@ -467,6 +492,76 @@ def run_ours(args, world, rank, local):
             del batch[k]
         result["uneven_batch"] = batch
     print(json.dumps(result), flush=True)
+
+
+def run_c4(args, D, world, local, stream, peaks):
+    """Tucker (multilinear ranks 8, 8, 8) and TT (ranks 8, 8) inputs on n = 1024
+    per axis, R = 61: batched calls (one Toeplitz-FFT launch for all axes,
+    nodes, components and items) captured in a CUDA graph and replayed."""
+    import torch
+    import synth
+    n, B = 1024, args.c4_batch
+    n3, h, R = (n,) * 3, (1.0 / n,) * 3, 61
+    P = D.demag_build_factors(n3, h, R)
+    M = P.M
+    rt, rr = (8, 8, 8), (8, 8)
+    tot = sum(rt)
+    tucker_in = synth.tucker_inputs(n3, rt, 1500)
+    V = torch.cat([torch.from_numpy(synth.tucker_inputs(n3, rt, 1500 + b)[1].ravel()) for b in range(B)]).cuda()
+    tw = torch.empty(B * M * 3, device="cuda")
+    tV = torch.empty(B * M * 3 * tot * n, device="cuda")
+    tt_in = synth.tt_inputs(n3, rr, 1600)
+    tts = [tt_in] + [synth.tt_inputs(n3, rr, 1600 + b) for b in range(1, B)]
+    G = [torch.cat([torch.from_numpy(t[i].ravel()) for t in tts]).cuda() for i in range(3)]
+    sizes = [8 * n, 64 * n, 8 * n]
+    ww = torch.empty(B * M * 3, device="cuda")
+    tO = [torch.empty(B * M * 3 * sz, device="cuda") for sz in sizes]
+    hbm = peaks.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"])
+    out = {"n": n, "R": R, "batch": B, "_cfg": (n3, h, R)}
+    sym_bytes = 3 * 4.0 * M * 2 * (n + 1)
+    legs = {
+        "tucker": (lambda st: D.demag_apply_tucker_batched(P, B, rt, V, tw, tV, st),
+                   4.0 * (3 * tot * n) + 4.0 * (M * 3 * tot * n + M * 3)),
+        "tt": (lambda st: D.demag_apply_tt_batched(P, B, rr, G[0], G[1], G[2], ww, *tO, stream=st),
+               4.0 * 3 * sum(sizes) + 4.0 * (M * 3 * sum(sizes) + M * 3)),
+    }
+    for name, (call, bytes_app) in legs.items():
+        fn = lambda: call(stream)  # noqa: E731
+        fn()  # warm-up outside the capture (plan-level setup, kernel attributes)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        side = torch.cuda.Stream()
+        side.wait_stream(stream)
+        with torch.cuda.stream(side):
+            with torch.cuda.graph(g, stream=side):
+                call(side)
+        stream.wait_stream(side)
+        replay = lambda: g.replay()  # noqa: E731
+        for _ in range(args.warmup):
+            replay()
+        torch.cuda.synchronize()
+        l0 = D.demag_launch_count(P)
+        D.demag_profile(P, True)
+        fn()
+        D.demag_profile(P, False)
+        fft_ms, fft_n = D.demag_profile_read(P, "fft")
+        launches = D.demag_launch_count(P) - l0
+        barrier(world)
+        with ClockSampler(local) as clk:
+            ms = time_region(replay, max(3, args.steps), stream)
+        ms = max_over_ranks(ms, world)
+        gbs = (B * bytes_app + sym_bytes) / (fft_ms * 1e-3) / 1e9
+        out[name] = {"value": whole_job_rate(B, ms, world), "unit": "apps/s", "ms_per_batch": ms,
+                     "kernel_ms_per_batch": fft_ms, "fft_launches_per_batch": fft_n, "gpu_launches": int(launches),
+                     "roofline": {"kernel": "toeplitz_fft_kernel", "bound": "hbm", "achieved": gbs, "peak": hbm,
+                                  "unit": "GB/s", "frac": gbs / hbm, "traffic": None,
+                                  "algorithmic_bytes_per_app": bytes_app},
+                     "clocks": clk.summary(), "timing": "CUDA-graph replays of the batched call"}
+    out["_tucker_in"] = tucker_in
+    out["_tucker_out"] = tV[:M * 3 * tot * n]
+    out["_tt_in"] = tt_in
+    out["_tt_out"] = [o[:M * 3 * sz] for o, sz in zip(tO, sizes)]
+    return out
 
 
 def run_uneven_batch(args, D, world, local, stream, form):

@@ -199,6 +199,11 @@ demag_status demag_apply_cp_batched(demag_plan* plan, int batch, int r, const fl
  * out_w: float [M][3]; out_V: three mode blocks, block p = [M][3][r_p][n_p]. */
 demag_status demag_apply_tucker(demag_plan* plan, const int r[3], const float* V,
                                 float* out_w, float* out_V, void* stream);
+/* `batch` independent Tucker inputs in one launch per FFT length: item b of
+ * V, out_w and out_V follows the single-item layout above at item strides
+ * 3 sum_p r_p n_p, 3M and 3M sum_p r_p n_p floats.  batch >= 1. */
+demag_status demag_apply_tucker_batched(demag_plan* plan, int batch, const int r[3], const float* V,
+                                        float* out_w, float* out_V, void* stream);
 
 /* Tensor train (App. C Eq. tt_3d_1, a 3D TT is the Tucker2 tensor
  * [[G2; G1, id, G3^T]], Eq. tt_3d_2) -> TT output: term (k, q) has weight
@@ -210,6 +215,13 @@ demag_status demag_apply_tucker(demag_plan* plan, const int r[3], const float* V
 demag_status demag_apply_tt(demag_plan* plan, const int r[2], const float* G1,
                             const float* G2, const float* G3, float* out_w, float* oG1,
                             float* oG2, float* oG3, void* stream);
+/* `batch` independent TT inputs in one launch per FFT length: item b of each
+ * array follows the single-item layout above, items one after another
+ * (G1 item stride 3 r1 n1, G2 3 r1 r2 n2, G3 3 r2 n3, out_w 3M, oG_p M times
+ * the input stride).  batch >= 1. */
+demag_status demag_apply_tt_batched(demag_plan* plan, int batch, const int r[2], const float* G1,
+                                    const float* G2, const float* G3, float* out_w, float* oG1,
+                                    float* oG2, float* oG3, void* stream);
 
 /* ---- stray field, energy and gradient (h_d = -grad phi, Sec. 1) ---------- */
 

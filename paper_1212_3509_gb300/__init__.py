@@ -19,7 +19,9 @@ from ._abi import (  # noqa: F401
     demag_apply_full,
     demag_apply_full_batched,
     demag_apply_tt,
+    demag_apply_tt_batched,
     demag_apply_tucker,
+    demag_apply_tucker_batched,
     demag_autotune,
     demag_autotune_count,
     demag_autotune_entry,

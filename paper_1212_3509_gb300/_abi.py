@@ -58,6 +58,8 @@ _SIGS = {
     "demag_apply_cp_batched": (_i, [_vp, _i, _i, _vp, _vp, _vp, _vp, _vp]),
     "demag_apply_tucker": (_i, [_vp, ctypes.POINTER(_i), _vp, _vp, _vp, _vp]),
     "demag_apply_tt": (_i, [_vp, ctypes.POINTER(_i), _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "demag_apply_tucker_batched": (_i, [_vp, _i, ctypes.POINTER(_i), _vp, _vp, _vp, _vp]),
+    "demag_apply_tt_batched": (_i, [_vp, _i, ctypes.POINTER(_i), _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "demag_stray_field": (_i, [_vp, _vp, _vp, _vp]),
     "demag_energy": (_i, [_vp, _vp, _vp, _vp, _i, _vp]),
     "demag_sync_status": (_i, [_vp, _vp]),
@@ -277,25 +279,36 @@ def demag_apply_cp_batched(plan: Plan, batch: int, r: int, lam, U, out_w, out_U,
 
 
 def demag_apply_tucker(plan: Plan, ranks, V, out_w, out_V, stream=None):
+    demag_apply_tucker_batched(plan, 1, ranks, V, out_w, out_V, stream)
+
+
+def demag_apply_tucker_batched(plan: Plan, batch: int, ranks, V, out_w, out_V, stream=None):
     import torch
     r = (_i * 3)(*[int(v) for v in ranks])
     tot = sum(int(ranks[p]) * plan.n[p] for p in range(3))
-    f32 = torch.float32
-    _check(lib.demag_apply_tucker(plan.ptr, r, _ptr(V, 3 * tot, f32, "V"), _ptr(out_w, plan.M * 3, f32, "out_w"),
-                                  _ptr(out_V, plan.M * 3 * tot, f32, "out_V"), _stream(stream)), plan.ptr)
+    f32, b = torch.float32, int(batch)
+    _check(lib.demag_apply_tucker_batched(plan.ptr, b, r, _ptr(V, b * 3 * tot, f32, "V"),
+                                          _ptr(out_w, b * plan.M * 3, f32, "out_w"),
+                                          _ptr(out_V, b * plan.M * 3 * tot, f32, "out_V"), _stream(stream)), plan.ptr)
 
 
 def demag_apply_tt(plan: Plan, ranks, G1, G2, G3, out_w, oG1, oG2, oG3, stream=None):
+    demag_apply_tt_batched(plan, 1, ranks, G1, G2, G3, out_w, oG1, oG2, oG3, stream)
+
+
+def demag_apply_tt_batched(plan: Plan, batch: int, ranks, G1, G2, G3, out_w, oG1, oG2, oG3, stream=None):
     import torch
     r1, r2 = int(ranks[0]), int(ranks[1])
     n1, n2, n3 = plan.n
-    M = plan.M
+    M, b = plan.M, int(batch)
     f32 = torch.float32
     r = (_i * 2)(r1, r2)
-    _check(lib.demag_apply_tt(plan.ptr, r, _ptr(G1, 3 * r1 * n1, f32, "G1"), _ptr(G2, 3 * r1 * r2 * n2, f32, "G2"),
-                              _ptr(G3, 3 * r2 * n3, f32, "G3"), _ptr(out_w, M * 3, f32, "out_w"),
-                              _ptr(oG1, M * 3 * r1 * n1, f32, "oG1"), _ptr(oG2, M * 3 * r1 * r2 * n2, f32, "oG2"),
-                              _ptr(oG3, M * 3 * r2 * n3, f32, "oG3"), _stream(stream)), plan.ptr)
+    _check(lib.demag_apply_tt_batched(plan.ptr, b, r, _ptr(G1, b * 3 * r1 * n1, f32, "G1"),
+                                      _ptr(G2, b * 3 * r1 * r2 * n2, f32, "G2"),
+                                      _ptr(G3, b * 3 * r2 * n3, f32, "G3"), _ptr(out_w, b * M * 3, f32, "out_w"),
+                                      _ptr(oG1, b * M * 3 * r1 * n1, f32, "oG1"),
+                                      _ptr(oG2, b * M * 3 * r1 * r2 * n2, f32, "oG2"),
+                                      _ptr(oG3, b * M * 3 * r2 * n3, f32, "oG3"), _stream(stream)), plan.ptr)
 
 
 def demag_stray_field(plan: Plan, phi, hd, stream=None):

@@ -30,6 +30,7 @@
 // a stage in one persistent launch.
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "internal.h"
@@ -945,10 +946,13 @@ static demag_status prepare_form(demag_plan* P, TcState* S, cudaStream_t st) {
                      (typename F::T*)S->B[p][1]));
     DEMAG_LAUNCHED(P, "tc_factor_kernel");
   }
-  static bool attr = false;
-  if (!attr) {
+  static unsigned long long attr = 0;  // devices whose kernel attribute is set
+  int dev = 0;
+  DEMAG_CUDA(P, cudaGetDevice(&dev));
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (!(attr & bit)) {
     DEMAG_CUDA(P, cudaFuncSetAttribute(tc_gemm_kernel<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
-    attr = true;
+    attr |= bit;
   }
   return DEMAG_OK;
 }
@@ -1254,12 +1258,18 @@ demag_status tc_batch_create(demag_plan* const* plans, int count, demag_precisio
   B->plans.assign(plans, plans + count);
   for (int i = 0; i < count; ++i) B->serials.push_back(plans[i]->serial);
   B->prec = (int)prec;
+  // largest grids first: the dynamic tile counter then hands out their long
+  // tile streams early and the small grids' tiles fill the tail of the launch
+  std::vector<int> order(count);
+  for (int i = 0; i < count; ++i) order[i] = i;
+  auto cells = [&](int i) { return (long long)plans[i]->n[0] * plans[i]->n[1] * plans[i]->n[2]; };
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cells(a) > cells(b); });
   std::vector<TcGroup> g(3 * (size_t)count);
   std::vector<int> t0(3 * (size_t)(count + 1));
   for (int st3 = 0; st3 < 3; ++st3) {
     int acc = 0;
     for (int i = 0; i < count; ++i) {
-      const TcState* S = state(plans[i], prec);
+      const TcState* S = state(plans[order[i]], prec);
       g[st3 * count + i] = S->host_prog[kFwd1 + st3];
       t0[st3 * (count + 1) + i] = acc;
       acc += S->host_prog[kFwd1 + st3].ntiles;

@@ -380,9 +380,18 @@ template <int LOGN>
 static cudaError_t launch_toep(demag_plan* P, const ToepLaunch& a, int gx, cudaStream_t st) {
   using Cfg = ToepCfg<LOGN>;
   if (Cfg::smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(toeplitz_fft_kernel<LOGN>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::smem);
-    if (e != cudaSuccess) return e;
+    // once per device (so that later launches, e.g. under stream capture,
+    // make no attribute calls)
+    static unsigned long long done = 0;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (!(done & bit)) {
+      cudaError_t e = cudaFuncSetAttribute(toeplitz_fft_kernel<LOGN>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::smem);
+      if (e != cudaSuccess) return e;
+      done |= bit;
+    }
   }
   int gy = (a.M + a.kgroup - 1) / a.kgroup;
   DEMAG_LAUNCH(P, kFamFFT, st, toeplitz_fft_kernel<LOGN><<<dim3(gx, gy), 256, Cfg::smem, st>>>(a));
@@ -567,10 +576,11 @@ extern "C" demag_status demag_apply_cp(demag_plan* P, int r, const float* lambda
   return demag_apply_cp_batched(P, 1, r, lambda, U, out_w, out_U, stream);
 }
 
-extern "C" demag_status demag_apply_tucker(demag_plan* P, const int r[3], const float* V, float* out_w,
-                                           float* out_V, void* stream) {
+extern "C" demag_status demag_apply_tucker_batched(demag_plan* P, int batch, const int r[3], const float* V,
+                                                   float* out_w, float* out_V, void* stream) {
   demag_status s = check_fft_plan(P, "demag_apply_tucker");
   if (s != DEMAG_OK) return s;
+  if (batch < 1) return set_error(P, DEMAG_EINVAL, "demag_apply_tucker: batch must be >= 1");
   if (!r || !V || !out_w || !out_V) return set_error(P, DEMAG_EINVAL, "demag_apply_tucker: NULL pointer");
   for (int p = 0; p < 3; ++p)
     if (r[p] < 1) return set_error(P, DEMAG_EINVAL, "demag_apply_tucker: r[%d] must be >= 1", p);
@@ -584,24 +594,30 @@ extern "C" demag_status demag_apply_tucker(demag_plan* P, const int r[3], const 
     a = ToepAxis{};
     a.axis = p;
     a.rcols = r[p];
-    a.ncols = 3 * r[p];
+    a.ncols = batch * 3 * r[p];
     a.in = V + aoff;
-    a.in_bstride = 0;
+    a.in_bstride = 3 * qstride;
     a.in_qstride = qstride;
     a.out = out_V + (long)P->M * 3 * aoff;
-    a.out_bstride = 0;
+    a.out_bstride = (long)P->M * 3 * qstride;
     aoff += (long)r[p] * P->n[p];
   }
   s = run_axes(P, ax, 3, "toeplitz_fft_kernel (tucker)", st);
   if (s != DEMAG_OK) return s;
-  return launch_weights(P, 1, 1, nullptr, out_w, st);
+  return launch_weights(P, batch, 1, nullptr, out_w, st);
 }
 
-extern "C" demag_status demag_apply_tt(demag_plan* P, const int r[2], const float* G1, const float* G2,
-                                       const float* G3, float* out_w, float* oG1, float* oG2, float* oG3,
-                                       void* stream) {
+extern "C" demag_status demag_apply_tucker(demag_plan* P, const int r[3], const float* V, float* out_w,
+                                           float* out_V, void* stream) {
+  return demag_apply_tucker_batched(P, 1, r, V, out_w, out_V, stream);
+}
+
+extern "C" demag_status demag_apply_tt_batched(demag_plan* P, int batch, const int r[2], const float* G1,
+                                               const float* G2, const float* G3, float* out_w, float* oG1,
+                                               float* oG2, float* oG3, void* stream) {
   demag_status s = check_fft_plan(P, "demag_apply_tt");
   if (s != DEMAG_OK) return s;
+  if (batch < 1) return set_error(P, DEMAG_EINVAL, "demag_apply_tt: batch must be >= 1");
   if (!r || !G1 || !G2 || !G3 || !out_w || !oG1 || !oG2 || !oG3)
     return set_error(P, DEMAG_EINVAL, "demag_apply_tt: NULL pointer");
   if (r[0] < 1 || r[1] < 1) return set_error(P, DEMAG_EINVAL, "demag_apply_tt: TT ranks must be >= 1");
@@ -615,14 +631,20 @@ extern "C" demag_status demag_apply_tt(demag_plan* P, const int r[2], const floa
     a = ToepAxis{};
     a.axis = p;
     a.rcols = rc[p];
-    a.ncols = 3 * rc[p];
+    a.ncols = batch * 3 * rc[p];
     a.in = ins[p];
-    a.in_bstride = 0;
     a.in_qstride = (long)rc[p] * P->n[p];
+    a.in_bstride = 3 * a.in_qstride;
     a.out = outs[p];
-    a.out_bstride = 0;
+    a.out_bstride = (long)P->M * 3 * a.in_qstride;
   }
   s = run_axes(P, ax, 3, "toeplitz_fft_kernel (tt)", st);
   if (s != DEMAG_OK) return s;
-  return launch_weights(P, 1, 1, nullptr, out_w, st);
+  return launch_weights(P, batch, 1, nullptr, out_w, st);
+}
+
+extern "C" demag_status demag_apply_tt(demag_plan* P, const int r[2], const float* G1, const float* G2,
+                                       const float* G3, float* out_w, float* oG1, float* oG2, float* oG3,
+                                       void* stream) {
+  return demag_apply_tt_batched(P, 1, r, G1, G2, G3, out_w, oG1, oG2, oG3, stream);
 }

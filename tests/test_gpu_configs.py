@@ -180,3 +180,57 @@ def test_c5_gradient_vs_fp64_finite_differences(D):
     print(f"C5 gradient vs FD: max pointwise err / max|g| {max(errs):.2e}, directional rel {dir_err:.2e}")
     assert max(errs) < 1e-5 and dir_err < 1e-5
     assert float(E) == pytest.approx(oen.energy_from_m(m64, n3, h, R), rel=1e-5)
+
+
+def test_c4_batched_and_graph_captured(D):
+    """C4 as a batch: Tucker and TT items in one launch equal single applies,
+    and the batched calls replay from a captured CUDA graph."""
+    n3, h, R = (1024,) * 3, (1 / 1024,) * 3, 61
+    P = D.demag_build_factors(n3, h, R)
+    M, B = P.M, 3
+    rt, rr = (8, 8, 8), (8, 8)
+    tot = sum(rt[p] * 1024 for p in range(3))
+    V = torch.cat([dev(synth.tucker_inputs(n3, rt, 1300 + b)[1].ravel()) for b in range(B)])
+    wB = torch.empty(B * M * 3, device="cuda")
+    oB = torch.empty(B * M * 3 * tot, device="cuda")
+    tts = [synth.tt_inputs(n3, rr, 1400 + b) for b in range(B)]
+    G = [torch.cat([dev(t[i].ravel()) for t in tts]) for i in range(3)]
+    sizes = [8 * 1024, 64 * 1024, 8 * 1024]
+    tw = torch.empty(B * M * 3, device="cuda")
+    tO = [torch.empty(B * M * 3 * s, device="cuda") for s in sizes]
+
+    def run():
+        D.demag_apply_tucker_batched(P, B, rt, V, wB, oB)
+        D.demag_apply_tt_batched(P, B, rr, G[0], G[1], G[2], tw, *tO)
+
+    run()
+    torch.cuda.synchronize()
+    for b in range(B):
+        w1 = torch.empty(M * 3, device="cuda")
+        o1 = torch.empty(M * 3 * tot, device="cuda")
+        D.demag_apply_tucker(P, rt, V[b * 3 * tot:(b + 1) * 3 * tot], w1, o1)
+        t1 = [torch.empty(M * 3 * s, device="cuda") for s in sizes]
+        D.demag_apply_tt(P, rr, *[G[i][b * 3 * sizes[i]:(b + 1) * 3 * sizes[i]] for i in range(3)], w1, *t1)
+        torch.cuda.synchronize()
+        assert torch.equal(oB[b * M * 3 * tot:(b + 1) * M * 3 * tot], o1)
+        for i in range(3):
+            assert torch.equal(tO[i][b * M * 3 * sizes[i]:(b + 1) * M * 3 * sizes[i]], t1[i])
+    ref = [oB.clone()] + [t.clone() for t in tO]
+    oB.fill_(float("nan"))
+    for t in tO:
+        t.fill_(float("nan"))
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            run()
+    torch.cuda.current_stream().wait_stream(s)
+    g.replay()
+    torch.cuda.synchronize()
+    for got, want in zip([oB] + tO, ref):
+        assert torch.equal(got, want)
+    # spot check against the oracle: first Tucker item
+    core, Vh = synth.tucker_inputs(n3, rt, 1300)
+    rw, rV = ost.apply_tucker(core, Vh, n3, rt, h, R)
+    assert rel_l2(host(oB[:M * 3 * tot]), np.concatenate([rV[p].ravel() for p in range(3)])) <= TOL["fp32"]
