@@ -585,6 +585,11 @@ def run_uneven_batch(args, D, world, local, stream, form):
         phis.append(torch.empty(sn[2], sn[1], sn[0], device="cuda"))
     M = plans[0].M
     flops = sum(2.0 * M * (a * b * c) * (3 * a + 3 * b + 2 * c) for a, b, c in shapes)
+
+    def stage_bytes(a, b, c):  # algorithmic DRAM bytes of one grid's three BF16x3 stages
+        pp3 = max(1, 400 // (-(-c // 32) * 6))
+        return 4.0 * a * b * c * (3 + 10 * M) + 4.0 * (-(-2 * M // pp3)) * a * b * c
+    batch_bytes = sum(stage_bytes(*sh) for sh in shapes)
     G = D.demag_graph_create_batched(plans, ms, phis, form)
     graph_fn = lambda: G.launch(stream)  # noqa: E731
     seq_fn = lambda: [D.demag_apply_full(P, m, f, form) for P, m, f in zip(plans, ms, phis)]  # noqa: E731
@@ -608,6 +613,7 @@ def run_uneven_batch(args, D, world, local, stream, form):
     return {"grids": len(shapes), "form": form, "value": world * len(shapes) * 1e3 / ms_graph,
             "unit": "grids/s", "ms_per_batch": ms_graph, "ms_per_batch_one_call_per_grid": ms_seq,
             "algorithmic_tflops": flops / (ms_graph * 1e-3) / 1e12, "algorithmic_flops_per_batch": flops,
+            "hbm_achieved_gbs": batch_bytes / (ms_graph * 1e-3) / 1e9, "algorithmic_bytes_per_batch": batch_bytes,
             "cells": int(sum(a * b * c for a, b, c in shapes)),
             "shapes": {f"{a}x{b}x{c}": shapes.count((a, b, c)) for a, b, c in sorted(set(shapes))},
             "gpu_launches": int(launches), "graph_kernels": G.kernels, "clocks": clk.summary(),
