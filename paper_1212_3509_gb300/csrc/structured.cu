@@ -29,6 +29,8 @@
 //                        keep) are computed and stored to HBM.
 // Twiddles: one value per item from a two-level shared table
 // (W_L^m = T1[m >> 7] * T0[m & 127]) and its powers by a product tree.
+#include <type_traits>
+
 #include "internal.h"
 #include "fft.cuh"
 
@@ -247,7 +249,6 @@ __global__ void __launch_bounds__(256, ToepCfg<LOGN>::minblocks)
 
   const int axis = A.axis;
   const int type = (axis == q) ? 1 : 0;  // F on the axis of the component
-  const float fsign = type ? -1.f : 1.f;
   const int k0 = blockIdx.y * a.kgroup;
   const int k1 = min(a.M, k0 + a.kgroup);
   float* outbase = A.out + b * A.out_bstride + (long)l * n;
@@ -264,100 +265,108 @@ __global__ void __launch_bounds__(256, ToepCfg<LOGN>::minblocks)
     w.y = -w.y;
     powers<16>(w, pw_last);
   }
-  for (int k = k0; k < k1; ++k) {
-    const float2* sp = a.sympair + ((long)(k * 2 + type) * 3 + axis) * a.pairstride;
-    // 3. first pass in registers on the bins j + r N/R1 of item j
-    constexpr int items1 = N / R1;
-    constexpr int ipt1 = (items1 + TG - 1) / TG;
-#pragma unroll
-    for (int it = 0; it < ipt1; ++it) {
-      const int j = lt + it * TG;
-      if (items1 % TG == 0 || j < items1) {
-        float2 v[R1];
-#pragma unroll
-        for (int r = 0; r < R1; ++r) {
-          const int f = j + r * items1;
-          const float2 s2 = __ldg(sp + f);
-          const float4 pq = PQ[f];  // (P, Q)
-          // E: s_f P + s_c Q ;  F: i (s_f P - s_c Q)
-          const float sc = fsign * s2.y;
-          const float zx = fmaf(s2.x, pq.x, sc * pq.z);
-          const float zy = fmaf(s2.x, pq.y, sc * pq.w);
-          v[r] = type ? make_float2(-zy, zx) : make_float2(zx, zy);
-        }
-        dft_reg<R1, true>(v);
-        if constexpr (NPASS <= 1) {
-          // single pass: outputs j + r*items1, keep the first half
-#pragma unroll
-          for (int r = 0; r < R1; ++r) {
-            const int i = j + r * items1;
-            if (active && 2 * i < n) {
-              float* o = outbase + (long)(k * 3 + q) * rcols * n;
-              o[2 * i] = v[r].x;
-              if (2 * i + 1 < n) o[2 * i + 1] = v[r].y;
-            }
-          }
-        } else {
-#pragma unroll
-          for (int r = 0; r < R1; ++r) buf[pad16(j * R1 + r)] = v[r];
-        }
-      }
-    }
-    if constexpr (NPASS > 1) {
-      __syncthreads();
-      // 4. middle radix-16 passes in place
-      int Ns = R1;
-#pragma unroll
-      for (int ps = 1; ps < NPASS - 1; ++ps) {
-        mid_pass<16, N, TG>(buf, Ns, lt, tw);
-        Ns *= 16;
-      }
-      // 5. last radix-16 pass (Ns = N/16): outputs j + r N/16, keep r < 8
-      constexpr int items = N / 16;
-      constexpr int ipt = (items + TG - 1) / TG;
-#pragma unroll
-      for (int it = 0; it < ipt; ++it) {
+  // the node loop, specialised on the factor type (E or F), which is fixed per column
+  auto node_loop = [&](auto type_tag) {
+    constexpr int TYPE = decltype(type_tag)::value;
+    for (int k = k0; k < k1; ++k) {
+      const float2* sp = a.sympair + ((long)(k * 2 + TYPE) * 3 + axis) * a.pairstride;
+      // 3. first pass in registers on the bins j + r N/R1 of item j
+      constexpr int items1 = N / R1;
+      constexpr int ipt1 = (items1 + TG - 1) / TG;
+  #pragma unroll
+      for (int it = 0; it < ipt1; ++it) {
         const int j = lt + it * TG;
-        if (items % TG == 0 || j < items) {
-          float2 v[16];
-          float2 pw[16];
-          if constexpr (keep_tw) {
-#pragma unroll
-            for (int r = 0; r < 16; ++r) pw[r] = pw_last[r];
-          } else {
-            float2 w = tw.L(2 * j);  // W_N^j (Ns = N/16, so k = j), inverse: conjugate
-            w.y = -w.y;
-            powers<16>(w, pw);
+        if (items1 % TG == 0 || j < items1) {
+          float2 v[R1];
+  #pragma unroll
+          for (int r = 0; r < R1; ++r) {
+            const int f = j + r * items1;
+            const float2 s2 = __ldg(sp + f);
+            const float4 pq = PQ[f];  // (P, Q)
+            // E: s_f P + s_c Q ;  F: i (s_f P - s_c Q)
+            const float sc = TYPE ? -s2.y : s2.y;
+            const float zx = fmaf(s2.x, pq.x, sc * pq.z);
+            const float zy = fmaf(s2.x, pq.y, sc * pq.w);
+            v[r] = TYPE ? make_float2(-zy, zx) : make_float2(zx, zy);
           }
-#pragma unroll
-          for (int r = 0; r < 16; ++r) {
-            const float2 x =
-                (items % 16 == 0) ? buf[pad16(j) + r * PadStride<items>::value] : buf[pad16(j + r * items)];
-            v[r] = r > 0 ? cmul(x, pw[r]) : x;
-          }
-          idft16_first_half(v);
-          if (active) {
-            float* o = outbase + (long)(k * 3 + q) * rcols * n;
-#pragma unroll
-            for (int r = 0; r < 8; ++r) {
-              const int i = j + r * items;
-              if (2 * i + 1 < n) {
-                if (vec)
-                  reinterpret_cast<float2*>(o)[i] = v[r];
-                else {
-                  o[2 * i] = v[r].x;
-                  o[2 * i + 1] = v[r].y;
-                }
-              } else if (2 * i < n) {
+          dft_reg<R1, true>(v);
+          if constexpr (NPASS <= 1) {
+            // single pass: outputs j + r*items1, keep the first half
+  #pragma unroll
+            for (int r = 0; r < R1; ++r) {
+              const int i = j + r * items1;
+              if (active && 2 * i < n) {
+                float* o = outbase + (long)(k * 3 + q) * rcols * n;
                 o[2 * i] = v[r].x;
+                if (2 * i + 1 < n) o[2 * i + 1] = v[r].y;
+              }
+            }
+          } else {
+  #pragma unroll
+            for (int r = 0; r < R1; ++r) buf[pad16(j * R1 + r)] = v[r];
+          }
+        }
+      }
+      if constexpr (NPASS > 1) {
+        __syncthreads();
+        // 4. middle radix-16 passes in place
+        int Ns = R1;
+  #pragma unroll
+        for (int ps = 1; ps < NPASS - 1; ++ps) {
+          mid_pass<16, N, TG>(buf, Ns, lt, tw);
+          Ns *= 16;
+        }
+        // 5. last radix-16 pass (Ns = N/16): outputs j + r N/16, keep r < 8
+        constexpr int items = N / 16;
+        constexpr int ipt = (items + TG - 1) / TG;
+  #pragma unroll
+        for (int it = 0; it < ipt; ++it) {
+          const int j = lt + it * TG;
+          if (items % TG == 0 || j < items) {
+            float2 v[16];
+            float2 pw[16];
+            if constexpr (keep_tw) {
+  #pragma unroll
+              for (int r = 0; r < 16; ++r) pw[r] = pw_last[r];
+            } else {
+              float2 w = tw.L(2 * j);  // W_N^j (Ns = N/16, so k = j), inverse: conjugate
+              w.y = -w.y;
+              powers<16>(w, pw);
+            }
+  #pragma unroll
+            for (int r = 0; r < 16; ++r) {
+              const float2 x =
+                  (items % 16 == 0) ? buf[pad16(j) + r * PadStride<items>::value] : buf[pad16(j + r * items)];
+              v[r] = r > 0 ? cmul(x, pw[r]) : x;
+            }
+            idft16_first_half(v);
+            if (active) {
+              float* o = outbase + (long)(k * 3 + q) * rcols * n;
+  #pragma unroll
+              for (int r = 0; r < 8; ++r) {
+                const int i = j + r * items;
+                if (2 * i + 1 < n) {
+                  if (vec)
+                    reinterpret_cast<float2*>(o)[i] = v[r];
+                  else {
+                    o[2 * i] = v[r].x;
+                    o[2 * i + 1] = v[r].y;
+                  }
+                } else if (2 * i < n) {
+                  o[2 * i] = v[r].x;
+                }
               }
             }
           }
         }
       }
+      __syncthreads();
     }
-    __syncthreads();
-  }
+  };
+  if (type)
+    node_loop(std::integral_constant<int, 1>{});
+  else
+    node_loop(std::integral_constant<int, 0>{});
 }
 
 // weights: out_w[b][k][q][l] = c s omega_k * lambda[b][q][l] (lambda NULL -> 1)
