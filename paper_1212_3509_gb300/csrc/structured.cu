@@ -255,6 +255,8 @@ __global__ void __launch_bounds__(256, ToepCfg<LOGN>::minblocks)
   // paired stores need an even length and an 8-byte aligned column start
   // (every (k, q) offset is a multiple of n, so one check per column)
   const bool vec = ((n & 1) == 0) && ((reinterpret_cast<uintptr_t>(outbase) & 7) == 0);
+  // the last pass keeps outputs i < N/2 (as pairs 2i, 2i + 1): all exist when n >= N
+  const bool full_vec = vec && n >= N;
   // The last pass's twiddles depend only on the thread's item: with one item
   // per thread they are computed once here and reused for every node.
   constexpr int items_last = N / 16;
@@ -340,7 +342,12 @@ __global__ void __launch_bounds__(256, ToepCfg<LOGN>::minblocks)
               v[r] = r > 0 ? cmul(x, pw[r]) : x;
             }
             idft16_first_half(v);
-            if (active) {
+            if (active && full_vec) {
+              // every kept output exists: 8-byte stores, no bounds tests
+              float2* o = reinterpret_cast<float2*>(outbase + (long)(k * 3 + q) * rcols * n);
+  #pragma unroll
+              for (int r = 0; r < 8; ++r) o[j + r * items] = v[r];
+            } else if (active) {
               float* o = outbase + (long)(k * 3 + q) * rcols * n;
   #pragma unroll
               for (int r = 0; r < 8; ++r) {
