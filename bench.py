@@ -434,6 +434,19 @@ def run_ours(args, world, rank, local):
         forms[f] = {"apps_per_s": 1e3 / ms_f, "ms_per_app": ms_f}
         phis[f] = out
 
+    # ---------------- demag energy and its gradient (forward, adjoint, FD stencils), 256^3 BF16x3
+    energy = None
+    if form in ("bf16x3", "tf32x3"):
+        e_out = torch.empty(1, dtype=torch.float64, device="cuda")
+        grad = torch.empty_like(m)
+        efn = lambda: D.demag_energy(P, m, e_out, grad, form)  # noqa: E731
+        efn()
+        torch.cuda.synchronize()
+        ms_e = time_region(efn, max(3, args.steps // 2), stream)
+        energy = {"value": whole_job_rate(1, max_over_ranks(ms_e, world), world), "unit": "energy+gradient evals/s",
+                  "ms_per_eval": ms_e, "form": form,
+                  "work": "phi = P m, h_d = -D phi, E = -1/2 h^3 sum m.h_d, grad = 1/2 h^3 (D P m + P^T D^T m)"}
+
     # ---------------- parity against the oracle (sampled) and CPU baseline
     if not args.no_oracle and rank == 0:
         from oracle import full as ofull, structured as ost
@@ -456,6 +469,8 @@ def run_ours(args, world, rank, local):
         result["cp"]["rel_l2"] = float(np.linalg.norm(got_cp - ref_cp) / np.linalg.norm(ref_cp))
         result["cpu_baseline"] = cpu_baseline(n3, h, R, m_host, budget_s=20.0)
     result["forms_full"] = forms
+    if energy is not None:
+        result["energy_gradient"] = energy
     if c4 is not None:
         if not args.no_oracle and rank == 0:
             from oracle import structured as ost
