@@ -619,6 +619,97 @@ __global__ void reduce_parts_kernel(const __grid_constant__ ReduceList L) {
   }
 }
 
+// ---------------------------------------------------------------- short axes on CUDA cores
+
+// A stage whose axis has at most kSmallAxis cells (thin films) would pad both
+// the contraction (32-element k-blocks) and the output columns (16-wide tiles)
+// on the tensor cores; it runs here instead: one thread per (job, row), the
+// job's factor matrices in shared memory (FP32 from the FP64 generators), FP32
+// accumulation, the same output layout and hi/lo split as the tensor-core epilogue.
+constexpr int kSmallAxis = 16;
+constexpr int kSmallChunk = 32;  // factor matrices staged per round (32 x 16 x 16 floats = 32 KB)
+
+struct SmallStage {
+  const void* a_hi;
+  const void* a_lo;       // input planes: field f, row r at f * a_field + r * a_ld
+  long long a_field;
+  int a_ld;
+  int rows, n, axis;      // rows per field; axis length (contraction and output columns)
+  int glen;
+  const double* gen;      // [M][2][3][glen]
+  const double* scale;    // [M], applied on the third axis
+  const TcJob* jobs;
+  const short2* pairs;    // (A field, matrix 2k + type)
+  int njobs;
+  void* out_hi;
+  void* out_lo;
+  long long field_elems, s_a;
+  int ldC, n_inner, mode;
+  float alpha;
+};
+
+template <class F>
+__global__ void __launch_bounds__(256) small_stage_kernel(const __grid_constant__ SmallStage S) {
+  using T = typename F::T;
+  __shared__ float sB[kSmallChunk * kSmallAxis * kSmallAxis];
+  const TcJob J = S.jobs[blockIdx.y];
+  const int n = S.n;
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool valid = row < S.rows;
+  float acc[kSmallAxis];
+#pragma unroll
+  for (int a = 0; a < kSmallAxis; ++a) acc[a] = 0.f;
+  for (int p0 = 0; p0 < J.npairs; p0 += kSmallChunk) {
+    const int np = min(kSmallChunk, J.npairs - p0);
+    __syncthreads();  // the previous round's matrices are consumed
+    for (int i = threadIdx.x; i < np * n * n; i += blockDim.x) {
+      const int p = i / (n * n), rem = i - p * n * n;
+      const int a = rem / n, kk = rem - a * n;
+      const short2 pr = S.pairs[J.pair0 + p0 + p];
+      const int k = pr.y >> 1;
+      double v = S.gen[((long long)pr.y * 3 + S.axis) * S.glen + (a - kk + n - 1)];
+      if (S.axis == 2) v *= S.scale[k];
+      sB[i] = (float)v;
+    }
+    __syncthreads();
+    if (!valid) continue;
+    for (int p = 0; p < np; ++p) {
+      const short2 pr = S.pairs[J.pair0 + p0 + p];
+      const long long off = (long long)pr.x * S.a_field + (long long)row * S.a_ld;
+      const T* hi = reinterpret_cast<const T*>(S.a_hi) + off;
+      const T* lo = reinterpret_cast<const T*>(S.a_lo) + off;
+      float x[kSmallAxis];
+#pragma unroll
+      for (int kk = 0; kk < kSmallAxis; ++kk) x[kk] = kk < n ? (float)hi[kk] + (float)lo[kk] : 0.f;
+      const float* b = sB + p * n * n;
+#pragma unroll
+      for (int a = 0; a < kSmallAxis; ++a) {
+        if (a >= n) break;
+        float t = acc[a];
+#pragma unroll
+        for (int kk = 0; kk < kSmallAxis; ++kk)
+          if (kk < n) t = fmaf(b[a * n + kk], x[kk], t);
+        acc[a] = t;
+      }
+    }
+  }
+  if (!valid) return;
+  const int outer = row / S.n_inner, inner = row - outer * S.n_inner;
+  const long long rbase = (long long)J.out_field * S.field_elems + (long long)outer * S.ldC + inner;
+#pragma unroll
+  for (int a = 0; a < kSmallAxis; ++a) {
+    if (a >= n) break;
+    if (S.mode == kOutSplit) {
+      T h, l;
+      F::split(acc[a], h, l);
+      reinterpret_cast<T*>(S.out_hi)[rbase + a * S.s_a] = h;
+      reinterpret_cast<T*>(S.out_lo)[rbase + a * S.s_a] = l;
+    } else {
+      reinterpret_cast<float*>(S.out_hi)[rbase + a * S.s_a] = S.alpha * acc[a];
+    }
+  }
+}
+
 // ---------------------------------------------------------------- host side
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -697,6 +788,8 @@ struct TcState {
   short2* pairs;          // device, all programs
   int* tile0;             // device [kPrograms][2]: {0, ntiles} for single-group launches
   TcGroup host_prog[kPrograms];
+  bool small[kPrograms];          // program runs on CUDA cores (axis of at most kSmallAxis cells)
+  SmallStage small_prog[kPrograms];
   size_t bytes;
 };
 
@@ -922,6 +1015,40 @@ static demag_status build_programs(demag_plan* P, TcState* S, const CUtensorMap 
     H[p].njobs = jend - b.job0[p];
     H[p].ntiles = H[p].njobs * H[p].m_tiles * H[p].n_tiles;
   }
+  // stages along an axis of at most kSmallAxis cells run on CUDA cores
+  {
+    const void* in_hi[3] = {S->X[0], S->buf1[0], S->buf2[0]};
+    const void* in_lo[3] = {S->X[1], S->buf1[1], S->buf2[1]};
+    const long long rows_of[3] = {(long long)n3 * n2, (long long)n1 * n3, (long long)n2 * n1};
+    for (int p = 0; p < kPrograms; ++p) {
+      const int stage = p % 3;
+      S->small[p] = P->n[stage] <= kSmallAxis;
+      if (!S->small[p]) continue;
+      SmallStage& Q = S->small_prog[p];
+      const TcGroup& G = H[p];
+      Q.a_hi = in_hi[stage];
+      Q.a_lo = in_lo[stage];
+      Q.a_ld = S->ld[stage];
+      Q.a_field = rows_of[stage] * S->ld[stage];
+      Q.rows = G.rows;
+      Q.n = P->n[stage];
+      Q.axis = stage;
+      Q.glen = P->glen;
+      Q.gen = P->gen64;
+      Q.scale = P->scale;
+      Q.jobs = G.jobs;
+      Q.pairs = G.pairs;
+      Q.njobs = G.njobs;
+      Q.out_hi = G.out_hi;
+      Q.out_lo = G.out_lo;
+      Q.field_elems = G.field_elems;
+      Q.s_a = G.s_a;
+      Q.ldC = G.ldC;
+      Q.n_inner = G.n_inner;
+      Q.mode = G.mode;
+      Q.alpha = G.alpha;
+    }
+  }
   DEMAG_CUDA(P, cudaMalloc(&S->prog, sizeof(TcGroup) * kPrograms));
   DEMAG_CUDA(P, cudaMemcpy(S->prog, H, sizeof(TcGroup) * kPrograms, cudaMemcpyHostToDevice));
   int t0[2 * kPrograms];
@@ -988,6 +1115,7 @@ static demag_status tune_tile_widths(demag_plan* P, TcState* S, cudaStream_t st)
   DEMAG_CUDA(P, cudaEventCreate(&e1));
   demag_status s = DEMAG_OK;
   for (int prog = 0; prog < kPrograms && s == DEMAG_OK; ++prog) {
+    if (S->small[prog]) continue;  // runs on CUDA cores
     const int def = S->host_prog[prog].bn;
     std::vector<int> cands{def};
     for (int c = 128; c >= 64; c /= 2)
@@ -1066,6 +1194,9 @@ demag_status tc_prepare(demag_plan* P, demag_precision prec, cudaStream_t st) {
     // TF32x3 issues twice the MMAs per K of BF16x3 in stages 1-2 as well, so its
     // node sum gets half the accumulation budget
     S->pp3 = pairs_per_split(kb3, S->elem == 4 ? 200 : 400);
+    // a node-sum stage on CUDA cores accumulates in round-to-nearest FP32; its
+    // groups only split the work (one job per group) over more blocks
+    if (n3 <= kSmallAxis) S->pp3 = std::min(S->pp3, 4);
     const int gf = (2 * M + S->pp3 - 1) / S->pp3;   // forward: 2M pairs in one sum
     const int ga = (M + S->pp3 - 1) / S->pp3;       // adjoint: M pairs per component
     const int fields = gf > 3 * ga ? gf : 3 * ga;
@@ -1077,15 +1208,22 @@ demag_status tc_prepare(demag_plan* P, demag_precision prec, cudaStream_t st) {
     return set_error(P, DEMAG_ENOMEM, "tensor-core workspace allocation failed");
   }
   CUtensorMap mapB[3][2], mapX[2], map1[2], map2[2], out1[2], out2[2], out3;
+  memset(mapB, 0, sizeof(mapB));  // maps of CUDA-core stages stay unset
+  memset(mapX, 0, sizeof(mapX));
+  memset(map1, 0, sizeof(map1));
+  memset(map2, 0, sizeof(map2));
   memset(out1, 0, sizeof(out1));
   memset(out2, 0, sizeof(out2));
   memset(&out3, 0, sizeof(out3));
   for (int h = 0; h < 2; ++h) {
     for (int p = 0; p < 3; ++p)
-      ok = ok && make_map(&mapB[p][h], S->B[p][h], S->elem, P->n[p], P->n[p], 2 * M, S->ld[p], S->bn[p]);
-    ok = ok && make_map(&mapX[h], S->X[h], S->elem, n1, (uint64_t)n3 * n2, 3, S->ld[0], kBM);
-    ok = ok && make_map(&map1[h], S->buf1[h], S->elem, n2, (uint64_t)n1 * n3, 3 * M, S->ld[1], kBM);
-    ok = ok && make_map(&map2[h], S->buf2[h], S->elem, n3, (uint64_t)n2 * n1, 3 * M, S->ld[2], kBM);
+      if (P->n[p] > kSmallAxis)
+        ok = ok && make_map(&mapB[p][h], S->B[p][h], S->elem, P->n[p], P->n[p], 2 * M, S->ld[p], S->bn[p]);
+    if (n1 > kSmallAxis) ok = ok && make_map(&mapX[h], S->X[h], S->elem, n1, (uint64_t)n3 * n2, 3, S->ld[0], kBM);
+    if (n2 > kSmallAxis)
+      ok = ok && make_map(&map1[h], S->buf1[h], S->elem, n2, (uint64_t)n1 * n3, 3 * M, S->ld[1], kBM);
+    if (n3 > kSmallAxis)
+      ok = ok && make_map(&map2[h], S->buf2[h], S->elem, n3, (uint64_t)n2 * n1, 3 * M, S->ld[2], kBM);
   }
   // epilogue stores through TMA where a warp's 32 output rows share one outer
   // index (n_inner % 32 == 0) and a 32 x 32 chunk fits the staging buffer
@@ -1151,7 +1289,16 @@ static demag_status launch_groups(demag_plan* P, const TcGroup* groups, const in
 }
 
 template <class F>
+static demag_status launch_small(demag_plan* P, const SmallStage& Q, cudaStream_t st) {
+  const dim3 grid((unsigned)((Q.rows + 255) / 256), (unsigned)Q.njobs);
+  DEMAG_LAUNCH(P, kFamGemmSimt, st, small_stage_kernel<F><<<grid, 256, 0, st>>>(Q));
+  DEMAG_LAUNCHED(P, "small_stage_kernel");
+  return DEMAG_OK;
+}
+
+template <class F>
 static demag_status run_program(demag_plan* P, TcState* S, int prog, cudaStream_t st) {
+  if (S->small[prog]) return launch_small<F>(P, S->small_prog[prog], st);
   return launch_groups<F>(P, S->prog + prog, S->tile0 + 2 * prog, 1, S->host_prog[prog].ntiles, S->counter,
                           S->status, st);
 }
@@ -1272,7 +1419,8 @@ demag_status tc_batch_create(demag_plan* const* plans, int count, demag_precisio
       const TcState* S = state(plans[order[i]], prec);
       g[st3 * count + i] = S->host_prog[kFwd1 + st3];
       t0[st3 * (count + 1) + i] = acc;
-      acc += S->host_prog[kFwd1 + st3].ntiles;
+      // a stage that runs on CUDA cores keeps its slot with no tiles
+      if (!S->small[kFwd1 + st3]) acc += S->host_prog[kFwd1 + st3].ntiles;
     }
     t0[st3 * (count + 1) + count] = acc;
     B->total[st3] = acc;
@@ -1314,6 +1462,10 @@ static demag_status batched_chain(const TcBatch* B, const float* const* m, float
   for (int st3 = 0; st3 < 3; ++st3) {
     demag_status s = launch_groups<F>(P0, B->groups + (size_t)st3 * count, B->tile0 + (size_t)st3 * (count + 1),
                                       count, B->total[st3], S0->counter, S0->status, st);
+    for (int i = 0; i < count && s == DEMAG_OK; ++i) {
+      TcState* S = state(B->plans[i], prec);
+      if (S->small[kFwd1 + st3]) s = launch_small<F>(B->plans[i], S->small_prog[kFwd1 + st3], st);
+    }
     if (s != DEMAG_OK) return s;
   }
   for (int i0 = 0; i0 < count; i0 += kMaxItems) {
