@@ -153,6 +153,16 @@ def whole_job_rate(units_per_rank: float, ms_max: float, world: int) -> float:
 
 # ------------------------------------------------------------------ workloads
 
+def bench_config(args, form, world):
+    """The workload the headline value is quoted on (both arms report it)."""
+    n, ncp, B = args.n, args.cp_n, args.cp_batch
+    return {"workload": f"full format {n}^3, R=41 (M=20), form {form}; "
+                        f"CP n={ncp} rank 4/component, R=61 (M=30), batch {B}",
+            "grid": [n] * 3, "R": 41, "form": form, "cp_n": ncp, "cp_rank": 4, "cp_R": 61, "cp_batch": B,
+            "parallelism": f"replicas x{world}",
+            "l2": "inputs larger than L2 (m = 201 MB at 256^3; CP batch outputs 4.5 GB)"}
+
+
 def full_config(n):
     return (n, n, n), (1.0 / n,) * 3, 41
 
@@ -374,11 +384,7 @@ def run_ours(args, world, rank, local):
         "dtype": {"fp32": "f32", "fp64": "f64", "tf32x3": "tf32x3 (f32 accumulate)",
                   "bf16x3": "bf16x3 (f32 accumulate)"}[form],
         "data": "synthetic (seeded vortex state + 5% noise; smooth random CP factors)",
-        "config": {"workload": f"full format {args.n}^3, R=41 (M=20), form {form}; "
-                               f"CP n={ncp} rank {r}/component, R=61 (M=30), batch {B}",
-                   "grid": [args.n] * 3, "R": R, "form": form, "cp_n": ncp, "cp_rank": r, "cp_R": cR,
-                   "cp_batch": B, "parallelism": f"replicas x{world}",
-                   "l2": "inputs larger than L2 (m = 201 MB at 256^3; CP batch outputs 4.5 GB)"},
+        "config": bench_config(args, form, world),
         "roofline": {"kernel": "mode-product GEMM (" + fam + "), all stages of one application",
                      "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
                      "frac": achieved / peak,
@@ -670,8 +676,7 @@ def run_reference(args, world, rank, local):
     out = {"metric": METRIC, "value": value, "unit": "apps/s", "impl": "reference", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 * M, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded vortex state)",
-           "config": {"workload": f"full format {args.n}^3, R=41 (M=20); FP64 CPU oracle", "grid": [args.n] * 3,
-                      "R": R, "parallelism": "host cores"},
+           "config": dict(bench_config(args, "fp64 CPU oracle", world), parallelism="host cores"),
            "cpu_baseline": {"value": value, "unit": "apps/s", "cores": os.cpu_count(), "kind": "oracle",
                             "sample": f"each step: 1 of {M} nodes of the {args.n}^3 full-format application, "
                                       "scaled to one app"},
