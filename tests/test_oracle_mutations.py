@@ -67,3 +67,64 @@ def test_mutation_is_caught(monkeypatch, name, mod, fn):
         if hasattr(other, name):
             monkeypatch.setattr(other, name, fn)
     assert _kron_vs_exact_error() > 1e-3
+
+
+# ---- the analytic stray field (oracle/field.py): plant mistakes in its
+# derivative generators and scale, and check that the closed-form box field
+# or the derivative of the shifted potential catches each one
+from oracle import field  # noqa: E402
+
+
+def _field_pin_errors():
+    import test_oracle_field as T
+    errs = []
+    n, h, R = (6, 5, 7), (0.11, 0.09, 0.13), 11
+    rng = np.random.default_rng(3)
+    m = rng.standard_normal((3, n[2], n[1], n[0]))
+    s, hh = generators.scaled_spacing(n, h)
+    for axis in range(3):
+        d = 1e-4 * hh[axis]
+        fd = (T._shifted_potential(m, n, h, R, axis, d) - T._shifted_potential(m, n, h, R, axis, -d)) / (2 * d * s)
+        hd = field.apply_field(m, n, h, R)
+        errs.append(np.max(np.abs(-fd - hd[axis])) / np.max(np.abs(hd[axis])))
+    n, h = (10, 8, 12), (0.1, 0.1, 0.1)
+    mu = synth.uniform_m(n, 2).astype(np.float64)
+    hd = field.apply_field(mu, n, h, 41)
+    for p in range(3):
+        e = np.zeros(3)
+        e[p] = 1e-6
+        ref = -(T._box_potential_at(n, h, 2, e) - T._box_potential_at(n, h, 2, -e)) / 2e-6
+        errs.append(np.max(np.abs(hd[p] - ref)) / np.max(np.abs(ref)))
+    return max(errs)
+
+
+def test_field_unmutated_is_accurate():
+    assert _field_pin_errors() < 2e-4
+
+
+def _field_mutations():
+    orig_dE, orig_dF, orig_c = field.gen_dE, field.gen_dF, field.C_POT
+
+    def dE_sign(tau, hh, n):
+        return -orig_dE(tau, hh, n)
+
+    def dF_one_face(tau, hh, n):  # only the upper cell face
+        d = np.abs(np.arange(-(n - 1), n, dtype=np.float64))
+        b = (d + 0.5) * hh
+        return b * np.exp(-tau * tau * b * b)
+
+    def dE_no_tau2(tau, hh, n):  # the factor 2 tau^2 dropped
+        return orig_dE(tau, hh, n) / (2.0 * tau * tau)
+
+    return [
+        ("gen_dE", dE_sign),
+        ("gen_dF", dF_one_face),
+        ("gen_dE", dE_no_tau2),
+        ("C_POT", orig_c * 1.2),  # the domain scale s = 1.2 of the box grid kept in the field
+    ]
+
+
+@pytest.mark.parametrize("name,fn", _field_mutations(), ids=lambda x: x if isinstance(x, str) else "")
+def test_field_mutation_is_caught(monkeypatch, name, fn):
+    monkeypatch.setattr(field, name, fn)
+    assert _field_pin_errors() > 1e-3
