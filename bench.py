@@ -452,6 +452,15 @@ def run_ours(args, world, rank, local):
         energy = {"value": whole_job_rate(1, max_over_ranks(ms_e, world), world), "unit": "energy+gradient evals/s",
                   "ms_per_eval": ms_e, "form": form,
                   "work": "phi = P m, h_d = -D phi, E = -1/2 h^3 sum m.h_d, grad = 1/2 h^3 (D P m + P^T D^T m)"}
+        # analytic stray field: the three derivative chains (eight stage launches)
+        hd = torch.empty_like(m)
+        ffn = lambda: D.demag_stray_field_exact(P, m, hd, form)  # noqa: E731
+        ffn()
+        torch.cuda.synchronize()
+        ms_f = time_region(ffn, max(3, args.steps // 2), stream)
+        energy["exact_stray_field"] = {"value": whole_job_rate(1, max_over_ranks(ms_f, world), world),
+                                       "unit": "fields/s", "ms_per_field": ms_f, "form": form,
+                                       "work": "h_d = -grad phi from derivative Kronecker factors, 3 directions"}
 
     # ---------------- parity against the oracle (sampled) and CPU baseline
     if not args.no_oracle and rank == 0:

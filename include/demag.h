@@ -239,6 +239,20 @@ demag_status demag_stray_field(demag_plan* plan, const float* phi, float* hd, vo
 demag_status demag_energy(demag_plan* plan, const float* m, double* energy, float* grad,
                           demag_precision prec, void* stream);
 
+/* Stray field without finite differences: hd[p] = -d phi / d xi_p at the cell
+ * centres, p = 1..3.  In the Kronecker form (Cor. 3) the collocation point
+ * enters each 1D factor only through the limits of its cell integral, so the
+ * derivative along axis p replaces the axis-p factors by dE = -2 tau_k^2 F and
+ * dF[d] = b e^{-tau^2 b^2} - a e^{-tau^2 a^2} (a, b the cell limits; the
+ * relations used for the micromagnetic stray field after Fig. 2), with 1/s for
+ * the domain scaling.  Computed by the full-format chains of `prec` with the
+ * derivative factors along one axis (the three directions share their first
+ * stages: eight stage launches).  m: float [3][n3][n2][n1]; hd: float
+ * [3][n3][n2][n1] (overwritten).  Allocates the derivative factors on first
+ * use of a precision. */
+demag_status demag_stray_field_exact(demag_plan* plan, const float* m, float* hd, demag_precision prec,
+                                     void* stream);
+
 /* Read and clear the device-side status word of the plan (bounded waits that
  * gave up set DEMAG_ETIMEOUT there).  Synchronizes `stream`. */
 demag_status demag_sync_status(demag_plan* plan, void* stream);

@@ -40,6 +40,7 @@ from ._abi import (  # noqa: F401
     demag_plan_destroy,
     demag_reserve_workspace,
     demag_stray_field,
+    demag_stray_field_exact,
     demag_symbols_size,
     demag_sync_status,
     demag_launch_count,

@@ -61,6 +61,7 @@ _SIGS = {
     "demag_apply_tucker_batched": (_i, [_vp, _i, ctypes.POINTER(_i), _vp, _vp, _vp, _vp]),
     "demag_apply_tt_batched": (_i, [_vp, _i, ctypes.POINTER(_i), _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "demag_stray_field": (_i, [_vp, _vp, _vp, _vp]),
+    "demag_stray_field_exact": (_i, [_vp, _vp, _vp, _i, _vp]),
     "demag_energy": (_i, [_vp, _vp, _vp, _vp, _i, _vp]),
     "demag_sync_status": (_i, [_vp, _vp]),
     "demag_apply_full_noalloc": (_i, [ctypes.POINTER(GridDesc), _vp, _vp, _vp]),
@@ -321,6 +322,14 @@ def demag_energy(plan: Plan, m, energy, grad=None, precision="fp32", stream=None
     import torch
     _check(lib.demag_energy(plan.ptr, _ptr(m, 3 * plan.N, torch.float32, "m"), _ptr(energy, 1, torch.float64, "energy"),
                             _ptr(grad, 3 * plan.N, torch.float32, "grad"), _prec(precision), _stream(stream)), plan.ptr)
+
+
+def demag_stray_field_exact(plan: Plan, m, hd, precision="fp32", stream=None):
+    """hd = -grad phi from the analytic derivative factors (no finite differences)."""
+    import torch
+    _check(lib.demag_stray_field_exact(plan.ptr, _ptr(m, 3 * plan.N, torch.float32, "m"),
+                                       _ptr(hd, 3 * plan.N, torch.float32, "hd"), _prec(precision),
+                                       _stream(stream)), plan.ptr)
 
 
 def demag_sync_status(plan: Plan, stream=None):

@@ -270,7 +270,10 @@ __global__ void narrow_kernel(const double* in, float* out, size_t count) {
 
 // forward: m (3 fields, type T) -> phi (type T) using workspace `ws` of type T
 template <typename T>
-static demag_status simt_forward(demag_plan* P, const T* m, T* phi, const T* Tm, T* ws, cudaStream_t st) {
+// Tax[p]: the factor table used along axis p (the analytic stray field swaps
+// in the derivative factors along one axis); alpha scales the result.
+static demag_status simt_forward(demag_plan* P, const T* m, T* phi, const T* const (&Tax)[3], T* ws,
+                                 cudaStream_t st, float alpha = 1.f) {
   constexpr int BM = 16 * SimtCfg<T>::TM;
   const int n1 = P->n[0], n2 = P->n[1], n3 = P->n[2];
   const size_t N = field_size(P);
@@ -280,14 +283,14 @@ static demag_status simt_forward(demag_plan* P, const T* m, T* phi, const T* Tm,
   for (int k = 0; k < M; ++k) {
     BatchBuilder b1;
     for (int q = 0; q < 3; ++q) {
-      const T* B = factor(P, Tm, k, q == 0 ? 1 : 0, 0);
+      const T* B = factor(P, Tax[0], k, q == 0 ? 1 : 0, 0);
       b1.add(n3 * n2, n1, n1, n1, n1, n3 * n2, Y + q * N, 1.f, {{m + q * N, B}}, BM);
     }
     cudaError_t e = launch_batch<T>(P, b1, st);
     if (e != cudaSuccess) return cuda_error(P, e, "gemm_tn_kernel (mode 1)");
     BatchBuilder b2;
-    const T* E2 = factor(P, Tm, k, 0, 1);
-    const T* F2 = factor(P, Tm, k, 1, 1);
+    const T* E2 = factor(P, Tax[1], k, 0, 1);
+    const T* F2 = factor(P, Tax[1], k, 1, 1);
     b2.add(n1 * n3, n2, n2, n2, n2, n1 * n3, UV + (2 * k) * N, 1.f, {{Y, E2}, {Y + N, F2}}, BM);
     b2.add(n1 * n3, n2, n2, n2, n2, n1 * n3, UV + (2 * k + 1) * N, 1.f, {{Y + 2 * N, E2}}, BM);
     e = launch_batch<T>(P, b2, st);
@@ -296,10 +299,10 @@ static demag_status simt_forward(demag_plan* P, const T* m, T* phi, const T* Tm,
   BatchBuilder b3;
   std::vector<std::pair<const void*, const void*>> pairs;
   for (int k = 0; k < M; ++k) {
-    pairs.push_back({UV + (2 * k) * N, factor(P, Tm, k, 0, 2)});
-    pairs.push_back({UV + (2 * k + 1) * N, factor(P, Tm, k, 1, 2)});
+    pairs.push_back({UV + (2 * k) * N, factor(P, Tax[2], k, 0, 2)});
+    pairs.push_back({UV + (2 * k + 1) * N, factor(P, Tax[2], k, 1, 2)});
   }
-  b3.add(n2 * n1, n3, n3, n3, n3, n2 * n1, phi, 1.f, pairs, BM);
+  b3.add(n2 * n1, n3, n3, n3, n3, n2 * n1, phi, alpha, pairs, BM);
   cudaError_t e = launch_batch<T>(P, b3, st);
   if (e != cudaSuccess) return cuda_error(P, e, "gemm_tn_kernel (mode 3)");
   return DEMAG_OK;
@@ -352,17 +355,72 @@ demag_status full_forward(demag_plan* P, const float* m, float* phi, demag_preci
   s = ensure_workspace(P, prec);
   if (s != DEMAG_OK) return s;
   const size_t N = field_size(P);
-  if (prec == DEMAG_FP32) return simt_forward<float>(P, m, phi, P->T32, (float*)P->ws[prec].base, st);
+  if (prec == DEMAG_FP32) {
+    const float* const tax[3] = {P->T32, P->T32, P->T32};
+    return simt_forward<float>(P, m, phi, tax, (float*)P->ws[prec].base, st);
+  }
   double* ws = (double*)P->ws[prec].base;
   double* m64 = ws + (3 * (size_t)P->M + 3) * N;
   double* phi64 = m64 + 3 * N;
   DEMAG_LAUNCH(P, kFamSplit, st, convert_kernel<double><<<conv_blocks(3 * N), 256, 0, st>>>(m, m64, 3 * N));
   DEMAG_LAUNCHED(P, "convert_kernel");
-  s = simt_forward<double>(P, m64, phi64, P->T64, ws, st);
+  const double* const tax[3] = {P->T64, P->T64, P->T64};
+  s = simt_forward<double>(P, m64, phi64, tax, ws, st);
   if (s != DEMAG_OK) return s;
   DEMAG_LAUNCH(P, kFamSplit, st, narrow_kernel<<<conv_blocks(N), 256, 0, st>>>(phi64, phi, N));
   DEMAG_LAUNCHED(P, "narrow_kernel");
   return DEMAG_OK;
+}
+
+// ---------------------------------------------------------------- analytic stray field (CUDA cores)
+
+// h_d[p] = -dphi/dxi_p for p = 1..3: the forward chain with the axis-p factor
+// table replaced by the derivative table (built from the derivative generators).
+demag_status simt_field(demag_plan* P, const float* m, float* hd, demag_precision prec, cudaStream_t st) {
+  demag_status s = ensure_dense_factors(P, prec, st);
+  if (s == DEMAG_OK) s = ensure_workspace(P, prec);
+  if (s == DEMAG_OK) s = ensure_field_generators(P, st);
+  if (s != DEMAG_OK) return s;
+  const size_t total = (size_t)P->M * 2 * P->tgroup;
+  int blocks = (int)((total + 255) / 256);
+  if (blocks > 152 * 64) blocks = 152 * 64;
+  const size_t N = field_size(P);
+  if (prec == DEMAG_FP32) {
+    if (!P->T32d) {
+      DEMAG_CUDA(P, cudaMalloc(&P->T32d, sizeof(float) * total));
+      DEMAG_LAUNCH(P, kFamSetup, st,
+                   dense_factor_kernel<float><<<blocks, 256, 0, st>>>(P->M, P->glen, P->n[0], P->n[1], P->n[2],
+                                                                      P->tgroup, P->toff[1], P->toff[2], P->gend,
+                                                                      P->scale, P->T32d));
+      DEMAG_LAUNCHED(P, "dense_factor_kernel");
+    }
+    for (int p = 0; p < 3 && s == DEMAG_OK; ++p) {
+      const float* const tax[3] = {p == 0 ? P->T32d : P->T32, p == 1 ? P->T32d : P->T32, p == 2 ? P->T32d : P->T32};
+      s = simt_forward<float>(P, m, hd + p * N, tax, (float*)P->ws[prec].base, st, -1.f);
+    }
+    return s;
+  }
+  if (!P->T64d) {
+    DEMAG_CUDA(P, cudaMalloc(&P->T64d, sizeof(double) * total));
+    DEMAG_LAUNCH(P, kFamSetup, st,
+                 dense_factor_kernel<double><<<blocks, 256, 0, st>>>(P->M, P->glen, P->n[0], P->n[1], P->n[2],
+                                                                     P->tgroup, P->toff[1], P->toff[2], P->gend,
+                                                                     P->scale, P->T64d));
+    DEMAG_LAUNCHED(P, "dense_factor_kernel");
+  }
+  double* ws = (double*)P->ws[prec].base;
+  double* m64 = ws + (3 * (size_t)P->M + 3) * N;
+  double* out64 = m64 + 3 * N;
+  DEMAG_LAUNCH(P, kFamSplit, st, convert_kernel<double><<<conv_blocks(3 * N), 256, 0, st>>>(m, m64, 3 * N));
+  DEMAG_LAUNCHED(P, "convert_kernel");
+  for (int p = 0; p < 3 && s == DEMAG_OK; ++p) {
+    const double* const tax[3] = {p == 0 ? P->T64d : P->T64, p == 1 ? P->T64d : P->T64, p == 2 ? P->T64d : P->T64};
+    s = simt_forward<double>(P, m64, out64, tax, ws, st, -1.f);
+    if (s != DEMAG_OK) break;
+    DEMAG_LAUNCH(P, kFamSplit, st, narrow_kernel<<<conv_blocks(N), 256, 0, st>>>(out64, hd + p * N, N));
+    DEMAG_LAUNCHED(P, "narrow_kernel");
+  }
+  return s;
 }
 
 demag_status full_adjoint(demag_plan* P, const float* y, float* g, demag_precision prec, cudaStream_t st) {

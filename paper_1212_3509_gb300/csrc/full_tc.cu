@@ -790,6 +790,14 @@ struct TcState {
   TcGroup host_prog[kPrograms];
   bool small[kPrograms];          // program runs on CUDA cores (axis of at most kSmallAxis cells)
   SmallStage small_prog[kPrograms];
+  // analytic stray field: the forward stage programs with the derivative
+  // factors of their axis (built on first use)
+  bool field_ready;
+  void* Bd[3][2];                 // per axis: hi / lo derivative factors [M][2][n][ld]
+  TcGroup dprog_host[3];
+  TcGroup* dprog;                 // device [3]
+  int* dtile0;                    // device [3][2]
+  SmallStage small_dprog[3];
   size_t bytes;
 };
 
@@ -845,6 +853,10 @@ static void free_state(TcState* S) {
   cudaFree(S->jobs);
   cudaFree(S->pairs);
   cudaFree(S->tile0);
+  for (int p = 0; p < 3; ++p)
+    for (int h = 0; h < 2; ++h) cudaFree(S->Bd[p][h]);
+  cudaFree(S->dprog);
+  cudaFree(S->dtile0);
   delete S;
 }
 
@@ -1501,6 +1513,91 @@ demag_status tc_forward_batched(demag_plan* const* plans, const float* const* m,
     B = H->cache;
   }
   return tc_batch_run(B, m, phi, st);
+}
+
+// ---------------------------------------------------------------- analytic stray field
+
+// Derivative factors of every axis and the three derivative stage programs
+// (copies of the forward stage programs reading the derivative factors).
+template <class F>
+static demag_status prepare_field(demag_plan* P, TcState* S, cudaStream_t st) {
+  if (S->field_ready) return DEMAG_OK;
+  demag_status s = ensure_field_generators(P, st);
+  if (s != DEMAG_OK) return s;
+  const int M = P->M;
+  for (int p = 0; p < 3; ++p) {
+    const size_t bytes = (size_t)M * 2 * P->n[p] * S->ld[p] * S->elem;
+    for (int h = 0; h < 2; ++h) {
+      DEMAG_CUDA(P, cudaMalloc(&S->Bd[p][h], bytes));
+      DEMAG_CUDA(P, cudaMemsetAsync(S->Bd[p][h], 0, bytes, st));
+    }
+    const long long total = (long long)M * 2 * P->n[p] * P->n[p];
+    DEMAG_LAUNCH(P, kFamSetup, st,
+                 tc_factor_kernel<F><<<grid_blocks(total), 256, 0, st>>>(
+                     M, P->glen, p, P->n[p], S->ld[p], P->gend, P->scale, (typename F::T*)S->Bd[p][0],
+                     (typename F::T*)S->Bd[p][1]));
+    DEMAG_LAUNCHED(P, "tc_factor_kernel");
+  }
+  int t0[6];
+  for (int st3 = 0; st3 < 3; ++st3) {
+    TcGroup& G = S->dprog_host[st3];
+    G = S->host_prog[kFwd1 + st3];
+    if (!S->small[kFwd1 + st3]) {
+      const int p = st3;  // stage s contracts axis s
+      for (int h = 0; h < 2; ++h)
+        if (!make_map(h ? &G.b_lo : &G.b_hi, S->Bd[p][h], S->elem, P->n[p], P->n[p], 2 * M, S->ld[p], G.bn))
+          return set_error(P, DEMAG_ECUDA, "tensor map encoding failed");
+    }
+    S->small_dprog[st3] = S->small_prog[kFwd1 + st3];
+    S->small_dprog[st3].gen = P->gend;
+    t0[2 * st3] = 0;
+    t0[2 * st3 + 1] = G.ntiles;
+  }
+  DEMAG_CUDA(P, cudaMalloc(&S->dprog, sizeof(TcGroup) * 3));
+  DEMAG_CUDA(P, cudaMalloc(&S->dtile0, sizeof(t0)));
+  DEMAG_CUDA(P, cudaMemcpy(S->dprog, S->dprog_host, sizeof(TcGroup) * 3, cudaMemcpyHostToDevice));
+  DEMAG_CUDA(P, cudaMemcpy(S->dtile0, t0, sizeof(t0), cudaMemcpyHostToDevice));
+  S->field_ready = true;
+  return DEMAG_OK;
+}
+
+template <class F>
+static demag_status run_deriv(demag_plan* P, TcState* S, int st3, cudaStream_t st) {
+  if (S->small[kFwd1 + st3]) return launch_small<F>(P, S->small_dprog[st3], st);
+  return launch_groups<F>(P, S->dprog + st3, S->dtile0 + 2 * st3, 1, S->dprog_host[st3].ntiles, S->counter,
+                          S->status, st);
+}
+
+// h_d[p] = -dphi/dxi_p.  The three chains share work: the stage-1 output feeds
+// the directions 3 and 2, the stage-2 output direction 3, so eight stage
+// launches give the three fields (three independent chains would take nine).
+template <class F>
+static demag_status field_chain(demag_plan* P, TcState* S, const float* m, float* hd, cudaStream_t st) {
+  const long long N = (long long)P->n[0] * P->n[1] * P->n[2];
+  demag_status s = prepare_field<F>(P, S, st);
+  if (s == DEMAG_OK) s = split_input<F>(P, S, m, 3, st);
+  // direction 3: stages 1, 2 as for phi, derivative stage 3
+  if (s == DEMAG_OK) s = run_program<F>(P, S, kFwd1, st);
+  if (s == DEMAG_OK) s = run_program<F>(P, S, kFwd2, st);
+  if (s == DEMAG_OK) s = run_deriv<F>(P, S, 2, st);
+  if (s == DEMAG_OK) s = reduce_parts(P, S, S->groups_fwd, 1, -1.f, hd + 2 * N, st);
+  // direction 2: derivative stage 2 on the stage-1 output, stage 3 as for phi
+  if (s == DEMAG_OK) s = run_deriv<F>(P, S, 1, st);
+  if (s == DEMAG_OK) s = run_program<F>(P, S, kFwd3, st);
+  if (s == DEMAG_OK) s = reduce_parts(P, S, S->groups_fwd, 1, -1.f, hd + N, st);
+  // direction 1: derivative stage 1, stages 2 and 3 as for phi
+  if (s == DEMAG_OK) s = run_deriv<F>(P, S, 0, st);
+  if (s == DEMAG_OK) s = run_program<F>(P, S, kFwd2, st);
+  if (s == DEMAG_OK) s = run_program<F>(P, S, kFwd3, st);
+  if (s == DEMAG_OK) s = reduce_parts(P, S, S->groups_fwd, 1, -1.f, hd, st);
+  return s;
+}
+
+demag_status tc_field(demag_plan* P, const float* m, float* hd, demag_precision prec, cudaStream_t st) {
+  demag_status s = tc_prepare(P, prec, st);
+  if (s != DEMAG_OK) return s;
+  TcState* S = state(P, prec);
+  return prec == DEMAG_TF32X3 ? field_chain<Tf32Form>(P, S, m, hd, st) : field_chain<Bf16Form>(P, S, m, hd, st);
 }
 
 demag_status tc_sync_status(demag_plan* P, cudaStream_t st) {

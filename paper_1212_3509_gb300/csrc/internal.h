@@ -46,12 +46,15 @@ struct demag_plan {
   float2* twid[3] = {nullptr, nullptr, nullptr};  // per axis: exp(-2 pi i m / L_p), m < L_p
   float2* sympair = nullptr; // [M][2][3][Lmax/2]: (symbol[f], symbol[L_p/2 - f]) for f < L_p/2
   double* scale = nullptr;   // [M]: c * s * omega_k
+  double* gend = nullptr;    // [M][2][3][glen]: derivative generators dE/s, dF/s (lazily, analytic stray field)
 
   // dense factor matrices of the full path, per precision (device, lazily built)
   // layout [M][2][3] blocks of n_p x n_p (row-major T[i][j] = gen[i-j]),
   // axis-3 blocks carry the scale c*s*omega_k.
   float* T32 = nullptr;
   double* T64 = nullptr;
+  float* T32d = nullptr;     // the same layout from the derivative generators (analytic stray field)
+  double* T64d = nullptr;
   size_t toff[3];            // element offset of axis p inside one (k, type) group
   size_t tgroup;             // elements per (k, type) group = sum_p n_p^2
 
@@ -121,6 +124,9 @@ inline size_t field_size(const demag_plan* p) { return (size_t)p->n[0] * p->n[1]
 
 // full format (full_simt.cu / full_tc.cu) ---------------------------------------
 demag_status ensure_dense_factors(demag_plan* plan, demag_precision prec, cudaStream_t st);
+demag_status ensure_field_generators(demag_plan* plan, cudaStream_t st);
+demag_status simt_field(demag_plan* plan, const float* m, float* hd, demag_precision prec, cudaStream_t st);
+demag_status tc_field(demag_plan* plan, const float* m, float* hd, demag_precision prec, cudaStream_t st);
 demag_status ensure_workspace(demag_plan* plan, demag_precision prec);
 size_t workspace_bytes(const demag_plan* plan, demag_precision prec);
 demag_status full_forward(demag_plan* plan, const float* m, float* phi, demag_precision prec,

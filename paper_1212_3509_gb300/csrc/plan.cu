@@ -239,6 +239,9 @@ static void free_plan_buffers(demag_plan* P) {
   }
   cudaFree(P->T32);
   cudaFree(P->T64);
+  cudaFree(P->T32d);
+  cudaFree(P->T64d);
+  cudaFree(P->gend);
   for (auto& w : P->ws) cudaFree(w.base);
   cudaFree(P->dev_status);
   for (auto e : P->prof_pool) cudaEventDestroy(e);

@@ -112,3 +112,16 @@ def test_derivative_generators_parity():
         a, b = d - 0.025, d + 0.025
         direct = b * np.exp(-tau * tau * b * b) - a * np.exp(-tau * tau * a * a)
         assert np.allclose(dF, direct, rtol=1e-10, atol=1e-300)
+
+
+def test_cube_demagnetizing_factor_one_third():
+    # N_x + N_y + N_z = 1 and a cube is symmetric, so the volume average of the
+    # field inside a uniformly magnetized cube is -m/3 along m and 0 across it
+    n, h = (12, 12, 12), (1 / 12,) * 3
+    for q in range(3):
+        m = synth.uniform_m(n, q).astype(np.float64)
+        hd = field.apply_field(m, n, h, 41)
+        assert abs(hd[q].mean() + 1.0 / 3.0) < 1e-5
+        for p in range(3):
+            if p != q:
+                assert abs(hd[p].mean()) < 1e-12
