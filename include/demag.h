@@ -128,6 +128,19 @@ size_t demag_symbols_size(const demag_plan* plan);
 demag_status demag_apply_full(demag_plan* plan, const float* m, float* phi,
                               demag_precision prec, void* stream);
 
+/* The same phi = sum_q P^(q) m^(q) by one 3D FFT convolution (Sec. 4.2,
+ * Eq. conv_pot and Eq. fft_pot): the node sum is folded once per plan into a
+ * dense Fourier kernel K^(q) on the padded grid L_p (the plan's power of two
+ * >= 2 n_p - 1), so an application costs five passes of FP32 shared-memory
+ * FFTs independent of R.  m: float [3][n3][n2][n1], phi: float [n3][n2][n1]
+ * (overwritten), device pointers, 4-byte aligned, not overlapping.  The
+ * first call builds the kernel (FP64 sums, stored FP32: 12 (L1/2+1)
+ * (L2/2+1) (L3/2+1) bytes) and the spectra workspace (about
+ * 8 (3 (L1/2+1) n3 n2 + 3 L2 (L1/2+1) n3) bytes), so make it before any
+ * stream capture; later calls allocate nothing.  Asynchronous on `stream`.
+ * DEMAG_EUNSUPPORTED when some n_p > 512. */
+demag_status demag_apply_full_fft(demag_plan* plan, const float* m, float* phi, void* stream);
+
 /* Apply several plans' operators in one call: phi[i] = P_i m[i] for
  * i < count.  Arrays of device pointers live in HOST memory.  Grids may
  * differ in shape; every plan must already have its workspace for `prec`
@@ -295,7 +308,8 @@ unsigned long long demag_launch_count(const demag_plan* plan);
  * recorded durations (milliseconds) and counts the launches of one family:
  * 0 = mode-product GEMM on CUDA cores, 1 = mode-product GEMM on tensor
  * cores, 2 = Toeplitz FFT, 3 = operand split / conversion, 4 = setup,
- * 5 = stray field / energy, 6 = small bookkeeping kernels (term weights).
+ * 5 = stray field / energy, 6 = small bookkeeping kernels (term weights),
+ * 7 = passes of the 3D FFT convolution (demag_apply_full_fft).
  * Reading waits for the recorded events. */
 demag_status demag_profile(demag_plan* plan, int enable);
 demag_status demag_profile_read(demag_plan* plan, int family, double* total_ms, long long* launches);

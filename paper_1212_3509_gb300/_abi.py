@@ -46,6 +46,7 @@ _SIGS = {
     "demag_generators_size": (_sz, [_vp]),
     "demag_symbols_size": (_sz, [_vp]),
     "demag_apply_full": (_i, [_vp, _vp, _vp, _i, _vp]),
+    "demag_apply_full_fft": (_i, [_vp, _vp, _vp, _vp]),
     "demag_apply_full_batched": (_i, [ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i, _i, _vp]),
     "demag_graph_create_batched": (_i, [ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i, _i,
                                         ctypes.POINTER(_vp)]),
@@ -76,7 +77,8 @@ _SIGS = {
     "demag_profile_launch": (_i, [_vp, ctypes.c_longlong, ctypes.POINTER(_i), ctypes.POINTER(ctypes.c_double)]),
 }
 
-FAMILIES = {"gemm_simt": 0, "gemm_tc": 1, "fft": 2, "split": 3, "setup": 4, "energy": 5, "misc": 6}
+FAMILIES = {"gemm_simt": 0, "gemm_tc": 1, "fft": 2, "split": 3, "setup": 4, "energy": 5, "misc": 6,
+            "fft3d": 7}
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(lib, _name)
     _f.restype = _res
@@ -196,6 +198,12 @@ def demag_apply_full(plan: Plan, m, phi, precision="fp32", stream=None):
     import torch
     _check(lib.demag_apply_full(plan.ptr, _ptr(m, 3 * plan.N, torch.float32, "m"),
                                 _ptr(phi, plan.N, torch.float32, "phi"), _prec(precision), _stream(stream)), plan.ptr)
+
+
+def demag_apply_full_fft(plan: Plan, m, phi, stream=None):
+    import torch
+    _check(lib.demag_apply_full_fft(plan.ptr, _ptr(m, 3 * plan.N, torch.float32, "m"),
+                                    _ptr(phi, plan.N, torch.float32, "phi"), _stream(stream)), plan.ptr)
 
 
 def demag_apply_full_batched(plans, ms, phis, precision="bf16x3", stream=None):

@@ -151,6 +151,34 @@ __device__ __forceinline__ void stockham_pass(C* buf, int Ns, int lt, const TW& 
   __syncthreads();
 }
 
+// Padded shared-memory index: one spare slot per 16, so that strided
+// accesses of a Stockham pass fall into distinct banks.
+__device__ __forceinline__ int pad16(int i) { return i + (i >> 4); }
+// pad16(i + r * S) = pad16(i) + r * (S + S / 16) when S is a multiple of 16
+template <int S> struct PadStride { static constexpr int value = S + S / 16; };
+
+// pw[r] = w^r for r < R by a product tree of depth <= 4 (w^2, w^4, w^8 by
+// squaring, the rest as one product of those), so each power carries only a
+// few roundings of the table value w.
+template <int R>
+__device__ __forceinline__ void powers(float2 w, float2 (&pw)[R]) {
+  pw[0] = make_float2(1.f, 0.f);
+  if constexpr (R > 1) pw[1] = w;
+  if constexpr (R > 2) pw[2] = cmul(w, w);
+  if constexpr (R > 3) pw[3] = cmul(pw[2], w);
+  if constexpr (R > 4) {
+    pw[4] = cmul(pw[2], pw[2]);
+    pw[5] = cmul(pw[4], w);
+    pw[6] = cmul(pw[4], pw[2]);
+    pw[7] = cmul(pw[4], pw[3]);
+  }
+  if constexpr (R > 8) {
+    pw[8] = cmul(pw[4], pw[4]);
+#pragma unroll
+    for (int r = 9; r < R; ++r) pw[r] = cmul(pw[8], pw[r - 8]);
+  }
+}
+
 // Full complex FFT of length N = 2^LOGN in place on buf (unnormalised).
 // All threads of the block must call it (it synchronises the block); threads
 // of a group share buf.  `lt` is the thread index inside its group of TG.

@@ -1,0 +1,644 @@
+// The potential of a full tensor by one 3D FFT convolution with a dense
+// Fourier kernel (Sec. 4.2, Eq. conv_op, Eq. conv_pot, Eq. fft_pot).
+//
+// P^(q) is a convolution with the separable kernel G^(q)[J], |J_p| < n_p, so
+// on a grid padded to L_p >= 2 n_p - 1 per axis (the power of two of the
+// plan) phi = IDFT( sum_q K^(q) . DFT(m^(q)) ).  The node sum of
+// Eq. conv_pot is linear, so it is summed once per plan into
+//
+//   K^(q)[w] = c s / (L1 L2 L3) sum_k omega_k prod_p S_{k,q,p}[w_p],
+//
+// S the DFT of the circulant embedding of the generator F (p == q, odd,
+// purely imaginary spectrum) or E (p != q, even, real spectrum).  Hence K^(q)
+// is i times a real array, odd in w_q and even in the other frequencies: the
+// plan keeps only its imaginary part on the octant 0 <= w_p <= L_p/2
+// (FP64 sums rounded once to FP32).  The cost of an application is then
+// independent of R.
+//
+// An application is five passes of batched shared-memory FFTs over fibres;
+// each pass reads contiguous fibres and writes its result transposed, so the
+// next pass again reads contiguous fibres (index order slowest -> fastest):
+//   P1  m[c][i3][i2][i1]    real FFT along i1 (two fibres per complex FFT)
+//       -> S1[c][w1][i3][i2]  (w1 <= L1/2)
+//   P2  FFT along i2 (zero-padded)   -> S2[c][w2][w1][i3]
+//   P3  FFT along i3 (zero-padded), times K^(c), summed over c, inverse FFT
+//       along w3, kept i3 < n3      -> S3[i3][w1][w2]   (aliases S1)
+//   P4  inverse FFT along w2, kept i2 < n2 -> S4[i2][i3][w1]   (aliases S2)
+//   P5  inverse real FFT along w1 (two fibres per complex FFT) -> phi[i3][i2][i1]
+// All arithmetic after the FP64 kernel setup is FP32.
+#include <algorithm>
+#include <cmath>
+#include <new>
+
+#include "fft.cuh"
+#include "internal.h"
+
+namespace demag {
+
+constexpr int kFft3dMaxLog = 10;  // L_p <= 1024 (n_p <= 512)
+
+// Launch shape for an FFT of length N = 2^LOGN along one axis: TG threads
+// per fibre, G fibres per block (at least 16, so that the transposed stores
+// write runs of >= 128 bytes), buffers padded by pad16 and separated by an
+// odd stride so that the same bin of different fibres falls in different banks.
+constexpr int f3_tg(int N) { return N / 16 < 1 ? 1 : (N / 16 > 32 ? 32 : N / 16); }
+constexpr int f3_block(int N) { return 16 * f3_tg(N) < 256 ? 256 : 16 * f3_tg(N); }
+constexpr int f3_fibres(int N) { return f3_block(N) / f3_tg(N); }
+// P3 double-buffers its fibres: half the fibres per block at N = 1024 (shared memory)
+constexpr int f3_fibres_p3(int N) { return N >= 1024 ? f3_fibres(N) / 2 : f3_fibres(N); }
+
+template <int LOGN> struct F3 {
+  static constexpr int N = 1 << LOGN;
+  static constexpr int R1 = LOGN < 4 ? N : ((LOGN % 4) ? (1 << (LOGN % 4)) : 16);
+  static constexpr int NPASS = LOGN < 4 ? 1 : 1 + (LOGN - (LOGN % 4 ? LOGN % 4 : 4)) / 4;
+  static constexpr int TG = f3_tg(N);
+  static constexpr int BLOCK = f3_block(N);
+  static constexpr int G = f3_fibres(N);
+  static constexpr int BS = N + N / 16 + 1;  // per-fibre buffer stride (odd)
+  static constexpr size_t smem = ((size_t)N + (size_t)G * BS) * sizeof(float2);
+  static constexpr int G3 = f3_fibres_p3(N);  // P3: fibres per block, two buffers each
+  static constexpr int BLOCK3 = G3 * TG;
+  static constexpr size_t smem3 = ((size_t)N + (size_t)2 * G3 * BS) * sizeof(float2);
+  static constexpr int PER = N / TG;  // bins per thread of its fibre
+};
+
+// In-place complex FFT of length N on a pad16-indexed buffer by the TG
+// threads of one group (Stockham, natural order in and out).  First a pass
+// of radix R1 (no twiddles), then radix-16 passes.  tw[m] = exp(-2 pi i m / N).
+// Every thread of the block must call it (it synchronises the block).
+template <int LOGN, bool INV>
+__device__ __forceinline__ void fft_pad(float2* buf, int lt, const float2* tw) {
+  using C = F3<LOGN>;
+  constexpr int N = C::N, TG = C::TG, R1 = C::R1;
+  {
+    constexpr int items = N / R1;
+    constexpr int ipt = (items + TG - 1) / TG;
+    float2 v[ipt][R1];
+#pragma unroll
+    for (int it = 0; it < ipt; ++it) {
+      const int j = lt + it * TG;
+      if (items % TG == 0 || j < items) {
+#pragma unroll
+        for (int r = 0; r < R1; ++r) v[it][r] = buf[pad16(j + r * items)];
+        dft_reg<R1, INV>(v[it]);
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < ipt; ++it) {
+      const int j = lt + it * TG;
+      if (items % TG == 0 || j < items) {
+#pragma unroll
+        for (int r = 0; r < R1; ++r) buf[pad16(j * R1 + r)] = v[it][r];
+      }
+    }
+    __syncthreads();
+  }
+  if constexpr (C::NPASS > 1) {
+    int Ns = R1;
+#pragma unroll
+    for (int ps = 1; ps < C::NPASS; ++ps) {
+      constexpr int items = N / 16;
+      constexpr int ipt = (items + TG - 1) / TG;
+      float2 v[ipt][16];
+#pragma unroll
+      for (int it = 0; it < ipt; ++it) {
+        const int j = lt + it * TG;
+        if (items % TG == 0 || j < items) {
+          const int k = j % Ns;
+          float2 w = tw[k * (N / (Ns * 16))];
+          if (INV) w.y = -w.y;
+          float2 pw[16];
+          powers<16>(w, pw);
+#pragma unroll
+          for (int r = 0; r < 16; ++r) {
+            const float2 x = buf[pad16(j + r * items)];
+            v[it][r] = r > 0 ? cmul(x, pw[r]) : x;
+          }
+          dft_reg<16, INV>(v[it]);
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int it = 0; it < ipt; ++it) {
+        const int j = lt + it * TG;
+        if (items % TG == 0 || j < items) {
+          const int k = j % Ns;
+          const int base = (j / Ns) * Ns * 16 + k;
+#pragma unroll
+          for (int r = 0; r < 16; ++r) buf[pad16(base + r * Ns)] = v[it][r];
+        }
+      }
+      __syncthreads();
+      Ns *= 16;
+    }
+  }
+}
+
+struct Fft3dArgs {
+  int n1, n2, n3;
+  int L1, L2, L3;
+  int H1, H2, H3;         // L_p / 2 + 1
+  const float* m;         // [3][n3][n2][n1]
+  float2* s1;             // [3][H1][n3][n2]; S3 [n3][H1][L2] aliases it
+  float2* s2;             // [3][L2][H1][n3]; S4 [n2][n3][H1] aliases it
+  float* phi;             // [n3][n2][n1]
+  const float* kst;       // [3][H1][H2][H3]: Im K^(q) on the octant
+  const float2* tw;       // exp(-2 pi i m / N) of this pass's axis, m < N
+};
+
+template <int LOGN>
+__device__ __forceinline__ void load_twiddles(float2* tw, const float2* src) {
+  for (int i = threadIdx.x; i < (1 << LOGN); i += blockDim.x) tw[i] = __ldg(src + i);
+}
+
+// Fibre in[0..n) zero-padded to N into the pad16-indexed buffer; every load
+// is issued before the first shared-memory store.
+template <int LOGN>
+__device__ __forceinline__ void stage_fibre(float2* buf, int lt, const float2* in, int n) {
+  using C = F3<LOGN>;
+  float2 ld[C::PER];
+#pragma unroll
+  for (int i = 0; i < C::PER; ++i) {
+    const int j = lt + i * C::TG;
+    ld[i] = j < n ? __ldg(in + j) : make_float2(0.f, 0.f);
+  }
+#pragma unroll
+  for (int i = 0; i < C::PER; ++i) buf[pad16(lt + i * C::TG)] = ld[i];
+}
+
+// cp.async of one float2 into shared memory; zero-filled (nothing read) when !pred.
+__device__ __forceinline__ void cp_async8(float2* dst, const float2* src, bool pred) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(pred ? 8 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int PENDING>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(PENDING) : "memory");
+}
+
+// The same fibre copy as stage_fibre, asynchronous (cp.async); `in` must be
+// a valid address even when n == 0.
+template <int LOGN>
+__device__ __forceinline__ void copy_fibre_async(float2* buf, int lt, const float2* in, int n) {
+  using C = F3<LOGN>;
+#pragma unroll
+  for (int i = 0; i < C::PER; ++i) {
+    const int j = lt + i * C::TG;
+    cp_async8(buf + pad16(j), j < n ? in + j : in, j < n);
+  }
+}
+
+// P1: real FFT along i1 of fibre pairs (i2, i2 + 1) at fixed (c, i3).
+template <int LOGN>
+__global__ void __launch_bounds__(F3<LOGN>::BLOCK) fft3d_p1_kernel(const __grid_constant__ Fft3dArgs a) {
+  using C = F3<LOGN>;
+  constexpr int N = C::N, TG = C::TG, G = C::G, BS = C::BS, T = 2 * G;
+  extern __shared__ float2 sm3[];
+  float2* tw = sm3;
+  float2* bufs = sm3 + N;
+  load_twiddles<LOGN>(tw, a.tw);
+  const int g = threadIdx.x / TG, lt = threadIdx.x % TG;
+  float2* buf = bufs + g * BS;
+  const int tiles = (a.n2 + T - 1) / T;
+  const int tile = blockIdx.x % tiles;
+  const int ci3 = blockIdx.x / tiles;  // c * n3 + i3
+  const int i2a = tile * T + 2 * g;
+  const float* row = a.m + (size_t)ci3 * a.n2 * a.n1;
+  const bool va = i2a < a.n2, vb = i2a + 1 < a.n2;
+  // all loads of the fibre pair in flight before the first shared-memory store
+  float2 ld[C::PER];
+#pragma unroll
+  for (int i = 0; i < C::PER; ++i) {
+    const int j = lt + i * TG;
+    float x = 0.f, y = 0.f;
+    if (j < a.n1) {
+      if (va) x = __ldg(row + (size_t)i2a * a.n1 + j);
+      if (vb) y = __ldg(row + (size_t)(i2a + 1) * a.n1 + j);
+    }
+    ld[i] = make_float2(x, y);
+  }
+#pragma unroll
+  for (int i = 0; i < C::PER; ++i) buf[pad16(lt + i * TG)] = ld[i];
+  __syncthreads();
+  fft_pad<LOGN, false>(buf, lt, tw);
+  // X_a = (Z_w + conj Z_{N-w}) / 2, X_b = (Z_w - conj Z_{N-w}) / 2i; stored at S1[c][w][i3][i2]
+  const int c = ci3 / a.n3, i3 = ci3 % a.n3;
+  float2* out = a.s1 + (size_t)c * a.H1 * a.n3 * a.n2 + (size_t)i3 * a.n2 + (size_t)tile * T;
+  const int lim = min(T, a.n2 - tile * T);
+  for (int idx = threadIdx.x; idx < a.H1 * T; idx += C::BLOCK) {
+    const int w = idx / T, g2 = idx % T;
+    if (g2 >= lim) continue;
+    const float2* b = bufs + (g2 >> 1) * BS;
+    const float2 Z = b[pad16(w)], Zc = b[pad16((N - w) & (N - 1))];
+    const float2 X = (g2 & 1) ? make_float2(0.5f * (Z.y + Zc.y), -0.5f * (Z.x - Zc.x))
+                              : make_float2(0.5f * (Z.x + Zc.x), 0.5f * (Z.y - Zc.y));
+    out[(size_t)w * a.n3 * a.n2 + g2] = X;
+  }
+}
+
+// P2: FFT along i2 (n2 samples zero-padded to L2) of fibres i3 at fixed (c, w1).
+template <int LOGN>
+__global__ void __launch_bounds__(F3<LOGN>::BLOCK) fft3d_p2_kernel(const __grid_constant__ Fft3dArgs a) {
+  using C = F3<LOGN>;
+  constexpr int N = C::N, TG = C::TG, G = C::G, BS = C::BS;
+  extern __shared__ float2 sm3[];
+  float2* tw = sm3;
+  float2* bufs = sm3 + N;
+  load_twiddles<LOGN>(tw, a.tw);
+  const int g = threadIdx.x / TG, lt = threadIdx.x % TG;
+  float2* buf = bufs + g * BS;
+  const int tiles = (a.n3 + G - 1) / G;
+  const int tile = blockIdx.x % tiles;
+  const int cw1 = blockIdx.x / tiles;  // c * H1 + w1
+  const int i3 = tile * G + g;
+  const float2* in = a.s1 + ((size_t)cw1 * a.n3 + i3) * a.n2;
+  stage_fibre<LOGN>(buf, lt, in, i3 < a.n3 ? a.n2 : 0);
+  __syncthreads();
+  fft_pad<LOGN, false>(buf, lt, tw);
+  const int c = cw1 / a.H1, w1 = cw1 % a.H1;
+  float2* out = a.s2 + (size_t)c * a.L2 * a.H1 * a.n3 + (size_t)w1 * a.n3 + (size_t)tile * G;
+  const int lim = min(G, a.n3 - tile * G);
+  for (int idx = threadIdx.x; idx < N * G; idx += C::BLOCK) {
+    const int w2 = idx / G, gg = idx % G;
+    if (gg < lim) out[(size_t)w2 * a.H1 * a.n3 + gg] = bufs[gg * BS + pad16(w2)];
+  }
+}
+
+// P3: at fixed w1, fibres w2 along i3: forward FFT of each component,
+// times K^(c), summed over c in registers, inverse FFT, i3 < n3 kept.  The
+// next component's fibres are copied in (cp.async, zero-filled past n3) into
+// a second buffer while the current one is transformed.
+template <int LOGN>
+__global__ void __launch_bounds__(F3<LOGN>::BLOCK3) fft3d_p3_kernel(const __grid_constant__ Fft3dArgs a) {
+  using C = F3<LOGN>;
+  constexpr int N = C::N, TG = C::TG, G = C::G3, BS = C::BS, PER = C::PER;
+  extern __shared__ float2 sm3[];
+  float2* tw = sm3;
+  const int g = threadIdx.x / TG, lt = threadIdx.x % TG;
+  float2* bufc[2] = {sm3 + N + g * BS, sm3 + N + (G + g) * BS};
+  const int tiles = (a.L2 + G - 1) / G;
+  const int tile = blockIdx.x % tiles;
+  const int w1 = blockIdx.x / tiles;
+  const int w2 = tile * G + g;
+  const bool valid = w2 < a.L2;
+  const int w2f = w2 <= a.L2 / 2 ? w2 : a.L2 - w2;
+  const int nload = valid ? a.n3 : 0;
+  auto fibre = [&](int c) { return a.s2 + (((size_t)c * a.L2 + (valid ? w2 : 0)) * a.H1 + w1) * a.n3; };
+  copy_fibre_async<LOGN>(bufc[0], lt, fibre(0), nload);
+  cp_async_commit();
+  load_twiddles<LOGN>(tw, a.tw);
+  float2 acc[PER];
+#pragma unroll
+  for (int j = 0; j < PER; ++j) acc[j] = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    float2* buf = bufc[c & 1];
+    if (c < 2) {
+      copy_fibre_async<LOGN>(bufc[(c + 1) & 1], lt, fibre(c + 1), nload);
+      cp_async_commit();
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();
+    fft_pad<LOGN, false>(buf, lt, tw);
+    const float* krow = a.kst + (((size_t)c * a.H1 + w1) * a.H2 + (valid ? w2f : 0)) * a.H3;
+    const float s2sign = (c == 1 && w2 > a.L2 / 2) ? -1.f : 1.f;
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+      const int w3 = lt + j * TG;
+      const int w3f = w3 <= N / 2 ? w3 : N - w3;
+      float kv = __ldg(krow + w3f) * s2sign;
+      if (c == 2 && w3 > N / 2) kv = -kv;
+      const float2 Z = buf[pad16(w3)];
+      // (i kv) Z
+      acc[j].x = fmaf(-kv, Z.y, acc[j].x);
+      acc[j].y = fmaf(kv, Z.x, acc[j].y);
+    }
+    __syncthreads();
+  }
+  float2* buf = bufc[0];
+#pragma unroll
+  for (int j = 0; j < PER; ++j) buf[pad16(lt + j * TG)] = acc[j];
+  __syncthreads();
+  fft_pad<LOGN, true>(buf, lt, tw);
+  float2* out = a.s1 + (size_t)w1 * a.L2 + (size_t)tile * G;  // S3[i3][w1][w2]
+  const int lim = min(G, a.L2 - tile * G);
+  const float2* bufs = sm3 + N;
+  for (int idx = threadIdx.x; idx < a.n3 * G; idx += C::BLOCK3) {
+    const int i3 = idx / G, gg = idx % G;
+    if (gg < lim) out[(size_t)i3 * a.H1 * a.L2 + gg] = bufs[gg * BS + pad16(i3)];
+  }
+}
+
+// P4: inverse FFT along w2 of fibres w1 at fixed i3, i2 < n2 kept.
+template <int LOGN>
+__global__ void __launch_bounds__(F3<LOGN>::BLOCK) fft3d_p4_kernel(const __grid_constant__ Fft3dArgs a) {
+  using C = F3<LOGN>;
+  constexpr int N = C::N, TG = C::TG, G = C::G, BS = C::BS;
+  extern __shared__ float2 sm3[];
+  float2* tw = sm3;
+  float2* bufs = sm3 + N;
+  load_twiddles<LOGN>(tw, a.tw);
+  const int g = threadIdx.x / TG, lt = threadIdx.x % TG;
+  float2* buf = bufs + g * BS;
+  const int tiles = (a.H1 + G - 1) / G;
+  const int tile = blockIdx.x % tiles;
+  const int i3 = blockIdx.x / tiles;
+  const int w1 = tile * G + g;
+  const float2* in = a.s1 + ((size_t)i3 * a.H1 + w1) * a.L2;
+  stage_fibre<LOGN>(buf, lt, in, w1 < a.H1 ? N : 0);
+  __syncthreads();
+  fft_pad<LOGN, true>(buf, lt, tw);
+  float2* out = a.s2 + (size_t)i3 * a.H1 + (size_t)tile * G;  // S4[i2][i3][w1]
+  const int lim = min(G, a.H1 - tile * G);
+  for (int idx = threadIdx.x; idx < a.n2 * G; idx += C::BLOCK) {
+    const int i2 = idx / G, gg = idx % G;
+    if (gg < lim) out[(size_t)i2 * a.n3 * a.H1 + gg] = bufs[gg * BS + pad16(i2)];
+  }
+}
+
+// P5: inverse real FFT along w1 of fibre pairs f, f + 1 (f = i2 n3 + i3).
+template <int LOGN>
+__global__ void __launch_bounds__(F3<LOGN>::BLOCK) fft3d_p5_kernel(const __grid_constant__ Fft3dArgs a) {
+  using C = F3<LOGN>;
+  constexpr int N = C::N, TG = C::TG, G = C::G, BS = C::BS, T = 2 * G;
+  extern __shared__ float2 sm3[];
+  float2* tw = sm3;
+  float2* bufs = sm3 + N;
+  load_twiddles<LOGN>(tw, a.tw);
+  const int g = threadIdx.x / TG, lt = threadIdx.x % TG;
+  float2* buf = bufs + g * BS;
+  const int nf = a.n2 * a.n3;
+  const int fa = blockIdx.x * T + 2 * g;
+  const bool va = fa < nf, vb = fa + 1 < nf;
+  const float2* ina = a.s2 + (size_t)fa * a.H1;
+  const float2* inb = ina + a.H1;
+  const float2 zero = make_float2(0.f, 0.f);
+  // two rounds of loads (half the bins each), all of a round in flight before its stores
+  constexpr int HALF = C::PER > 1 ? C::PER / 2 : 1;
+#pragma unroll
+  for (int i0 = 0; i0 < C::PER; i0 += HALF) {
+    float2 la[HALF], lb[HALF];
+#pragma unroll
+    for (int i = 0; i < HALF; ++i) {
+      const int w = lt + (i0 + i) * TG;
+      const int src = w <= N / 2 ? w : N - w;
+      la[i] = va ? __ldg(ina + src) : zero;
+      lb[i] = vb ? __ldg(inb + src) : zero;
+    }
+#pragma unroll
+    for (int i = 0; i < HALF; ++i) {
+      const int w = lt + (i0 + i) * TG;
+      // Hermitian extension X_w = conj X_{N-w}; the imaginary parts at w = 0, N/2 are dropped
+      float2 xa = la[i], xb = lb[i];
+      if (w > N / 2) {
+        xa.y = -xa.y;
+        xb.y = -xb.y;
+      }
+      if (w == 0 || w == N / 2) {
+        xa.y = 0.f;
+        xb.y = 0.f;
+      }
+      buf[pad16(w)] = make_float2(xa.x - xb.y, xa.y + xb.x);  // X_a + i X_b
+    }
+  }
+  __syncthreads();
+  fft_pad<LOGN, true>(buf, lt, tw);
+  if (va) {
+    const int i2 = fa / a.n3, i3 = fa % a.n3;
+    float* o = a.phi + ((size_t)i3 * a.n2 + i2) * a.n1;
+    for (int j = lt; j < a.n1; j += TG) o[j] = buf[pad16(j)].x;
+  }
+  if (vb) {
+    const int i2 = (fa + 1) / a.n3, i3 = (fa + 1) % a.n3;
+    float* o = a.phi + ((size_t)i3 * a.n2 + i2) * a.n1;
+    for (int j = lt; j < a.n1; j += TG) o[j] = buf[pad16(j)].y;
+  }
+}
+
+// ---------------------------------------------------------------- setup
+
+// sym[k][type][p][w] (w <= L_p/2), FP64: the DFT of the circulant embedding
+// of generator row (k, type, p) divided by L_p; type 0 (E, even): the real
+// part E0 + 2 sum_d E_d cos(2 pi w d / L); type 1 (F, odd): the imaginary part
+// -2 sum_d F_d sin(2 pi w d / L).  Angles are reduced exactly ((w d) mod L).
+__global__ void fft3d_symbols_kernel(int M, int glen, int hstride, int n1, int n2, int n3, int L1, int L2, int L3,
+                                     const double* gen64, double* sym) {
+  const long total = (long)M * 2 * 3 * hstride;
+  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long)gridDim.x * blockDim.x) {
+    const int w = (int)(idx % hstride);
+    long rest = idx / hstride;
+    const int p = (int)(rest % 3);
+    rest /= 3;
+    const int type = (int)(rest % 2);
+    const int k = (int)(rest / 2);
+    const int n = p == 0 ? n1 : (p == 1 ? n2 : n3);
+    const int L = p == 0 ? L1 : (p == 1 ? L2 : L3);
+    double val = 0.0;
+    if (w <= L / 2) {
+      const double* t = gen64 + (((long)k * 2 + type) * 3 + p) * glen + (n - 1);  // t[d], |d| < n
+      double acc = 0.0;
+      for (int d = 1; d < n; ++d) {
+        const int r = (int)(((long)w * d) % L);
+        double sn, cs;
+        sincospi(2.0 * (double)r / (double)L, &sn, &cs);
+        acc += type == 0 ? t[d] * cs : t[d] * sn;
+      }
+      val = type == 0 ? (t[0] + 2.0 * acc) : (-2.0 * acc);
+      val /= (double)L;
+    }
+    sym[idx] = val;
+  }
+}
+
+// kst[c][w1][w2][w3] = sum_k scale_k S_{k,c,1}[w1] S_{k,c,2}[w2] S_{k,c,3}[w3]
+// (FP64 sum, one rounding to FP32); scale_k = c s omega_k.  One block per
+// (c, w1, w2), threads over w3.
+__global__ void fft3d_kernel_kernel(int M, int hstride, int H1, int H2, int H3, const double* scale,
+                                    const double* sym, float* kst) {
+  __shared__ double a[kMaxTerms];
+  const int w2 = blockIdx.x % H2;
+  const int cw1 = blockIdx.x / H2;
+  const int w1 = cw1 % H1, c = cw1 / H1;
+  const int t1 = c == 0, t2 = c == 1, t3 = c == 2;
+  for (int k = threadIdx.x; k < M; k += blockDim.x)
+    a[k] = scale[k] * sym[(((long)k * 2 + t1) * 3 + 0) * hstride + w1] *
+           sym[(((long)k * 2 + t2) * 3 + 1) * hstride + w2];
+  __syncthreads();
+  float* out = kst + ((size_t)cw1 * H2 + w2) * H3;
+  for (int w3 = threadIdx.x; w3 < H3; w3 += blockDim.x) {
+    double acc = 0.0;
+    for (int k = 0; k < M; ++k) acc += a[k] * sym[(((long)k * 2 + t3) * 3 + 2) * hstride + w3];
+    out[w3] = (float)acc;
+  }
+}
+
+struct Fft3dState {
+  int logL[3];
+  float* kst = nullptr;
+  float2* s1 = nullptr;
+  float2* s2 = nullptr;
+  size_t s1_elems = 0, s2_elems = 0;
+};
+
+static int log2_exact(int v) {
+  int l = 0;
+  while ((1 << l) < v) ++l;
+  return l;
+}
+
+template <int LOGN>
+static demag_status launch_pass(demag_plan* P, int pass, const Fft3dArgs& a, int blocks, cudaStream_t st) {
+  using C = F3<LOGN>;
+  const void* fn = pass == 1 ? (const void*)fft3d_p1_kernel<LOGN>
+                 : pass == 2 ? (const void*)fft3d_p2_kernel<LOGN>
+                 : pass == 3 ? (const void*)fft3d_p3_kernel<LOGN>
+                 : pass == 4 ? (const void*)fft3d_p4_kernel<LOGN>
+                             : (const void*)fft3d_p5_kernel<LOGN>;
+  // the attribute is set on first use per kernel and device (so that later
+  // launches, e.g. under stream capture, make no attribute calls)
+  static unsigned long long done[6] = {0, 0, 0, 0, 0, 0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const unsigned long long bit = 1ull << (dev & 63);
+  const size_t smem = pass == 3 ? C::smem3 : C::smem;
+  if (smem > 48 * 1024 && !(done[pass] & bit)) {
+    DEMAG_CUDA(P, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    done[pass] |= bit;
+  }
+  switch (pass) {
+    case 1: DEMAG_LAUNCH(P, kFamFFT3D, st, fft3d_p1_kernel<LOGN><<<blocks, C::BLOCK, C::smem, st>>>(a)); break;
+    case 2: DEMAG_LAUNCH(P, kFamFFT3D, st, fft3d_p2_kernel<LOGN><<<blocks, C::BLOCK, C::smem, st>>>(a)); break;
+    case 3: DEMAG_LAUNCH(P, kFamFFT3D, st, fft3d_p3_kernel<LOGN><<<blocks, C::BLOCK3, C::smem3, st>>>(a)); break;
+    case 4: DEMAG_LAUNCH(P, kFamFFT3D, st, fft3d_p4_kernel<LOGN><<<blocks, C::BLOCK, C::smem, st>>>(a)); break;
+    default: DEMAG_LAUNCH(P, kFamFFT3D, st, fft3d_p5_kernel<LOGN><<<blocks, C::BLOCK, C::smem, st>>>(a)); break;
+  }
+  DEMAG_LAUNCHED(P, "fft3d pass");
+  return DEMAG_OK;
+}
+
+static demag_status dispatch_pass(demag_plan* P, int logn, int pass, const Fft3dArgs& a, int blocks,
+                                  cudaStream_t st) {
+  switch (logn) {
+    case 1: return launch_pass<1>(P, pass, a, blocks, st);
+    case 2: return launch_pass<2>(P, pass, a, blocks, st);
+    case 3: return launch_pass<3>(P, pass, a, blocks, st);
+    case 4: return launch_pass<4>(P, pass, a, blocks, st);
+    case 5: return launch_pass<5>(P, pass, a, blocks, st);
+    case 6: return launch_pass<6>(P, pass, a, blocks, st);
+    case 7: return launch_pass<7>(P, pass, a, blocks, st);
+    case 8: return launch_pass<8>(P, pass, a, blocks, st);
+    case 9: return launch_pass<9>(P, pass, a, blocks, st);
+    case 10: return launch_pass<10>(P, pass, a, blocks, st);
+    default: return set_error(P, DEMAG_EUNSUPPORTED, "fft3d: FFT length 2^%d not supported", logn);
+  }
+}
+
+demag_status fft3d_prepare(demag_plan* P, cudaStream_t st) {
+  if (P->f3) return DEMAG_OK;
+  for (int p = 0; p < 3; ++p)
+    if (P->L[p] > (1 << kFft3dMaxLog))
+      return set_error(P, DEMAG_EUNSUPPORTED, "demag_apply_full_fft: n[%d] = %d exceeds %d", p, P->n[p],
+                       (1 << kFft3dMaxLog) / 2);
+  if (!P->twid[0] || !P->twid[1] || !P->twid[2])
+    return set_error(P, DEMAG_EUNSUPPORTED, "demag_apply_full_fft: plan has no FFT twiddles");
+  Fft3dState* S = new (std::nothrow) Fft3dState();
+  if (!S) return set_error(P, DEMAG_ENOMEM, "host allocation failed");
+  const int n1 = P->n[0], n2 = P->n[1], n3 = P->n[2];
+  const int L1 = P->L[0], L2 = P->L[1], L3 = P->L[2];
+  const int H1 = L1 / 2 + 1, H2 = L2 / 2 + 1, H3 = L3 / 2 + 1;
+  for (int p = 0; p < 3; ++p) S->logL[p] = log2_exact(P->L[p]);
+  // S1 holds [3][H1][n3][n2] and later S3 [n3][H1][L2]; S2 [3][L2][H1][n3] and later S4 [n2][n3][H1]
+  S->s1_elems = std::max((size_t)3 * H1 * n3 * n2, (size_t)n3 * H1 * L2);
+  S->s2_elems = std::max((size_t)3 * L2 * H1 * n3, (size_t)n2 * n3 * H1);
+  const int hstride = std::max(H1, std::max(H2, H3));
+  double* sym = nullptr;
+  auto fail = [&](cudaError_t e, const char* what) {
+    cudaFree(sym);
+    cudaFree(S->kst);
+    cudaFree(S->s1);
+    cudaFree(S->s2);
+    delete S;
+    return cuda_error(P, e, what);
+  };
+  cudaError_t e;
+  if ((e = cudaMalloc(&S->kst, sizeof(float) * 3 * (size_t)H1 * H2 * H3)) != cudaSuccess) return fail(e, "malloc kst");
+  if ((e = cudaMalloc(&S->s1, sizeof(float2) * S->s1_elems)) != cudaSuccess) return fail(e, "malloc s1");
+  if ((e = cudaMalloc(&S->s2, sizeof(float2) * S->s2_elems)) != cudaSuccess) return fail(e, "malloc s2");
+  if ((e = cudaMalloc(&sym, sizeof(double) * (size_t)P->M * 6 * hstride)) != cudaSuccess) return fail(e, "malloc sym");
+  {
+    const long total = (long)P->M * 6 * hstride;
+    int blocks = (int)((total + 255) / 256);
+    if (blocks > 152 * 32) blocks = 152 * 32;
+    DEMAG_LAUNCH(P, kFamSetup, st,
+                 fft3d_symbols_kernel<<<blocks, 256, 0, st>>>(P->M, P->glen, hstride, n1, n2, n3, L1, L2, L3,
+                                                              P->gen64, sym));
+    if ((e = cudaGetLastError()) != cudaSuccess) return fail(e, "fft3d_symbols_kernel");
+    DEMAG_LAUNCH(P, kFamSetup, st,
+                 fft3d_kernel_kernel<<<3 * H1 * H2, 256, 0, st>>>(P->M, hstride, H1, H2, H3, P->scale, sym,
+                                                                  S->kst));
+    if ((e = cudaGetLastError()) != cudaSuccess) return fail(e, "fft3d_kernel_kernel");
+  }
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return fail(e, "fft3d setup");
+  cudaFree(sym);
+  P->f3 = S;
+  return DEMAG_OK;
+}
+
+void fft3d_destroy(demag_plan* P) {
+  Fft3dState* S = static_cast<Fft3dState*>(P->f3);
+  if (!S) return;
+  cudaFree(S->kst);
+  cudaFree(S->s1);
+  cudaFree(S->s2);
+  delete S;
+  P->f3 = nullptr;
+}
+
+demag_status fft3d_forward(demag_plan* P, const float* m, float* phi, cudaStream_t st) {
+  demag_status rc = fft3d_prepare(P, st);
+  if (rc != DEMAG_OK) return rc;
+  const Fft3dState* S = static_cast<const Fft3dState*>(P->f3);
+  Fft3dArgs a;
+  a.n1 = P->n[0];
+  a.n2 = P->n[1];
+  a.n3 = P->n[2];
+  a.L1 = P->L[0];
+  a.L2 = P->L[1];
+  a.L3 = P->L[2];
+  a.H1 = a.L1 / 2 + 1;
+  a.H2 = a.L2 / 2 + 1;
+  a.H3 = a.L3 / 2 + 1;
+  a.m = m;
+  a.s1 = S->s1;
+  a.s2 = S->s2;
+  a.phi = phi;
+  a.kst = S->kst;
+  const int l1 = S->logL[0], l2 = S->logL[1], l3 = S->logL[2];
+  const int G1 = f3_fibres(1 << l1), G2 = f3_fibres(1 << l2), G3 = f3_fibres_p3(1 << l3);
+  auto cdiv = [](long x, long y) { return (int)((x + y - 1) / y); };
+  a.tw = P->twid[0];
+  if ((rc = dispatch_pass(P, l1, 1, a, 3 * a.n3 * cdiv(a.n2, 2 * G1), st)) != DEMAG_OK) return rc;
+  a.tw = P->twid[1];
+  if ((rc = dispatch_pass(P, l2, 2, a, 3 * a.H1 * cdiv(a.n3, G2), st)) != DEMAG_OK) return rc;
+  a.tw = P->twid[2];
+  if ((rc = dispatch_pass(P, l3, 3, a, a.H1 * cdiv(a.L2, G3), st)) != DEMAG_OK) return rc;
+  a.tw = P->twid[1];
+  if ((rc = dispatch_pass(P, l2, 4, a, a.n3 * cdiv(a.H1, G2), st)) != DEMAG_OK) return rc;
+  a.tw = P->twid[0];
+  return dispatch_pass(P, l1, 5, a, cdiv((long)a.n2 * a.n3, 2 * G1), st);
+}
+
+}  // namespace demag
+
+using namespace demag;
+
+extern "C" demag_status demag_apply_full_fft(demag_plan* P, const float* m, float* phi, void* stream) {
+  if (!P) return set_error(nullptr, DEMAG_EINVAL, "demag_apply_full_fft: plan is NULL");
+  if (!m || !phi) return set_error(P, DEMAG_EINVAL, "demag_apply_full_fft: NULL pointer");
+  return fft3d_forward(P, m, phi, (cudaStream_t)stream);
+}

@@ -62,6 +62,8 @@ struct demag_plan {
   int* dev_status = nullptr; // device status word (DEMAG_ETIMEOUT etc.)
   // tensor-core state (opaque, owned by full_tc.cu)
   void* tc = nullptr;
+  // 3D FFT convolution state (opaque, owned by fft3d.cu): dense Fourier kernel and spectra
+  void* f3 = nullptr;
   // energy / gradient scratch: phi, D^T m (1 field each) and P^T D^T m (3 fields)
   float* ews = nullptr;
 
@@ -89,7 +91,8 @@ struct demag_plan {
 namespace demag {
 
 // kernel families for demag_profile_read
-enum Family { kFamGemmSimt = 0, kFamGemmTc = 1, kFamFFT = 2, kFamSplit = 3, kFamSetup = 4, kFamEnergy = 5, kFamMisc = 6 };
+enum Family { kFamGemmSimt = 0, kFamGemmTc = 1, kFamFFT = 2, kFamSplit = 3, kFamSetup = 4, kFamEnergy = 5, kFamMisc = 6,
+             kFamFFT3D = 7 };
 
 void prof_begin(demag_plan* P, int family, cudaStream_t st);
 void prof_end(demag_plan* P, cudaStream_t st);
@@ -150,6 +153,10 @@ size_t tc_workspace_bytes(const demag_plan* plan, demag_precision prec);
 demag_status tc_sync_status(demag_plan* plan, cudaStream_t st);
 bool tc_ready(const demag_plan* plan, demag_precision prec);
 void tc_destroy(demag_plan* plan);
+
+// 3D FFT convolution (fft3d.cu)
+demag_status fft3d_forward(demag_plan* plan, const float* m, float* phi, cudaStream_t st);
+void fft3d_destroy(demag_plan* plan);
 
 // setup kernels (plan.cu)
 struct GridInfo {

@@ -247,6 +247,7 @@ static void free_plan_buffers(demag_plan* P) {
   for (auto e : P->prof_pool) cudaEventDestroy(e);
   P->prof_pool.clear();
   tc_destroy(P);
+  fft3d_destroy(P);
   energy_destroy(P);
 }
 

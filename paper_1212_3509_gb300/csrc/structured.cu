@@ -61,10 +61,6 @@ struct ToepLaunch {
   const float2* sympair;  // [M][2][3][pairstride]: (s_f, s_{N-f})
 };
 
-__device__ __forceinline__ int pad16(int i) { return i + (i >> 4); }
-// pad16(i + r * S) = pad16(i) + r * (S + S / 16) when S is a multiple of 16
-template <int S> struct PadStride { static constexpr int value = S + S / 16; };
-
 template <int LOGN> struct ToepCfg {
   static constexpr int N = 1 << LOGN;
   static constexpr int L = 2 * N;
@@ -93,28 +89,6 @@ struct TwN {
   TwSmem s;
   __device__ __forceinline__ float2 operator()(int m) const { return s.L(2 * m); }
 };
-
-// pw[r] = w^r for r < R by a product tree of depth <= 4 (w^2, w^4, w^8 by
-// squaring, the rest as one product of those), so each power carries only a
-// few roundings of the table value w.
-template <int R>
-__device__ __forceinline__ void powers(float2 w, float2 (&pw)[R]) {
-  pw[0] = make_float2(1.f, 0.f);
-  if constexpr (R > 1) pw[1] = w;
-  if constexpr (R > 2) pw[2] = cmul(w, w);
-  if constexpr (R > 3) pw[3] = cmul(pw[2], w);
-  if constexpr (R > 4) {
-    pw[4] = cmul(pw[2], pw[2]);
-    pw[5] = cmul(pw[4], w);
-    pw[6] = cmul(pw[4], pw[2]);
-    pw[7] = cmul(pw[4], pw[3]);
-  }
-  if constexpr (R > 8) {
-    pw[8] = cmul(pw[4], pw[4]);
-#pragma unroll
-    for (int r = 9; r < R; ++r) pw[r] = cmul(pw[8], pw[r - 8]);
-  }
-}
 
 // The first 8 outputs of an inverse 16-point DFT (the kept half of the last
 // pass): two 8-point DFTs of the even and odd inputs and the "+" half of the
