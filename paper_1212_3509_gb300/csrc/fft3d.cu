@@ -44,8 +44,9 @@ constexpr int kFft3dMaxLog = 10;  // L_p <= 1024 (n_p <= 512)
 constexpr int f3_tg(int N) { return N / 16 < 1 ? 1 : (N / 16 > 32 ? 32 : N / 16); }
 constexpr int f3_block(int N) { return 16 * f3_tg(N) < 256 ? 256 : 16 * f3_tg(N); }
 constexpr int f3_fibres(int N) { return f3_block(N) / f3_tg(N); }
-// P3 double-buffers its fibres: half the fibres per block at N = 1024 (shared memory)
-constexpr int f3_fibres_p3(int N) { return N >= 1024 ? f3_fibres(N) / 2 : f3_fibres(N); }
+// P3 double-buffers its fibres: half the fibres per block from N = 512 (two
+// blocks of 256 threads per SM at 128 registers instead of one of 512)
+constexpr int f3_fibres_p3(int N) { return N >= 512 ? f3_fibres(N) / 2 : f3_fibres(N); }
 
 template <int LOGN> struct F3 {
   static constexpr int N = 1 << LOGN;
@@ -60,12 +61,17 @@ template <int LOGN> struct F3 {
   static constexpr int BLOCK3 = G3 * TG;
   static constexpr size_t smem3 = ((size_t)N + (size_t)2 * G3 * BS) * sizeof(float2);
   static constexpr int PER = N / TG;  // bins per thread of its fibre
+  // N = 2^(4j+1): the radix-2 pass is skipped on zero-padded input (forward)
+  // and folded into the reader of the first N/2 outputs (inverse)
+  static constexpr bool FOLD = LOGN >= 5 && LOGN % 4 == 1;
+  static constexpr int SL = FOLD ? N / 2 : N;  // staged length of a forward input
 };
 
 // In-place complex FFT of length N on a pad16-indexed buffer by the TG
 // threads of one group (Stockham, natural order in and out).  First a pass
 // of radix R1 (no twiddles), then radix-16 passes.  tw[m] = exp(-2 pi i m / N).
-// Every thread of the block must call it (it synchronises the block).
+// A group lies inside one warp (TG <= 32), so the passes synchronise the
+// warp only; every lane of the warp must call it.
 template <int LOGN, bool INV>
 __device__ __forceinline__ void fft_pad(float2* buf, int lt, const float2* tw) {
   using C = F3<LOGN>;
@@ -83,7 +89,7 @@ __device__ __forceinline__ void fft_pad(float2* buf, int lt, const float2* tw) {
         dft_reg<R1, INV>(v[it]);
       }
     }
-    __syncthreads();
+    __syncwarp();
 #pragma unroll
     for (int it = 0; it < ipt; ++it) {
       const int j = lt + it * TG;
@@ -92,7 +98,7 @@ __device__ __forceinline__ void fft_pad(float2* buf, int lt, const float2* tw) {
         for (int r = 0; r < R1; ++r) buf[pad16(j * R1 + r)] = v[it][r];
       }
     }
-    __syncthreads();
+    __syncwarp();
   }
   if constexpr (C::NPASS > 1) {
     int Ns = R1;
@@ -118,7 +124,7 @@ __device__ __forceinline__ void fft_pad(float2* buf, int lt, const float2* tw) {
           dft_reg<16, INV>(v[it]);
         }
       }
-      __syncthreads();
+      __syncwarp();
 #pragma unroll
       for (int it = 0; it < ipt; ++it) {
         const int j = lt + it * TG;
@@ -129,9 +135,107 @@ __device__ __forceinline__ void fft_pad(float2* buf, int lt, const float2* tw) {
           for (int r = 0; r < 16; ++r) buf[pad16(base + r * Ns)] = v[it][r];
         }
       }
-      __syncthreads();
+      __syncwarp();
       Ns *= 16;
     }
+  }
+}
+
+// One in-place radix-16 Stockham pass over sub-transforms of size Ns.  With
+// DUP the pass input is y[m] = x[m >> 1]: the output of a radix-2 first pass
+// on an input with x[j] = 0 for j >= N/2, which only duplicates
+// (y[2j] = y[2j+1] = x[j]) and is therefore not done.
+template <int LOGN, bool INV, bool DUP>
+__device__ __forceinline__ void r16_pass(float2* buf, int Ns, int lt, const float2* tw) {
+  using C = F3<LOGN>;
+  constexpr int N = C::N, TG = C::TG;
+  constexpr int items = N / 16;
+  constexpr int ipt = (items + TG - 1) / TG;
+  float2 v[ipt][16];
+#pragma unroll
+  for (int it = 0; it < ipt; ++it) {
+    const int j = lt + it * TG;
+    if (items % TG == 0 || j < items) {
+      const int k = j % Ns;
+#pragma unroll
+      for (int r = 0; r < 16; ++r) {
+        // pad16(i + r S) = pad16(i) + r (S + S/16) when S is a multiple of 16
+        if constexpr (DUP && (items / 2) % 16 == 0)
+          v[it][r] = buf[pad16(j >> 1) + r * PadStride<items / 2>::value];
+        else if constexpr (!DUP && items % 16 == 0)
+          v[it][r] = buf[pad16(j) + r * PadStride<items>::value];
+        else
+          v[it][r] = buf[pad16(DUP ? ((j + r * items) >> 1) : (j + r * items))];
+      }
+      if (Ns > 1) {  // (Ns = 1: all twiddles are 1)
+        float2 w = tw[k * (N / (Ns * 16))];
+        if (INV) w.y = -w.y;
+        float2 pw[16];
+        powers<16>(w, pw);
+#pragma unroll
+        for (int r = 1; r < 16; ++r) v[it][r] = cmul(v[it][r], pw[r]);
+      }
+      dft_reg<16, INV>(v[it]);
+    }
+  }
+  __syncwarp();
+#pragma unroll
+  for (int it = 0; it < ipt; ++it) {
+    const int j = lt + it * TG;
+    if (items % TG == 0 || j < items) {
+      const int k = j % Ns;
+      const int base = (j / Ns) * Ns * 16 + k;
+      if (Ns % 16 == 0) {
+        const int b0 = pad16(base), step = Ns + (Ns >> 4);
+#pragma unroll
+        for (int r = 0; r < 16; ++r) buf[b0 + r * step] = v[it][r];
+      } else {
+#pragma unroll
+        for (int r = 0; r < 16; ++r) buf[pad16(base + r * Ns)] = v[it][r];
+      }
+    }
+  }
+  __syncwarp();
+}
+
+// Forward FFT of a fibre staged in its first SL slots (zeros past the data).
+template <int LOGN>
+__device__ __forceinline__ void fwd_fft(float2* buf, int lt, const float2* tw) {
+  using C = F3<LOGN>;
+  if constexpr (C::FOLD) {
+    r16_pass<LOGN, false, true>(buf, 2, lt, tw);
+#pragma unroll
+    for (int ps = 2, Ns = 32; ps < C::NPASS; ++ps, Ns *= 16) r16_pass<LOGN, false, false>(buf, Ns, lt, tw);
+  } else {
+    fft_pad<LOGN, false>(buf, lt, tw);
+  }
+}
+
+// Inverse FFT whose outputs k < N/2 are then read with inv_out (with FOLD the
+// last radix-2 pass is left to inv_out).
+template <int LOGN>
+__device__ __forceinline__ void inv_fft(float2* buf, int lt, const float2* tw) {
+  using C = F3<LOGN>;
+  if constexpr (C::FOLD) {
+#pragma unroll
+    for (int ps = 1, Ns = 1; ps < C::NPASS; ++ps, Ns *= 16) r16_pass<LOGN, true, false>(buf, Ns, lt, tw);
+  } else {
+    fft_pad<LOGN, true>(buf, lt, tw);
+  }
+}
+
+// Output k < N/2 of inv_fft: with FOLD the last radix-2 butterfly (Ns = N/2)
+// y_k = x_k + conj(W_N^k) x_{k + N/2}.
+template <int LOGN>
+__device__ __forceinline__ float2 inv_out(const float2* buf, int k, const float2* tw) {
+  using C = F3<LOGN>;
+  if constexpr (C::FOLD) {
+    float2 w = tw[k];
+    w.y = -w.y;
+    const float2 a = buf[pad16(k)], b = buf[pad16(k + C::N / 2)];
+    return cadd(a, cmul(b, w));
+  } else {
+    return buf[pad16(k)];
   }
 }
 
@@ -154,17 +258,21 @@ __device__ __forceinline__ void load_twiddles(float2* tw, const float2* src) {
 
 // Fibre in[0..n) zero-padded to N into the pad16-indexed buffer; every load
 // is issued before the first shared-memory store.
-template <int LOGN>
+template <int LOGN, int LEN>
 __device__ __forceinline__ void stage_fibre(float2* buf, int lt, const float2* in, int n) {
   using C = F3<LOGN>;
-  float2 ld[C::PER];
+  constexpr int CNT = (LEN + C::TG - 1) / C::TG;
+  float2 ld[CNT];
 #pragma unroll
-  for (int i = 0; i < C::PER; ++i) {
+  for (int i = 0; i < CNT; ++i) {
     const int j = lt + i * C::TG;
     ld[i] = j < n ? __ldg(in + j) : make_float2(0.f, 0.f);
   }
 #pragma unroll
-  for (int i = 0; i < C::PER; ++i) buf[pad16(lt + i * C::TG)] = ld[i];
+  for (int i = 0; i < CNT; ++i) {
+    const int j = lt + i * C::TG;
+    if (LEN % C::TG == 0 || j < LEN) buf[pad16(j)] = ld[i];
+  }
 }
 
 // cp.async of one float2 into shared memory; zero-filled (nothing read) when !pred.
@@ -180,13 +288,14 @@ __device__ __forceinline__ void cp_async_wait() {
 
 // The same fibre copy as stage_fibre, asynchronous (cp.async); `in` must be
 // a valid address even when n == 0.
-template <int LOGN>
+template <int LOGN, int LEN>
 __device__ __forceinline__ void copy_fibre_async(float2* buf, int lt, const float2* in, int n) {
   using C = F3<LOGN>;
+  constexpr int CNT = (LEN + C::TG - 1) / C::TG;
 #pragma unroll
-  for (int i = 0; i < C::PER; ++i) {
+  for (int i = 0; i < CNT; ++i) {
     const int j = lt + i * C::TG;
-    cp_async8(buf + pad16(j), j < n ? in + j : in, j < n);
+    if (LEN % C::TG == 0 || j < LEN) cp_async8(buf + pad16(j), j < n ? in + j : in, j < n);
   }
 }
 
@@ -208,9 +317,10 @@ __global__ void __launch_bounds__(F3<LOGN>::BLOCK) fft3d_p1_kernel(const __grid_
   const float* row = a.m + (size_t)ci3 * a.n2 * a.n1;
   const bool va = i2a < a.n2, vb = i2a + 1 < a.n2;
   // all loads of the fibre pair in flight before the first shared-memory store
-  float2 ld[C::PER];
+  constexpr int CNT = C::SL / TG;
+  float2 ld[CNT];
 #pragma unroll
-  for (int i = 0; i < C::PER; ++i) {
+  for (int i = 0; i < CNT; ++i) {
     const int j = lt + i * TG;
     float x = 0.f, y = 0.f;
     if (j < a.n1) {
@@ -220,21 +330,35 @@ __global__ void __launch_bounds__(F3<LOGN>::BLOCK) fft3d_p1_kernel(const __grid_
     ld[i] = make_float2(x, y);
   }
 #pragma unroll
-  for (int i = 0; i < C::PER; ++i) buf[pad16(lt + i * TG)] = ld[i];
+  for (int i = 0; i < CNT; ++i) buf[pad16(lt + i * TG)] = ld[i];
   __syncthreads();
-  fft_pad<LOGN, false>(buf, lt, tw);
+  fwd_fft<LOGN>(buf, lt, tw);
+  __syncthreads();  // the split step reads every fibre pair's buffer
   // X_a = (Z_w + conj Z_{N-w}) / 2, X_b = (Z_w - conj Z_{N-w}) / 2i; stored at S1[c][w][i3][i2]
   const int c = ci3 / a.n3, i3 = ci3 % a.n3;
   float2* out = a.s1 + (size_t)c * a.H1 * a.n3 * a.n2 + (size_t)i3 * a.n2 + (size_t)tile * T;
   const int lim = min(T, a.n2 - tile * T);
-  for (int idx = threadIdx.x; idx < a.H1 * T; idx += C::BLOCK) {
-    const int w = idx / T, g2 = idx % T;
-    if (g2 >= lim) continue;
+  auto split = [&](int w, int g2) {
     const float2* b = bufs + (g2 >> 1) * BS;
     const float2 Z = b[pad16(w)], Zc = b[pad16((N - w) & (N - 1))];
-    const float2 X = (g2 & 1) ? make_float2(0.5f * (Z.y + Zc.y), -0.5f * (Z.x - Zc.x))
-                              : make_float2(0.5f * (Z.x + Zc.x), 0.5f * (Z.y - Zc.y));
-    out[(size_t)w * a.n3 * a.n2 + g2] = X;
+    return (g2 & 1) ? make_float2(0.5f * (Z.y + Zc.y), -0.5f * (Z.x - Zc.x))
+                    : make_float2(0.5f * (Z.x + Zc.x), 0.5f * (Z.y - Zc.y));
+  };
+  if constexpr (C::BLOCK % T == 0) {
+    // thread -> fibre g2 = tid % T (fixed), rows w = tid / T + k (BLOCK / T)
+    constexpr int WS = C::BLOCK / T;
+    const int g2 = threadIdx.x % T;
+    if (g2 < lim) {
+      const size_t step = (size_t)WS * a.n3 * a.n2;
+      float2* dst = out + g2 + (size_t)(threadIdx.x / T) * a.n3 * a.n2;
+#pragma unroll 4
+      for (int w = threadIdx.x / T; w < a.H1; w += WS, dst += step) *dst = split(w, g2);
+    }
+  } else {
+    for (int idx = threadIdx.x; idx < a.H1 * T; idx += C::BLOCK) {
+      const int w = idx / T, g2 = idx % T;
+      if (g2 < lim) out[(size_t)w * a.n3 * a.n2 + g2] = split(w, g2);
+    }
   }
 }
 
@@ -254,15 +378,21 @@ __global__ void __launch_bounds__(F3<LOGN>::BLOCK) fft3d_p2_kernel(const __grid_
   const int cw1 = blockIdx.x / tiles;  // c * H1 + w1
   const int i3 = tile * G + g;
   const float2* in = a.s1 + ((size_t)cw1 * a.n3 + i3) * a.n2;
-  stage_fibre<LOGN>(buf, lt, in, i3 < a.n3 ? a.n2 : 0);
+  stage_fibre<LOGN, C::SL>(buf, lt, in, i3 < a.n3 ? a.n2 : 0);
   __syncthreads();
-  fft_pad<LOGN, false>(buf, lt, tw);
+  fwd_fft<LOGN>(buf, lt, tw);
+  __syncthreads();  // the transposed store reads every fibre's buffer
   const int c = cw1 / a.H1, w1 = cw1 % a.H1;
   float2* out = a.s2 + (size_t)c * a.L2 * a.H1 * a.n3 + (size_t)w1 * a.n3 + (size_t)tile * G;
   const int lim = min(G, a.n3 - tile * G);
-  for (int idx = threadIdx.x; idx < N * G; idx += C::BLOCK) {
-    const int w2 = idx / G, gg = idx % G;
-    if (gg < lim) out[(size_t)w2 * a.H1 * a.n3 + gg] = bufs[gg * BS + pad16(w2)];
+  // thread -> fibre gg = tid % G (fixed), rows w2 = tid / G + k TG
+  const int gg = threadIdx.x % G;
+  if (gg < lim) {
+    const float2* src = bufs + gg * BS;
+    const size_t step = (size_t)TG * a.H1 * a.n3;
+    float2* dst = out + gg + (size_t)(threadIdx.x / G) * a.H1 * a.n3;
+#pragma unroll 4
+    for (int w2 = threadIdx.x / G; w2 < N; w2 += TG, dst += step) *dst = src[pad16(w2)];
   }
 }
 
@@ -271,7 +401,7 @@ __global__ void __launch_bounds__(F3<LOGN>::BLOCK) fft3d_p2_kernel(const __grid_
 // next component's fibres are copied in (cp.async, zero-filled past n3) into
 // a second buffer while the current one is transformed.
 template <int LOGN>
-__global__ void __launch_bounds__(F3<LOGN>::BLOCK3) fft3d_p3_kernel(const __grid_constant__ Fft3dArgs a) {
+__global__ void __launch_bounds__(F3<LOGN>::BLOCK3, LOGN <= 9 ? 2 : 1) fft3d_p3_kernel(const __grid_constant__ Fft3dArgs a) {
   using C = F3<LOGN>;
   constexpr int N = C::N, TG = C::TG, G = C::G3, BS = C::BS, PER = C::PER;
   extern __shared__ float2 sm3[];
@@ -286,7 +416,7 @@ __global__ void __launch_bounds__(F3<LOGN>::BLOCK3) fft3d_p3_kernel(const __grid
   const int w2f = w2 <= a.L2 / 2 ? w2 : a.L2 - w2;
   const int nload = valid ? a.n3 : 0;
   auto fibre = [&](int c) { return a.s2 + (((size_t)c * a.L2 + (valid ? w2 : 0)) * a.H1 + w1) * a.n3; };
-  copy_fibre_async<LOGN>(bufc[0], lt, fibre(0), nload);
+  copy_fibre_async<LOGN, C::SL>(bufc[0], lt, fibre(0), nload);
   cp_async_commit();
   load_twiddles<LOGN>(tw, a.tw);
   float2 acc[PER];
@@ -296,14 +426,18 @@ __global__ void __launch_bounds__(F3<LOGN>::BLOCK3) fft3d_p3_kernel(const __grid
   for (int c = 0; c < 3; ++c) {
     float2* buf = bufc[c & 1];
     if (c < 2) {
-      copy_fibre_async<LOGN>(bufc[(c + 1) & 1], lt, fibre(c + 1), nload);
+      copy_fibre_async<LOGN, C::SL>(bufc[(c + 1) & 1], lt, fibre(c + 1), nload);
       cp_async_commit();
       cp_async_wait<1>();
     } else {
       cp_async_wait<0>();
     }
-    __syncthreads();
-    fft_pad<LOGN, false>(buf, lt, tw);
+    // the fibre's copies were issued by its own warp; the twiddle table by the block
+    if (c == 0)
+      __syncthreads();
+    else
+      __syncwarp();
+    fwd_fft<LOGN>(buf, lt, tw);
     const float* krow = a.kst + (((size_t)c * a.H1 + w1) * a.H2 + (valid ? w2f : 0)) * a.H3;
     const float s2sign = (c == 1 && w2 > a.L2 / 2) ? -1.f : 1.f;
 #pragma unroll
@@ -317,19 +451,24 @@ __global__ void __launch_bounds__(F3<LOGN>::BLOCK3) fft3d_p3_kernel(const __grid
       acc[j].x = fmaf(-kv, Z.y, acc[j].x);
       acc[j].y = fmaf(kv, Z.x, acc[j].y);
     }
-    __syncthreads();
+    __syncwarp();
   }
   float2* buf = bufc[0];
 #pragma unroll
   for (int j = 0; j < PER; ++j) buf[pad16(lt + j * TG)] = acc[j];
-  __syncthreads();
-  fft_pad<LOGN, true>(buf, lt, tw);
+  __syncwarp();
+  inv_fft<LOGN>(buf, lt, tw);
+  __syncthreads();  // the transposed store reads every fibre's buffer
   float2* out = a.s1 + (size_t)w1 * a.L2 + (size_t)tile * G;  // S3[i3][w1][w2]
   const int lim = min(G, a.L2 - tile * G);
   const float2* bufs = sm3 + N;
-  for (int idx = threadIdx.x; idx < a.n3 * G; idx += C::BLOCK3) {
-    const int i3 = idx / G, gg = idx % G;
-    if (gg < lim) out[(size_t)i3 * a.H1 * a.L2 + gg] = bufs[gg * BS + pad16(i3)];
+  const int gg = threadIdx.x % G;
+  if (gg < lim) {
+    const float2* src = bufs + gg * BS;
+    const size_t step = (size_t)TG * a.H1 * a.L2;
+    float2* dst = out + gg + (size_t)(threadIdx.x / G) * a.H1 * a.L2;
+#pragma unroll 4
+    for (int i3 = threadIdx.x / G; i3 < a.n3; i3 += TG, dst += step) *dst = inv_out<LOGN>(src, i3, tw);
   }
 }
 
@@ -349,14 +488,19 @@ __global__ void __launch_bounds__(F3<LOGN>::BLOCK) fft3d_p4_kernel(const __grid_
   const int i3 = blockIdx.x / tiles;
   const int w1 = tile * G + g;
   const float2* in = a.s1 + ((size_t)i3 * a.H1 + w1) * a.L2;
-  stage_fibre<LOGN>(buf, lt, in, w1 < a.H1 ? N : 0);
+  stage_fibre<LOGN, N>(buf, lt, in, w1 < a.H1 ? N : 0);
   __syncthreads();
-  fft_pad<LOGN, true>(buf, lt, tw);
+  inv_fft<LOGN>(buf, lt, tw);
+  __syncthreads();  // the transposed store reads every fibre's buffer
   float2* out = a.s2 + (size_t)i3 * a.H1 + (size_t)tile * G;  // S4[i2][i3][w1]
   const int lim = min(G, a.H1 - tile * G);
-  for (int idx = threadIdx.x; idx < a.n2 * G; idx += C::BLOCK) {
-    const int i2 = idx / G, gg = idx % G;
-    if (gg < lim) out[(size_t)i2 * a.n3 * a.H1 + gg] = bufs[gg * BS + pad16(i2)];
+  const int gg = threadIdx.x % G;
+  if (gg < lim) {
+    const float2* src = bufs + gg * BS;
+    const size_t step = (size_t)TG * a.n3 * a.H1;
+    float2* dst = out + gg + (size_t)(threadIdx.x / G) * a.n3 * a.H1;
+#pragma unroll 4
+    for (int i2 = threadIdx.x / G; i2 < a.n2; i2 += TG, dst += step) *dst = inv_out<LOGN>(src, i2, tw);
   }
 }
 
@@ -406,16 +550,13 @@ __global__ void __launch_bounds__(F3<LOGN>::BLOCK) fft3d_p5_kernel(const __grid_
     }
   }
   __syncthreads();
-  fft_pad<LOGN, true>(buf, lt, tw);
-  if (va) {
-    const int i2 = fa / a.n3, i3 = fa % a.n3;
-    float* o = a.phi + ((size_t)i3 * a.n2 + i2) * a.n1;
-    for (int j = lt; j < a.n1; j += TG) o[j] = buf[pad16(j)].x;
-  }
-  if (vb) {
-    const int i2 = (fa + 1) / a.n3, i3 = (fa + 1) % a.n3;
-    float* o = a.phi + ((size_t)i3 * a.n2 + i2) * a.n1;
-    for (int j = lt; j < a.n1; j += TG) o[j] = buf[pad16(j)].y;
+  inv_fft<LOGN>(buf, lt, tw);
+  float* oa = a.phi + ((size_t)(fa % a.n3) * a.n2 + fa / a.n3) * a.n1;
+  float* ob = a.phi + ((size_t)((fa + 1) % a.n3) * a.n2 + (fa + 1) / a.n3) * a.n1;
+  for (int j = lt; j < a.n1; j += TG) {
+    const float2 v = inv_out<LOGN>(buf, j, tw);
+    if (va) oa[j] = v.x;
+    if (vb) ob[j] = v.y;
   }
 }
 
