@@ -91,6 +91,32 @@ typedef struct demag_plan demag_plan;
  * On success *out receives the plan; on failure *out is set to NULL. */
 demag_status demag_build_factors(const demag_grid_desc* desc, demag_plan** out, void* stream);
 
+/* A non-uniform tensor grid (Sec. 3.1 notation: each axis partitioned into
+ * arbitrary sub-intervals I_j = [edges[p][j], edges[p][j+1]], collocation at
+ * their midpoints).  edges[p] points to n[p] + 1 strictly increasing finite
+ * doubles in HOST memory, read only during the build; n[0] is the fastest
+ * index as in demag_grid_desc. */
+typedef struct {
+  int n[3];
+  const double* edges[3];
+  int R;
+  double c0;
+} demag_grid_edges_desc;
+
+/* Build a plan for a non-uniform tensor grid.  The factors of Eq. sep_integrands
+ * are then dense n_p x n_p matrices (cell integrals with the true limits, FP64,
+ * the same erf/erfcx/expm1 forms as the uniform generators), no longer Toeplitz,
+ * and the domain is scaled by its longest edge as in the uniform case.  Such a
+ * plan serves the full format: demag_apply_full in all four precisions
+ * (batched and graph forms included) and demag_apply_adjoint in DEMAG_FP32 and
+ * DEMAG_FP64 (transposed factors: P^T = -P holds only on uniform grids).  Every
+ * path that needs Toeplitz structure or uniform spacing (CP / Tucker / TT, the
+ * 3D FFT convolution, the finite-difference stray field and energy, the
+ * analytic stray field, the split-precision adjoint, generator and symbol
+ * copies) returns DEMAG_EUNSUPPORTED for it.  Synchronizes `stream`. */
+demag_status demag_build_factors_nonuniform(const demag_grid_edges_desc* desc, demag_plan** out,
+                                            void* stream);
+
 /* Release every device buffer the plan owns.  NULL is accepted. */
 void demag_plan_destroy(demag_plan* plan);
 

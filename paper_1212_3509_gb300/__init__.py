@@ -17,6 +17,7 @@ from ._abi import (  # noqa: F401
     demag_apply_cp,
     demag_apply_cp_batched,
     demag_apply_full,
+    demag_build_factors_nonuniform,
     demag_apply_full_fft,
     demag_apply_full_batched,
     demag_apply_tt,

@@ -29,6 +29,11 @@ class GridDesc(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int * 3), ("h", ctypes.c_double * 3), ("R", ctypes.c_int), ("c0", ctypes.c_double)]
 
 
+class GridEdgesDesc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int * 3), ("edges", ctypes.POINTER(ctypes.c_double) * 3), ("R", ctypes.c_int),
+                ("c0", ctypes.c_double)]
+
+
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"libdemag is not built ({LIB_PATH} missing); run paper_1212_3509_gb300.build.build()")
 
@@ -47,6 +52,7 @@ _SIGS = {
     "demag_symbols_size": (_sz, [_vp]),
     "demag_apply_full": (_i, [_vp, _vp, _vp, _i, _vp]),
     "demag_apply_full_fft": (_i, [_vp, _vp, _vp, _vp]),
+    "demag_build_factors_nonuniform": (_i, [ctypes.POINTER(GridEdgesDesc), ctypes.POINTER(_vp), _vp]),
     "demag_apply_full_batched": (_i, [ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i, _i, _vp]),
     "demag_graph_create_batched": (_i, [ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i, _i,
                                         ctypes.POINTER(_vp)]),
@@ -155,6 +161,24 @@ def demag_build_factors(n, h, R: int, c0: float = 2.15, stream=None) -> Plan:
     out = _vp()
     _check(lib.demag_build_factors(ctypes.byref(d), ctypes.byref(out), _stream(stream)))
     return Plan(out.value, n, h, R, c0)
+
+
+def demag_build_factors_nonuniform(edges, R: int, c0: float = 2.15, stream=None) -> Plan:
+    """Plan for a non-uniform tensor grid: edges[p] = the n_p + 1 increasing cell edges of axis p (i1 first)."""
+    arrs = [(ctypes.c_double * len(e))(*[float(v) for v in e]) for e in edges]
+    if len(arrs) != 3 or any(len(a) < 2 for a in arrs):
+        raise ValueError("edges: three arrays of at least two cell edges")
+    n = [len(a) - 1 for a in arrs]
+    d = GridEdgesDesc((ctypes.c_int * 3)(*n),
+                      (ctypes.POINTER(ctypes.c_double) * 3)(*[ctypes.cast(a, ctypes.POINTER(ctypes.c_double))
+                                                              for a in arrs]),
+                      int(R), float(c0))
+    out = _vp()
+    _check(lib.demag_build_factors_nonuniform(ctypes.byref(d), ctypes.byref(out), _stream(stream)))
+    mean_h = [(float(e[-1]) - float(e[0])) / (len(e) - 1) for e in edges]
+    plan = Plan(out.value, n, mean_h, R, c0)
+    plan.edges = [tuple(float(v) for v in e) for e in edges]
+    return plan
 
 
 def demag_plan_destroy(plan: Plan):

@@ -129,6 +129,8 @@ using namespace demag;
 extern "C" demag_status demag_stray_field(demag_plan* P, const float* phi, float* hd, void* stream) {
   if (!P) return set_error(nullptr, DEMAG_EINVAL, "demag_stray_field: plan is NULL");
   if (!phi || !hd) return set_error(P, DEMAG_EINVAL, "demag_stray_field: NULL pointer");
+  demag_status u = require_uniform(P, "demag_stray_field");  // uniform difference stencils
+  if (u != DEMAG_OK) return u;
   return fd_gradient(P, phi, hd, -1.f, (cudaStream_t)stream);
 }
 
@@ -136,6 +138,8 @@ extern "C" demag_status demag_energy(demag_plan* P, const float* m, double* ener
                                      demag_precision prec, void* stream) {
   if (!P) return set_error(nullptr, DEMAG_EINVAL, "demag_energy: plan is NULL");
   if (!m || !energy) return set_error(P, DEMAG_EINVAL, "demag_energy: NULL pointer");
+  demag_status u = require_uniform(P, "demag_energy");  // uniform difference stencils and cell volume
+  if (u != DEMAG_OK) return u;
   cudaStream_t st = (cudaStream_t)stream;
   const long N = (long)field_size(P);
   if (!P->ews) DEMAG_CUDA(P, cudaMalloc(&P->ews, sizeof(float) * 5 * N));

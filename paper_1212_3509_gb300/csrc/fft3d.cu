@@ -681,6 +681,8 @@ static demag_status dispatch_pass(demag_plan* P, int logn, int pass, const Fft3d
 
 demag_status fft3d_prepare(demag_plan* P, cudaStream_t st) {
   if (P->f3) return DEMAG_OK;
+  demag_status u = require_uniform(P, "demag_apply_full_fft");  // a convolution needs Toeplitz factors
+  if (u != DEMAG_OK) return u;
   for (int p = 0; p < 3; ++p)
     if (P->L[p] > (1 << kFft3dMaxLog))
       return set_error(P, DEMAG_EUNSUPPORTED, "demag_apply_full_fft: n[%d] = %d exceeds %d", p, P->n[p],

@@ -82,6 +82,8 @@ extern "C" demag_status demag_stray_field_exact(demag_plan* P, const float* m, f
                                                 void* stream) {
   if (!P) return set_error(nullptr, DEMAG_EINVAL, "demag_stray_field_exact: plan is NULL");
   if (!m || !hd) return set_error(P, DEMAG_EINVAL, "demag_stray_field_exact: NULL pointer");
+  demag_status u = require_uniform(P, "demag_stray_field_exact");  // derivative generators are Toeplitz
+  if (u != DEMAG_OK) return u;
   if ((int)prec < 0 || (int)prec > (int)DEMAG_BF16X3)
     return set_error(P, DEMAG_EINVAL, "demag_stray_field_exact: unknown precision %d", (int)prec);
   cudaStream_t st = (cudaStream_t)stream;

@@ -188,7 +188,8 @@ static cudaError_t launch_batch(demag_plan* P, const BatchBuilder& bb, cudaStrea
 // axis-3 blocks multiplied by S_k = c s omega_k.
 template <typename T>
 __global__ void dense_factor_kernel(int M, int glen, int n0, int n1, int n2, size_t tgroup, size_t off1,
-                                    size_t off2, const double* gen, const double* scale, T* out) {
+                                    size_t off2, const double* gen, const double* scale, T* out,
+                                    const double* fac = nullptr, bool transpose = false) {
   const size_t total = (size_t)M * 2 * tgroup;
   for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
        idx += (size_t)gridDim.x * blockDim.x) {
@@ -200,7 +201,13 @@ __global__ void dense_factor_kernel(int M, int glen, int n0, int n1, int n2, siz
     else if (e < off2) { axis = 1; n = n1; local = e - off1; }
     else { axis = 2; n = n2; local = e - off2; }
     int i = (int)(local / n), jj = (int)(local % n);
-    double v = gen[(kt * 3 + axis) * glen + (i - jj + n - 1)];
+    if (transpose) {
+      const int t = i;
+      i = jj;
+      jj = t;
+    }
+    // Toeplitz generator (uniform grid) or the full matrix (non-uniform grid)
+    double v = fac ? fac[kt * tgroup + (e - local) + (size_t)i * n + jj] : gen[(kt * 3 + axis) * glen + (i - jj + n - 1)];
     if (axis == 2) v *= scale[kt / 2];
     out[idx] = (T)v;
   }
@@ -221,16 +228,41 @@ demag_status ensure_dense_factors(demag_plan* P, demag_precision prec, cudaStrea
     DEMAG_LAUNCH(P, kFamSetup, st,
                  dense_factor_kernel<double><<<blocks, 256, 0, st>>>(P->M, P->glen, P->n[0], P->n[1], P->n[2],
                                                                      P->tgroup, P->toff[1], P->toff[2], P->gen64,
-                                                                     P->scale, P->T64));
+                                                                     P->scale, P->T64, P->fac64));
   } else {
     if (P->T32) return DEMAG_OK;
     DEMAG_CUDA(P, cudaMalloc(&P->T32, sizeof(float) * total));
     DEMAG_LAUNCH(P, kFamSetup, st,
                  dense_factor_kernel<float><<<blocks, 256, 0, st>>>(P->M, P->glen, P->n[0], P->n[1], P->n[2],
                                                                     P->tgroup, P->toff[1], P->toff[2], P->gen64,
-                                                                    P->scale, P->T32));
+                                                                    P->scale, P->T32, P->fac64));
   }
   DEMAG_LAUNCHED(P, "dense_factor_kernel");
+  return DEMAG_OK;
+}
+
+// Transposed factor tables of a non-uniform plan, for the adjoint on CUDA
+// cores: (P^(q))^T = c sum_k omega_k U3^T (x) U2^T (x) U1^T.
+static demag_status ensure_transposed_factors(demag_plan* P, demag_precision prec, cudaStream_t st) {
+  const size_t total = (size_t)P->M * 2 * P->tgroup;
+  int blocks = (int)((total + 255) / 256);
+  if (blocks > 152 * 64) blocks = 152 * 64;
+  if (prec == DEMAG_FP64) {
+    if (P->T64t) return DEMAG_OK;
+    DEMAG_CUDA(P, cudaMalloc(&P->T64t, sizeof(double) * total));
+    DEMAG_LAUNCH(P, kFamSetup, st,
+                 dense_factor_kernel<double><<<blocks, 256, 0, st>>>(P->M, P->glen, P->n[0], P->n[1], P->n[2],
+                                                                     P->tgroup, P->toff[1], P->toff[2], P->gen64,
+                                                                     P->scale, P->T64t, P->fac64, true));
+  } else {
+    if (P->T32t) return DEMAG_OK;
+    DEMAG_CUDA(P, cudaMalloc(&P->T32t, sizeof(float) * total));
+    DEMAG_LAUNCH(P, kFamSetup, st,
+                 dense_factor_kernel<float><<<blocks, 256, 0, st>>>(P->M, P->glen, P->n[0], P->n[1], P->n[2],
+                                                                    P->tgroup, P->toff[1], P->toff[2], P->gen64,
+                                                                    P->scale, P->T32t, P->fac64, true));
+  }
+  DEMAG_LAUNCHED(P, "dense_factor_kernel (transposed)");
   return DEMAG_OK;
 }
 
@@ -308,9 +340,12 @@ static demag_status simt_forward(demag_plan* P, const T* m, T* phi, const T* con
   return DEMAG_OK;
 }
 
-// adjoint: y (1 field) -> g (3 fields): g^(q) = -P^(q) y
+// adjoint: y (1 field) -> g (3 fields).  Uniform grid: g^(q) = -P^(q) y with
+// the forward tables (sign -1); non-uniform grid: the transposed tables and
+// sign +1.
 template <typename T>
-static demag_status simt_adjoint(demag_plan* P, const T* y, T* g, const T* Tm, T* ws, cudaStream_t st) {
+static demag_status simt_adjoint(demag_plan* P, const T* y, T* g, const T* Tm, T* ws, cudaStream_t st,
+                                 float sign = -1.f) {
   constexpr int BM = 16 * SimtCfg<T>::TM;
   const int n1 = P->n[0], n2 = P->n[1], n3 = P->n[2];
   const size_t N = field_size(P);
@@ -336,7 +371,7 @@ static demag_status simt_adjoint(demag_plan* P, const T* y, T* g, const T* Tm, T
   for (int q = 0; q < 3; ++q) {
     std::vector<std::pair<const void*, const void*>> pairs;
     for (int k = 0; k < M; ++k) pairs.push_back({Z + (3 * k + q) * N, factor(P, Tm, k, q == 2 ? 1 : 0, 2)});
-    b3.add(n2 * n1, n3, n3, n3, n3, n2 * n1, g + q * N, -1.f, pairs, BM);
+    b3.add(n2 * n1, n3, n3, n3, n3, n2 * n1, g + q * N, sign, pairs, BM);
   }
   cudaError_t e = launch_batch<T>(P, b3, st);
   if (e != cudaSuccess) return cuda_error(P, e, "gemm_tn_kernel (adjoint mode 3)");
@@ -424,19 +459,26 @@ demag_status simt_field(demag_plan* P, const float* m, float* hd, demag_precisio
 }
 
 demag_status full_adjoint(demag_plan* P, const float* y, float* g, demag_precision prec, cudaStream_t st) {
-  if (prec == DEMAG_TF32X3 || prec == DEMAG_BF16X3) return tc_adjoint(P, y, g, prec, st);
-  demag_status s = ensure_dense_factors(P, prec, st);
+  if (prec == DEMAG_TF32X3 || prec == DEMAG_BF16X3) {
+    // the split-precision adjoint programs rely on P^T = -P (uniform grids)
+    demag_status u = require_uniform(P, "demag_apply_adjoint in split precision");
+    if (u != DEMAG_OK) return u;
+    return tc_adjoint(P, y, g, prec, st);
+  }
+  demag_status s = P->nonuniform ? ensure_transposed_factors(P, prec, st) : ensure_dense_factors(P, prec, st);
   if (s != DEMAG_OK) return s;
   s = ensure_workspace(P, prec);
   if (s != DEMAG_OK) return s;
   const size_t N = field_size(P);
-  if (prec == DEMAG_FP32) return simt_adjoint<float>(P, y, g, P->T32, (float*)P->ws[prec].base, st);
+  const float sign = P->nonuniform ? 1.f : -1.f;
+  if (prec == DEMAG_FP32)
+    return simt_adjoint<float>(P, y, g, P->nonuniform ? P->T32t : P->T32, (float*)P->ws[prec].base, st, sign);
   double* ws = (double*)P->ws[prec].base;
   double* y64 = ws + (3 * (size_t)P->M + 3) * N;
   double* g64 = y64 + 3 * N;
   DEMAG_LAUNCH(P, kFamSplit, st, convert_kernel<double><<<conv_blocks(N), 256, 0, st>>>(y, y64, N));
   DEMAG_LAUNCHED(P, "convert_kernel");
-  s = simt_adjoint<double>(P, y64, g64, P->T64, ws, st);
+  s = simt_adjoint<double>(P, y64, g64, P->nonuniform ? P->T64t : P->T64, ws, st, sign);
   if (s != DEMAG_OK) return s;
   DEMAG_LAUNCH(P, kFamSplit, st, narrow_kernel<<<conv_blocks(3 * N), 256, 0, st>>>(g64, g, 3 * N));
   DEMAG_LAUNCHED(P, "narrow_kernel");

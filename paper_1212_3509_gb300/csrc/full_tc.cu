@@ -526,7 +526,8 @@ __global__ void split_rows_kernel(const __grid_constant__ SplitList L) {
 // carries the scale c s omega_k.
 template <class F>
 __global__ void tc_factor_kernel(int M, int glen, int axis, int n, int ld, const double* gen, const double* scale,
-                                 typename F::T* hi, typename F::T* lo) {
+                                 typename F::T* hi, typename F::T* lo, const double* fac, size_t tgroup,
+                                 size_t toff) {
   const long long total = (long long)M * 2 * n * n;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
@@ -534,7 +535,9 @@ __global__ void tc_factor_kernel(int M, int glen, int axis, int n, int ld, const
     const long long t = i / n;
     const int ii = (int)(t % n);
     const int kt = (int)(t / n);  // k*2 + type
-    double v = gen[((long long)kt * 3 + axis) * glen + (ii - jj + n - 1)];
+    // Toeplitz generator (uniform grid) or the full matrix (non-uniform grid)
+    double v = fac ? fac[(size_t)kt * tgroup + toff + (size_t)ii * n + jj]
+                   : gen[((long long)kt * 3 + axis) * glen + (ii - jj + n - 1)];
     if (axis == 2) v *= scale[kt / 2];
     typename F::T h, l;
     F::split((float)v, h, l);
@@ -637,6 +640,8 @@ struct SmallStage {
   int rows, n, axis;      // rows per field; axis length (contraction and output columns)
   int glen;
   const double* gen;      // [M][2][3][glen]
+  const double* fac;      // non-uniform grid: full matrices [M][2][tgroup] (gen unused), else NULL
+  long long fac_group, fac_off;  // tgroup and this axis' block offset
   const double* scale;    // [M], applied on the third axis
   const TcJob* jobs;
   const short2* pairs;    // (A field, matrix 2k + type)
@@ -667,7 +672,8 @@ __global__ void __launch_bounds__(256) small_stage_kernel(const __grid_constant_
       const int a = rem / n, kk = rem - a * n;
       const short2 pr = S.pairs[J.pair0 + p0 + p];
       const int k = pr.y >> 1;
-      double v = S.gen[((long long)pr.y * 3 + S.axis) * S.glen + (a - kk + n - 1)];
+      double v = S.fac ? S.fac[(long long)pr.y * S.fac_group + S.fac_off + (long long)a * n + kk]
+                       : S.gen[((long long)pr.y * 3 + S.axis) * S.glen + (a - kk + n - 1)];
       if (S.axis == 2) v *= S.scale[k];
       sB[i] = (float)v;
     }
@@ -1047,6 +1053,9 @@ static demag_status build_programs(demag_plan* P, TcState* S, const CUtensorMap 
       Q.axis = stage;
       Q.glen = P->glen;
       Q.gen = P->gen64;
+      Q.fac = P->fac64;
+      Q.fac_group = (long long)P->tgroup;
+      Q.fac_off = (long long)P->toff[stage];
       Q.scale = P->scale;
       Q.jobs = G.jobs;
       Q.pairs = G.pairs;
@@ -1082,7 +1091,7 @@ static demag_status prepare_form(demag_plan* P, TcState* S, cudaStream_t st) {
     DEMAG_LAUNCH(P, kFamSetup, st,
                  tc_factor_kernel<F><<<grid_blocks(total), 256, 0, st>>>(
                      M, P->glen, p, P->n[p], S->ld[p], P->gen64, P->scale, (typename F::T*)S->B[p][0],
-                     (typename F::T*)S->B[p][1]));
+                     (typename F::T*)S->B[p][1], P->fac64, P->tgroup, P->toff[p]));
     DEMAG_LAUNCHED(P, "tc_factor_kernel");
   }
   static unsigned long long attr = 0;  // devices whose kernel attribute is set
@@ -1535,7 +1544,7 @@ static demag_status prepare_field(demag_plan* P, TcState* S, cudaStream_t st) {
     DEMAG_LAUNCH(P, kFamSetup, st,
                  tc_factor_kernel<F><<<grid_blocks(total), 256, 0, st>>>(
                      M, P->glen, p, P->n[p], S->ld[p], P->gend, P->scale, (typename F::T*)S->Bd[p][0],
-                     (typename F::T*)S->Bd[p][1]));
+                     (typename F::T*)S->Bd[p][1], nullptr, 0, 0));
     DEMAG_LAUNCHED(P, "tc_factor_kernel");
   }
   int t0[6];
@@ -1550,6 +1559,7 @@ static demag_status prepare_field(demag_plan* P, TcState* S, cudaStream_t st) {
     }
     S->small_dprog[st3] = S->small_prog[kFwd1 + st3];
     S->small_dprog[st3].gen = P->gend;
+    S->small_dprog[st3].fac = nullptr;
     t0[2 * st3] = 0;
     t0[2 * st3 + 1] = G.ntiles;
   }

@@ -53,6 +53,13 @@ struct demag_plan {
   // axis-3 blocks carry the scale c*s*omega_k.
   float* T32 = nullptr;
   double* T64 = nullptr;
+  // non-uniform tensor grid (demag_build_factors_nonuniform): the factors are
+  // dense, not Toeplitz.  fac64 holds them in FP64 in the T64 layout without
+  // the scale; gen64, sym and the twiddles stay unset (no FFT forms).
+  bool nonuniform = false;
+  double* fac64 = nullptr;   // [M][2][tgroup]
+  float* T32t = nullptr;     // transposed tables for the adjoint (CUDA cores)
+  double* T64t = nullptr;
   float* T32d = nullptr;     // the same layout from the derivative generators (analytic stray field)
   double* T64d = nullptr;
   size_t toff[3];            // element offset of axis p inside one (k, type) group
@@ -165,6 +172,9 @@ struct GridInfo {
 };
 __global__ void nodes_kernel(int M, double c0, double cscale, double* nodes, double* scale);
 __global__ void generators_kernel(int M, int glen, GridInfo g, const double* nodes, double* gen);
+demag_status require_uniform(demag_plan* plan, const char* what);
+__global__ void nonuniform_factor_kernel(int M, int n0, int n1, int n2, size_t tgroup, size_t off1, size_t off2,
+                                         int yoff1, int yoff2, const double* nodes, const double* y, double* fac);
 
 // energy (energy.cu)
 demag_status fd_gradient(demag_plan* plan, const float* phi, float* out, float scale,

@@ -6,6 +6,7 @@
 #include <cmath>
 #include <atomic>
 #include <new>
+#include <vector>
 
 #include "internal.h"
 #include "fft.cuh"
@@ -226,6 +227,8 @@ using namespace demag;
 
 // ---------------------------------------------------------------- ABI
 
+static std::atomic<unsigned long long> g_next_serial{1};  // plan serials (cache keys)
+
 static void free_plan_buffers(demag_plan* P) {
   cudaFree(P->nodes);
   cudaFree(P->gen64);
@@ -239,6 +242,9 @@ static void free_plan_buffers(demag_plan* P) {
   }
   cudaFree(P->T32);
   cudaFree(P->T64);
+  cudaFree(P->fac64);
+  cudaFree(P->T32t);
+  cudaFree(P->T64t);
   cudaFree(P->T32d);
   cudaFree(P->T64d);
   cudaFree(P->gend);
@@ -272,8 +278,7 @@ extern "C" demag_status demag_build_factors(const demag_grid_desc* d, demag_plan
   demag_plan* P = new (std::nothrow) demag_plan();
   if (!P) return set_error(nullptr, DEMAG_ENOMEM, "host allocation failed");
   snprintf(P->err, sizeof(P->err), "no error");
-  static std::atomic<unsigned long long> next_serial{1};
-  P->serial = next_serial.fetch_add(1);
+  P->serial = g_next_serial.fetch_add(1);
   P->R = d->R;
   P->M = (d->R - 1) / 2;
   P->c0 = d->c0;
@@ -364,6 +369,104 @@ extern "C" demag_status demag_build_factors(const demag_grid_desc* d, demag_plan
   }
   TRY_CUDA(cudaStreamSynchronize(st));
 #undef TRY_CUDA
+  *out = P;
+  return DEMAG_OK;
+}
+
+extern "C" demag_status demag_build_factors_nonuniform(const demag_grid_edges_desc* d, demag_plan** out,
+                                                       void* stream) {
+  if (!out) return set_error(nullptr, DEMAG_EINVAL, "demag_build_factors_nonuniform: out is NULL");
+  *out = nullptr;
+  if (!d) return set_error(nullptr, DEMAG_EINVAL, "demag_build_factors_nonuniform: desc is NULL");
+  for (int p = 0; p < 3; ++p) {
+    if (d->n[p] < 1) return set_error(nullptr, DEMAG_EINVAL, "n[%d] = %d must be >= 1", p, d->n[p]);
+    if (d->n[p] > (1 << 20)) return set_error(nullptr, DEMAG_EUNSUPPORTED, "n[%d] too large", p);
+    if (!d->edges[p]) return set_error(nullptr, DEMAG_EINVAL, "edges[%d] is NULL", p);
+    for (int j = 0; j <= d->n[p]; ++j)
+      if (!std::isfinite(d->edges[p][j]) || (j > 0 && !(d->edges[p][j] > d->edges[p][j - 1])))
+        return set_error(nullptr, DEMAG_EINVAL, "edges[%d] must be finite and strictly increasing", p);
+  }
+  if (d->R < 5 || d->R % 2 == 0)
+    return set_error(nullptr, DEMAG_EINVAL, "R = %d must be odd and >= 5 (R = 2M+1)", d->R);
+  if ((d->R - 1) / 2 > kMaxTerms)
+    return set_error(nullptr, DEMAG_EUNSUPPORTED, "R = %d exceeds 2*%d+1", d->R, kMaxTerms);
+  if (!(d->c0 > 0.0) || !std::isfinite(d->c0))
+    return set_error(nullptr, DEMAG_EINVAL, "c0 must be positive and finite");
+
+  cudaStream_t st = (cudaStream_t)stream;
+  demag_plan* P = new (std::nothrow) demag_plan();
+  if (!P) return set_error(nullptr, DEMAG_ENOMEM, "host allocation failed");
+  snprintf(P->err, sizeof(P->err), "no error");
+  P->serial = g_next_serial.fetch_add(1);
+  P->nonuniform = true;
+  P->R = d->R;
+  P->M = (d->R - 1) / 2;
+  P->c0 = d->c0;
+  P->s = 0.0;
+  P->nmax = 0;
+  P->Lmax = 0;
+  for (int p = 0; p < 3; ++p) {
+    const double len = d->edges[p][d->n[p]] - d->edges[p][0];
+    P->n[p] = d->n[p];
+    P->h[p] = len / d->n[p];  // mean cell width (informational)
+    P->s = fmax(P->s, len);
+    P->nmax = P->n[p] > P->nmax ? P->n[p] : P->nmax;
+  }
+  for (int p = 0; p < 3; ++p) {
+    P->hh[p] = P->h[p] / P->s;
+    int L = next_pow2(2 * P->n[p] - 1);
+    P->L[p] = L < 2 ? 2 : L;
+    P->Lmax = P->L[p] > P->Lmax ? P->L[p] : P->Lmax;
+  }
+  P->glen = 2 * P->nmax - 1;
+  P->tgroup = 0;
+  for (int p = 0; p < 3; ++p) {
+    P->toff[p] = P->tgroup;
+    P->tgroup += (size_t)P->n[p] * P->n[p];
+  }
+  const int M = P->M;
+  double* ydev = nullptr;
+  auto fail = [&](demag_status s) {
+    snprintf(g_err, sizeof(g_err), "%s", P->err);
+    cudaFree(ydev);
+    free_plan_buffers(P);
+    delete P;
+    return s;
+  };
+#define TRY_CUDA(call)                                         \
+  do {                                                         \
+    cudaError_t e_ = (call);                                   \
+    if (e_ != cudaSuccess) return fail(cuda_error(P, e_, #call)); \
+  } while (0)
+  TRY_CUDA(cudaMalloc(&P->nodes, sizeof(double) * 3 * M));
+  TRY_CUDA(cudaMalloc(&P->scale, sizeof(double) * M));
+  TRY_CUDA(cudaMalloc(&P->dev_status, sizeof(int)));
+  TRY_CUDA(cudaMemsetAsync(P->dev_status, 0, sizeof(int), st));
+  DEMAG_LAUNCH(P, kFamSetup, st, nodes_kernel<<<(M + 63) / 64, 64, 0, st>>>(M, P->c0, kCPot * P->s, P->nodes, P->scale));
+  TRY_CUDA(cudaGetLastError());
+  // edges scaled by the longest domain edge, the three axes concatenated
+  std::vector<double> y;
+  int yoff[3];
+  for (int p = 0; p < 3; ++p) {
+    yoff[p] = (int)y.size();
+    for (int j = 0; j <= P->n[p]; ++j) y.push_back(d->edges[p][j] / P->s);
+  }
+  TRY_CUDA(cudaMalloc(&ydev, sizeof(double) * y.size()));
+  TRY_CUDA(cudaMemcpyAsync(ydev, y.data(), sizeof(double) * y.size(), cudaMemcpyHostToDevice, st));
+  const size_t total = (size_t)M * 2 * P->tgroup;
+  TRY_CUDA(cudaMalloc(&P->fac64, sizeof(double) * total));
+  {
+    size_t blocks = (total + 255) / 256;
+    if (blocks > 152 * 64) blocks = 152 * 64;
+    DEMAG_LAUNCH(P, kFamSetup, st,
+                 nonuniform_factor_kernel<<<(int)blocks, 256, 0, st>>>(M, P->n[0], P->n[1], P->n[2], P->tgroup,
+                                                                      P->toff[1], P->toff[2], yoff[1], yoff[2],
+                                                                      P->nodes, ydev, P->fac64));
+    TRY_CUDA(cudaGetLastError());
+  }
+  TRY_CUDA(cudaStreamSynchronize(st));
+#undef TRY_CUDA
+  cudaFree(ydev);
   *out = P;
   return DEMAG_OK;
 }

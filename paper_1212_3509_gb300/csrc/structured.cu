@@ -513,6 +513,8 @@ static demag_status run_axes(demag_plan* P, ToepAxis* axes, int count, const cha
 
 static demag_status check_fft_plan(demag_plan* P, const char* what) {
   if (!P) return set_error(nullptr, DEMAG_EINVAL, "%s: plan is NULL", what);
+  demag_status u = require_uniform(P, what);  // Toeplitz factors only
+  if (u != DEMAG_OK) return u;
   if (!P->sym || !P->sympair)
     return set_error(P, DEMAG_EUNSUPPORTED, "%s: n_p up to %d supported by the FFT path", what,
                      1 << kMaxFFTLog);
