@@ -106,3 +106,27 @@ def apply_full(m: np.ndarray, edges, R: int, c0: float = 2.15, transpose: bool =
             else:
                 out += omega[k] * X
     return (C_POT * s) * out
+
+
+def apply_full_lines(m: np.ndarray, edges, R: int, lines, c0: float = 2.15) -> np.ndarray:
+    """phi[i3, i2, :] for a list of (i3, i2) pairs without forming all of phi (float64 [len(lines), n1]).
+
+    The same sum as apply_full with the mode-3 and mode-2 products restricted
+    to the requested output rows.
+    """
+    _check(edges, R)
+    M = (R - 1) // 2
+    s = scale_of(edges)
+    _, _, tau, omega = sinc_nodes(M, c0)
+    m = np.asarray(m, dtype=np.float64)
+    out = np.zeros((len(lines), len(edges[0]) - 1))
+    for k in range(M):
+        mats = {}
+        for p in range(3):
+            mats[(p, "E")], mats[(p, "F")] = factor_matrices(edges[p], s, tau[k])
+        for q in range(3):
+            U1, U2, U3 = (mats[(p, factor_kind(p, q))] for p in range(3))
+            for idx, (i3, i2) in enumerate(lines):
+                w = np.tensordot(U3[i3], m[q], axes=([0], [0]))  # [n2, n1]
+                out[idx] += omega[k] * (U1 @ (U2[i2] @ w))
+    return (C_POT * s) * out

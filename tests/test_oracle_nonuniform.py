@@ -118,3 +118,14 @@ def test_planted_mistakes_are_caught(monkeypatch):
         with monkeypatch.context() as mp:
             mp.setattr(nu, name, fn)
             assert err() > 1e-3, name
+
+
+def test_line_sampler_equals_the_full_application():
+    edges = _edges()
+    n = [len(e) - 1 for e in edges]
+    m = np.random.default_rng(8).standard_normal((3, n[2], n[1], n[0]))
+    full_phi = nu.apply_full(m, edges, 21)
+    lines = [(0, 0), (5, 3), (2, 1)]
+    got = nu.apply_full_lines(m, edges, 21, lines)
+    for (i3, i2), row in zip(lines, got):
+        assert np.allclose(row, full_phi[i3, i2], rtol=1e-13, atol=1e-15 * np.abs(full_phi).max())
