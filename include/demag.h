@@ -238,6 +238,36 @@ demag_status demag_apply_cp_batched(demag_plan* plan, int batch, int r, const fl
  * out_w: float [M][3]; out_V: three mode blocks, block p = [M][3][r_p][n_p]. */
 demag_status demag_apply_tucker(demag_plan* plan, const int r[3], const float* V,
                                 float* out_w, float* out_V, void* stream);
+/* ---- Alg. 2 with compressed kernels (Sec. 4.2 Alg. 2; Alg. 1 HOOI; App. B) --
+ * demag_compress_kernel compresses the CP convolution kernel of each
+ * component (Eq. conv_pot: M terms of generator columns, weights c s omega_k)
+ * to a Tucker tensor: QR of the generator matrices, HOSVD ranks by the rule
+ * of Alg. 1 (discarded singular values of each unfolding <= tol/sqrt(3) of its
+ * norm), the largest rank over the three components per mode, then HOOI
+ * sweeps at those ranks; FP64 on the device, so ||K - K_tucker||_F <= tol ||K||_F.
+ * It replaces any earlier compression of the plan and synchronizes `stream`.
+ * tol in (0, 1).  Uniform grids whose FFT path exists only. */
+demag_status demag_compress_kernel(demag_plan* plan, double tol, void* stream);
+/* rho[p]: the Tucker ranks of the compressed kernels (shared by the components). */
+demag_status demag_compressed_ranks(const demag_plan* plan, int rho[3]);
+/* Device copies of the compressed kernels: gen (optional) double
+ * [rhomax][3 q][3 p][2 nmax - 1] (row (i, q, p) = column i of U_p^(q), entries
+ * d + n_p - 1 for |d| < n_p, zero past; rhomax = max rho), core (optional)
+ * float [3 q][rho3][rho2][rho1].  Synchronous on `stream`. */
+demag_status demag_copy_compressed(const demag_plan* plan, double* gen, float* core, void* stream);
+/* Apply the compressed kernels to `batch` Tucker magnetizations (Alg. 2:
+ * Lemma DFT_tucker and the Tucker Hadamard product of App. B Eq. t_had2, done
+ * as circulant-FFT Toeplitz matvecs of the compressed generators).  Input as
+ * demag_apply_tucker_batched plus the cores: core float [batch][3][r3][r2][r1],
+ * V float blocks (q, p) [r_p][n_p] per item.  Output per item b and component q:
+ * out_core float [batch][3][rho3 r3][rho2 r2][rho1 r1] = C^(q) (x) G^(q) with
+ * index (i, l) = i r_p + l, and out_V: three mode blocks per item, block p =
+ * [rho_p][3][r_p][n_p], row (i, q, l) = T(U_p^(q)[:, i]) V^(q,p)[:, l];
+ * phi = sum_q [[out_core^(q); W^(q,1), W^(q,2), W^(q,3)]] with W^(q,p) column
+ * (i, l) = row (i, q, l) of block p.  FP32. */
+demag_status demag_apply_tucker_compressed(demag_plan* plan, int batch, const int r[3], const float* core,
+                                           const float* V, float* out_core, float* out_V, void* stream);
+
 /* `batch` independent Tucker inputs in one launch per FFT length: item b of
  * V, out_w and out_V follows the single-item layout above at item strides
  * 3 sum_p r_p n_p, 3M and 3M sum_p r_p n_p floats.  batch >= 1. */

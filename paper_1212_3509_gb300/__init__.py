@@ -18,6 +18,10 @@ from ._abi import (  # noqa: F401
     demag_apply_cp_batched,
     demag_apply_full,
     demag_build_factors_nonuniform,
+    demag_compress_kernel,
+    demag_compressed_ranks,
+    demag_copy_compressed,
+    demag_apply_tucker_compressed,
     demag_apply_full_fft,
     demag_apply_full_batched,
     demag_apply_tt,

@@ -53,6 +53,10 @@ _SIGS = {
     "demag_apply_full": (_i, [_vp, _vp, _vp, _i, _vp]),
     "demag_apply_full_fft": (_i, [_vp, _vp, _vp, _vp]),
     "demag_build_factors_nonuniform": (_i, [ctypes.POINTER(GridEdgesDesc), ctypes.POINTER(_vp), _vp]),
+    "demag_compress_kernel": (_i, [_vp, ctypes.c_double, _vp]),
+    "demag_compressed_ranks": (_i, [_vp, ctypes.POINTER(ctypes.c_int)]),
+    "demag_copy_compressed": (_i, [_vp, _vp, _vp, _vp]),
+    "demag_apply_tucker_compressed": (_i, [_vp, _i, ctypes.POINTER(ctypes.c_int), _vp, _vp, _vp, _vp, _vp]),
     "demag_apply_full_batched": (_i, [ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i, _i, _vp]),
     "demag_graph_create_batched": (_i, [ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i, _i,
                                         ctypes.POINTER(_vp)]),
@@ -179,6 +183,41 @@ def demag_build_factors_nonuniform(edges, R: int, c0: float = 2.15, stream=None)
     plan = Plan(out.value, n, mean_h, R, c0)
     plan.edges = [tuple(float(v) for v in e) for e in edges]
     return plan
+
+
+def demag_compress_kernel(plan: Plan, tol: float, stream=None):
+    """Alg. 2 setup: compress the three CP kernels to Tucker tensors (HOOI, tolerance tol)."""
+    _check(lib.demag_compress_kernel(plan.ptr, float(tol), _stream(stream)), plan.ptr)
+
+
+def demag_compressed_ranks(plan: Plan) -> tuple:
+    rho = (ctypes.c_int * 3)()
+    _check(lib.demag_compressed_ranks(plan.ptr, rho), plan.ptr)
+    return tuple(int(v) for v in rho)
+
+
+def demag_copy_compressed(plan: Plan, gen=None, core=None, stream=None):
+    import torch
+    rho = demag_compressed_ranks(plan)
+    glen = 2 * max(plan.n) - 1
+    _check(lib.demag_copy_compressed(plan.ptr, _ptr(gen, max(rho) * 9 * glen, torch.float64, "gen"),
+                                     _ptr(core, 3 * rho[0] * rho[1] * rho[2], torch.float32, "core"),
+                                     _stream(stream)), plan.ptr)
+
+
+def demag_apply_tucker_compressed(plan: Plan, batch: int, r, core, V, out_core, out_V, stream=None):
+    import torch
+    rho = demag_compressed_ranks(plan)
+    rr = (ctypes.c_int * 3)(*[int(v) for v in r])
+    f32 = torch.float32
+    qs = sum(int(r[p]) * plan.n[p] for p in range(3))
+    os_ = sum(3 * rho[p] * int(r[p]) * plan.n[p] for p in range(3))
+    ncore = int(r[0]) * int(r[1]) * int(r[2])
+    nout = rho[0] * r[0] * rho[1] * r[1] * rho[2] * r[2]
+    _check(lib.demag_apply_tucker_compressed(plan.ptr, int(batch), rr, _ptr(core, batch * 3 * ncore, f32, "core"),
+                                             _ptr(V, batch * 3 * qs, f32, "V"),
+                                             _ptr(out_core, batch * 3 * nout, f32, "out_core"),
+                                             _ptr(out_V, batch * os_, f32, "out_V"), _stream(stream)), plan.ptr)
 
 
 def demag_plan_destroy(plan: Plan):

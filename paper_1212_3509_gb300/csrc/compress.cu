@@ -1,0 +1,553 @@
+// Alg. 2 with compressed kernels: Tucker compression of the CP convolution
+// kernels by HOOI (Alg. 1) and their application to Tucker magnetizations.
+//
+// Kernel of component q (Eq. conv_pot): K^(q) = sum_k lam_k a_{1k} (x) a_{2k} (x) a_{3k},
+// lam_k = c s omega_k, a_{pk} the generator F_k^(p) (p == q) or E_k^(p) (p != q),
+// 2 n_p - 1 entries.  With A_p = Q_p R_p (QR of the M generator columns of one
+// type and axis) every Gram matrix of an unfolding of K^(q), after projecting
+// the other modes on V_s, V_r, is
+//   Y_(p) Y_(p)^T = Q_p S_p Q_p^T,  S_p = R_p Lam ((B_s^T B_s) o (B_r^T B_r)) Lam R_p^T,
+//   B_x = V_x^T R_x  (B_x = R_x for the HOSVD start),
+// so HOSVD and the HOOI sweeps of Alg. 1 only need eigen-decompositions of
+// M x M matrices: the mode-p factor is U_p = Q_p V_p, V_p the leading
+// eigenvectors of S_p, and the core is C = sum_k lam_k b_{1k} (x) b_{2k} (x) b_{3k}
+// with b_{pk} = V_p^T R_p[:, k].  The ranks follow the HOSVD rule of Alg. 1
+// (discarded singular values of each unfolding below tol/sqrt(3) of its
+// norm), the largest over the three components, so all components share one
+// rank per mode; HOOI then sweeps at those ranks.  The columns of U_p are
+// generators of Toeplitz matrices again (linear combinations of E or F
+// generators), so the compressed kernel is applied with the circulant FFT
+// kernel of the structured formats, one symbol set per component.
+//
+// Application (Lemma DFT_tucker, App. B Eq. t_had2): for a Tucker
+// magnetization [[G^(q); V^(q,1), V^(q,2), V^(q,3)]] the result is
+//   sum_q [[C^(q) (x) G^(q); W^(q,1), W^(q,2), W^(q,3)]],  W^(q,p)[:, (i, l)] = T(U_p^(q)[:, i]) V^(q,p)[:, l],
+// factors written [rho_p][3][r_p][n_p] (i major) and cores
+// [(rho3 r3)][(rho2 r2)][(rho1 r1)] with the same (i, l) index order.
+// Setup arithmetic is FP64; the application is FP32 (like the uncompressed
+// structured path).
+#include <algorithm>
+#include <cmath>
+#include <new>
+#include <vector>
+
+#include "internal.h"
+
+namespace demag {
+
+struct Compressed {
+  double tol = 0.0;
+  int rho[3] = {0, 0, 0};
+  double* cgen = nullptr;   // [rhomax][3 q][3 p][glen] compressed generators
+  float* csym = nullptr;    // [rhomax][3][3][Lmax/2 + 1]
+  float2* cpair = nullptr;  // [rhomax][3][3][Lmax/2]
+  float* core = nullptr;    // [3 q][rho3][rho2][rho1]
+};
+
+namespace {
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// block-wide sum (blockDim a multiple of 32, <= 1024); every thread gets the result
+__device__ double block_sum(double v, double* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double t = 0.0;
+  for (int w = 0; w < nw; ++w) t += red[w];
+  __syncthreads();
+  return t;
+}
+
+}  // namespace
+
+// QR of the generator matrix of (type, axis) = (j / 3, j % 3) by classical
+// Gram-Schmidt with two re-orthogonalisation passes, FP64, one block per
+// matrix.  Q column k at Q + (j M + k) glen (zero past m_p); R [j][M][M] upper
+// triangular.  The generators of neighbouring nodes are numerically
+// dependent (for large tau they all approach a multiple of the unit vector
+// at d = 0): a column whose residual is below 1e-12 of its own norm is taken
+// as in the span of the previous ones (R_kk = 0, zero Q column), so the
+// residual noise is never normalised into a non-orthogonal direction; the
+// factorisation then holds to 1e-12 of each column.
+__global__ void __launch_bounds__(256) cmp_qr_kernel(int M, int glen, int m0, int m1, int m2, const double* gen,
+                                                     double* Q, double* Rm) {
+  __shared__ double coef[kMaxTerms];
+  __shared__ double red[32];
+  const int j = blockIdx.x, axis = j % 3, type = j / 3;
+  const int m = axis == 0 ? m0 : (axis == 1 ? m1 : m2);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  double* Qj = Q + (size_t)j * M * glen;
+  double* R = Rm + (size_t)j * M * M;
+  for (int i = threadIdx.x; i < M * M; i += blockDim.x) R[i] = 0.0;
+  for (int k = 0; k < M; ++k) {
+    double* v = Qj + (size_t)k * glen;
+    const double* a = gen + (((size_t)k * 2 + type) * 3 + axis) * glen;
+    double a2 = 0.0;
+    for (int e = threadIdx.x; e < glen; e += blockDim.x) {
+      const double x = e < m ? a[e] : 0.0;
+      v[e] = x;
+      a2 += x * x;
+    }
+    const double anrm = sqrt(block_sum(a2, red));
+    for (int pass = 0; pass < 3; ++pass) {
+      for (int b = warp; b < k; b += nw) {
+        const double* qb = Qj + (size_t)b * glen;
+        double acc = 0.0;
+        for (int e = lane; e < m; e += 32) acc += qb[e] * v[e];
+        acc = warp_sum(acc);
+        if (lane == 0) coef[b] = acc;
+      }
+      __syncthreads();
+      for (int e = threadIdx.x; e < m; e += blockDim.x) {
+        double t = v[e];
+        for (int b = 0; b < k; ++b) t -= coef[b] * Qj[(size_t)b * glen + e];
+        v[e] = t;
+      }
+      if (threadIdx.x < k) R[threadIdx.x * M + k] += coef[threadIdx.x];
+      __syncthreads();
+    }
+    double s2 = 0.0;
+    for (int e = threadIdx.x; e < m; e += blockDim.x) s2 += v[e] * v[e];
+    double nrm = sqrt(block_sum(s2, red));
+    if (nrm <= 1e-12 * anrm) nrm = 0.0;
+    const double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
+    for (int e = threadIdx.x; e < m; e += blockDim.x) v[e] *= inv;
+    if (threadIdx.x == 0) R[k * M + k] = nrm;
+    __syncthreads();
+  }
+}
+
+// Symmetric eigen-decomposition of A (n x n, n even, leading dimension n, in
+// shared memory) by cyclic Jacobi with a round-robin ordering (n/2 disjoint
+// rotations per round): on return A is diagonal (the eigenvalues) and V holds
+// the eigenvectors in its columns.  Each rotation G = [[c, s], [-s, c]] in
+// rows/columns (p, q) zeroes a_pq with t = sgn(theta) / (|theta| + sqrt(1 + theta^2)),
+// theta = (a_qq - a_pp) / (2 a_pq).  Stops when the off-diagonal part is below
+// 1e-15 of the norm (squared: 1e-30) or after 30 sweeps.
+__device__ void jacobi_eigen(double* A, double* V, int n, double* red) {
+  __shared__ double rc[32], rs[32];
+  __shared__ int rp[32], rq[32];
+  for (int i = threadIdx.x; i < n * n; i += blockDim.x) V[i] = (i / n == i % n) ? 1.0 : 0.0;
+  __syncthreads();
+  for (int sweep = 0; sweep < 30; ++sweep) {
+    double off = 0.0, all = 0.0;
+    for (int i = threadIdx.x; i < n * n; i += blockDim.x) {
+      const double x = A[i] * A[i];
+      all += x;
+      if (i / n != i % n) off += x;
+    }
+    off = block_sum(off, red);
+    all = block_sum(all, red);
+    if (!(off > 1e-30 * all)) break;
+    for (int round = 0; round < n - 1; ++round) {
+      if (threadIdx.x < n / 2) {
+        auto pos = [&](int x) { return x == 0 ? 0 : 1 + (x - 1 + round) % (n - 1); };
+        int p = pos(threadIdx.x), q = pos(n - 1 - threadIdx.x);
+        if (p > q) {
+          const int t = p;
+          p = q;
+          q = t;
+        }
+        const double apq = A[p * n + q];
+        double c = 1.0, s = 0.0;
+        if (apq != 0.0) {
+          const double theta = (A[q * n + q] - A[p * n + p]) / (2.0 * apq);
+          const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(1.0 + theta * theta));
+          c = 1.0 / sqrt(1.0 + t * t);
+          s = t * c;
+        }
+        rp[threadIdx.x] = p;
+        rq[threadIdx.x] = q;
+        rc[threadIdx.x] = c;
+        rs[threadIdx.x] = s;
+      }
+      __syncthreads();
+      const int half = n / 2;
+      for (int idx = threadIdx.x; idx < half * n; idx += blockDim.x) {  // rows p, q
+        const int r = idx / n, col = idx % n;
+        const int p = rp[r], q = rq[r];
+        const double c = rc[r], s = rs[r];
+        const double ap = A[p * n + col], aq = A[q * n + col];
+        A[p * n + col] = c * ap - s * aq;
+        A[q * n + col] = s * ap + c * aq;
+      }
+      __syncthreads();
+      for (int idx = threadIdx.x; idx < half * n; idx += blockDim.x) {  // columns p, q of A and V
+        const int r = idx / n, row = idx % n;
+        const int p = rp[r], q = rq[r];
+        const double c = rc[r], s = rs[r];
+        const double ap = A[row * n + p], aq = A[row * n + q];
+        A[row * n + p] = c * ap - s * aq;
+        A[row * n + q] = s * ap + c * aq;
+        const double vp = V[row * n + p], vq = V[row * n + q];
+        V[row * n + p] = c * vp - s * vq;
+        V[row * n + q] = s * vp + c * vq;
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// S_p into A (n x n, zero past M):  S = R_p Lam (H_s o H_r) Lam R_p^T with
+// H_x = B_x^T B_x, B_x = V_x^T R_x (V_x [M][M] column-major in its first rho_x
+// columns) or B_x = R_x when V_x is NULL.  R matrices [M][M] row-major, upper
+// triangular.  X and T are scratch (n x n).
+__device__ void mode_matrix(int M, int n, const double* Rp, const double* Rs, const double* Rr, const double* Vs,
+                            int rho_s, const double* Vr, int rho_r, const double* lam, double* X, double* T,
+                            double* A) {
+  for (int pass = 0; pass < 2; ++pass) {
+    const double* R = pass ? Rr : Rs;
+    const double* V = pass ? Vr : Vs;
+    const int rho = V ? (pass ? rho_r : rho_s) : M;
+    for (int idx = threadIdx.x; idx < rho * M; idx += blockDim.x) {  // B_x into T
+      const int i = idx / M, a = idx % M;
+      double b = 0.0;
+      if (V) {
+        for (int k = 0; k < M; ++k) b += V[k * M + i] * R[k * M + a];
+      } else {
+        b = R[i * M + a];
+      }
+      T[i * n + a] = b;
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+      const int a = idx / n, b = idx % n;
+      double h = 0.0;
+      if (a < M && b < M)
+        for (int i = 0; i < rho; ++i) h += T[i * n + a] * T[i * n + b];
+      X[idx] = pass ? X[idx] * h * lam[a < M ? a : 0] * lam[b < M ? b : 0] : h;
+    }
+    __syncthreads();
+  }
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {  // T = R_p X
+    const int i = idx / n, b = idx % n;
+    double t = 0.0;
+    if (i < M && b < M)
+      for (int a = i; a < M; ++a) t += Rp[i * M + a] * X[a * n + b];
+    T[idx] = t;
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {  // A = T R_p^T
+    const int i = idx / n, j = idx % n;
+    double t = 0.0;
+    if (i < M && j < M)
+      for (int b = j; b < M; ++b) t += T[i * n + b] * Rp[j * M + b];
+    A[idx] = t;
+  }
+  __syncthreads();
+}
+
+// Eigenvalues of A (after jacobi_eigen) in descending order of the first M
+// indices (a padding index stays decoupled), eigenvectors written column i of
+// Vout [M][M].  Returns nothing; eig gets M values.
+__device__ void sorted_out(int M, int n, const double* A, const double* V, double* eig, double* Vout) {
+  __shared__ int ord[kMaxTerms];
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < M; ++i) ord[i] = i;
+    for (int i = 0; i < M; ++i) {
+      int best = i;
+      for (int j = i + 1; j < M; ++j)
+        if (A[ord[j] * n + ord[j]] > A[ord[best] * n + ord[best]]) best = j;
+      const int t = ord[i];
+      ord[i] = ord[best];
+      ord[best] = t;
+    }
+  }
+  __syncthreads();
+  if (eig)
+    for (int i = threadIdx.x; i < M; i += blockDim.x) eig[i] = A[ord[i] * n + ord[i]];
+  for (int idx = threadIdx.x; idx < M * M; idx += blockDim.x) {
+    const int k = idx / M, i = idx % M;
+    Vout[idx] = V[k * n + ord[i]];
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ const double* r_of(const double* Rm, int M, int axis, int q) {
+  return Rm + (size_t)((axis == q ? 1 : 0) * 3 + axis) * M * M;
+}
+
+// HOSVD of K^(q) (block q): eigen-decomposition of S_p with B_x = R_x, for p = 1..3.
+__global__ void __launch_bounds__(256) cmp_hosvd_kernel(int M, int n, const double* Rm, const double* lam,
+                                                        double* eig, double* Vfull) {
+  extern __shared__ double smc[];
+  __shared__ double red[32];
+  double *X = smc, *T = X + n * n, *A = T + n * n, *V = A + n * n;
+  const int q = blockIdx.x;
+  for (int p = 0; p < 3; ++p) {
+    const int s = (p + 1) % 3, r = (p + 2) % 3;
+    mode_matrix(M, n, r_of(Rm, M, p, q), r_of(Rm, M, s, q), r_of(Rm, M, r, q), nullptr, 0, nullptr, 0, lam, X, T, A);
+    jacobi_eigen(A, V, n, red);
+    sorted_out(M, n, A, V, eig + (size_t)(q * 3 + p) * M, Vfull + (size_t)(q * 3 + p) * M * M);
+  }
+}
+
+// HOOI sweeps of Alg. 1 at ranks rho (block q) from the HOSVD start in Vcur,
+// then the core C[i3][i2][i1] = sum_k lam_k b_{1k}[i1] b_{2k}[i2] b_{3k}[i3].
+__global__ void __launch_bounds__(256) cmp_hooi_kernel(int M, int n, int rho0, int rho1, int rho2, int sweeps,
+                                                       const double* Rm, const double* lam, double* Vcur,
+                                                       float* core) {
+  extern __shared__ double smc[];
+  __shared__ double red[32];
+  double *X = smc, *T = X + n * n, *A = T + n * n, *V = A + n * n;
+  const int q = blockIdx.x;
+  const int rho[3] = {rho0, rho1, rho2};
+  double* Vq = Vcur + (size_t)q * 3 * M * M;
+  for (int sw = 0; sw < sweeps; ++sw) {
+    for (int p = 0; p < 3; ++p) {
+      const int s = (p + 1) % 3, r = (p + 2) % 3;
+      mode_matrix(M, n, r_of(Rm, M, p, q), r_of(Rm, M, s, q), r_of(Rm, M, r, q), Vq + (size_t)s * M * M, rho[s],
+                  Vq + (size_t)r * M * M, rho[r], lam, X, T, A);
+      jacobi_eigen(A, V, n, red);
+      sorted_out(M, n, A, V, nullptr, Vq + (size_t)p * M * M);
+    }
+  }
+  // b_p = V_p^T R_p into X (p = 0), T (1), A (2): [rho_p][M] at leading dimension n
+  double* B[3] = {X, T, A};
+  for (int p = 0; p < 3; ++p) {
+    const double* R = r_of(Rm, M, p, q);
+    const double* Vp = Vq + (size_t)p * M * M;
+    for (int idx = threadIdx.x; idx < rho[p] * M; idx += blockDim.x) {
+      const int i = idx / M, a = idx % M;
+      double b = 0.0;
+      for (int k = 0; k < M; ++k) b += Vp[k * M + i] * R[k * M + a];
+      B[p][i * n + a] = b;
+    }
+  }
+  __syncthreads();
+  const int total = rho0 * rho1 * rho2;
+  float* Cq = core + (size_t)q * total;
+  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+    const int i1 = idx % rho0, i2 = (idx / rho0) % rho1, i3 = idx / (rho0 * rho1);
+    double c = 0.0;
+    for (int k = 0; k < M; ++k) c += lam[k] * X[i1 * n + k] * T[i2 * n + k] * A[i3 * n + k];
+    Cq[idx] = (float)c;
+  }
+}
+
+// Compressed generators U_p^(q) = Q_{type,p} V_p^(q): row (i, q, p) of cgen, i < rho_p, e < m_p.
+__global__ void cmp_gen_kernel(int M, int glen, int rho0, int rho1, int rho2, int m0, int m1, int m2,
+                               const double* Q, const double* Vcur, double* cgen) {
+  const int rho[3] = {rho0, rho1, rho2};
+  const int mm[3] = {m0, m1, m2};
+  const int rmax = max(rho0, max(rho1, rho2));
+  const long total = (long)rmax * 9 * glen;
+  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
+    const int e = (int)(idx % glen);
+    const long row = idx / glen;  // (i * 3 + q) * 3 + p
+    const int p = (int)(row % 3), q = (int)((row / 3) % 3), i = (int)(row / 9);
+    double v = 0.0;
+    if (i < rho[p] && e < mm[p]) {
+      const int j = (p == q ? 1 : 0) * 3 + p;
+      const double* Qj = Q + (size_t)j * M * glen;
+      const double* Vp = Vcur + (size_t)(q * 3 + p) * M * M;
+      for (int k = 0; k < M; ++k) v += Qj[(size_t)k * glen + e] * Vp[k * M + i];
+    }
+    cgen[idx] = v;
+  }
+}
+
+// out_core[b][q][(i3 r3 + l3)][(i2 r2 + l2)][(i1 r1 + l1)] = C^(q)[i3][i2][i1] G[b][q][l3][l2][l1]
+__global__ void cmp_core_kernel(int batch, int rho0, int rho1, int rho2, int r0, int r1, int r2, const float* C,
+                                const float* G, float* out) {
+  const long per = (long)rho0 * r0 * rho1 * r1 * rho2 * r2;
+  const long total = (long)batch * 3 * per;
+  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
+    long t = idx % per;
+    const long bq = idx / per;
+    const int q = (int)(bq % 3);
+    const int c1 = (int)(t % ((long)rho0 * r0));
+    t /= (long)rho0 * r0;
+    const int c2 = (int)(t % ((long)rho1 * r1));
+    const int c3 = (int)(t / ((long)rho1 * r1));
+    const int i1 = c1 / r0, l1 = c1 % r0, i2 = c2 / r1, l2 = c2 % r1, i3 = c3 / r2, l3 = c3 % r2;
+    const float cv = C[(size_t)q * rho0 * rho1 * rho2 + ((size_t)i3 * rho1 + i2) * rho0 + i1];
+    const float gv = G[(size_t)bq * r0 * r1 * r2 + ((size_t)l3 * r1 + l2) * r0 + l1];
+    out[idx] = cv * gv;
+  }
+}
+
+void compress_destroy(demag_plan* P) {
+  Compressed* C = static_cast<Compressed*>(P->cmp);
+  if (!C) return;
+  cudaFree(C->cgen);
+  cudaFree(C->csym);
+  cudaFree(C->cpair);
+  cudaFree(C->core);
+  delete C;
+  P->cmp = nullptr;
+}
+
+bool compressed_view(const demag_plan* P, CompressedView* v) {
+  const Compressed* C = static_cast<const Compressed*>(P ? P->cmp : nullptr);
+  if (!C) return false;
+  for (int p = 0; p < 3; ++p) v->rho[p] = C->rho[p];
+  v->cpair = C->cpair;
+  v->core = C->core;
+  return true;
+}
+
+demag_status launch_core_kron(demag_plan* P, int batch, const int r[3], const float* G, float* out, cudaStream_t st) {
+  const Compressed* C = static_cast<const Compressed*>(P->cmp);
+  const long total = (long)batch * 3 * C->rho[0] * r[0] * C->rho[1] * r[1] * C->rho[2] * r[2];
+  long blocks = (total + 255) / 256;
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  DEMAG_LAUNCH(P, kFamMisc, st,
+               cmp_core_kernel<<<(int)blocks, 256, 0, st>>>(batch, C->rho[0], C->rho[1], C->rho[2], r[0], r[1], r[2],
+                                                            C->core, G, out));
+  DEMAG_LAUNCHED(P, "cmp_core_kernel");
+  return DEMAG_OK;
+}
+
+}  // namespace demag
+
+using namespace demag;
+
+// tail[r] = sum_{i >= r} sigma_i^2 of descending eigenvalues sigma^2; the
+// smallest r with tail[r] <= (tol^2 / 3) sum sigma^2 (at least 1).
+static int truncation_rank(const double* sig2, int M, double tol) {
+  double total = 0.0;
+  for (int i = 0; i < M; ++i) total += sig2[i] > 0.0 ? sig2[i] : 0.0;
+  const double bound = tol * tol / 3.0 * total;
+  double tail = total;
+  for (int r = 1; r <= M; ++r) {
+    tail -= sig2[r - 1] > 0.0 ? sig2[r - 1] : 0.0;
+    if (tail <= bound) return r;
+  }
+  return M;
+}
+
+extern "C" demag_status demag_compress_kernel(demag_plan* P, double tol, void* stream) {
+  if (!P) return set_error(nullptr, DEMAG_EINVAL, "demag_compress_kernel: plan is NULL");
+  demag_status u = require_uniform(P, "demag_compress_kernel");
+  if (u != DEMAG_OK) return u;
+  if (!(tol > 0.0 && tol < 1.0)) return set_error(P, DEMAG_EINVAL, "demag_compress_kernel: tol must be in (0, 1)");
+  if (!P->sympair || !P->twid[0])
+    return set_error(P, DEMAG_EUNSUPPORTED, "demag_compress_kernel: n_p up to %d supported by the FFT path",
+                     1 << kMaxFFTLog);
+  cudaStream_t st = (cudaStream_t)stream;
+  const int M = P->M, glen = P->glen, n = M + (M & 1);
+  const int m[3] = {2 * P->n[0] - 1, 2 * P->n[1] - 1, 2 * P->n[2] - 1};
+  double *Q = nullptr, *R = nullptr, *eig = nullptr, *Vfull = nullptr, *Vcur = nullptr;
+  Compressed* C = new (std::nothrow) Compressed();
+  if (!C) return set_error(P, DEMAG_ENOMEM, "host allocation failed");
+  auto cleanup = [&]() {
+    cudaFree(Q);
+    cudaFree(R);
+    cudaFree(eig);
+    cudaFree(Vfull);
+    cudaFree(Vcur);
+  };
+  auto fail = [&](demag_status s) {
+    cleanup();
+    cudaFree(C->cgen);
+    cudaFree(C->csym);
+    cudaFree(C->cpair);
+    cudaFree(C->core);
+    delete C;
+    return s;
+  };
+#define CMP_CUDA(call)                                          \
+  do {                                                          \
+    cudaError_t e_ = (call);                                    \
+    if (e_ != cudaSuccess) return fail(cuda_error(P, e_, #call)); \
+  } while (0)
+  CMP_CUDA(cudaMalloc(&Q, sizeof(double) * 6 * M * glen));
+  CMP_CUDA(cudaMalloc(&R, sizeof(double) * 6 * M * M));
+  CMP_CUDA(cudaMalloc(&eig, sizeof(double) * 9 * M));
+  CMP_CUDA(cudaMalloc(&Vfull, sizeof(double) * 9 * M * M));
+  CMP_CUDA(cudaMalloc(&Vcur, sizeof(double) * 9 * M * M));
+  const size_t smem = sizeof(double) * 4 * n * n;
+  static unsigned long long attr = 0;  // devices whose kernel attributes are set
+  int dev = 0;
+  CMP_CUDA(cudaGetDevice(&dev));
+  if (!(attr & (1ull << (dev & 63)))) {
+    CMP_CUDA(cudaFuncSetAttribute(cmp_hosvd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * 64 * 64 * 8));
+    CMP_CUDA(cudaFuncSetAttribute(cmp_hooi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * 64 * 64 * 8));
+    attr |= 1ull << (dev & 63);
+  }
+  DEMAG_LAUNCH(P, kFamSetup, st, cmp_qr_kernel<<<6, 256, 0, st>>>(M, glen, m[0], m[1], m[2], P->gen64, Q, R));
+  CMP_CUDA(cudaGetLastError());
+  DEMAG_LAUNCH(P, kFamSetup, st, cmp_hosvd_kernel<<<3, 256, smem, st>>>(M, n, R, P->scale, eig, Vfull));
+  CMP_CUDA(cudaGetLastError());
+  std::vector<double> eh((size_t)9 * M);
+  CMP_CUDA(cudaMemcpyAsync(eh.data(), eig, sizeof(double) * 9 * M, cudaMemcpyDeviceToHost, st));
+  CMP_CUDA(cudaStreamSynchronize(st));
+  for (int p = 0; p < 3; ++p) {
+    C->rho[p] = 1;
+    for (int q = 0; q < 3; ++q) C->rho[p] = std::max(C->rho[p], truncation_rank(&eh[(size_t)(q * 3 + p) * M], M, tol));
+  }
+  C->tol = tol;
+  CMP_CUDA(cudaMemcpyAsync(Vcur, Vfull, sizeof(double) * 9 * M * M, cudaMemcpyDeviceToDevice, st));
+  CMP_CUDA(cudaMalloc(&C->core, sizeof(float) * 3 * C->rho[0] * C->rho[1] * C->rho[2]));
+  DEMAG_LAUNCH(P, kFamSetup, st,
+               cmp_hooi_kernel<<<3, 256, smem, st>>>(M, n, C->rho[0], C->rho[1], C->rho[2], 4, R, P->scale, Vcur,
+                                                     C->core));
+  CMP_CUDA(cudaGetLastError());
+  const int rmax = std::max(C->rho[0], std::max(C->rho[1], C->rho[2]));
+  CMP_CUDA(cudaMalloc(&C->cgen, sizeof(double) * (size_t)rmax * 9 * glen));
+  {
+    const long total = (long)rmax * 9 * glen;
+    long blocks = (total + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    DEMAG_LAUNCH(P, kFamSetup, st,
+                 cmp_gen_kernel<<<(int)blocks, 256, 0, st>>>(M, glen, C->rho[0], C->rho[1], C->rho[2], m[0], m[1], m[2],
+                                                             Q, Vcur, C->cgen));
+    CMP_CUDA(cudaGetLastError());
+  }
+  const int symstride = P->Lmax / 2 + 1, pairstride = P->Lmax / 2;
+  CMP_CUDA(cudaMalloc(&C->csym, sizeof(float) * (size_t)rmax * 9 * symstride));
+  CMP_CUDA(cudaMemsetAsync(C->csym, 0, sizeof(float) * (size_t)rmax * 9 * symstride, st));
+  CMP_CUDA(cudaMalloc(&C->cpair, sizeof(float2) * (size_t)rmax * 9 * pairstride));
+  for (int p = 0; p < 3; ++p) {
+    dispatch_symbol(P, p, C->rho[p], 3, C->cgen, C->csym, st);
+    CMP_CUDA(cudaGetLastError());
+    const int N = P->L[p] / 2;
+    const long total = (long)C->rho[p] * 3 * N;
+    long blocks = (total + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    DEMAG_LAUNCH(P, kFamSetup, st,
+                 sympair_kernel<<<(int)blocks, 256, 0, st>>>(C->rho[p], 3, p, N, symstride, pairstride, C->csym,
+                                                             C->cpair));
+    CMP_CUDA(cudaGetLastError());
+  }
+  CMP_CUDA(cudaStreamSynchronize(st));
+#undef CMP_CUDA
+  cleanup();
+  compress_destroy(P);
+  P->cmp = C;
+  return DEMAG_OK;
+}
+
+extern "C" demag_status demag_compressed_ranks(const demag_plan* plan, int rho[3]) {
+  demag_plan* P = const_cast<demag_plan*>(plan);
+  if (!P || !rho) return set_error(P, DEMAG_EINVAL, "demag_compressed_ranks: NULL argument");
+  const Compressed* C = static_cast<const Compressed*>(P->cmp);
+  if (!C) return set_error(P, DEMAG_EINVAL, "demag_compressed_ranks: no compressed kernel (demag_compress_kernel)");
+  for (int p = 0; p < 3; ++p) rho[p] = C->rho[p];
+  return DEMAG_OK;
+}
+
+extern "C" demag_status demag_copy_compressed(const demag_plan* plan, double* gen, float* core, void* stream) {
+  demag_plan* P = const_cast<demag_plan*>(plan);
+  if (!P) return set_error(nullptr, DEMAG_EINVAL, "demag_copy_compressed: plan is NULL");
+  const Compressed* C = static_cast<const Compressed*>(P->cmp);
+  if (!C) return set_error(P, DEMAG_EINVAL, "demag_copy_compressed: no compressed kernel (demag_compress_kernel)");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int rmax = std::max(C->rho[0], std::max(C->rho[1], C->rho[2]));
+  if (gen)
+    DEMAG_CUDA(P, cudaMemcpyAsync(gen, C->cgen, sizeof(double) * (size_t)rmax * 9 * P->glen,
+                                  cudaMemcpyDeviceToDevice, st));
+  if (core)
+    DEMAG_CUDA(P, cudaMemcpyAsync(core, C->core, sizeof(float) * 3 * C->rho[0] * C->rho[1] * C->rho[2],
+                                  cudaMemcpyDeviceToDevice, st));
+  DEMAG_CUDA(P, cudaStreamSynchronize(st));
+  return DEMAG_OK;
+}

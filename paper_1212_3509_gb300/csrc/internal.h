@@ -71,6 +71,8 @@ struct demag_plan {
   void* tc = nullptr;
   // 3D FFT convolution state (opaque, owned by fft3d.cu): dense Fourier kernel and spectra
   void* f3 = nullptr;
+  // compressed (Tucker) kernels of Alg. 2 (opaque, owned by compress.cu)
+  void* cmp = nullptr;
   // energy / gradient scratch: phi, D^T m (1 field each) and P^T D^T m (3 fields)
   float* ews = nullptr;
 
@@ -161,6 +163,17 @@ demag_status tc_sync_status(demag_plan* plan, cudaStream_t st);
 bool tc_ready(const demag_plan* plan, demag_precision prec);
 void tc_destroy(demag_plan* plan);
 
+// compressed kernels (compress.cu)
+struct CompressedView {
+  int rho[3];
+  const float2* cpair;  // symbol pairs [rhomax][3 q][3 p][Lmax/2]
+  const float* core;    // [3 q][rho3][rho2][rho1]
+};
+bool compressed_view(const demag_plan* plan, CompressedView* v);
+void compress_destroy(demag_plan* plan);
+demag_status launch_core_kron(demag_plan* plan, int batch, const int r[3], const float* G, float* out,
+                              cudaStream_t st);
+
 // 3D FFT convolution (fft3d.cu)
 demag_status fft3d_forward(demag_plan* plan, const float* m, float* phi, cudaStream_t st);
 void fft3d_destroy(demag_plan* plan);
@@ -173,6 +186,9 @@ struct GridInfo {
 __global__ void nodes_kernel(int M, double c0, double cscale, double* nodes, double* scale);
 __global__ void generators_kernel(int M, int glen, GridInfo g, const double* nodes, double* gen);
 demag_status require_uniform(demag_plan* plan, const char* what);
+void dispatch_symbol(demag_plan* P, int axis, int M, int nsets, const double* gen, float* sym, cudaStream_t st);
+__global__ void sympair_kernel(int M, int nsets, int axis, int N, int symstride, int pairstride, const float* sym,
+                               float2* pair);
 __global__ void nonuniform_factor_kernel(int M, int n0, int n1, int n2, size_t tgroup, size_t off1, size_t off2,
                                          int yoff1, int yoff2, const double* nodes, const double* y, double* fac);
 

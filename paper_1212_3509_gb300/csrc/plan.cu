@@ -139,14 +139,18 @@ struct TwiddleD {
 // Circulant symbol of one generator (Sec. 4.2, Eq. fft_pot): c[j] = t[j],
 // c[L-d] = t[-d], zero elsewhere; real FFT of length L = 2N in FP64; E keeps
 // Re/L and F keeps Im/L (E even -> real symbol, F odd -> imaginary symbol).
+// Generators are rows (k * nsets + set) * 3 + axis of `gen`; with nsets = 2
+// the set is the type (0 E, 1 F), with nsets = 3 it is the component q of a
+// compressed kernel, whose axis-q generators are odd (F-like).
 template <int LOGN>
-__global__ void __launch_bounds__(256) symbol_kernel(int M, int glen, int axis, int n, int symstride,
+__global__ void __launch_bounds__(256) symbol_kernel(int M, int nsets, int glen, int axis, int n, int symstride,
                                                      const double* gen, float* sym) {
   constexpr int N = 1 << LOGN;
   constexpr int L = 2 * N;
   extern __shared__ double2 zs[];
-  const int k = blockIdx.x, type = blockIdx.y;
-  const double* t = gen + (((long)k * 2 + type) * 3 + axis) * glen;  // t[d + n - 1]
+  const int k = blockIdx.x, set = blockIdx.y;
+  const int type = nsets == 2 ? set : (set == axis ? 1 : 0);
+  const double* t = gen + (((long)k * nsets + set) * 3 + axis) * glen;  // t[d + n - 1]
   auto circ = [&](int j) -> double {
     if (j < n) return t[j + n - 1];
     if (j > L - n) return t[(j - L) + n - 1];
@@ -155,7 +159,7 @@ __global__ void __launch_bounds__(256) symbol_kernel(int M, int glen, int axis, 
   for (int j = threadIdx.x; j < N; j += blockDim.x) zs[j] = make_double2(circ(2 * j), circ(2 * j + 1));
   __syncthreads();
   fft_inplace<LOGN, 256, false>(zs, threadIdx.x, TwiddleD{N});
-  float* out = sym + (((long)k * 2 + type) * 3 + axis) * symstride;
+  float* out = sym + (((long)k * nsets + set) * 3 + axis) * symstride;
   for (int f = threadIdx.x; f <= N; f += blockDim.x) {
     double2 a = zs[f % N];
     double2 b = zs[(N - f) % N];
@@ -172,12 +176,12 @@ __global__ void __launch_bounds__(256) symbol_kernel(int M, int glen, int axis, 
 }
 
 // (s[f], s[N - f]) pairs of one axis for the structured kernels, f < N = L_p/2
-__global__ void sympair_kernel(int M, int axis, int N, int symstride, int pairstride, const float* sym,
+__global__ void sympair_kernel(int M, int nsets, int axis, int N, int symstride, int pairstride, const float* sym,
                                float2* pair) {
-  const long total = (long)M * 2 * N;
+  const long total = (long)M * nsets * N;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
     const int f = (int)(i % N);
-    const long kt = i / N;  // k*2 + type
+    const long kt = i / N;  // k * nsets + set
     const float* s = sym + (kt * 3 + axis) * symstride;
     pair[(kt * 3 + axis) * pairstride + f] = make_float2(s[f], s[N - f]);
   }
@@ -192,31 +196,33 @@ __global__ void twiddle_kernel(int L, float2* tw) {
 }
 
 template <int LOGN>
-static void launch_symbol(demag_plan* P, int axis, cudaStream_t st) {
+static void launch_symbol(demag_plan* P, int axis, int M, int nsets, const double* gen, float* sym,
+                          cudaStream_t st) {
   size_t smem = sizeof(double2) << LOGN;
   if (smem > 48 * 1024)
     cudaFuncSetAttribute(symbol_kernel<LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   DEMAG_LAUNCH(P, kFamSetup, st,
-               symbol_kernel<LOGN><<<dim3(P->M, 2), 256, smem, st>>>(P->M, P->glen, axis, P->n[axis],
-                                                                     P->Lmax / 2 + 1, P->gen64, P->sym));
+               symbol_kernel<LOGN><<<dim3(M, nsets), 256, smem, st>>>(M, nsets, P->glen, axis, P->n[axis],
+                                                                      P->Lmax / 2 + 1, gen, sym));
 }
 
-static void dispatch_symbol(demag_plan* P, int axis, cudaStream_t st) {
+// Symbols of axis `axis` for generator rows [M][nsets][3][glen] into [M][nsets][3][Lmax/2 + 1].
+void dispatch_symbol(demag_plan* P, int axis, int M, int nsets, const double* gen, float* sym, cudaStream_t st) {
   switch (ilog2(P->L[axis] / 2)) {
-    case 0: launch_symbol<0>(P, axis, st); break;
-    case 1: launch_symbol<1>(P, axis, st); break;
-    case 2: launch_symbol<2>(P, axis, st); break;
-    case 3: launch_symbol<3>(P, axis, st); break;
-    case 4: launch_symbol<4>(P, axis, st); break;
-    case 5: launch_symbol<5>(P, axis, st); break;
-    case 6: launch_symbol<6>(P, axis, st); break;
-    case 7: launch_symbol<7>(P, axis, st); break;
-    case 8: launch_symbol<8>(P, axis, st); break;
-    case 9: launch_symbol<9>(P, axis, st); break;
-    case 10: launch_symbol<10>(P, axis, st); break;
-    case 11: launch_symbol<11>(P, axis, st); break;
-    case 12: launch_symbol<12>(P, axis, st); break;
-    case 13: launch_symbol<13>(P, axis, st); break;
+    case 0: launch_symbol<0>(P, axis, M, nsets, gen, sym, st); break;
+    case 1: launch_symbol<1>(P, axis, M, nsets, gen, sym, st); break;
+    case 2: launch_symbol<2>(P, axis, M, nsets, gen, sym, st); break;
+    case 3: launch_symbol<3>(P, axis, M, nsets, gen, sym, st); break;
+    case 4: launch_symbol<4>(P, axis, M, nsets, gen, sym, st); break;
+    case 5: launch_symbol<5>(P, axis, M, nsets, gen, sym, st); break;
+    case 6: launch_symbol<6>(P, axis, M, nsets, gen, sym, st); break;
+    case 7: launch_symbol<7>(P, axis, M, nsets, gen, sym, st); break;
+    case 8: launch_symbol<8>(P, axis, M, nsets, gen, sym, st); break;
+    case 9: launch_symbol<9>(P, axis, M, nsets, gen, sym, st); break;
+    case 10: launch_symbol<10>(P, axis, M, nsets, gen, sym, st); break;
+    case 11: launch_symbol<11>(P, axis, M, nsets, gen, sym, st); break;
+    case 12: launch_symbol<12>(P, axis, M, nsets, gen, sym, st); break;
+    case 13: launch_symbol<13>(P, axis, M, nsets, gen, sym, st); break;
     default: break;
   }
 }
@@ -254,6 +260,7 @@ static void free_plan_buffers(demag_plan* P) {
   P->prof_pool.clear();
   tc_destroy(P);
   fft3d_destroy(P);
+  compress_destroy(P);
   energy_destroy(P);
 }
 
@@ -352,7 +359,7 @@ extern "C" demag_status demag_build_factors(const demag_grid_desc* d, demag_plan
         DEMAG_LAUNCH(P, kFamSetup, st, twiddle_kernel<<<(P->L[p] + 255) / 256, 256, 0, st>>>(P->L[p], P->twid[p]));
         TRY_CUDA(cudaGetLastError());
       }
-      dispatch_symbol(P, p, st);
+      dispatch_symbol(P, p, P->M, 2, P->gen64, P->sym, st);
       TRY_CUDA(cudaGetLastError());
     }
     TRY_CUDA(cudaMalloc(&P->sympair, sizeof(float2) * (size_t)M * 6 * (P->Lmax / 2)));
@@ -362,7 +369,7 @@ extern "C" demag_status demag_build_factors(const demag_grid_desc* d, demag_plan
       int blocks = (int)((total + 255) / 256);
       if (blocks > 152 * 16) blocks = 152 * 16;
       DEMAG_LAUNCH(P, kFamSetup, st,
-                   sympair_kernel<<<blocks, 256, 0, st>>>(M, p, N, P->Lmax / 2 + 1, P->Lmax / 2, P->sym,
+                   sympair_kernel<<<blocks, 256, 0, st>>>(M, 2, p, N, P->Lmax / 2 + 1, P->Lmax / 2, P->sym,
                                                           P->sympair));
       TRY_CUDA(cudaGetLastError());
     }

@@ -46,6 +46,7 @@ struct ToepAxis {
   long in_bstride, in_qstride;
   float* out;      // node k: out + b*out_bstride + ((k*3 + q)*rcols + l)*n
   long out_bstride;
+  int kmax;        // nodes (generators) of this axis: k < kmax
   const float2* twid;     // exp(-2 pi i m / L), m < L
 };
 
@@ -55,10 +56,11 @@ struct ToepLaunch {
   ToepAxis ax[3];
   int naxes;
   int bx0[4];
-  int M;           // number of nodes
+  int M;           // number of nodes (the largest kmax)
   int kgroup;      // nodes per block
   int pairstride;  // Lmax/2
-  const float2* sympair;  // [M][2][3][pairstride]: (s_f, s_{N-f})
+  int nsets;       // symbol sets per node: 2 (types E, F) or 3 (components of a compressed kernel)
+  const float2* sympair;  // [M][nsets][3][pairstride]: (s_f, s_{N-f}); set = type, or q when nsets = 3
 };
 
 template <int LOGN> struct ToepCfg {
@@ -224,7 +226,7 @@ __global__ void __launch_bounds__(256, ToepCfg<LOGN>::minblocks)
   const int axis = A.axis;
   const int type = (axis == q) ? 1 : 0;  // F on the axis of the component
   const int k0 = blockIdx.y * a.kgroup;
-  const int k1 = min(a.M, k0 + a.kgroup);
+  const int k1 = min(min(a.M, A.kmax), k0 + a.kgroup);
   float* outbase = A.out + b * A.out_bstride + (long)l * n;
   // paired stores need an even length and an 8-byte aligned column start
   // (every (k, q) offset is a multiple of n, so one check per column)
@@ -245,7 +247,7 @@ __global__ void __launch_bounds__(256, ToepCfg<LOGN>::minblocks)
   auto node_loop = [&](auto type_tag) {
     constexpr int TYPE = decltype(type_tag)::value;
     for (int k = k0; k < k1; ++k) {
-      const float2* sp = a.sympair + ((long)(k * 2 + TYPE) * 3 + axis) * a.pairstride;
+      const float2* sp = a.sympair + ((long)(k * a.nsets + (a.nsets == 3 ? q : TYPE)) * 3 + axis) * a.pairstride;
       // 3. first pass in registers on the bins j + r N/R1 of item j
       constexpr int items1 = N / R1;
       constexpr int ipt1 = (items1 + TG - 1) / TG;
@@ -481,22 +483,26 @@ static cudaError_t pick_kgroup(demag_plan* P, int logn, ToepLaunch& a, int gx, c
 
 // Toeplitz matvecs of the given axes: axes that share an FFT length run in
 // one launch (normally all three), each as its own range of blocks.
-static demag_status run_axes(demag_plan* P, ToepAxis* axes, int count, const char* what, cudaStream_t st) {
+static demag_status run_axes(demag_plan* P, ToepAxis* axes, int count, const char* what, cudaStream_t st,
+                             const float2* sympair = nullptr, int nsets = 2) {
   bool done[3] = {false, false, false};
   for (int i = 0; i < count; ++i) {
     if (done[i]) continue;
     const int logn = ilog2i(P->L[axes[i].axis] / 2);
     const int G = groups_per_block(logn);
     ToepLaunch a{};
-    a.M = P->M;
+    a.M = 0;
     a.pairstride = P->Lmax / 2;
-    a.sympair = P->sympair;
+    a.sympair = sympair ? sympair : P->sympair;
+    a.nsets = nsets;
     int gx = 0;
     for (int j = i; j < count; ++j) {
       if (done[j] || ilog2i(P->L[axes[j].axis] / 2) != logn) continue;
       ToepAxis x = axes[j];
       x.n = P->n[x.axis];
       x.twid = P->twid[x.axis];
+      if (x.kmax <= 0) x.kmax = P->M;
+      a.M = x.kmax > a.M ? x.kmax : a.M;
       a.ax[a.naxes] = x;
       a.bx0[a.naxes] = gx;
       gx += (x.ncols + G - 1) / G;
@@ -597,6 +603,49 @@ extern "C" demag_status demag_apply_tucker_batched(demag_plan* P, int batch, con
   s = run_axes(P, ax, 3, "toeplitz_fft_kernel (tucker)", st);
   if (s != DEMAG_OK) return s;
   return launch_weights(P, batch, 1, nullptr, out_w, st);
+}
+
+// Alg. 2 with the compressed kernels of demag_compress_kernel: factors
+// W^(q,p)[:, (i, l)] = T(U_p^(q)[:, i]) V^(q,p)[:, l] through the circulant FFT
+// kernel with the per-component symbol sets, and cores C^(q) (x) G^(q).
+extern "C" demag_status demag_apply_tucker_compressed(demag_plan* P, int batch, const int r[3], const float* core,
+                                                      const float* V, float* out_core, float* out_V, void* stream) {
+  demag_status s = check_fft_plan(P, "demag_apply_tucker_compressed");
+  if (s != DEMAG_OK) return s;
+  if (batch < 1) return set_error(P, DEMAG_EINVAL, "demag_apply_tucker_compressed: batch must be >= 1");
+  if (!r || !core || !V || !out_core || !out_V)
+    return set_error(P, DEMAG_EINVAL, "demag_apply_tucker_compressed: NULL pointer");
+  for (int p = 0; p < 3; ++p)
+    if (r[p] < 1) return set_error(P, DEMAG_EINVAL, "demag_apply_tucker_compressed: r[%d] must be >= 1", p);
+  CompressedView cv;
+  if (!compressed_view(P, &cv))
+    return set_error(P, DEMAG_EINVAL, "demag_apply_tucker_compressed: no compressed kernel (demag_compress_kernel)");
+  cudaStream_t st = (cudaStream_t)stream;
+  long qstride = 0, ostride = 0;
+  for (int p = 0; p < 3; ++p) {
+    qstride += (long)r[p] * P->n[p];
+    ostride += 3L * cv.rho[p] * r[p] * P->n[p];
+  }
+  ToepAxis ax[3];
+  long aoff = 0, ooff = 0;
+  for (int p = 0; p < 3; ++p) {
+    ToepAxis& a = ax[p];
+    a = ToepAxis{};
+    a.axis = p;
+    a.rcols = r[p];
+    a.ncols = batch * 3 * r[p];
+    a.in = V + aoff;
+    a.in_bstride = 3 * qstride;
+    a.in_qstride = qstride;
+    a.out = out_V + ooff;
+    a.out_bstride = ostride;
+    a.kmax = cv.rho[p];
+    aoff += (long)r[p] * P->n[p];
+    ooff += 3L * cv.rho[p] * r[p] * P->n[p];
+  }
+  s = run_axes(P, ax, 3, "toeplitz_fft_kernel (compressed tucker)", st, cv.cpair, 3);
+  if (s != DEMAG_OK) return s;
+  return launch_core_kron(P, batch, r, core, out_core, st);
 }
 
 extern "C" demag_status demag_apply_tucker(demag_plan* P, const int r[3], const float* V, float* out_w,
