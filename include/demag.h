@@ -264,7 +264,10 @@ demag_status demag_copy_compressed(const demag_plan* plan, double* gen, float* c
  * index (i, l) = i r_p + l, and out_V: three mode blocks per item, block p =
  * [rho_p][3][r_p][n_p], row (i, q, l) = T(U_p^(q)[:, i]) V^(q,p)[:, l];
  * phi = sum_q [[out_core^(q); W^(q,1), W^(q,2), W^(q,3)]] with W^(q,p) column
- * (i, l) = row (i, q, l) of block p.  FP32. */
+ * (i, l) = row (i, q, l) of block p.  The core of a component has
+ * prod_p rho_p r_p entries (the ranks multiply, App. B); with out_core NULL it
+ * is left implicit as the Kronecker product of C^(q) (demag_copy_compressed)
+ * and the input core, and core may then be NULL too.  FP32. */
 demag_status demag_apply_tucker_compressed(demag_plan* plan, int batch, const int r[3], const float* core,
                                            const float* V, float* out_core, float* out_V, void* stream);
 

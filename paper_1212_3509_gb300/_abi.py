@@ -214,7 +214,8 @@ def demag_apply_tucker_compressed(plan: Plan, batch: int, r, core, V, out_core, 
     os_ = sum(3 * rho[p] * int(r[p]) * plan.n[p] for p in range(3))
     ncore = int(r[0]) * int(r[1]) * int(r[2])
     nout = rho[0] * r[0] * rho[1] * r[1] * rho[2] * r[2]
-    _check(lib.demag_apply_tucker_compressed(plan.ptr, int(batch), rr, _ptr(core, batch * 3 * ncore, f32, "core"),
+    _check(lib.demag_apply_tucker_compressed(plan.ptr, int(batch), rr,
+                                             _ptr(core, batch * 3 * ncore, f32, "core"),
                                              _ptr(V, batch * 3 * qs, f32, "V"),
                                              _ptr(out_core, batch * 3 * nout, f32, "out_core"),
                                              _ptr(out_V, batch * os_, f32, "out_V"), _stream(stream)), plan.ptr)

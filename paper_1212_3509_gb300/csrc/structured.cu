@@ -613,7 +613,7 @@ extern "C" demag_status demag_apply_tucker_compressed(demag_plan* P, int batch, 
   demag_status s = check_fft_plan(P, "demag_apply_tucker_compressed");
   if (s != DEMAG_OK) return s;
   if (batch < 1) return set_error(P, DEMAG_EINVAL, "demag_apply_tucker_compressed: batch must be >= 1");
-  if (!r || !core || !V || !out_core || !out_V)
+  if (!r || !V || !out_V || (out_core && !core))
     return set_error(P, DEMAG_EINVAL, "demag_apply_tucker_compressed: NULL pointer");
   for (int p = 0; p < 3; ++p)
     if (r[p] < 1) return set_error(P, DEMAG_EINVAL, "demag_apply_tucker_compressed: r[%d] must be >= 1", p);
@@ -644,7 +644,7 @@ extern "C" demag_status demag_apply_tucker_compressed(demag_plan* P, int batch, 
     ooff += 3L * cv.rho[p] * r[p] * P->n[p];
   }
   s = run_axes(P, ax, 3, "toeplitz_fft_kernel (compressed tucker)", st, cv.cpair, 3);
-  if (s != DEMAG_OK) return s;
+  if (s != DEMAG_OK || !out_core) return s;
   return launch_core_kron(P, batch, r, core, out_core, st);
 }
 

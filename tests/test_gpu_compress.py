@@ -185,3 +185,15 @@ def test_needs_compression_first(D):
         D.demag_compressed_ranks(P)
     with pytest.raises(D.DemagError):
         D.demag_compress_kernel(P, 0.0)
+
+
+def test_implicit_core_gives_the_same_factors(D):
+    n, ranks = (20, 24, 16), (2, 3, 2)
+    P = D.demag_build_factors(n, (1.0, 1.0, 1.0), 21)
+    D.demag_compress_kernel(P, 1e-5)
+    core, flat = _inputs(n, ranks, 4)
+    rho, _, oV = _run(D, P, n, ranks, core, flat)
+    out_V = torch.empty(len(oV), device="cuda")
+    D.demag_apply_tucker_compressed(P, 1, ranks, None, dev(flat), None, out_V)
+    torch.cuda.synchronize()
+    assert np.array_equal(host(out_V), oV)
