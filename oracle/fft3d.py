@@ -92,3 +92,54 @@ def apply_fft3d(m: np.ndarray, n, h, R: int, c0: float = 2.15, K=None) -> np.nda
         acc += K[q] * np.fft.fftn(m[q], s=L, axes=(0, 1, 2))
     phi = np.fft.ifftn(acc)
     return phi.real[: n[2], : n[1], : n[0]].copy()
+
+
+def dense_field_kernels(n, h, R: int, c0: float = 2.15, L=None):
+    """K_pq (p, q = 1..3) of h_d[p] = sum_q IDFT(K_pq . DFT(m^(q))): complex [3, 3, L3, L2, L1].
+
+    h_d = -grad phi with the analytic derivative factors of oracle.field: the
+    axis-p factor of every term of Eq. conv_pot is replaced by its derivative
+    (dE for E, dF for F), and the node sum is folded in Fourier space as for
+    the potential.  The derivative generators carry 1/s, so the scale is c.
+    """
+    from .field import gen_dE, gen_dF
+    n = tuple(int(v) for v in n)
+    if R < 5 or R % 2 == 0:
+        raise ValueError("R must be odd and >= 5")
+    M = (R - 1) // 2
+    s, hh = scaled_spacing(n, h)
+    _, _, tau, omega = sinc_nodes(M, c0)
+    L = padded_lengths(n) if L is None else tuple(int(v) for v in L)
+    K = np.zeros((3, 3, L[2], L[1], L[0]), dtype=np.complex128)
+    for k in range(M):
+        spec = {}
+        for p in range(3):
+            gens = (("E", gen_E), ("F", gen_F), ("dE", gen_dE), ("dF", gen_dF))
+            for kind, gen in gens:
+                g = gen(tau[k], hh[p], n[p])
+                if kind.startswith("d"):
+                    g = g / s
+                spec[(p, kind)] = np.fft.fft(circulant_column(g, n[p], L[p]))
+        for d in range(3):
+            for q in range(3):
+                a = []
+                for p in range(3):
+                    kind = factor_kind(p, q)
+                    a.append(spec[(p, "d" + kind if p == d else kind)])
+                K[d, q] -= omega[k] * (a[2][:, None, None] * a[1][None, :, None] * a[0][None, None, :])
+    return (C_POT * s) * K
+
+
+def apply_field_fft3d(m: np.ndarray, n, h, R: int, c0: float = 2.15, K=None) -> np.ndarray:
+    """h_d [3, n3, n2, n1] by one 3D FFT convolution with the summed derivative kernels."""
+    n = tuple(int(v) for v in n)
+    m = np.asarray(m, dtype=np.float64)
+    if K is None:
+        K = dense_field_kernels(n, h, R, c0)
+    L = K.shape[2:]
+    X = [np.fft.fftn(m[q], s=L, axes=(0, 1, 2)) for q in range(3)]
+    out = np.zeros((3, n[2], n[1], n[0]))
+    for d in range(3):
+        acc = sum(K[d, q] * X[q] for q in range(3))
+        out[d] = np.fft.ifftn(acc).real[: n[2], : n[1], : n[0]]
+    return out

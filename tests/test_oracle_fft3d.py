@@ -107,3 +107,30 @@ def test_planted_mistakes_are_caught(monkeypatch):
         mp.setattr(fft3d, "factor_kind", lambda p, q: orig_kind(p, (q + 1) % 3))
         assert _fft_vs_modes() > 1e-3, "component"
     assert _fft_vs_modes() < 1e-12
+
+
+@pytest.mark.parametrize("n,h", SHAPES[:2])
+def test_field_by_fft_equals_the_kronecker_field(n, h):
+    from oracle import field as ofield
+    rng = np.random.default_rng(12)
+    m = rng.standard_normal((3, n[2], n[1], n[0]))
+    ref = ofield.apply_field(m, n, h, 21)
+    got = fft3d.apply_field_fft3d(m, n, h, 21)
+    assert np.linalg.norm(got - ref) <= 1e-12 * np.linalg.norm(ref)
+
+
+def test_field_kernels_real_symmetric_and_parities():
+    # K_pq real, K_pq = K_qp, odd in w_p and w_q for p != q, even otherwise
+    n, h = (6, 4, 5), (1.0, 0.7, 1.3)
+    K = fft3d.dense_field_kernels(n, h, 21)
+    scale = np.abs(K).max()
+    assert np.abs(K.imag).max() <= 1e-13 * scale
+    for p in range(3):
+        for q in range(3):
+            assert np.abs(K[p, q] - K[q, p]).max() <= 1e-13 * scale
+            Kr = K[p, q].real
+            for a in range(3):
+                ax = 2 - a
+                mirrored = np.roll(np.flip(Kr, axis=ax), 1, axis=ax)
+                odd = (p != q) and (a == p or a == q)
+                assert np.abs(mirrored - (-Kr if odd else Kr)).max() <= 1e-13 * scale, (p, q, a)
