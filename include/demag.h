@@ -167,6 +167,18 @@ demag_status demag_apply_full(demag_plan* plan, const float* m, float* phi,
  * DEMAG_EUNSUPPORTED when some n_p > 512. */
 demag_status demag_apply_full_fft(demag_plan* plan, const float* m, float* phi, void* stream);
 
+/* The stray field h_d = -grad phi of demag_stray_field_exact (analytic
+ * derivative factors, h_d[p] = sum_q K_pq * m^(q)) by one 3D FFT convolution:
+ * the six node-summed derivative kernels K_pq (real, K_pq = K_qp) are built
+ * once per plan (FP64 sums, stored FP32 on the octant: 24 prod_p (L_p/2+1)
+ * bytes) and an application is five FFT passes, the axis-3 pass multiplying
+ * the three component spectra by the 3 x 3 kernel.  m: float [3][n3][n2][n1],
+ * hd: float [3][n3][n2][n1] (overwritten), device pointers, not overlapping.
+ * The first call builds the kernels and grows the spectra workspace (make it
+ * before any stream capture).  Uniform grids with n_p <= 512 only
+ * (DEMAG_EUNSUPPORTED otherwise).  Asynchronous on `stream`. */
+demag_status demag_stray_field_fft(demag_plan* plan, const float* m, float* hd, void* stream);
+
 /* Apply several plans' operators in one call: phi[i] = P_i m[i] for
  * i < count.  Arrays of device pointers live in HOST memory.  Grids may
  * differ in shape; every plan must already have its workspace for `prec`

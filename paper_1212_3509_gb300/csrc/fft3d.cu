@@ -60,6 +60,7 @@ template <int LOGN> struct F3 {
   static constexpr int G3 = f3_fibres_p3(N);  // P3: fibres per block, two buffers each
   static constexpr int BLOCK3 = G3 * TG;
   static constexpr size_t smem3 = ((size_t)N + (size_t)2 * G3 * BS) * sizeof(float2);
+  static constexpr size_t smem3f = ((size_t)N + (size_t)3 * G3 * BS) * sizeof(float2);  // field: 3 spectra
   static constexpr int PER = N / TG;  // bins per thread of its fibre
   // N = 2^(4j+1): the radix-2 pass is skipped on zero-padded input (forward)
   // and folded into the reader of the first N/2 outputs (inverse)
@@ -248,7 +249,9 @@ struct Fft3dArgs {
   float2* s2;             // [3][L2][H1][n3]; S4 [n2][n3][H1] aliases it
   float* phi;             // [n3][n2][n1]
   const float* kst;       // [3][H1][H2][H3]: Im K^(q) on the octant
+  const float* kfield;    // [6][H1][H2][H3]: the real field kernels K_pq on the octant (pairs 00 11 22 01 02 12)
   const float2* tw;       // exp(-2 pi i m / N) of this pass's axis, m < N
+  int nco;                // components after P3: 1 (potential) or 3 (field)
 };
 
 template <int LOGN>
@@ -472,7 +475,79 @@ __global__ void __launch_bounds__(F3<LOGN>::BLOCK3, LOGN <= 9 ? 2 : 1) fft3d_p3_
   }
 }
 
-// P4: inverse FFT along w2 of fibres w1 at fixed i3, i2 < n2 kept.
+// P3 of the stray field: at fixed w1, fibres w2 along i3: forward FFT of the
+// three components (all three copied in at once, cp.async), then per bin
+// Y_p = sum_q K_pq X_q with the real, symmetric field kernels (in place: a
+// bin of Y needs only the same bin of the X), inverse FFTs, i3 < n3 kept, into
+// S3[p][i3][w1][w2].  K_pq is odd in w_p and w_q for p != q and even
+// otherwise, so the octant value takes a sign for each mirrored odd axis.
+template <int LOGN>
+__global__ void __launch_bounds__(F3<LOGN>::BLOCK3, LOGN <= 9 ? 2 : 1) fft3d_p3f_kernel(const __grid_constant__ Fft3dArgs a) {
+  using C = F3<LOGN>;
+  constexpr int N = C::N, TG = C::TG, G = C::G3, BS = C::BS, PER = C::PER;
+  extern __shared__ float2 sm3[];
+  float2* tw = sm3;
+  const int g = threadIdx.x / TG, lt = threadIdx.x % TG;
+  float2* bq[3] = {sm3 + N + g * BS, sm3 + N + (G + g) * BS, sm3 + N + (2 * G + g) * BS};
+  const int tiles = (a.L2 + G - 1) / G;
+  const int tile = blockIdx.x % tiles;
+  const int w1 = blockIdx.x / tiles;
+  const int w2 = tile * G + g;
+  const bool valid = w2 < a.L2;
+  const bool m2 = w2 > a.L2 / 2;
+  const int w2f = m2 ? a.L2 - w2 : w2;
+  const int nload = valid ? a.n3 : 0;
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+    copy_fibre_async<LOGN, C::SL>(bq[c], lt, a.s2 + (((size_t)c * a.L2 + (valid ? w2 : 0)) * a.H1 + w1) * a.n3, nload);
+  cp_async_commit();
+  load_twiddles<LOGN>(tw, a.tw);
+  cp_async_wait<0>();
+  __syncthreads();
+#pragma unroll
+  for (int c = 0; c < 3; ++c) fwd_fft<LOGN>(bq[c], lt, tw);
+  const size_t oct = (size_t)a.H1 * a.H2 * a.H3;
+  const float* krow = a.kfield + ((size_t)w1 * a.H2 + (valid ? w2f : 0)) * a.H3;
+#pragma unroll 4
+  for (int j = 0; j < PER; ++j) {
+    const int w3 = lt + j * TG;
+    const bool m3 = w3 > N / 2;
+    const int w3f = m3 ? N - w3 : w3;
+    const float k00 = __ldg(krow + w3f), k11 = __ldg(krow + oct + w3f), k22 = __ldg(krow + 2 * oct + w3f);
+    float k01 = __ldg(krow + 3 * oct + w3f), k02 = __ldg(krow + 4 * oct + w3f), k12 = __ldg(krow + 5 * oct + w3f);
+    if (m2) {
+      k01 = -k01;
+      k12 = -k12;
+    }
+    if (m3) {
+      k02 = -k02;
+      k12 = -k12;
+    }
+    const int b = pad16(w3);
+    const float2 x0 = bq[0][b], x1 = bq[1][b], x2 = bq[2][b];
+    bq[0][b] = make_float2(k00 * x0.x + k01 * x1.x + k02 * x2.x, k00 * x0.y + k01 * x1.y + k02 * x2.y);
+    bq[1][b] = make_float2(k01 * x0.x + k11 * x1.x + k12 * x2.x, k01 * x0.y + k11 * x1.y + k12 * x2.y);
+    bq[2][b] = make_float2(k02 * x0.x + k12 * x1.x + k22 * x2.x, k02 * x0.y + k12 * x1.y + k22 * x2.y);
+  }
+  __syncwarp();
+#pragma unroll
+  for (int c = 0; c < 3; ++c) inv_fft<LOGN>(bq[c], lt, tw);
+  __syncthreads();  // the transposed stores read every fibre's buffers
+  const int lim = min(G, a.L2 - tile * G);
+  const int gg = threadIdx.x % G;
+  if (gg < lim) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const float2* src = sm3 + N + (c * G + gg) * BS;
+      const size_t step = (size_t)TG * a.H1 * a.L2;
+      float2* dst = a.s1 + (size_t)c * a.n3 * a.H1 * a.L2 + (size_t)w1 * a.L2 + (size_t)tile * G + gg +
+                    (size_t)(threadIdx.x / G) * a.H1 * a.L2;
+      for (int i3 = threadIdx.x / G; i3 < a.n3; i3 += TG, dst += step) *dst = inv_out<LOGN>(src, i3, tw);
+    }
+  }
+}
+
+// P4: inverse FFT along w2 of fibres w1 at fixed (c, i3), i2 < n2 kept.
 template <int LOGN>
 __global__ void __launch_bounds__(F3<LOGN>::BLOCK) fft3d_p4_kernel(const __grid_constant__ Fft3dArgs a) {
   using C = F3<LOGN>;
@@ -485,14 +560,15 @@ __global__ void __launch_bounds__(F3<LOGN>::BLOCK) fft3d_p4_kernel(const __grid_
   float2* buf = bufs + g * BS;
   const int tiles = (a.H1 + G - 1) / G;
   const int tile = blockIdx.x % tiles;
-  const int i3 = blockIdx.x / tiles;
+  const int ci3 = blockIdx.x / tiles;  // c * n3 + i3
+  const int c = ci3 / a.n3, i3 = ci3 % a.n3;
   const int w1 = tile * G + g;
-  const float2* in = a.s1 + ((size_t)i3 * a.H1 + w1) * a.L2;
+  const float2* in = a.s1 + (size_t)c * a.n3 * a.H1 * a.L2 + ((size_t)i3 * a.H1 + w1) * a.L2;
   stage_fibre<LOGN, N>(buf, lt, in, w1 < a.H1 ? N : 0);
   __syncthreads();
   inv_fft<LOGN>(buf, lt, tw);
   __syncthreads();  // the transposed store reads every fibre's buffer
-  float2* out = a.s2 + (size_t)i3 * a.H1 + (size_t)tile * G;  // S4[i2][i3][w1]
+  float2* out = a.s2 + (size_t)c * a.n2 * a.n3 * a.H1 + (size_t)i3 * a.H1 + (size_t)tile * G;  // S4[c][i2][i3][w1]
   const int lim = min(G, a.H1 - tile * G);
   const int gg = threadIdx.x % G;
   if (gg < lim) {
@@ -504,7 +580,7 @@ __global__ void __launch_bounds__(F3<LOGN>::BLOCK) fft3d_p4_kernel(const __grid_
   }
 }
 
-// P5: inverse real FFT along w1 of fibre pairs f, f + 1 (f = i2 n3 + i3).
+// P5: inverse real FFT along w1 of fibre pairs f, f + 1 (f = (c n2 + i2) n3 + i3).
 template <int LOGN>
 __global__ void __launch_bounds__(F3<LOGN>::BLOCK) fft3d_p5_kernel(const __grid_constant__ Fft3dArgs a) {
   using C = F3<LOGN>;
@@ -515,7 +591,7 @@ __global__ void __launch_bounds__(F3<LOGN>::BLOCK) fft3d_p5_kernel(const __grid_
   load_twiddles<LOGN>(tw, a.tw);
   const int g = threadIdx.x / TG, lt = threadIdx.x % TG;
   float2* buf = bufs + g * BS;
-  const int nf = a.n2 * a.n3;
+  const int nf = a.nco * a.n2 * a.n3;
   const int fa = blockIdx.x * T + 2 * g;
   const bool va = fa < nf, vb = fa + 1 < nf;
   const float2* ina = a.s2 + (size_t)fa * a.H1;
@@ -551,8 +627,14 @@ __global__ void __launch_bounds__(F3<LOGN>::BLOCK) fft3d_p5_kernel(const __grid_
   }
   __syncthreads();
   inv_fft<LOGN>(buf, lt, tw);
-  float* oa = a.phi + ((size_t)(fa % a.n3) * a.n2 + fa / a.n3) * a.n1;
-  float* ob = a.phi + ((size_t)((fa + 1) % a.n3) * a.n2 + (fa + 1) / a.n3) * a.n1;
+  // fibre f = (c n2 + i2) n3 + i3 -> phi[c][i3][i2][:]
+  auto row = [&](int f) {
+    const int i3 = f % a.n3, ci2 = f / a.n3;
+    const int i2 = ci2 % a.n2, c = ci2 / a.n2;
+    return a.phi + (((size_t)c * a.n3 + i3) * a.n2 + i2) * a.n1;
+  };
+  float* oa = row(va ? fa : 0);
+  float* ob = row(vb ? fa + 1 : 0);
   for (int j = lt; j < a.n1; j += TG) {
     const float2 v = inv_out<LOGN>(buf, j, tw);
     if (va) oa[j] = v.x;
@@ -563,11 +645,12 @@ __global__ void __launch_bounds__(F3<LOGN>::BLOCK) fft3d_p5_kernel(const __grid_
 // ---------------------------------------------------------------- setup
 
 // sym[k][type][p][w] (w <= L_p/2), FP64: the DFT of the circulant embedding
-// of generator row (k, type, p) divided by L_p; type 0 (E, even): the real
-// part E0 + 2 sum_d E_d cos(2 pi w d / L); type 1 (F, odd): the imaginary part
-// -2 sum_d F_d sin(2 pi w d / L).  Angles are reduced exactly ((w d) mod L).
+// of generator row (k, type, p) divided by L_p; an even generator: the real
+// part t0 + 2 sum_d t_d cos(2 pi w d / L); the odd one (type odd_type: F of
+// the generators, dE of the derivative generators): the imaginary part
+// -2 sum_d t_d sin(2 pi w d / L).  Angles are reduced exactly ((w d) mod L).
 __global__ void fft3d_symbols_kernel(int M, int glen, int hstride, int n1, int n2, int n3, int L1, int L2, int L3,
-                                     const double* gen64, double* sym) {
+                                     const double* gen64, double* sym, int odd_type) {
   const long total = (long)M * 2 * 3 * hstride;
   for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total;
        idx += (long)gridDim.x * blockDim.x) {
@@ -587,9 +670,9 @@ __global__ void fft3d_symbols_kernel(int M, int glen, int hstride, int n1, int n
         const int r = (int)(((long)w * d) % L);
         double sn, cs;
         sincospi(2.0 * (double)r / (double)L, &sn, &cs);
-        acc += type == 0 ? t[d] * cs : t[d] * sn;
+        acc += type != odd_type ? t[d] * cs : t[d] * sn;
       }
-      val = type == 0 ? (t[0] + 2.0 * acc) : (-2.0 * acc);
+      val = type != odd_type ? (t[0] + 2.0 * acc) : (-2.0 * acc);
       val /= (double)L;
     }
     sym[idx] = val;
@@ -618,9 +701,41 @@ __global__ void fft3d_kernel_kernel(int M, int hstride, int H1, int H2, int H3, 
   }
 }
 
+// kfield[pair][w1][w2][w3] (pairs (d, q) = 00 11 22 01 02 12), the real field
+// kernels of h_d[d] = sum_q K_dq * m^(q): every factor of Eq. conv_pot's term k
+// with the axis-d factor replaced by its derivative (dE for E, dF for F; the
+// derivative generators carry 1/s), summed over k with scale_k = c s omega_k
+// (FP64, one rounding).  From the reduced symbols (real part of an even
+// factor, imaginary part of an odd one): d == q has no odd factor and the sign
+// of h = -grad phi; d != q has two (dE along d, F along q), i^2 = -1, sign +.
+__global__ void fft3d_field_kernel_kernel(int M, int hstride, int H1, int H2, int H3, const double* scale,
+                                          const double* sym, const double* dsym, float* kf) {
+  __shared__ double a[kMaxTerms];
+  const int pd[6] = {0, 1, 2, 0, 0, 1}, pq[6] = {0, 1, 2, 1, 2, 2};
+  const int w2 = blockIdx.x % H2;
+  const int rest = blockIdx.x / H2;
+  const int w1 = rest % H1, pair = rest / H1;
+  const int d = pd[pair], q = pq[pair];
+  auto factor = [&](int k, int axis, int w) {
+    const int type = axis == q ? 1 : 0;
+    const double* src = axis == d ? dsym : sym;
+    return src[(((long)k * 2 + type) * 3 + axis) * hstride + w];
+  };
+  const double sign = d == q ? -1.0 : 1.0;
+  for (int k = threadIdx.x; k < M; k += blockDim.x) a[k] = sign * scale[k] * factor(k, 0, w1) * factor(k, 1, w2);
+  __syncthreads();
+  float* out = kf + (((size_t)pair * H1 + w1) * H2 + w2) * H3;
+  for (int w3 = threadIdx.x; w3 < H3; w3 += blockDim.x) {
+    double acc = 0.0;
+    for (int k = 0; k < M; ++k) acc += a[k] * factor(k, 2, w3);
+    out[w3] = (float)acc;
+  }
+}
+
 struct Fft3dState {
   int logL[3];
   float* kst = nullptr;
+  float* kfield = nullptr;  // stray-field kernels, built on first use
   float2* s1 = nullptr;
   float2* s2 = nullptr;
   size_t s1_elems = 0, s2_elems = 0;
@@ -635,18 +750,20 @@ static int log2_exact(int v) {
 template <int LOGN>
 static demag_status launch_pass(demag_plan* P, int pass, const Fft3dArgs& a, int blocks, cudaStream_t st) {
   using C = F3<LOGN>;
+  // pass 6 is the P3 of the stray field
   const void* fn = pass == 1 ? (const void*)fft3d_p1_kernel<LOGN>
                  : pass == 2 ? (const void*)fft3d_p2_kernel<LOGN>
                  : pass == 3 ? (const void*)fft3d_p3_kernel<LOGN>
                  : pass == 4 ? (const void*)fft3d_p4_kernel<LOGN>
-                             : (const void*)fft3d_p5_kernel<LOGN>;
+                 : pass == 5 ? (const void*)fft3d_p5_kernel<LOGN>
+                             : (const void*)fft3d_p3f_kernel<LOGN>;
   // the attribute is set on first use per kernel and device (so that later
   // launches, e.g. under stream capture, make no attribute calls)
-  static unsigned long long done[6] = {0, 0, 0, 0, 0, 0};
+  static unsigned long long done[7] = {0, 0, 0, 0, 0, 0, 0};
   int dev = 0;
   cudaGetDevice(&dev);
   const unsigned long long bit = 1ull << (dev & 63);
-  const size_t smem = pass == 3 ? C::smem3 : C::smem;
+  const size_t smem = pass == 3 ? C::smem3 : (pass == 6 ? C::smem3f : C::smem);
   if (smem > 48 * 1024 && !(done[pass] & bit)) {
     DEMAG_CUDA(P, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     done[pass] |= bit;
@@ -656,7 +773,8 @@ static demag_status launch_pass(demag_plan* P, int pass, const Fft3dArgs& a, int
     case 2: DEMAG_LAUNCH(P, kFamFFT3D, st, fft3d_p2_kernel<LOGN><<<blocks, C::BLOCK, C::smem, st>>>(a)); break;
     case 3: DEMAG_LAUNCH(P, kFamFFT3D, st, fft3d_p3_kernel<LOGN><<<blocks, C::BLOCK3, C::smem3, st>>>(a)); break;
     case 4: DEMAG_LAUNCH(P, kFamFFT3D, st, fft3d_p4_kernel<LOGN><<<blocks, C::BLOCK, C::smem, st>>>(a)); break;
-    default: DEMAG_LAUNCH(P, kFamFFT3D, st, fft3d_p5_kernel<LOGN><<<blocks, C::BLOCK, C::smem, st>>>(a)); break;
+    case 5: DEMAG_LAUNCH(P, kFamFFT3D, st, fft3d_p5_kernel<LOGN><<<blocks, C::BLOCK, C::smem, st>>>(a)); break;
+    default: DEMAG_LAUNCH(P, kFamFFT3D, st, fft3d_p3f_kernel<LOGN><<<blocks, C::BLOCK3, C::smem3f, st>>>(a)); break;
   }
   DEMAG_LAUNCHED(P, "fft3d pass");
   return DEMAG_OK;
@@ -719,7 +837,7 @@ demag_status fft3d_prepare(demag_plan* P, cudaStream_t st) {
     if (blocks > 152 * 32) blocks = 152 * 32;
     DEMAG_LAUNCH(P, kFamSetup, st,
                  fft3d_symbols_kernel<<<blocks, 256, 0, st>>>(P->M, P->glen, hstride, n1, n2, n3, L1, L2, L3,
-                                                              P->gen64, sym));
+                                                              P->gen64, sym, 1));
     if ((e = cudaGetLastError()) != cudaSuccess) return fail(e, "fft3d_symbols_kernel");
     DEMAG_LAUNCH(P, kFamSetup, st,
                  fft3d_kernel_kernel<<<3 * H1 * H2, 256, 0, st>>>(P->M, hstride, H1, H2, H3, P->scale, sym,
@@ -732,9 +850,61 @@ demag_status fft3d_prepare(demag_plan* P, cudaStream_t st) {
   return DEMAG_OK;
 }
 
+// The stray-field kernels (once per plan) and room for three components in
+// S3 (it aliases S1).
+static demag_status fft3d_prepare_field(demag_plan* P, cudaStream_t st) {
+  demag_status rc = fft3d_prepare(P, st);
+  if (rc != DEMAG_OK) return rc;
+  Fft3dState* S = static_cast<Fft3dState*>(P->f3);
+  if (S->kfield) return DEMAG_OK;
+  rc = ensure_field_generators(P, st);
+  if (rc != DEMAG_OK) return rc;
+  const int n1 = P->n[0], n2 = P->n[1], n3 = P->n[2];
+  const int L1 = P->L[0], L2 = P->L[1], L3 = P->L[2];
+  const int H1 = L1 / 2 + 1, H2 = L2 / 2 + 1, H3 = L3 / 2 + 1;
+  const size_t s1_need = std::max(S->s1_elems, (size_t)3 * n3 * H1 * L2);
+  if (s1_need > S->s1_elems) {
+    DEMAG_CUDA(P, cudaStreamSynchronize(st));
+    cudaFree(S->s1);
+    S->s1 = nullptr;
+    S->s1_elems = 0;
+    DEMAG_CUDA(P, cudaMalloc(&S->s1, sizeof(float2) * s1_need));
+    S->s1_elems = s1_need;
+  }
+  const int hstride = std::max(H1, std::max(H2, H3));
+  const size_t nsym = (size_t)P->M * 6 * hstride;
+  double* sym = nullptr;
+  float* kf = nullptr;
+  auto fail = [&](cudaError_t e, const char* what) {
+    cudaFree(sym);
+    cudaFree(kf);
+    return cuda_error(P, e, what);
+  };
+  cudaError_t e;
+  if ((e = cudaMalloc(&sym, sizeof(double) * 2 * nsym)) != cudaSuccess) return fail(e, "malloc field symbols");
+  if ((e = cudaMalloc(&kf, sizeof(float) * 6 * (size_t)H1 * H2 * H3)) != cudaSuccess) return fail(e, "malloc kfield");
+  int blocks = (int)((nsym + 255) / 256);
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  DEMAG_LAUNCH(P, kFamSetup, st,
+               fft3d_symbols_kernel<<<blocks, 256, 0, st>>>(P->M, P->glen, hstride, n1, n2, n3, L1, L2, L3, P->gen64,
+                                                            sym, 1));
+  DEMAG_LAUNCH(P, kFamSetup, st,
+               fft3d_symbols_kernel<<<blocks, 256, 0, st>>>(P->M, P->glen, hstride, n1, n2, n3, L1, L2, L3, P->gend,
+                                                            sym + nsym, 0));
+  DEMAG_LAUNCH(P, kFamSetup, st,
+               fft3d_field_kernel_kernel<<<6 * H1 * H2, 256, 0, st>>>(P->M, hstride, H1, H2, H3, P->scale, sym,
+                                                                      sym + nsym, kf));
+  if ((e = cudaGetLastError()) != cudaSuccess) return fail(e, "fft3d field kernels");
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return fail(e, "fft3d field setup");
+  cudaFree(sym);
+  S->kfield = kf;
+  return DEMAG_OK;
+}
+
 void fft3d_destroy(demag_plan* P) {
   Fft3dState* S = static_cast<Fft3dState*>(P->f3);
   if (!S) return;
+  cudaFree(S->kfield);
   cudaFree(S->kst);
   cudaFree(S->s1);
   cudaFree(S->s2);
@@ -742,11 +912,15 @@ void fft3d_destroy(demag_plan* P) {
   P->f3 = nullptr;
 }
 
-demag_status fft3d_forward(demag_plan* P, const float* m, float* phi, cudaStream_t st) {
-  demag_status rc = fft3d_prepare(P, st);
+// potential (field == false: one output component through P3) or stray
+// field (three output components through the field P3)
+static demag_status fft3d_run(demag_plan* P, const float* m, float* out, bool field, cudaStream_t st) {
+  demag_status rc = field ? fft3d_prepare_field(P, st) : fft3d_prepare(P, st);
   if (rc != DEMAG_OK) return rc;
   const Fft3dState* S = static_cast<const Fft3dState*>(P->f3);
   Fft3dArgs a;
+  a.nco = field ? 3 : 1;
+  a.kfield = S->kfield;
   a.n1 = P->n[0];
   a.n2 = P->n[1];
   a.n3 = P->n[2];
@@ -759,7 +933,7 @@ demag_status fft3d_forward(demag_plan* P, const float* m, float* phi, cudaStream
   a.m = m;
   a.s1 = S->s1;
   a.s2 = S->s2;
-  a.phi = phi;
+  a.phi = out;
   a.kst = S->kst;
   const int l1 = S->logL[0], l2 = S->logL[1], l3 = S->logL[2];
   const int G1 = f3_fibres(1 << l1), G2 = f3_fibres(1 << l2), G3 = f3_fibres_p3(1 << l3);
@@ -769,16 +943,28 @@ demag_status fft3d_forward(demag_plan* P, const float* m, float* phi, cudaStream
   a.tw = P->twid[1];
   if ((rc = dispatch_pass(P, l2, 2, a, 3 * a.H1 * cdiv(a.n3, G2), st)) != DEMAG_OK) return rc;
   a.tw = P->twid[2];
-  if ((rc = dispatch_pass(P, l3, 3, a, a.H1 * cdiv(a.L2, G3), st)) != DEMAG_OK) return rc;
+  if ((rc = dispatch_pass(P, l3, field ? 6 : 3, a, a.H1 * cdiv(a.L2, G3), st)) != DEMAG_OK) return rc;
   a.tw = P->twid[1];
-  if ((rc = dispatch_pass(P, l2, 4, a, a.n3 * cdiv(a.H1, G2), st)) != DEMAG_OK) return rc;
+  if ((rc = dispatch_pass(P, l2, 4, a, a.nco * a.n3 * cdiv(a.H1, G2), st)) != DEMAG_OK) return rc;
   a.tw = P->twid[0];
-  return dispatch_pass(P, l1, 5, a, cdiv((long)a.n2 * a.n3, 2 * G1), st);
+  return dispatch_pass(P, l1, 5, a, cdiv((long)a.nco * a.n2 * a.n3, 2 * G1), st);
+}
+
+demag_status fft3d_forward(demag_plan* P, const float* m, float* phi, cudaStream_t st) {
+  return fft3d_run(P, m, phi, false, st);
 }
 
 }  // namespace demag
 
 using namespace demag;
+
+extern "C" demag_status demag_stray_field_fft(demag_plan* P, const float* m, float* hd, void* stream) {
+  if (!P) return set_error(nullptr, DEMAG_EINVAL, "demag_stray_field_fft: plan is NULL");
+  if (!m || !hd) return set_error(P, DEMAG_EINVAL, "demag_stray_field_fft: NULL pointer");
+  demag_status u = require_uniform(P, "demag_stray_field_fft");
+  if (u != DEMAG_OK) return u;
+  return fft3d_run(P, m, hd, true, (cudaStream_t)stream);
+}
 
 extern "C" demag_status demag_apply_full_fft(demag_plan* P, const float* m, float* phi, void* stream) {
   if (!P) return set_error(nullptr, DEMAG_EINVAL, "demag_apply_full_fft: plan is NULL");

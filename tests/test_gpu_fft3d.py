@@ -140,3 +140,58 @@ def test_fft3d_too_long_axis_is_rejected(D):
     with pytest.raises(D.DemagError) as ei:
         D.demag_apply_full_fft(P, m, phi)
     assert ei.value.status == 5  # DEMAG_EUNSUPPORTED
+
+
+FIELD_SHAPES = [
+    ((16, 16, 16), (1 / 16,) * 3, 41),
+    ((20, 13, 7), (0.1, 0.2, 0.15), 41),
+    ((1, 1, 1), (1.0, 1.0, 1.0), 5),
+    ((2, 3, 1), (0.5, 0.5, 1.0), 11),
+    ((130, 3, 5), (0.01, 0.01, 0.02), 21),
+    ((33, 129, 2), (1.0, 1.0, 1.0), 21),
+    ((5, 40, 67), (2e-9, 3e-9, 1e-9), 41),
+]
+
+
+@pytest.mark.parametrize("n,h,R", FIELD_SHAPES)
+def test_field_fft_vs_oracle(D, n, h, R):
+    from oracle import field as ofield
+    m = synth.random_unit_m(n, 33 + sum(n))
+    P = D.demag_build_factors(n, h, R)
+    hd = torch.empty(3, n[2], n[1], n[0], device="cuda")
+    D.demag_stray_field_fft(P, dev(m), hd)
+    torch.cuda.synchronize()
+    ref = ofield.apply_field(m, n, h, R)
+    assert rel_l2(host(hd), ref) <= 1e-5, rel_l2(host(hd), ref)
+
+
+def test_field_fft_cube_demag_factor(D):
+    n, h = (24, 24, 24), (1 / 24,) * 3
+    P = D.demag_build_factors(n, h, 41)
+    for q in range(3):
+        m = synth.uniform_m(n, q)
+        hd = torch.empty(3, 24, 24, 24, device="cuda")
+        D.demag_stray_field_fft(P, dev(m), hd)
+        torch.cuda.synchronize()
+        mean = host(hd).reshape(3, -1).mean(axis=1)
+        assert abs(mean[q] + 1.0 / 3.0) < 5e-3
+        assert np.all(np.abs(np.delete(mean, q)) < 1e-5)
+
+
+def test_field_fft_matches_the_tensor_core_field_at_128(D):
+    n, h = (128, 128, 128), (1 / 128,) * 3
+    m = dev(synth.vortex_m(n, 4))
+    P = D.demag_build_factors(n, h, 41)
+    a = torch.empty(3, 128, 128, 128, device="cuda")
+    b = torch.empty_like(a)
+    D.demag_stray_field_fft(P, m, a)
+    D.demag_stray_field_exact(P, m, b, "tf32x3")
+    torch.cuda.synchronize()
+    assert rel_l2(host(a), host(b)) <= 2e-5
+    # the potential path still works on the same plan after the field grew the workspace
+    phi = torch.empty(128, 128, 128, device="cuda")
+    D.demag_apply_full_fft(P, m, phi)
+    tc = torch.empty_like(phi)
+    D.demag_apply_full(P, m, tc, "tf32x3")
+    torch.cuda.synchronize()
+    assert rel_l2(host(phi), host(tc)) <= 2e-5
