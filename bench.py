@@ -481,6 +481,16 @@ def run_ours(args, world, rank, local):
                                          (hf - hd).double())) / (den if den > 0 else 1.0),
                                      "work": "h_d[p] = IDFT(sum_q K_pq . DFT(m^(q))), K_pq the node-summed "
                                              "derivative kernels; five FFT passes"}
+        ee = torch.empty(1, dtype=torch.float64, device="cuda")
+        gg = torch.empty_like(m)
+        efn2 = lambda: D.demag_energy_field_fft(P, m, ee, gg)  # noqa: E731
+        efn2()
+        torch.cuda.synchronize()
+        ms_e2 = time_region(efn2, max(3, args.steps // 2), stream)
+        energy["energy_field_fft"] = {"value": whole_job_rate(1, max_over_ranks(ms_e2, world), world),
+                                      "unit": "energy+gradient evals/s", "ms_per_eval": ms_e2,
+                                      "work": "E = -1/2 V sum m.h_d and dE/dm = -V h_d with h_d the analytic "
+                                              "collocation field by one 3D FFT convolution"}
 
     # ---------------- parity against the oracle (sampled) and CPU baseline
     if not args.no_oracle and rank == 0:

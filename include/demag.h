@@ -179,6 +179,16 @@ demag_status demag_apply_full_fft(demag_plan* plan, const float* m, float* phi, 
  * (DEMAG_EUNSUPPORTED otherwise).  Asynchronous on `stream`. */
 demag_status demag_stray_field_fft(demag_plan* plan, const float* m, float* hd, void* stream);
 
+/* Demag energy from the analytic stray field of demag_stray_field_fft:
+ * E = -1/2 h1 h2 h3 sum_i m_i . h_d,i (FP64 sum) and, when grad is not NULL,
+ * dE/dm = -h1 h2 h3 h_d (the field operator is symmetric: its Fourier kernels
+ * are real with K_pq = K_qp, so its real-space kernels are even).  energy: one
+ * double on the device (overwritten); grad: float [3][n3][n2][n1].  Uses a
+ * plan-owned field buffer (3 fields, allocated on the first call).  This is
+ * the energy of the analytic collocation field; demag_energy uses the
+ * second-order difference field instead. */
+demag_status demag_energy_field_fft(demag_plan* plan, const float* m, double* energy, float* grad, void* stream);
+
 /* Apply several plans' operators in one call: phi[i] = P_i m[i] for
  * i < count.  Arrays of device pointers live in HOST memory.  Grids may
  * differ in shape; every plan must already have its workspace for `prec`

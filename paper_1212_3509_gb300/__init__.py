@@ -24,6 +24,7 @@ from ._abi import (  # noqa: F401
     demag_apply_tucker_compressed,
     demag_apply_full_fft,
     demag_stray_field_fft,
+    demag_energy_field_fft,
     demag_apply_full_batched,
     demag_apply_tt,
     demag_apply_tt_batched,

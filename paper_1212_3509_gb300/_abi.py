@@ -53,6 +53,7 @@ _SIGS = {
     "demag_apply_full": (_i, [_vp, _vp, _vp, _i, _vp]),
     "demag_apply_full_fft": (_i, [_vp, _vp, _vp, _vp]),
     "demag_stray_field_fft": (_i, [_vp, _vp, _vp, _vp]),
+    "demag_energy_field_fft": (_i, [_vp, _vp, _vp, _vp, _vp]),
     "demag_build_factors_nonuniform": (_i, [ctypes.POINTER(GridEdgesDesc), ctypes.POINTER(_vp), _vp]),
     "demag_compress_kernel": (_i, [_vp, ctypes.c_double, _vp]),
     "demag_compressed_ranks": (_i, [_vp, ctypes.POINTER(ctypes.c_int)]),
@@ -275,6 +276,13 @@ def demag_stray_field_fft(plan: Plan, m, hd, stream=None):
     import torch
     _check(lib.demag_stray_field_fft(plan.ptr, _ptr(m, 3 * plan.N, torch.float32, "m"),
                                      _ptr(hd, 3 * plan.N, torch.float32, "hd"), _stream(stream)), plan.ptr)
+
+
+def demag_energy_field_fft(plan: Plan, m, energy, grad=None, stream=None):
+    import torch
+    _check(lib.demag_energy_field_fft(plan.ptr, _ptr(m, 3 * plan.N, torch.float32, "m"),
+                                      _ptr(energy, 1, torch.float64, "energy"),
+                                      _ptr(grad, 3 * plan.N, torch.float32, "grad"), _stream(stream)), plan.ptr)
 
 
 def demag_apply_full_batched(plans, ms, phis, precision="bf16x3", stream=None):

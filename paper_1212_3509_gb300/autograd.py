@@ -3,7 +3,9 @@
 Forward calls ``demag_energy`` (phi = P m, h_d = -D phi, E = -1/2 V sum m.h_d,
 all in CUDA kernels) and, when m requires grad, the same call also returns
 dE/dm = 1/2 V (D P m + P^T D^T m) from the hand-written adjoint; backward
-scales that saved gradient by the incoming grad.
+scales that saved gradient by the incoming grad.  With precision "fft_field"
+the energy of the analytic collocation field is used instead
+(``demag_energy_field_fft``: one 3D FFT convolution, dE/dm = -V h_d).
 """
 from __future__ import annotations
 
@@ -20,7 +22,10 @@ class DemagEnergy(torch.autograd.Function):
         m = m.contiguous()
         e = torch.empty((), dtype=torch.float64, device=m.device)
         grad = torch.empty_like(m) if ctx.needs_input_grad[0] else None
-        _abi.demag_energy(plan, m, e, grad, precision)
+        if precision == "fft_field":
+            _abi.demag_energy_field_fft(plan, m, e, grad)
+        else:
+            _abi.demag_energy(plan, m, e, grad, precision)
         ctx.save_for_backward(grad if grad is not None else torch.empty(0, device=m.device))
         return e
 

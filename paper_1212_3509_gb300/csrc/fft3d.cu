@@ -736,6 +736,7 @@ struct Fft3dState {
   int logL[3];
   float* kst = nullptr;
   float* kfield = nullptr;  // stray-field kernels, built on first use
+  float* hfield = nullptr;  // [3][n3][n2][n1] field scratch of the energy
   float2* s1 = nullptr;
   float2* s2 = nullptr;
   size_t s1_elems = 0, s2_elems = 0;
@@ -905,6 +906,7 @@ void fft3d_destroy(demag_plan* P) {
   Fft3dState* S = static_cast<Fft3dState*>(P->f3);
   if (!S) return;
   cudaFree(S->kfield);
+  cudaFree(S->hfield);
   cudaFree(S->kst);
   cudaFree(S->s1);
   cudaFree(S->s2);
@@ -954,6 +956,46 @@ demag_status fft3d_forward(demag_plan* P, const float* m, float* phi, cudaStream
   return fft3d_run(P, m, phi, false, st);
 }
 
+// energy += -1/2 V sum_i m_i . h_i (FP64, one atomic per block), grad = -V h
+__global__ void field_energy_kernel(long count, const float* m, const float* h, double half_vol, float vol,
+                                    double* energy, float* grad) {
+  __shared__ double red[32];
+  double acc = 0.0;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < count; i += (long)gridDim.x * blockDim.x) {
+    const float hv = h[i];
+    acc += (double)m[i] * (double)hv;
+    if (grad) grad[i] = -vol * hv;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    atomicAdd(energy, -half_vol * t);
+  }
+}
+
+demag_status fft3d_energy(demag_plan* P, const float* m, double* energy, float* grad, cudaStream_t st) {
+  demag_status rc = fft3d_prepare_field(P, st);
+  if (rc != DEMAG_OK) return rc;
+  Fft3dState* S = static_cast<Fft3dState*>(P->f3);
+  const long count = 3L * (long)field_size(P);
+  if (!S->hfield) DEMAG_CUDA(P, cudaMalloc(&S->hfield, sizeof(float) * count));
+  rc = fft3d_run(P, m, S->hfield, true, st);
+  if (rc != DEMAG_OK) return rc;
+  const double vol = P->h[0] * P->h[1] * P->h[2];
+  DEMAG_CUDA(P, cudaMemsetAsync(energy, 0, sizeof(double), st));
+  long blocks = (count + 255) / 256;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  DEMAG_LAUNCH(P, kFamEnergy, st,
+               field_energy_kernel<<<(int)blocks, 256, 0, st>>>(count, m, S->hfield, 0.5 * vol, (float)vol, energy,
+                                                               grad));
+  DEMAG_LAUNCHED(P, "field_energy_kernel");
+  return DEMAG_OK;
+}
+
 }  // namespace demag
 
 using namespace demag;
@@ -964,6 +1006,15 @@ extern "C" demag_status demag_stray_field_fft(demag_plan* P, const float* m, flo
   demag_status u = require_uniform(P, "demag_stray_field_fft");
   if (u != DEMAG_OK) return u;
   return fft3d_run(P, m, hd, true, (cudaStream_t)stream);
+}
+
+extern "C" demag_status demag_energy_field_fft(demag_plan* P, const float* m, double* energy, float* grad,
+                                               void* stream) {
+  if (!P) return set_error(nullptr, DEMAG_EINVAL, "demag_energy_field_fft: plan is NULL");
+  if (!m || !energy) return set_error(P, DEMAG_EINVAL, "demag_energy_field_fft: NULL pointer");
+  demag_status u = require_uniform(P, "demag_energy_field_fft");
+  if (u != DEMAG_OK) return u;
+  return fft3d_energy(P, m, energy, grad, (cudaStream_t)stream);
 }
 
 extern "C" demag_status demag_apply_full_fft(demag_plan* P, const float* m, float* phi, void* stream) {

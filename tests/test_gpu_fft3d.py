@@ -195,3 +195,40 @@ def test_field_fft_matches_the_tensor_core_field_at_128(D):
     D.demag_apply_full(P, m, tc, "tf32x3")
     torch.cuda.synchronize()
     assert rel_l2(host(phi), host(tc)) <= 2e-5
+
+
+def test_energy_from_the_fft_field(D):
+    from oracle import field as ofield
+    n, h, R = (20, 13, 7), (0.1, 0.2, 0.15), 41
+    m = synth.random_unit_m(n, 71)
+    P = D.demag_build_factors(n, h, R)
+    e = torch.empty(1, dtype=torch.float64, device="cuda")
+    g = torch.empty(3, n[2], n[1], n[0], device="cuda")
+    D.demag_energy_field_fft(P, dev(m), e, g)
+    torch.cuda.synchronize()
+    hd = ofield.apply_field(m, n, h, R)
+    V = h[0] * h[1] * h[2]
+    ref = -0.5 * V * np.sum(m.astype(np.float64) * hd)
+    assert abs(float(host(e)[0]) - ref) <= 1e-5 * abs(ref)
+    assert rel_l2(host(g), -V * hd) <= 1e-5
+    # uniform cube: E = V_total / 6 (demagnetizing factor 1/3, E = 1/2 N |m|^2 V)
+    n, h = (16, 16, 16), (1 / 16,) * 3
+    P = D.demag_build_factors(n, h, 41)
+    D.demag_energy_field_fft(P, dev(synth.uniform_m(n, 2)), e, None)
+    torch.cuda.synchronize()
+    assert abs(float(host(e)[0]) - 1.0 / 6.0) < 2e-3
+
+
+def test_autograd_energy_fft_field(D):
+    from paper_1212_3509_gb300.autograd import demag_energy_fn
+    n, h = (12, 10, 8), (0.1, 0.1, 0.1)
+    P = D.demag_build_factors(n, h, 21)
+    m = dev(synth.random_unit_m(n, 5)).requires_grad_()
+    E = demag_energy_fn(m, P, "fft_field")
+    E.backward()
+    g = torch.empty_like(m)
+    e = torch.empty(1, dtype=torch.float64, device="cuda")
+    D.demag_energy_field_fft(P, m.detach(), e, g)
+    torch.cuda.synchronize()
+    assert float(E.detach()) == pytest.approx(float(host(e)[0]), rel=1e-12)
+    assert torch.equal(m.grad, g)

@@ -125,3 +125,25 @@ def test_cube_demagnetizing_factor_one_third():
         for p in range(3):
             if p != q:
                 assert abs(hd[p].mean()) < 1e-12
+
+
+def test_field_operator_is_symmetric_so_the_energy_gradient_is_minus_v_h():
+    # h_d = -A m with A symmetric (real, even Fourier kernels K_pq = K_qp): then
+    # E = -1/2 V sum m . h_d has gradient -V h_d; checked by central differences
+    n, h, R = (5, 4, 3), (0.2, 0.25, 0.3), 11
+    rng = np.random.default_rng(21)
+    a, b = rng.standard_normal((2, 3, n[2], n[1], n[0]))
+    ha = field.apply_field(a, n, h, R)
+    hb = field.apply_field(b, n, h, R)
+    assert abs(np.sum(a * hb) - np.sum(b * ha)) <= 1e-12 * np.abs(np.sum(a * hb))
+    V = h[0] * h[1] * h[2]
+
+    def energy(m):
+        return -0.5 * V * np.sum(m * field.apply_field(m, n, h, R))
+
+    grad = -V * ha
+    for _ in range(3):
+        d = rng.standard_normal(a.shape)
+        eps = 1e-4
+        fd = (energy(a + eps * d) - energy(a - eps * d)) / (2 * eps)
+        assert abs(fd - np.sum(grad * d)) <= 1e-8 * abs(fd)
