@@ -443,6 +443,9 @@ def run_ours(args, world, rank, local):
     # ---------------- the same operator by one 3D FFT convolution (Eq. fft_pot, node-summed kernel)
     fft3d = run_fft3d(args, D, world, local, stream, P, m, phi, peaks, n3)
 
+    # ---------------- the FFT path at 1024^3 (1.07 G cells; the cost does not depend on R)
+    fft1024 = run_fft3d_1024(args, D, world, local, stream) if args.n == 256 else None
+
     # ---------------- the same application on a graded (non-uniform) 256^3 grid, BF16x3
     nonuni = run_nonuniform(args, D, world, local, stream, m, n3) if form == "bf16x3" else None
 
@@ -530,6 +533,8 @@ def run_ours(args, world, rank, local):
         nonuni.pop("_phi", None)
         nonuni.pop("_edges", None)
         result["full_nonuniform"] = nonuni
+    if fft1024 is not None:
+        result["full_fft3d_1024"] = fft1024
     if energy is not None:
         result["energy_gradient"] = energy
     if c4 is not None:
@@ -631,6 +636,37 @@ def run_fft3d(args, D, world, local, stream, P, m, phi, peaks, n3):
                                       "frac": pb[top] / (per[top] * 1e-3) / 1e9 / hbm},
                          "traffic": None},
             "clocks": clk.summary(), "_phi": out}
+
+
+def run_fft3d_1024(args, D, world, local, stream):
+    """demag_apply_full_fft on 1024^3, R = 41 (vortex state): about 110 GB of device memory for the
+    input, output, spectra and kernel; skipped when that much is not free."""
+    import gc
+    import torch
+    import synth
+    free, _ = torch.cuda.mem_get_info()
+    if free < 160e9:
+        return {"skipped": f"needs ~110 GB free device memory, {free / 1e9:.0f} GB free"}
+    n3 = (1024, 1024, 1024)
+    P = D.demag_build_factors(n3, (1.0 / 1024,) * 3, 41)
+    m = torch.from_numpy(synth.vortex_m(n3, 1212)).cuda()
+    phi = torch.empty(1024, 1024, 1024, device="cuda")
+    fn = lambda: D.demag_apply_full_fft(P, m, phi)  # noqa: E731
+    fn()
+    torch.cuda.synchronize()
+    fn()
+    barrier(world)
+    with ClockSampler(local) as clk:
+        ms = time_region(fn, 3, stream)
+    ms = max_over_ranks(ms, world)
+    pb = sum(fft3d_pass_bytes(n3))
+    out = {"value": whole_job_rate(1, ms, world), "unit": "apps/s", "ms_per_app": ms, "cells": 1024 ** 3,
+           "algorithmic_bytes_per_app": pb, "hbm_achieved_gbs": pb / (ms * 1e-3) / 1e9,
+           "work": "the 256^3 FFT path at 1024^3 (FFT length 2048 per axis); one GPU", "clocks": clk.summary()}
+    del P, m, phi
+    gc.collect()
+    torch.cuda.empty_cache()
+    return out
 
 
 def graded_edges(n, ratio):

@@ -164,7 +164,7 @@ demag_status demag_apply_full(demag_plan* plan, const float* m, float* phi,
  * (L2/2+1) (L3/2+1) bytes) and the spectra workspace (about
  * 8 (3 (L1/2+1) n3 n2 + 3 L2 (L1/2+1) n3) bytes), so make it before any
  * stream capture; later calls allocate nothing.  Asynchronous on `stream`.
- * DEMAG_EUNSUPPORTED when some n_p > 512. */
+ * DEMAG_EUNSUPPORTED when some n_p > 1024. */
 demag_status demag_apply_full_fft(demag_plan* plan, const float* m, float* phi, void* stream);
 
 /* The stray field h_d = -grad phi of demag_stray_field_exact (analytic
@@ -175,7 +175,7 @@ demag_status demag_apply_full_fft(demag_plan* plan, const float* m, float* phi, 
  * the three component spectra by the 3 x 3 kernel.  m: float [3][n3][n2][n1],
  * hd: float [3][n3][n2][n1] (overwritten), device pointers, not overlapping.
  * The first call builds the kernels and grows the spectra workspace (make it
- * before any stream capture).  Uniform grids with n_p <= 512 only
+ * before any stream capture).  Uniform grids with n_p <= 1024 only
  * (DEMAG_EUNSUPPORTED otherwise).  Asynchronous on `stream`. */
 demag_status demag_stray_field_fft(demag_plan* plan, const float* m, float* hd, void* stream);
 

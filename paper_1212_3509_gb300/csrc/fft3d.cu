@@ -35,15 +35,17 @@
 
 namespace demag {
 
-constexpr int kFft3dMaxLog = 10;  // L_p <= 1024 (n_p <= 512)
+constexpr int kFft3dMaxLog = 11;  // L_p <= 2048 (n_p <= 1024)
 
 // Launch shape for an FFT of length N = 2^LOGN along one axis: TG threads
 // per fibre, G fibres per block (at least 16, so that the transposed stores
 // write runs of >= 128 bytes), buffers padded by pad16 and separated by an
 // odd stride so that the same bin of different fibres falls in different banks.
-constexpr int f3_tg(int N) { return N / 16 < 1 ? 1 : (N / 16 > 32 ? 32 : N / 16); }
-constexpr int f3_block(int N) { return 16 * f3_tg(N) < 256 ? 256 : 16 * f3_tg(N); }
-constexpr int f3_fibres(int N) { return f3_block(N) / f3_tg(N); }
+// N = 2048 takes 64 threads (two warps) per fibre and 8 fibres per block
+// (register and shared-memory budget); its groups synchronise the block.
+constexpr int f3_tg(int N) { return N >= 2048 ? 64 : (N / 16 < 1 ? 1 : (N / 16 > 32 ? 32 : N / 16)); }
+constexpr int f3_fibres(int N) { return N >= 2048 ? 8 : (16 * f3_tg(N) < 256 ? 256 / f3_tg(N) : 16); }
+constexpr int f3_block(int N) { return f3_fibres(N) * f3_tg(N); }
 // P3 double-buffers its fibres: half the fibres per block from N = 512 (two
 // blocks of 256 threads per SM at 128 registers instead of one of 512)
 constexpr int f3_fibres_p3(int N) { return N >= 512 ? f3_fibres(N) / 2 : f3_fibres(N); }
@@ -68,6 +70,16 @@ template <int LOGN> struct F3 {
   static constexpr int SL = FOLD ? N / 2 : N;  // staged length of a forward input
 };
 
+// Synchronise the threads of one FFT group: a warp when the group lies inside
+// one (TG <= 32), else the block (all groups run the same code in lockstep).
+template <int TG>
+__device__ __forceinline__ void group_sync() {
+  if constexpr (TG > 32)
+    __syncthreads();
+  else
+    __syncwarp();
+}
+
 // In-place complex FFT of length N on a pad16-indexed buffer by the TG
 // threads of one group (Stockham, natural order in and out).  First a pass
 // of radix R1 (no twiddles), then radix-16 passes.  tw[m] = exp(-2 pi i m / N).
@@ -90,7 +102,7 @@ __device__ __forceinline__ void fft_pad(float2* buf, int lt, const float2* tw) {
         dft_reg<R1, INV>(v[it]);
       }
     }
-    __syncwarp();
+    group_sync<TG>();
 #pragma unroll
     for (int it = 0; it < ipt; ++it) {
       const int j = lt + it * TG;
@@ -99,7 +111,7 @@ __device__ __forceinline__ void fft_pad(float2* buf, int lt, const float2* tw) {
         for (int r = 0; r < R1; ++r) buf[pad16(j * R1 + r)] = v[it][r];
       }
     }
-    __syncwarp();
+    group_sync<TG>();
   }
   if constexpr (C::NPASS > 1) {
     int Ns = R1;
@@ -125,7 +137,7 @@ __device__ __forceinline__ void fft_pad(float2* buf, int lt, const float2* tw) {
           dft_reg<16, INV>(v[it]);
         }
       }
-      __syncwarp();
+      group_sync<TG>();
 #pragma unroll
       for (int it = 0; it < ipt; ++it) {
         const int j = lt + it * TG;
@@ -136,7 +148,7 @@ __device__ __forceinline__ void fft_pad(float2* buf, int lt, const float2* tw) {
           for (int r = 0; r < 16; ++r) buf[pad16(base + r * Ns)] = v[it][r];
         }
       }
-      __syncwarp();
+      group_sync<TG>();
       Ns *= 16;
     }
   }
@@ -179,7 +191,7 @@ __device__ __forceinline__ void r16_pass(float2* buf, int Ns, int lt, const floa
       dft_reg<16, INV>(v[it]);
     }
   }
-  __syncwarp();
+  group_sync<TG>();
 #pragma unroll
   for (int it = 0; it < ipt; ++it) {
     const int j = lt + it * TG;
@@ -196,7 +208,7 @@ __device__ __forceinline__ void r16_pass(float2* buf, int Ns, int lt, const floa
       }
     }
   }
-  __syncwarp();
+  group_sync<TG>();
 }
 
 // Forward FFT of a fibre staged in its first SL slots (zeros past the data).
@@ -439,7 +451,7 @@ __global__ void __launch_bounds__(F3<LOGN>::BLOCK3, LOGN <= 9 ? 2 : 1) fft3d_p3_
     if (c == 0)
       __syncthreads();
     else
-      __syncwarp();
+      group_sync<TG>();
     fwd_fft<LOGN>(buf, lt, tw);
     const float* krow = a.kst + (((size_t)c * a.H1 + w1) * a.H2 + (valid ? w2f : 0)) * a.H3;
     const float s2sign = (c == 1 && w2 > a.L2 / 2) ? -1.f : 1.f;
@@ -454,12 +466,12 @@ __global__ void __launch_bounds__(F3<LOGN>::BLOCK3, LOGN <= 9 ? 2 : 1) fft3d_p3_
       acc[j].x = fmaf(-kv, Z.y, acc[j].x);
       acc[j].y = fmaf(kv, Z.x, acc[j].y);
     }
-    __syncwarp();
+    group_sync<TG>();
   }
   float2* buf = bufc[0];
 #pragma unroll
   for (int j = 0; j < PER; ++j) buf[pad16(lt + j * TG)] = acc[j];
-  __syncwarp();
+  group_sync<TG>();
   inv_fft<LOGN>(buf, lt, tw);
   __syncthreads();  // the transposed store reads every fibre's buffer
   float2* out = a.s1 + (size_t)w1 * a.L2 + (size_t)tile * G;  // S3[i3][w1][w2]
@@ -529,7 +541,7 @@ __global__ void __launch_bounds__(F3<LOGN>::BLOCK3, LOGN <= 9 ? 2 : 1) fft3d_p3f
     bq[1][b] = make_float2(k01 * x0.x + k11 * x1.x + k12 * x2.x, k01 * x0.y + k11 * x1.y + k12 * x2.y);
     bq[2][b] = make_float2(k02 * x0.x + k12 * x1.x + k22 * x2.x, k02 * x0.y + k12 * x1.y + k22 * x2.y);
   }
-  __syncwarp();
+  group_sync<TG>();
 #pragma unroll
   for (int c = 0; c < 3; ++c) inv_fft<LOGN>(bq[c], lt, tw);
   __syncthreads();  // the transposed stores read every fibre's buffers
@@ -794,6 +806,7 @@ static demag_status dispatch_pass(demag_plan* P, int logn, int pass, const Fft3d
     case 8: return launch_pass<8>(P, pass, a, blocks, st);
     case 9: return launch_pass<9>(P, pass, a, blocks, st);
     case 10: return launch_pass<10>(P, pass, a, blocks, st);
+    case 11: return launch_pass<11>(P, pass, a, blocks, st);
     default: return set_error(P, DEMAG_EUNSUPPORTED, "fft3d: FFT length 2^%d not supported", logn);
   }
 }

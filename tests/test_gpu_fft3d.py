@@ -133,10 +133,56 @@ def test_fft3d_repeatable_and_graph_capturable(D):
     assert torch.equal(a, c)
 
 
+@pytest.mark.parametrize("n", [(1024, 6, 5), (6, 1024, 5), (5, 6, 1024)])
+def test_fft3d_length_2048_axes(D, n):
+    # n_p = 1024: FFT length 2048, two warps per fibre
+    h, R = (1.0, 1.0, 1.0), 11
+    m = synth.random_unit_m(n, 8)
+    P = D.demag_build_factors(n, h, R)
+    got = _apply(D, P, m, n)
+    assert rel_l2(got, ofull.apply_full(m, n, h, R)) <= TOL["fp32"]
+    from oracle import field as ofield
+    hd = torch.empty(3, n[2], n[1], n[0], device="cuda")
+    D.demag_stray_field_fft(P, dev(m), hd)
+    torch.cuda.synchronize()
+    assert rel_l2(host(hd), ofield.apply_field(m, n, h, R)) <= 1e-5
+
+
+def test_fft3d_1024_cubed_uniform_box(D):
+    # 1024^3 (1.07 G cells, ~110 GB of spectra and kernel) on one GPU: the uniformly
+    # magnetized cube against its closed-form potential at sampled cells.  R = 129: the
+    # largest node must exceed ~2/h for the near field (with R = 81 the boundary cells are
+    # off by 2e-4; on 64^3 the same ratio of nodes to 1/h gives 1.6e-5 and 2.7e-7 at R = 33, 41)
+    free, _ = torch.cuda.mem_get_info()
+    if free < 160e9:
+        pytest.skip("needs ~110 GB of free device memory")
+    import gc
+    n, h = (1024, 1024, 1024), (1 / 1024,) * 3
+    P = D.demag_build_factors(n, h, 129)
+    m = torch.zeros(3, 1024, 1024, 1024, device="cuda")
+    m[2] = 1.0
+    phi = torch.empty(1024, 1024, 1024, device="cuda")
+    D.demag_apply_full_fft(P, m, phi)
+    torch.cuda.synchronize()
+    pts = [(0, 0, 0), (1023, 511, 7), (512, 512, 512), (100, 900, 1023), (3, 1020, 600)]
+    got = np.array([float(phi[i3, i2, i1]) for i1, i2, i3 in pts])
+    ref = []
+    for i1, i2, i3 in pts:  # (1/4pi)(far face - near face) of the charged faces normal to z
+        x = [(i + 0.5) / 1024 for i in (i1, i2, i3)]
+        top = oex.rect_integral(x[0] - 1, x[0], x[1] - 1, x[1], x[2] - 1)
+        bottom = oex.rect_integral(x[0] - 1, x[0], x[1] - 1, x[1], x[2])
+        ref.append(float((top - bottom) / (4 * np.pi)))
+    ref = np.array(ref)
+    assert np.max(np.abs(got - ref)) < 1e-4 * np.max(np.abs(ref)), (got, ref)
+    del P, m, phi
+    gc.collect()
+    torch.cuda.empty_cache()
+
+
 def test_fft3d_too_long_axis_is_rejected(D):
-    P = D.demag_build_factors((513, 2, 2), (1.0, 1.0, 1.0), 5)
-    m = torch.zeros(3, 2, 2, 513, device="cuda")
-    phi = torch.empty(2, 2, 513, device="cuda")
+    P = D.demag_build_factors((1025, 2, 2), (1.0, 1.0, 1.0), 5)
+    m = torch.zeros(3, 2, 2, 1025, device="cuda")
+    phi = torch.empty(2, 2, 1025, device="cuda")
     with pytest.raises(D.DemagError) as ei:
         D.demag_apply_full_fft(P, m, phi)
     assert ei.value.status == 5  # DEMAG_EUNSUPPORTED
