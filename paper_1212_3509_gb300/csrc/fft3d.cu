@@ -26,6 +26,11 @@
 //   P4  inverse FFT along w2, kept i2 < n2 -> S4[i2][i3][w1]   (aliases S2)
 //   P5  inverse real FFT along w1 (two fibres per complex FFT) -> phi[i3][i2][i1]
 // All arithmetic after the FP64 kernel setup is FP32.
+//
+// The stray field of the analytic derivative factors runs the same passes with
+// six real kernels K_pq (h_d[p] = sum_q K_pq * m^(q)): the axis-3 pass then
+// transforms the three components, multiplies each bin by the 3 x 3 kernel
+// and inverse-transforms three outputs, and P4 / P5 run over three components.
 #include <algorithm>
 #include <cmath>
 #include <new>
