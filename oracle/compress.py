@@ -154,3 +154,20 @@ def tucker_hadamard(C, U, D, V):
     E = np.einsum("abc,def->adbecf", C, D).reshape(C.shape[0] * D.shape[0], C.shape[1] * D.shape[1],
                                                    C.shape[2] * D.shape[2])
     return E, W
+
+
+def recompress(parts, tol: float):
+    """Alg. 2's last step, approximate summation: phi = sum_q [[E_q; W_q]] recompressed to one
+    Tucker tensor with ||phi - phi_hat|| <= tol ||phi|| by a truncated HOSVD of the dense sum
+    (the rank rule of Alg. 1 per mode at tol / sqrt(3)); small grids only.
+
+    Returns (C [r3, r2, r1], [U_1, U_2, U_3] with U_p [n_p, r_p] orthonormal, ranks).
+    """
+    phi = sum(tucker_to_dense(E, W) for E, W in parts)
+    spec = hosvd_spectra(phi)
+    ranks = [truncation_rank(spec[p][1], tol) for p in range(3)]
+    U = [spec[p][0][:, : ranks[p]] for p in range(3)]
+    C = phi
+    for p in range(3):
+        C = mode_mult(C, U[p].T, p)
+    return C, U, ranks

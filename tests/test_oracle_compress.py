@@ -127,3 +127,27 @@ def test_planted_mistakes_are_caught(monkeypatch):
         err = np.linalg.norm(X - oc.tucker_to_dense(*comp[0])) / np.linalg.norm(X)
         assert err > 1e-2
     assert oc.hooi is orig_hooi
+
+
+@pytest.mark.parametrize("tol", [1e-2, 1e-4, 1e-6])
+def test_recompression_bound_and_ranks(tol):
+    # the summed potential of the three components (ranks 3 x 10 x 3 = 90 per mode),
+    # recompressed: the HOSVD bound holds and the ranks drop below the grid size
+    n, h, rk = (24, 20, 16), (1.0, 1.0, 1.0), (3, 3, 3)
+    core, flat = synth.tucker_inputs(n, rk, 5)
+    V, off = [], 0
+    for q in range(3):
+        row = []
+        for p in range(3):
+            size = rk[p] * n[p]
+            row.append(flat[off:off + size].reshape(rk[p], n[p]).T.astype(np.float64))
+            off += size
+        V.append(row)
+    _, comp = oc.compress_kernels(n, h, 21, 1e-8)
+    parts, phi = oc.apply_tucker_compressed(core.astype(np.float64), V, n, comp)
+    C, U, ranks = oc.recompress(parts, tol)
+    err = np.linalg.norm(oc.tucker_to_dense(C, U) - phi) / np.linalg.norm(phi)
+    assert err <= tol * (1 + 1e-9)
+    assert sum(ranks) < sum(n) if tol >= 1e-4 else all(r <= n[p] for p, r in enumerate(ranks))
+    for p in range(3):
+        assert np.allclose(U[p].T @ U[p], np.eye(ranks[p]), atol=1e-12)
