@@ -293,6 +293,24 @@ demag_status demag_copy_compressed(const demag_plan* plan, double* gen, float* c
 demag_status demag_apply_tucker_compressed(demag_plan* plan, int batch, const int r[3], const float* core,
                                            const float* V, float* out_core, float* out_V, void* stream);
 
+/* Alg. 2's approximate summation with tolerance tol: the output of
+ * demag_apply_tucker_compressed for ONE item (core: its input cores G^(q),
+ * float [3][r3][r2][r1]; V: its factor blocks, the out_V of that call) is
+ * recompressed to one Tucker tensor phi_hat = [[C; U_1, U_2, U_3]] with
+ * ||phi - phi_hat||_F <= tol ||phi||_F.  The range of each unfolding is sampled
+ * with Khatri-Rao products of +-1 test vectors (16, 32, then 64 samples until
+ * the projection error, computed exactly from the Tucker Gram matrices, is
+ * below tol/2), the core projected, and an HOSVD of that core truncated with
+ * the rank rule of Alg. 1 within the remaining error budget.  Outputs:
+ * ranks_out[3]; core_out float [r3][r2][r1] (capacity 64^3); U_out float, per
+ * mode p the rows [r_p][n_p] (orthonormal columns of U_p; capacity
+ * 64 (n1 + n2 + n3)); err_out (optional, host) the relative error bound reached.
+ * FP64 internally, synchronous.  DEMAG_EUNSUPPORTED when more than 64 ranks per
+ * mode would be needed. */
+demag_status demag_recompress_tucker(demag_plan* plan, const int r[3], const float* core, const float* V,
+                                     double tol, int ranks_out[3], float* core_out, float* U_out,
+                                     double* err_out, void* stream);
+
 /* `batch` independent Tucker inputs in one launch per FFT length: item b of
  * V, out_w and out_V follows the single-item layout above at item strides
  * 3 sum_p r_p n_p, 3M and 3M sum_p r_p n_p floats.  batch >= 1. */

@@ -59,6 +59,8 @@ _SIGS = {
     "demag_compressed_ranks": (_i, [_vp, ctypes.POINTER(ctypes.c_int)]),
     "demag_copy_compressed": (_i, [_vp, _vp, _vp, _vp]),
     "demag_apply_tucker_compressed": (_i, [_vp, _i, ctypes.POINTER(ctypes.c_int), _vp, _vp, _vp, _vp, _vp]),
+    "demag_recompress_tucker": (_i, [_vp, ctypes.POINTER(ctypes.c_int), _vp, _vp, ctypes.c_double,
+                                     ctypes.POINTER(ctypes.c_int), _vp, _vp, ctypes.POINTER(ctypes.c_double), _vp]),
     "demag_apply_full_batched": (_i, [ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i, _i, _vp]),
     "demag_graph_create_batched": (_i, [ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i, _i,
                                         ctypes.POINTER(_vp)]),
@@ -221,6 +223,29 @@ def demag_apply_tucker_compressed(plan: Plan, batch: int, r, core, V, out_core, 
                                              _ptr(V, batch * 3 * qs, f32, "V"),
                                              _ptr(out_core, batch * 3 * nout, f32, "out_core"),
                                              _ptr(out_V, batch * os_, f32, "out_V"), _stream(stream)), plan.ptr)
+
+
+def demag_recompress_tucker(plan: Plan, r, core, V, tol: float, stream=None):
+    """Recompress one item's compressed Tucker output: returns (ranks, core [r3, r2, r1], [U_p [r_p, n_p]], err)."""
+    import torch
+    rho = demag_compressed_ranks(plan)
+    rr = (ctypes.c_int * 3)(*[int(v) for v in r])
+    f32 = torch.float32
+    nv = sum(3 * rho[p] * int(r[p]) * plan.n[p] for p in range(3))
+    core_out = torch.empty(64 ** 3, device="cuda")
+    U_out = torch.empty(64 * sum(plan.n), device="cuda")
+    ranks = (ctypes.c_int * 3)()
+    err = ctypes.c_double()
+    _check(lib.demag_recompress_tucker(plan.ptr, rr, _ptr(core, 3 * int(r[0]) * int(r[1]) * int(r[2]), f32, "core"),
+                                       _ptr(V, nv, f32, "V"), float(tol), ranks, core_out.data_ptr(),
+                                       U_out.data_ptr(), ctypes.byref(err), _stream(stream)), plan.ptr)
+    rk = tuple(int(v) for v in ranks)
+    C = core_out[: rk[0] * rk[1] * rk[2]].reshape(rk[2], rk[1], rk[0])
+    Us, off = [], 0
+    for p in range(3):
+        Us.append(U_out[off: off + rk[p] * plan.n[p]].reshape(rk[p], plan.n[p]))
+        off += rk[p] * plan.n[p]
+    return rk, C, Us, err.value
 
 
 def demag_plan_destroy(plan: Plan):

@@ -374,6 +374,216 @@ __global__ void cmp_core_kernel(int batch, int rho0, int rho1, int rho2, int r0,
   }
 }
 
+// ---------------------------------------------------------------- recompression of phi
+//
+// Alg. 2's last step ("approximate summation with tolerance tol") for the
+// output of demag_apply_tucker_compressed: phi = sum_q [[E_q; W_q1, W_q2, W_q3]]
+// with E_q = C^(q) (x) G^(q) (ranks R_p = rho_p r_p per component) is brought to
+// one Tucker tensor [[C; U_1, U_2, U_3]].  Range of each unfolding: phi_(p)
+// applied to k Khatri-Rao test vectors (+-1 entries from a counter hash), QR
+// (the CGS kernel above); core C = phi x_p U_p^T; the projection error is
+// ||phi||^2 - ||C||^2 exactly (U_p orthonormal), with
+// ||phi||^2 = sum_{q,q'} <E_q, E_q' x_p (W_qp^T W_q'p)>; then an HOSVD of the
+// small core truncated so that the total error stays below tol ||phi||.
+// FP64 throughout.
+
+// Column-major [cols][m] matrix from the compressed factors of one item:
+// W_qp column (i r_p + l) = row (i, q, l) of mode block p.
+__global__ void rc_gather_kernel(int q, int p, int rho, int r, int n, const float* block, double* W) {
+  const long total = (long)rho * r * n;
+  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
+    const int e = (int)(idx % n);
+    const long c = idx / n;
+    const int i = (int)(c / r), l = (int)(c % r);
+    W[idx] = (double)block[(((size_t)i * 3 + q) * r + l) * n + e];
+  }
+}
+
+// E[(i3 r3 + l3)][(i2 r2 + l2)][(i1 r1 + l1)] = C[i3][i2][i1] G[l3][l2][l1] (one component)
+__global__ void rc_core_kernel(int rho0, int rho1, int rho2, int r0, int r1, int r2, const float* C, const float* G,
+                               double* E) {
+  const long R0 = (long)rho0 * r0, R1 = (long)rho1 * r1, total = R0 * R1 * rho2 * r2;
+  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
+    const long c1 = idx % R0, c2 = (idx / R0) % R1, c3 = idx / (R0 * R1);
+    const int i1 = (int)(c1 / r0), l1 = (int)(c1 % r0), i2 = (int)(c2 / r1), l2 = (int)(c2 % r1);
+    const int i3 = (int)(c3 / r2), l3 = (int)(c3 % r2);
+    E[idx] = (double)C[((size_t)i3 * rho1 + i2) * rho0 + i1] * (double)G[((size_t)l3 * r1 + l2) * r0 + l1];
+  }
+}
+
+// out = X x_p Mx (Eq. modemul): X [d2][d1][d0] (d0 fastest), Mx [e][d_p] row-major; out has d_p -> e.
+// With acc the result is added to out.
+__global__ void rc_mode_kernel(int d0, int d1, int d2, int p, int e, const double* X, const double* Mx, double* out,
+                               int acc) {
+  const int o0 = p == 0 ? e : d0, o1 = p == 1 ? e : d1, o2 = p == 2 ? e : d2;
+  const long total = (long)o0 * o1 * o2;
+  const int dp = p == 0 ? d0 : (p == 1 ? d1 : d2);
+  const long stride = p == 0 ? 1 : (p == 1 ? d0 : (long)d0 * d1);
+  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
+    const int a0 = (int)(idx % o0), a1 = (int)((idx / o0) % o1), a2 = (int)(idx / ((long)o0 * o1));
+    const int a = p == 0 ? a0 : (p == 1 ? a1 : a2);
+    const long base = (p == 0 ? 0 : a0) + (long)(p == 1 ? 0 : a1) * d0 + (long)(p == 2 ? 0 : a2) * d0 * d1;
+    double t = 0.0;
+    for (int b = 0; b < dp; ++b) t += Mx[(long)a * dp + b] * X[base + b * stride];
+    out[idx] = acc ? out[idx] + t : t;
+  }
+}
+
+// G[i][j] = sum_e A[i m + e] B[j m + e] (column-major A [a][m], B [b][m]); one warp per entry
+__global__ void rc_gram_kernel(int m, int a, int b, const double* A, const double* B, double* G) {
+  const int lane = threadIdx.x & 31;
+  const long warps = (long)gridDim.x * (blockDim.x >> 5);
+  for (long w = blockIdx.x * (long)(blockDim.x >> 5) + (threadIdx.x >> 5); w < (long)a * b; w += warps) {
+    const int i = (int)(w / b), j = (int)(w % b);
+    double t = 0.0;
+    for (int e = lane; e < m; e += 32) t += A[(long)i * m + e] * B[(long)j * m + e];
+    t = warp_sum(t);
+    if (lane == 0) G[w] = t;
+  }
+}
+
+// +-1 test entry of (mode, row e, sample j) from a counter hash (splitmix-style mixing)
+__device__ __forceinline__ double rc_sign(unsigned long long seed, int mode, int e, int j) {
+  unsigned long long z = seed + 0x9E3779B97F4A7C15ull * (((unsigned long long)mode << 48) ^
+                                                         ((unsigned long long)j << 32) ^ (unsigned)e);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  return (z & 1ull) ? 1.0 : -1.0;
+}
+
+// A[c][j] = sum_e W[c m + e] omega_mode(e, j): the test vectors seen through a factor
+__global__ void rc_probe_kernel(int m, int cols, int k, int mode, unsigned long long seed, const double* W, double* A) {
+  const long total = (long)cols * k;
+  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
+    const int c = (int)(idx / k), j = (int)(idx % k);
+    double t = 0.0;
+    for (int e = 0; e < m; ++e) t += W[(long)c * m + e] * rc_sign(seed, mode, e, j);
+    A[idx] = t;
+  }
+}
+
+// Z[i][j] = sum_{a, b} E[.. i ..] As[a][j] Ar[b][j], the core contracted on modes s, r
+// with sample j of the test vectors (Khatri-Rao test); E dims R0, R1, R2 (R0 fastest)
+__global__ void rc_sketch_kernel(int R0, int R1, int R2, int p, int k, const double* E, const double* As,
+                                 const double* Ar, double* Z) {
+  const int Rd[3] = {R0, R1, R2};
+  const int s = (p + 1) % 3, r = (p + 2) % 3;
+  const long st[3] = {1, R0, (long)R0 * R1};
+  const long total = (long)Rd[p] * k;
+  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
+    const int i = (int)(idx / k), j = (int)(idx % k);
+    double t = 0.0;
+    for (int b = 0; b < Rd[r]; ++b) {
+      double u = 0.0;
+      const double* row = E + i * st[p] + b * st[r];
+      for (int a = 0; a < Rd[s]; ++a) u += row[a * st[s]] * As[(long)a * k + j];
+      t += u * Ar[(long)b * k + j];
+    }
+    Z[idx] = t;
+  }
+}
+
+// Y[j][e] (column-major [k][n]) += sum_c W[c n + e] Z[c][j]
+__global__ void rc_range_kernel(int n, int cols, int k, const double* W, const double* Z, double* Y, int acc) {
+  const long total = (long)k * n;
+  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
+    const int j = (int)(idx / n), e = (int)(idx % n);
+    double t = 0.0;
+    for (int c = 0; c < cols; ++c) t += W[(long)c * n + e] * Z[(long)c * k + j];
+    Y[idx] = acc ? Y[idx] + t : t;
+  }
+}
+
+// QR of a column-major [M][m] matrix by the same CGS (three passes, 1e-12 drop) as cmp_qr_kernel
+__global__ void __launch_bounds__(256) rc_qr_kernel(int M, int m, const double* A, double* Q, double* R) {
+  __shared__ double coef[kMaxTerms];
+  __shared__ double red[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i = threadIdx.x; i < M * M; i += blockDim.x) R[i] = 0.0;
+  for (int k = 0; k < M; ++k) {
+    double* v = Q + (size_t)k * m;
+    double a2 = 0.0;
+    for (int e = threadIdx.x; e < m; e += blockDim.x) {
+      const double x = A[(size_t)k * m + e];
+      v[e] = x;
+      a2 += x * x;
+    }
+    const double anrm = sqrt(block_sum(a2, red));
+    for (int pass = 0; pass < 3; ++pass) {
+      for (int b = warp; b < k; b += nw) {
+        const double* qb = Q + (size_t)b * m;
+        double acc = 0.0;
+        for (int e = lane; e < m; e += 32) acc += qb[e] * v[e];
+        acc = warp_sum(acc);
+        if (lane == 0) coef[b] = acc;
+      }
+      __syncthreads();
+      for (int e = threadIdx.x; e < m; e += blockDim.x) {
+        double t = v[e];
+        for (int b = 0; b < k; ++b) t -= coef[b] * Q[(size_t)b * m + e];
+        v[e] = t;
+      }
+      if (threadIdx.x < k) R[threadIdx.x * M + k] += coef[threadIdx.x];
+      __syncthreads();
+    }
+    double s2 = 0.0;
+    for (int e = threadIdx.x; e < m; e += blockDim.x) s2 += v[e] * v[e];
+    double nrm = sqrt(block_sum(s2, red));
+    if (nrm <= 1e-12 * anrm) nrm = 0.0;
+    const double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
+    for (int e = threadIdx.x; e < m; e += blockDim.x) v[e] *= inv;
+    if (threadIdx.x == 0) R[k * M + k] = nrm;
+    __syncthreads();
+  }
+}
+
+// sum of x[i] y[i] into *out (FP64, one atomic per block)
+__global__ void rc_dot_kernel(long count, const double* x, const double* y, double* out) {
+  __shared__ double red[32];
+  double t = 0.0;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < count; i += (long)gridDim.x * blockDim.x)
+    t += x[i] * y[i];
+  t = warp_sum(t);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+    atomicAdd(out, s);
+  }
+}
+
+// HOSVD of the small core (dims k0, k1, k2 <= 64, k0 fastest; one block): for
+// each mode the unfolding Gram (k_p x k_p, padded to n even), Jacobi,
+// eigenvalues (descending) into eig + 64 p and eigenvectors into V + 4096 p
+// ([k_p][k_p], column i = vector i).
+__global__ void __launch_bounds__(256) rc_core_hosvd_kernel(int k0, int k1, int k2, int n, const double* C,
+                                                            double* eig, double* V) {
+  extern __shared__ double smc[];
+  __shared__ double red[32];
+  double *A = smc, *Vs = A + n * n;
+  const int kd[3] = {k0, k1, k2};
+  const long st[3] = {1, k0, (long)k0 * k1};
+  for (int p = 0; p < 3; ++p) {
+    const int s = (p + 1) % 3, r = (p + 2) % 3, kp = kd[p];
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+      const int a = idx / n, b = idx % n;
+      double t = 0.0;
+      if (a < kp && b < kp)
+        for (int x = 0; x < kd[s]; ++x)
+          for (int y = 0; y < kd[r]; ++y) {
+            const long off = x * st[s] + y * st[r];
+            t += C[off + a * st[p]] * C[off + b * st[p]];
+          }
+      A[idx] = t;
+    }
+    __syncthreads();
+    jacobi_eigen(A, Vs, n, red);
+    sorted_out(kp, n, A, Vs, eig + 64 * p, V + 4096 * p);
+  }
+}
+
 void compress_destroy(demag_plan* P) {
   Compressed* C = static_cast<Compressed*>(P->cmp);
   if (!C) return;
@@ -549,5 +759,257 @@ extern "C" demag_status demag_copy_compressed(const demag_plan* plan, double* ge
     DEMAG_CUDA(P, cudaMemcpyAsync(core, C->core, sizeof(float) * 3 * C->rho[0] * C->rho[1] * C->rho[2],
                                   cudaMemcpyDeviceToDevice, st));
   DEMAG_CUDA(P, cudaStreamSynchronize(st));
+  return DEMAG_OK;
+}
+
+static int rc_blocks(long total) {
+  long b = (total + 255) / 256;
+  if (b > 152 * 32) b = 152 * 32;
+  return (int)(b < 1 ? 1 : b);
+}
+
+extern "C" demag_status demag_recompress_tucker(demag_plan* P, const int r[3], const float* core, const float* V,
+                                                double tol, int ranks_out[3], float* core_out, float* U_out,
+                                                double* err_out, void* stream) {
+  if (!P) return set_error(nullptr, DEMAG_EINVAL, "demag_recompress_tucker: plan is NULL");
+  if (!r || !core || !V || !ranks_out || !core_out || !U_out)
+    return set_error(P, DEMAG_EINVAL, "demag_recompress_tucker: NULL pointer");
+  if (!(tol > 0.0 && tol < 1.0)) return set_error(P, DEMAG_EINVAL, "demag_recompress_tucker: tol must be in (0, 1)");
+  CompressedView cv;
+  if (!compressed_view(P, &cv))
+    return set_error(P, DEMAG_EINVAL, "demag_recompress_tucker: no compressed kernel (demag_compress_kernel)");
+  for (int p = 0; p < 3; ++p)
+    if (r[p] < 1) return set_error(P, DEMAG_EINVAL, "demag_recompress_tucker: r[%d] must be >= 1", p);
+  cudaStream_t st = (cudaStream_t)stream;
+  const int n[3] = {P->n[0], P->n[1], P->n[2]};
+  int Rr[3];
+  for (int p = 0; p < 3; ++p) Rr[p] = cv.rho[p] * r[p];
+  const long Rtot = (long)Rr[0] * Rr[1] * Rr[2];
+  long tmpn = Rtot;
+  for (int p = 0; p < 3; ++p) tmpn = std::max(tmpn, (long)64 * Rr[(p + 1) % 3] * Rr[(p + 2) % 3]);
+  tmpn = std::max(tmpn, (long)64 * 64 * 64);
+  long wsize = 0;
+  long woff[3][3];
+  for (int q = 0; q < 3; ++q)
+    for (int p = 0; p < 3; ++p) {
+      woff[q][p] = wsize;
+      wsize += (long)Rr[p] * n[p];
+    }
+  const int Rmax = std::max(Rr[0], std::max(Rr[1], Rr[2]));
+  const int nmax = std::max(n[0], std::max(n[1], n[2]));
+  std::vector<void*> owned;
+  auto alloc = [&](double** ptr, long count) {
+    cudaError_t e = cudaMalloc(ptr, sizeof(double) * (size_t)std::max(count, 1L));
+    if (e == cudaSuccess) owned.push_back(*ptr);
+    return e;
+  };
+  auto release = [&]() {
+    for (void* q : owned) cudaFree(q);
+    owned.clear();
+  };
+  double *W, *E, *T1, *T2, *G, *Y[3], *Q[3], *Rq, *A1, *A2, *Z, *B, *Ch, *acc, *eig, *Vh, *Mt;
+  cudaError_t e = cudaSuccess;
+  if ((e = alloc(&W, wsize)) != cudaSuccess || (e = alloc(&E, 3 * Rtot)) != cudaSuccess ||
+      (e = alloc(&T1, tmpn)) != cudaSuccess || (e = alloc(&T2, tmpn)) != cudaSuccess ||
+      (e = alloc(&G, (long)Rmax * Rmax)) != cudaSuccess || (e = alloc(&Rq, 64 * 64)) != cudaSuccess ||
+      (e = alloc(&A1, (long)Rmax * 64)) != cudaSuccess || (e = alloc(&A2, (long)Rmax * 64)) != cudaSuccess ||
+      (e = alloc(&Z, (long)Rmax * 64)) != cudaSuccess || (e = alloc(&B, (long)64 * Rmax)) != cudaSuccess ||
+      (e = alloc(&Ch, 64 * 64 * 64)) != cudaSuccess || (e = alloc(&acc, 2)) != cudaSuccess ||
+      (e = alloc(&eig, 3 * 64)) != cudaSuccess || (e = alloc(&Vh, 3 * 4096)) != cudaSuccess ||
+      (e = alloc(&Mt, 64 * 64)) != cudaSuccess) {
+    release();
+    return cuda_error(P, e, "demag_recompress_tucker: workspace");
+  }
+  for (int p = 0; p < 3; ++p) {
+    if ((e = alloc(&Y[p], (long)64 * n[p])) != cudaSuccess || (e = alloc(&Q[p], (long)64 * n[p])) != cudaSuccess) {
+      release();
+      return cuda_error(P, e, "demag_recompress_tucker: workspace");
+    }
+  }
+#define RC_LAUNCH(name, ...)                                 \
+  do {                                                       \
+    DEMAG_LAUNCH(P, kFamMisc, st, __VA_ARGS__);              \
+    if ((e = cudaGetLastError()) != cudaSuccess) {           \
+      release();                                             \
+      return cuda_error(P, e, name);                         \
+    }                                                        \
+  } while (0)
+  // 1. factors in FP64, dense component cores
+  {
+    long boff = 0;
+    for (int p = 0; p < 3; ++p) {
+      const float* block = V + boff;
+      for (int q = 0; q < 3; ++q)
+        RC_LAUNCH("rc_gather_kernel", rc_gather_kernel<<<rc_blocks((long)Rr[p] * n[p]), 256, 0, st>>>(
+                                          q, p, cv.rho[p], r[p], n[p], block, W + woff[q][p]));
+      boff += 3L * cv.rho[p] * r[p] * n[p];
+    }
+    const long gsize = (long)r[0] * r[1] * r[2];
+    const long csize = (long)cv.rho[0] * cv.rho[1] * cv.rho[2];
+    for (int q = 0; q < 3; ++q)
+      RC_LAUNCH("rc_core_kernel", rc_core_kernel<<<rc_blocks(Rtot), 256, 0, st>>>(
+                                      cv.rho[0], cv.rho[1], cv.rho[2], r[0], r[1], r[2], cv.core + q * csize,
+                                      core + q * gsize, E + q * Rtot));
+  }
+  // 2. ||phi||^2 = sum_{q,q'} <E_q, E_q' x_p (W_qp^T W_q'p)>
+  DEMAG_CUDA(P, cudaMemsetAsync(acc, 0, sizeof(double) * 2, st));
+  for (int q = 0; q < 3; ++q)
+    for (int q2 = q; q2 < 3; ++q2) {
+      const double* X = E + q2 * Rtot;
+      double* outs[3] = {T1, T2, T1};
+      for (int p = 0; p < 3; ++p) {
+        RC_LAUNCH("rc_gram_kernel", rc_gram_kernel<<<rc_blocks((long)Rr[p] * Rr[p] * 32), 256, 0, st>>>(
+                                        n[p], Rr[p], Rr[p], W + woff[q][p], W + woff[q2][p], G));
+        RC_LAUNCH("rc_mode_kernel", rc_mode_kernel<<<rc_blocks(Rtot), 256, 0, st>>>(
+                                        Rr[0], Rr[1], Rr[2], p, Rr[p], X, G, outs[p], 0));
+        X = outs[p];
+      }
+      // the pair (q2, q) gives the same inner product: count it twice
+      RC_LAUNCH("rc_dot_kernel", rc_dot_kernel<<<rc_blocks(Rtot), 256, 0, st>>>(Rtot, E + q * Rtot, X, acc));
+      if (q2 != q) RC_LAUNCH("rc_dot_kernel", rc_dot_kernel<<<rc_blocks(Rtot), 256, 0, st>>>(Rtot, E + q * Rtot, X, acc));
+    }
+  double phi2 = 0.0;
+  DEMAG_CUDA(P, cudaMemcpyAsync(&phi2, acc, sizeof(double), cudaMemcpyDeviceToHost, st));
+  DEMAG_CUDA(P, cudaStreamSynchronize(st));
+  if (!(phi2 > 0.0)) {
+    release();
+    return set_error(P, DEMAG_EINVAL, "demag_recompress_tucker: the potential is zero");
+  }
+  // 3. sketched ranges, growing the sample count until the projection error is below tol/2
+  int kd[3] = {0, 0, 0};
+  double es2 = 0.0;
+  const unsigned long long seed = 0x5EEDull;
+  for (int k = 16;; k *= 2) {
+    for (int p = 0; p < 3; ++p) kd[p] = std::min(k, n[p]);
+    for (int p = 0; p < 3; ++p) {
+      const int s = (p + 1) % 3, rr = (p + 2) % 3;
+      for (int q = 0; q < 3; ++q) {
+        RC_LAUNCH("rc_probe_kernel", rc_probe_kernel<<<rc_blocks((long)Rr[s] * kd[p]), 256, 0, st>>>(
+                                         n[s], Rr[s], kd[p], s, seed, W + woff[q][s], A1));
+        RC_LAUNCH("rc_probe_kernel", rc_probe_kernel<<<rc_blocks((long)Rr[rr] * kd[p]), 256, 0, st>>>(
+                                         n[rr], Rr[rr], kd[p], rr, seed, W + woff[q][rr], A2));
+        RC_LAUNCH("rc_sketch_kernel", rc_sketch_kernel<<<rc_blocks((long)Rr[p] * kd[p]), 256, 0, st>>>(
+                                          Rr[0], Rr[1], Rr[2], p, kd[p], E + q * Rtot, A1, A2, Z));
+        RC_LAUNCH("rc_range_kernel", rc_range_kernel<<<rc_blocks((long)kd[p] * n[p]), 256, 0, st>>>(
+                                         n[p], Rr[p], kd[p], W + woff[q][p], Z, Y[p], q > 0));
+      }
+      RC_LAUNCH("rc_qr_kernel", rc_qr_kernel<<<1, 256, 0, st>>>(kd[p], n[p], Y[p], Q[p], Rq));
+    }
+    // C = sum_q E_q x_p (Q_p^T W_qp)
+    const long csz = (long)kd[0] * kd[1] * kd[2];
+    for (int q = 0; q < 3; ++q) {
+      const double* X = E + q * Rtot;
+      int d[3] = {Rr[0], Rr[1], Rr[2]};
+      double* outs[3] = {T1, T2, Ch};
+      for (int p = 0; p < 3; ++p) {
+        RC_LAUNCH("rc_gram_kernel", rc_gram_kernel<<<rc_blocks((long)kd[p] * Rr[p] * 32), 256, 0, st>>>(
+                                        n[p], kd[p], Rr[p], Q[p], W + woff[q][p], B));
+        const long osz = (long)(p == 0 ? kd[0] : d[0]) * (p == 1 ? kd[1] : d[1]) * (p == 2 ? kd[2] : d[2]);
+        RC_LAUNCH("rc_mode_kernel", rc_mode_kernel<<<rc_blocks(osz), 256, 0, st>>>(
+                                        d[0], d[1], d[2], p, kd[p], X, B, outs[p], p == 2 && q > 0));
+        d[p] = kd[p];
+        X = outs[p];
+      }
+    }
+    DEMAG_CUDA(P, cudaMemsetAsync(acc + 1, 0, sizeof(double), st));
+    RC_LAUNCH("rc_dot_kernel", rc_dot_kernel<<<rc_blocks(csz), 256, 0, st>>>(csz, Ch, Ch, acc + 1));
+    double c2 = 0.0;
+    DEMAG_CUDA(P, cudaMemcpyAsync(&c2, acc + 1, sizeof(double), cudaMemcpyDeviceToHost, st));
+    DEMAG_CUDA(P, cudaStreamSynchronize(st));
+    es2 = std::max(0.0, phi2 - c2);
+    const bool full = kd[0] == n[0] && kd[1] == n[1] && kd[2] == n[2];
+    if (es2 <= 0.25 * tol * tol * phi2 || full) break;
+    if (k >= 64) {
+      release();
+      return set_error(P, DEMAG_EUNSUPPORTED,
+                       "demag_recompress_tucker: ranks above 64 needed for tol %g (projection error %g)", tol,
+                       sqrt(es2 / phi2));
+    }
+  }
+  // 4. HOSVD of the small core, truncated within the remaining error budget
+  const int npad = std::max(kd[0], std::max(kd[1], kd[2]));
+  const int nev = npad + (npad & 1);
+  {
+    const size_t smem = sizeof(double) * 2 * nev * nev;
+    static unsigned long long attr = 0;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (!(attr & (1ull << (dev & 63)))) {
+      DEMAG_CUDA(P, cudaFuncSetAttribute(rc_core_hosvd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         2 * 64 * 64 * 8));
+      attr |= 1ull << (dev & 63);
+    }
+    RC_LAUNCH("rc_core_hosvd_kernel",
+              rc_core_hosvd_kernel<<<1, 256, smem, st>>>(kd[0], kd[1], kd[2], nev, Ch, eig, Vh));
+  }
+  std::vector<double> eh(3 * 64), vh(3 * 4096);
+  DEMAG_CUDA(P, cudaMemcpyAsync(eh.data(), eig, sizeof(double) * 3 * 64, cudaMemcpyDeviceToHost, st));
+  DEMAG_CUDA(P, cudaMemcpyAsync(vh.data(), Vh, sizeof(double) * 3 * 4096, cudaMemcpyDeviceToHost, st));
+  DEMAG_CUDA(P, cudaStreamSynchronize(st));
+  const double budget = std::max(0.0, tol * tol * phi2 - es2);
+  double tails = 0.0;
+  int rk[3];
+  for (int p = 0; p < 3; ++p) {
+    double tot = 0.0;
+    for (int i = 0; i < kd[p]; ++i) tot += std::max(0.0, eh[64 * p + i]);
+    double tail = tot;
+    rk[p] = kd[p];
+    for (int rr = 1; rr <= kd[p]; ++rr) {
+      tail -= std::max(0.0, eh[64 * p + rr - 1]);
+      if (tail <= budget / 3.0) {
+        rk[p] = rr;
+        break;
+      }
+    }
+    double kept = 0.0;
+    for (int i = 0; i < rk[p]; ++i) kept += std::max(0.0, eh[64 * p + i]);
+    tails += std::max(0.0, tot - kept);
+  }
+  // 5. U_p = Q_p V_p[:, :rk] (rows of U_out), C' = C x_p V_p[:, :rk]^T
+  {
+    long uoff = 0;
+    for (int p = 0; p < 3; ++p) {
+      std::vector<double> vp((size_t)kd[p] * kd[p]);
+      for (int c = 0; c < kd[p]; ++c)
+        for (int i = 0; i < kd[p]; ++i) vp[(size_t)c * kd[p] + i] = vh[4096 * p + (size_t)c * kd[p] + i];
+      DEMAG_CUDA(P, cudaMemcpyAsync(Mt, vp.data(), sizeof(double) * vp.size(), cudaMemcpyHostToDevice, st));
+      RC_LAUNCH("rc_range_kernel", rc_range_kernel<<<rc_blocks((long)kd[p] * n[p]), 256, 0, st>>>(
+                                       n[p], kd[p], kd[p], Q[p], Mt, Y[p], 0));
+      DEMAG_CUDA(P, cudaStreamSynchronize(st));  // Mt is reused
+      // rows 0..rk-1 of Y[p] ([k][n] column-major) are the columns of U_p
+      std::vector<float> tmp;
+      std::vector<double> yh((size_t)rk[p] * n[p]);
+      DEMAG_CUDA(P, cudaMemcpy(yh.data(), Y[p], sizeof(double) * yh.size(), cudaMemcpyDeviceToHost));
+      tmp.resize(yh.size());
+      for (size_t i = 0; i < yh.size(); ++i) tmp[i] = (float)yh[i];
+      DEMAG_CUDA(P, cudaMemcpy(U_out + uoff, tmp.data(), sizeof(float) * tmp.size(), cudaMemcpyHostToDevice));
+      uoff += (long)rk[p] * n[p];
+    }
+    double* X = Ch;
+    int d[3] = {kd[0], kd[1], kd[2]};
+    double* outs[3] = {T1, T2, T1};  // T1 is free again once mode 2 has read it
+    for (int p = 0; p < 3; ++p) {
+      std::vector<double> mt((size_t)rk[p] * kd[p]);  // [a][b] = V_p[b][a]
+      for (int a = 0; a < rk[p]; ++a)
+        for (int b = 0; b < kd[p]; ++b) mt[(size_t)a * kd[p] + b] = vh[4096 * p + (size_t)b * kd[p] + a];
+      DEMAG_CUDA(P, cudaMemcpy(Mt, mt.data(), sizeof(double) * mt.size(), cudaMemcpyHostToDevice));
+      const long osz = (long)(p == 0 ? rk[0] : d[0]) * (p == 1 ? rk[1] : d[1]) * (p == 2 ? rk[2] : d[2]);
+      RC_LAUNCH("rc_mode_kernel", rc_mode_kernel<<<rc_blocks(osz), 256, 0, st>>>(d[0], d[1], d[2], p, rk[p], X, Mt,
+                                                                                 outs[p], 0));
+      DEMAG_CUDA(P, cudaStreamSynchronize(st));
+      d[p] = rk[p];
+      X = outs[p];
+    }
+    const long cn = (long)rk[0] * rk[1] * rk[2];
+    std::vector<double> ch(cn);
+    DEMAG_CUDA(P, cudaMemcpy(ch.data(), X, sizeof(double) * cn, cudaMemcpyDeviceToHost));
+    std::vector<float> cf(cn);
+    for (long i = 0; i < cn; ++i) cf[i] = (float)ch[i];
+    DEMAG_CUDA(P, cudaMemcpy(core_out, cf.data(), sizeof(float) * cn, cudaMemcpyHostToDevice));
+  }
+#undef RC_LAUNCH
+  release();
+  for (int p = 0; p < 3; ++p) ranks_out[p] = rk[p];
+  if (err_out) *err_out = sqrt((es2 + tails) / phi2);
   return DEMAG_OK;
 }

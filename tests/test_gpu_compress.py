@@ -197,3 +197,48 @@ def test_implicit_core_gives_the_same_factors(D):
     D.demag_apply_tucker_compressed(P, 1, ranks, None, dev(flat), None, out_V)
     torch.cuda.synchronize()
     assert np.array_equal(host(out_V), oV)
+
+
+@pytest.mark.parametrize("tol", [1e-2, 1e-4])
+def test_recompression_bound(D, tol):
+    # Alg. 2's approximate summation on the GPU: the recompressed Tucker tensor is within
+    # tol of the summed potential, its factors are orthonormal, and its ranks are those of
+    # the oracle's dense HOSVD of the same potential (up to the sketch)
+    n, h, ranks = (24, 20, 16), (1.0, 1.0, 1.0), (3, 3, 3)
+    P = D.demag_build_factors(n, h, 21)
+    D.demag_compress_kernel(P, 1e-8)
+    core, flat = _inputs(n, ranks, 5)
+    rho, oc_, oV = _run(D, P, n, ranks, core, flat)
+    parts = _parts(rho, n, ranks, oc_, oV)
+    phi = _dense(parts)
+    rk, C, Us, err = D.demag_recompress_tucker(P, ranks, dev(core.ravel()), dev(oV), tol)
+    approx = oc.tucker_to_dense(host(C).astype(np.float64), [host(U).astype(np.float64).T for U in Us])
+    assert rel_l2(approx, phi) <= tol * 1.01 + 1e-6
+    assert err <= tol * (1 + 1e-9)
+    for U in Us:
+        Uh = host(U).astype(np.float64)
+        assert np.allclose(Uh @ Uh.T, np.eye(Uh.shape[0]), atol=1e-5)
+    _, _, ref_ranks = oc.recompress(parts, tol)
+    assert all(a <= b + 2 for a, b in zip(rk, ref_ranks)), (rk, ref_ranks)
+    assert sum(rk) < sum(3 * rho[p] * ranks[p] for p in range(3))
+
+
+def test_recompression_1024(D):
+    n, ranks, tol = (1024, 1024, 1024), (8, 8, 8), 1e-5
+    P = D.demag_build_factors(n, (1.0 / 1024,) * 3, 61)
+    D.demag_compress_kernel(P, 1e-6)
+    core, flat = _inputs(n, ranks, 3)
+    rho, oc_, oV = _run(D, P, n, ranks, core, flat)
+    parts = _parts(rho, n, ranks, oc_, oV)
+    rk, C, Us, err = D.demag_recompress_tucker(P, ranks, dev(core.ravel()), dev(oV), tol)
+    assert err <= tol and max(rk) <= 64
+    Ch = host(C).astype(np.float64)
+    Uh = [host(U).astype(np.float64) for U in Us]
+    pts = np.random.default_rng(1).integers(0, 1024, size=(24, 3))
+    num = den = 0.0
+    for i1, i2, i3 in pts:
+        a = sum(np.einsum("cba,a,b,c->", E, W[0][i1], W[1][i2], W[2][i3]) for E, W in parts)
+        b = np.einsum("cba,a,b,c->", Ch, Uh[0][:, i1], Uh[1][:, i2], Uh[2][:, i3])
+        num += (a - b) ** 2
+        den += a ** 2
+    assert (num / den) ** 0.5 <= 10 * tol
