@@ -765,11 +765,39 @@ def run_c4(args, D, world, local, stream, peaks):
                                   "algorithmic_bytes_per_app": bytes_app},
                      "clocks": clk.summary(), "timing": "CUDA-graph replays of the batched call"}
     out["tucker_compressed"] = run_tucker_compressed(args, D, world, local, stream, P, n3, rt, B, V, tw, tV, hbm)
+    out["tt_rounded"] = run_tt_round(D, P, n3)
     out["_tucker_in"] = tucker_in
     out["_tucker_out"] = tV[:M * 3 * tot * n]
     out["_tt_in"] = tt_in
     out["_tt_out"] = [o[:M * 3 * sz] for o, sz in zip(tO, sizes)]
     return out
+
+
+def run_tt_round(D, P, n3, tol=1e-5, rr=(8, 8)):
+    """TT rounding (App. C) of the potential of one smooth rank-(8, 8) TT magnetization on the
+    1024^3 grid: the 3M output trains of demag_apply_tt rounded to one train with relative
+    error <= tol (second call timed; host-driven and synchronous)."""
+    import torch
+    import synth
+    n, M = n3[0], P.M
+    G = [torch.from_numpy(x.ravel()).cuda() for x in synth.tt_smooth_inputs(n3, rr, 1700)]
+    w = torch.empty(M * 3, device="cuda")
+    o = [torch.empty(M * 3 * sz, device="cuda") for sz in (rr[0] * n, rr[0] * rr[1] * n, rr[1] * n)]
+    D.demag_apply_tt(P, rr, G[0], G[1], G[2], w, *o)
+    torch.cuda.synchronize()
+    try:
+        D.demag_round_tt(P, rr, w, *o, tol)
+        t0 = time.perf_counter()
+        rk, _, _, _, err = D.demag_round_tt(P, rr, w, *o, tol)
+        secs = time.perf_counter() - t0
+    except D.DemagError as e:
+        return {"tol": tol, "unavailable": str(e)}
+    return {"tol": tol, "input_ranks": list(rr), "ranks": list(rk), "error": err, "seconds": secs,
+            "ranks_before": [3 * M * rr[0], 3 * M * rr[1]],
+            "floats_before": 3 * M * (rr[0] * n + rr[0] * rr[1] * n + rr[1] * n) + 3 * M,
+            "floats_after": rk[0] * n + rk[0] * rk[1] * n + rk[1] * n,
+            "work": "randomized TT rounding in FP64: exact ||phi|| from the term Grams, Khatri-Rao sketches "
+                    "of both unfoldings, TT-SVD truncation of the projected train, last core by projection"}
 
 
 def run_tucker_compressed(args, D, world, local, stream, P, n3, rt, B, V, tw, tV, hbm, tol=1e-6):

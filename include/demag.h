@@ -335,6 +335,28 @@ demag_status demag_apply_tt_batched(demag_plan* plan, int batch, const int r[2],
                                     const float* G2, const float* G3, float* out_w, float* oG1,
                                     float* oG2, float* oG3, void* stream);
 
+/* TT rounding of the potential (App. C: the 3M output trains of
+ * demag_apply_tt summed and rounded to one train, the recompression that
+ * section cites) with tolerance tol: phi_hat = [G1, G2, G3] with
+ * ||phi - phi_hat||_F <= tol ||phi||_F.  Inputs: the output of
+ * demag_apply_tt for ONE item (r[2] its TT ranks; w float [M][3]; o1, o2, o3
+ * its cores).  The range of the first unfolding is sampled with Khatri-Rao
+ * products of +-1 test vectors (16, 32, then 64 samples until the projection
+ * error, exact from the pairwise Gram matrices of the terms, is below tol/4),
+ * the projected train's (1,2)-unfolding alike; the small train is truncated
+ * as in TT-SVD (mode-1 Gram, QR of the middle core, Gram of the last core)
+ * within the remaining budget, and the last core is the orthogonal projection
+ * of phi on the first two.  Outputs: ranks_out[2]; G1_out float [r1][n1]
+ * (orthonormal rows; capacity 64 n1); G2_out float [r1 r2][n2] (row
+ * a1 r2 + a2; capacity 64^2 n2); G3_out float [r2][n3] (capacity 64 n3);
+ * err_out (optional, host) = sqrt(1 - ||G3||^2 / ||phi||^2), the relative
+ * error reached (exact up to a rounding floor near 1e-8).  FP64 internally,
+ * synchronous.  DEMAG_EUNSUPPORTED when more than 64 samples per unfolding
+ * would be needed; DEMAG_EINVAL for a zero potential. */
+demag_status demag_round_tt(demag_plan* plan, const int r[2], const float* w, const float* o1,
+                            const float* o2, const float* o3, double tol, int ranks_out[2],
+                            float* G1_out, float* G2_out, float* G3_out, double* err_out, void* stream);
+
 /* ---- stray field, energy and gradient (h_d = -grad phi, Sec. 1) ---------- */
 
 /* Second-order finite-difference stray field h_d = -D phi: central

@@ -23,6 +23,7 @@ from ._abi import (  # noqa: F401
     demag_copy_compressed,
     demag_apply_tucker_compressed,
     demag_recompress_tucker,
+    demag_round_tt,
     demag_apply_full_fft,
     demag_stray_field_fft,
     demag_energy_field_fft,

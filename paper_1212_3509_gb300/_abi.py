@@ -61,6 +61,8 @@ _SIGS = {
     "demag_apply_tucker_compressed": (_i, [_vp, _i, ctypes.POINTER(ctypes.c_int), _vp, _vp, _vp, _vp, _vp]),
     "demag_recompress_tucker": (_i, [_vp, ctypes.POINTER(ctypes.c_int), _vp, _vp, ctypes.c_double,
                                      ctypes.POINTER(ctypes.c_int), _vp, _vp, ctypes.POINTER(ctypes.c_double), _vp]),
+    "demag_round_tt": (_i, [_vp, ctypes.POINTER(ctypes.c_int), _vp, _vp, _vp, _vp, ctypes.c_double,
+                            ctypes.POINTER(ctypes.c_int), _vp, _vp, _vp, ctypes.POINTER(ctypes.c_double), _vp]),
     "demag_apply_full_batched": (_i, [ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i, _i, _vp]),
     "demag_graph_create_batched": (_i, [ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i, _i,
                                         ctypes.POINTER(_vp)]),
@@ -223,6 +225,28 @@ def demag_apply_tucker_compressed(plan: Plan, batch: int, r, core, V, out_core, 
                                              _ptr(V, batch * 3 * qs, f32, "V"),
                                              _ptr(out_core, batch * 3 * nout, f32, "out_core"),
                                              _ptr(out_V, batch * os_, f32, "out_V"), _stream(stream)), plan.ptr)
+
+
+def demag_round_tt(plan: Plan, r, w, o1, o2, o3, tol: float, stream=None):
+    """Round one item's TT output (demag_apply_tt): returns ((r1, r2), G1 [r1, n1], G2 [r1 r2, n2], G3 [r2, n3], err)."""
+    import torch
+    n1, n2, n3 = plan.n
+    r1, r2 = int(r[0]), int(r[1])
+    M = plan.M
+    f32 = torch.float32
+    rr = (ctypes.c_int * 2)(r1, r2)
+    G1o = torch.empty(64 * n1, device="cuda")
+    G2o = torch.empty(64 * 64 * n2, device="cuda")
+    G3o = torch.empty(64 * n3, device="cuda")
+    ranks = (ctypes.c_int * 2)()
+    err = ctypes.c_double()
+    _check(lib.demag_round_tt(plan.ptr, rr, _ptr(w, 3 * M, f32, "w"), _ptr(o1, 3 * M * r1 * n1, f32, "o1"),
+                              _ptr(o2, 3 * M * r1 * r2 * n2, f32, "o2"), _ptr(o3, 3 * M * r2 * n3, f32, "o3"),
+                              float(tol), ranks, G1o.data_ptr(), G2o.data_ptr(), G3o.data_ptr(), ctypes.byref(err),
+                              _stream(stream)), plan.ptr)
+    q1, q2 = int(ranks[0]), int(ranks[1])
+    return ((q1, q2), G1o[: q1 * n1].reshape(q1, n1), G2o[: q1 * q2 * n2].reshape(q1 * q2, n2),
+            G3o[: q2 * n3].reshape(q2, n3), err.value)
 
 
 def demag_recompress_tucker(plan: Plan, r, core, V, tol: float, stream=None):

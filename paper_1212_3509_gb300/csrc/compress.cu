@@ -584,6 +584,175 @@ __global__ void __launch_bounds__(256) rc_core_hosvd_kernel(int k0, int k1, int 
   }
 }
 
+// ---------------------------------------------------------------- TT rounding of phi
+//
+// App. C: the potential of a TT magnetization is a sum of T = 3M trains
+// (w_t G1_t G2_t G3_t, ranks r1, r2 each).  Rounding to tolerance tol: the
+// range of the first unfolding is sampled with Khatri-Rao products of +-1
+// test vectors (through the train: Y1 = sum_t w_t G1_t (G2_t x omega2) (G3_t omega3)),
+// QR'd (Q1); the projected train's (1,2)-unfolding is sampled with omega3 and
+// QR'd (Q2); the last core is Z = Q2^T (Q1^T phi).  The projection error
+// ||phi||^2 - ||Z||^2 is exact (||phi||^2 from the pairwise Grams of the terms);
+// samples grow (16, 32, 64) until it is below tol/2.  Then the small train
+// [Q1, Q2, Z] is truncated as in TT-SVD: the mode-1 Gram (Jacobi), a QR of the
+// truncated middle core, the Gram of the new last core; each truncation keeps
+// its discarded part within half of the remaining budget.  FP64 throughout.
+
+__global__ void rc_f2d_kernel(long count, const float* x, double* y) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < count; i += (long)gridDim.x * blockDim.x)
+    y[i] = (double)x[i];
+}
+
+// ||phi||^2 = sum_{t,t'} w_t w_t' sum GA[(t a1),(t' b1)] GB[(t a1 a2),(t' b1 b2)] GC[(t a2),(t' b2)]
+__global__ void tt_norm_kernel(int T, int ra, int rb, const double* w, const double* GA, const double* GB,
+                               const double* GC, double* out) {
+  __shared__ double red[32];
+  const long na = (long)T * ra, nb = (long)T * ra * rb, nc = (long)T * rb;
+  double acc = 0.0;
+  for (long pr = blockIdx.x * (long)blockDim.x + threadIdx.x; pr < (long)T * T; pr += (long)gridDim.x * blockDim.x) {
+    const int t = (int)(pr / T), u = (int)(pr % T);
+    double s = 0.0;
+    for (int a1 = 0; a1 < ra; ++a1)
+      for (int b1 = 0; b1 < ra; ++b1) {
+        const double ga = GA[((long)t * ra + a1) * na + (long)u * ra + b1];
+        for (int a2 = 0; a2 < rb; ++a2)
+          for (int b2 = 0; b2 < rb; ++b2)
+            s += ga * GB[(((long)t * ra + a1) * rb + a2) * nb + ((long)u * ra + b1) * rb + b2] *
+                 GC[((long)t * rb + a2) * nc + (long)u * rb + b2];
+      }
+    acc += w[t] * w[u] * s;
+  }
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double v = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) v += red[i];
+    atomicAdd(out, v);
+  }
+}
+
+// h[(t a1)][j] = w_t sum_a2 BW[(t a1 a2)][j] CW[(t a2)][j]
+__global__ void tt_h_kernel(int T, int ra, int rb, int k, const double* w, const double* BW, const double* CW,
+                            double* h) {
+  const long total = (long)T * ra * k;
+  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
+    const int j = (int)(idx % k);
+    const long ta = idx / k;
+    const int t = (int)(ta / ra);
+    double s = 0.0;
+    for (int a2 = 0; a2 < rb; ++a2) s += BW[(ta * rb + a2) * k + j] * CW[((long)t * rb + a2) * k + j];
+    h[idx] = w[t] * s;
+  }
+}
+
+// F[(t a1)][i2][j] = w_t sum_a2 B[(t a1 a2)][i2] CW[(t a2)][j]
+__global__ void tt_f_kernel(int T, int ra, int rb, int n2, int k, const double* w, const double* B, const double* CW,
+                            double* F) {
+  const long total = (long)T * ra * n2 * k;
+  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
+    const int j = (int)(idx % k);
+    const long r = idx / k;
+    const int i2 = (int)(r % n2);
+    const long ta = r / n2;
+    const int t = (int)(ta / ra);
+    double s = 0.0;
+    for (int a2 = 0; a2 < rb; ++a2) s += B[(ta * rb + a2) * n2 + i2] * CW[((long)t * rb + a2) * k + j];
+    F[idx] = w[t] * s;
+  }
+}
+
+// Y2[j][(a i2)] = sum_c AP[a][c] F[c][i2][j], c = (t a1) < cols; Y2 column-major [k][k1 n2]
+__global__ void tt_y2_kernel(int k1, int n2, int k, int cols, const double* AP, const double* F, double* Y2) {
+  const long m = (long)k1 * n2, total = m * k;
+  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
+    const int j = (int)(idx / m);
+    const long row = idx % m;
+    const int a = (int)(row / n2), i2 = (int)(row % n2);
+    double s = 0.0;
+    for (int c = 0; c < cols; ++c) s += AP[(long)a * cols + c] * F[((long)c * n2 + i2) * k + j];
+    Y2[idx] = s;
+  }
+}
+
+// Pm[c][i2][j] = sum_a Q2[j][(a i2)] AP[a][c]
+__global__ void tt_p_kernel(int k1, int n2, int k2, int cols, const double* Q2, const double* AP, double* Pm) {
+  const long total = (long)cols * n2 * k2;
+  const long m = (long)k1 * n2;
+  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
+    const int j = (int)(idx % k2);
+    const long r = idx / k2;
+    const int i2 = (int)(r % n2);
+    const long c = r / n2;
+    double s = 0.0;
+    for (int a = 0; a < k1; ++a) s += Q2[(long)j * m + (long)a * n2 + i2] * AP[(long)a * cols + c];
+    Pm[idx] = s;
+  }
+}
+
+// wE[(t a2)][j] = w_t sum_{a1, i2} Pm[(t a1)][i2][j] B[(t a1 a2)][i2]
+__global__ void tt_e_kernel(int T, int ra, int rb, int n2, int k2, const double* w, const double* Pm, const double* B,
+                            double* wE) {
+  const long total = (long)T * rb * k2;
+  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
+    const int j = (int)(idx % k2);
+    const long tb = idx / k2;
+    const int t = (int)(tb / rb), a2 = (int)(tb % rb);
+    double s = 0.0;
+    for (int a1 = 0; a1 < ra; ++a1) {
+      const long c = (long)t * ra + a1;
+      const double* brow = B + (c * rb + a2) * n2;
+      for (int i2 = 0; i2 < n2; ++i2) s += Pm[(c * n2 + i2) * k2 + j] * brow[i2];
+    }
+    wE[idx] = w[t] * s;
+  }
+}
+
+// out[(b i2)][j] = sum_a Wm[a][b] V[j][(a i2)]  -> stored column-major [k2][rb1 n2] (V' = W1^T x_1 V)
+__global__ void tt_vprime_kernel(int k1, int rb1, int n2, int k2, const double* Wm, const double* V, double* out) {
+  const long m = (long)rb1 * n2, total = m * k2;
+  const long mv = (long)k1 * n2;
+  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
+    const int j = (int)(idx / m);
+    const long row = idx % m;
+    const int b = (int)(row / n2), i2 = (int)(row % n2);
+    double s = 0.0;
+    for (int a = 0; a < k1; ++a) s += Wm[(long)a * rb1 + b] * V[(long)j * mv + (long)a * n2 + i2];
+    out[idx] = s;
+  }
+}
+
+// M1[a][b] = sum_{j, i2} V[j][(a i2)] VZ[j][(b i2)] with VZ = V ZZ (the mode-1 Gram of [V; Z])
+__global__ void tt_m1_kernel(int k1, int n2, int k2, const double* V, const double* VZ, double* M1) {
+  const long m = (long)k1 * n2;
+  const int lane = threadIdx.x & 31;
+  const long warps = (long)gridDim.x * (blockDim.x >> 5);
+  for (long wI = blockIdx.x * (long)(blockDim.x >> 5) + (threadIdx.x >> 5); wI < (long)k1 * k1; wI += warps) {
+    const int a = (int)(wI / k1), b = (int)(wI % k1);
+    double s = 0.0;
+    for (long x = lane; x < (long)k2 * n2; x += 32) {
+      const int j = (int)(x / n2), i2 = (int)(x % n2);
+      s += V[(long)j * m + (long)a * n2 + i2] * VZ[(long)j * m + (long)b * n2 + i2];
+    }
+    s = warp_sum(s);
+    if (lane == 0) M1[wI] = s;
+  }
+}
+
+// eigen-decomposition of one k x k symmetric matrix (one block, k <= 64): eig desc, V [k][k]
+__global__ void __launch_bounds__(256) rc_eig_kernel(int k, int n, const double* S, double* eig, double* V) {
+  extern __shared__ double smc[];
+  __shared__ double red[32];
+  double *A = smc, *Vs = A + n * n;
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    const int a = idx / n, b = idx % n;
+    A[idx] = (a < k && b < k) ? S[(long)a * k + b] : 0.0;
+  }
+  __syncthreads();
+  jacobi_eigen(A, Vs, n, red);
+  sorted_out(k, n, A, Vs, eig, V);
+}
+
 void compress_destroy(demag_plan* P) {
   Compressed* C = static_cast<Compressed*>(P->cmp);
   if (!C) return;
@@ -918,7 +1087,7 @@ extern "C" demag_status demag_recompress_tucker(demag_plan* P, const int r[3], c
     DEMAG_CUDA(P, cudaStreamSynchronize(st));
     es2 = std::max(0.0, phi2 - c2);
     const bool full = kd[0] == n[0] && kd[1] == n[1] && kd[2] == n[2];
-    if (es2 <= 0.25 * tol * tol * phi2 || full) break;
+    if (es2 <= 0.0625 * tol * tol * phi2 || full) break;
     if (k >= 64) {
       release();
       return set_error(P, DEMAG_EUNSUPPORTED,
@@ -1011,5 +1180,252 @@ extern "C" demag_status demag_recompress_tucker(demag_plan* P, const int r[3], c
   release();
   for (int p = 0; p < 3; ++p) ranks_out[p] = rk[p];
   if (err_out) *err_out = sqrt((es2 + tails) / phi2);
+  return DEMAG_OK;
+}
+
+// smallest r >= 1 whose discarded eigenvalues (descending, k of them) sum to <= bound; tail returned
+static int tail_rank(const double* ev, int k, double bound, double* tail_out) {
+  double tot = 0.0;
+  for (int i = 0; i < k; ++i) tot += std::max(0.0, ev[i]);
+  double tail = tot;
+  int r = k;
+  for (int rr = 1; rr <= k; ++rr) {
+    tail -= std::max(0.0, ev[rr - 1]);
+    if (tail <= bound) {
+      r = rr;
+      break;
+    }
+  }
+  double kept = 0.0;
+  for (int i = 0; i < r; ++i) kept += std::max(0.0, ev[i]);
+  *tail_out = std::max(0.0, tot - kept);
+  return r;
+}
+
+extern "C" demag_status demag_round_tt(demag_plan* P, const int r[2], const float* w, const float* G1,
+                                       const float* G2, const float* G3, double tol, int ranks_out[2],
+                                       float* G1_out, float* G2_out, float* G3_out, double* err_out,
+                                       void* stream) {
+  if (!P) return set_error(nullptr, DEMAG_EINVAL, "demag_round_tt: plan is NULL");
+  if (!r || !w || !G1 || !G2 || !G3 || !ranks_out || !G1_out || !G2_out || !G3_out)
+    return set_error(P, DEMAG_EINVAL, "demag_round_tt: NULL pointer");
+  if (r[0] < 1 || r[1] < 1) return set_error(P, DEMAG_EINVAL, "demag_round_tt: ranks must be >= 1");
+  if (!(tol > 0.0 && tol < 1.0)) return set_error(P, DEMAG_EINVAL, "demag_round_tt: tol must be in (0, 1)");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int T = 3 * P->M, ra = r[0], rb = r[1];
+  const int n1 = P->n[0], n2 = P->n[1], n3 = P->n[2];
+  const long nA = (long)T * ra * n1, nB = (long)T * ra * rb * n2, nC = (long)T * rb * n3;
+  const long kmax = 64;
+  std::vector<void*> owned;
+  cudaError_t e = cudaSuccess;
+  auto alloc = [&](double** ptr, long count) {
+    if (e != cudaSuccess) return;
+    e = cudaMalloc(ptr, sizeof(double) * (size_t)std::max(count, 1L));
+    if (e == cudaSuccess) owned.push_back(*ptr);
+  };
+  auto release = [&]() {
+    for (void* q : owned) cudaFree(q);
+    owned.clear();
+  };
+  double *wd, *A, *B, *C, *GA, *GB, *GC, *acc, *CW1, *CW2, *BW, *hh, *Y1, *Q1, *R1, *AP, *F, *Y2, *Q2, *R2, *wE, *Z;
+  double *ZZ, *VZ, *M1, *ev, *EV, *Wm, *Vp, *Qv, *Rv, *Zp, *O1, *O2, *O3;
+  const long m12 = kmax * n2;  // rows of the (1,2) unfolding at most
+  alloc(&wd, T);
+  alloc(&A, nA);
+  alloc(&B, nB);
+  alloc(&C, nC);
+  alloc(&GA, (long)T * ra * T * ra);
+  alloc(&GB, (long)T * ra * rb * T * ra * rb);
+  alloc(&GC, (long)T * rb * T * rb);
+  alloc(&acc, 2);
+  alloc(&CW1, (long)T * rb * kmax);
+  alloc(&CW2, (long)T * rb * kmax);
+  alloc(&BW, (long)T * ra * rb * kmax);
+  alloc(&hh, (long)T * ra * kmax);
+  alloc(&Y1, kmax * n1);
+  alloc(&Q1, kmax * n1);
+  alloc(&R1, kmax * kmax);
+  alloc(&AP, kmax * T * ra);
+  alloc(&F, (long)T * ra * n2 * kmax);
+  alloc(&Y2, kmax * m12);
+  alloc(&Q2, kmax * m12);
+  alloc(&R2, kmax * kmax);
+  alloc(&wE, (long)T * rb * kmax);
+  alloc(&Z, kmax * n3);
+  alloc(&ZZ, kmax * kmax);
+  alloc(&VZ, kmax * m12);
+  alloc(&M1, kmax * kmax);
+  alloc(&ev, kmax);
+  alloc(&EV, kmax * kmax);
+  alloc(&Wm, kmax * kmax);
+  alloc(&Vp, kmax * m12);
+  alloc(&Qv, kmax * m12);
+  alloc(&Rv, kmax * kmax);
+  alloc(&Zp, kmax * n3);
+  alloc(&O1, kmax * n1);
+  alloc(&O2, kmax * m12);
+  alloc(&O3, kmax * n3);
+  if (e != cudaSuccess) {
+    release();
+    return cuda_error(P, e, "demag_round_tt: workspace");
+  }
+#define TT_LAUNCH(name, ...)                                 \
+  do {                                                       \
+    DEMAG_LAUNCH(P, kFamMisc, st, __VA_ARGS__);              \
+    if ((e = cudaGetLastError()) != cudaSuccess) {           \
+      release();                                             \
+      return cuda_error(P, e, name);                         \
+    }                                                        \
+  } while (0)
+#define TT_CUDA(call)                                        \
+  do {                                                       \
+    if ((e = (call)) != cudaSuccess) {                       \
+      release();                                             \
+      return cuda_error(P, e, #call);                        \
+    }                                                        \
+  } while (0)
+  TT_LAUNCH("rc_f2d_kernel", rc_f2d_kernel<<<rc_blocks(T), 256, 0, st>>>(T, w, wd));
+  TT_LAUNCH("rc_f2d_kernel", rc_f2d_kernel<<<rc_blocks(nA), 256, 0, st>>>(nA, G1, A));
+  TT_LAUNCH("rc_f2d_kernel", rc_f2d_kernel<<<rc_blocks(nB), 256, 0, st>>>(nB, G2, B));
+  TT_LAUNCH("rc_f2d_kernel", rc_f2d_kernel<<<rc_blocks(nC), 256, 0, st>>>(nC, G3, C));
+  // 1. ||phi||^2 from the pairwise Grams of the terms
+  const long na = (long)T * ra, nbb = (long)T * ra * rb, nc = (long)T * rb;
+  TT_LAUNCH("rc_gram_kernel", rc_gram_kernel<<<rc_blocks(na * na * 32), 256, 0, st>>>(n1, (int)na, (int)na, A, A, GA));
+  TT_LAUNCH("rc_gram_kernel", rc_gram_kernel<<<rc_blocks(nbb * nbb * 32), 256, 0, st>>>(n2, (int)nbb, (int)nbb, B, B, GB));
+  TT_LAUNCH("rc_gram_kernel", rc_gram_kernel<<<rc_blocks(nc * nc * 32), 256, 0, st>>>(n3, (int)nc, (int)nc, C, C, GC));
+  TT_CUDA(cudaMemsetAsync(acc, 0, sizeof(double) * 2, st));
+  TT_LAUNCH("tt_norm_kernel", tt_norm_kernel<<<rc_blocks((long)T * T), 256, 0, st>>>(T, ra, rb, wd, GA, GB, GC, acc));
+  double phi2 = 0.0;
+  TT_CUDA(cudaMemcpyAsync(&phi2, acc, sizeof(double), cudaMemcpyDeviceToHost, st));
+  TT_CUDA(cudaStreamSynchronize(st));
+  if (!(phi2 > 0.0)) {
+    release();
+    return set_error(P, DEMAG_EINVAL, "demag_round_tt: the potential is zero");
+  }
+  // 2. sketched ranges
+  const unsigned long long seed = 0x7717ull;
+  int k1 = 0, k2 = 0;
+  double es2 = 0.0;
+  for (int k = 16;; k *= 2) {
+    k1 = std::min(k, n1);
+    k2 = (int)std::min<long>(std::min<long>(k, (long)k1 * n2), n3);
+    TT_LAUNCH("rc_probe_kernel", rc_probe_kernel<<<rc_blocks(nc * k1), 256, 0, st>>>(n3, (int)nc, k1, 2, seed, C, CW1));
+    TT_LAUNCH("rc_probe_kernel", rc_probe_kernel<<<rc_blocks(nbb * k1), 256, 0, st>>>(n2, (int)nbb, k1, 1, seed, B, BW));
+    TT_LAUNCH("tt_h_kernel", tt_h_kernel<<<rc_blocks(na * k1), 256, 0, st>>>(T, ra, rb, k1, wd, BW, CW1, hh));
+    TT_LAUNCH("rc_range_kernel", rc_range_kernel<<<rc_blocks((long)k1 * n1), 256, 0, st>>>(n1, (int)na, k1, A, hh, Y1, 0));
+    TT_LAUNCH("rc_qr_kernel", rc_qr_kernel<<<1, 256, 0, st>>>(k1, n1, Y1, Q1, R1));
+    TT_LAUNCH("rc_gram_kernel", rc_gram_kernel<<<rc_blocks((long)k1 * na * 32), 256, 0, st>>>(n1, k1, (int)na, Q1, A, AP));
+    TT_LAUNCH("rc_probe_kernel", rc_probe_kernel<<<rc_blocks(nc * k2), 256, 0, st>>>(n3, (int)nc, k2, 3, seed, C, CW2));
+    TT_LAUNCH("tt_f_kernel", tt_f_kernel<<<rc_blocks(na * n2 * k2), 256, 0, st>>>(T, ra, rb, n2, k2, wd, B, CW2, F));
+    TT_LAUNCH("tt_y2_kernel", tt_y2_kernel<<<rc_blocks((long)k1 * n2 * k2), 256, 0, st>>>(k1, n2, k2, (int)na, AP, F, Y2));
+    TT_LAUNCH("rc_qr_kernel", rc_qr_kernel<<<1, 256, 0, st>>>(k2, k1 * n2, Y2, Q2, R2));
+    TT_LAUNCH("tt_p_kernel", tt_p_kernel<<<rc_blocks(na * n2 * k2), 256, 0, st>>>(k1, n2, k2, (int)na, Q2, AP, F));
+    TT_LAUNCH("tt_e_kernel", tt_e_kernel<<<rc_blocks(nc * k2), 256, 0, st>>>(T, ra, rb, n2, k2, wd, F, B, wE));
+    TT_LAUNCH("rc_range_kernel", rc_range_kernel<<<rc_blocks((long)k2 * n3), 256, 0, st>>>(n3, (int)nc, k2, C, wE, Z, 0));
+    TT_CUDA(cudaMemsetAsync(acc + 1, 0, sizeof(double), st));
+    TT_LAUNCH("rc_dot_kernel", rc_dot_kernel<<<rc_blocks((long)k2 * n3), 256, 0, st>>>((long)k2 * n3, Z, Z, acc + 1));
+    double z2 = 0.0;
+    TT_CUDA(cudaMemcpyAsync(&z2, acc + 1, sizeof(double), cudaMemcpyDeviceToHost, st));
+    TT_CUDA(cudaStreamSynchronize(st));
+    es2 = std::max(0.0, phi2 - z2);
+    const bool full = k1 == n1 && k2 == (int)std::min<long>((long)k1 * n2, n3);
+    if (es2 <= 0.0625 * tol * tol * phi2 || full) break;
+    if (k >= 64) {
+      release();
+      return set_error(P, DEMAG_EUNSUPPORTED, "demag_round_tt: ranks above 64 needed for tol %g (projection error %g)",
+                       tol, sqrt(es2 / phi2));
+    }
+  }
+  // 3. truncations of the projected train: ||phi - phi_hat|| <= sqrt(es2) + sqrt(tail1 + tail2),
+  // so the two tails share (tol ||phi|| - sqrt(es2))^2, half each
+  const double room = std::max(0.0, tol * sqrt(phi2) - sqrt(es2));
+  const double half = 0.5 * room * room;
+  auto eig = [&](int k, const double* S, std::vector<double>& evh, std::vector<double>& vh) -> demag_status {
+    const int n = k + (k & 1);
+    TT_LAUNCH("rc_eig_kernel", rc_eig_kernel<<<1, 256, sizeof(double) * 2 * n * n, st>>>(k, n, S, ev, EV));
+    evh.resize(k);
+    vh.resize((size_t)k * k);
+    TT_CUDA(cudaMemcpyAsync(evh.data(), ev, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
+    TT_CUDA(cudaMemcpyAsync(vh.data(), EV, sizeof(double) * k * k, cudaMemcpyDeviceToHost, st));
+    TT_CUDA(cudaStreamSynchronize(st));
+    return DEMAG_OK;
+  };
+  {
+    static unsigned long long attr = 0;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (!(attr & (1ull << (dev & 63)))) {
+      TT_CUDA(cudaFuncSetAttribute(rc_eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 64 * 64 * 8));
+      attr |= 1ull << (dev & 63);
+    }
+  }
+  std::vector<double> evh, vh;
+  // mode 1
+  TT_LAUNCH("rc_gram_kernel", rc_gram_kernel<<<rc_blocks((long)k2 * k2 * 32), 256, 0, st>>>(n3, k2, k2, Z, Z, ZZ));
+  TT_LAUNCH("rc_range_kernel", rc_range_kernel<<<rc_blocks((long)k2 * k1 * n2), 256, 0, st>>>(k1 * n2, k2, k2, Q2, ZZ, VZ, 0));
+  TT_LAUNCH("tt_m1_kernel", tt_m1_kernel<<<rc_blocks((long)k1 * k1 * 32), 256, 0, st>>>(k1, n2, k2, Q2, VZ, M1));
+  demag_status rs = eig(k1, M1, evh, vh);
+  if (rs != DEMAG_OK) return rs;
+  double tail1 = 0.0, tail2 = 0.0;
+  const int q1 = tail_rank(evh.data(), k1, half, &tail1);
+  std::vector<double> w1((size_t)k1 * q1);  // [a][i]
+  for (int a = 0; a < k1; ++a)
+    for (int i = 0; i < q1; ++i) w1[(size_t)a * q1 + i] = vh[(size_t)a * k1 + i];
+  TT_CUDA(cudaMemcpyAsync(Wm, w1.data(), sizeof(double) * w1.size(), cudaMemcpyHostToDevice, st));
+  TT_LAUNCH("rc_range_kernel", rc_range_kernel<<<rc_blocks((long)q1 * n1), 256, 0, st>>>(n1, k1, q1, Q1, Wm, O1, 0));
+  TT_LAUNCH("tt_vprime_kernel", tt_vprime_kernel<<<rc_blocks((long)q1 * n2 * k2), 256, 0, st>>>(k1, q1, n2, k2, Wm, Q2, Vp));
+  TT_LAUNCH("rc_qr_kernel", rc_qr_kernel<<<1, 256, 0, st>>>(k2, q1 * n2, Vp, Qv, Rv));
+  std::vector<double> rvh((size_t)k2 * k2), rvt((size_t)k2 * k2);
+  TT_CUDA(cudaMemcpyAsync(rvh.data(), Rv, sizeof(double) * rvh.size(), cudaMemcpyDeviceToHost, st));
+  TT_CUDA(cudaStreamSynchronize(st));
+  for (int j = 0; j < k2; ++j)
+    for (int c = 0; c < k2; ++c) rvt[(size_t)c * k2 + j] = rvh[(size_t)j * k2 + c];  // Zm[c][j] = Rv[j][c]
+  TT_CUDA(cudaMemcpyAsync(Wm, rvt.data(), sizeof(double) * rvt.size(), cudaMemcpyHostToDevice, st));
+  TT_LAUNCH("rc_range_kernel", rc_range_kernel<<<rc_blocks((long)k2 * n3), 256, 0, st>>>(n3, k2, k2, Z, Wm, Zp, 0));
+  // mode 2 (the (1,2) interface)
+  TT_CUDA(cudaStreamSynchronize(st));
+  TT_LAUNCH("rc_gram_kernel", rc_gram_kernel<<<rc_blocks((long)k2 * k2 * 32), 256, 0, st>>>(n3, k2, k2, Zp, Zp, ZZ));
+  rs = eig(k2, ZZ, evh, vh);
+  if (rs != DEMAG_OK) return rs;
+  const int q2 = tail_rank(evh.data(), k2, half, &tail2);
+  std::vector<double> w2((size_t)k2 * q2);
+  for (int j = 0; j < k2; ++j)
+    for (int c = 0; c < q2; ++c) w2[(size_t)j * q2 + c] = vh[(size_t)j * k2 + c];
+  TT_CUDA(cudaMemcpyAsync(Wm, w2.data(), sizeof(double) * w2.size(), cudaMemcpyHostToDevice, st));
+  TT_LAUNCH("rc_range_kernel", rc_range_kernel<<<rc_blocks((long)q2 * q1 * n2), 256, 0, st>>>(q1 * n2, k2, q2, Qv, Wm, O2, 0));
+  // 4. last core as the orthogonal projection of phi itself on the first two cores,
+  // G3 = G2^T (G1^T phi); then ||phi - phi_hat||^2 = ||phi||^2 - ||G3||^2 exactly
+  TT_LAUNCH("rc_gram_kernel", rc_gram_kernel<<<rc_blocks((long)q1 * na * 32), 256, 0, st>>>(n1, q1, (int)na, O1, A, AP));
+  TT_LAUNCH("tt_p_kernel", tt_p_kernel<<<rc_blocks(na * n2 * q2), 256, 0, st>>>(q1, n2, q2, (int)na, O2, AP, F));
+  TT_LAUNCH("tt_e_kernel", tt_e_kernel<<<rc_blocks(nc * q2), 256, 0, st>>>(T, ra, rb, n2, q2, wd, F, B, wE));
+  TT_LAUNCH("rc_range_kernel", rc_range_kernel<<<rc_blocks((long)q2 * n3), 256, 0, st>>>(n3, (int)nc, q2, C, wE, O3, 0));
+  TT_CUDA(cudaMemsetAsync(acc + 1, 0, sizeof(double), st));
+  TT_LAUNCH("rc_dot_kernel", rc_dot_kernel<<<rc_blocks((long)q2 * n3), 256, 0, st>>>((long)q2 * n3, O3, O3, acc + 1));
+  double g32 = 0.0;
+  TT_CUDA(cudaMemcpyAsync(&g32, acc + 1, sizeof(double), cudaMemcpyDeviceToHost, st));
+  TT_CUDA(cudaStreamSynchronize(st));
+  // outputs (FP32): G1 [q1][n1]; G2 [(b c)][n2] from O2 [c][(b i2)]; G3 [q2][n3]
+  {
+    std::vector<double> o1((size_t)q1 * n1), o2((size_t)q2 * q1 * n2), o3((size_t)q2 * n3);
+    TT_CUDA(cudaMemcpyAsync(o1.data(), O1, sizeof(double) * o1.size(), cudaMemcpyDeviceToHost, st));
+    TT_CUDA(cudaMemcpyAsync(o2.data(), O2, sizeof(double) * o2.size(), cudaMemcpyDeviceToHost, st));
+    TT_CUDA(cudaMemcpyAsync(o3.data(), O3, sizeof(double) * o3.size(), cudaMemcpyDeviceToHost, st));
+    TT_CUDA(cudaStreamSynchronize(st));
+    std::vector<float> f1(o1.begin(), o1.end()), f3(o3.begin(), o3.end()), f2((size_t)q1 * q2 * n2);
+    for (int b = 0; b < q1; ++b)
+      for (int c = 0; c < q2; ++c)
+        for (int i2 = 0; i2 < n2; ++i2)
+          f2[((size_t)b * q2 + c) * n2 + i2] = (float)o2[(size_t)c * q1 * n2 + (size_t)b * n2 + i2];
+    TT_CUDA(cudaMemcpyAsync(G1_out, f1.data(), sizeof(float) * f1.size(), cudaMemcpyHostToDevice, st));
+    TT_CUDA(cudaMemcpyAsync(G2_out, f2.data(), sizeof(float) * f2.size(), cudaMemcpyHostToDevice, st));
+    TT_CUDA(cudaMemcpyAsync(G3_out, f3.data(), sizeof(float) * f3.size(), cudaMemcpyHostToDevice, st));
+    TT_CUDA(cudaStreamSynchronize(st));
+  }
+#undef TT_LAUNCH
+#undef TT_CUDA
+  release();
+  ranks_out[0] = q1;
+  ranks_out[1] = q2;
+  if (err_out) *err_out = sqrt(std::max(0.0, phi2 - g32) / phi2);
   return DEMAG_OK;
 }

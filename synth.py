@@ -161,6 +161,21 @@ def tt_inputs(n, ranks, seed: int):
     return G1.astype(np.float32), G2.astype(np.float32), G3.astype(np.float32)
 
 
+def tt_smooth_inputs(n, ranks, seed: int):
+    """3D tensor trains per component with smooth cores (each fibre from smooth_vectors).
+
+    Same layouts as tt_inputs; the represented tensors are smooth, like a
+    magnetization sampled from a smooth field, so the potential has small TT
+    ranks at moderate tolerances.
+    """
+    n1, n2, n3 = n
+    r1, r2 = ranks
+    G1 = np.stack([smooth_vectors(n1, r1, seed * 131 + q) for q in range(3)])
+    G2 = np.stack([smooth_vectors(n2, r1 * r2, seed * 131 + 7 + q) for q in range(3)])
+    G3 = np.stack([smooth_vectors(n3, r2, seed * 131 + 17 + q) for q in range(3)])
+    return G1.astype(np.float32), G2.astype(np.float32), G3.astype(np.float32)
+
+
 def uneven_batch_shapes(count: int, seed: int):
     """Mixed full-format grid shapes: cubes 32^3..192^3 and thin films.
 
