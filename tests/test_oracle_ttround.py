@@ -52,3 +52,32 @@ def test_planted_split_breaks_the_bound_sometimes():
         G1, G2, G3, rk = otr.tt_round_dense(X, tol)
         assert np.linalg.norm(ost.tt_to_full(G1, G2, G3, rk) - X) <= tol * np.linalg.norm(X) * (1 + 1e-9)
     assert worst > 1.0
+
+
+def test_known_tt_rank_is_recovered_exactly():
+    # a tensor built as a train of ranks (2, 3) has exactly those TT ranks (generic cores):
+    # rounding at a tiny tolerance recovers them and the tensor
+    rng = np.random.default_rng(3)
+    n1, n2, n3 = 9, 8, 7
+    A = rng.standard_normal((2, n1))
+    B = rng.standard_normal((2 * 3, n2))
+    C = rng.standard_normal((3, n3))
+    X = ost.tt_to_full(A, B, C, (2, 3))
+    G1, G2, G3, rk = otr.tt_round_dense(X, 1e-12)
+    assert rk == (2, 3)
+    assert np.linalg.norm(ost.tt_to_full(G1, G2, G3, rk) - X) <= 1e-12 * np.linalg.norm(X)
+
+
+def test_cores_are_left_orthonormal_and_first_truncation_is_optimal():
+    X, _ = _phi()
+    G1, G2, G3, (r1, r2) = otr.tt_round_dense(X, 1e-3)
+    assert np.allclose(G1 @ G1.T, np.eye(r1), atol=1e-12)
+    n2 = X.shape[1]
+    L = G2.reshape(r1, r2, n2).transpose(0, 2, 1).reshape(r1 * n2, r2)
+    assert np.allclose(L.T @ L, np.eye(r2), atol=1e-12)
+    # Eckart-Young: projecting the first unfolding on G1 leaves exactly the discarded singular values
+    n3, _, n1 = X.shape
+    X1 = X.transpose(2, 1, 0).reshape(n1, -1)
+    s = np.linalg.svd(X1, compute_uv=False)
+    resid = np.linalg.norm(X1 - G1.T @ (G1 @ X1))
+    assert abs(resid - np.sqrt(np.sum(s[r1:] ** 2))) <= 1e-10 * np.linalg.norm(X1)
