@@ -76,3 +76,27 @@ def energy_gradient(m, n, h, R: int, c0: float = 2.15) -> np.ndarray:
     DPm = gradient(apply_full(m, n, h, R, c0), h)
     PtDtm = apply_adjoint(gradient_adjoint(m, h), n, h, R, c0)
     return 0.5 * V * (DPm + PtDtm)
+
+
+def energy_tucker(core, V, n, ranks, h, R: int, c0: float = 2.15) -> float:
+    """Energy of a Tucker magnetization through the structured path (Alg. 2's application, then
+    the second-order energy of the study after Alg. 2): m^(q) = [[G^(q); V^(q,p)]] and
+    phi = sum_{k,q} w_kq [[G^(q); T_{k,q,p} V^(q,p)]] (Eq. kron_eval_tuck) are formed densely and
+    E is taken by `energy`.  core: [3][r3][r2][r1]; V: the flat ABI blocks (q, p) [r_p][n_p]."""
+    from . import structured as ost
+
+    n = tuple(int(v) for v in n)
+    core = np.asarray(core, dtype=np.float64)
+    w, outV = ost.apply_tucker(core, V, n, ranks, h, R, c0)
+    phi = ost.tucker_output_to_full(core, w, outV)
+    return energy(tucker_magnetization(core, V, n, ranks), phi, h)
+
+
+def tucker_magnetization(core, V, n, ranks) -> np.ndarray:
+    """The dense field [3][n3][n2][n1] of a Tucker magnetization (ABI layout of core and V)."""
+    from . import structured as ost
+
+    n = tuple(int(v) for v in n)
+    core = np.asarray(core, dtype=np.float64)
+    Vb = ost._split_blocks(V, n, ranks)
+    return np.stack([ost.tucker_to_full(core[q], [Vb[q][p] for p in range(3)]) for q in range(3)])

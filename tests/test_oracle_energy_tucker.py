@@ -1,0 +1,40 @@
+"""Pins of the oracle's energy of a Tucker magnetization (oracle/energy.py: energy_tucker).
+
+1. The structured route (Eq. kron_eval_tuck per node and component, then the
+   second-order energy) gives the energy of the full-format route on the same
+   dense magnetization.
+2. Uniform magnetization of the unit cube, the case of the energy study after
+   Alg. 2: the Tucker-route energy equals the energy of the closed-form exact
+   collocation potential (charged-rectangle integrals), up to the sinc
+   quadrature error, which vanishes as R grows.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import energy as oe
+from oracle import exact
+
+
+def test_tucker_energy_equals_the_full_format_energy():
+    n, ranks, h, R = (9, 7, 6), (2, 3, 2), (0.11, 0.11, 0.11), 21
+    core, V = synth.tucker_inputs(n, ranks, 41)
+    E = oe.energy_tucker(core, V, n, ranks, h, R)
+    m = oe.tucker_magnetization(core, V, n, ranks)
+    ref = oe.energy_from_m(m, n, h, R)
+    assert abs(E - ref) <= 1e-12 * abs(ref)
+
+
+@pytest.mark.parametrize("n", [16, 32])
+def test_uniform_cube_energy_is_the_exact_collocation_energy(n):
+    h = (1.0 / n,) * 3
+    core = np.zeros((3, 1, 1, 1))
+    core[2] = 1.0
+    V = np.ones(3 * 3 * n)
+    m = synth.uniform_m((n, n, n), 2).astype(np.float64)
+    exact_E = oe.energy(m, exact.uniform_box_potential((n, n, n), h, 2), h)
+    errs = [abs(oe.energy_tucker(core, V, (n, n, n), (1, 1, 1), h, R) - exact_E) / exact_E for R in (21, 41, 129)]
+    assert errs[2] <= 1e-10
+    assert errs[0] > errs[1] > errs[2] or errs[1] <= 1e-10
+    # and the discretisation error itself, near 1/6 (the text after Fig. 2)
+    assert abs(exact_E - 1.0 / 6.0) < 3e-3
