@@ -359,6 +359,26 @@ demag_status demag_round_tt(demag_plan* plan, const int r[2], const float* w, co
 
 /* ---- stray field, energy and gradient (h_d = -grad phi, Sec. 1) ---------- */
 
+/* Demag energy of a Tucker magnetization without forming a full tensor (Alg. 2
+ * and the energy study after it): E = 1/2 h1 h2 h3 sum_q <m^(q), D_q phi>,
+ * m^(q) = [[G^(q); V^(q,1), V^(q,2), V^(q,3)]], D_q the second-order difference
+ * along axis q (the stencils of demag_stray_field) applied to the factors of
+ * that axis, inner products of Tucker tensors through their factor Grams.
+ * phi is the output of demag_apply_tucker for this input (out_w float [M][3],
+ * out_V its three mode blocks).  r[3] in [1, 64]; core float [3][r3][r2][r1];
+ * V float blocks (q, p) [r_p][n_p]; energy: one double on the device
+ * (overwritten).  FP64 accumulation.  Uniform grids only. */
+demag_status demag_energy_tucker(demag_plan* plan, const int r[3], const float* core, const float* V,
+                                 const float* out_w, const float* out_V, double* energy, void* stream);
+
+/* The same energy with phi given as one Tucker tensor [[phi_core; U_1, U_2, U_3]]
+ * of ranks rho[3] in [1, 64] (the output of demag_recompress_tucker: phi_core
+ * float [rho3][rho2][rho1], phi_U float rows [rho_p][n_p] per mode, modes one
+ * after another). */
+demag_status demag_energy_tucker_phi(demag_plan* plan, const int r[3], const float* core, const float* V,
+                                     const int rho[3], const float* phi_core, const float* phi_U,
+                                     double* energy, void* stream);
+
 /* Second-order finite-difference stray field h_d = -D phi: central
  * differences inside, 3-point one-sided at the first and last cell of each
  * axis (two-point for n_p = 2, zero for n_p = 1).

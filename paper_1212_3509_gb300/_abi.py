@@ -77,6 +77,8 @@ _SIGS = {
     "demag_apply_tt": (_i, [_vp, ctypes.POINTER(_i), _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "demag_apply_tucker_batched": (_i, [_vp, _i, ctypes.POINTER(_i), _vp, _vp, _vp, _vp]),
     "demag_apply_tt_batched": (_i, [_vp, _i, ctypes.POINTER(_i), _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "demag_energy_tucker": (_i, [_vp, ctypes.POINTER(_i), _vp, _vp, _vp, _vp, _vp, _vp]),
+    "demag_energy_tucker_phi": (_i, [_vp, ctypes.POINTER(_i), _vp, _vp, ctypes.POINTER(_i), _vp, _vp, _vp, _vp]),
     "demag_stray_field": (_i, [_vp, _vp, _vp, _vp]),
     "demag_stray_field_exact": (_i, [_vp, _vp, _vp, _i, _vp]),
     "demag_energy": (_i, [_vp, _vp, _vp, _vp, _i, _vp]),
@@ -458,6 +460,34 @@ def demag_energy(plan: Plan, m, energy, grad=None, precision="fp32", stream=None
     import torch
     _check(lib.demag_energy(plan.ptr, _ptr(m, 3 * plan.N, torch.float32, "m"), _ptr(energy, 1, torch.float64, "energy"),
                             _ptr(grad, 3 * plan.N, torch.float32, "grad"), _prec(precision), _stream(stream)), plan.ptr)
+
+
+def demag_energy_tucker(plan: Plan, ranks, core, V, out_w, out_V, energy, stream=None):
+    """Energy of a Tucker magnetization from its demag_apply_tucker output (energy: device float64)."""
+    import torch
+    r = (_i * 3)(*[int(v) for v in ranks])
+    tot = sum(int(ranks[p]) * plan.n[p] for p in range(3))
+    f32 = torch.float32
+    _check(lib.demag_energy_tucker(plan.ptr, r, _ptr(core, 3 * int(ranks[0]) * int(ranks[1]) * int(ranks[2]), f32,
+                                                     "core"),
+                                   _ptr(V, 3 * tot, f32, "V"), _ptr(out_w, plan.M * 3, f32, "out_w"),
+                                   _ptr(out_V, plan.M * 3 * tot, f32, "out_V"),
+                                   _ptr(energy, 1, torch.float64, "energy"), _stream(stream)), plan.ptr)
+
+
+def demag_energy_tucker_phi(plan: Plan, ranks, core, V, rho, phi_core, phi_U, energy, stream=None):
+    """Energy of a Tucker magnetization with phi one Tucker tensor [[phi_core; U]] of ranks rho."""
+    import torch
+    r = (_i * 3)(*[int(v) for v in ranks])
+    rr = (_i * 3)(*[int(v) for v in rho])
+    tot = sum(int(ranks[p]) * plan.n[p] for p in range(3))
+    f32 = torch.float32
+    _check(lib.demag_energy_tucker_phi(plan.ptr, r,
+                                       _ptr(core, 3 * int(ranks[0]) * int(ranks[1]) * int(ranks[2]), f32, "core"),
+                                       _ptr(V, 3 * tot, f32, "V"), rr,
+                                       _ptr(phi_core, int(rho[0]) * int(rho[1]) * int(rho[2]), f32, "phi_core"),
+                                       _ptr(phi_U, sum(int(rho[p]) * plan.n[p] for p in range(3)), f32, "phi_U"),
+                                       _ptr(energy, 1, torch.float64, "energy"), _stream(stream)), plan.ptr)
 
 
 def demag_stray_field_exact(plan: Plan, m, hd, precision="fp32", stream=None):

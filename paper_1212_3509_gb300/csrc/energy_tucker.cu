@@ -1,0 +1,233 @@
+// Demag energy of a Tucker magnetization from its potential in Tucker form,
+// without forming a full tensor (Alg. 2 and the energy study after it).
+//
+// m^(q) = [[G^(q); V^(q,1), V^(q,2), V^(q,3)]] (Eq. tucker_rep) and
+// phi = sum_t w_t [[C_t; W_t1, W_t2, W_t3]]: either the terms (k, q') of the
+// Tucker application (core G^(q'), factors T_{k,q',p} V^(q',p), weight
+// c s omega_k; Eq. kron_eval_tuck) or one Tucker tensor (the approximate sum
+// of Alg. 2).  The stray field is -D phi with the second-order stencils of
+// energy.cu; along axis q the difference acts on the factors of that axis
+// only, so with W'_tp = D_q W_tp (p = q) or W_tp (p != q)
+//   E = 1/2 h1 h2 h3 sum_q sum_t w_t < m^(q), [[C_t; W'_t1, W'_t2, W'_t3]] >.
+// The inner product of two Tucker tensors contracts the cores through the
+// factor Grams M_p = V^(q,p)^T W'_tp:
+//   <[[G; V]], [[C; W']]> = sum_{a,b} G[a] C[b] prod_p M_p[a_p][b_p].
+// One block per (term, component): the Grams in shared memory, the core
+// contraction mode by mode through a global workspace, FP64 throughout from
+// the FP32 factors; the per-block values are summed in a fixed order.
+#include "internal.h"
+
+namespace demag {
+
+constexpr int kEnMaxRank = 64;
+
+__device__ __forceinline__ double en_warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+struct EnTucker {
+  int n[3];
+  double inv2h[3];   // 1 / (2 h_p)
+  int r[3];          // multilinear ranks of m
+  const float* G;    // [3][r3][r2][r1]
+  const float* V;    // blocks (q, p), each [r_p][n_p]
+  int s[3];          // ranks of every phi term
+  const float* C;    // term cores [s3][s2][s1]: C + (core_by_q ? t % 3 : 0) * s1 s2 s3
+  int core_by_q;
+  const float* W[3]; // term t, mode p: rows W[p] + t * s_p * n_p
+  const float* w;    // term weights (NULL: 1)
+  int T;             // number of terms
+  double* ws;        // per block r1 s3 (s2 + r2) doubles
+  double* part;      // [T][3]
+};
+
+// (D w)[i] of one factor row with the second-order stencils (central inside,
+// 3-point one-sided at the ends, two-point for n = 2, zero for n = 1)
+__device__ __forceinline__ double fd_row(const float* w, int i, int n, double inv2h) {
+  if (n == 1) return 0.0;
+  if (n == 2) return 2.0 * inv2h * ((double)w[1] - (double)w[0]);
+  if (i == 0) return inv2h * (-3.0 * (double)w[0] + 4.0 * (double)w[1] - (double)w[2]);
+  if (i == n - 1) return inv2h * (3.0 * (double)w[n - 1] - 4.0 * (double)w[n - 2] + (double)w[n - 3]);
+  return inv2h * ((double)w[i + 1] - (double)w[i - 1]);
+}
+
+__global__ void __launch_bounds__(256) tucker_energy_kernel(const __grid_constant__ EnTucker a) {
+  extern __shared__ double Mg[];
+  __shared__ double red[32];
+  const int t = blockIdx.x, q = blockIdx.y;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int r1 = a.r[0], r2 = a.r[1], r3 = a.r[2];
+  const int s1 = a.s[0], s2 = a.s[1], s3 = a.s[2];
+  // 1. Grams M_p [r_p][s_p] at offsets sum_{p' < p} r_p' s_p'
+  long voff = (long)q * ((long)r1 * a.n[0] + (long)r2 * a.n[1] + (long)r3 * a.n[2]);
+  int moff = 0;
+  int mo[3];
+  for (int p = 0; p < 3; ++p) {
+    const int n = a.n[p], rp = a.r[p], sp = a.s[p];
+    const float* Vq = a.V + voff;
+    const float* Wt = a.W[p] + (long)t * sp * n;
+    mo[p] = moff;
+    for (int e = warp; e < rp * sp; e += nw) {
+      const int ia = e / sp, ib = e % sp;
+      const float* vr = Vq + (long)ia * n;
+      const float* wr = Wt + (long)ib * n;
+      double acc = 0.0;
+      if (p == q)
+        for (int i = lane; i < n; i += 32) acc += (double)vr[i] * fd_row(wr, i, n, a.inv2h[p]);
+      else
+        for (int i = lane; i < n; i += 32) acc += (double)vr[i] * (double)wr[i];
+      acc = en_warp_sum(acc);
+      if (lane == 0) Mg[moff + e] = acc;
+    }
+    voff += (long)rp * n;
+    moff += rp * sp;
+  }
+  __syncthreads();
+  const double *M1 = Mg + mo[0], *M2 = Mg + mo[1], *M3 = Mg + mo[2];
+  const float* Ct = a.C + (a.core_by_q ? (long)(t % 3) * s1 * s2 * s3 : 0L);
+  double* Y1 = a.ws + ((long)t * 3 + q) * ((long)r1 * s3 * (s2 + r2));
+  double* Y2 = Y1 + (long)r1 * s2 * s3;
+  // 2. Y1[b3][b2][a1] = sum_b1 M1[a1][b1] C[b3][b2][b1]
+  for (long idx = threadIdx.x; idx < (long)s3 * s2 * r1; idx += blockDim.x) {
+    const int a1 = (int)(idx % r1);
+    const long bb = idx / r1;  // b3 s2 + b2
+    const float* crow = Ct + bb * s1;
+    double acc = 0.0;
+    for (int b1 = 0; b1 < s1; ++b1) acc += M1[a1 * s1 + b1] * (double)crow[b1];
+    Y1[idx] = acc;
+  }
+  __syncthreads();
+  // 3. Y2[b3][a2][a1] = sum_b2 M2[a2][b2] Y1[b3][b2][a1]
+  for (long idx = threadIdx.x; idx < (long)s3 * r2 * r1; idx += blockDim.x) {
+    const int a1 = (int)(idx % r1);
+    const int a2 = (int)((idx / r1) % r2);
+    const long b3 = idx / ((long)r1 * r2);
+    double acc = 0.0;
+    for (int b2 = 0; b2 < s2; ++b2) acc += M2[a2 * s2 + b2] * Y1[(b3 * s2 + b2) * r1 + a1];
+    Y2[idx] = acc;
+  }
+  __syncthreads();
+  // 4. X = sum_a G^(q)[a3][a2][a1] sum_b3 M3[a3][b3] Y2[b3][a2][a1]
+  const float* Gq = a.G + (long)q * r1 * r2 * r3;
+  double x = 0.0;
+  for (long idx = threadIdx.x; idx < (long)r3 * r2 * r1; idx += blockDim.x) {
+    const long a21 = idx % ((long)r2 * r1);
+    const int a3 = (int)(idx / ((long)r2 * r1));
+    double acc = 0.0;
+    for (int b3 = 0; b3 < s3; ++b3) acc += M3[a3 * s3 + b3] * Y2[(long)b3 * r2 * r1 + a21];
+    x += (double)Gq[idx] * acc;
+  }
+  x = en_warp_sum(x);
+  if (lane == 0) red[warp] = x;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double v = 0.0;
+    for (int i = 0; i < nw; ++i) v += red[i];
+    a.part[(long)t * 3 + q] = (a.w ? (double)a.w[t] : 1.0) * v;
+  }
+}
+
+// energy = scale * sum part[0..count) in a fixed order (one block)
+__global__ void __launch_bounds__(256) energy_sum_kernel(long count, const double* part, double scale, double* energy) {
+  __shared__ double red[32];
+  double acc = 0.0;
+  for (long i = threadIdx.x; i < count; i += blockDim.x) acc += part[i];
+  acc = en_warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double v = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) v += red[i];
+    *energy = scale * v;
+  }
+}
+
+static demag_status run_tucker_energy(demag_plan* P, EnTucker& a, double* energy, cudaStream_t st, const char* who) {
+  for (int p = 0; p < 3; ++p)
+    if (a.r[p] < 1 || a.r[p] > kEnMaxRank || a.s[p] < 1 || a.s[p] > kEnMaxRank)
+      return set_error(P, DEMAG_EINVAL, "%s: ranks must be in [1, %d]", who, kEnMaxRank);
+  for (int p = 0; p < 3; ++p) {
+    a.n[p] = P->n[p];
+    a.inv2h[p] = 0.5 / P->h[p];
+  }
+  const size_t smem = sizeof(double) * ((size_t)a.r[0] * a.s[0] + (size_t)a.r[1] * a.s[1] + (size_t)a.r[2] * a.s[2]);
+  if (smem > 48 * 1024) {
+    static unsigned long long done = 0;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (!(done & (1ull << (dev & 63)))) {
+      DEMAG_CUDA(P, cudaFuncSetAttribute(tucker_energy_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(sizeof(double) * 3 * kEnMaxRank * kEnMaxRank)));
+      done |= 1ull << (dev & 63);
+    }
+  }
+  const long blocks = (long)a.T * 3;
+  const long per = (long)a.r[0] * a.s[2] * (a.s[1] + a.r[1]);
+  void* mem = nullptr;
+  DEMAG_CUDA(P, cudaMallocAsync(&mem, sizeof(double) * (size_t)(blocks * per + blocks), st));
+  a.ws = static_cast<double*>(mem);
+  a.part = a.ws + blocks * per;
+  DEMAG_LAUNCH(P, kFamEnergy, st, tucker_energy_kernel<<<dim3(a.T, 3), 256, smem, st>>>(a));
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) {
+    const double vol = P->h[0] * P->h[1] * P->h[2];
+    DEMAG_LAUNCH(P, kFamEnergy, st, energy_sum_kernel<<<1, 256, 0, st>>>(blocks, a.part, 0.5 * vol, energy));
+    e = cudaGetLastError();
+  }
+  cudaFreeAsync(mem, st);
+  if (e != cudaSuccess) return cuda_error(P, e, who);
+  return DEMAG_OK;
+}
+
+}  // namespace demag
+
+using namespace demag;
+
+extern "C" demag_status demag_energy_tucker(demag_plan* P, const int r[3], const float* core, const float* V,
+                                            const float* out_w, const float* out_V, double* energy, void* stream) {
+  if (!P) return set_error(nullptr, DEMAG_EINVAL, "demag_energy_tucker: plan is NULL");
+  if (!r || !core || !V || !out_w || !out_V || !energy)
+    return set_error(P, DEMAG_EINVAL, "demag_energy_tucker: NULL pointer");
+  demag_status u = require_uniform(P, "demag_energy_tucker");  // uniform stencils and cell volume
+  if (u != DEMAG_OK) return u;
+  EnTucker a{};
+  for (int p = 0; p < 3; ++p) a.r[p] = a.s[p] = r[p];
+  a.G = core;
+  a.V = V;
+  a.C = core;
+  a.core_by_q = 1;
+  const long per_mode[3] = {(long)P->M * 3 * r[0] * P->n[0], (long)P->M * 3 * r[1] * P->n[1],
+                            (long)P->M * 3 * r[2] * P->n[2]};
+  a.W[0] = out_V;
+  a.W[1] = out_V + per_mode[0];
+  a.W[2] = out_V + per_mode[0] + per_mode[1];
+  a.w = out_w;
+  a.T = 3 * P->M;
+  return run_tucker_energy(P, a, energy, (cudaStream_t)stream, "demag_energy_tucker");
+}
+
+extern "C" demag_status demag_energy_tucker_phi(demag_plan* P, const int r[3], const float* core, const float* V,
+                                                const int rho[3], const float* phi_core, const float* phi_U,
+                                                double* energy, void* stream) {
+  if (!P) return set_error(nullptr, DEMAG_EINVAL, "demag_energy_tucker_phi: plan is NULL");
+  if (!r || !core || !V || !rho || !phi_core || !phi_U || !energy)
+    return set_error(P, DEMAG_EINVAL, "demag_energy_tucker_phi: NULL pointer");
+  demag_status u = require_uniform(P, "demag_energy_tucker_phi");
+  if (u != DEMAG_OK) return u;
+  EnTucker a{};
+  for (int p = 0; p < 3; ++p) {
+    a.r[p] = r[p];
+    a.s[p] = rho[p];
+  }
+  a.G = core;
+  a.V = V;
+  a.C = phi_core;
+  a.core_by_q = 0;
+  a.W[0] = phi_U;
+  a.W[1] = phi_U + (long)rho[0] * P->n[0];
+  a.W[2] = a.W[1] + (long)rho[1] * P->n[1];
+  a.w = nullptr;
+  a.T = 1;
+  return run_tucker_energy(P, a, energy, (cudaStream_t)stream, "demag_energy_tucker_phi");
+}

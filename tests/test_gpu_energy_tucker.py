@@ -1,0 +1,105 @@
+"""GPU parity of the Tucker-format demag energy (demag_energy_tucker, demag_energy_tucker_phi)
+against the oracle (oracle/energy.py: energy_tucker), the exact-collocation cube energy and the
+full-format GPU energy, through the C ABI."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import energy as oe
+from oracle import exact
+from gpu_helpers import dev
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def D():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1212_3509_gb300 as D
+    return D
+
+
+def _energy(D, P, n, ranks, core, V):
+    tot = sum(ranks[p] * n[p] for p in range(3))
+    w = torch.empty(P.M * 3, device="cuda")
+    oV = torch.empty(P.M * 3 * tot, device="cuda")
+    cd, Vd = dev(np.ascontiguousarray(core, dtype=np.float32).ravel()), dev(np.ascontiguousarray(V, dtype=np.float32))
+    D.demag_apply_tucker(P, ranks, Vd, w, oV)
+    E = torch.empty((), dtype=torch.float64, device="cuda")
+    D.demag_energy_tucker(P, ranks, cd, Vd, w, oV, E)
+    torch.cuda.synchronize()
+    return float(E.item()), (cd, Vd, w, oV)
+
+
+@pytest.mark.parametrize("n,ranks,R", [((12, 10, 8), (2, 3, 2), 21), ((17, 9, 23), (1, 4, 3), 41),
+                                       ((2, 5, 3), (1, 2, 2), 21)])
+def test_energy_tucker_vs_oracle(D, n, ranks, R):
+    h = (1.0 / max(n),) * 3
+    core, V = synth.tucker_inputs(n, ranks, 77)
+    P = D.demag_build_factors(n, h, R)
+    E, _ = _energy(D, P, n, ranks, core, V)
+    ref = oe.energy_tucker(core, V, n, ranks, h, R)
+    assert abs(E - ref) <= 1e-5 * abs(ref) + 1e-12, (E, ref)
+
+
+def test_energy_tucker_vs_full_format_gpu_energy(D):
+    n, ranks, R = (64, 48, 40), (3, 3, 3), 41
+    h = (1.0 / 64,) * 3
+    core, V = synth.tucker_inputs(n, ranks, 78)
+    P = D.demag_build_factors(n, h, R)
+    E, _ = _energy(D, P, n, ranks, core, V)
+    m = torch.from_numpy(oe.tucker_magnetization(core, V, n, ranks).astype(np.float32)).cuda().contiguous()
+    Ef = torch.empty((), dtype=torch.float64, device="cuda")
+    D.demag_energy(P, m, Ef, None, "fp32")
+    torch.cuda.synchronize()
+    assert abs(E - Ef.item()) <= 2e-5 * abs(Ef.item())
+
+
+@pytest.mark.parametrize("n", [32, 64])
+def test_uniform_cube_energy_is_the_exact_collocation_energy(D, n):
+    # the case of the energy study after Alg. 2: rank-1 Tucker m = z, R = 129
+    h = (1.0 / n,) * 3
+    core = np.zeros((3, 1, 1, 1), dtype=np.float32)
+    core[2] = 1.0
+    V = np.ones(3 * 3 * n, dtype=np.float32)
+    P = D.demag_build_factors((n, n, n), h, 129)
+    E, _ = _energy(D, P, (n, n, n), (1, 1, 1), core, V)
+    m = synth.uniform_m((n, n, n), 2).astype(np.float64)
+    ref = oe.energy(m, exact.uniform_box_potential((n, n, n), h, 2), h)
+    assert abs(E - ref) <= 1e-5 * ref, (E, ref)
+
+
+def test_energy_of_the_recompressed_potential(D):
+    # Alg. 2 end to end: compressed kernels, application, approximate summation, energy of the
+    # single Tucker potential; it agrees with the energy of the unsummed output within the tolerances
+    n, ranks, R = (24, 20, 16), (2, 2, 2), 21
+    h = (1.0 / 24,) * 3
+    core, V = synth.tucker_inputs(n, ranks, 79)
+    P = D.demag_build_factors(n, h, R)
+    E0, _ = _energy(D, P, n, ranks, core, V)
+    D.demag_compress_kernel(P, 1e-8)
+    rho = D.demag_compressed_ranks(P)
+    cd, Vd = dev(core.ravel()), dev(V)
+    out_V = torch.empty(sum(3 * rho[p] * ranks[p] * n[p] for p in range(3)), device="cuda")
+    D.demag_apply_tucker_compressed(P, 1, ranks, cd, Vd, None, out_V)
+    rk, C, Us, err = D.demag_recompress_tucker(P, ranks, cd, out_V, 1e-7)
+    E = torch.empty((), dtype=torch.float64, device="cuda")
+    D.demag_energy_tucker_phi(P, ranks, cd, Vd, rk, C.contiguous().view(-1),
+                              torch.cat([u.reshape(-1) for u in Us]), E)
+    torch.cuda.synchronize()
+    assert abs(E.item() - E0) <= 2e-5 * abs(E0), (E.item(), E0)
+    ref = oe.energy_tucker(core, V, n, ranks, h, R)
+    assert abs(E.item() - ref) <= 2e-5 * abs(ref)
+
+
+def test_rejects_bad_ranks(D):
+    n = (8, 8, 8)
+    P = D.demag_build_factors(n, (1 / 8,) * 3, 21)
+    core, V = synth.tucker_inputs(n, (1, 1, 1), 1)
+    E = torch.empty((), dtype=torch.float64, device="cuda")
+    with pytest.raises(RuntimeError, match="ranks"):
+        D.demag_energy_tucker_phi(P, (1, 1, 1), dev(core.ravel()), dev(V), (65, 1, 1),
+                                  torch.zeros(65, device="cuda"), torch.zeros(65 * 8 + 16, device="cuda"), E)
