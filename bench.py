@@ -447,6 +447,7 @@ def run_ours(args, world, rank, local):
 
     # ---------------- the same operator by one 3D FFT convolution (Eq. fft_pot, node-summed kernel)
     fft3d = run_fft3d(args, D, world, local, stream, P, m, phi, peaks, n3)
+    fibres = run_fibres(args, D, world, local, stream, P, m, phi, peaks, n3)
 
     # ---------------- the FFT path at 1024^3 (1.07 G cells; the cost does not depend on R)
     fft1024 = run_fft3d_1024(args, D, world, local, stream) if args.n == 256 else None
@@ -518,6 +519,8 @@ def run_ours(args, world, rank, local):
             forms[f]["rel_l2"] = sampled_err(field)
         if fft3d is not None:
             fft3d["rel_l2"] = sampled_err(fft3d.pop("_phi"))
+        if fibres is not None:
+            fibres["rel_l2"] = sampled_err(fibres.pop("_phi"))
         if nonuni is not None:
             from oracle import nonuniform as onu
             ref_nu = onu.apply_full_lines(m_host, nonuni.pop("_edges"), R, lines)
@@ -534,6 +537,9 @@ def run_ours(args, world, rank, local):
     if fft3d is not None:
         fft3d.pop("_phi", None)
         result["full_fft3d"] = fft3d
+    if fibres is not None:
+        fibres.pop("_phi", None)
+        result["full_fibres"] = fibres
     if nonuni is not None:
         nonuni.pop("_phi", None)
         nonuni.pop("_edges", None)
@@ -698,6 +704,41 @@ def run_fft3d(args, D, world, local, stream, P, m, phi, peaks, n3):
                          "unit": "GB/s", "frac": ach / hbm,
                          "top_pass": {"pass": top + 1, "ms": per[top], "achieved": pb[top] / (per[top] * 1e-3) / 1e9,
                                       "frac": pb[top] / (per[top] * 1e-3) / 1e9 / hbm},
+                         "traffic": None},
+            "clocks": clk.summary(), "_phi": out}
+
+
+def run_fibres(args, D, world, local, stream, P, m, phi, peaks, n3):
+    """demag_apply_full_fibres on the headline grid: per-fibre 1D Toeplitz FFTs along each axis
+    (all nodes along axis 1, node by node along axes 2 and 3), transposes between, weighted sum."""
+    import torch
+    out = torch.empty_like(phi)
+    fn = lambda: D.demag_apply_full_fibres(P, m, out)  # noqa: E731
+    try:
+        fn()
+    except D.DemagError:
+        return None
+    for _ in range(args.warmup):
+        fn()
+    torch.cuda.synchronize()
+    barrier(world)
+    with ClockSampler(local) as clk:
+        ms = time_region(fn, max(3, args.steps), stream)
+    ms_max = max_over_ranks(ms, world)
+    N = n3[0] * n3[1] * n3[2]
+    M = P.M
+    # m in, 3M fields out of each of the three Toeplitz stages and the two transposes (read + write
+    # between), the sum reads 3M fields and writes phi
+    bytes_app = 4.0 * (4 * N + 30 * M * N)
+    hbm = peaks.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"])
+    ach = bytes_app / (ms_max * 1e-3) / 1e9
+    launches = 6
+    return {"value": whole_job_rate(1, ms_max, world), "unit": "apps/s", "ms_per_app": ms_max,
+            "work": "Toeplitz FFTs of the axis-1 fibres for all M nodes, then of the axis-2 and axis-3 fibres "
+                    "of each (node, component) volume; two batched transposes; weighted sum over (k, q)",
+            "launches_per_app": launches,
+            "roofline": {"kernel": "per-fibre chain (all six launches)", "bound": "hbm", "achieved": ach,
+                         "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "algorithmic_bytes_per_app": bytes_app,
                          "traffic": None},
             "clocks": clk.summary(), "_phi": out}
 

@@ -167,6 +167,18 @@ demag_status demag_apply_full(demag_plan* plan, const float* m, float* phi,
  * DEMAG_EUNSUPPORTED when some n_p > 1024. */
 demag_status demag_apply_full_fft(demag_plan* plan, const float* m, float* phi, void* stream);
 
+/* The same phi by per-fibre 1D Toeplitz FFTs (Sec. 4.2 applied to the mode
+ * products of Eq. kron_operator, O(R n^3 log n)): the axis-1 fibres of each
+ * component through the circulant FFT kernel for all M nodes at once, then
+ * the axis-2 and axis-3 fibres of every (node, component) volume with that
+ * node's factor, batched transposes between the stages, and the weighted sum
+ * over nodes and components.  FP32.  m: float [3][n3][n2][n1], phi: float
+ * [n3][n2][n1] (overwritten), device pointers, not overlapping.  The first
+ * call allocates two work volumes of 3 M n1 n2 n3 floats each in the plan
+ * (make it before any stream capture).  Asynchronous on `stream`.
+ * DEMAG_EUNSUPPORTED when some n_p exceeds the FFT path's length. */
+demag_status demag_apply_full_fibres(demag_plan* plan, const float* m, float* phi, void* stream);
+
 /* The stray field h_d = -grad phi of demag_stray_field_exact (analytic
  * derivative factors, h_d[p] = sum_q K_pq * m^(q)) by one 3D FFT convolution:
  * the six node-summed derivative kernels K_pq (real, K_pq = K_qp) are built

@@ -52,6 +52,7 @@ _SIGS = {
     "demag_symbols_size": (_sz, [_vp]),
     "demag_apply_full": (_i, [_vp, _vp, _vp, _i, _vp]),
     "demag_apply_full_fft": (_i, [_vp, _vp, _vp, _vp]),
+    "demag_apply_full_fibres": (_i, [_vp, _vp, _vp, _vp]),
     "demag_stray_field_fft": (_i, [_vp, _vp, _vp, _vp]),
     "demag_energy_field_fft": (_i, [_vp, _vp, _vp, _vp, _vp]),
     "demag_build_factors_nonuniform": (_i, [ctypes.POINTER(GridEdgesDesc), ctypes.POINTER(_vp), _vp]),
@@ -321,6 +322,12 @@ def demag_apply_full_fft(plan: Plan, m, phi, stream=None):
     import torch
     _check(lib.demag_apply_full_fft(plan.ptr, _ptr(m, 3 * plan.N, torch.float32, "m"),
                                     _ptr(phi, plan.N, torch.float32, "phi"), _stream(stream)), plan.ptr)
+
+
+def demag_apply_full_fibres(plan: Plan, m, phi, stream=None):
+    import torch
+    _check(lib.demag_apply_full_fibres(plan.ptr, _ptr(m, 3 * plan.N, torch.float32, "m"),
+                                       _ptr(phi, plan.N, torch.float32, "phi"), _stream(stream)), plan.ptr)
 
 
 def demag_stray_field_fft(plan: Plan, m, hd, stream=None):

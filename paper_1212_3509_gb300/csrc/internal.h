@@ -75,6 +75,8 @@ struct demag_plan {
   void* cmp = nullptr;
   // energy / gradient scratch: phi, D^T m (1 field each) and P^T D^T m (3 fields)
   float* ews = nullptr;
+  // per-fibre full format: two work volumes of 3M fields each
+  float* fib_ws = nullptr;
 
   // autotuning: when on, launch shapes not yet tuned are timed on first use
   bool autotune = false;

@@ -254,6 +254,8 @@ static void free_plan_buffers(demag_plan* P) {
   cudaFree(P->T32d);
   cudaFree(P->T64d);
   cudaFree(P->gend);
+  cudaFree(P->fib_ws);
+  P->fib_ws = nullptr;
   for (auto& w : P->ws) cudaFree(w.base);
   cudaFree(P->dev_status);
   for (auto e : P->prof_pool) cudaEventDestroy(e);

@@ -29,6 +29,7 @@
 //                        keep) are computed and stored to HBM.
 // Twiddles: one value per item from a two-level shared table
 // (W_L^m = T1[m >> 7] * T0[m & 127]) and its powers by a product tree.
+#include <climits>
 #include <type_traits>
 
 #include "internal.h"
@@ -60,6 +61,7 @@ struct ToepLaunch {
   int kgroup;      // nodes per block
   int pairstride;  // Lmax/2
   int nsets;       // symbol sets per node: 2 (types E, F) or 3 (components of a compressed kernel)
+  int diag;        // 1: column (b, q, l) applies node b only and writes it as node 0 of its item
   const float2* sympair;  // [M][nsets][3][pairstride]: (s_f, s_{N-f}); set = type, or q when nsets = 3
 };
 
@@ -225,8 +227,9 @@ __global__ void __launch_bounds__(256, ToepCfg<LOGN>::minblocks)
 
   const int axis = A.axis;
   const int type = (axis == q) ? 1 : 0;  // F on the axis of the component
-  const int k0 = blockIdx.y * a.kgroup;
-  const int k1 = min(min(a.M, A.kmax), k0 + a.kgroup);
+  const int k0 = a.diag ? b : blockIdx.y * a.kgroup;
+  const int k1 = a.diag ? b + 1 : min(min(a.M, A.kmax), k0 + a.kgroup);
+  const int kofs = a.diag ? k0 : 0;  // output node index = k - kofs
   float* outbase = A.out + b * A.out_bstride + (long)l * n;
   // paired stores need an even length and an 8-byte aligned column start
   // (every (k, q) offset is a multiple of n, so one check per column)
@@ -274,7 +277,7 @@ __global__ void __launch_bounds__(256, ToepCfg<LOGN>::minblocks)
             for (int r = 0; r < R1; ++r) {
               const int i = j + r * items1;
               if (active && 2 * i < n) {
-                float* o = outbase + (long)(k * 3 + q) * rcols * n;
+                float* o = outbase + (long)((k - kofs) * 3 + q) * rcols * n;
                 o[2 * i] = v[r].x;
                 if (2 * i + 1 < n) o[2 * i + 1] = v[r].y;
               }
@@ -320,11 +323,11 @@ __global__ void __launch_bounds__(256, ToepCfg<LOGN>::minblocks)
             idft16_first_half(v);
             if (active && full_vec) {
               // every kept output exists: 8-byte stores, no bounds tests
-              float2* o = reinterpret_cast<float2*>(outbase + (long)(k * 3 + q) * rcols * n);
+              float2* o = reinterpret_cast<float2*>(outbase + (long)((k - kofs) * 3 + q) * rcols * n);
   #pragma unroll
               for (int r = 0; r < 8; ++r) o[j + r * items] = v[r];
             } else if (active) {
-              float* o = outbase + (long)(k * 3 + q) * rcols * n;
+              float* o = outbase + (long)((k - kofs) * 3 + q) * rcols * n;
   #pragma unroll
               for (int r = 0; r < 8; ++r) {
                 const int i = j + r * items;
@@ -484,7 +487,7 @@ static cudaError_t pick_kgroup(demag_plan* P, int logn, ToepLaunch& a, int gx, c
 // Toeplitz matvecs of the given axes: axes that share an FFT length run in
 // one launch (normally all three), each as its own range of blocks.
 static demag_status run_axes(demag_plan* P, ToepAxis* axes, int count, const char* what, cudaStream_t st,
-                             const float2* sympair = nullptr, int nsets = 2) {
+                             const float2* sympair = nullptr, int nsets = 2, int diag = 0) {
   bool done[3] = {false, false, false};
   for (int i = 0; i < count; ++i) {
     if (done[i]) continue;
@@ -510,7 +513,12 @@ static demag_status run_axes(demag_plan* P, ToepAxis* axes, int count, const cha
       done[j] = true;
     }
     a.bx0[a.naxes] = gx;
-    cudaError_t e = pick_kgroup(P, logn, a, gx, st);
+    a.diag = diag;
+    cudaError_t e = cudaSuccess;
+    if (diag)
+      a.kgroup = a.M;  // one node per column: grid.y = 1
+    else
+      e = pick_kgroup(P, logn, a, gx, st);
     if (e == cudaSuccess) e = launch_logn(P, logn, a, gx, st);
     if (e != cudaSuccess) return cuda_error(P, e, what);
   }
@@ -537,9 +545,150 @@ static demag_status launch_weights(demag_plan* P, int batch, int rq, const float
   return DEMAG_OK;
 }
 
+// ---------------------------------------------------------------- full format by per-fibre Toeplitz FFTs
+//
+// phi = c s sum_k omega_k sum_q T_{k,q,3} x_3 T_{k,q,2} x_2 T_{k,q,1} x_1 m^(q) (Eq. kron_operator) with
+// every mode product done as 1D Toeplitz matvecs of the fibres through the circulant FFT kernel
+// (Sec. 4.2): axis 1 for all nodes at once (one forward FFT per fibre), then axes 2 and 3 per
+// (node, component) volume (diagonal mode), with batched transposes between so that every FFT
+// reads contiguous fibres, and a weighted sum over (k, q) that transposes back.
+
+// out[b][c][r] = in[b][r][c]: 32 x 32 tiles through shared memory, grid-stride over all tiles
+__global__ void __launch_bounds__(256) transpose_batched_kernel(long B, int R, int C, const float* in, float* out) {
+  __shared__ float tile[32][33];
+  const int tr = (R + 31) / 32, tc = (C + 31) / 32;
+  const long total = B * tr * tc;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (long t = blockIdx.x; t < total; t += gridDim.x) {
+    const long b = t / ((long)tr * tc);
+    const int rem = (int)(t - b * tr * tc);
+    const int r0 = (rem / tc) * 32, c0 = (rem % tc) * 32;
+    const float* src = in + b * (long)R * C;
+    float* dst = out + b * (long)R * C;
+    for (int i = ty; i < 32; i += 8) {
+      const int r = r0 + i, c = c0 + tx;
+      tile[i][tx] = (r < R && c < C) ? src[(long)r * C + c] : 0.f;
+    }
+    __syncthreads();
+    for (int i = ty; i < 32; i += 8) {
+      const int c = c0 + i, r = r0 + tx;
+      if (r < R && c < C) dst[(long)c * R + r] = tile[tx][i];
+    }
+    __syncthreads();
+  }
+}
+
+// phi[i3][i2][i1] = sum_{k, q} scale[k] Y[k][q][i1][i2][i3]: per i2 a 32 x 32 (i1, i3) tile,
+// read along i3 and written along i1
+__global__ void __launch_bounds__(256) fibre_sum_kernel(int M, int n1, int n2, int n3, const double* scale,
+                                                        const float* Y, float* phi) {
+  __shared__ float tile[32][33];
+  const int t1 = (n1 + 31) / 32, t3 = (n3 + 31) / 32;
+  const long total = (long)n2 * t1 * t3;
+  const long N = (long)n1 * n2 * n3;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (long t = blockIdx.x; t < total; t += gridDim.x) {
+    const int i2 = (int)(t / ((long)t1 * t3));
+    const int rem = (int)(t - (long)i2 * t1 * t3);
+    const int a0 = (rem / t3) * 32, c0 = (rem % t3) * 32;  // i1 and i3 tile origins
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int k = 0; k < M; ++k) {
+      const float w = (float)scale[k];
+      for (int q = 0; q < 3; ++q) {
+        const float* src = Y + ((long)k * 3 + q) * N;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int i1 = a0 + ty + 8 * u, i3 = c0 + tx;
+          if (i1 < n1 && i3 < n3) acc[u] = fmaf(w, src[((long)i1 * n2 + i2) * n3 + i3], acc[u]);
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) tile[ty + 8 * u][tx] = acc[u];
+    __syncthreads();
+    for (int i = ty; i < 32; i += 8) {
+      const int i3 = c0 + i, i1 = a0 + tx;
+      if (i1 < n1 && i3 < n3) phi[((long)i3 * n2 + i2) * n1 + i1] = tile[tx][i];
+    }
+    __syncthreads();
+  }
+}
+
+static int grid_for_tiles(long tiles) { return (int)(tiles < 152L * 16 ? (tiles < 1 ? 1 : tiles) : 152L * 16); }
+
 }  // namespace demag
 
 using namespace demag;
+
+extern "C" demag_status demag_apply_full_fibres(demag_plan* P, const float* m, float* phi, void* stream) {
+  demag_status s = check_fft_plan(P, "demag_apply_full_fibres");
+  if (s != DEMAG_OK) return s;
+  if (!m || !phi) return set_error(P, DEMAG_EINVAL, "demag_apply_full_fibres: NULL pointer");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int n1 = P->n[0], n2 = P->n[1], n3 = P->n[2], M = P->M;
+  const long N = (long)n1 * n2 * n3, vol = 3L * M * N;
+  if ((long)M * 3 * n1 * n2 > INT_MAX || (long)M * 3 * n3 * n1 > INT_MAX || 3L * n2 * n3 > INT_MAX)
+    return set_error(P, DEMAG_EUNSUPPORTED, "demag_apply_full_fibres: too many fibres for one launch");
+  if (!P->fib_ws) DEMAG_CUDA(P, cudaMalloc(&P->fib_ws, sizeof(float) * 2 * (size_t)vol));
+  float* Y = P->fib_ws;
+  float* Z = Y + vol;
+  // axis 1, every node: Y[k][q][i3][i2][i1]
+  ToepAxis a{};
+  a.axis = 0;
+  a.rcols = n2 * n3;
+  a.ncols = 3 * a.rcols;
+  a.in = m;
+  a.in_qstride = N;
+  a.out = Y;
+  s = run_axes(P, &a, 1, "toeplitz_fft_kernel (fibres, axis 1)", st);
+  if (s != DEMAG_OK) return s;
+  // Z[k][q][i3][i1][i2]
+  {
+    const long B = 3L * M * n3;
+    const long tiles = B * ((n2 + 31) / 32) * ((n1 + 31) / 32);
+    DEMAG_LAUNCH(P, kFamMisc, st, transpose_batched_kernel<<<grid_for_tiles(tiles), 256, 0, st>>>(B, n2, n1, Y, Z));
+    DEMAG_LAUNCHED(P, "transpose_batched_kernel");
+  }
+  // axis 2, node k on volume k: Y[k][q][i3][i1][i2]
+  ToepAxis b{};
+  b.axis = 1;
+  b.rcols = n3 * n1;
+  b.ncols = M * 3 * b.rcols;
+  b.in = Z;
+  b.in_bstride = 3 * N;
+  b.in_qstride = N;
+  b.out = Y;
+  b.out_bstride = 3 * N;
+  s = run_axes(P, &b, 1, "toeplitz_fft_kernel (fibres, axis 2)", st, nullptr, 2, 1);
+  if (s != DEMAG_OK) return s;
+  // Z[k][q][i1][i2][i3]
+  {
+    const long B = 3L * M;
+    const long tiles = B * ((n3 + 31) / 32) * (((long)n1 * n2 + 31) / 32);
+    DEMAG_LAUNCH(P, kFamMisc, st,
+                 transpose_batched_kernel<<<grid_for_tiles(tiles), 256, 0, st>>>(B, n3, n1 * n2, Y, Z));
+    DEMAG_LAUNCHED(P, "transpose_batched_kernel");
+  }
+  // axis 3, node k on volume k: Y[k][q][i1][i2][i3]
+  ToepAxis c{};
+  c.axis = 2;
+  c.rcols = n1 * n2;
+  c.ncols = M * 3 * c.rcols;
+  c.in = Z;
+  c.in_bstride = 3 * N;
+  c.in_qstride = N;
+  c.out = Y;
+  c.out_bstride = 3 * N;
+  s = run_axes(P, &c, 1, "toeplitz_fft_kernel (fibres, axis 3)", st, nullptr, 2, 1);
+  if (s != DEMAG_OK) return s;
+  {
+    const long tiles = (long)n2 * ((n1 + 31) / 32) * ((n3 + 31) / 32);
+    DEMAG_LAUNCH(P, kFamMisc, st,
+                 fibre_sum_kernel<<<grid_for_tiles(tiles), 256, 0, st>>>(M, n1, n2, n3, P->scale, Y, phi));
+    DEMAG_LAUNCHED(P, "fibre_sum_kernel");
+  }
+  return DEMAG_OK;
+}
 
 extern "C" demag_status demag_apply_cp_batched(demag_plan* P, int batch, int r, const float* lambda,
                                                const float* U, float* out_w, float* out_U, void* stream) {
