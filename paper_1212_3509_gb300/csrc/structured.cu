@@ -68,6 +68,8 @@ struct ToepLaunch {
 template <int LOGN> struct ToepCfg {
   static constexpr int N = 1 << LOGN;
   static constexpr int L = 2 * N;
+  // at least one warp per column: the node loop is specialised on the factor type of the column
+  // and holds block barriers, so every thread of a warp must take the same specialisation
   static constexpr int TG = (N / 16) < 32 ? 32 : ((N / 16) > 256 ? 256 : (N / 16));
   static constexpr int G = 256 / TG;
   static constexpr int NP = N + N / 16;            // padded buffer length
