@@ -9,7 +9,7 @@ factor alone and replaces it by f(b_d) - f(a_d) (a_d, b_d as in generators):
     f(x) = exp(-tau^2 x^2)       ->  dE[d] = exp(-tau^2 b^2) - exp(-tau^2 a^2) = -2 tau^2 F[d]
     f(x) = x exp(-tau^2 x^2)     ->  dF[d] = b exp(-tau^2 b^2) - a exp(-tau^2 a^2)
 
-(the relations the survey's next-steps list quotes for the analytic stray
+(the derivative relations of the cell integrals behind the analytic stray
 field).  dE is odd and dF even in d.  With the domain scaled by s (Sec. 3.4),
 d/dxi_phys = (1/s) d/dxi_scaled, so the field carries c omega_k without the
 factor s of phi.  dF is evaluated as exp(-tau^2 a^2) (h + b expm1(-2 |d| tau^2 h^2))
