@@ -52,7 +52,7 @@ typedef enum {
   DEMAG_ENOMEM = 2,      /* device allocation failed */
   DEMAG_ECUDA = 3,       /* a CUDA runtime call or launch failed */
   DEMAG_ETIMEOUT = 4,    /* a bounded device-side wait gave up */
-  DEMAG_EUNSUPPORTED = 5 /* valid request outside this build's limits */
+  DEMAG_EUNSUPPORTED = 5 /* valid request outside the library's limits */
 } demag_status;
 
 /* Arithmetic of the full-format mode products (Sec. 2.2 Eq. modemul).
