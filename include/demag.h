@@ -347,6 +347,28 @@ demag_status demag_apply_tt_batched(demag_plan* plan, int batch, const int r[2],
                                     const float* G2, const float* G3, float* out_w, float* oG1,
                                     float* oG2, float* oG3, void* stream);
 
+/* Tensor-train arithmetic of App. C, three components per call, layouts as
+ * demag_apply_tt (G1 [3][r1][n1], G2 [3][r1 r2][n2] with row a1 r2 + a2,
+ * G3 [3][r2][n3]); FP32, asynchronous, no allocation.
+ * demag_tucker_to_tt: the Tucker magnetization (core float [3][r3][r2][r1],
+ * V blocks (q, p) [r_p][n_p]) as trains of ranks (r1, r3), the second factor
+ * multiplied into the core (the remark after Eq. tt_3d_2): G1 = V^(q,1),
+ * G3 = V^(q,3), G2(a1, i2, a3) = sum_a2 G^(q)[a3][a2][a1] V^(q,2)[a2][i2].
+ * demag_cp_to_tt: the CP magnetization (lambda float [3][r], U blocks (q, p)
+ * [r][n_p]) as trains of ranks (r, r) with a diagonal middle core
+ * G2(a1, i2, a2) = [a1 = a2] lambda_a1 U^(q,2)[a1][i2].
+ * demag_tt_hadamard: C^(q) = A^(q) .* B^(q) element-wise as trains of ranks
+ * (ra1 rb1, ra2 rb2) (the cores multiply as Kronecker products of their rank
+ * indices): C1 row a rb1 + b, C2 row (a1 rb1 + b1)(ra2 rb2) + (a2 rb2 + b2),
+ * C3 row a2 rb2 + b2. */
+demag_status demag_tucker_to_tt(demag_plan* plan, const int r[3], const float* core, const float* V,
+                                float* G1, float* G2, float* G3, void* stream);
+demag_status demag_cp_to_tt(demag_plan* plan, int r, const float* lambda, const float* U, float* G1,
+                            float* G2, float* G3, void* stream);
+demag_status demag_tt_hadamard(demag_plan* plan, const int ra[2], const float* A1, const float* A2,
+                               const float* A3, const int rb[2], const float* B1, const float* B2,
+                               const float* B3, float* C1, float* C2, float* C3, void* stream);
+
 /* TT rounding of the potential (App. C: the 3M output trains of
  * demag_apply_tt summed and rounded to one train, the recompression that
  * section cites) with tolerance tol: phi_hat = [G1, G2, G3] with

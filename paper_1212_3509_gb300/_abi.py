@@ -62,6 +62,10 @@ _SIGS = {
     "demag_apply_tucker_compressed": (_i, [_vp, _i, ctypes.POINTER(ctypes.c_int), _vp, _vp, _vp, _vp, _vp]),
     "demag_recompress_tucker": (_i, [_vp, ctypes.POINTER(ctypes.c_int), _vp, _vp, ctypes.c_double,
                                      ctypes.POINTER(ctypes.c_int), _vp, _vp, ctypes.POINTER(ctypes.c_double), _vp]),
+    "demag_tucker_to_tt": (_i, [_vp, ctypes.POINTER(_i), _vp, _vp, _vp, _vp, _vp, _vp]),
+    "demag_cp_to_tt": (_i, [_vp, _i, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "demag_tt_hadamard": (_i, [_vp, ctypes.POINTER(_i), _vp, _vp, _vp, ctypes.POINTER(_i), _vp, _vp, _vp, _vp, _vp,
+                               _vp, _vp]),
     "demag_round_tt": (_i, [_vp, ctypes.POINTER(ctypes.c_int), _vp, _vp, _vp, _vp, ctypes.c_double,
                             ctypes.POINTER(ctypes.c_int), _vp, _vp, _vp, ctypes.POINTER(ctypes.c_double), _vp]),
     "demag_apply_full_batched": (_i, [ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i, _i, _vp]),
@@ -228,6 +232,47 @@ def demag_apply_tucker_compressed(plan: Plan, batch: int, r, core, V, out_core, 
                                              _ptr(V, batch * 3 * qs, f32, "V"),
                                              _ptr(out_core, batch * 3 * nout, f32, "out_core"),
                                              _ptr(out_V, batch * os_, f32, "out_V"), _stream(stream)), plan.ptr)
+
+
+def _tt_sizes(plan: Plan, r1: int, r2: int):
+    return 3 * r1 * plan.n[0], 3 * r1 * r2 * plan.n[1], 3 * r2 * plan.n[2]
+
+
+def demag_tucker_to_tt(plan: Plan, ranks, core, V, G1, G2, G3, stream=None):
+    """Tucker magnetization -> trains of ranks (r1, r3) (App. C)."""
+    import torch
+    r = (_i * 3)(*[int(v) for v in ranks])
+    f32 = torch.float32
+    s1, s2, s3 = _tt_sizes(plan, int(ranks[0]), int(ranks[2]))
+    tot = sum(int(ranks[p]) * plan.n[p] for p in range(3))
+    _check(lib.demag_tucker_to_tt(plan.ptr, r, _ptr(core, 3 * int(ranks[0]) * int(ranks[1]) * int(ranks[2]), f32,
+                                                    "core"),
+                                  _ptr(V, 3 * tot, f32, "V"), _ptr(G1, s1, f32, "G1"), _ptr(G2, s2, f32, "G2"),
+                                  _ptr(G3, s3, f32, "G3"), _stream(stream)), plan.ptr)
+
+
+def demag_cp_to_tt(plan: Plan, r: int, lam, U, G1, G2, G3, stream=None):
+    """CP magnetization -> trains of ranks (r, r) with a diagonal middle core (App. C)."""
+    import torch
+    f32 = torch.float32
+    s1, s2, s3 = _tt_sizes(plan, int(r), int(r))
+    _check(lib.demag_cp_to_tt(plan.ptr, int(r), _ptr(lam, 3 * int(r), f32, "lambda"),
+                              _ptr(U, 3 * int(r) * sum(plan.n), f32, "U"), _ptr(G1, s1, f32, "G1"),
+                              _ptr(G2, s2, f32, "G2"), _ptr(G3, s3, f32, "G3"), _stream(stream)), plan.ptr)
+
+
+def demag_tt_hadamard(plan: Plan, ra, A, rb, B, C, stream=None):
+    """C = A .* B per component; A, B, C are (G1, G2, G3) triples; C has ranks (ra1 rb1, ra2 rb2)."""
+    import torch
+    f32 = torch.float32
+    a = (_i * 2)(int(ra[0]), int(ra[1]))
+    b = (_i * 2)(int(rb[0]), int(rb[1]))
+    sa = _tt_sizes(plan, int(ra[0]), int(ra[1]))
+    sb = _tt_sizes(plan, int(rb[0]), int(rb[1]))
+    sc = _tt_sizes(plan, int(ra[0]) * int(rb[0]), int(ra[1]) * int(rb[1]))
+    _check(lib.demag_tt_hadamard(plan.ptr, a, *[_ptr(A[i], sa[i], f32, f"A{i + 1}") for i in range(3)], b,
+                                 *[_ptr(B[i], sb[i], f32, f"B{i + 1}") for i in range(3)],
+                                 *[_ptr(C[i], sc[i], f32, f"C{i + 1}") for i in range(3)], _stream(stream)), plan.ptr)
 
 
 def demag_round_tt(plan: Plan, r, w, o1, o2, o3, tol: float, stream=None):
