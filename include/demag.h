@@ -29,7 +29,9 @@
  *    library never frees or retains it after the call returns.  The plan owns
  *    its generators, symbols, dense factor matrices and workspace.
  *  - Streams: `stream` is a cudaStream_t (NULL = legacy default stream).  All
- *    compute entry points are asynchronous on that stream.
+ *    compute entry points are asynchronous on that stream, except the
+ *    host-driven ones documented as synchronous (kernel compression,
+ *    recompression, TT rounding).
  *  - Errors: arguments are validated before any launch; a rejected call
  *    returns DEMAG_EINVAL (or DEMAG_EUNSUPPORTED) and launches nothing.  A
  *    failed launch returns DEMAG_ECUDA.  The message of the last error of a
