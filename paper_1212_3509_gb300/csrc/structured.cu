@@ -68,9 +68,11 @@ struct ToepLaunch {
 template <int LOGN> struct ToepCfg {
   static constexpr int N = 1 << LOGN;
   static constexpr int L = 2 * N;
-  // at least one warp per column: the node loop is specialised on the factor type of the column
-  // and holds block barriers, so every thread of a warp must take the same specialisation
-  static constexpr int TG = (N / 16) < 32 ? 32 : ((N / 16) > 256 ? 256 : (N / 16));
+  // one thread per item of a radix-16 pass, at least 16.  With TG >= 32 the node loop is
+  // specialised on the factor type of the column; a group narrower than a warp shares its warp
+  // with columns of the other type, so there the type is a runtime value and every thread runs
+  // the same code through the block barriers
+  static constexpr int TG = (N / 16) < 16 ? 16 : ((N / 16) > 256 ? 256 : (N / 16));
   static constexpr int G = 256 / TG;
   static constexpr int NP = N + N / 16;            // padded buffer length
   static constexpr int T0 = L < 128 ? L : 128;     // fine twiddle table
@@ -250,9 +252,10 @@ __global__ void __launch_bounds__(256, ToepCfg<LOGN>::minblocks)
   }
   // the node loop, specialised on the factor type (E or F), which is fixed per column
   auto node_loop = [&](auto type_tag) {
-    constexpr int TYPE = decltype(type_tag)::value;
+    constexpr int TYPE = decltype(type_tag)::value;  // 0 E, 1 F, -1 taken from the column at run time
+    const int ftype = TYPE < 0 ? type : TYPE;
     for (int k = k0; k < k1; ++k) {
-      const float2* sp = a.sympair + ((long)(k * a.nsets + (a.nsets == 3 ? q : TYPE)) * 3 + axis) * a.pairstride;
+      const float2* sp = a.sympair + ((long)(k * a.nsets + (a.nsets == 3 ? q : ftype)) * 3 + axis) * a.pairstride;
       // 3. first pass in registers on the bins j + r N/R1 of item j
       constexpr int items1 = N / R1;
       constexpr int ipt1 = (items1 + TG - 1) / TG;
@@ -267,10 +270,10 @@ __global__ void __launch_bounds__(256, ToepCfg<LOGN>::minblocks)
             const float2 s2 = __ldg(sp + f);
             const float4 pq = PQ[f];  // (P, Q)
             // E: s_f P + s_c Q ;  F: i (s_f P - s_c Q)
-            const float sc = TYPE ? -s2.y : s2.y;
+            const float sc = ftype ? -s2.y : s2.y;
             const float zx = fmaf(s2.x, pq.x, sc * pq.z);
             const float zy = fmaf(s2.x, pq.y, sc * pq.w);
-            v[r] = TYPE ? make_float2(-zy, zx) : make_float2(zx, zy);
+            v[r] = ftype ? make_float2(-zy, zx) : make_float2(zx, zy);
           }
           dft_reg<R1, true>(v);
           if constexpr (NPASS <= 1) {
@@ -351,7 +354,9 @@ __global__ void __launch_bounds__(256, ToepCfg<LOGN>::minblocks)
       __syncthreads();
     }
   };
-  if (type)
+  if constexpr (TG < 32)
+    node_loop(std::integral_constant<int, -1>{});
+  else if (type)
     node_loop(std::integral_constant<int, 1>{});
   else
     node_loop(std::integral_constant<int, 0>{});
@@ -403,7 +408,7 @@ static int ilog2i(int v) {
 
 static int groups_per_block(int logn) {
   int N = 1 << logn;
-  int TG = N / 16 < 32 ? 32 : (N / 16 > 256 ? 256 : N / 16);
+  int TG = N / 16 < 16 ? 16 : (N / 16 > 256 ? 256 : N / 16);
   return 256 / TG;
 }
 
