@@ -872,6 +872,7 @@ def run_c4(args, D, world, local, stream, peaks):
     out["tucker_compressed"] = run_tucker_compressed(args, D, world, local, stream, P, n3, rt, B, V, tw, tV, hbm)
     out["tt_rounded"] = run_tt_round(D, P, n3)
     out["tucker_energy"] = run_tucker_energy(D, P, n3, rt, tucker_in, stream)
+    out["tt_energy"] = run_tt_energy(D, P, n3, rr, tt_in, stream)
     out["_tucker_in"] = tucker_in
     out["_tucker_out"] = tV[:M * 3 * tot * n]
     out["_tt_in"] = tt_in
@@ -902,6 +903,27 @@ def run_tucker_energy(D, P, n3, rt, tucker_in, stream):
     return {"value": 1e3 / ms, "unit": "energy evals/s", "ms_per_eval": ms, "energy": float(E.item()),
             "work": "Tucker application (3M terms) and the energy from factor Grams and core contractions; "
                     "the 1024^3 magnetization and potential are never formed"}
+
+
+def run_tt_energy(D, P, n3, rr, tt_in, stream):
+    """Demag energy of one rank-(8, 8) TT magnetization on the 1024^3 grid without forming a full
+    tensor: demag_apply_tt + demag_energy_tt, CUDA events over 10 calls."""
+    import torch
+    n, M = n3[0], P.M
+    G = [torch.from_numpy(x.ravel()).cuda() for x in tt_in]
+    w = torch.empty(M * 3, device="cuda")
+    o = [torch.empty(M * 3 * s, device="cuda") for s in (rr[0] * n, rr[0] * rr[1] * n, rr[1] * n)]
+    E = torch.empty((), dtype=torch.float64, device="cuda")
+
+    def fn():
+        D.demag_apply_tt(P, rr, G[0], G[1], G[2], w, *o)
+        D.demag_energy_tt(P, rr, G[0], G[1], G[2], w, *o, E)
+    for _ in range(3):
+        fn()
+    torch.cuda.synchronize()
+    ms = time_region(fn, 10, stream)
+    return {"value": 1e3 / ms, "unit": "energy evals/s", "ms_per_eval": ms, "energy": float(E.item()),
+            "work": "TT application (3M trains) and the energy from the Grams of first, middle and last cores"}
 
 
 def run_tt_round(D, P, n3, tol=1e-5, rr=(8, 8)):

@@ -407,6 +407,15 @@ demag_status demag_round_tt(demag_plan* plan, const int r[2], const float* w, co
 demag_status demag_energy_tucker(demag_plan* plan, const int r[3], const float* core, const float* V,
                                  const float* out_w, const float* out_V, double* energy, void* stream);
 
+/* The same energy for a TT magnetization (Eq. tt_3d_1; G1 float [3][r1][n1],
+ * G2 float [3][r1 r2][n2], G3 float [3][r2][n3]) from the output of
+ * demag_apply_tt for it (out_w float [M][3], oG1, oG2, oG3): the inner
+ * products of trains through the Grams of their first, middle and last cores.
+ * r1, r2 in [1, 64] with r1 r2 <= 128; energy: one double on the device. */
+demag_status demag_energy_tt(demag_plan* plan, const int r[2], const float* G1, const float* G2,
+                             const float* G3, const float* out_w, const float* oG1, const float* oG2,
+                             const float* oG3, double* energy, void* stream);
+
 /* The same energy with phi given as one Tucker tensor [[phi_core; U_1, U_2, U_3]]
  * of ranks rho[3] in [1, 64] (the output of demag_recompress_tucker: phi_core
  * float [rho3][rho2][rho1], phi_U float rows [rho_p][n_p] per mode, modes one

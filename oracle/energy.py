@@ -100,3 +100,16 @@ def tucker_magnetization(core, V, n, ranks) -> np.ndarray:
     core = np.asarray(core, dtype=np.float64)
     Vb = ost._split_blocks(V, n, ranks)
     return np.stack([ost.tucker_to_full(core[q], [Vb[q][p] for p in range(3)]) for q in range(3)])
+
+
+def energy_tt(G1, G2, G3, n, ranks, h, R: int, c0: float = 2.15) -> float:
+    """Energy of a TT magnetization (Eq. tt_3d_1, cores per component in the ABI layout) through the
+    TT application (App. C, Eq. tt_3d_2 with the Toeplitz factors): m and phi formed densely, E by
+    `energy`."""
+    from . import structured as ost
+
+    n = tuple(int(v) for v in n)
+    w, o1, o2, o3 = ost.apply_tt(G1, G2, G3, n, ranks, h, R, c0)
+    phi = ost.tt_output_to_full(w, o1, o2, o3, ranks)
+    m = np.stack([ost.tt_to_full(G1[q], G2[q], G3[q], ranks) for q in range(3)])
+    return energy(m, phi, h)

@@ -83,6 +83,7 @@ _SIGS = {
     "demag_apply_tucker_batched": (_i, [_vp, _i, ctypes.POINTER(_i), _vp, _vp, _vp, _vp]),
     "demag_apply_tt_batched": (_i, [_vp, _i, ctypes.POINTER(_i), _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "demag_energy_tucker": (_i, [_vp, ctypes.POINTER(_i), _vp, _vp, _vp, _vp, _vp, _vp]),
+    "demag_energy_tt": (_i, [_vp, ctypes.POINTER(_i), _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "demag_energy_tucker_phi": (_i, [_vp, ctypes.POINTER(_i), _vp, _vp, ctypes.POINTER(_i), _vp, _vp, _vp, _vp]),
     "demag_stray_field": (_i, [_vp, _vp, _vp, _vp]),
     "demag_stray_field_exact": (_i, [_vp, _vp, _vp, _i, _vp]),
@@ -525,6 +526,21 @@ def demag_energy_tucker(plan: Plan, ranks, core, V, out_w, out_V, energy, stream
                                    _ptr(V, 3 * tot, f32, "V"), _ptr(out_w, plan.M * 3, f32, "out_w"),
                                    _ptr(out_V, plan.M * 3 * tot, f32, "out_V"),
                                    _ptr(energy, 1, torch.float64, "energy"), _stream(stream)), plan.ptr)
+
+
+def demag_energy_tt(plan: Plan, ranks, G1, G2, G3, out_w, oG1, oG2, oG3, energy, stream=None):
+    """Energy of a TT magnetization from its demag_apply_tt output (energy: device float64)."""
+    import torch
+    r1, r2 = int(ranks[0]), int(ranks[1])
+    rr = (_i * 2)(r1, r2)
+    f32 = torch.float32
+    s1, s2, s3 = r1 * plan.n[0], r1 * r2 * plan.n[1], r2 * plan.n[2]
+    M = plan.M
+    _check(lib.demag_energy_tt(plan.ptr, rr, _ptr(G1, 3 * s1, f32, "G1"), _ptr(G2, 3 * s2, f32, "G2"),
+                               _ptr(G3, 3 * s3, f32, "G3"), _ptr(out_w, 3 * M, f32, "out_w"),
+                               _ptr(oG1, 3 * M * s1, f32, "oG1"), _ptr(oG2, 3 * M * s2, f32, "oG2"),
+                               _ptr(oG3, 3 * M * s3, f32, "oG3"), _ptr(energy, 1, torch.float64, "energy"),
+                               _stream(stream)), plan.ptr)
 
 
 def demag_energy_tucker_phi(plan: Plan, ranks, core, V, rho, phi_core, phi_U, energy, stream=None):

@@ -128,6 +128,66 @@ __global__ void __launch_bounds__(256) tucker_energy_kernel(const __grid_constan
   }
 }
 
+// The same energy for a TT magnetization (Eq. tt_3d_1) and the 3M trains of its potential: one
+// block per (term t, component q); the inner product of two trains contracts the first-core Gram
+// M1[a1][b1], the middle-core Gram M2[(a1 a2)][(b1 b2)] and the last-core Gram M3[a2][b2]:
+//   <A, B'> = sum_{a2, b2} M3[a2][b2] sum_{a1, b1} M1[a1][b1] M2[(a1 a2)][(b1 b2)],
+// with D_q applied to the axis-q core of the term.
+struct EnTT {
+  int n[3];
+  double inv2h[3];
+  int r1, r2;                    // ranks of the magnetization and of every term
+  const float* A[3];             // magnetization cores, component q at A[p] + q * (size of core p)
+  const float* B[3];             // term cores, term t at B[p] + t * (size of core p)
+  const float* w;                // term weights
+  int T;
+  double* part;                  // [T][3]
+};
+
+__global__ void __launch_bounds__(256) tt_energy_kernel(const __grid_constant__ EnTT a) {
+  extern __shared__ double sg[];
+  __shared__ double red[32];
+  const int t = blockIdx.x, q = blockIdx.y;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int r1 = a.r1, r2 = a.r2, r12 = r1 * r2;
+  const int rows[3] = {r1, r12, r2};
+  double* Mg[3] = {sg, sg + r1 * r1, sg + r1 * r1 + (long)r12 * r12};
+  for (int p = 0; p < 3; ++p) {
+    const int n = a.n[p], rp = rows[p];
+    const float* Aq = a.A[p] + (long)q * rp * n;
+    const float* Bt = a.B[p] + (long)t * rp * n;
+    for (int e = warp; e < rp * rp; e += nw) {
+      const int ia = e / rp, ib = e % rp;
+      const float* ar = Aq + (long)ia * n;
+      const float* br = Bt + (long)ib * n;
+      double acc = 0.0;
+      if (p == q)
+        for (int i = lane; i < n; i += 32) acc += (double)ar[i] * fd_row(br, i, n, a.inv2h[p]);
+      else
+        for (int i = lane; i < n; i += 32) acc += (double)ar[i] * (double)br[i];
+      acc = en_warp_sum(acc);
+      if (lane == 0) Mg[p][e] = acc;
+    }
+  }
+  __syncthreads();
+  double x = 0.0;
+  for (int e = threadIdx.x; e < r2 * r2; e += blockDim.x) {
+    const int a2 = e / r2, b2 = e % r2;
+    double s = 0.0;
+    for (int a1 = 0; a1 < r1; ++a1)
+      for (int b1 = 0; b1 < r1; ++b1) s += Mg[0][a1 * r1 + b1] * Mg[1][(long)(a1 * r2 + a2) * r12 + b1 * r2 + b2];
+    x += s * Mg[2][e];
+  }
+  x = en_warp_sum(x);
+  if (lane == 0) red[warp] = x;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double v = 0.0;
+    for (int i = 0; i < nw; ++i) v += red[i];
+    a.part[(long)t * 3 + q] = (double)a.w[t] * v;
+  }
+}
+
 // energy = scale * sum part[0..count) in a fixed order (one block)
 __global__ void __launch_bounds__(256) energy_sum_kernel(long count, const double* part, double scale, double* energy) {
   __shared__ double red[32];
@@ -180,9 +240,67 @@ static demag_status run_tucker_energy(demag_plan* P, EnTucker& a, double* energy
   return DEMAG_OK;
 }
 
+constexpr int kEnMaxTTRank = 128;  // r1 r2: the middle-core Gram holds (r1 r2)^2 doubles in shared memory
+
 }  // namespace demag
 
 using namespace demag;
+
+extern "C" demag_status demag_energy_tt(demag_plan* P, const int r[2], const float* G1, const float* G2,
+                                        const float* G3, const float* out_w, const float* oG1, const float* oG2,
+                                        const float* oG3, double* energy, void* stream) {
+  if (!P) return set_error(nullptr, DEMAG_EINVAL, "demag_energy_tt: plan is NULL");
+  if (!r || !G1 || !G2 || !G3 || !out_w || !oG1 || !oG2 || !oG3 || !energy)
+    return set_error(P, DEMAG_EINVAL, "demag_energy_tt: NULL pointer");
+  demag_status u = require_uniform(P, "demag_energy_tt");
+  if (u != DEMAG_OK) return u;
+  if (r[0] < 1 || r[1] < 1 || r[0] > kEnMaxRank || r[1] > kEnMaxRank || r[0] * r[1] > kEnMaxTTRank)
+    return set_error(P, DEMAG_EINVAL, "demag_energy_tt: ranks must be in [1, %d] with r1 r2 <= %d", kEnMaxRank,
+                     kEnMaxTTRank);
+  cudaStream_t st = (cudaStream_t)stream;
+  EnTT a{};
+  for (int p = 0; p < 3; ++p) {
+    a.n[p] = P->n[p];
+    a.inv2h[p] = 0.5 / P->h[p];
+  }
+  a.r1 = r[0];
+  a.r2 = r[1];
+  a.A[0] = G1;
+  a.A[1] = G2;
+  a.A[2] = G3;
+  a.B[0] = oG1;
+  a.B[1] = oG2;
+  a.B[2] = oG3;
+  a.w = out_w;
+  a.T = 3 * P->M;
+  const int r12 = r[0] * r[1];
+  const size_t smem = sizeof(double) * ((size_t)r[0] * r[0] + (size_t)r12 * r12 + (size_t)r[1] * r[1]);
+  if (smem > 48 * 1024) {
+    static unsigned long long done = 0;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (!(done & (1ull << (dev & 63)))) {
+      // largest request: r1, r2 <= 64 and r1 r2 <= 128 give at most 2 * 64^2 + 128^2 doubles (192 KB)
+      const int cap = (int)(sizeof(double) * ((size_t)kEnMaxTTRank * kEnMaxTTRank + 2 * kEnMaxRank * kEnMaxRank));
+      DEMAG_CUDA(P, cudaFuncSetAttribute(tt_energy_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
+      done |= 1ull << (dev & 63);
+    }
+  }
+  const long blocks = (long)a.T * 3;
+  void* mem = nullptr;
+  DEMAG_CUDA(P, cudaMallocAsync(&mem, sizeof(double) * (size_t)blocks, st));
+  a.part = static_cast<double*>(mem);
+  DEMAG_LAUNCH(P, kFamEnergy, st, tt_energy_kernel<<<dim3(a.T, 3), 256, smem, st>>>(a));
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) {
+    const double vol = P->h[0] * P->h[1] * P->h[2];
+    DEMAG_LAUNCH(P, kFamEnergy, st, energy_sum_kernel<<<1, 256, 0, st>>>(blocks, a.part, 0.5 * vol, energy));
+    e = cudaGetLastError();
+  }
+  cudaFreeAsync(mem, st);
+  if (e != cudaSuccess) return cuda_error(P, e, "demag_energy_tt");
+  return DEMAG_OK;
+}
 
 extern "C" demag_status demag_energy_tucker(demag_plan* P, const int r[3], const float* core, const float* V,
                                             const float* out_w, const float* out_V, double* energy, void* stream) {

@@ -103,3 +103,53 @@ def test_rejects_bad_ranks(D):
     with pytest.raises(RuntimeError, match="ranks"):
         D.demag_energy_tucker_phi(P, (1, 1, 1), dev(core.ravel()), dev(V), (65, 1, 1),
                                   torch.zeros(65, device="cuda"), torch.zeros(65 * 8 + 16, device="cuda"), E)
+
+
+def _apply_tt(D, P, n, ranks, G):
+    M, (r1, r2) = P.M, ranks
+    w = torch.empty(M * 3, device="cuda")
+    o = [torch.empty(M * 3 * s, device="cuda") for s in (r1 * n[0], r1 * r2 * n[1], r2 * n[2])]
+    D.demag_apply_tt(P, ranks, *G, w, *o)
+    return w, o
+
+
+@pytest.mark.parametrize("n,ranks,R", [((10, 8, 6), (2, 3), 21), ((3, 17, 2), (1, 2), 41)])
+def test_energy_tt_vs_oracle(D, n, ranks, R):
+    h = (1.0 / max(n),) * 3
+    G1, G2, G3 = synth.tt_inputs(n, ranks, 81)
+    P = D.demag_build_factors(n, h, R)
+    G = [dev(x) for x in (G1, G2, G3)]
+    w, o = _apply_tt(D, P, n, ranks, G)
+    E = torch.empty((), dtype=torch.float64, device="cuda")
+    D.demag_energy_tt(P, ranks, *G, w, *o, E)
+    torch.cuda.synchronize()
+    ref = oe.energy_tt(G1, G2, G3, n, ranks, h, R)
+    assert abs(E.item() - ref) <= 1e-5 * abs(ref), (E.item(), ref)
+
+
+def test_energy_tt_of_a_converted_tucker_equals_the_tucker_energy(D):
+    n, ranks, R = (48, 40, 32), (2, 3, 2), 41
+    h = (1.0 / 48,) * 3
+    core, V = synth.tucker_inputs(n, ranks, 82)
+    P = D.demag_build_factors(n, h, R)
+    Et, _ = _energy(D, P, n, ranks, core, V)
+    t = (ranks[0], ranks[2])
+    G = (torch.empty(3 * t[0] * n[0], device="cuda"), torch.empty(3 * t[0] * t[1] * n[1], device="cuda"),
+         torch.empty(3 * t[1] * n[2], device="cuda"))
+    D.demag_tucker_to_tt(P, ranks, dev(core.ravel()), dev(V), *G)
+    w, o = _apply_tt(D, P, n, t, G)
+    E = torch.empty((), dtype=torch.float64, device="cuda")
+    D.demag_energy_tt(P, t, *G, w, *o, E)
+    torch.cuda.synchronize()
+    assert abs(E.item() - Et) <= 2e-5 * abs(Et), (E.item(), Et)
+
+
+def test_energy_tt_rejects_large_ranks(D):
+    n = (8, 8, 8)
+    P = D.demag_build_factors(n, (1 / 8,) * 3, 21)
+    r = (12, 12)
+    G = [torch.zeros(3 * s, device="cuda") for s in (12 * 8, 144 * 8, 12 * 8)]
+    o = [torch.zeros(3 * P.M * s, device="cuda") for s in (12 * 8, 144 * 8, 12 * 8)]
+    E = torch.empty((), dtype=torch.float64, device="cuda")
+    with pytest.raises(RuntimeError, match="ranks"):
+        D.demag_energy_tt(P, r, *G, torch.zeros(3 * P.M, device="cuda"), *o, E)

@@ -7,6 +7,8 @@
    Alg. 2: the Tucker-route energy equals the energy of the closed-form exact
    collocation potential (charged-rectangle integrals), up to the sinc
    quadrature error, which vanishes as R grows.
+3. The TT route (oracle/energy.py: energy_tt) gives the full-format energy of
+   the formed TT magnetization.
 """
 import numpy as np
 import pytest
@@ -38,3 +40,13 @@ def test_uniform_cube_energy_is_the_exact_collocation_energy(n):
     assert errs[0] > errs[1] > errs[2] or errs[1] <= 1e-10
     # and the discretisation error itself, near 1/6 (the text after Fig. 2)
     assert abs(exact_E - 1.0 / 6.0) < 3e-3
+
+
+def test_tt_energy_equals_the_full_format_energy():
+    from oracle import structured as ost
+    n, ranks, h, R = (8, 7, 6), (2, 3), (0.12, 0.12, 0.12), 21
+    G1, G2, G3 = synth.tt_inputs(n, ranks, 42)
+    E = oe.energy_tt(G1, G2, G3, n, ranks, h, R)
+    m = np.stack([ost.tt_to_full(G1[q], G2[q], G3[q], ranks) for q in range(3)])
+    ref = oe.energy_from_m(m, n, h, R)
+    assert abs(E - ref) <= 1e-12 * abs(ref)
