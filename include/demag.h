@@ -411,7 +411,7 @@ demag_status demag_energy_tucker(demag_plan* plan, const int r[3], const float* 
  * G2 float [3][r1 r2][n2], G3 float [3][r2][n3]) from the output of
  * demag_apply_tt for it (out_w float [M][3], oG1, oG2, oG3): the inner
  * products of trains through the Grams of their first, middle and last cores.
- * r1, r2 in [1, 64] with r1 r2 <= 128; energy: one double on the device. */
+ * r1, r2 in [1, 64] with r1 r2 <= 64; energy: one double on the device. */
 demag_status demag_energy_tt(demag_plan* plan, const int r[2], const float* G1, const float* G2,
                              const float* G3, const float* out_w, const float* oG1, const float* oG2,
                              const float* oG3, double* energy, void* stream);

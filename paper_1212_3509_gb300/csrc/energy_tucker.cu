@@ -20,6 +20,9 @@
 namespace demag {
 
 constexpr int kEnMaxRank = 64;
+// static shared memory of both energy kernels: the two [64][33] float tiles of block_gram and a
+// 32-double reduction buffer
+constexpr size_t kEnStaticSmem = 2 * 64 * 33 * sizeof(float) + 32 * sizeof(double);
 
 __device__ __forceinline__ double en_warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -52,9 +55,63 @@ __device__ __forceinline__ double fd_row(const float* w, int i, int n, double in
   return inv2h * ((double)w[i + 1] - (double)w[i - 1]);
 }
 
+// Mout[a][b] = sum_i A[a][i] B'[b][i] (B' = D B when deriv) for ra, rb <= 64 rows of length n:
+// 32-column tiles of A and B' through shared memory (tA, tB: [64][33] floats), each of the 256
+// threads a 4 x 4 block of outputs, FP32 products summed within a tile and FP64 across tiles.
+__device__ void block_gram(const float* A, int ra, const float* B, int rb, int n, bool deriv, double inv2h,
+                           float* tA, float* tB, double* Mout) {
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  double acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+  for (int i0 = 0; i0 < n; i0 += 32) {
+    for (int e = threadIdx.x; e < 64 * 32; e += blockDim.x) {
+      const int r = e >> 5, c = e & 31, i = i0 + c;
+      tA[r * 33 + c] = (r < ra && i < n) ? A[(long)r * n + i] : 0.f;
+      float bv = 0.f;
+      if (r < rb && i < n) bv = deriv ? (float)fd_row(B + (long)r * n, i, n, inv2h) : B[(long)r * n + i];
+      tB[r * 33 + c] = bv;
+    }
+    __syncthreads();
+    float part[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) part[i][j] = 0.f;
+#pragma unroll 8
+    for (int c = 0; c < 32; ++c) {
+      float av[4], bw[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        av[i] = tA[(ty + 16 * i) * 33 + c];
+        bw[i] = tB[(tx + 16 * i) * 33 + c];
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) part[i][j] = fmaf(av[i], bw[j], part[i][j]);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] += (double)part[i][j];
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int ia = ty + 16 * i, ib = tx + 16 * j;
+      if (ia < ra && ib < rb) Mout[ia * rb + ib] = acc[i][j];
+    }
+}
+
 __global__ void __launch_bounds__(256) tucker_energy_kernel(const __grid_constant__ EnTucker a) {
   extern __shared__ double Mg[];
   __shared__ double red[32];
+  __shared__ float tA[64 * 33], tB[64 * 33];
   const int t = blockIdx.x, q = blockIdx.y;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int r1 = a.r[0], r2 = a.r[1], r3 = a.r[2];
@@ -65,21 +122,8 @@ __global__ void __launch_bounds__(256) tucker_energy_kernel(const __grid_constan
   int mo[3];
   for (int p = 0; p < 3; ++p) {
     const int n = a.n[p], rp = a.r[p], sp = a.s[p];
-    const float* Vq = a.V + voff;
-    const float* Wt = a.W[p] + (long)t * sp * n;
     mo[p] = moff;
-    for (int e = warp; e < rp * sp; e += nw) {
-      const int ia = e / sp, ib = e % sp;
-      const float* vr = Vq + (long)ia * n;
-      const float* wr = Wt + (long)ib * n;
-      double acc = 0.0;
-      if (p == q)
-        for (int i = lane; i < n; i += 32) acc += (double)vr[i] * fd_row(wr, i, n, a.inv2h[p]);
-      else
-        for (int i = lane; i < n; i += 32) acc += (double)vr[i] * (double)wr[i];
-      acc = en_warp_sum(acc);
-      if (lane == 0) Mg[moff + e] = acc;
-    }
+    block_gram(a.V + voff, rp, a.W[p] + (long)t * sp * n, sp, n, p == q, a.inv2h[p], tA, tB, Mg + moff);
     voff += (long)rp * n;
     moff += rp * sp;
   }
@@ -147,6 +191,7 @@ struct EnTT {
 __global__ void __launch_bounds__(256) tt_energy_kernel(const __grid_constant__ EnTT a) {
   extern __shared__ double sg[];
   __shared__ double red[32];
+  __shared__ float tA[64 * 33], tB[64 * 33];
   const int t = blockIdx.x, q = blockIdx.y;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int r1 = a.r1, r2 = a.r2, r12 = r1 * r2;
@@ -154,20 +199,8 @@ __global__ void __launch_bounds__(256) tt_energy_kernel(const __grid_constant__ 
   double* Mg[3] = {sg, sg + r1 * r1, sg + r1 * r1 + (long)r12 * r12};
   for (int p = 0; p < 3; ++p) {
     const int n = a.n[p], rp = rows[p];
-    const float* Aq = a.A[p] + (long)q * rp * n;
-    const float* Bt = a.B[p] + (long)t * rp * n;
-    for (int e = warp; e < rp * rp; e += nw) {
-      const int ia = e / rp, ib = e % rp;
-      const float* ar = Aq + (long)ia * n;
-      const float* br = Bt + (long)ib * n;
-      double acc = 0.0;
-      if (p == q)
-        for (int i = lane; i < n; i += 32) acc += (double)ar[i] * fd_row(br, i, n, a.inv2h[p]);
-      else
-        for (int i = lane; i < n; i += 32) acc += (double)ar[i] * (double)br[i];
-      acc = en_warp_sum(acc);
-      if (lane == 0) Mg[p][e] = acc;
-    }
+    block_gram(a.A[p] + (long)q * rp * n, rp, a.B[p] + (long)t * rp * n, rp, n, p == q, a.inv2h[p], tA, tB,
+               Mg[p]);
   }
   __syncthreads();
   double x = 0.0;
@@ -212,7 +245,7 @@ static demag_status run_tucker_energy(demag_plan* P, EnTucker& a, double* energy
     a.inv2h[p] = 0.5 / P->h[p];
   }
   const size_t smem = sizeof(double) * ((size_t)a.r[0] * a.s[0] + (size_t)a.r[1] * a.s[1] + (size_t)a.r[2] * a.s[2]);
-  if (smem > 48 * 1024) {
+  if (smem + kEnStaticSmem > 48 * 1024) {  // dynamic plus the kernels' static tiles
     static unsigned long long done = 0;
     int dev = 0;
     cudaGetDevice(&dev);
@@ -240,7 +273,7 @@ static demag_status run_tucker_energy(demag_plan* P, EnTucker& a, double* energy
   return DEMAG_OK;
 }
 
-constexpr int kEnMaxTTRank = 128;  // r1 r2: the middle-core Gram holds (r1 r2)^2 doubles in shared memory
+constexpr int kEnMaxTTRank = 64;  // r1 r2: the middle core's rows, at most 64 per Gram side
 
 }  // namespace demag
 
@@ -275,12 +308,12 @@ extern "C" demag_status demag_energy_tt(demag_plan* P, const int r[2], const flo
   a.T = 3 * P->M;
   const int r12 = r[0] * r[1];
   const size_t smem = sizeof(double) * ((size_t)r[0] * r[0] + (size_t)r12 * r12 + (size_t)r[1] * r[1]);
-  if (smem > 48 * 1024) {
+  if (smem + kEnStaticSmem > 48 * 1024) {  // dynamic plus the kernels' static tiles
     static unsigned long long done = 0;
     int dev = 0;
     cudaGetDevice(&dev);
     if (!(done & (1ull << (dev & 63)))) {
-      // largest request: r1, r2 <= 64 and r1 r2 <= 128 give at most 2 * 64^2 + 128^2 doubles (192 KB)
+      // largest request: r1, r2 <= 64 and r1 r2 <= 64 give at most 3 * 64^2 doubles (96 KB)
       const int cap = (int)(sizeof(double) * ((size_t)kEnMaxTTRank * kEnMaxTTRank + 2 * kEnMaxRank * kEnMaxRank));
       DEMAG_CUDA(P, cudaFuncSetAttribute(tt_energy_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
       done |= 1ull << (dev & 63);

@@ -35,7 +35,8 @@ def _energy(D, P, n, ranks, core, V):
 
 
 @pytest.mark.parametrize("n,ranks,R", [((12, 10, 8), (2, 3, 2), 21), ((17, 9, 23), (1, 4, 3), 41),
-                                       ((2, 5, 3), (1, 2, 2), 21)])
+                                       ((2, 5, 3), (1, 2, 2), 21),
+                                       ((12, 10, 8), (40, 40, 40), 21)])  # Grams above 48 KB of shared memory
 def test_energy_tucker_vs_oracle(D, n, ranks, R):
     h = (1.0 / max(n),) * 3
     core, V = synth.tucker_inputs(n, ranks, 77)
@@ -113,7 +114,8 @@ def _apply_tt(D, P, n, ranks, G):
     return w, o
 
 
-@pytest.mark.parametrize("n,ranks,R", [((10, 8, 6), (2, 3), 21), ((3, 17, 2), (1, 2), 41)])
+@pytest.mark.parametrize("n,ranks,R", [((10, 8, 6), (2, 3), 21), ((3, 17, 2), (1, 2), 41),
+                                       ((16, 12, 10), (8, 8), 21)])
 def test_energy_tt_vs_oracle(D, n, ranks, R):
     h = (1.0 / max(n),) * 3
     G1, G2, G3 = synth.tt_inputs(n, ranks, 81)
