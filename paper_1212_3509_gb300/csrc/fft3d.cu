@@ -46,14 +46,18 @@ constexpr int kFft3dMaxLog = 11;  // L_p <= 2048 (n_p <= 1024)
 // per fibre, G fibres per block (at least 16, so that the transposed stores
 // write runs of >= 128 bytes), buffers padded by pad16 and separated by an
 // odd stride so that the same bin of different fibres falls in different banks.
-// N = 2048 takes 64 threads (two warps) per fibre and 8 fibres per block
-// (register and shared-memory budget); its groups synchronise the block.
-constexpr int f3_tg(int N) { return N >= 2048 ? 64 : (N / 16 < 1 ? 1 : (N / 16 > 32 ? 32 : N / 16)); }
-constexpr int f3_fibres(int N) { return N >= 2048 ? 8 : (16 * f3_tg(N) < 256 ? 256 / f3_tg(N) : 16); }
+// N = 2048 takes 128 threads (four warps, 16 bins each) per fibre and 4
+// fibres per block (register and shared-memory budget); its groups
+// synchronise the block.
+constexpr int f3_tg(int N) { return N >= 2048 ? 128 : (N / 16 < 1 ? 1 : (N / 16 > 32 ? 32 : N / 16)); }
+constexpr int f3_fibres(int N) { return N >= 2048 ? 4 : (16 * f3_tg(N) < 256 ? 256 / f3_tg(N) : 16); }
 constexpr int f3_block(int N) { return f3_fibres(N) * f3_tg(N); }
-// P3 double-buffers its fibres: half the fibres per block from N = 512 (two
-// blocks of 256 threads per SM at 128 registers instead of one of 512)
-constexpr int f3_fibres_p3(int N) { return N >= 512 ? f3_fibres(N) / 2 : f3_fibres(N); }
+// P3 double-buffers its fibres: half the fibres per block for N = 512 and
+// 1024 (two blocks of 256 threads per SM at 128 registers instead of one of
+// 512); N = 2048 keeps its 4 fibres (512 threads, one block per SM)
+constexpr int f3_fibres_p3(int N) {
+  return N >= 2048 ? f3_fibres(N) : (N >= 512 ? f3_fibres(N) / 2 : f3_fibres(N));
+}
 
 template <int LOGN> struct F3 {
   static constexpr int N = 1 << LOGN;
