@@ -128,3 +128,97 @@ def _field_mutations():
 def test_field_mutation_is_caught(monkeypatch, name, fn):
     monkeypatch.setattr(field, name, fn)
     assert _field_pin_errors() > 1e-3
+
+
+# ---- App. C TT arithmetic and the structured energies: plant mistakes and check that the
+# dense comparisons of their pins catch each one
+from oracle import energy as oen  # noqa: E402
+from oracle import structured as ost  # noqa: E402
+from oracle import ttround  # noqa: E402
+
+
+def _tt_pin_errors():
+    rng = np.random.default_rng(9)
+    errs = []
+    r, n = (2, 3, 4), (7, 6, 5)
+    C = rng.standard_normal((r[2], r[1], r[0]))
+    V = [rng.standard_normal((r[p], n[p])) for p in range(3)]
+    G = ttround.tucker_to_tt(C, *V)
+    ref = ost.tucker_to_full(C, V)
+    errs.append(np.linalg.norm(ost.tt_to_full(*G, (r[0], r[2])) - ref) / np.linalg.norm(ref))
+    lam = rng.standard_normal(3) + 2.0
+    U = [rng.standard_normal((3, n[p])) for p in range(3)]
+    G = ttround.cp_to_tt(lam, *U)
+    ref = np.einsum("l,li,lj,lk->kji", lam, U[0], U[1], U[2])
+    errs.append(np.linalg.norm(ost.tt_to_full(*G, (3, 3)) - ref) / np.linalg.norm(ref))
+    ra, rb = (2, 3), (3, 2)
+    A = (rng.standard_normal((2, n[0])), rng.standard_normal((6, n[1])), rng.standard_normal((3, n[2])))
+    B = (rng.standard_normal((3, n[0])), rng.standard_normal((6, n[1])), rng.standard_normal((2, n[2])))
+    Cc = ttround.tt_hadamard(A, ra, B, rb)
+    ref = ost.tt_to_full(*A, ra) * ost.tt_to_full(*B, rb)
+    errs.append(np.linalg.norm(ost.tt_to_full(*Cc, (6, 6)) - ref) / np.linalg.norm(ref))
+    return max(errs)
+
+
+def _energy_pin_error():
+    n, ranks, h, R = (6, 5, 4), (2, 2, 1), (0.15, 0.15, 0.15), 11
+    core, V = synth.tucker_inputs(n, ranks, 43)
+    E = oen.energy_tucker(core, V, n, ranks, h, R)
+    ref = oen.energy_from_m(oen.tucker_magnetization(core, V, n, ranks), n, h, R)
+    errs = [abs(E - ref) / abs(ref)]
+    G1, G2, G3 = synth.tt_inputs(n, (2, 2), 44)
+    E = oen.energy_tt(G1, G2, G3, n, (2, 2), h, R)
+    m = np.stack([ost.tt_to_full(G1[q], G2[q], G3[q], (2, 2)) for q in range(3)])
+    ref = oen.energy_from_m(m, n, h, R)
+    errs.append(abs(E - ref) / abs(ref))
+    return max(errs)
+
+
+def test_tt_and_energy_unmutated_are_exact():
+    assert _tt_pin_errors() < 1e-12
+    assert _energy_pin_error() < 1e-12
+
+
+def _tt_mutations():
+    orig_t2t, orig_c2t, orig_had = ttround.tucker_to_tt, ttround.cp_to_tt, ttround.tt_hadamard
+
+    def t2t_rows_swapped(core, V1, V2, V3):  # middle-core rows (a3, a1) instead of (a1, a3)
+        G1, G2, G3 = orig_t2t(core, V1, V2, V3)
+        r1, r3 = G1.shape[0], G3.shape[0]
+        return G1, G2.reshape(r1, r3, -1).transpose(1, 0, 2).reshape(r1 * r3, -1), G3
+
+    def c2t_no_lambda(lam, U1, U2, U3):
+        return orig_c2t(np.ones_like(np.asarray(lam, dtype=np.float64)), U1, U2, U3)
+
+    def had_first_core_b_major(A, ra, B, rb):  # Kronecker order of the first core flipped
+        C1, C2, C3 = orig_had(A, ra, B, rb)
+        n1 = C1.shape[1]
+        return C1.reshape(ra[0], rb[0], n1).transpose(1, 0, 2).reshape(-1, n1), C2, C3
+
+    return [("tucker_to_tt", t2t_rows_swapped), ("cp_to_tt", c2t_no_lambda), ("tt_hadamard", had_first_core_b_major)]
+
+
+@pytest.mark.parametrize("name,fn", _tt_mutations(), ids=lambda x: x if isinstance(x, str) else "")
+def test_tt_mutation_is_caught(monkeypatch, name, fn):
+    monkeypatch.setattr(ttround, name, fn)
+    assert _tt_pin_errors() > 1e-3
+
+
+def _energy_mutations():
+    orig_apply_tucker, orig_apply_tt = ost.apply_tucker, ost.apply_tt
+
+    def tucker_wrong_component(core, V, n, ranks, h, R, c0=2.15):  # outputs of component q + 1 for q
+        w, outV = orig_apply_tucker(core, V, n, ranks, h, R, c0)
+        return w, [np.roll(o, 1, axis=1) for o in outV]
+
+    def tt_no_weights(G1, G2, G3, n, ranks, h, R, c0=2.15):  # c s omega_k dropped
+        w, o1, o2, o3 = orig_apply_tt(G1, G2, G3, n, ranks, h, R, c0)
+        return np.ones_like(w), o1, o2, o3
+
+    return [("apply_tucker", tucker_wrong_component), ("apply_tt", tt_no_weights)]
+
+
+@pytest.mark.parametrize("name,fn", _energy_mutations(), ids=lambda x: x if isinstance(x, str) else "")
+def test_energy_mutation_is_caught(monkeypatch, name, fn):
+    monkeypatch.setattr(ost, name, fn)
+    assert _energy_pin_error() > 1e-3
