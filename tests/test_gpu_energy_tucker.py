@@ -155,3 +155,21 @@ def test_energy_tt_rejects_large_ranks(D):
     E = torch.empty((), dtype=torch.float64, device="cuda")
     with pytest.raises(RuntimeError, match="ranks"):
         D.demag_energy_tt(P, r, *G, torch.zeros(3 * P.M, device="cuda"), *o, E)
+
+
+def test_energy_1024_tucker_and_tt_routes_agree(D):
+    # the 1024^3 workload (ranks 8, R = 61): the Tucker energy and the TT energy of the same
+    # magnetization converted to a train (independent kernels) agree
+    n, ranks, R = (1024, 1024, 1024), (8, 8, 8), 61
+    core, V = synth.tucker_inputs(n, ranks, 1500)
+    P = D.demag_build_factors(n, (1.0 / 1024,) * 3, R)
+    Et, _ = _energy(D, P, n, ranks, core, V)
+    t = (8, 8)
+    G = (torch.empty(3 * 8 * 1024, device="cuda"), torch.empty(3 * 64 * 1024, device="cuda"),
+         torch.empty(3 * 8 * 1024, device="cuda"))
+    D.demag_tucker_to_tt(P, ranks, dev(core.ravel()), dev(V), *G)
+    w, o = _apply_tt(D, P, n, t, G)
+    E = torch.empty((), dtype=torch.float64, device="cuda")
+    D.demag_energy_tt(P, t, *G, w, *o, E)
+    torch.cuda.synchronize()
+    assert abs(E.item() - Et) <= 2e-5 * abs(Et), (E.item(), Et)

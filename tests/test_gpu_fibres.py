@@ -47,3 +47,18 @@ def test_fibres_vs_fft3d_and_repeatable(D):
     torch.cuda.synchronize()
     assert torch.equal(a, b)
     assert rel_l2(host(a), host(c)) <= 2e-6
+
+
+def test_fibres_256_sampled_lines(D):
+    # the bench's 256^3 workload (R = 41, vortex state) at four output lines against the oracle
+    from oracle import full as of
+    n3, h, R = (256, 256, 256), (1 / 256,) * 3, 41
+    m = synth.vortex_m(n3, 1213)
+    P = D.demag_build_factors(n3, h, R)
+    phi = torch.empty(256, 256, 256, device="cuda")
+    D.demag_apply_full_fibres(P, dev(m), phi)
+    torch.cuda.synchronize()
+    lines = [(0, 0), (17, 200), (128, 129), (255, 31)]
+    ref = of.apply_full_lines(m, n3, h, R, lines)
+    got = host(phi)
+    assert rel_l2(np.stack([got[i3, i2] for i3, i2 in lines]), ref) <= 1e-5
