@@ -25,20 +25,28 @@ __device__ __forceinline__ float fd_coef(int i, int j, int n, float inv2h) {
   return j == i + 1 ? inv2h : j == i - 1 ? -inv2h : 0.f;
 }
 
-// derivative along axis p at cell idx (stride st along that axis, coordinate c)
-__device__ __forceinline__ float fd_apply(const float* f, long idx, int c, int n, long st, float inv2h) {
-  float acc = 0.f;
-  int lo = c - 2 < 0 ? 0 : c - 2, hi = c + 2 > n - 1 ? n - 1 : c + 2;
-  for (int j = lo; j <= hi; ++j) acc += fd_coef(c, j, n, inv2h) * f[idx + (long)(j - c) * st];
-  return acc;
-}
-
 // transpose: sum_i D[i][c] g[i]
 __device__ __forceinline__ float fdT_apply(const float* g, long idx, int c, int n, long st, float inv2h) {
   float acc = 0.f;
   int lo = c - 2 < 0 ? 0 : c - 2, hi = c + 2 > n - 1 ? n - 1 : c + 2;
   for (int i = lo; i <= hi; ++i) acc += fd_coef(i, c, n, inv2h) * g[idx + (long)(i - c) * st];
   return acc;
+}
+
+// The same stencils written out: central inside, one-sided at the two end cells
+__device__ __forceinline__ float fd_fast(const float* f, long idx, int c, int n, long st, float inv2h) {
+  if (c > 0 && c < n - 1) return inv2h * (f[idx + st] - f[idx - st]);
+  if (n == 1) return 0.f;
+  if (n == 2) return 2.f * inv2h * (c == 0 ? f[idx + st] - f[idx] : f[idx] - f[idx - st]);
+  if (c == 0) return inv2h * (-3.f * f[idx] + 4.f * f[idx + st] - f[idx + 2 * st]);
+  return inv2h * (3.f * f[idx] - 4.f * f[idx - st] + f[idx - 2 * st]);
+}
+
+// transpose: away from the ends (3 <= c <= n - 4) only the central rows c - 1 and c + 1 reach
+// column c; near the ends the one-sided rows contribute too (general loop)
+__device__ __forceinline__ float fdT_fast(const float* g, long idx, int c, int n, long st, float inv2h) {
+  if (c >= 3 && c <= n - 4) return inv2h * (g[idx - st] - g[idx + st]);
+  return fdT_apply(g, idx, c, n, st, inv2h);
 }
 
 // out[p][cell] = scale * (D_p phi)[cell]
@@ -48,9 +56,9 @@ __global__ void fd_gradient_kernel(FDGrid g, const float* phi, float* out, float
     int i1 = (int)(idx % g.n[0]);
     int i2 = (int)((idx / g.n[0]) % g.n[1]);
     int i3 = (int)(idx / ((long)g.n[0] * g.n[1]));
-    out[idx] = scale * fd_apply(phi, idx, i1, g.n[0], 1, g.inv2h[0]);
-    out[N + idx] = scale * fd_apply(phi, idx, i2, g.n[1], g.n[0], g.inv2h[1]);
-    out[2 * N + idx] = scale * fd_apply(phi, idx, i3, g.n[2], (long)g.n[0] * g.n[1], g.inv2h[2]);
+    out[idx] = scale * fd_fast(phi, idx, i1, g.n[0], 1, g.inv2h[0]);
+    out[N + idx] = scale * fd_fast(phi, idx, i2, g.n[1], g.n[0], g.inv2h[1]);
+    out[2 * N + idx] = scale * fd_fast(phi, idx, i3, g.n[2], (long)g.n[0] * g.n[1], g.inv2h[2]);
   }
 }
 
@@ -61,24 +69,32 @@ __global__ void fd_adjoint_kernel(FDGrid g, const float* v, float* out) {
     int i1 = (int)(idx % g.n[0]);
     int i2 = (int)((idx / g.n[0]) % g.n[1]);
     int i3 = (int)(idx / ((long)g.n[0] * g.n[1]));
-    out[idx] = fdT_apply(v, idx, i1, g.n[0], 1, g.inv2h[0]) +
-               fdT_apply(v + N, idx, i2, g.n[1], g.n[0], g.inv2h[1]) +
-               fdT_apply(v + 2 * N, idx, i3, g.n[2], (long)g.n[0] * g.n[1], g.inv2h[2]);
+    out[idx] = fdT_fast(v, idx, i1, g.n[0], 1, g.inv2h[0]) +
+               fdT_fast(v + N, idx, i2, g.n[1], g.n[0], g.inv2h[1]) +
+               fdT_fast(v + 2 * N, idx, i3, g.n[2], (long)g.n[0] * g.n[1], g.inv2h[2]);
   }
 }
 
-// energy += half_vol * sum_cells m . (D phi), accumulated in FP64
-__global__ void energy_kernel(FDGrid g, const float* m, const float* phi, double half_vol, double* energy) {
+// energy += half_vol * sum_cells m . (D phi) (each cell's three products in FP32, cells summed in
+// FP64) and, with grad, grad[p][cell] = gscale ((D_p phi)[cell] + ptdtm[p][cell]): the energy and
+// its gradient 1/2 h1 h2 h3 (D P m + P^T D^T m) in one pass over phi, m and P^T D^T m
+__global__ void energy_grad_kernel(FDGrid g, const float* m, const float* phi, const float* ptdtm, double half_vol,
+                                   float gscale, double* energy, float* grad) {
   const long N = (long)g.n[0] * g.n[1] * g.n[2];
   double acc = 0.0;
   for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < N; idx += (long)gridDim.x * blockDim.x) {
     int i1 = (int)(idx % g.n[0]);
     int i2 = (int)((idx / g.n[0]) % g.n[1]);
     int i3 = (int)(idx / ((long)g.n[0] * g.n[1]));
-    float d1 = fd_apply(phi, idx, i1, g.n[0], 1, g.inv2h[0]);
-    float d2 = fd_apply(phi, idx, i2, g.n[1], g.n[0], g.inv2h[1]);
-    float d3 = fd_apply(phi, idx, i3, g.n[2], (long)g.n[0] * g.n[1], g.inv2h[2]);
-    acc += (double)m[idx] * d1 + (double)m[N + idx] * d2 + (double)m[2 * N + idx] * d3;
+    const float d1 = fd_fast(phi, idx, i1, g.n[0], 1, g.inv2h[0]);
+    const float d2 = fd_fast(phi, idx, i2, g.n[1], g.n[0], g.inv2h[1]);
+    const float d3 = fd_fast(phi, idx, i3, g.n[2], (long)g.n[0] * g.n[1], g.inv2h[2]);
+    acc += (double)fmaf(m[idx], d1, fmaf(m[N + idx], d2, m[2 * N + idx] * d3));
+    if (grad) {
+      grad[idx] = gscale * (d1 + ptdtm[idx]);
+      grad[N + idx] = gscale * (d2 + ptdtm[N + idx]);
+      grad[2 * N + idx] = gscale * (d3 + ptdtm[2 * N + idx]);
+    }
   }
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   __shared__ double part[32];
@@ -89,11 +105,6 @@ __global__ void energy_kernel(FDGrid g, const float* m, const float* phi, double
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     if (threadIdx.x == 0) atomicAdd(energy, half_vol * v);
   }
-}
-
-__global__ void axpy_kernel(float* y, const float* x, float a, long count) {
-  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < count; i += (long)gridDim.x * blockDim.x)
-    y[i] += a * x[i];
 }
 
 static FDGrid fd_grid(const demag_plan* P) {
@@ -149,18 +160,17 @@ extern "C" demag_status demag_energy(demag_plan* P, const float* m, double* ener
   demag_status s = full_forward(P, m, phi, prec, st);
   if (s != DEMAG_OK) return s;
   const double vol = P->h[0] * P->h[1] * P->h[2];
+  if (grad) {
+    // P^T (D^T m) first, then one pass for the energy and grad = 1/2 V (D P m + P^T D^T m)
+    DEMAG_LAUNCH(P, kFamEnergy, st, fd_adjoint_kernel<<<blocks_for(N), 256, 0, st>>>(fd_grid(P), m, dtm));
+    DEMAG_LAUNCHED(P, "fd_adjoint_kernel");
+    s = full_adjoint(P, dtm, ptdtm, prec, st);
+    if (s != DEMAG_OK) return s;
+  }
   DEMAG_CUDA(P, cudaMemsetAsync(energy, 0, sizeof(double), st));
-  DEMAG_LAUNCH(P, kFamEnergy, st, energy_kernel<<<blocks_for(N), 256, 0, st>>>(fd_grid(P), m, phi, 0.5 * vol, energy));
-  DEMAG_LAUNCHED(P, "energy_kernel");
-  if (!grad) return DEMAG_OK;
-  // grad = 1/2 V (D P m) + 1/2 V P^T (D^T m)
-  s = fd_gradient(P, phi, grad, (float)(0.5 * vol), st);
-  if (s != DEMAG_OK) return s;
-  DEMAG_LAUNCH(P, kFamEnergy, st, fd_adjoint_kernel<<<blocks_for(N), 256, 0, st>>>(fd_grid(P), m, dtm));
-  DEMAG_LAUNCHED(P, "fd_adjoint_kernel");
-  s = full_adjoint(P, dtm, ptdtm, prec, st);
-  if (s != DEMAG_OK) return s;
-  DEMAG_LAUNCH(P, kFamEnergy, st, axpy_kernel<<<blocks_for(3 * N), 256, 0, st>>>(grad, ptdtm, (float)(0.5 * vol), 3 * N));
-  DEMAG_LAUNCHED(P, "axpy_kernel");
+  DEMAG_LAUNCH(P, kFamEnergy, st,
+               energy_grad_kernel<<<blocks_for(N), 256, 0, st>>>(fd_grid(P), m, phi, grad ? ptdtm : nullptr,
+                                                                 0.5 * vol, (float)(0.5 * vol), energy, grad));
+  DEMAG_LAUNCHED(P, "energy_grad_kernel");
   return DEMAG_OK;
 }
