@@ -49,6 +49,7 @@ CASES = [
     ((40, 36, 32), (2, 3), 21, 1e-4, False),   # needs 64 samples on the first unfolding
     ((64, 64, 64), (2, 2), 41, 1e-6, True),
     ((33, 17, 5), (1, 1), 21, 1e-5, True),     # rank-1 input, odd sizes, thin third axis
+    ((1, 9, 7), (1, 2), 21, 1e-4, True),       # a single cell along the first axis
 ]
 
 
