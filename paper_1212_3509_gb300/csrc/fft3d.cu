@@ -982,12 +982,20 @@ demag_status fft3d_forward(demag_plan* P, const float* m, float* phi, cudaStream
 __global__ void field_energy_kernel(long count, const float* m, const float* h, double half_vol, float vol,
                                     double* energy, float* grad) {
   __shared__ double red[32];
-  double acc = 0.0;
+  double acc = 0.0;  // FP32 partial sums of 8 products, added in FP64
+  float part = 0.f;
+  int cnt = 0;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < count; i += (long)gridDim.x * blockDim.x) {
     const float hv = h[i];
-    acc += (double)m[i] * (double)hv;
+    part = fmaf(m[i], hv, part);
+    if (++cnt == 8) {
+      acc += (double)part;
+      part = 0.f;
+      cnt = 0;
+    }
     if (grad) grad[i] = -vol * hv;
   }
+  acc += (double)part;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
