@@ -5,8 +5,7 @@ import numpy as np
 import pytest
 
 import synth
-from oracle import field as ofield, full as ofull
-from oracle import energy as oen
+from oracle import field as ofield
 from gpu_helpers import TOL, dev, host, rel_l2
 
 pytestmark = pytest.mark.gpu

@@ -9,7 +9,7 @@ import numpy as np
 import pytest
 
 import synth
-from oracle import exact, full, quadrature as Q
+from oracle import exact, full
 
 FACTS = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_facts.json")))
 
