@@ -70,8 +70,10 @@ typedef enum {
 
 /* Grid and quadrature (Sec. 3.1 notation; Alg. 2 signature potential(M, h, R, c0, tol)).
  * n[p] >= 1 cells on axis p (n[0] = n1 is the fastest index), h[p] > 0 the
- * cell edge, R = 2M+1 odd and >= 5 the number of symmetric sinc nodes,
- * c0 > 0 the step constant (2.15 in Sec. 3.4, Fig. 1). */
+ * cell edge, R = 2M+1 odd, 5 <= R <= 513 (M <= 256), the number of symmetric
+ * sinc nodes (the rule is not uniform in h, Remark after Lemma 2: R grows with
+ * n), c0 > 0 the step constant (2.15 in Sec. 3.4, Fig. 1).  Larger R is
+ * rejected with DEMAG_EUNSUPPORTED; demag_compress_kernel takes R <= 129. */
 typedef struct {
   int n[3];
   double h[3];
@@ -476,7 +478,11 @@ demag_status demag_sync_status(demag_plan* plan, void* stream);
  * before anything is launched.
  * The first call on a device looks up the array's device address (once per
  * device, with that device current); make that first call before any stream
- * capture.  Every call on a device uses the same array and leaves its
+ * capture.  The address is kept for the life of the process: after
+ * cudaDeviceReset, or anything else that destroys the device's primary
+ * context, the module may be loaded again elsewhere and the kept address is
+ * stale, so this call must not be used on that device again in the same
+ * process.  Every call on a device uses the same array and leaves its
  * contents there; nothing in it has to start at zero.  Calls whose work can
  * overlap on the GPU (other streams, other host threads) race on the array:
  * serialise them.  Errors are reported through demag_last_error(NULL). */

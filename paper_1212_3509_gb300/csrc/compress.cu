@@ -78,7 +78,7 @@ __device__ double block_sum(double v, double* red) {
 // factorisation then holds to 1e-12 of each column.
 __global__ void __launch_bounds__(256) cmp_qr_kernel(int M, int glen, int m0, int m1, int m2, const double* gen,
                                                      double* Q, double* Rm) {
-  __shared__ double coef[kMaxTerms];
+  __shared__ double coef[kMaxCompressTerms];
   __shared__ double red[32];
   const int j = blockIdx.x, axis = j % 3, type = j / 3;
   const int m = axis == 0 ? m0 : (axis == 1 ? m1 : m2);
@@ -248,7 +248,7 @@ __device__ void mode_matrix(int M, int n, const double* Rp, const double* Rs, co
 // indices (a padding index stays decoupled), eigenvectors written column i of
 // Vout [M][M].  Returns nothing; eig gets M values.
 __device__ void sorted_out(int M, int n, const double* A, const double* V, double* eig, double* Vout) {
-  __shared__ int ord[kMaxTerms];
+  __shared__ int ord[kMaxCompressTerms];
   if (threadIdx.x == 0) {
     for (int i = 0; i < M; ++i) ord[i] = i;
     for (int i = 0; i < M; ++i) {
@@ -497,7 +497,7 @@ __global__ void rc_range_kernel(int n, int cols, int k, const double* W, const d
 
 // QR of a column-major [M][m] matrix by the same CGS (three passes, 1e-12 drop) as cmp_qr_kernel
 __global__ void __launch_bounds__(256) rc_qr_kernel(int M, int m, const double* A, double* Q, double* R) {
-  __shared__ double coef[kMaxTerms];
+  __shared__ double coef[kMaxCompressTerms];
   __shared__ double red[32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int i = threadIdx.x; i < M * M; i += blockDim.x) R[i] = 0.0;
@@ -811,6 +811,9 @@ extern "C" demag_status demag_compress_kernel(demag_plan* P, double tol, void* s
   if (!P->sympair || !P->twid[0])
     return set_error(P, DEMAG_EUNSUPPORTED, "demag_compress_kernel: n_p up to %d supported by the FFT path",
                      1 << kMaxFFTLog);
+  if (P->M > kMaxCompressTerms)
+    return set_error(P, DEMAG_EUNSUPPORTED, "demag_compress_kernel: M = %d terms, at most %d (R <= %d) supported",
+                     P->M, kMaxCompressTerms, 2 * kMaxCompressTerms + 1);
   cudaStream_t st = (cudaStream_t)stream;
   const int M = P->M, glen = P->glen, n = M + (M & 1);
   const int m[3] = {2 * P->n[0] - 1, 2 * P->n[1] - 1, 2 * P->n[2] - 1};

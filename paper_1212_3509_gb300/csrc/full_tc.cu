@@ -25,9 +25,26 @@
 // A launch runs one or several "groups": a group is one GEMM stage of one
 // grid (tensor maps, shapes, a job table and a pair table in device memory,
 // built once per plan).  A tile is (group, job, 128-row block, BN-column
-// block); a job is one output field with a list of (A field, B matrix) pairs
-// whose contractions it sums.  Several grids of different shapes therefore run
-// a stage in one persistent launch.
+// block); a job is one output field (or one half of it, below) with a list of
+// (A field, B matrix) pairs whose contractions it sums.  Several grids of
+// different shapes therefore run a stage in one persistent launch.
+//
+// Even / odd halves.  On a uniform grid every 1D factor is Toeplitz with an
+// even generator (E, Eq. f_anal) or an odd one (F), so with J the reversal of
+// an axis J E J = E and J F J = -F (centro-symmetric and skew
+// centro-symmetric).  Writing an axis of n cells (padded by one empty cell
+// to n_e = 2h when n is odd) as x+_j = x_j + x_{n_e-1-j}, x-_j = x_j - x_{n_e-1-j},
+// j < h, turns E into diag(E+, E-) and F into [[0, F-], [F+, 0]] with the
+// h x h blocks
+//     T+-[a][j] = T[a - j] +- T[a - (n_e - 1 - j)]
+// (terms with |d| >= n vanish): y+ = E+ x+, y- = E- x- and y+ = F- x-,
+// y- = F+ x+.  The input is folded once on every axis longer than 16 cells
+// (fold_split_kernel), each mode product then contracts h instead of n
+// entries (half the MMAs), and the node-sum reduction unfolds the potential
+// (x_j = (x+ + x-)/2, x_{n_e-1-j} = (x+ - x-)/2).  In the split layout a folded
+// axis has extent 2 hq (the odd half starts at hq = h rounded up to a 16-byte
+// multiple); a job covers one output half, and a pair's contraction reads the
+// input half given by its factor type.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -61,10 +78,6 @@ constexpr int kOutBufsPerWarp = kOutStaging / (kOutBuf * kEpiWarps);
 constexpr int kSmemBytes = kStages * kStageBytes + kOutStaging + kBarBytes + 1024;
 constexpr int kTcThreads = 64 + 32 * kEpiWarps;
 constexpr int kRing = 4;                           // tile ids handed from the producer to the other roles
-#ifndef DEMAG_TC_ROW_GROUP
-#define DEMAG_TC_ROW_GROUP 1
-#endif
-constexpr int kRowGroup = DEMAG_TC_ROW_GROUP;      // default row blocks per super-block of the tile order
 constexpr uint64_t kWaitNs = 2000000000ull;        // 2 s bound on every wait
 constexpr uint32_t kSwizzle64 = 4;                 // descriptor code of SWIZZLE_64B
 constexpr uint32_t kSBO = 8 * kRowBytes;           // 8 rows x 64 bytes per swizzle atom
@@ -117,58 +130,93 @@ struct Tf32Form {
 };
 
 struct TcJob {
-  int pair0, npairs, out_field, pad;
+  int pair0, npairs, out_field;
+  int half;                            // output half (0 even, 1 odd; 0 on an axis not folded)
 };
 
-// One GEMM stage of one grid, in device memory (64-byte aligned for the maps).
-struct alignas(64) TcGroup {
-  CUtensorMap a_hi, a_lo, b_hi, b_lo;  // 3D maps: (K, rows, field | matrix)
-  CUtensorMap o_hi, o_lo;              // 4D output maps (inner, outer, a, field) when tma_out
+// One GEMM stage of one grid, in device memory (aligned as its tensor maps).
+struct alignas(128) TcGroup {
+  CUtensorMap a_hi, a_lo;              // 3D maps: (K, rows, field)
+  CUtensorMap b_hi, b_lo;              // 4D maps: (K, a, half, matrix)
+  CUtensorMap o_hi, o_lo;              // 5D output maps (inner, outer, a, half, field) when tma_out
   const TcJob* jobs;
-  const short2* pairs;                 // (A field, B matrix)
+  const short2* pairs;                 // (A field, B matrix 2k + type)
   void* out_hi;                        // split: hi plane base; f32: float base
   void* out_lo;                        // split: lo plane base
   long long field_elems;               // elements per output field
   long long s_a;                       // output stride of the column index a
   int ldC, n_inner;                    // output row stride and row split (outer, inner)
   int rows, n_a, kblocks, bn, mode, tma_out;
+  int hq;                              // folded axis: start of the odd half (K and output columns), else 0
+  int pxor;                            // 1 when type 0 factors are the odd ones (derivative factors)
   float alpha;
   int njobs, m_tiles, n_tiles, ntiles;
-  int rgroup;                          // row blocks per super-block of the tile order
+};
+
+// A launch's tiles are cut into segments, contiguous in launch order: each a
+// block of jobs and row blocks of one group (tile order inside: row block,
+// then job, then column tile), with field offsets for the A operand and the
+// output (ring buffers), an optional dependency (a counter that must reach a
+// value before the segment's operands are loaded) and an optional completion
+// counter (each epilogue warp adds 1 after its stores of a tile are visible).
+struct TcSeg {
+  int group;                           // index into TcLaunch::groups
+  int tile0;                           // first launch tile of the segment
+  int job0, njobs;                     // jobs [job0, job0 + njobs) of the group
+  int rb0, nrb;                        // row blocks [rb0, rb0 + nrb)
+  int a_fofs, o_fofs;                  // added to every A field / output field
+  int dep, dep_target;                 // wait for counters[dep] >= dep_target (dep < 0: none)
+  int done;                            // completion counter (< 0: none)
+  int pad;
 };
 
 struct TcLaunch {
   const TcGroup* groups;               // device array
-  const int* tile0;                    // device prefix sums of group tiles, [ngroups + 1]
-  int ngroups, total_tiles;
+  const TcSeg* segs;                   // device array, ascending tile0
+  int nsegs, total_tiles;
   int* tile_counter;                   // zeroed before the launch
+  int* counters;                       // dependency counters, zeroed before the launch (or NULL)
   int* status;
 };
 
-__device__ __forceinline__ void tile_coords(const TcLaunch& L, int tile, int& g, int& j, int& mt, int& nt) {
-  int lo = 0, hi = L.ngroups - 1;
-  while (lo < hi) {  // last group whose first tile <= tile
+struct TileRef {
+  int seg, g, j, mt, nt;
+};
+
+__device__ __forceinline__ TileRef tile_coords(const TcLaunch& L, int tile) {
+  int lo = 0, hi = L.nsegs - 1;
+  while (lo < hi) {  // last segment whose first tile <= tile
     const int mid = (lo + hi + 1) >> 1;
-    if (__ldg(L.tile0 + mid) <= tile) lo = mid; else hi = mid - 1;
+    if (__ldg(&L.segs[mid].tile0) <= tile) lo = mid; else hi = mid - 1;
   }
-  g = lo;
-  const TcGroup& G = L.groups[g];
-  int t = tile - __ldg(L.tile0 + g);
-  // Tile order: super-blocks of `rgroup` row blocks; inside one, every job
-  // in turn over all of its row blocks (column tiles fastest).  rgroup = 1
-  // (the default) runs all jobs of one row block back to back, so the A rows
-  // they share are read from L2; larger groups make concurrently running
-  // tiles write neighbouring rows of one field instead (measured no faster on
-  // 160^3-256^3 grids, kept as a compile-time option).
-  const int per_sb = G.njobs * G.rgroup * G.n_tiles;
-  const int sb = t / per_sb;
-  t -= sb * per_sb;
-  const int rb0 = sb * G.rgroup;
-  const int gsb = min(G.rgroup, G.m_tiles - rb0);  // row blocks in this super-block
-  nt = t % G.n_tiles;
+  const TcSeg& S = L.segs[lo];
+  const TcGroup& G = L.groups[S.group];
+  int t = tile - S.tile0;
+  TileRef r;
+  r.seg = lo;
+  r.g = S.group;
+  r.nt = t % G.n_tiles;
   t /= G.n_tiles;
-  mt = rb0 + t % gsb;
-  j = t / gsb;
+  r.j = S.job0 + t % S.njobs;
+  r.mt = S.rb0 + t / S.njobs;
+  return r;
+}
+
+// Count one epilogue warp's part of `count` finished tiles on completion
+// counter `ctr`: their stores must be visible at GPU scope first.  TMA stores:
+// all but the `keep` newest bulk groups of lane 0 (a later tile's) must be
+// complete; direct stores: the warp's lanes are ordered before lane 0's release.
+__device__ __forceinline__ void epi_signal(int* counters, int ctr, int count, bool tma, int keep, int lane) {
+  __syncwarp();
+  if (lane == 0) {
+    if (tma) {
+      ptx::bulk_wait_keep(keep);
+      ptx::fence_proxy_async_global();
+    }
+    __threadfence();
+    ptx::red_release_gpu_add(counters + ctr, count);
+  }
+  __syncwarp();
 }
 
 __device__ __forceinline__ void tc_fail(volatile int* abort, int* status) {
@@ -227,6 +275,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const __grid_con
       uint32_t ph = 0;
       int rs = 0;
       uint32_t rph = 0;
+      int met_dep = -1, met_target = 0;  // last dependency seen satisfied (counters only grow)
       while (!*abort) {
         // take the next tile and hand its id to the MMA and epilogue roles
         if (!ptx::mbar_wait(&sempty[rs], rph ^ 1, abort, kWaitNs)) {
@@ -238,13 +287,28 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const __grid_con
         ptx::mbar_arrive(&sfull[rs]);
         if (++rs == kRing) { rs = 0; rph ^= 1; }
         if (tile >= L.total_tiles) break;
-        int g, j, mt, nt;
-        tile_coords(L, tile, g, j, mt, nt);
-        const TcGroup& G = L.groups[g];
-        const TcJob J = G.jobs[j];
+        const TileRef tr = tile_coords(L, tile);
+        const TcSeg& SG = L.segs[tr.seg];
+        const TcGroup& G = L.groups[tr.g];
+        const TcJob J = G.jobs[tr.j];
+        const int mt = tr.mt, nt = tr.nt;
+        if (SG.dep >= 0 && !(SG.dep == met_dep && SG.dep_target <= met_target)) {
+          // the operands of this segment are written by earlier tiles of the launch
+          if (!ptx::counter_wait(L.counters + SG.dep, SG.dep_target, abort, kWaitNs)) {
+            tc_fail(abort, L.status);
+            break;
+          }
+          ptx::fence_proxy_async_global();  // their generic-proxy release before our TMA reads
+          met_dep = SG.dep;
+          met_target = SG.dep_target;
+        }
         const uint32_t bytes = 2 * kTileA + 2 * (uint32_t)G.bn * kRowBytes;
         for (int pi = 0; pi < J.npairs && !*abort; ++pi) {
-          const short2 pr = G.pairs[J.pair0 + pi];
+          short2 pr = G.pairs[J.pair0 + pi];
+          pr.x = (short)(pr.x + SG.a_fofs);
+          // input half read by this pair: the output half for an even factor,
+          // the other one for an odd factor
+          const int koff = ((J.half ^ (pr.y & 1) ^ G.pxor) & 1) * G.hq;
           for (int kb = 0; kb < G.kblocks; ++kb) {
             if (!ptx::mbar_wait(&empty[s], ph ^ 1, abort, kWaitNs)) {
               tc_fail(abort, L.status);
@@ -252,10 +316,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const __grid_con
             }
             uint8_t* st = smem + s * kStageBytes;
             ptx::mbar_arrive_expect_tx(&full[s], bytes);
-            ptx::tma_load_3d(st, &G.a_hi, &full[s], kb * F::kBK, mt * kBM, pr.x);
-            ptx::tma_load_3d(st + kTileA, &G.a_lo, &full[s], kb * F::kBK, mt * kBM, pr.x);
-            ptx::tma_load_3d(st + 2 * kTileA, &G.b_hi, &full[s], kb * F::kBK, nt * G.bn, pr.y);
-            ptx::tma_load_3d(st + 2 * kTileA + kTileB, &G.b_lo, &full[s], kb * F::kBK, nt * G.bn, pr.y);
+            ptx::tma_load_3d(st, &G.a_hi, &full[s], koff + kb * F::kBK, mt * kBM, pr.x);
+            ptx::tma_load_3d(st + kTileA, &G.a_lo, &full[s], koff + kb * F::kBK, mt * kBM, pr.x);
+            ptx::tma_load_4d(st + 2 * kTileA, &G.b_hi, &full[s], kb * F::kBK, nt * G.bn, J.half, pr.y);
+            ptx::tma_load_4d(st + 2 * kTileA + kTileB, &G.b_lo, &full[s], kb * F::kBK, nt * G.bn, J.half, pr.y);
             if (++s == kStages) { s = 0; ph ^= 1; }
           }
         }
@@ -277,10 +341,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const __grid_con
         ptx::mbar_arrive(&sempty[rs]);
         if (++rs == kRing) { rs = 0; rph ^= 1; }
         if (tile < 0) break;
-        int g, j, mt, nt;
-        tile_coords(L, tile, g, j, mt, nt);
-        const TcGroup& G = L.groups[g];
-        const TcJob J = G.jobs[j];
+        const TileRef tr = tile_coords(L, tile);
+        const TcGroup& G = L.groups[tr.g];
+        const TcJob J = G.jobs[tr.j];
         const uint32_t idesc = ptx::instr_desc(F::kFormat, kBM, (uint32_t)G.bn);
         const int kblocks = G.kblocks;
         if (!ptx::mbar_wait(&tempty[buf], tph ^ 1, abort, kWaitNs)) {
@@ -332,7 +395,20 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const __grid_con
     int rs = 0;
     uint32_t rph = 0;
     uint32_t chunk = 0;  // staged chunks of this warp so far: selects the staging buffer
+    // Finished tiles are counted on their completion counter in one release
+    // per run of tiles of the same counter: when a tile of another counter
+    // follows (after that tile's own stores are issued, so the earlier ones
+    // have had a tile's time to land), or as soon as the warp would otherwise
+    // wait for work.  A warp never waits while holding counts that a later
+    // tile may depend on.
+    int pend = -1;       // completion counter of the tiles not yet counted
+    int pend_n = 0;      // how many
+    bool pend_tma = false;
     while (!*abort) {
+      if (pend >= 0 && !ptx::mbar_try_wait(&sfull[rs], rph)) {
+        epi_signal(L.counters, pend, pend_n, pend_tma, 0, lane);
+        pend = -1;
+      }
       if (!ptx::mbar_wait(&sfull[rs], rph, abort, kWaitNs)) {
         tc_fail(abort, L.status);
         break;
@@ -342,15 +418,22 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const __grid_con
       if (lane == 0) ptx::mbar_arrive(&sempty[rs]);
       if (++rs == kRing) { rs = 0; rph ^= 1; }
       if (tile < 0) break;
-      int g, j, mt, nt;
-      tile_coords(L, tile, g, j, mt, nt);
-      const TcGroup& G = L.groups[g];
-      const int out_field = G.jobs[j].out_field;
+      const TileRef tr = tile_coords(L, tile);
+      const TcSeg& SG = L.segs[tr.seg];
+      const TcGroup& G = L.groups[tr.g];
+      const int out_field = G.jobs[tr.j].out_field + SG.o_fofs;
+      const int half = G.jobs[tr.j].half;
+      const int mt = tr.mt, nt = tr.nt;
+      if (pend >= 0 && !ptx::mbar_try_wait(&tfull[buf], tph)) {
+        epi_signal(L.counters, pend, pend_n, pend_tma, 0, lane);
+        pend = -1;
+      }
       if (!ptx::mbar_wait(&tfull[buf], tph, abort, kWaitNs)) {
         tc_fail(abort, L.status);
         break;
       }
       ptx::tc_fence_after();
+      int commits = 0;  // bulk groups lane 0 commits for this tile
       const uint32_t taddr = tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * kBN);
       const int a0 = nt * G.bn;
       const int bn = G.bn;
@@ -395,19 +478,23 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const __grid_con
           ptx::fence_proxy_async_smem();
           __syncwarp();
           if (lane == 0) {
-            ptx::tma_store_4d(&G.o_hi, sb, inner_w, outer_w, a0 + c0, out_field);
+            // the map's column extent is the half's valid count: columns past
+            // it (padding, or the other half) are not written
+            ptx::tma_store_5d(&G.o_hi, sb, inner_w, outer_w, a0 + c0, half, out_field);
             if (mode == kOutSplit)
-              ptx::tma_store_4d(&G.o_lo, sb + 32 * 32 * sizeof(T), inner_w, outer_w, a0 + c0, out_field);
+              ptx::tma_store_5d(&G.o_lo, sb + 32 * 32 * sizeof(T), inner_w, outer_w, a0 + c0, half, out_field);
             ptx::bulk_commit();
           }
+          ++commits;
         }
       } else {
         const int row = mt * kBM + rloc;
         const bool valid = row < G.rows;
         const int outer = row / n_inner, inner = row - outer * n_inner;
         const long long s_a = G.s_a;
-        const long long rbase = (long long)out_field * G.field_elems + (long long)outer * G.ldC + inner;
-        const int acount = min(bn, G.n_a - a0);  // columns of this tile that exist
+        const long long rbase = (long long)out_field * G.field_elems + (long long)outer * G.ldC + inner +
+                                (long long)(half * G.hq) * s_a;
+        const int acount = min(bn, G.n_a - a0);  // columns of this tile that exist (in its half)
         for (int c0 = 32 * slice; c0 < bn; c0 += 32 * kEpiSlices) {
           uint32_t r[32];
           ptx::tmem_ld32(taddr + (uint32_t)c0, r);
@@ -442,7 +529,21 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const __grid_con
       if (lane == 0) ptx::mbar_arrive(&tempty[buf]);
       buf ^= 1;
       if (buf == 0) tph ^= 1;
+      if (pend >= 0 && pend != SG.done) {  // earlier tiles' stores: all but this tile's newest groups
+        epi_signal(L.counters, pend, pend_n, pend_tma, G.tma_out ? commits : 0, lane);
+        pend = -1;
+      }
+      if (SG.done >= 0) {  // later tiles of the launch read what this tile wrote
+        if (pend < 0) {
+          pend = SG.done;
+          pend_n = 0;
+          pend_tma = false;
+        }
+        ++pend_n;
+        pend_tma = pend_tma || G.tma_out != 0;
+      }
     }
+    if (pend >= 0) epi_signal(L.counters, pend, pend_n, pend_tma, 0, lane);
     if (lane == 0) ptx::bulk_wait_all();  // staged stores finished before the block exits
   }
 
@@ -474,76 +575,144 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const __grid_con
 // indices only grow, so it finds its item by advancing from the last one.
 constexpr int kMaxItems = 128;
 
-struct SplitItem {
-  const float* x;      // [rows][n] FP32
-  void* hi;            // [rows][ld] planes
+// Geometry of one grid in the split layout: per axis the cell count n, the
+// valid entries per half h, the start of the odd half hq and the extent ext
+// (2 hq on a folded axis; n, h = n, hq = 0 otherwise).
+struct AxisGeo {
+  int n[3], h[3], hq[3], ext[3];
+};
+
+struct FoldItem {
+  const float* x;      // [fields][n3][n2][n1] FP32
+  void* hi;            // [fields][ext3][ext2][ld1] planes
   void* lo;
-  long long begin;     // first flat index of this item
-  int n, ld;
-  int vec;             // n % 4 == 0 and x 16-byte aligned
+  long long begin;     // first row of this item in the launch's row space
+  AxisGeo g;
+  int ld1;
 };
 
-struct SplitList {
+struct FoldList {
   int count;
-  long long total;
-  SplitItem it[kMaxItems];
+  long long total;     // rows (field, j3, j2) over all items
+  FoldItem it[kMaxItems];
 };
 
-// hi/lo split of [rows][n] FP32 tensors into [rows][ld] planes.  The flat
-// index space counts groups of four consecutive elements of a row (rows are
-// padded to a multiple of four), so a row with n % 4 == 0 moves as 16-byte
-// loads and 4-element stores.
+// Orbit counts per axis: a folded axis has hq positions per half (the last
+// hq - h of them padding), an axis not folded n.
+__device__ __forceinline__ int orbit_count(const AxisGeo& g, int p) { return g.hq[p] ? g.hq[p] : g.n[p]; }
+
+// Fold every folded axis of [fields][n3][n2][n1] FP32 tensors into even / odd
+// halves (x+- = x_j +- x_{n_e-1-j}, the padding cell of an odd axis being 0)
+// and split the result into hi / lo planes.  A block takes one orbit row
+// (field, j3, j2) at a time; its threads take the orbits j1 of the row: each
+// reads the up to 8 cells (j or n_e-1-j on each folded axis) once and writes
+// the up to 8 folded entries (even or odd half on each folded axis), so reads
+// and writes are coalesced along i1.
 template <class F>
-__global__ void split_rows_kernel(const __grid_constant__ SplitList L) {
+__global__ void __launch_bounds__(128) fold_split_kernel(const __grid_constant__ FoldList L) {
   using T = typename F::T;
   int item = 0;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < L.total;
-       i += (long long)gridDim.x * blockDim.x) {
-    while (item + 1 < L.count && i >= L.it[item + 1].begin) ++item;
-    const SplitItem& S = L.it[item];
-    const int quads = (S.n + 3) >> 2;
-    const long long e = i - S.begin;
-    const long long r = e / quads;
-    const int c = (int)(e - r * quads) * 4;
-    const float* src = S.x + r * S.n + c;
-    T* hi = reinterpret_cast<T*>(S.hi) + r * S.ld + c;
-    T* lo = reinterpret_cast<T*>(S.lo) + r * S.ld + c;
-    if (S.vec) {
-      const float4 v = *reinterpret_cast<const float4*>(src);
-      const float vv[4] = {v.x, v.y, v.z, v.w};
-      T h[4], l[4];
+  for (long long r = blockIdx.x; r < L.total; r += gridDim.x) {
+    while (item + 1 < L.count && r >= L.it[item + 1].begin) ++item;
+    const FoldItem& S = L.it[item];
+    const AxisGeo& g = S.g;
+    const int c1 = orbit_count(g, 0), c2 = orbit_count(g, 1), c3 = orbit_count(g, 2);
+    int e = (int)(r - S.begin);
+    const int j2 = e % c2;
+    e /= c2;
+    const int j3 = e % c3;
+    const int q = e / c3;
+    const int f1 = g.hq[0] ? 1 : 0, f2 = g.hq[1] ? 1 : 0, f3 = g.hq[2] ? 1 : 0;
+    const bool live = j2 < g.h[1] && j3 < g.h[2];
+    // source rows for (e3, e2) and destination rows for (s3, s2), index e2 + 2 e3
+    const float* src[4];
+    long long dst[4];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) F::split(vv[j], h[j], l[j]);
-      F::store4(hi, h);
-      F::store4(lo, l);
-    } else {
-      for (int j = 0; j < 4 && c + j < S.n; ++j) F::split(src[j], hi[j], lo[j]);
+    for (int k = 0; k < 4; ++k) {
+      const int b2 = k & 1, b3 = k >> 1;
+      const int m2 = b2 ? 2 * g.h[1] - 1 - j2 : j2, m3 = b3 ? 2 * g.h[2] - 1 - j3 : j3;
+      const bool ok = live && b2 <= f2 && b3 <= f3 && m2 < g.n[1] && m3 < g.n[2];
+      src[k] = ok ? S.x + (((long long)q * g.n[2] + m3) * g.n[1] + m2) * g.n[0] : nullptr;
+      dst[k] = (b2 <= f2 && b3 <= f3)
+                   ? (((long long)q * g.ext[2] + b3 * g.hq[2] + j3) * g.ext[1] + b2 * g.hq[1] + j2) * S.ld1
+                   : -1;
+    }
+    for (int j1 = threadIdx.x; j1 < c1; j1 += blockDim.x) {
+      const bool l1 = j1 < g.h[0];
+      const int m1[2] = {j1, 2 * g.h[0] - 1 - j1};
+      float v[8];  // [e3][e2][e1], then [s3][s2][s1] after the butterflies
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int b1 = k & 1, row = k >> 1;
+        float x = 0.f;
+        if (src[row] && l1 && b1 <= f1 && m1[b1] < g.n[0]) x = __ldg(src[row] + m1[b1]);
+        v[k] = x;
+      }
+      const int fl[3] = {f1, f2, f3};
+#pragma unroll
+      for (int p = 0; p < 3; ++p) {
+        if (!fl[p]) continue;
+        const int bit = 1 << p;
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+          if (!(k & bit)) {
+            const float a = v[k], b = v[k | bit];
+            v[k] = a + b;
+            v[k | bit] = a - b;
+          }
+      }
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int b1 = k & 1, row = k >> 1;
+        if (dst[row] < 0 || b1 > f1) continue;
+        const long long o = dst[row] + b1 * g.hq[0] + j1;
+        T h, l;
+        F::split(v[k], h, l);
+        reinterpret_cast<T*>(S.hi)[o] = h;
+        reinterpret_cast<T*>(S.lo)[o] = l;
+      }
     }
   }
 }
 
-// Dense Toeplitz factors of one axis, hi/lo, [M][2][n][ld]; the third axis
-// carries the scale c s omega_k.
+// Dense factors of one axis, hi/lo: on an axis not folded the Toeplitz
+// matrix [M][2][n][ldB] (or the non-uniform grid's full matrix); on a folded
+// axis the blocks [M][2][2 halves][h][ldB] of the header (even half: T+ for
+// an even factor, T- for an odd one; odd half: the other sign).  The third
+// axis carries the scale c s omega_k.  pxor = 1 swaps the parity of the two
+// factor types (the derivative factors of the stray field: dE odd, dF even).
 template <class F>
-__global__ void tc_factor_kernel(int M, int glen, int axis, int n, int ld, const double* gen, const double* scale,
-                                 typename F::T* hi, typename F::T* lo, const double* fac, size_t tgroup,
-                                 size_t toff) {
-  const long long total = (long long)M * 2 * n * n;
+__global__ void tc_factor_kernel(int M, int glen, int axis, int n, int h, int halves, int ldB, int pxor,
+                                 const double* gen, const double* scale, typename F::T* hi, typename F::T* lo,
+                                 const double* fac, size_t tgroup, size_t toff) {
+  const long long total = (long long)M * 2 * halves * h * h;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
-    const int jj = (int)(i % n);
-    const long long t = i / n;
-    const int ii = (int)(t % n);
-    const int kt = (int)(t / n);  // k*2 + type
-    // Toeplitz generator (uniform grid) or the full matrix (non-uniform grid)
-    double v = fac ? fac[(size_t)kt * tgroup + toff + (size_t)ii * n + jj]
-                   : gen[((long long)kt * 3 + axis) * glen + (ii - jj + n - 1)];
+    const int jj = (int)(i % h);
+    long long t = i / h;
+    const int ii = (int)(t % h);
+    t /= h;
+    const int half = (int)(t % halves);
+    const int kt = (int)(t / halves);  // k*2 + type
+    const double* row = gen + ((long long)kt * 3 + axis) * glen + (n - 1);  // row[d] = T[d], |d| < n
+    double v;
+    if (fac) {
+      v = fac[(size_t)kt * tgroup + toff + (size_t)ii * n + jj];  // non-uniform grid: never folded
+    } else if (halves == 1) {
+      v = row[ii - jj];
+    } else {
+      const int jm = 2 * h - 1 - jj;
+      const int dm = ii - jm;
+      const double t2 = (dm > -n && dm < n) ? row[dm] : 0.0;
+      const bool even = ((kt & 1) ^ pxor) == 0;
+      v = ((half == 0) == even) ? row[ii - jj] + t2 : row[ii - jj] - t2;
+    }
     if (axis == 2) v *= scale[kt / 2];
-    typename F::T h, l;
-    F::split((float)v, h, l);
-    const long long o = ((long long)kt * n + ii) * ld + jj;
-    hi[o] = h;
-    lo[o] = l;
+    typename F::T hv, lv;
+    F::split((float)v, hv, lv);
+    const long long o = (((long long)kt * halves + half) * h + ii) * ldB + jj;
+    hi[o] = hv;
+    lo[o] = lv;
   }
 }
 
@@ -559,20 +728,19 @@ static int pairs_per_split(int kblocks, int budget) {
   return pp < 1 ? 1 : pp;
 }
 
-struct ReduceItem {
-  const float* part;   // [nout][groups][N] partial fields
-  float* out;          // [nout][N]
-  long long begin;     // first flat index of this item
-  long long N;
+struct UnfoldItem {
+  const float* part;   // [nout][groups][ext3][ext2][ext1] partial fields
+  float* out;          // [nout][n3][n2][n1]
+  long long begin;     // first row of this item in the launch's row space
+  AxisGeo g;
   int groups;
-  float alpha;
-  int vec;             // N % 4 == 0 and out 16-byte aligned: groups of four elements
+  float alpha;         // includes 1/2 per folded axis
 };
 
-struct ReduceList {
+struct UnfoldList {
   int count;
-  long long total;
-  ReduceItem it[kMaxItems];
+  long long total;     // rows (output field, j3, j2) over all items
+  UnfoldItem it[kMaxItems];
 };
 
 // Neumaier's compensated sum: s + c carries the exact sum of the terms to a
@@ -588,36 +756,84 @@ struct Csum {
   __device__ __forceinline__ float value() const { return s + c; }
 };
 
-// out[q][i] = alpha * sum_g part[q*groups + g][i], compensated; the flat index
-// space counts groups of four elements when N % 4 == 0 (16-byte accesses)
-__global__ void reduce_parts_kernel(const __grid_constant__ ReduceList L) {
+// out[q] = alpha * unfold(sum_g part[q][g]): the node-sum partial fields are
+// summed (compensated), then every folded axis is unfolded
+// (x_j = x+ + x-, x_{n_e-1-j} = x+ - x-, the 1/2 in alpha).  A block takes one
+// orbit row (field, j3, j2) of valid entries (j < h) at a time, its threads
+// the orbits j1 of the row; the loads of up to kUnfoldBatch partial fields
+// are issued together before they are summed.
+constexpr int kUnfoldBatch = 4;
+
+__global__ void __launch_bounds__(128) unfold_reduce_kernel(const __grid_constant__ UnfoldList L) {
   int item = 0;
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < L.total;
-       idx += (long long)gridDim.x * blockDim.x) {
-    while (item + 1 < L.count && idx >= L.it[item + 1].begin) ++item;
-    const ReduceItem& R = L.it[item];
-    const long long e = idx - R.begin;
-    if (R.vec) {
-      const long long nq = R.N >> 2;
-      const long long q = e / nq, i4 = e - q * nq;
-      const float4* src = reinterpret_cast<const float4*>(R.part + q * R.groups * R.N) + i4;
-      Csum a[4];
-      for (int g = 0; g < R.groups; ++g) {
-        const float4 v = src[g * nq];
-        a[0].add(v.x);
-        a[1].add(v.y);
-        a[2].add(v.z);
-        a[3].add(v.w);
+  for (long long r = blockIdx.x; r < L.total; r += gridDim.x) {
+    while (item + 1 < L.count && r >= L.it[item + 1].begin) ++item;
+    const UnfoldItem& R = L.it[item];
+    const AxisGeo& g = R.g;
+    int e = (int)(r - R.begin);
+    const int j2 = e % g.h[1];
+    e /= g.h[1];
+    const int j3 = e % g.h[2];
+    const int q = e / g.h[2];
+    const int f1 = g.hq[0] ? 1 : 0, f2 = g.hq[1] ? 1 : 0, f3 = g.hq[2] ? 1 : 0;
+    const long long fe = (long long)g.ext[0] * g.ext[1] * g.ext[2];
+    const float* base = R.part + (long long)q * R.groups * fe;
+    // source rows for (s3, s2) and destination rows for (e3, e2), index b2 + 2 b3
+    const float* src[4];
+    float* dst[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int b2 = k & 1, b3 = k >> 1;
+      const bool on = b2 <= f2 && b3 <= f3;
+      src[k] = on ? base + ((long long)(b3 * g.hq[2] + j3) * g.ext[1] + b2 * g.hq[1] + j2) * g.ext[0] : nullptr;
+      const int m2 = b2 ? 2 * g.h[1] - 1 - j2 : j2, m3 = b3 ? 2 * g.h[2] - 1 - j3 : j3;
+      dst[k] = (on && m2 < g.n[1] && m3 < g.n[2])
+                   ? R.out + (((long long)q * g.n[2] + m3) * g.n[1] + m2) * g.n[0]
+                   : nullptr;
+    }
+    for (int j1 = threadIdx.x; j1 < g.h[0]; j1 += blockDim.x) {
+      Csum a[8];
+      for (int g0 = 0; g0 < R.groups; g0 += kUnfoldBatch) {
+        const int ng = min(kUnfoldBatch, R.groups - g0);
+        float x[8][kUnfoldBatch];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const int b1 = k & 1, row = k >> 1;
+#pragma unroll
+          for (int gi = 0; gi < kUnfoldBatch; ++gi)
+            x[k][gi] = (src[row] && b1 <= f1 && gi < ng)
+                           ? __ldg(src[row] + (g0 + gi) * fe + b1 * g.hq[0] + j1)
+                           : 0.f;
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+#pragma unroll
+          for (int gi = 0; gi < kUnfoldBatch; ++gi)
+            if (gi < ng) a[k].add(x[k][gi]);
       }
-      reinterpret_cast<float4*>(R.out + q * R.N)[i4] =
-          make_float4(R.alpha * a[0].value(), R.alpha * a[1].value(), R.alpha * a[2].value(),
-                      R.alpha * a[3].value());
-    } else {
-      const long long q = e / R.N, i = e - q * R.N;
-      const float* src = R.part + q * R.groups * R.N + i;
-      Csum a;
-      for (int g = 0; g < R.groups; ++g) a.add(src[g * R.N]);
-      R.out[e] = R.alpha * a.value();
+      float v[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) v[k] = a[k].value();
+      const int fl[3] = {f1, f2, f3};
+#pragma unroll
+      for (int p = 0; p < 3; ++p) {
+        if (!fl[p]) continue;
+        const int bit = 1 << p;
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+          if (!(k & bit)) {
+            const float u = v[k], w = v[k | bit];
+            v[k] = u + w;
+            v[k | bit] = u - w;
+          }
+      }
+      const int m1[2] = {j1, 2 * g.h[0] - 1 - j1};
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int b1 = k & 1, row = k >> 1;
+        if (!dst[row] || b1 > f1 || m1[b1] >= g.n[0]) continue;
+        dst[row][m1[b1]] = R.alpha * v[k];
+      }
     }
   }
 }
@@ -750,19 +966,40 @@ static bool make_map(CUtensorMap* m, void* base, int elem_bytes, uint64_t dim0, 
   return r == CUDA_SUCCESS;
 }
 
-// 4D map over an output field set: (inner, outer, a, field) with the given
-// strides in elements; box (32, 1, 32, 1) = one epilogue warp's 32 rows x 32
-// output columns, no swizzle.
-static bool make_out_map(CUtensorMap* m, void* base, int elem_bytes, uint64_t inner, uint64_t outer, uint64_t na,
-                         uint64_t fields, uint64_t ld, uint64_t s_a, uint64_t field_elems) {
+// 4D map over the factor blocks of one axis [2M][halves][h][ldB]:
+// (K, a, half, matrix), box (64 bytes, box1, 1, 1), 64B swizzle.  Columns and
+// rows past h read as zeros.
+static bool make_bmap(CUtensorMap* m, void* base, int elem_bytes, uint64_t h, uint64_t halves, uint64_t mats,
+                      uint64_t ldB, uint32_t box1) {
   EncodeTiledFn enc = encode_fn();
   if (!enc) return false;
-  cuuint64_t dims[4] = {inner, outer, na, fields};
-  cuuint64_t strides[3] = {ld * elem_bytes, s_a * elem_bytes, field_elems * elem_bytes};
-  cuuint32_t box[4] = {32, 1, 32, 1};
+  cuuint64_t dims[4] = {h, h, halves, mats};
+  cuuint64_t strides[3] = {ldB * elem_bytes, ldB * h * elem_bytes, ldB * h * halves * elem_bytes};
+  cuuint32_t box[4] = {(cuuint32_t)(kRowBytes / elem_bytes), box1, 1, 1};
   cuuint32_t estr[4] = {1, 1, 1, 1};
   const CUtensorMapDataType dt = elem_bytes == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
   CUresult r = enc(m, dt, 4, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+// 5D map over an output field set: (inner, outer, a, half, field) with the
+// given strides in elements, the column index a limited to the na valid
+// columns of a half (the odd half starts hq columns after the even one);
+// box (32, 1, 32, 1, 1) = one epilogue warp's 32 rows x 32 output columns,
+// no swizzle.
+static bool make_out_map(CUtensorMap* m, void* base, int elem_bytes, uint64_t inner, uint64_t outer, uint64_t na,
+                         uint64_t halves, uint64_t hq, uint64_t fields, uint64_t ld, uint64_t s_a,
+                         uint64_t field_elems) {
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return false;
+  cuuint64_t dims[5] = {inner, outer, na, halves, fields};
+  const uint64_t s_half = (halves > 1 ? hq : na) * s_a;
+  cuuint64_t strides[4] = {ld * elem_bytes, s_a * elem_bytes, s_half * elem_bytes, field_elems * elem_bytes};
+  cuuint32_t box[5] = {32, 1, 32, 1, 1};
+  cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+  const CUtensorMapDataType dt = elem_bytes == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  CUresult r = enc(m, dt, 5, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
@@ -775,12 +1012,15 @@ enum { kFwd1 = 0, kFwd2, kFwd3, kAdj1, kAdj2, kAdj3, kPrograms };
 // Per-plan, per-form tensor-core state.
 struct TcState {
   int elem;               // bytes per element (2 BF16, 4 TF32)
-  int ld[3];              // padded row lengths (16-byte multiples)
+  AxisGeo geo;            // split layout per axis (folded into halves or not)
+  int halves[3];          // 2 on a folded axis, else 1
+  int ld[3];              // padded row lengths of the extents (16-byte multiples)
+  int ldB[3];             // padded row length of the factor blocks
   int bn[3];              // N tile width per axis
-  void* B[3][2];          // per axis: hi / lo factors [M][2][n][ld]
-  void* X[2];             // split input: [3][n3 n2][ld1]
-  void* buf1[2];          // [3M][n1 n3][ld2]
-  void* buf2[2];          // [3M][n2 n1][ld3]
+  void* B[3][2];          // per axis: hi / lo factors [M][2][halves][h][ldB]
+  void* X[2];             // split input: [3][ext3 ext2][ld1]
+  void* buf1[2];          // [3M][ext1 ext3][ld2]
+  void* buf2[2];          // [3M][ext2 ext1][ld3]
   int* status;
   int* counter;           // dynamic tile counter of the running launch
   float* part;            // split node-sum partial fields
@@ -792,7 +1032,7 @@ struct TcState {
   TcGroup* prog;          // device [kPrograms]
   TcJob* jobs;            // device, all programs
   short2* pairs;          // device, all programs
-  int* tile0;             // device [kPrograms][2]: {0, ntiles} for single-group launches
+  TcSeg* seg;             // device [kPrograms]: one whole-program segment each
   TcGroup host_prog[kPrograms];
   bool small[kPrograms];          // program runs on CUDA cores (axis of at most kSmallAxis cells)
   SmallStage small_prog[kPrograms];
@@ -802,20 +1042,23 @@ struct TcState {
   void* Bd[3][2];                 // per axis: hi / lo derivative factors [M][2][n][ld]
   TcGroup dprog_host[3];
   TcGroup* dprog;                 // device [3]
-  int* dtile0;                    // device [3][2]
+  TcSeg* dseg;                    // device [3]
   SmallStage small_dprog[3];
   size_t bytes;
 };
 
-// Grouped descriptors of the forward stages of several plans (one launch per
-// stage over all of them); owned by a plan's cache or by a captured graph.
+// The forward stages of several plans as one launch (every stage of every
+// grid, later stages of a grid waiting for its earlier ones); owned by a
+// plan's cache or by a captured graph.
 struct TcBatch {
   std::vector<demag_plan*> plans;
   std::vector<unsigned long long> serials;  // with the pointers, the cache key
   int prec = -1;
   TcGroup* groups = nullptr;           // device [3][count]
-  int* tile0 = nullptr;                // device [3][count + 1]
-  int total[3] = {0, 0, 0};
+  TcSeg* segs = nullptr;               // device [nsegs]
+  int nsegs = 0, total = 0;
+  int* ctr = nullptr;                  // device [1 + 2 count]: tile counter, then stage-done counters
+  int nctr = 0;
 };
 
 struct TcHolder {
@@ -830,16 +1073,39 @@ static TcState* state(demag_plan* P, demag_precision prec) {
   return H ? H->s[form_index(prec)] : nullptr;
 }
 
+// Split layout of a plan's grid for elements of `elem` bytes: every axis of a
+// uniform grid longer than kSmallAxis cells is folded into even / odd halves.
+struct TcGeo {
+  AxisGeo g;
+  int halves[3], ld[3], ldB[3];
+};
+
+static TcGeo tc_geometry(const demag_plan* P, int elem) {
+  const int al = 16 / elem;
+  TcGeo G;
+  for (int p = 0; p < 3; ++p) {
+    const int n = P->n[p];
+    const bool fold = !P->nonuniform && n > kSmallAxis;
+    G.g.n[p] = n;
+    G.g.h[p] = fold ? (n + 1) / 2 : n;
+    G.g.hq[p] = fold ? round_up(G.g.h[p], al) : 0;
+    G.g.ext[p] = fold ? 2 * G.g.hq[p] : n;
+    G.halves[p] = fold ? 2 : 1;
+    G.ld[p] = round_up(G.g.ext[p], al);
+    G.ldB[p] = round_up(G.g.h[p], al);
+  }
+  return G;
+}
+
 size_t tc_workspace_bytes(const demag_plan* P, demag_precision prec) {
   const size_t e = prec == DEMAG_TF32X3 ? 4 : 2;
-  const int al = (int)(16 / e);
+  const TcGeo G = tc_geometry(P, (int)e);
+  const size_t x1 = G.g.ext[0], x2 = G.g.ext[1], x3 = G.g.ext[2];
   size_t b = 0;
-  const int n1 = P->n[0], n2 = P->n[1], n3 = P->n[2];
-  const size_t l1 = round_up(n1, al), l2 = round_up(n2, al), l3 = round_up(n3, al);
-  for (int p = 0; p < 3; ++p) b += 2 * (size_t)P->M * 2 * P->n[p] * round_up(P->n[p], al) * e;
-  b += 2 * 3 * (size_t)n3 * n2 * l1 * e;
-  b += 2 * 3 * (size_t)P->M * n1 * n3 * l2 * e;
-  b += 2 * 3 * (size_t)P->M * n2 * n1 * l3 * e;
+  for (int p = 0; p < 3; ++p) b += 2 * (size_t)P->M * 2 * G.halves[p] * G.g.h[p] * G.ldB[p] * e;
+  b += 2 * 3 * x3 * x2 * G.ld[0] * e;
+  b += 2 * 3 * (size_t)P->M * x1 * x3 * G.ld[1] * e;
+  b += 2 * 3 * (size_t)P->M * x2 * x1 * G.ld[2] * e;
   return b;
 }
 
@@ -858,11 +1124,11 @@ static void free_state(TcState* S) {
   cudaFree(S->prog);
   cudaFree(S->jobs);
   cudaFree(S->pairs);
-  cudaFree(S->tile0);
+  cudaFree(S->seg);
   for (int p = 0; p < 3; ++p)
     for (int h = 0; h < 2; ++h) cudaFree(S->Bd[p][h]);
   cudaFree(S->dprog);
-  cudaFree(S->dtile0);
+  cudaFree(S->dseg);
   delete S;
 }
 
@@ -883,12 +1149,15 @@ static int grid_blocks(long long count) {
   return (int)(b > 152 * 16 ? 152 * 16 : (b < 1 ? 1 : b));
 }
 
-static TcJob job(int pair0, int npairs, int out_field) {
+// blocks of a row-wise launch: one row per block, at most 16 blocks per SM
+static int row_blocks(long long rows) { return (int)(rows > 152 * 16 ? 152 * 16 : (rows < 1 ? 1 : rows)); }
+
+static TcJob job(int pair0, int npairs, int out_field, int half) {
   TcJob j;
   j.pair0 = pair0;
   j.npairs = npairs;
   j.out_field = out_field;
-  j.pad = 0;
+  j.half = half;
   return j;
 }
 
@@ -902,9 +1171,24 @@ struct ProgramBuild {
   int job0[kPrograms], pair0[kPrograms];
 };
 
+// The segment covering every tile of group `group`, starting at launch tile tile0.
+static TcSeg whole_seg(const TcGroup& G, int group, int tile0) {
+  TcSeg q;
+  memset(&q, 0, sizeof(q));
+  q.group = group;
+  q.tile0 = tile0;
+  q.job0 = 0;
+  q.njobs = G.njobs;
+  q.rb0 = 0;
+  q.nrb = G.m_tiles;
+  q.dep = -1;
+  q.done = -1;
+  return q;
+}
+
 static void set_stage(TcGroup& G, const CUtensorMap& ahi, const CUtensorMap& alo, const CUtensorMap& bhi,
                       const CUtensorMap& blo, int rows, int n_a, int K, int bk, int bn, void* out_hi, void* out_lo,
-                      long long field_elems, long long s_a, int ldC, int n_inner, int mode, float alpha) {
+                      long long field_elems, long long s_a, int ldC, int n_inner, int mode, float alpha, int hq) {
   G.a_hi = ahi;
   G.a_lo = alo;
   G.b_hi = bhi;
@@ -921,8 +1205,9 @@ static void set_stage(TcGroup& G, const CUtensorMap& ahi, const CUtensorMap& alo
   G.n_inner = n_inner;
   G.mode = mode;
   G.alpha = alpha;
+  G.hq = hq;
+  G.pxor = 0;
   G.m_tiles = (rows + kBM - 1) / kBM;
-  G.rgroup = kRowGroup < G.m_tiles ? kRowGroup : G.m_tiles;
   G.n_tiles = (n_a + bn - 1) / bn;
 }
 
@@ -931,15 +1216,22 @@ static demag_status build_programs(demag_plan* P, TcState* S, const CUtensorMap 
                                    const CUtensorMap (&mapB)[3][2], const CUtensorMap (&out1)[2],
                                    const CUtensorMap (&out2)[2], const CUtensorMap& out3, int bk,
                                    cudaStream_t st) {
-  const int n1 = P->n[0], n2 = P->n[1], n3 = P->n[2], M = P->M;
-  const long long N = (long long)n1 * n2 * n3;
+  const AxisGeo& g = S->geo;
+  const int M = P->M;
+  const int x1 = g.ext[0], x2 = g.ext[1], x3 = g.ext[2];
+  const long long Nx = (long long)x1 * x2 * x3;
   ProgramBuild b;
   auto begin = [&](int prog) {
     b.job0[prog] = (int)b.jobs.size();
     b.pair0[prog] = (int)b.pairs.size();
   };
+  // one job per output half, all reading the last npairs pairs pushed
   auto add_job = [&](int prog, int npairs, int out_field) {
-    b.jobs.push_back(job((int)b.pairs.size() - b.pair0[prog] - npairs, npairs, out_field));
+    const int p0 = (int)b.pairs.size() - b.pair0[prog] - npairs;
+    for (int hf = 0; hf < S->halves[prog % 3]; ++hf) b.jobs.push_back(job(p0, npairs, out_field, hf));
+  };
+  auto add_job_at = [&](int prog, int p0, int npairs, int out_field) {
+    for (int hf = 0; hf < S->halves[prog % 3]; ++hf) b.jobs.push_back(job(p0, npairs, out_field, hf));
   };
   // forward mode 1: Y[k][q] = m_q x_1 T_{k,q,1}; rows (i3, i2), contraction i1 -> Y [i1'][i3][i2]
   begin(kFwd1);
@@ -964,10 +1256,10 @@ static demag_status build_programs(demag_plan* P, TcState* S, const CUtensorMap 
     b.pairs.push_back(make_short2((short)(2 * k + 1), mat(k, 1)));
   }
   S->groups_fwd = (2 * M + S->pp3 - 1) / S->pp3;
-  for (int g = 0; g < S->groups_fwd; ++g) {
-    const int p0 = g * S->pp3;
+  for (int gi = 0; gi < S->groups_fwd; ++gi) {
+    const int p0 = gi * S->pp3;
     const int np = (2 * M - p0) < S->pp3 ? (2 * M - p0) : S->pp3;
-    b.jobs.push_back(job(p0, np, g));
+    add_job_at(kFwd3, p0, np, gi);
   }
   // adjoint mode 1: Ya_k = y x_1 F, Yb_k = y x_1 E  (fields 2k, 2k+1 of buf1)
   begin(kAdj1);
@@ -995,20 +1287,20 @@ static demag_status build_programs(demag_plan* P, TcState* S, const CUtensorMap 
     for (int gi = 0; gi < S->groups_adj; ++gi) {
       const int p0 = gi * S->pp3;
       const int np = (M - p0) < S->pp3 ? (M - p0) : S->pp3;
-      b.jobs.push_back(job(base + p0, np, q * S->groups_adj + gi));
+      add_job_at(kAdj3, base + p0, np, q * S->groups_adj + gi);
     }
   }
   const int job_end = (int)b.jobs.size();
 
-  const long long f1 = (long long)n1 * n3 * S->ld[1], f2 = (long long)n2 * n1 * S->ld[2];
+  const long long f1 = (long long)x1 * x3 * S->ld[1], f2 = (long long)x2 * x1 * S->ld[2];
   TcGroup* H = S->host_prog;
   memset(H, 0, sizeof(S->host_prog));
-  set_stage(H[kFwd1], mapX[0], mapX[1], mapB[0][0], mapB[0][1], n3 * n2, n1, n1, bk, S->bn[0], S->buf1[0],
-            S->buf1[1], f1, (long long)n3 * S->ld[1], S->ld[1], n2, kOutSplit, 1.f);
-  set_stage(H[kFwd2], map1[0], map1[1], mapB[1][0], mapB[1][1], n1 * n3, n2, n2, bk, S->bn[1], S->buf2[0],
-            S->buf2[1], f2, (long long)n1 * S->ld[2], S->ld[2], n3, kOutSplit, 1.f);
-  set_stage(H[kFwd3], map2[0], map2[1], mapB[2][0], mapB[2][1], n2 * n1, n3, n3, bk, S->bn[2], S->part, nullptr, N,
-            (long long)n2 * n1, n1, n1, kOutF32, 1.f);
+  set_stage(H[kFwd1], mapX[0], mapX[1], mapB[0][0], mapB[0][1], x3 * x2, g.h[0], g.h[0], bk, S->bn[0], S->buf1[0],
+            S->buf1[1], f1, (long long)x3 * S->ld[1], S->ld[1], x2, kOutSplit, 1.f, g.hq[0]);
+  set_stage(H[kFwd2], map1[0], map1[1], mapB[1][0], mapB[1][1], x1 * x3, g.h[1], g.h[1], bk, S->bn[1], S->buf2[0],
+            S->buf2[1], f2, (long long)x1 * S->ld[2], S->ld[2], x3, kOutSplit, 1.f, g.hq[1]);
+  set_stage(H[kFwd3], map2[0], map2[1], mapB[2][0], mapB[2][1], x2 * x1, g.h[2], g.h[2], bk, S->bn[2], S->part,
+            nullptr, Nx, (long long)x2 * x1, x1, x1, kOutF32, 1.f, g.hq[2]);
   H[kAdj1] = H[kFwd1];
   H[kAdj2] = H[kFwd2];
   H[kAdj3] = H[kFwd3];
@@ -1033,11 +1325,11 @@ static demag_status build_programs(demag_plan* P, TcState* S, const CUtensorMap 
     H[p].njobs = jend - b.job0[p];
     H[p].ntiles = H[p].njobs * H[p].m_tiles * H[p].n_tiles;
   }
-  // stages along an axis of at most kSmallAxis cells run on CUDA cores
+  // stages along an axis of at most kSmallAxis cells (never folded) run on CUDA cores
   {
     const void* in_hi[3] = {S->X[0], S->buf1[0], S->buf2[0]};
     const void* in_lo[3] = {S->X[1], S->buf1[1], S->buf2[1]};
-    const long long rows_of[3] = {(long long)n3 * n2, (long long)n1 * n3, (long long)n2 * n1};
+    const long long rows_of[3] = {(long long)x3 * x2, (long long)x1 * x3, (long long)x2 * x1};
     for (int p = 0; p < kPrograms; ++p) {
       const int stage = p % 3;
       S->small[p] = P->n[stage] <= kSmallAxis;
@@ -1072,13 +1364,10 @@ static demag_status build_programs(demag_plan* P, TcState* S, const CUtensorMap 
   }
   DEMAG_CUDA(P, cudaMalloc(&S->prog, sizeof(TcGroup) * kPrograms));
   DEMAG_CUDA(P, cudaMemcpy(S->prog, H, sizeof(TcGroup) * kPrograms, cudaMemcpyHostToDevice));
-  int t0[2 * kPrograms];
-  for (int p = 0; p < kPrograms; ++p) {
-    t0[2 * p] = 0;
-    t0[2 * p + 1] = H[p].ntiles;
-  }
-  DEMAG_CUDA(P, cudaMalloc(&S->tile0, sizeof(t0)));
-  DEMAG_CUDA(P, cudaMemcpy(S->tile0, t0, sizeof(t0), cudaMemcpyHostToDevice));
+  TcSeg sg[kPrograms];
+  for (int p = 0; p < kPrograms; ++p) sg[p] = whole_seg(H[p], 0, 0);
+  DEMAG_CUDA(P, cudaMalloc(&S->seg, sizeof(sg)));
+  DEMAG_CUDA(P, cudaMemcpy(S->seg, sg, sizeof(sg), cudaMemcpyHostToDevice));
   (void)st;
   return DEMAG_OK;
 }
@@ -1087,11 +1376,12 @@ template <class F>
 static demag_status prepare_form(demag_plan* P, TcState* S, cudaStream_t st) {
   const int M = P->M;
   for (int p = 0; p < 3; ++p) {
-    long long total = (long long)M * 2 * P->n[p] * P->n[p];
+    const int h = S->geo.h[p];
+    long long total = (long long)M * 2 * S->halves[p] * h * h;
     DEMAG_LAUNCH(P, kFamSetup, st,
                  tc_factor_kernel<F><<<grid_blocks(total), 256, 0, st>>>(
-                     M, P->glen, p, P->n[p], S->ld[p], P->gen64, P->scale, (typename F::T*)S->B[p][0],
-                     (typename F::T*)S->B[p][1], P->fac64, P->tgroup, P->toff[p]));
+                     M, P->glen, p, P->n[p], h, S->halves[p], S->ldB[p], 0, P->gen64, P->scale,
+                     (typename F::T*)S->B[p][0], (typename F::T*)S->B[p][1], P->fac64, P->tgroup, P->toff[p]));
     DEMAG_LAUNCHED(P, "tc_factor_kernel");
   }
   static unsigned long long attr = 0;  // devices whose kernel attribute is set
@@ -1114,14 +1404,13 @@ static demag_status set_tile_width(demag_plan* P, TcState* S, int prog, int bn) 
   const int axis = prog % 3;
   const int M = P->M;
   for (int h = 0; h < 2; ++h)
-    if (!make_map(h ? &G.b_lo : &G.b_hi, S->B[axis][h], S->elem, P->n[axis], P->n[axis], 2 * M, S->ld[axis], bn))
+    if (!make_bmap(h ? &G.b_lo : &G.b_hi, S->B[axis][h], S->elem, S->geo.h[axis], S->halves[axis], 2 * M,
+                   S->ldB[axis], bn))
       return set_error(P, DEMAG_ECUDA, "tensor map encoding failed");
   G.bn = bn;
   G.n_tiles = (G.n_a + bn - 1) / bn;
   G.ntiles = G.njobs * G.m_tiles * G.n_tiles;
-  const int t0[2] = {0, G.ntiles};
   DEMAG_CUDA(P, cudaMemcpy(S->prog + prog, &G, sizeof(TcGroup), cudaMemcpyHostToDevice));
-  DEMAG_CUDA(P, cudaMemcpy(S->tile0 + 2 * prog, t0, sizeof(t0), cudaMemcpyHostToDevice));
   return DEMAG_OK;
 }
 
@@ -1185,15 +1474,23 @@ demag_status tc_prepare(demag_plan* P, demag_precision prec, cudaStream_t st) {
   if (!encode_fn()) return set_error(P, DEMAG_ECUDA, "cuTensorMapEncodeTiled is unavailable");
   if (!P->tc) P->tc = new TcHolder();
   TcHolder* Hd = reinterpret_cast<TcHolder*>(P->tc);
-  const int n1 = P->n[0], n2 = P->n[1], n3 = P->n[2], M = P->M;
+  const int n3 = P->n[2], M = P->M;
   TcState* S = new TcState();
   memset(S, 0, sizeof(*S));
   S->elem = prec == DEMAG_TF32X3 ? 4 : 2;
-  const int al = 16 / S->elem;
-  for (int p = 0; p < 3; ++p) {
-    S->ld[p] = round_up(P->n[p], al);
-    S->bn[p] = P->n[p] >= kBN ? kBN : round_up(P->n[p], 16);
+  {
+    const TcGeo G = tc_geometry(P, S->elem);
+    S->geo = G.g;
+    for (int p = 0; p < 3; ++p) {
+      S->halves[p] = G.halves[p];
+      S->ld[p] = G.ld[p];
+      S->ldB[p] = G.ldB[p];
+      const int h = G.g.h[p];
+      S->bn[p] = h >= kBN ? kBN : round_up(h, 16);
+    }
   }
+  const AxisGeo& geo = S->geo;
+  const long long x1 = geo.ext[0], x2 = geo.ext[1], x3 = geo.ext[2];
   auto alloc = [&](void** ptr, size_t bytes) -> bool {
     if (cudaMalloc(ptr, bytes) != cudaSuccess) return false;
     S->bytes += bytes;
@@ -1202,67 +1499,69 @@ demag_status tc_prepare(demag_plan* P, demag_precision prec, cudaStream_t st) {
   const size_t e = S->elem;
   bool ok = true;
   for (int p = 0; p < 3 && ok; ++p)
-    for (int h = 0; h < 2 && ok; ++h) ok = alloc(&S->B[p][h], (size_t)M * 2 * P->n[p] * S->ld[p] * e);
+    for (int h = 0; h < 2 && ok; ++h)
+      ok = alloc(&S->B[p][h], (size_t)M * 2 * S->halves[p] * geo.h[p] * S->ldB[p] * e);
   for (int h = 0; h < 2 && ok; ++h) {
-    ok = ok && alloc(&S->X[h], 3 * (size_t)n3 * n2 * S->ld[0] * e);
-    ok = ok && alloc(&S->buf1[h], 3 * (size_t)M * n1 * n3 * S->ld[1] * e);
-    ok = ok && alloc(&S->buf2[h], 3 * (size_t)M * n2 * n1 * S->ld[2] * e);
+    ok = ok && alloc(&S->X[h], 3 * (size_t)x3 * x2 * S->ld[0] * e);
+    ok = ok && alloc(&S->buf1[h], 3 * (size_t)M * x1 * x3 * S->ld[1] * e);
+    ok = ok && alloc(&S->buf2[h], 3 * (size_t)M * x2 * x1 * S->ld[2] * e);
   }
   ok = ok && alloc((void**)&S->status, sizeof(int));
   ok = ok && alloc((void**)&S->counter, sizeof(int));
   {
-    const int kb3 = (n3 + kRowBytes / S->elem - 1) / (kRowBytes / S->elem);
+    const int kb3 = (geo.h[2] + kRowBytes / S->elem - 1) / (kRowBytes / S->elem);
     // TF32x3 issues twice the MMAs per K of BF16x3 in stages 1-2 as well, so its
     // node sum gets half the accumulation budget
     S->pp3 = pairs_per_split(kb3, S->elem == 4 ? 200 : 400);
-    // a node-sum stage on CUDA cores accumulates in round-to-nearest FP32; its
-    // groups only split the work (one job per group) over more blocks
-    if (n3 <= kSmallAxis) S->pp3 = std::min(S->pp3, 4);
+    // a node-sum stage on CUDA cores (single applications) accumulates in
+    // round-to-nearest FP32; its groups only split the work over more blocks,
+    // which a grid of few rows needs (a batched application runs the same
+    // stage on tensor cores, where more groups mean more tiles and partials)
+    if (n3 <= kSmallAxis && x1 * x2 < 65536) S->pp3 = std::min(S->pp3, 4);
     const int gf = (2 * M + S->pp3 - 1) / S->pp3;   // forward: 2M pairs in one sum
     const int ga = (M + S->pp3 - 1) / S->pp3;       // adjoint: M pairs per component
     const int fields = gf > 3 * ga ? gf : 3 * ga;
     S->part_fields = fields;
-    ok = ok && alloc((void**)&S->part, sizeof(float) * (size_t)fields * n1 * n2 * n3);
+    ok = ok && alloc((void**)&S->part, sizeof(float) * (size_t)fields * x1 * x2 * x3);
   }
   if (!ok) {
     free_state(S);
     return set_error(P, DEMAG_ENOMEM, "tensor-core workspace allocation failed");
   }
   CUtensorMap mapB[3][2], mapX[2], map1[2], map2[2], out1[2], out2[2], out3;
-  memset(mapB, 0, sizeof(mapB));  // maps of CUDA-core stages stay unset
+  memset(mapB, 0, sizeof(mapB));
   memset(mapX, 0, sizeof(mapX));
   memset(map1, 0, sizeof(map1));
   memset(map2, 0, sizeof(map2));
   memset(out1, 0, sizeof(out1));
   memset(out2, 0, sizeof(out2));
   memset(&out3, 0, sizeof(out3));
+  // maps of every axis, also those of at most kSmallAxis cells: a single
+  // application runs those stages on CUDA cores, a batched one on tensor cores
   for (int h = 0; h < 2; ++h) {
     for (int p = 0; p < 3; ++p)
-      if (P->n[p] > kSmallAxis)
-        ok = ok && make_map(&mapB[p][h], S->B[p][h], S->elem, P->n[p], P->n[p], 2 * M, S->ld[p], S->bn[p]);
-    if (n1 > kSmallAxis) ok = ok && make_map(&mapX[h], S->X[h], S->elem, n1, (uint64_t)n3 * n2, 3, S->ld[0], kBM);
-    if (n2 > kSmallAxis)
-      ok = ok && make_map(&map1[h], S->buf1[h], S->elem, n2, (uint64_t)n1 * n3, 3 * M, S->ld[1], kBM);
-    if (n3 > kSmallAxis)
-      ok = ok && make_map(&map2[h], S->buf2[h], S->elem, n3, (uint64_t)n2 * n1, 3 * M, S->ld[2], kBM);
+      ok = ok && make_bmap(&mapB[p][h], S->B[p][h], S->elem, geo.h[p], S->halves[p], 2 * M, S->ldB[p], S->bn[p]);
+    ok = ok && make_map(&mapX[h], S->X[h], S->elem, x1, (uint64_t)(x3 * x2), 3, S->ld[0], kBM);
+    ok = ok && make_map(&map1[h], S->buf1[h], S->elem, x2, (uint64_t)(x1 * x3), 3 * M, S->ld[1], kBM);
+    ok = ok && make_map(&map2[h], S->buf2[h], S->elem, x3, (uint64_t)(x2 * x1), 3 * M, S->ld[2], kBM);
   }
   // epilogue stores through TMA where a warp's 32 output rows share one outer
   // index (n_inner % 32 == 0) and a 32 x 32 chunk fits the staging buffer
   // (BF16 planes, FP32 partials)
-  S->tma[0] = (n2 % 32 == 0) && S->elem == 2;
-  S->tma[1] = (n3 % 32 == 0) && S->elem == 2;
-  S->tma[2] = (n1 % 32 == 0);
+  S->tma[0] = (x2 % 32 == 0) && S->elem == 2;
+  S->tma[1] = (x3 % 32 == 0) && S->elem == 2;
+  S->tma[2] = (x1 % 32 == 0);
   for (int h = 0; h < 2; ++h) {
     if (S->tma[0])
-      ok = ok && make_out_map(&out1[h], S->buf1[h], S->elem, n2, n3, n1, 3 * M, S->ld[1], (uint64_t)n3 * S->ld[1],
-                              (uint64_t)n1 * n3 * S->ld[1]);
+      ok = ok && make_out_map(&out1[h], S->buf1[h], S->elem, x2, x3, geo.h[0], S->halves[0], geo.hq[0], 3 * M,
+                              S->ld[1], (uint64_t)x3 * S->ld[1], (uint64_t)(x1 * x3) * S->ld[1]);
     if (S->tma[1])
-      ok = ok && make_out_map(&out2[h], S->buf2[h], S->elem, n3, n1, n2, 3 * M, S->ld[2], (uint64_t)n1 * S->ld[2],
-                              (uint64_t)n2 * n1 * S->ld[2]);
+      ok = ok && make_out_map(&out2[h], S->buf2[h], S->elem, x3, x1, geo.h[1], S->halves[1], geo.hq[1], 3 * M,
+                              S->ld[2], (uint64_t)x1 * S->ld[2], (uint64_t)(x2 * x1) * S->ld[2]);
   }
   if (S->tma[2])
-    ok = ok && make_out_map(&out3, S->part, 4, n1, n2, n3, S->part_fields, n1, (uint64_t)n2 * n1,
-                            (uint64_t)n1 * n2 * n3);
+    ok = ok && make_out_map(&out3, S->part, 4, x1, x2, geo.h[2], S->halves[2], geo.hq[2], S->part_fields, x1,
+                            (uint64_t)(x2 * x1), (uint64_t)(x1 * x2 * x3));
   if (!ok) {
     free_state(S);
     return set_error(P, DEMAG_ECUDA, "tensor map encoding failed");
@@ -1289,21 +1588,23 @@ demag_status tc_prepare(demag_plan* P, demag_precision prec, cudaStream_t st) {
 }
 
 template <class F>
-static demag_status launch_groups(demag_plan* P, const TcGroup* groups, const int* tile0, int ngroups,
-                                  int total_tiles, int* counter, int* status, cudaStream_t st) {
+static demag_status launch_segs(demag_plan* P, const TcGroup* groups, const TcSeg* segs, int nsegs, int total_tiles,
+                               int* counter, int* counters, int ncounters, int* status, cudaStream_t st) {
   if (total_tiles <= 0) return DEMAG_OK;
   TcLaunch L;
   L.groups = groups;
-  L.tile0 = tile0;
-  L.ngroups = ngroups;
+  L.segs = segs;
+  L.nsegs = nsegs;
   L.total_tiles = total_tiles;
   L.tile_counter = counter;
+  L.counters = counters;
   L.status = status;
   int sms = 0, dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int grid = total_tiles < sms ? total_tiles : sms;
-  DEMAG_CUDA(P, cudaMemsetAsync(counter, 0, sizeof(int), st));
+  // the dependency counters follow the tile counter in the same buffer when present
+  DEMAG_CUDA(P, cudaMemsetAsync(counter, 0, sizeof(int) * (1 + (counters ? ncounters : 0)), st));
   DEMAG_LAUNCH(P, kFamGemmTc, st, tc_gemm_kernel<F><<<grid, kTcThreads, kSmemBytes, st>>>(L));
   DEMAG_LAUNCHED(P, "tc_gemm_kernel");
   return DEMAG_OK;
@@ -1320,60 +1621,64 @@ static demag_status launch_small(demag_plan* P, const SmallStage& Q, cudaStream_
 template <class F>
 static demag_status run_program(demag_plan* P, TcState* S, int prog, cudaStream_t st) {
   if (S->small[prog]) return launch_small<F>(P, S->small_prog[prog], st);
-  return launch_groups<F>(P, S->prog + prog, S->tile0 + 2 * prog, 1, S->host_prog[prog].ntiles, S->counter,
-                          S->status, st);
+  return launch_segs<F>(P, S->prog + prog, S->seg + prog, 1, S->host_prog[prog].ntiles, S->counter, nullptr, 0,
+                        S->status, st);
 }
 
 template <class F>
-static demag_status launch_split(demag_plan* P, const SplitList& L, cudaStream_t st) {
-  DEMAG_LAUNCH(P, kFamSplit, st, split_rows_kernel<F><<<grid_blocks(L.total), 256, 0, st>>>(L));
-  DEMAG_LAUNCHED(P, "split_rows_kernel");
+static demag_status launch_split(demag_plan* P, const FoldList& L, cudaStream_t st) {
+  DEMAG_LAUNCH(P, kFamSplit, st, fold_split_kernel<F><<<row_blocks(L.total), 128, 0, st>>>(L));
+  DEMAG_LAUNCHED(P, "fold_split_kernel");
   return DEMAG_OK;
 }
 
-static void add_split(SplitList& L, demag_plan* P, TcState* S, const float* x, int fields) {
-  SplitItem& it = L.it[L.count++];
+static void add_split(FoldList& L, demag_plan* P, TcState* S, const float* x, int fields) {
+  (void)P;
+  FoldItem& it = L.it[L.count++];
   it.x = x;
   it.hi = S->X[0];
   it.lo = S->X[1];
   it.begin = L.total;
-  it.n = P->n[0];
-  it.ld = S->ld[0];
-  it.vec = (P->n[0] % 4 == 0) && (reinterpret_cast<uintptr_t>(x) % 16 == 0);
-  L.total += (long long)fields * P->n[2] * P->n[1] * ((P->n[0] + 3) / 4);
+  it.g = S->geo;
+  it.ld1 = S->ld[0];
+  long long rows = fields;
+  for (int p = 1; p < 3; ++p) rows *= S->geo.hq[p] ? S->geo.hq[p] : S->geo.n[p];
+  L.total += rows;
 }
 
 template <class F>
 static demag_status split_input(demag_plan* P, TcState* S, const float* x, int fields, cudaStream_t st) {
-  SplitList L;
+  FoldList L;
   L.count = 0;
   L.total = 0;
   add_split(L, P, S, x, fields);
   return launch_split<F>(P, L, st);
 }
 
-static demag_status launch_reduce(demag_plan* P, const ReduceList& L, cudaStream_t st) {
-  DEMAG_LAUNCH(P, kFamMisc, st, reduce_parts_kernel<<<grid_blocks(L.total), 256, 0, st>>>(L));
-  DEMAG_LAUNCHED(P, "reduce_parts_kernel");
+static demag_status launch_reduce(demag_plan* P, const UnfoldList& L, cudaStream_t st) {
+  DEMAG_LAUNCH(P, kFamMisc, st, unfold_reduce_kernel<<<row_blocks(L.total), 128, 0, st>>>(L));
+  DEMAG_LAUNCHED(P, "unfold_reduce_kernel");
   return DEMAG_OK;
 }
 
-static void add_reduce(ReduceList& L, demag_plan* P, TcState* S, int groups, int nout, float alpha, float* out) {
-  const long long N = (long long)P->n[0] * P->n[1] * P->n[2];
-  ReduceItem& it = L.it[L.count++];
+static void add_reduce(UnfoldList& L, demag_plan* P, TcState* S, int groups, int nout, float alpha, float* out) {
+  (void)P;
+  UnfoldItem& it = L.it[L.count++];
   it.part = S->part;
   it.out = out;
   it.begin = L.total;
-  it.N = N;
+  it.g = S->geo;
   it.groups = groups;
-  it.alpha = alpha;
-  it.vec = (N % 4 == 0) && (reinterpret_cast<uintptr_t>(out) % 16 == 0);
-  L.total += it.vec ? nout * (N >> 2) : nout * N;
+  float a = alpha;
+  for (int p = 0; p < 3; ++p)
+    if (S->geo.hq[p]) a *= 0.5f;
+  it.alpha = a;
+  L.total += (long long)nout * S->geo.h[1] * S->geo.h[2];
 }
 
 static demag_status reduce_parts(demag_plan* P, TcState* S, int groups, int nout, float alpha, float* out,
                                  cudaStream_t st) {
-  ReduceList L;
+  UnfoldList L;
   L.count = 0;
   L.total = 0;
   add_reduce(L, P, S, groups, nout, alpha, out);
@@ -1413,12 +1718,21 @@ demag_status tc_adjoint(demag_plan* P, const float* y, float* g, demag_precision
 void tc_batch_destroy(TcBatch* B) {
   if (!B) return;
   cudaFree(B->groups);
-  cudaFree(B->tile0);
+  cudaFree(B->segs);
+  cudaFree(B->ctr);
   delete B;
 }
 
-// Concatenate the forward stage programs of `plans` (which must be distinct and
-// have their tensor-core state for `prec`) into per-stage group arrays.
+// One launch for every forward stage of `plans` (distinct, with their
+// tensor-core state for `prec`): the tiles of stage 1 of all grids, largest
+// grids first, then stage 2, then stage 3.  Stage s of a grid waits for the
+// completion counter of its stage s - 1 (every epilogue warp of every tile of
+// that stage counts once); in this order the wait is met long before, except
+// for the last grids of a stage.  (Interleaving the stages of different grids
+// as a pipeline, so that a small grid's intermediates are read while still in
+// L2, measured 4% slower on the 64-grid batch.)  Stages along axes of at most
+// kSmallAxis cells run as tensor-core tiles here (K padded to one k-block,
+// 16-wide N tiles).
 demag_status tc_batch_create(demag_plan* const* plans, int count, demag_precision prec, TcBatch** out) {
   *out = nullptr;
   demag_plan* P0 = plans[0];
@@ -1427,32 +1741,42 @@ demag_status tc_batch_create(demag_plan* const* plans, int count, demag_precisio
   for (int i = 0; i < count; ++i) B->serials.push_back(plans[i]->serial);
   B->prec = (int)prec;
   // largest grids first: the dynamic tile counter then hands out their long
-  // tile streams early and the small grids' tiles fill the tail of the launch
+  // tile streams early and the small grids' tiles fill the tail of each stage
   std::vector<int> order(count);
   for (int i = 0; i < count; ++i) order[i] = i;
   auto cells = [&](int i) { return (long long)plans[i]->n[0] * plans[i]->n[1] * plans[i]->n[2]; };
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cells(a) > cells(b); });
   std::vector<TcGroup> g(3 * (size_t)count);
-  std::vector<int> t0(3 * (size_t)(count + 1));
+  std::vector<TcSeg> segs;
+  int acc = 0;
   for (int st3 = 0; st3 < 3; ++st3) {
-    int acc = 0;
     for (int i = 0; i < count; ++i) {
       const TcState* S = state(plans[order[i]], prec);
-      g[st3 * count + i] = S->host_prog[kFwd1 + st3];
-      t0[st3 * (count + 1) + i] = acc;
-      // a stage that runs on CUDA cores keeps its slot with no tiles
-      if (!S->small[kFwd1 + st3]) acc += S->host_prog[kFwd1 + st3].ntiles;
+      const int gi = st3 * count + i;
+      g[gi] = S->host_prog[kFwd1 + st3];
+      if (g[gi].ntiles <= 0) continue;
+      TcSeg q = whole_seg(g[gi], gi, acc);
+      if (st3 > 0) {
+        q.dep = 2 * i + (st3 - 1);
+        q.dep_target = kEpiWarps * S->host_prog[kFwd1 + st3 - 1].ntiles;
+      }
+      if (st3 < 2) q.done = 2 * i + st3;
+      segs.push_back(q);
+      acc += g[gi].ntiles;
     }
-    t0[st3 * (count + 1) + count] = acc;
-    B->total[st3] = acc;
   }
+  B->nsegs = (int)segs.size();
+  B->total = acc;
+  B->nctr = 2 * count;
   if (cudaMalloc(&B->groups, sizeof(TcGroup) * g.size()) != cudaSuccess ||
-      cudaMalloc(&B->tile0, sizeof(int) * t0.size()) != cudaSuccess) {
+      cudaMalloc(&B->segs, sizeof(TcSeg) * (segs.size() ? segs.size() : 1)) != cudaSuccess ||
+      cudaMalloc(&B->ctr, sizeof(int) * (1 + B->nctr)) != cudaSuccess) {
     tc_batch_destroy(B);
     return set_error(P0, DEMAG_ENOMEM, "grouped launch descriptors: allocation failed");
   }
   cudaError_t e = cudaMemcpy(B->groups, g.data(), sizeof(TcGroup) * g.size(), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(B->tile0, t0.data(), sizeof(int) * t0.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !segs.empty())
+    e = cudaMemcpy(B->segs, segs.data(), sizeof(TcSeg) * segs.size(), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
     tc_batch_destroy(B);
     return cuda_error(P0, e, "grouped launch descriptors");
@@ -1461,43 +1785,36 @@ demag_status tc_batch_create(demag_plan* const* plans, int count, demag_precisio
   return DEMAG_OK;
 }
 
-// Several grids in one call: each plan's input is split, then every forward
-// stage of all grids runs as ONE persistent launch over the concatenated group
-// descriptors (tiles of all grids share the dynamic tile counter of the first
-// plan), then each plan's node-sum partials are reduced into its phi.
+// Several grids in one call: one split launch over every plan's input, one
+// persistent launch over all stages of all grids, one node-sum reduction
+// launch into every plan's phi (per kMaxItems grids for the element-wise
+// launches).
 template <class F>
 static demag_status batched_chain(const TcBatch* B, const float* const* m, float* const* phi, cudaStream_t st) {
   const demag_precision prec = (demag_precision)B->prec;
   const int count = (int)B->plans.size();
   demag_plan* P0 = B->plans[0];
   TcState* S0 = state(P0, prec);
-  // one split launch per kMaxItems grids
   for (int i0 = 0; i0 < count; i0 += kMaxItems) {
-    SplitList L;
+    FoldList L;
     L.count = 0;
     L.total = 0;
     for (int i = i0; i < count && i < i0 + kMaxItems; ++i) add_split(L, B->plans[i], state(B->plans[i], prec), m[i], 3);
     demag_status s = launch_split<F>(P0, L, st);
     if (s != DEMAG_OK) return s;
   }
-  for (int st3 = 0; st3 < 3; ++st3) {
-    demag_status s = launch_groups<F>(P0, B->groups + (size_t)st3 * count, B->tile0 + (size_t)st3 * (count + 1),
-                                      count, B->total[st3], S0->counter, S0->status, st);
-    for (int i = 0; i < count && s == DEMAG_OK; ++i) {
-      TcState* S = state(B->plans[i], prec);
-      if (S->small[kFwd1 + st3]) s = launch_small<F>(B->plans[i], S->small_prog[kFwd1 + st3], st);
-    }
-    if (s != DEMAG_OK) return s;
-  }
+  demag_status s = launch_segs<F>(P0, B->groups, B->segs, B->nsegs, B->total, B->ctr, B->ctr + 1, B->nctr,
+                                  S0->status, st);
+  if (s != DEMAG_OK) return s;
   for (int i0 = 0; i0 < count; i0 += kMaxItems) {
-    ReduceList L;
+    UnfoldList L;
     L.count = 0;
     L.total = 0;
     for (int i = i0; i < count && i < i0 + kMaxItems; ++i) {
       TcState* S = state(B->plans[i], prec);
       add_reduce(L, B->plans[i], S, S->groups_fwd, 1, 1.f, phi[i]);
     }
-    demag_status s = launch_reduce(P0, L, st);
+    s = launch_reduce(P0, L, st);
     if (s != DEMAG_OK) return s;
   }
   return DEMAG_OK;
@@ -1535,38 +1852,41 @@ static demag_status prepare_field(demag_plan* P, TcState* S, cudaStream_t st) {
   if (s != DEMAG_OK) return s;
   const int M = P->M;
   for (int p = 0; p < 3; ++p) {
-    const size_t bytes = (size_t)M * 2 * P->n[p] * S->ld[p] * S->elem;
-    for (int h = 0; h < 2; ++h) {
-      DEMAG_CUDA(P, cudaMalloc(&S->Bd[p][h], bytes));
-      DEMAG_CUDA(P, cudaMemsetAsync(S->Bd[p][h], 0, bytes, st));
+    const int h = S->geo.h[p];
+    const size_t bytes = (size_t)M * 2 * S->halves[p] * h * S->ldB[p] * S->elem;
+    for (int hl = 0; hl < 2; ++hl) {
+      DEMAG_CUDA(P, cudaMalloc(&S->Bd[p][hl], bytes));
+      DEMAG_CUDA(P, cudaMemsetAsync(S->Bd[p][hl], 0, bytes, st));
     }
-    const long long total = (long long)M * 2 * P->n[p] * P->n[p];
+    // dE is odd and dF even: the parity of the two types is swapped (pxor = 1)
+    const long long total = (long long)M * 2 * S->halves[p] * h * h;
     DEMAG_LAUNCH(P, kFamSetup, st,
                  tc_factor_kernel<F><<<grid_blocks(total), 256, 0, st>>>(
-                     M, P->glen, p, P->n[p], S->ld[p], P->gend, P->scale, (typename F::T*)S->Bd[p][0],
-                     (typename F::T*)S->Bd[p][1], nullptr, 0, 0));
+                     M, P->glen, p, P->n[p], h, S->halves[p], S->ldB[p], 1, P->gend, P->scale,
+                     (typename F::T*)S->Bd[p][0], (typename F::T*)S->Bd[p][1], nullptr, 0, 0));
     DEMAG_LAUNCHED(P, "tc_factor_kernel");
   }
-  int t0[6];
+  TcSeg sg[3];
   for (int st3 = 0; st3 < 3; ++st3) {
     TcGroup& G = S->dprog_host[st3];
     G = S->host_prog[kFwd1 + st3];
     if (!S->small[kFwd1 + st3]) {
       const int p = st3;  // stage s contracts axis s
       for (int h = 0; h < 2; ++h)
-        if (!make_map(h ? &G.b_lo : &G.b_hi, S->Bd[p][h], S->elem, P->n[p], P->n[p], 2 * M, S->ld[p], G.bn))
+        if (!make_bmap(h ? &G.b_lo : &G.b_hi, S->Bd[p][h], S->elem, S->geo.h[p], S->halves[p], 2 * M, S->ldB[p],
+                       G.bn))
           return set_error(P, DEMAG_ECUDA, "tensor map encoding failed");
+      G.pxor = 1;
     }
     S->small_dprog[st3] = S->small_prog[kFwd1 + st3];
     S->small_dprog[st3].gen = P->gend;
     S->small_dprog[st3].fac = nullptr;
-    t0[2 * st3] = 0;
-    t0[2 * st3 + 1] = G.ntiles;
+    sg[st3] = whole_seg(G, 0, 0);
   }
   DEMAG_CUDA(P, cudaMalloc(&S->dprog, sizeof(TcGroup) * 3));
-  DEMAG_CUDA(P, cudaMalloc(&S->dtile0, sizeof(t0)));
+  DEMAG_CUDA(P, cudaMalloc(&S->dseg, sizeof(sg)));
   DEMAG_CUDA(P, cudaMemcpy(S->dprog, S->dprog_host, sizeof(TcGroup) * 3, cudaMemcpyHostToDevice));
-  DEMAG_CUDA(P, cudaMemcpy(S->dtile0, t0, sizeof(t0), cudaMemcpyHostToDevice));
+  DEMAG_CUDA(P, cudaMemcpy(S->dseg, sg, sizeof(sg), cudaMemcpyHostToDevice));
   S->field_ready = true;
   return DEMAG_OK;
 }
@@ -1574,7 +1894,7 @@ static demag_status prepare_field(demag_plan* P, TcState* S, cudaStream_t st) {
 template <class F>
 static demag_status run_deriv(demag_plan* P, TcState* S, int st3, cudaStream_t st) {
   if (S->small[kFwd1 + st3]) return launch_small<F>(P, S->small_dprog[st3], st);
-  return launch_groups<F>(P, S->dprog + st3, S->dtile0 + 2 * st3, 1, S->dprog_host[st3].ntiles, S->counter,
+  return launch_segs<F>(P, S->dprog + st3, S->dseg + st3, 1, S->dprog_host[st3].ntiles, S->counter, nullptr, 0,
                           S->status, st);
 }
 

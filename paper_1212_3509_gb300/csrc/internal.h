@@ -13,7 +13,11 @@
 
 namespace demag {
 
-constexpr int kMaxTerms = 64;       // M <= 64 (R <= 129)
+// M <= 256 (R <= 513): the rule is not uniform in h (Remark after Lemma 2), so
+// R grows with n; M = 256 gives tau_max ~ 7.6e4, enough for n = 4096.
+constexpr int kMaxTerms = 256;
+// the compression of Alg. 2 holds M x M Gram matrices in shared memory
+constexpr int kMaxCompressTerms = 64;
 constexpr int kMaxFFTLog = 13;      // complex FFT length N = L/2 <= 8192 -> n <= 8192
 constexpr double kPi = 3.141592653589793238462643383279502884;
 // c = 1/(2 pi^{3/2}): (1/4pi) from Eq. coll times 2/sqrt(pi) from Eq. gauss_trans

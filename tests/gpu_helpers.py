@@ -9,6 +9,29 @@ def rel_l2(got, ref) -> float:
     return float(np.linalg.norm(got - ref) / (den if den > 0 else 1.0))
 
 
+def rel_max(got, ref) -> float:
+    """Largest entry error relative to the largest reference entry."""
+    got = np.asarray(got, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    den = np.abs(ref).max() if ref.size else 0.0
+    return float(np.abs(got - ref).max() / (den if den > 0 else 1.0)) if ref.size else 0.0
+
+
+# A single wrong entry of an N-entry field moves the relative L2 error by only
+# ~1/sqrt(N); the max-abs bound catches it: every entry must lie within
+# MAXABS_FACTOR * tol * max|ref| of the reference.
+MAXABS_FACTOR = 10.0
+
+
+def assert_close(got, ref, tol, what=""):
+    """Relative L2 error <= tol and max-abs error <= MAXABS_FACTOR * tol * max|ref|."""
+    e2 = rel_l2(got, ref)
+    em = rel_max(got, ref)
+    assert e2 <= tol, (what, "rel-L2", e2, tol)
+    assert em <= MAXABS_FACTOR * tol, (what, "max-abs / max|ref|", em, MAXABS_FACTOR * tol)
+    return e2
+
+
 def dev(a):
     import torch
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
@@ -19,7 +42,11 @@ def host(t):
 
 
 # Tolerances on the relative L2 error against the FP64 oracle, per form.
-# FP32 / TF32x3 forms: 1e-5 and BF16x3: 1e-3 (the stated accuracy targets).
+# FP32 / TF32x3: 1e-5, the stated accuracy target of the FP32 forms.
+# BF16x3: 5e-5.  Its stated target is 1e-3, but the split products recover
+# FP32-level accuracy (6.6e-6 measured at 256^3, lower on the smaller grids
+# of the tests), so a gate at the stated 1e-3 would let a wrong tile edge
+# pass; 5e-5 keeps ~5x margin over the largest error measured.
 # FP64 form: its output is rounded to float32, so the floor is the float32
 # unit roundoff 2^-24 ~ 6e-8 per entry; 2e-7 leaves room for the input cast.
-TOL = {"fp64": 2e-7, "fp32": 1e-5, "tf32x3": 1e-5, "bf16x3": 1e-3}
+TOL = {"fp64": 2e-7, "fp32": 1e-5, "tf32x3": 1e-5, "bf16x3": 5e-5}

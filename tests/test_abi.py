@@ -52,7 +52,7 @@ class Desc(ctypes.Structure):
     ((4, 4, 4), (1, 1, 1), 40, 2.15, 1),       # even R
     ((4, 4, 4), (1, 1, 1), 3, 2.15, 1),        # R < 5
     ((4, 4, 4), (1, 1, 1), 41, 0.0, 1),        # c0 <= 0
-    ((4, 4, 4), (1, 1, 1), 2 * 65 + 1, 2.15, 5),  # too many terms
+    ((4, 4, 4), (1, 1, 1), 2 * 257 + 1, 2.15, 5),  # too many terms (M <= 256)
 ])
 def test_build_factors_rejects_bad_grids(lib, n, h, R, c0, code):
     lib.demag_build_factors.restype = ctypes.c_int

@@ -17,7 +17,7 @@ import synth
 from oracle import energy as oen
 from oracle import full as ofull
 from oracle import structured as ost
-from gpu_helpers import TOL, dev, host, rel_l2
+from gpu_helpers import assert_close, TOL, dev, host, rel_l2
 
 pytestmark = pytest.mark.gpu
 
@@ -51,7 +51,7 @@ def test_c2_full_256_sampled_lines(D, prec):
     got = host(phi)
     err = rel_l2(np.stack([got[i3, i2] for i3, i2 in lines]), ref)
     print(f"C2 256^3 {prec}: sampled rel L2 {err:.3e}")
-    assert err <= TOL[prec]
+    assert_close(np.stack([got[i3, i2] for i3, i2 in lines]), ref, TOL[prec])
 
 
 @pytest.mark.parametrize("prec", ["bf16x3", "tf32x3", "fp32", "fp64"])
@@ -62,9 +62,10 @@ def test_c2_full_128_every_output(D, prec):
     phi = torch.empty(128, 128, 128, device="cuda")
     D.demag_apply_full(P, dev(m), phi, prec)
     torch.cuda.synchronize()
-    err = rel_l2(host(phi), ofull.apply_full(m, n3, h, R))
+    ref_ = ofull.apply_full(m, n3, h, R)
+    err = rel_l2(host(phi), ref_)
     print(f"C2 128^3 {prec}: rel L2 {err:.3e}")
-    assert err <= TOL[prec]
+    assert_close(host(phi), ref_, TOL[prec])
 
 
 def test_c3_cp_4096_batched(D):
@@ -87,7 +88,7 @@ def test_c3_cp_4096_batched(D):
         ref = np.concatenate([rU[p].ravel() for p in range(3)])
         err = rel_l2(host(oU[b * per:(b + 1) * per]), ref)
         print(f"C3 CP n=4096 item {b}: rel L2 {err:.3e}")
-        assert err <= TOL["fp32"]
+        assert_close(host(oU[b * per:(b + 1) * per]), ref, TOL["fp32"])
         assert rel_l2(host(w[b * M * 3 * r:(b + 1) * M * 3 * r]), rw.ravel()) < 1e-6
 
 
@@ -102,9 +103,10 @@ def test_c4_tucker_1024(D):
     D.demag_apply_tucker(P, ranks, dev(V), w, oV)
     torch.cuda.synchronize()
     rw, rV = ost.apply_tucker(core, V, n3, ranks, h, R)
-    err = rel_l2(host(oV), np.concatenate([rV[p].ravel() for p in range(3)]))
+    ref_ = np.concatenate([rV[p].ravel() for p in range(3)])
+    err = rel_l2(host(oV), ref_)
     print(f"C4 Tucker n=1024: rel L2 {err:.3e}")
-    assert err <= TOL["fp32"]
+    assert_close(host(oV), ref_, TOL["fp32"])
 
 
 def test_c4_tt_1024(D):
@@ -120,13 +122,18 @@ def test_c4_tt_1024(D):
     torch.cuda.synchronize()
     rw, r1, r2, r3 = ost.apply_tt(G1, G2, G3, n3, ranks, h, R)
     for got, ref in ((o1, r1), (o2, r2), (o3, r3)):
-        err = rel_l2(host(got), ref.ravel())
+        ref_ = ref.ravel()
+        err = rel_l2(host(got), ref_)
         print(f"C4 TT n=1024: rel L2 {err:.3e}")
-        assert err <= TOL["fp32"]
+        assert_close(host(got), ref_, TOL["fp32"])
 
 
 def test_c5_mixed_grids_batched(D):
-    shapes = [(32, 32, 32), (48, 48, 48), (512, 512, 4), (256, 64, 8), (80, 80, 80), (64, 64, 64)]
+    # every shape of the 64-grid uneven workload (cubes 32^3..192^3 in steps of
+    # 16 and both films), in one batched call: one persistent launch runs all
+    # stages of all grids; large grids are checked on sampled output lines
+    shapes = sorted(set(synth.uneven_batch_shapes(64, 1215)), key=lambda s: s[0] * s[1] * s[2])
+    assert len(shapes) >= 13 and (512, 512, 4) in shapes and (256, 64, 8) in shapes
     plans, ms, phis = [], [], []
     for i, n3 in enumerate(shapes):
         h = (1.0 / max(n3),) * 3
@@ -148,7 +155,7 @@ def test_c5_mixed_grids_batched(D):
             got = np.stack([g[i3, i2] for i3, i2 in lines])
         err = rel_l2(got, ref)
         print(f"C5 {n3} bf16x3: rel L2 {err:.3e}")
-        assert err <= TOL["bf16x3"]
+        assert_close(got, ref, TOL["bf16x3"])
 
 
 def test_c5_gradient_vs_fp64_finite_differences(D):
@@ -233,4 +240,4 @@ def test_c4_batched_and_graph_captured(D):
     # spot check against the oracle: first Tucker item
     core, Vh = synth.tucker_inputs(n3, rt, 1300)
     rw, rV = ost.apply_tucker(core, Vh, n3, rt, h, R)
-    assert rel_l2(host(oB[:M * 3 * tot]), np.concatenate([rV[p].ravel() for p in range(3)])) <= TOL["fp32"]
+    assert_close(host(oB[:M * 3 * tot]), np.concatenate([rV[p].ravel() for p in range(3)]), TOL["fp32"])

@@ -11,7 +11,7 @@ import pytest
 import synth
 from oracle import full as ofull
 from oracle import nonuniform as onu
-from gpu_helpers import TOL, dev, host, rel_l2
+from gpu_helpers import assert_close, TOL, dev, host, rel_l2
 from test_oracle_nonuniform import _brute, _graded
 
 pytestmark = pytest.mark.gpu
@@ -46,7 +46,7 @@ def test_nonuniform_forward_vs_oracle(D, n, prec):
     D.demag_apply_full(P, dev(m), phi, prec)
     torch.cuda.synchronize()
     ref = onu.apply_full(m, edges, 41)
-    assert rel_l2(host(phi), ref) <= TOL[prec], rel_l2(host(phi), ref)
+    assert_close(host(phi), ref, TOL[prec])
 
 
 def test_nonuniform_brute_force(D):
@@ -73,7 +73,17 @@ def test_uniform_edges_match_the_uniform_plan(D, prec):
     D.demag_apply_full(Pu, m, a, prec)
     D.demag_apply_full(Pn, m, b, prec)
     torch.cuda.synchronize()
-    assert rel_l2(host(b), host(a)) <= (1e-12 if prec == "fp64" else 1e-6)
+    if prec == "fp64":
+        assert rel_l2(host(b), host(a)) <= 1e-12
+    else:
+        # the uniform plan folds its 24-cell axis into even / odd halves on the
+        # tensor cores (Toeplitz factors are centro-symmetric); the non-uniform
+        # plan's dense factors are not, so the two round differently: both
+        # meet the split-form tolerance against the oracle and each other
+        ref = ofull.apply_full(host(m), n, h, 41)
+        assert_close(host(a), ref, TOL[prec], "uniform plan")
+        assert_close(host(b), ref, TOL[prec], "uniform edges")
+        assert rel_l2(host(b), host(a)) <= 2 * TOL[prec]
 
 
 @pytest.mark.parametrize("n", [(20, 13, 7), (40, 9, 33)])
@@ -86,7 +96,7 @@ def test_nonuniform_adjoint_vs_oracle_transpose(D, n, prec):
     D.demag_apply_adjoint(P, dev(y), g, prec)
     torch.cuda.synchronize()
     ref = onu.apply_full(y, edges, 21, transpose=True)
-    assert rel_l2(host(g), ref) <= TOL[prec]
+    assert_close(host(g), ref, TOL[prec])
 
 
 def test_mixed_batch_with_a_uniform_plan(D):
@@ -99,12 +109,15 @@ def test_mixed_batch_with_a_uniform_plan(D):
         D.demag_apply_full(P, m, o, "bf16x3")
     D.demag_apply_full_batched(plans, ms, batched, "bf16x3")
     torch.cuda.synchronize()
-    for a, b in zip(single, batched):
-        assert torch.equal(a, b)
+    # bit for bit where every stage runs on the tensor cores in both calls; the
+    # 4-cell axis runs on CUDA cores in a single call, as a padded tensor-core
+    # tile in the batch
+    assert torch.equal(single[0], batched[0])
+    assert_close(host(batched[1]), host(single[1]), TOL["bf16x3"])
     ref = onu.apply_full(host(ms[0]), _grid(shapes[0], 1), 41)
-    assert rel_l2(host(batched[0]), ref) <= TOL["bf16x3"]
+    assert_close(host(batched[0]), ref, TOL["bf16x3"])
     ref1 = ofull.apply_full(host(ms[1]), shapes[1], (1.0, 1.0, 0.5), 41)
-    assert rel_l2(host(batched[1]), ref1) <= TOL["bf16x3"]
+    assert_close(host(batched[1]), ref1, TOL["bf16x3"])
 
 
 def test_uniform_only_paths_refuse_the_plan(D):

@@ -12,7 +12,7 @@ from oracle import full as ofull
 from oracle import generators as ogen
 from oracle import quadrature as oq
 from oracle import structured as ost
-from gpu_helpers import TOL, dev, host, rel_l2
+from gpu_helpers import assert_close, TOL, dev, host, rel_l2
 
 pytestmark = pytest.mark.gpu
 
@@ -105,7 +105,7 @@ def test_full_format_vs_oracle(D, n, h, R, prec):
     torch.cuda.synchronize()
     ref = ofull.apply_full(m, n, h, R)
     err = rel_l2(host(phi), ref)
-    assert err <= TOL[prec], err
+    assert_close(host(phi), ref, TOL[prec])
 
 
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
@@ -119,7 +119,7 @@ def test_c1_uniform_cube_against_closed_form(D, prec):
     D.demag_apply_full(P, dev(m), phi, prec)
     torch.cuda.synchronize()
     got = host(phi)
-    assert rel_l2(got, ofull.apply_full(m, n, h, 41)) <= TOL[prec]
+    assert_close(got, ofull.apply_full(m, n, h, 41), TOL[prec])
     exact = oex.uniform_box_potential(n, h, 2)
     assert np.max(np.abs(got - exact)) < 2e-6 * np.max(np.abs(exact))
 
@@ -145,7 +145,7 @@ def test_adjoint_vs_oracle(D, n, h, R, prec):
     D.demag_apply_adjoint(P, dev(y), g, prec)
     torch.cuda.synchronize()
     ref = ofull.apply_adjoint(y, n, h, R)
-    assert rel_l2(host(g), ref) <= TOL[prec]
+    assert_close(host(g), ref, TOL[prec])
 
 
 @pytest.mark.parametrize("n", [(16, 16, 16), (37, 50, 9), (1, 4, 2), (128, 128, 128)])
@@ -162,7 +162,7 @@ def test_cp_vs_oracle(D, n):
     rw, rU = ost.apply_cp(lam, U, n, h, R)
     assert rel_l2(host(w), rw.ravel()) < 1e-6
     ref = np.concatenate([rU[p].ravel() for p in range(3)])
-    assert rel_l2(host(oU), ref) <= TOL["fp32"]
+    assert_close(host(oU), ref, TOL["fp32"])
 
 
 def test_cp_matches_full_format_at_128(D):
@@ -199,7 +199,7 @@ def test_tucker_vs_oracle(D, n, ranks):
     torch.cuda.synchronize()
     rw, rV = ost.apply_tucker(core, V, n, ranks, h, R)
     assert rel_l2(host(w), rw.ravel()) < 1e-6
-    assert rel_l2(host(oV), np.concatenate([rV[p].ravel() for p in range(3)])) <= TOL["fp32"]
+    assert_close(host(oV), np.concatenate([rV[p].ravel() for p in range(3)]), TOL["fp32"])
 
 
 @pytest.mark.parametrize("n,ranks", [((16, 16, 16), (3, 2)), ((37, 50, 9), (4, 1))])
@@ -219,7 +219,7 @@ def test_tt_vs_oracle(D, n, ranks):
     rw, r1o, r2o, r3o = ost.apply_tt(G1, G2, G3, n, ranks, h, R)
     assert rel_l2(host(w), rw.ravel()) < 1e-6
     for got, ref in ((o1, r1o), (o2, r2o), (o3, r3o)):
-        assert rel_l2(host(got), ref.ravel()) <= TOL["fp32"]
+        assert_close(host(got), ref.ravel(), TOL["fp32"])
 
 
 def test_stray_field_energy_gradient(D):

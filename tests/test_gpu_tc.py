@@ -8,7 +8,7 @@ import pytest
 
 import synth
 from oracle import full as ofull
-from gpu_helpers import TOL, dev, host, rel_l2
+from gpu_helpers import assert_close, TOL, dev, host, rel_l2
 
 pytestmark = pytest.mark.gpu
 
@@ -44,9 +44,10 @@ def test_split_full_vs_oracle(D, n, h, R, prec):
     D.demag_apply_full(P, dev(m), phi, prec)
     torch.cuda.synchronize()
     D.demag_sync_status(P)
-    err = rel_l2(host(phi), ofull.apply_full(m, n, h, R))
+    ref_ = ofull.apply_full(m, n, h, R)
+    err = rel_l2(host(phi), ref_)
     print(f"{prec} {n}: rel L2 {err:.3e}")
-    assert err <= TOL[prec], err
+    assert_close(host(phi), ref_, TOL[prec])
 
 
 @pytest.mark.parametrize("prec", ["bf16x3", "tf32x3"])
@@ -59,9 +60,10 @@ def test_split_adjoint_vs_oracle(D, n, h, R, prec):
     D.demag_apply_adjoint(P, dev(y), g, prec)
     torch.cuda.synchronize()
     D.demag_sync_status(P)
-    err = rel_l2(host(g), ofull.apply_adjoint(y, n, h, R))
+    ref_ = ofull.apply_adjoint(y, n, h, R)
+    err = rel_l2(host(g), ref_)
     print(f"{prec} adjoint {n}: rel L2 {err:.3e}")
-    assert err <= TOL[prec], err
+    assert_close(host(g), ref_, TOL[prec])
 
 
 @pytest.mark.parametrize("n", [(40, 24, 16), (64, 32, 96), (96, 64, 32)])
@@ -81,9 +83,13 @@ def test_bf16x3_repeated_calls_are_identical(D, n):
 
 @pytest.mark.parametrize("prec", ["bf16x3", "tf32x3"])
 def test_grouped_batch_equals_single_applies(D, prec):
-    """One grouped launch per stage over grids of different shapes (TMA-stored
-    and directly stored epilogues mixed, a plan listed twice) gives, bit for
-    bit, what separate calls give: every tile runs the same MMA sequence."""
+    """One persistent launch over every stage of grids of different shapes
+    (TMA-stored and directly stored epilogues mixed, a plan listed twice, later
+    stages waiting for earlier ones through completion counters) gives, bit for
+    bit, what separate calls give on grids whose axes all run on the tensor
+    cores: every tile runs the same MMA sequence.  Axes of at most 16 cells run
+    on CUDA cores in a single call but as padded tensor-core tiles in the
+    batch, so those grids agree to the split-form tolerance."""
     cases = [TC_SHAPES[0], TC_SHAPES[1], TC_SHAPES[4], TC_SHAPES[7], TC_SHAPES[8]]
     plans, ms, single = [], [], []
     for i, (n, h, R) in enumerate(cases):
@@ -104,11 +110,15 @@ def test_grouped_batch_equals_single_applies(D, prec):
     torch.cuda.synchronize()
     for P in plans:
         D.demag_sync_status(P)
-    for got, ref in zip(outs, single + [ref_extra]):
-        assert torch.equal(got, ref)
+    for (n, _, _), got, ref in zip(cases + [cases[0]], outs, single + [ref_extra]):
+        if min(n) > 16:
+            assert torch.equal(got, ref), n
+        else:
+            assert_close(host(got), host(ref), TOL[prec], n)
     n, h, R = cases[3]
-    err = rel_l2(host(outs[3]), ofull.apply_full(host(ms[3]), n, h, R))
-    assert err <= TOL[prec], err
+    ref_ = ofull.apply_full(host(ms[3]), n, h, R)
+    err = rel_l2(host(outs[3]), ref_)
+    assert_close(host(outs[3]), ref_, TOL[prec])
 
 
 @pytest.mark.parametrize("prec", ["bf16x3", "fp32"])
