@@ -458,6 +458,15 @@ demag_status demag_stray_field_exact(demag_plan* plan, const float* m, float* hd
  * gave up set DEMAG_ETIMEOUT there).  Synchronizes `stream`. */
 demag_status demag_sync_status(demag_plan* plan, void* stream);
 
+/* Limit of every bounded device-side wait of the plan's tensor-core kernels
+ * (a pipeline barrier, a completion counter of an earlier tile), in seconds,
+ * 0 <= seconds <= 60 (default 2).  A wait that runs out makes the kernel set
+ * DEMAG_ETIMEOUT in the status word, let every copy and MMA it issued land,
+ * release its tensor memory and return; demag_sync_status then reports it and
+ * the plan stays usable.  For testing that failure path: limits this short
+ * make normal runs fail.  Build-only; no counterpart in the paper. */
+demag_status demag_set_wait_limit(demag_plan* plan, double seconds);
+
 /* ---- allocation-free full format (no counterpart in the paper) ---------- */
 
 /* phi = sum_q P^(q) m^(q) exactly as demag_apply_full with DEMAG_FP32 (same

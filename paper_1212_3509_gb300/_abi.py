@@ -92,6 +92,7 @@ _SIGS = {
     "demag_apply_full_noalloc": (_i, [ctypes.POINTER(GridDesc), _vp, _vp, _vp]),
     "demag_launch_count": (ctypes.c_ulonglong, [_vp]),
     "demag_autotune": (_i, [_vp, _i]),
+    "demag_set_wait_limit": (_i, [_vp, ctypes.c_double]),
     "demag_autotune_count": (_i, [_vp]),
     "demag_autotune_entry": (_i, [_vp, _i, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i),
                                   ctypes.POINTER(ctypes.c_float)]),
@@ -568,6 +569,10 @@ def demag_stray_field_exact(plan: Plan, m, hd, precision="fp32", stream=None):
 
 def demag_sync_status(plan: Plan, stream=None):
     _check(lib.demag_sync_status(plan.ptr, _stream(stream)), plan.ptr)
+
+
+def demag_set_wait_limit(plan: Plan, seconds: float):
+    _check(lib.demag_set_wait_limit(plan.ptr, float(seconds)), plan.ptr)
 
 
 def demag_autotune(plan: Plan, enable: bool = True):

@@ -57,15 +57,13 @@ namespace demag {
 
 constexpr int kBM = 128, kBN = 256;
 constexpr int kRowBytes = 64;                      // one 64-byte swizzled row per k-block
-constexpr int kStages = 4;
+constexpr int kMaxStages = 8;                      // operand ring depth: as many stages as fit (per launch)
 constexpr int kTileA = kBM * kRowBytes;            // 8 KB
-constexpr int kTileB = kBN * kRowBytes;            // 16 KB
-constexpr int kStageBytes = 2 * kTileA + 2 * kTileB;  // 48 KB
-constexpr int kBarBytes = 256;
+constexpr int kBarBytes = 1024;
 // Epilogue warps: kEpiWarps / 4 warps share each TMEM lane quadrant and take
-// its 32-column chunks in turn.  Four (one per quadrant) measured as fast as
-// eight: the stage time is set by the output write traffic, not by epilogue
-// latency.
+// its 32-column chunks in turn.  Four (one per quadrant) are faster than
+// eight with two staging buffers each (256^3 stage 1: 1.22 against 1.48 ms):
+// more stores in flight slow the output stream down.
 #ifndef DEMAG_TC_EPI_WARPS
 #define DEMAG_TC_EPI_WARPS 4
 #endif
@@ -73,12 +71,17 @@ constexpr int kEpiWarps = DEMAG_TC_EPI_WARPS;
 static_assert(kEpiWarps == 4 || kEpiWarps == 8, "4 or 8 epilogue warps");
 constexpr int kEpiSlices = kEpiWarps / 4;          // warps per TMEM lane quadrant
 constexpr int kOutBuf = 4096;                      // one 32 x 32 output chunk (2 BF16 planes or 1 FP32)
-constexpr int kOutStaging = 8 * kOutBuf;           // staging buffers shared out among the epilogue warps
-constexpr int kOutBufsPerWarp = kOutStaging / (kOutBuf * kEpiWarps);
-constexpr int kSmemBytes = kStages * kStageBytes + kOutStaging + kBarBytes + 1024;
+constexpr int kOutBufsPerWarp = 2;
+constexpr int kOutStaging = kOutBufsPerWarp * kEpiWarps * kOutBuf;  // epilogue staging buffers
+// dynamic shared memory: alignment slack, staging, barriers, then the operand
+// stages (each A_hi, A_lo of 128 rows and B_hi, B_lo of the launch's widest N tile)
+constexpr int kSmemFixed = 1024 + kOutStaging + kBarBytes;
+constexpr int kSmemMax = 227 * 1024;
 constexpr int kTcThreads = 64 + 32 * kEpiWarps;
 constexpr int kRing = 4;                           // tile ids handed from the producer to the other roles
-constexpr uint64_t kWaitNs = 2000000000ull;        // 2 s bound on every wait
+// Every pipeline wait gives up after the plan's wait limit (default 2 s,
+// demag_set_wait_limit); the drains of the abort path always allow 2 s.
+constexpr uint64_t kDrainNs = 2000000000ull;
 constexpr uint32_t kSwizzle64 = 4;                 // descriptor code of SWIZZLE_64B
 constexpr uint32_t kSBO = 8 * kRowBytes;           // 8 rows x 64 bytes per swizzle atom
 
@@ -174,9 +177,13 @@ struct TcLaunch {
   const TcGroup* groups;               // device array
   const TcSeg* segs;                   // device array, ascending tile0
   int nsegs, total_tiles;
+  int nstages;                         // operand stages in the ring (<= kMaxStages)
+  int btile;                           // bytes of one B plane tile: widest N tile x 64
+  int stage_bytes;                     // 2 kTileA + 2 btile
   int* tile_counter;                   // zeroed before the launch
   int* counters;                       // dependency counters, zeroed before the launch (or NULL)
   int* status;
+  unsigned long long wait_ns;          // limit of every pipeline wait
 };
 
 struct TileRef {
@@ -228,11 +235,15 @@ template <class F>
 __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const __grid_constant__ TcLaunch L) {
   using T = typename F::T;
   extern __shared__ uint8_t smem_raw[];
-  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint8_t* ostage = smem + kStages * kStageBytes;  // epilogue staging (1024-aligned)
+  uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* ostage = base;                                // epilogue staging (1024-aligned)
   uint64_t* full = reinterpret_cast<uint64_t*>(ostage + kOutStaging);
-  uint64_t* empty = full + kStages;
-  uint64_t* tfull = empty + kStages;   // [2]
+  uint8_t* smem = ostage + kOutStaging + kBarBytes;      // operand stages (1024-aligned)
+  const int nst = L.nstages;
+  const int stage_bytes = L.stage_bytes;
+  const int btile = L.btile;
+  uint64_t* empty = full + kMaxStages;
+  uint64_t* tfull = empty + kMaxStages;  // [2]
   uint64_t* tempty = tfull + 2;        // [2]
   uint64_t* drain = tempty + 2;        // [1]
   uint64_t* sfull = drain + 1;         // [kRing] a tile id is in the ring slot
@@ -243,7 +254,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const __grid_con
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kStages; ++s) {
+    for (int s = 0; s < nst; ++s) {
       ptx::mbar_init(&full[s], 1);
       ptx::mbar_init(&empty[s], 1);
     }
@@ -268,6 +279,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const __grid_con
   ptx::tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
   bool issued_mma = false;
+  // producer: stages armed at least once, and the phase parity of their last
+  // arming (an aborted launch waits for those loads to land before exiting)
+  uint32_t armed = 0, armed_par = 0;
 
   if (warp == 0) {
     if (lane == 0) {
@@ -278,7 +292,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const __grid_con
       int met_dep = -1, met_target = 0;  // last dependency seen satisfied (counters only grow)
       while (!*abort) {
         // take the next tile and hand its id to the MMA and epilogue roles
-        if (!ptx::mbar_wait(&sempty[rs], rph ^ 1, abort, kWaitNs)) {
+        if (!ptx::mbar_wait(&sempty[rs], rph ^ 1, abort, L.wait_ns)) {
           tc_fail(abort, L.status);
           break;
         }
@@ -294,7 +308,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const __grid_con
         const int mt = tr.mt, nt = tr.nt;
         if (SG.dep >= 0 && !(SG.dep == met_dep && SG.dep_target <= met_target)) {
           // the operands of this segment are written by earlier tiles of the launch
-          if (!ptx::counter_wait(L.counters + SG.dep, SG.dep_target, abort, kWaitNs)) {
+          if (!ptx::counter_wait(L.counters + SG.dep, SG.dep_target, abort, L.wait_ns)) {
             tc_fail(abort, L.status);
             break;
           }
@@ -310,17 +324,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const __grid_con
           // the other one for an odd factor
           const int koff = ((J.half ^ (pr.y & 1) ^ G.pxor) & 1) * G.hq;
           for (int kb = 0; kb < G.kblocks; ++kb) {
-            if (!ptx::mbar_wait(&empty[s], ph ^ 1, abort, kWaitNs)) {
+            if (!ptx::mbar_wait(&empty[s], ph ^ 1, abort, L.wait_ns)) {
               tc_fail(abort, L.status);
               break;
             }
-            uint8_t* st = smem + s * kStageBytes;
+            uint8_t* st = smem + s * stage_bytes;
+            armed |= 1u << s;
+            armed_par = (armed_par & ~(1u << s)) | (ph << s);
             ptx::mbar_arrive_expect_tx(&full[s], bytes);
             ptx::tma_load_3d(st, &G.a_hi, &full[s], koff + kb * F::kBK, mt * kBM, pr.x);
             ptx::tma_load_3d(st + kTileA, &G.a_lo, &full[s], koff + kb * F::kBK, mt * kBM, pr.x);
             ptx::tma_load_4d(st + 2 * kTileA, &G.b_hi, &full[s], kb * F::kBK, nt * G.bn, J.half, pr.y);
-            ptx::tma_load_4d(st + 2 * kTileA + kTileB, &G.b_lo, &full[s], kb * F::kBK, nt * G.bn, J.half, pr.y);
-            if (++s == kStages) { s = 0; ph ^= 1; }
+            ptx::tma_load_4d(st + 2 * kTileA + btile, &G.b_lo, &full[s], kb * F::kBK, nt * G.bn, J.half, pr.y);
+            if (++s == nst) { s = 0; ph ^= 1; }
           }
         }
       }
@@ -333,7 +349,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const __grid_con
       int rs = 0;
       uint32_t rph = 0;
       while (!*abort) {
-        if (!ptx::mbar_wait(&sfull[rs], rph, abort, kWaitNs)) {
+        if (!ptx::mbar_wait(&sfull[rs], rph, abort, L.wait_ns)) {
           tc_fail(abort, L.status);
           break;
         }
@@ -346,7 +362,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const __grid_con
         const TcJob J = G.jobs[tr.j];
         const uint32_t idesc = ptx::instr_desc(F::kFormat, kBM, (uint32_t)G.bn);
         const int kblocks = G.kblocks;
-        if (!ptx::mbar_wait(&tempty[buf], tph ^ 1, abort, kWaitNs)) {
+        if (!ptx::mbar_wait(&tempty[buf], tph ^ 1, abort, L.wait_ns)) {
           tc_fail(abort, L.status);
           break;
         }
@@ -356,20 +372,20 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const __grid_con
         bool ok = true;
         for (int pi = 0; pi < J.npairs && ok; ++pi) {
           for (int kb = 0; kb < kblocks; ++kb) {
-            if (!ptx::mbar_wait(&full[s], ph, abort, kWaitNs)) {
+            if (!ptx::mbar_wait(&full[s], ph, abort, L.wait_ns)) {
               tc_fail(abort, L.status);
               ok = false;
               break;
             }
             ptx::tc_fence_after();
-            const uint32_t st = ptx::smem_u32(smem + s * kStageBytes);
+            const uint32_t st = ptx::smem_u32(smem + s * stage_bytes);
 #pragma unroll
             for (int kk = 0; kk < 2; ++kk) {
               const uint32_t off = kk * 32;  // one MMA consumes 32 bytes of K
               const uint64_t ah = ptx::smem_desc(st + off, kSBO, kSwizzle64);
               const uint64_t al = ptx::smem_desc(st + kTileA + off, kSBO, kSwizzle64);
               const uint64_t bh = ptx::smem_desc(st + 2 * kTileA + off, kSBO, kSwizzle64);
-              const uint64_t bl = ptx::smem_desc(st + 2 * kTileA + kTileB + off, kSBO, kSwizzle64);
+              const uint64_t bl = ptx::smem_desc(st + 2 * kTileA + btile + off, kSBO, kSwizzle64);
               F::mma(d, ah, bh, idesc, acc);
               F::mma(d, ah, bl, idesc, 1u);
               F::mma(d, al, bh, idesc, 1u);
@@ -377,7 +393,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const __grid_con
             }
             issued_mma = true;
             ptx::mma_commit(&empty[s]);
-            if (++s == kStages) { s = 0; ph ^= 1; }
+            if (++s == nst) { s = 0; ph ^= 1; }
           }
         }
         if (!ok) break;
@@ -409,7 +425,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const __grid_con
         epi_signal(L.counters, pend, pend_n, pend_tma, 0, lane);
         pend = -1;
       }
-      if (!ptx::mbar_wait(&sfull[rs], rph, abort, kWaitNs)) {
+      if (!ptx::mbar_wait(&sfull[rs], rph, abort, L.wait_ns)) {
         tc_fail(abort, L.status);
         break;
       }
@@ -428,7 +444,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const __grid_con
         epi_signal(L.counters, pend, pend_n, pend_tma, 0, lane);
         pend = -1;
       }
-      if (!ptx::mbar_wait(&tfull[buf], tph, abort, kWaitNs)) {
+      if (!ptx::mbar_wait(&tfull[buf], tph, abort, L.wait_ns)) {
         tc_fail(abort, L.status);
         break;
       }
@@ -547,22 +563,22 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const __grid_con
     if (lane == 0) ptx::bulk_wait_all();  // staged stores finished before the block exits
   }
 
-  // teardown: after an abort let in-flight MMAs and copies land (bounded)
+  // teardown: after an abort let in-flight MMAs and copies land (each wait
+  // bounded by kDrainNs) before the shared memory and TMEM are released.  The
+  // epilogue warps have waited for their bulk stores after their loop.
   __syncwarp();
   ptx::tc_fence_before();
   __syncthreads();
   ptx::tc_fence_after();
   if (*abort) {
-    if (warp == 1 && lane == 0 && issued_mma) {
-      volatile int no_abort = 0;
+    volatile int no_abort = 0;
+    if (warp == 1 && lane == 0 && issued_mma) {  // every MMA issued so far
       ptx::mma_commit(drain);
-      ptx::mbar_wait(drain, 0, &no_abort, kWaitNs);
+      ptx::mbar_wait(drain, 0, &no_abort, kDrainNs);
     }
-    if (threadIdx.x == 0) {
-      const uint64_t t0 = ptx::globaltimer();
-      while (ptx::globaltimer() - t0 < 1000000ull) {
-      }
-    }
+    if (threadIdx.x == 0)  // the last loads into every stage: their phase completes when they land
+      for (int st = 0; st < nst; ++st)
+        if (armed & (1u << st)) ptx::mbar_wait(&full[st], (armed_par >> st) & 1u, &no_abort, kDrainNs);
     __syncthreads();
   }
   if (warp == 1) ptx::tmem_dealloc(tmem_base, 512);
@@ -1059,6 +1075,7 @@ struct TcBatch {
   int nsegs = 0, total = 0;
   int* ctr = nullptr;                  // device [1 + 2 count]: tile counter, then stage-done counters
   int nctr = 0;
+  int maxbn = 16;                      // widest N tile of all groups
 };
 
 struct TcHolder {
@@ -1389,7 +1406,7 @@ static demag_status prepare_form(demag_plan* P, TcState* S, cudaStream_t st) {
   DEMAG_CUDA(P, cudaGetDevice(&dev));
   const unsigned long long bit = 1ull << (dev & 63);
   if (!(attr & bit)) {
-    DEMAG_CUDA(P, cudaFuncSetAttribute(tc_gemm_kernel<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
+    DEMAG_CUDA(P, cudaFuncSetAttribute(tc_gemm_kernel<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax));
     attr |= bit;
   }
   return DEMAG_OK;
@@ -1589,23 +1606,29 @@ demag_status tc_prepare(demag_plan* P, demag_precision prec, cudaStream_t st) {
 
 template <class F>
 static demag_status launch_segs(demag_plan* P, const TcGroup* groups, const TcSeg* segs, int nsegs, int total_tiles,
-                               int* counter, int* counters, int ncounters, int* status, cudaStream_t st) {
+                               int maxbn, int* counter, int* counters, int ncounters, int* status, cudaStream_t st) {
   if (total_tiles <= 0) return DEMAG_OK;
   TcLaunch L;
   L.groups = groups;
   L.segs = segs;
   L.nsegs = nsegs;
   L.total_tiles = total_tiles;
+  // as many operand stages of the launch's widest N tile as fit
+  L.btile = maxbn * kRowBytes;
+  L.stage_bytes = (2 * kTileA + 2 * L.btile + 1023) / 1024 * 1024;
+  L.nstages = std::min(kMaxStages, (kSmemMax - kSmemFixed) / L.stage_bytes);
+  const int smem_bytes = kSmemFixed + L.nstages * L.stage_bytes;
   L.tile_counter = counter;
   L.counters = counters;
   L.status = status;
+  L.wait_ns = P->wait_ns;
   int sms = 0, dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int grid = total_tiles < sms ? total_tiles : sms;
   // the dependency counters follow the tile counter in the same buffer when present
   DEMAG_CUDA(P, cudaMemsetAsync(counter, 0, sizeof(int) * (1 + (counters ? ncounters : 0)), st));
-  DEMAG_LAUNCH(P, kFamGemmTc, st, tc_gemm_kernel<F><<<grid, kTcThreads, kSmemBytes, st>>>(L));
+  DEMAG_LAUNCH(P, kFamGemmTc, st, tc_gemm_kernel<F><<<grid, kTcThreads, smem_bytes, st>>>(L));
   DEMAG_LAUNCHED(P, "tc_gemm_kernel");
   return DEMAG_OK;
 }
@@ -1621,8 +1644,8 @@ static demag_status launch_small(demag_plan* P, const SmallStage& Q, cudaStream_
 template <class F>
 static demag_status run_program(demag_plan* P, TcState* S, int prog, cudaStream_t st) {
   if (S->small[prog]) return launch_small<F>(P, S->small_prog[prog], st);
-  return launch_segs<F>(P, S->prog + prog, S->seg + prog, 1, S->host_prog[prog].ntiles, S->counter, nullptr, 0,
-                        S->status, st);
+  return launch_segs<F>(P, S->prog + prog, S->seg + prog, 1, S->host_prog[prog].ntiles, S->host_prog[prog].bn,
+                        S->counter, nullptr, 0, S->status, st);
 }
 
 template <class F>
@@ -1765,6 +1788,7 @@ demag_status tc_batch_create(demag_plan* const* plans, int count, demag_precisio
       acc += g[gi].ntiles;
     }
   }
+  for (const TcGroup& gg : g) B->maxbn = std::max(B->maxbn, gg.bn);
   B->nsegs = (int)segs.size();
   B->total = acc;
   B->nctr = 2 * count;
@@ -1803,8 +1827,8 @@ static demag_status batched_chain(const TcBatch* B, const float* const* m, float
     demag_status s = launch_split<F>(P0, L, st);
     if (s != DEMAG_OK) return s;
   }
-  demag_status s = launch_segs<F>(P0, B->groups, B->segs, B->nsegs, B->total, B->ctr, B->ctr + 1, B->nctr,
-                                  S0->status, st);
+  demag_status s = launch_segs<F>(P0, B->groups, B->segs, B->nsegs, B->total, B->maxbn, B->ctr, B->ctr + 1,
+                                  B->nctr, S0->status, st);
   if (s != DEMAG_OK) return s;
   for (int i0 = 0; i0 < count; i0 += kMaxItems) {
     UnfoldList L;
@@ -1894,8 +1918,8 @@ static demag_status prepare_field(demag_plan* P, TcState* S, cudaStream_t st) {
 template <class F>
 static demag_status run_deriv(demag_plan* P, TcState* S, int st3, cudaStream_t st) {
   if (S->small[kFwd1 + st3]) return launch_small<F>(P, S->small_dprog[st3], st);
-  return launch_segs<F>(P, S->dprog + st3, S->dseg + st3, 1, S->dprog_host[st3].ntiles, S->counter, nullptr, 0,
-                          S->status, st);
+  return launch_segs<F>(P, S->dprog + st3, S->dseg + st3, 1, S->dprog_host[st3].ntiles, S->dprog_host[st3].bn,
+                        S->counter, nullptr, 0, S->status, st);
 }
 
 // h_d[p] = -dphi/dxi_p.  The three chains share work: the stage-1 output feeds

@@ -82,6 +82,9 @@ struct demag_plan {
   // per-fibre full format: two work volumes of 3M fields each
   float* fib_ws = nullptr;
 
+  // limit of the bounded device-side waits of the tensor-core kernels (ns)
+  unsigned long long wait_ns = 2000000000ull;
+
   // autotuning: when on, launch shapes not yet tuned are timed on first use
   bool autotune = false;
   struct Tuned {

@@ -542,6 +542,14 @@ extern "C" demag_status demag_sync_status(demag_plan* plan, void* stream) {
 
 extern "C" unsigned long long demag_launch_count(const demag_plan* plan) { return plan ? plan->launches : 0ULL; }
 
+extern "C" demag_status demag_set_wait_limit(demag_plan* plan, double seconds) {
+  if (!plan) return set_error(nullptr, DEMAG_EINVAL, "demag_set_wait_limit: plan is NULL");
+  if (!(seconds >= 0.0 && seconds <= 60.0))
+    return set_error(plan, DEMAG_EINVAL, "demag_set_wait_limit: %g s is outside [0, 60]", seconds);
+  plan->wait_ns = (unsigned long long)(seconds * 1e9);
+  return DEMAG_OK;
+}
+
 extern "C" demag_status demag_autotune(demag_plan* plan, int enable) {
   if (!plan) return set_error(nullptr, DEMAG_EINVAL, "demag_autotune: plan is NULL");
   plan->autotune = enable != 0;

@@ -1,0 +1,55 @@
+"""The bounded-wait failure path of the tensor-core kernels, made to happen.
+
+Every device-side wait of the tcgen05 pipeline (mbarriers between its roles,
+completion counters between tiles of one launch) gives up after the plan's
+wait limit, sets DEMAG_ETIMEOUT in the plan's status word, lets every copy and
+MMA it issued land, releases its tensor memory and returns.  A zero limit makes
+the first wait that is not already satisfied give up; the status must say so,
+and the same plan with the default limit must then give the oracle's result.
+No fault, trap or endless loop is involved: the kernel returns on its own.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import full as ofull
+from gpu_helpers import TOL, assert_close, dev, host
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def D():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1212_3509_gb300 as D
+    return D
+
+
+def test_zero_wait_limit_reports_timeout_then_plan_recovers(D):
+    n, h, R = (48, 40, 37), (1 / 48,) * 3, 21  # every axis > 16 cells: all stages on tcgen05
+    m = synth.random_unit_m(n, 1230)
+    P = D.demag_build_factors(n, h, R)
+    phi = torch.empty(n[2], n[1], n[0], device="cuda")
+    D.demag_apply_full(P, dev(m), phi, "bf16x3")  # prepares the tensor-core state
+    D.demag_sync_status(P)
+    D.demag_set_wait_limit(P, 0.0)
+    D.demag_apply_full(P, dev(m), phi, "bf16x3")
+    with pytest.raises(D.DemagError) as ei:
+        D.demag_sync_status(P)
+    assert ei.value.status == 4  # DEMAG_ETIMEOUT
+    D.demag_set_wait_limit(P, 2.0)
+    phi.fill_(float("nan"))
+    D.demag_apply_full(P, dev(m), phi, "bf16x3")
+    D.demag_sync_status(P)
+    assert_close(host(phi), ofull.apply_full(m, n, h, R), TOL["bf16x3"])
+
+
+def test_wait_limit_is_validated(D):
+    P = D.demag_build_factors((8, 8, 8), (1 / 8,) * 3, 11)
+    for bad in (-1.0, 61.0, float("nan")):
+        with pytest.raises(D.DemagError) as ei:
+            D.demag_set_wait_limit(P, bad)
+        assert ei.value.status == 1
