@@ -32,13 +32,38 @@ sys.path.insert(0, ROOT)
 
 METRIC = "demag potential apps/s at 256³ full & n=4096 CP; rel L2 err vs FP64 oracle"
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
-# DRAM bytes (read + write) from ncu captures of the kernels as they stand, scaled
-# to the bench workloads by the units processed (the captures are smaller cases;
-# traffic grows in proportion): the three tcgen05 mode-product stages at 192^3
-# BF16x3 (5.80 GB) scaled to one 256^3 application; the Toeplitz FFT launch for
-# a CP batch of 32 (549.8 MB) scaled to a batch of 256.
-NCU_TRAFFIC_FULL256_BF16X3 = 13.81e9
-NCU_TRAFFIC_CP4096_PER_APP = 549.8e6 / 32
+# DRAM bytes (read + write) per unit of work from ncu captures of smaller cases
+# of the same kernels (traffic grows in proportion to the units processed), each
+# keyed by a digest of the kernel's sources at capture time: a kernel changed
+# since its capture reports traffic null.  The capture commands and their
+# figures are summarised under profiles/.
+NCU_TRAFFIC = {
+    # the three tcgen05 mode-product stages of one application, BF16x3, R = 41,
+    # per cell of the grid (captured at 192^3, folded axes)
+    "tc_gemm_kernel": {"sources": ("full_tc.cu", "tc_ptx.cuh"), "sha": None, "bytes_per_cell": None},
+    # the Toeplitz FFT launch of a CP batch, n = 4096, r = 4, R = 61, per application
+    "toeplitz_fft_kernel": {"sources": ("structured.cu", "fft.cuh"), "sha": None, "bytes_per_app": None},
+}
+
+
+def sources_sha(names):
+    """Digest of the named CUDA sources of the package (the kernel as it stands)."""
+    import hashlib
+    hsh = hashlib.sha256()
+    for name in names:
+        with open(os.path.join(ROOT, "paper_1212_3509_gb300", "csrc", name), "rb") as f:
+            hsh.update(f.read())
+    return hsh.hexdigest()[:16]
+
+
+def ncu_traffic(kernel, units, unit_key):
+    """Captured DRAM bytes for `units` units, or None when the kernel changed since the capture."""
+    rec = NCU_TRAFFIC[kernel]
+    if rec["sha"] is None or rec.get(unit_key) is None or sources_sha(rec["sources"]) != rec["sha"]:
+        return None
+    return rec[unit_key] * units
+
+
 # FP32 CUDA-core peak of a GB300: 152 SMs x 128 FP32 lanes x 2 flops (FMA) x 2.07 GHz
 FP32_SIMT_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 
@@ -58,6 +83,10 @@ def parse():
     ap.add_argument("--no-oracle", action="store_true", help="skip the oracle error check and CPU baseline")
     ap.add_argument("--no-fig2", dest="fig2", action="store_false",
                     help="skip the uniform-cube energy study (Tucker format, n = 64..4096)")
+    ap.add_argument("--cpu-table", action="store_true",
+                    help="time the FP64 oracle on every configuration with 1 and with all host threads "
+                         "(bounded samples) and print one JSON object; no GPU work")
+    ap.add_argument("--cpu-one", default=None, help=argparse.SUPPRESS)
     return ap.parse_args()
 
 
@@ -211,6 +240,9 @@ def run_ours(args, world, rank, local):
     n3, h, R = full_config(args.n)
     form = args.form
     P = D.demag_build_factors(n3, h, R)
+    # the autotuner times its candidates when the tensor-core state is created
+    # (below, or on the first application), before the timed region
+    D.demag_autotune(P, True)
     if form == "auto":
         form = "fp32"
         for cand in ("bf16x3",):
@@ -249,34 +281,63 @@ def run_ours(args, world, rank, local):
     ms_full_max = max_over_ranks(ms_full, world)
 
     M = P.M
-    flops_app = 16.0 * (args.n ** 4) * M  # 8 mode-product GEMMs of n^4 MACs per node
+    N1 = args.n
+    # algorithmic work per application (the dense contraction of the survey's
+    # measurement section): 9 mode products of 2 n^4 flop per node; with the
+    # 8-GEMM sharing of the chain 16 n^4 per node
+    flops_app = 18.0 * (N1 ** 4) * M
+    flops_app_8 = 16.0 * (N1 ** 4) * M
     gemm_ms_app = gemm_ms / args.steps
     achieved_tflops = flops_app / (gemm_ms_app * 1e-3) / 1e12
     hbm = peaks.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"])
+    hbm_note = f"{peak_src} STREAM copy (HBM)"
     if fam == "gemm_tc":
         tpeak = peaks.get("bf16_tflops", PEAKS_FALLBACK["bf16_tflops"])
         if form == "tf32x3":
             tpeak = tpeak / 2.0  # TF32 dense rate is half the BF16 rate
         tpeak_note = f"{peak_src} dense {'bf16' if form == 'bf16x3' else 'tf32 (bf16/2)'} burst"
-        # algorithmic DRAM bytes of the three mode-product stages: the split
-        # input (3 fields), the stage-1 intermediates (3M fields, written and
-        # read), the stage-2 intermediates (2M fields, written and read), each
-        # as a hi and a lo plane, and the FP32 node-sum partial fields
+        # algorithmic DRAM bytes of the three mode-product stages (folded
+        # layout, the axis extents padded to 2 hq): the split input (3 fields),
+        # the stage-1 intermediates (3M fields, written and read), the stage-2
+        # intermediates (2M fields, written and read), each as a hi and a lo
+        # plane, and the FP32 node-sum partial fields
         pair = 4 if form == "bf16x3" else 8
-        kb3 = -(-args.n // (32 if form == "bf16x3" else 16))
+        al = 8 if form == "bf16x3" else 4
+        hq = -(-((N1 + 1) // 2) // al) * al
+        ext = 2 * hq if N1 > 16 else N1
+        Nc = ext ** 3
+        kb3 = -(-((N1 + 1) // 2 if N1 > 16 else N1) // (32 if form == "bf16x3" else 16))
         pp3 = max(1, (400 if form == "bf16x3" else 200) // (kb3 * 6))
         groups = -(-2 * M // pp3)
-        Nc = args.n ** 3
         gemm_bytes_app = pair * Nc * (3 + 10 * M) + 4.0 * groups * Nc
         achieved_gbs = gemm_bytes_app / (gemm_ms_app * 1e-3) / 1e9
-        bound, peak, achieved, unit = "hbm", hbm, achieved_gbs, "GB/s"
-        peak_note = f"{peak_src} STREAM copy (HBM)"
+        # the folded chain contracts h = n/2 entries per output (half the dense
+        # MACs); the split forms issue 3 tensor-core products per product
+        issued_tflops = flops_app_8 / 2.0 * 3.0 / (gemm_ms_app * 1e-3) / 1e12
+        traffic = ncu_traffic("tc_gemm_kernel", N1 ** 3, "bytes_per_cell") if form == "bf16x3" else None
+        roofline = {"kernel": "tc_gemm_kernel (tcgen05 mode products), the three stage launches of one application",
+                    "bound": "tensor", "achieved": achieved_tflops, "peak": tpeak, "unit": "TFLOP/s",
+                    "frac": achieved_tflops / tpeak, "traffic": traffic,
+                    "peak_source": tpeak_note,
+                    "algorithmic_flops_per_app": flops_app,
+                    "achieved_8gemm": flops_app_8 / (gemm_ms_app * 1e-3) / 1e12,
+                    "frac_8gemm": flops_app_8 / (gemm_ms_app * 1e-3) / 1e12 / tpeak,
+                    "algorithmic_flops_per_app_8gemm": flops_app_8,
+                    "issued_tflops": issued_tflops, "issued_frac": issued_tflops / tpeak,
+                    "hbm": {"achieved": achieved_gbs, "peak": hbm, "unit": "GB/s", "frac": achieved_gbs / hbm,
+                            "algorithmic_bytes_per_app": gemm_bytes_app, "peak_source": hbm_note},
+                    "launches_per_app": gemm_n / args.steps, "kernel_ms_per_app": gemm_ms_app,
+                    "stage_ms_per_app": stage_ms,
+                    "split_ms_per_app": split_ms / args.steps,
+                    "reduce_ms_per_app": misc_ms / args.steps}
     else:
-        gemm_bytes_app = None
         tpeak = FP32_SIMT_PEAK_TFLOPS
         tpeak_note = "FP32 FMA peak from unit counts and max clock (152 SMs x 128 lanes x 2 x 2.07 GHz)"
-        bound, peak, achieved, unit = "alu", tpeak, achieved_tflops, "TFLOP/s"
-        peak_note = tpeak_note
+        roofline = {"kernel": "gemm_tn_kernel (CUDA-core mode products), all stages of one application",
+                    "bound": "alu", "achieved": achieved_tflops, "peak": tpeak, "unit": "TFLOP/s",
+                    "frac": achieved_tflops / tpeak, "traffic": None, "peak_source": tpeak_note,
+                    "algorithmic_flops_per_app": flops_app, "launches_per_app": gemm_n / args.steps,
+                    "kernel_ms_per_app": gemm_ms_app, "stage_ms_per_app": stage_ms}
 
     # e2e through the public API with pinned host buffers: every step copies its
     # m from pinned host memory, applies the operator and reads phi back; steps
@@ -335,6 +396,7 @@ def run_ours(args, world, rank, local):
     Mc = PC.M
     out_w = torch.empty(B * Mc * 3 * r, device="cuda")
     out_U = torch.empty(B * Mc * 3 * r * 3 * ncp, device="cuda")
+    D.demag_autotune(PC, True)
     cp_fn = lambda: D.demag_apply_cp_batched(PC, B, r, lam, U, out_w, out_U)  # noqa: E731
     for _ in range(args.warmup):
         cp_fn()
@@ -390,49 +452,35 @@ def run_ours(args, world, rank, local):
                   "bf16x3": "bf16x3 (f32 accumulate)"}[form],
         "data": "synthetic (seeded vortex state + 5% noise; smooth random CP factors)",
         "config": bench_config(args, form, world),
-        "roofline": {"kernel": "mode-product GEMM (" + fam + "), all stages of one application",
-                     "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-                     "frac": achieved / peak,
-                     "traffic": (NCU_TRAFFIC_FULL256_BF16X3 if (form == "bf16x3" and args.n == 256) else None),
-                     "traffic_note": "DRAM bytes per application: ncu capture of the three stages at 192^3 "
-                                     "scaled by cells (profiles/tc_gemm_bf16x3_full192.md)",
-                     "peak_source": peak_note,
-                     "algorithmic_bytes_per_app": gemm_bytes_app,
-                     "launches_per_app": gemm_n / args.steps, "kernel_ms_per_app": gemm_ms_app,
-                     "split_ms_per_app": split_ms / args.steps,
-                     "stage_ms_per_app": stage_ms,
-                     "reduce_ms_per_app": misc_ms / args.steps,
-                     "tensor": {"achieved_tflops": achieved_tflops, "peak_tflops": tpeak,
-                                "frac": achieved_tflops / tpeak, "peak_source": tpeak_note,
-                                "algorithmic_flops_per_app": flops_app,
-                                # the split forms issue 3 tensor-core products per algorithmic product
-                                "issued_frac": achieved_tflops * (3 if fam == "gemm_tc" else 1) / tpeak}},
+        "roofline": roofline,
         "cp": {"value": world * B * 1e3 / ms_cp_max, "unit": "apps/s", "ms_per_batch": ms_cp_max,
                "batch": B,
-               "roofline": {"kernel": "toeplitz_fft_kernel", "bound": "alu", "achieved": fft_tflops,
-                            "peak": FP32_SIMT_PEAK_TFLOPS, "unit": "TFLOP/s",
-                            "frac": fft_tflops / FP32_SIMT_PEAK_TFLOPS,
-                            "traffic": (NCU_TRAFFIC_CP4096_PER_APP * B if ncp == 4096 else None),
-                            "traffic_note": "DRAM bytes per batch launch: ncu capture of a batch of 32 scaled "
-                                            "to the batch (profiles/toeplitz_fft_cp4096_b32.md)",
-                            "algorithmic_flops_per_app": fft_flops_app,
-                            "hbm_achieved_gbs": fft_gbs, "hbm_peak_gbs": hbm, "hbm_frac": fft_gbs / hbm,
+               "roofline": {"kernel": "toeplitz_fft_kernel", "bound": "hbm", "achieved": fft_gbs, "peak": hbm,
+                            "unit": "GB/s", "frac": fft_gbs / hbm,
+                            "traffic": (ncu_traffic("toeplitz_fft_kernel", B, "bytes_per_app")
+                                        if ncp == 4096 else None),
                             "algorithmic_bytes_per_app": bytes_app, "launches_per_batch": fft_n / args.steps,
-                            "kernel_ms_per_batch": fft_ms / args.steps,
-                            "peak_source": "FP32 FMA peak from unit counts and max clock; HBM: "
-                                           f"{peak_src} STREAM copy"},
+                            "kernel_ms_per_batch": fft_ms / args.steps, "peak_source": hbm_note,
+                            "alu": {"achieved": fft_tflops, "peak": FP32_SIMT_PEAK_TFLOPS, "unit": "TFLOP/s",
+                                    "frac": fft_tflops / FP32_SIMT_PEAK_TFLOPS,
+                                    "algorithmic_flops_per_app": fft_flops_app,
+                                    "peak_source": "FP32 FMA peak from unit counts and max clock"}},
                "gpu_launches": launches_cp,
                "clocks": clk_cp.summary()},
         "e2e": {"value": world * 1e3 / ms_e2e, "unit": "apps/s",
                 "h2d_bytes_per_step": int(m.numel() * 4), "d2h_bytes_per_step": int(phi.numel() * 4)},
         "gpu_launches": int(launches_full),
         "clocks": clk.summary(),
+        "autotune": {"full": [D.demag_autotune_entry(P, i) for i in range(D.demag_autotune_count(P))],
+                     "cp": [D.demag_autotune_entry(PC, i) for i in range(D.demag_autotune_count(PC))],
+                     "note": "chosen per stage program before the timed region; ms = chosen, "
+                             "ms_default = the default setting, per launch"},
     }
 
     # ---------------- every full-format form on the same input (C2: error per form)
     phis = {}
     forms = {}
-    for f in ("fp32", "tf32x3", "bf16x3"):
+    for f in ("fp64", "fp32", "tf32x3", "bf16x3"):
         try:
             D.demag_reserve_workspace(P, f)
         except D.DemagError:
@@ -441,9 +489,12 @@ def run_ours(args, world, rank, local):
         fn = lambda: D.demag_apply_full(P, m, out, f)  # noqa: E731
         fn()
         torch.cuda.synchronize()
-        ms_f = time_region(fn, max(2, args.steps // 3), stream)
+        ms_f = time_region(fn, 2 if f == "fp64" else max(2, args.steps // 3), stream)
         forms[f] = {"apps_per_s": 1e3 / ms_f, "ms_per_app": ms_f}
         phis[f] = out
+
+    # ---------------- the 128^3 point of the same configuration, every form
+    c2_128 = run_c2_128(args, D, stream) if args.n == 256 else None
 
     # ---------------- the same operator by one 3D FFT convolution (Eq. fft_pot, node-summed kernel)
     fft3d = run_fft3d(args, D, world, local, stream, P, m, phi, peaks, n3)
@@ -534,6 +585,20 @@ def run_ours(args, world, rank, local):
         result["cp"]["rel_l2"] = float(np.linalg.norm(got_cp - ref_cp) / np.linalg.norm(ref_cp))
         result["cpu_baseline"] = cpu_baseline(n3, h, R, m_host, budget_s=20.0)
     result["forms_full"] = forms
+    if c2_128 is not None:
+        if not args.no_oracle and rank == 0:
+            from oracle import full as ofull
+            n128, h128, R128 = full_config(128)
+            lines = [(0, 0), (64, 42), (127, 127), (32, 121)]
+            ref = ofull.apply_full_lines(c2_128["_m"], n128, h128, R128, lines)
+            for f, field in c2_128["_phi"].items():
+                got = field.cpu().numpy()
+                g = np.stack([got[i3, i2] for i3, i2 in lines])
+                c2_128["forms"][f]["rel_l2"] = float(np.linalg.norm(g - ref) / np.linalg.norm(ref))
+            c2_128["rel_l2_sample"] = f"{len(lines)} output lines phi[i3,i2,:] vs the FP64 oracle"
+        c2_128.pop("_m")
+        c2_128.pop("_phi")
+        result["full_128"] = c2_128
     if fft3d is not None:
         fft3d.pop("_phi", None)
         result["full_fft3d"] = fft3d
@@ -588,28 +653,64 @@ def run_ours(args, world, rank, local):
     print(json.dumps(result), flush=True)
 
 
-def run_fig2(args, D, stream, R=129, sizes=(64, 128, 256, 512, 1024, 2048, 4096), tol=1e-6):
+def run_c2_128(args, D, stream):
+    """The 128^3 point of the full-format configuration (R = 41, vortex + 5% noise), every form."""
+    import torch
+    import synth
+    n3, h, R = full_config(128)
+    P = D.demag_build_factors(n3, h, R)
+    m_host = synth.vortex_m(n3, 1213)
+    m = torch.from_numpy(m_host).cuda()
+    forms, phis = {}, {}
+    for f in ("fp64", "fp32", "tf32x3", "bf16x3"):
+        out = torch.empty(128, 128, 128, device="cuda")
+        fn = lambda: D.demag_apply_full(P, m, out, f)  # noqa: E731
+        fn()
+        torch.cuda.synchronize()
+        ms_f = time_region(fn, 3 if f == "fp64" else max(3, args.steps), stream)
+        forms[f] = {"apps_per_s": 1e3 / ms_f, "ms_per_app": ms_f}
+        phis[f] = out
+    D.demag_sync_status(P)
+    return {"grid": "128^3", "R": R, "forms": forms, "_m": m_host, "_phi": phis}
+
+
+def fig2_terms(n, c0=2.15):
+    """R for the n^3 uniform cube of the energy study: the sinc rule is not uniform
+    in h (Remark after Lemma 2), so the largest node tau_max = sinh(c0 ln M) must
+    grow with the cells per edge; the smallest M of 64, 128, 256 with
+    tau_max >= 8 n (tau_max h >= 8 on the unit cube)."""
+    import math
+    for M in (64, 128, 256):
+        if math.sinh(c0 * math.log(M)) >= 8 * n:
+            return 2 * M + 1
+    return 513
+
+
+def run_fig2(args, D, stream, sizes=(64, 128, 256, 512, 1024, 2048, 4096), tol=1e-6):
     """The energy study after Alg. 2: the uniformly magnetized unit cube (m = z, a rank-1 Tucker
     tensor) on n^3 grids, its potential in Tucker form and the second-order energy without forming
-    a full tensor.  Per n: the relative energy error against the continuum value 1/6 and the time
-    of one application plus energy (CUDA events, plain operator); and Alg. 2 proper (kernels
-    compressed at tol, compressed application, approximate summation at tol, energy of the single
-    Tucker potential): its ranks, energy error and wall time."""
+    a full tensor.  Per n (R growing with n, fig2_terms): the relative energy error against the
+    continuum value 1/6 and the time of one application plus energy (CUDA events, plain operator);
+    and Alg. 2 proper (kernels compressed at tol, compressed application, approximate summation at
+    tol, energy of the single Tucker potential) at R = 129, the largest R its compression takes:
+    its ranks, energy error and wall time."""
     import math
     import time as _t
     import torch
-    out = {"R": R, "tol": tol, "sizes": list(sizes), "rows": [],
+    out = {"tol": tol, "sizes": list(sizes), "R_rule": "smallest M in {64, 128, 256} with sinh(c0 ln M) >= 8 n",
+           "rows": [],
            "work": "demag_apply_tucker + demag_energy_tucker (rank 1); Alg. 2: demag_compress_kernel, "
-                   "demag_apply_tucker_compressed, demag_recompress_tucker, demag_energy_tucker_phi"}
+                   "demag_apply_tucker_compressed, demag_recompress_tucker, demag_energy_tucker_phi (R = 129)"}
     ranks = (1, 1, 1)
     for n in sizes:
-        P = D.demag_build_factors((n, n, n), (1.0 / n,) * 3, R)
+        R = fig2_terms(n)
         core = torch.zeros(3, device="cuda")
         core[2] = 1.0
         V = torch.ones(9 * n, device="cuda")
+        E = torch.empty((), dtype=torch.float64, device="cuda")
+        P = D.demag_build_factors((n, n, n), (1.0 / n,) * 3, R)
         w = torch.empty(P.M * 3, device="cuda")
         oV = torch.empty(P.M * 9 * n, device="cuda")
-        E = torch.empty((), dtype=torch.float64, device="cuda")
 
         def fn():
             D.demag_apply_tucker(P, ranks, V, w, oV)
@@ -619,29 +720,32 @@ def run_fig2(args, D, stream, R=129, sizes=(64, 128, 256, 512, 1024, 2048, 4096)
         torch.cuda.synchronize()
         ms = time_region(fn, 20, stream)
         e = float(E.item())
-        row = {"n": n, "energy": e, "rel_err": abs(e - 1.0 / 6.0) * 6.0, "ms_apply_energy": ms}
+        row = {"n": n, "R": R, "energy": e, "rel_err": abs(e - 1.0 / 6.0) * 6.0, "ms_apply_energy": ms}
+        del P
         try:
-            D.demag_compress_kernel(P, tol)
-            rho = D.demag_compressed_ranks(P)
+            P2 = D.demag_build_factors((n, n, n), (1.0 / n,) * 3, 129)
+            D.demag_compress_kernel(P2, tol)
+            rho = D.demag_compressed_ranks(P2)
             out_V = torch.empty(sum(3 * rho[p] * n for p in range(3)), device="cuda")
             torch.cuda.synchronize()
             t0 = _t.perf_counter()
-            D.demag_apply_tucker_compressed(P, 1, ranks, core, V, None, out_V)
-            rk, C, Us, _ = D.demag_recompress_tucker(P, ranks, core, out_V, tol)
-            D.demag_energy_tucker_phi(P, ranks, core, V, rk, C.contiguous().view(-1),
+            D.demag_apply_tucker_compressed(P2, 1, ranks, core, V, None, out_V)
+            rk, C, Us, _ = D.demag_recompress_tucker(P2, ranks, core, out_V, tol)
+            D.demag_energy_tucker_phi(P2, ranks, core, V, rk, C.contiguous().view(-1),
                                       torch.cat([u.reshape(-1) for u in Us]), E)
             ea = float(E.item())
-            row["alg2"] = {"kernel_ranks": list(rho), "phi_ranks": list(rk), "energy": ea,
+            row["alg2"] = {"R": 129, "kernel_ranks": list(rho), "phi_ranks": list(rk), "energy": ea,
                            "rel_err": abs(ea - 1.0 / 6.0) * 6.0, "seconds": _t.perf_counter() - t0}
+            del P2
         except D.DemagError as ex:
             row["alg2"] = {"unavailable": str(ex)}
         out["rows"].append(row)
-        del P
     errs = [r["rel_err"] for r in out["rows"]]
     out["order_per_doubling"] = [math.log2(errs[i] / errs[i + 1]) if errs[i + 1] > 0 else None
                                  for i in range(len(errs) - 1)]
-    out["note"] = ("errors are against the continuum energy 1/6; beyond n ~ 1024 the R = 129 sinc "
-                   "quadrature (tau_max ~ 3.8e3) no longer resolves the cell scale and its error dominates")
+    a2 = [r["alg2"].get("rel_err") for r in out["rows"]]
+    out["alg2_order_per_doubling"] = [math.log2(a2[i] / a2[i + 1]) if a2[i] and a2[i + 1] else None
+                                      for i in range(len(a2) - 1)]
     return out
 
 
@@ -1125,19 +1229,111 @@ def run_reference(args, world, rank, local):
         step()
     dt = (time.perf_counter() - t0) / args.steps
     value = (1.0 / M) / dt
+    # a step is the bounded sample (one node of M), timed as it runs; the rate
+    # counts it as 1/M of an application
     out = {"metric": METRIC, "value": value, "unit": "apps/s", "impl": "reference", "n_gpus": world,
-           "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 * M, "higher_is_better": True,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "app_fraction_per_step": 1.0 / M,
+           "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded vortex state)",
            "config": dict(bench_config(args, "fp64 CPU oracle", world), parallelism="host cores"),
            "cpu_baseline": {"value": value, "unit": "apps/s", "cores": os.cpu_count(), "kind": "oracle",
-                            "sample": f"each step: 1 of {M} nodes of the {args.n}^3 full-format application, "
-                                      "scaled to one app"},
+                            "sample": f"each step: 1 of {M} nodes of the {args.n}^3 full-format application "
+                                      "(numpy float64, default BLAS threads), counted as 1/M app"},
            "e2e": {"value": value, "unit": "apps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
 
+CPU_CONFIGS = ("c1_16", "c2_128", "c2_256", "c3_cp4096", "c4_tucker1024", "c4_tt1024", "c5_batch64")
+
+
+def cpu_one(cfg):
+    """One bounded oracle sample of configuration `cfg`: (apps per second, what was sampled)."""
+    import numpy as np
+    import synth
+    from oracle import full as ofull, structured as ost
+
+    def timed(fn):
+        t0 = time.perf_counter()
+        fn()
+        return time.perf_counter() - t0
+
+    if cfg in ("c1_16", "c2_128", "c2_256"):
+        n = {"c1_16": 16, "c2_128": 128, "c2_256": 256}[cfg]
+        n3, h, R = full_config(n)
+        M = (R - 1) // 2
+        m = synth.vortex_m(n3, 1213) if n > 16 else synth.random_unit_m(n3, 1212)
+        done, t = 0, 0.0
+        while done < M and t < 10.0:
+            t += timed(lambda: ofull.apply_full(m, n3, h, R, nodes=[done]))
+            done += 1
+        return (done / M) / t, f"full format {n}^3, R = {R}: {done} of {M} nodes, counted as {done}/{M} app"
+    if cfg == "c3_cp4096":
+        n3, h, R, r = cp_config(4096)
+        lam, U = synth.cp_inputs(n3, r, 1214)
+        t = timed(lambda: ost.apply_cp(lam, U, n3, h, R))
+        return 1.0 / t, "one CP application, n = 4096, rank 4, R = 61 (dense O(n^2) Toeplitz matvecs)"
+    if cfg == "c4_tucker1024":
+        n3, h = (1024,) * 3, (1 / 1024,) * 3
+        core, V = synth.tucker_inputs(n3, (8, 8, 8), 1219)
+        t = timed(lambda: ost.apply_tucker(core, V, n3, (8, 8, 8), h, 61))
+        return 1.0 / t, "one Tucker application, n = 1024, ranks (8, 8, 8), R = 61"
+    if cfg == "c4_tt1024":
+        n3, h = (1024,) * 3, (1 / 1024,) * 3
+        G1, G2, G3 = synth.tt_inputs(n3, (8, 8), 1220)
+        t = timed(lambda: ost.apply_tt(G1, G2, G3, n3, (8, 8), h, 61))
+        return 1.0 / t, "one TT application, n = 1024, TT ranks (8, 8), R = 61"
+    if cfg == "c5_batch64":
+        shapes = synth.uneven_batch_shapes(64, 1215)
+        total = 0.0
+        for sn in sorted(set(shapes)):
+            h = (1.0 / max(sn),) * 3
+            m = synth.random_unit_m(sn, 1216)
+            # one node of each distinct shape, scaled by the node count and its multiplicity
+            total += shapes.count(sn) * 20 * timed(lambda: ofull.apply_full(m, sn, h, 41, nodes=[0]))
+        return 64.0 / total, ("64-grid batch: one of 20 nodes of each of its 13 distinct shapes, "
+                              "scaled by 20 and by the shape's count; grids/s")
+    raise ValueError(cfg)
+
+
+def cpu_table():
+    """Oracle throughput per configuration with 1 host thread and with all of them."""
+    import platform
+    ncpu = os.cpu_count() or 1
+    model = platform.processor() or platform.machine()
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part", "hardware")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    rows = {}
+    for threads in (1, ncpu):
+        env = dict(os.environ)
+        for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
+            env[k] = str(threads)
+        for cfg in CPU_CONFIGS:
+            r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-one", cfg], env=env,
+                               capture_output=True, text=True)
+            try:
+                rec = json.loads(r.stdout.strip().splitlines()[-1])
+            except (ValueError, IndexError):
+                rec = {"error": (r.stderr or r.stdout)[-300:]}
+            rows.setdefault(cfg, {})[f"threads_{threads}"] = rec
+    print(json.dumps({"cpu_table": rows, "cores": ncpu, "cpu_model": model, "machine": platform.machine()}),
+          flush=True)
+
+
 def main():
     args = parse()
+    if args.cpu_one:
+        v, what = cpu_one(args.cpu_one)
+        print(json.dumps({"value": v, "sample": what}), flush=True)
+        return
+    if args.cpu_table:
+        cpu_table()
+        return
     world, rank, local = dist_init()
     if args.impl == "reference":
         run_reference(args, world, rank, local)

@@ -527,19 +527,35 @@ demag_status demag_profile_launch(demag_plan* plan, long long i, int* family, do
  *    three timed launches each, on the call's stream, which is synchronised)
  *    and keeps the fastest for later launches of that shape;
  *  - tensor-core state created afterwards (first DEMAG_TF32X3 / DEMAG_BF16X3
- *    use) times, per mode-product stage, the output-column tile widths
- *    {default, 128, 64} below the default (zero operands, stage timed alone)
- *    and keeps the fastest.
- * The tuning launches write the call's own outputs, so results are those of
- * an untuned call.  No tuning happens while the stream is being captured.
+ *    use) times, per mode-product stage program, one knob after the other
+ *    and keeps each at its fastest value: the output-column tile width
+ *    {default, 128, 64} below the default, the operand stages {as many as
+ *    fit, 4, 3, 2} and the tile order {every job of a row block in turn, every
+ *    row block of a job in turn} (operands as they are, stage timed alone).
+ * No knob changes the arithmetic of an output element: tuned and untuned
+ * results agree bit for bit.  The tuning launches write the call's own
+ * outputs.  No tuning happens while the stream is being captured.
  * demag_autotune(plan, 0) stops tuning and keeps what was chosen. */
 demag_status demag_autotune(demag_plan* plan, int enable);
-/* Number of tuned shapes, and entry i of them: kind (0 FFT node group, 1 BF16x3
- * tile width, 2 TF32x3 tile width), key (FFT: log2 of the complex FFT length,
- * column blocks, M; tensor core: stage program 0..5, default width, 0), the
- * chosen value and its time per launch in ms. */
+/* Number of tuned shapes, and entry i of them: kind (0 FFT node group; tensor
+ * cores, BF16x3 / TF32x3: 1 / 2 tile width, 3 / 4 operand stages (0 = as many
+ * as fit), 5 / 6 tile order), key (FFT: log2 of the complex FFT length, column
+ * blocks, M; tensor core: stage program 0..5, default value, 0), the chosen
+ * value, its time per launch and the default value's time per launch in ms
+ * (0 for an entry read from a cache). */
 int demag_autotune_count(const demag_plan* plan);
-demag_status demag_autotune_entry(const demag_plan* plan, int i, int* kind, int key[3], int* value, float* ms);
+demag_status demag_autotune_entry(const demag_plan* plan, int i, int* kind, int key[3], int* value, float* ms,
+                                  float* ms_default);
+/* Tuning cache: demag_autotune_save appends every entry of the plan to the
+ * text file `path` (HOST path), one JSON object per line keyed by the current
+ * GPU's UUID, the grid (n, R, uniform or not) and the entry's kind and key;
+ * demag_autotune_load reads the lines of `path` that match the current GPU
+ * and the plan's grid into the plan (a later line for the same entry wins;
+ * *loaded, if not NULL, receives their count; a missing file loads nothing).
+ * Load before the plan's first tensor-core use: its programs take the loaded
+ * entries when they are built, and tuning then skips what is already chosen. */
+demag_status demag_autotune_save(const demag_plan* plan, const char* path);
+demag_status demag_autotune_load(demag_plan* plan, const char* path, int* loaded);
 
 #ifdef __cplusplus
 }

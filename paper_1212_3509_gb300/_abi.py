@@ -95,7 +95,9 @@ _SIGS = {
     "demag_set_wait_limit": (_i, [_vp, ctypes.c_double]),
     "demag_autotune_count": (_i, [_vp]),
     "demag_autotune_entry": (_i, [_vp, _i, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i),
-                                  ctypes.POINTER(ctypes.c_float)]),
+                                  ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]),
+    "demag_autotune_save": (_i, [_vp, ctypes.c_char_p]),
+    "demag_autotune_load": (_i, [_vp, ctypes.c_char_p, ctypes.POINTER(_i)]),
     "demag_profile": (_i, [_vp, _i]),
     "demag_profile_read": (_i, [_vp, _i, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]),
     "demag_profile_count": (ctypes.c_longlong, [_vp]),
@@ -583,17 +585,28 @@ def demag_autotune_count(plan: Plan) -> int:
     return lib.demag_autotune_count(plan.ptr)
 
 
-TUNE_KINDS = {0: "fft_node_group", 1: "bf16x3_tile_width", 2: "tf32x3_tile_width"}
+TUNE_KINDS = {0: "fft_node_group", 1: "bf16x3_tile_width", 2: "tf32x3_tile_width", 3: "bf16x3_stages",
+              4: "tf32x3_stages", 5: "bf16x3_tile_order", 6: "tf32x3_tile_order"}
 
 
 def demag_autotune_entry(plan: Plan, i: int) -> dict:
     kind, value = _i(), _i()
     key = (_i * 3)()
-    ms = ctypes.c_float()
+    ms, ms_default = ctypes.c_float(), ctypes.c_float()
     _check(lib.demag_autotune_entry(plan.ptr, int(i), ctypes.byref(kind), key, ctypes.byref(value),
-                                    ctypes.byref(ms)), plan.ptr)
+                                    ctypes.byref(ms), ctypes.byref(ms_default)), plan.ptr)
     return {"kind": TUNE_KINDS.get(kind.value, kind.value), "key": list(key), "value": value.value,
-            "ms": ms.value}
+            "ms": ms.value, "ms_default": ms_default.value}
+
+
+def demag_autotune_save(plan: Plan, path: str):
+    _check(lib.demag_autotune_save(plan.ptr, os.fsencode(path)), plan.ptr)
+
+
+def demag_autotune_load(plan: Plan, path: str) -> int:
+    n = _i()
+    _check(lib.demag_autotune_load(plan.ptr, os.fsencode(path), ctypes.byref(n)), plan.ptr)
+    return n.value
 
 
 def demag_launch_count(plan: Plan) -> int:

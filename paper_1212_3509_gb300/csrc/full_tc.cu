@@ -170,7 +170,7 @@ struct TcSeg {
   int a_fofs, o_fofs;                  // added to every A field / output field
   int dep, dep_target;                 // wait for counters[dep] >= dep_target (dep < 0: none)
   int done;                            // completion counter (< 0: none)
-  int pad;
+  int order;                           // 0: row block outer, job, column tile; 1: job outer
 };
 
 struct TcLaunch {
@@ -204,8 +204,13 @@ __device__ __forceinline__ TileRef tile_coords(const TcLaunch& L, int tile) {
   r.g = S.group;
   r.nt = t % G.n_tiles;
   t /= G.n_tiles;
-  r.j = S.job0 + t % S.njobs;
-  r.mt = S.rb0 + t / S.njobs;
+  if (S.order) {  // every row block of one job in turn
+    r.mt = S.rb0 + t % S.nrb;
+    r.j = S.job0 + t / S.nrb;
+  } else {        // every job of one row block in turn (they share its A rows in L2)
+    r.j = S.job0 + t % S.njobs;
+    r.mt = S.rb0 + t / S.njobs;
+  }
   return r;
 }
 
@@ -1049,6 +1054,8 @@ struct TcState {
   TcJob* jobs;            // device, all programs
   short2* pairs;          // device, all programs
   TcSeg* seg;             // device [kPrograms]: one whole-program segment each
+  TcSeg host_seg[kPrograms];
+  int nst[kPrograms];     // operand stages of each program's launches (0: as many as fit)
   TcGroup host_prog[kPrograms];
   bool small[kPrograms];          // program runs on CUDA cores (axis of at most kSmallAxis cells)
   SmallStage small_prog[kPrograms];
@@ -1381,10 +1388,9 @@ static demag_status build_programs(demag_plan* P, TcState* S, const CUtensorMap 
   }
   DEMAG_CUDA(P, cudaMalloc(&S->prog, sizeof(TcGroup) * kPrograms));
   DEMAG_CUDA(P, cudaMemcpy(S->prog, H, sizeof(TcGroup) * kPrograms, cudaMemcpyHostToDevice));
-  TcSeg sg[kPrograms];
-  for (int p = 0; p < kPrograms; ++p) sg[p] = whole_seg(H[p], 0, 0);
-  DEMAG_CUDA(P, cudaMalloc(&S->seg, sizeof(sg)));
-  DEMAG_CUDA(P, cudaMemcpy(S->seg, sg, sizeof(sg), cudaMemcpyHostToDevice));
+  for (int p = 0; p < kPrograms; ++p) S->host_seg[p] = whole_seg(H[p], 0, 0);
+  DEMAG_CUDA(P, cudaMalloc(&S->seg, sizeof(S->host_seg)));
+  DEMAG_CUDA(P, cudaMemcpy(S->seg, S->host_seg, sizeof(S->host_seg), cudaMemcpyHostToDevice));
   (void)st;
   return DEMAG_OK;
 }
@@ -1431,51 +1437,117 @@ static demag_status set_tile_width(demag_plan* P, TcState* S, int prog, int bn) 
   return DEMAG_OK;
 }
 
-// Autotuning of the output-column tile width of every stage program: the
-// default (256, or the column count rounded up to 16) and 128 and 64 below it
-// are timed (one warm-up, three timed launches, operands as they are in the
-// workspace), and the fastest is kept.
+// Point stage program `prog` at tile order `order` (device copy included).
+static demag_status set_tile_order(demag_plan* P, TcState* S, int prog, int order) {
+  S->host_seg[prog].order = order;
+  DEMAG_CUDA(P, cudaMemcpy(S->seg + prog, &S->host_seg[prog], sizeof(TcSeg), cudaMemcpyHostToDevice));
+  return DEMAG_OK;
+}
+
+// Tuned entry kinds of the tensor-core programs, per form (BF16x3, TF32x3):
+// N tile width 1 / 2, operand stages 3 / 4, tile order 5 / 6; key = (stage
+// program, default value, 0).
+static int tune_kind(const TcState* S, int knob) { return 1 + 2 * knob + (S->elem == 2 ? 0 : 1); }
+
+static const demag_plan::Tuned* find_tuned(const demag_plan* P, int kind, int prog) {
+  for (const demag_plan::Tuned& t : P->tuned)
+    if (t.kind == kind && t.key[0] == prog) return &t;
+  return nullptr;
+}
+
+static demag_status set_knob(demag_plan* P, TcState* S, int prog, int knob, int v) {
+  if (knob == 0) return set_tile_width(P, S, prog, v);
+  if (knob == 1) {
+    S->nst[prog] = v;
+    return DEMAG_OK;
+  }
+  return set_tile_order(P, S, prog, v);
+}
+
+// Apply tuned entries already in the plan (a loaded cache) to its programs.
+static demag_status apply_tuned(demag_plan* P, TcState* S) {
+  for (int prog = 0; prog < kPrograms; ++prog) {
+    if (S->small[prog]) continue;
+    for (int knob = 0; knob < 3; ++knob) {
+      const demag_plan::Tuned* t = find_tuned(P, tune_kind(S, knob), prog);
+      if (!t) continue;
+      if (knob == 0 && !(t->value >= 16 && t->value <= kBN && t->value % 16 == 0)) continue;
+      demag_status s = set_knob(P, S, prog, knob, t->value);
+      if (s != DEMAG_OK) return s;
+    }
+  }
+  return DEMAG_OK;
+}
+
+// Autotuning of every stage program (one warm-up and three timed launches per
+// candidate, operands as they are in the workspace), one knob after the other,
+// each kept at its fastest value: the output-column tile width (the default:
+// 256, or the column count rounded up to 16; 128 and 64 below it), the number
+// of operand stages (as many as fit, 4, 3, 2) and the tile order (every job of
+// a row block in turn, or every row block of a job).  None of them changes the
+// arithmetic of an output element.
 template <class F>
-static demag_status tune_tile_widths(demag_plan* P, TcState* S, cudaStream_t st) {
+static demag_status tune_programs(demag_plan* P, TcState* S, cudaStream_t st) {
   cudaEvent_t e0, e1;
   DEMAG_CUDA(P, cudaEventCreate(&e0));
   DEMAG_CUDA(P, cudaEventCreate(&e1));
   demag_status s = DEMAG_OK;
+  auto time_prog = [&](int prog, float* ms) -> demag_status {
+    demag_status r = run_program<F>(P, S, prog, st);
+    if (r != DEMAG_OK) return r;
+    DEMAG_CUDA(P, cudaEventRecord(e0, st));
+    for (int i = 0; i < 3 && r == DEMAG_OK; ++i) r = run_program<F>(P, S, prog, st);
+    DEMAG_CUDA(P, cudaEventRecord(e1, st));
+    DEMAG_CUDA(P, cudaEventSynchronize(e1));
+    if (r != DEMAG_OK) return r;
+    cudaEventElapsedTime(ms, e0, e1);
+    *ms /= 3.f;
+    return DEMAG_OK;
+  };
   for (int prog = 0; prog < kPrograms && s == DEMAG_OK; ++prog) {
     if (S->small[prog]) continue;  // runs on CUDA cores
-    const int def = S->host_prog[prog].bn;
-    std::vector<int> cands{def};
-    for (int c = 128; c >= 64; c /= 2)
-      if (c < def) cands.push_back(c);
-    if (cands.size() == 1) continue;
-    float best = 1e30f;
-    int best_bn = def;
-    for (int c : cands) {
-      s = set_tile_width(P, S, prog, c);
-      if (s == DEMAG_OK) s = run_program<F>(P, S, prog, st);
-      if (s != DEMAG_OK) break;
-      DEMAG_CUDA(P, cudaEventRecord(e0, st));
-      for (int r = 0; r < 3 && s == DEMAG_OK; ++r) s = run_program<F>(P, S, prog, st);
-      DEMAG_CUDA(P, cudaEventRecord(e1, st));
-      DEMAG_CUDA(P, cudaEventSynchronize(e1));
-      if (s != DEMAG_OK) break;
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      if (ms < best) {
-        best = ms;
-        best_bn = c;
+    for (int knob = 0; knob < 3 && s == DEMAG_OK; ++knob) {
+      if (find_tuned(P, tune_kind(S, knob), prog)) continue;  // chosen before (a loaded cache)
+      std::vector<int> cands;
+      int def = 0;
+      if (knob == 0) {
+        def = S->host_prog[prog].bn;
+        cands.push_back(def);
+        for (int c = 128; c >= 64; c /= 2)
+          if (c < def) cands.push_back(c);
+      } else if (knob == 1) {
+        def = 0;  // as many as fit
+        cands = {0, 4, 3, 2};
+      } else {
+        def = 0;
+        cands = {0, 1};
       }
-    }
-    if (s == DEMAG_OK) s = set_tile_width(P, S, prog, best_bn);
-    if (s == DEMAG_OK) {
-      demag_plan::Tuned t;
-      t.kind = S->elem == 2 ? 1 : 2;
-      t.key[0] = prog;
-      t.key[1] = def;
-      t.key[2] = 0;
-      t.value = best_bn;
-      t.ms = best / 3.f;
-      P->tuned.push_back(t);
+      if (cands.size() == 1) continue;
+      float best = 1e30f, at_def = 0.f;
+      int best_v = def;
+      for (int c : cands) {
+        s = set_knob(P, S, prog, knob, c);
+        float ms = 0.f;
+        if (s == DEMAG_OK) s = time_prog(prog, &ms);
+        if (s != DEMAG_OK) break;
+        if (c == def) at_def = ms;
+        if (ms < best) {
+          best = ms;
+          best_v = c;
+        }
+      }
+      if (s == DEMAG_OK) s = set_knob(P, S, prog, knob, best_v);
+      if (s == DEMAG_OK) {
+        demag_plan::Tuned t;
+        t.kind = tune_kind(S, knob);
+        t.key[0] = prog;
+        t.key[1] = def;
+        t.key[2] = 0;
+        t.value = best_v;
+        t.ms = best;
+        t.ms_default = at_def;
+        P->tuned.push_back(t);
+      }
     }
   }
   cudaEventDestroy(e0);
@@ -1587,12 +1659,13 @@ demag_status tc_prepare(demag_plan* P, demag_precision prec, cudaStream_t st) {
   demag_status s = build_programs(P, S, mapX, map1, map2, mapB, out1, out2, out3, bk, st);
   if (s == DEMAG_OK)
     s = prec == DEMAG_TF32X3 ? prepare_form<Tf32Form>(P, S, st) : prepare_form<Bf16Form>(P, S, st);
+  if (s == DEMAG_OK) s = apply_tuned(P, S);
   if (s == DEMAG_OK && P->autotune) {
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     cudaStreamIsCapturing(st, &cap);
     if (cap == cudaStreamCaptureStatusNone) {
       Hd->s[form_index(prec)] = S;  // tc_sync_status reads the state through the holder
-      s = prec == DEMAG_TF32X3 ? tune_tile_widths<Tf32Form>(P, S, st) : tune_tile_widths<Bf16Form>(P, S, st);
+      s = prec == DEMAG_TF32X3 ? tune_programs<Tf32Form>(P, S, st) : tune_programs<Bf16Form>(P, S, st);
       Hd->s[form_index(prec)] = nullptr;
     }
   }
@@ -1606,7 +1679,8 @@ demag_status tc_prepare(demag_plan* P, demag_precision prec, cudaStream_t st) {
 
 template <class F>
 static demag_status launch_segs(demag_plan* P, const TcGroup* groups, const TcSeg* segs, int nsegs, int total_tiles,
-                               int maxbn, int* counter, int* counters, int ncounters, int* status, cudaStream_t st) {
+                               int maxbn, int* counter, int* counters, int ncounters, int* status, cudaStream_t st,
+                               int want_stages = 0) {
   if (total_tiles <= 0) return DEMAG_OK;
   TcLaunch L;
   L.groups = groups;
@@ -1617,6 +1691,7 @@ static demag_status launch_segs(demag_plan* P, const TcGroup* groups, const TcSe
   L.btile = maxbn * kRowBytes;
   L.stage_bytes = (2 * kTileA + 2 * L.btile + 1023) / 1024 * 1024;
   L.nstages = std::min(kMaxStages, (kSmemMax - kSmemFixed) / L.stage_bytes);
+  if (want_stages > 0) L.nstages = std::min(L.nstages, want_stages);
   const int smem_bytes = kSmemFixed + L.nstages * L.stage_bytes;
   L.tile_counter = counter;
   L.counters = counters;
@@ -1645,7 +1720,7 @@ template <class F>
 static demag_status run_program(demag_plan* P, TcState* S, int prog, cudaStream_t st) {
   if (S->small[prog]) return launch_small<F>(P, S->small_prog[prog], st);
   return launch_segs<F>(P, S->prog + prog, S->seg + prog, 1, S->host_prog[prog].ntiles, S->host_prog[prog].bn,
-                        S->counter, nullptr, 0, S->status, st);
+                        S->counter, nullptr, 0, S->status, st, S->nst[prog]);
 }
 
 template <class F>

@@ -88,10 +88,12 @@ struct demag_plan {
   // autotuning: when on, launch shapes not yet tuned are timed on first use
   bool autotune = false;
   struct Tuned {
-    int kind;      // 0 FFT nodes per block; 1 / 2 tensor-core N tile (BF16x3 / TF32x3)
-    int key[3];    // FFT: log2 N, column blocks, M; tensor core: stage program, default tile, 0
+    int kind;      // 0 FFT nodes per block; tensor cores (BF16x3 / TF32x3): 1 / 2 N tile,
+                   // 3 / 4 operand stages, 5 / 6 tile order
+    int key[3];    // FFT: log2 N, column blocks, M; tensor core: stage program, default value, 0
     int value;     // chosen setting
     float ms;      // its time per launch
+    float ms_default = 0.f;  // the default setting's time per launch (0: not timed, a loaded entry)
   };
   std::vector<Tuned> tuned;
 

@@ -559,7 +559,7 @@ extern "C" demag_status demag_autotune(demag_plan* plan, int enable) {
 extern "C" int demag_autotune_count(const demag_plan* plan) { return plan ? (int)plan->tuned.size() : 0; }
 
 extern "C" demag_status demag_autotune_entry(const demag_plan* plan, int i, int* kind, int key[3], int* value,
-                                             float* ms) {
+                                             float* ms, float* ms_default) {
   if (!plan || i < 0 || i >= (int)plan->tuned.size())
     return set_error(nullptr, DEMAG_EINVAL, "demag_autotune_entry: no entry %d", i);
   const demag_plan::Tuned& t = plan->tuned[i];
@@ -568,6 +568,77 @@ extern "C" demag_status demag_autotune_entry(const demag_plan* plan, int i, int*
     for (int j = 0; j < 3; ++j) key[j] = t.key[j];
   if (value) *value = t.value;
   if (ms) *ms = t.ms;
+  if (ms_default) *ms_default = t.ms_default;
+  return DEMAG_OK;
+}
+
+// "GPU-xxxxxxxx-xxxx-xxxx-xxxx-xxxxxxxxxxxx" of the current device (as nvidia-smi prints it).
+static bool current_gpu_uuid(char* out, size_t len) {
+  int dev = 0;
+  cudaDeviceProp prop;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return false;
+  const unsigned char* u = reinterpret_cast<const unsigned char*>(prop.uuid.bytes);
+  snprintf(out, len, "GPU-%02x%02x%02x%02x-%02x%02x-%02x%02x-%02x%02x-%02x%02x%02x%02x%02x%02x", u[0], u[1], u[2],
+           u[3], u[4], u[5], u[6], u[7], u[8], u[9], u[10], u[11], u[12], u[13], u[14], u[15]);
+  return true;
+}
+
+static const char* kTuneLine =
+    "{\"gpu\":\"%s\",\"n\":[%d,%d,%d],\"R\":%d,\"grid\":\"%s\",\"kind\":%d,\"key\":[%d,%d,%d],"
+    "\"value\":%d,\"ms\":%.6g,\"ms_default\":%.6g}\n";
+
+extern "C" demag_status demag_autotune_save(const demag_plan* plan, const char* path) {
+  if (!plan || !path) return set_error(nullptr, DEMAG_EINVAL, "demag_autotune_save: NULL argument");
+  char gpu[64];
+  if (!current_gpu_uuid(gpu, sizeof(gpu)))
+    return set_error(const_cast<demag_plan*>(plan), DEMAG_ECUDA, "demag_autotune_save: no device");
+  FILE* f = fopen(path, "a");
+  if (!f) return set_error(const_cast<demag_plan*>(plan), DEMAG_EINVAL, "demag_autotune_save: cannot open %s", path);
+  for (const demag_plan::Tuned& t : plan->tuned)
+    fprintf(f, kTuneLine, gpu, plan->n[0], plan->n[1], plan->n[2], plan->R,
+            plan->nonuniform ? "nonuniform" : "uniform", t.kind, t.key[0], t.key[1], t.key[2], t.value, t.ms,
+            t.ms_default);
+  fclose(f);
+  return DEMAG_OK;
+}
+
+extern "C" demag_status demag_autotune_load(demag_plan* plan, const char* path, int* loaded) {
+  if (loaded) *loaded = 0;
+  if (!plan || !path) return set_error(nullptr, DEMAG_EINVAL, "demag_autotune_load: NULL argument");
+  char gpu[64];
+  if (!current_gpu_uuid(gpu, sizeof(gpu))) return set_error(plan, DEMAG_ECUDA, "demag_autotune_load: no device");
+  FILE* f = fopen(path, "r");
+  if (!f) return DEMAG_OK;  // no cache yet
+  char line[512];
+  int count = 0;
+  while (fgets(line, sizeof(line), f)) {
+    char g[64], grid[16];
+    int n[3], R, kind, key[3], value;
+    float ms = 0.f, msd = 0.f;
+    const int got = sscanf(line,
+                           "{\"gpu\":\"%63[^\"]\",\"n\":[%d,%d,%d],\"R\":%d,\"grid\":\"%15[^\"]\",\"kind\":%d,"
+                           "\"key\":[%d,%d,%d],\"value\":%d,\"ms\":%f,\"ms_default\":%f}",
+                           g, &n[0], &n[1], &n[2], &R, grid, &kind, &key[0], &key[1], &key[2], &value, &ms, &msd);
+    if (got != 13 || strcmp(g, gpu) != 0 || n[0] != plan->n[0] || n[1] != plan->n[1] || n[2] != plan->n[2] ||
+        R != plan->R || strcmp(grid, plan->nonuniform ? "nonuniform" : "uniform") != 0)
+      continue;
+    demag_plan::Tuned t;
+    t.kind = kind;
+    for (int j = 0; j < 3; ++j) t.key[j] = key[j];
+    t.value = value;
+    t.ms = ms;
+    t.ms_default = msd;
+    bool replaced = false;  // a later line for the same shape wins
+    for (demag_plan::Tuned& e : plan->tuned)
+      if (e.kind == t.kind && e.key[0] == t.key[0] && e.key[1] == t.key[1] && e.key[2] == t.key[2]) {
+        e = t;
+        replaced = true;
+      }
+    if (!replaced) plan->tuned.push_back(t);
+    ++count;
+  }
+  fclose(f);
+  if (loaded) *loaded = count;
   return DEMAG_OK;
 }
 

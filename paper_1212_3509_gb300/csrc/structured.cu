@@ -458,7 +458,7 @@ static cudaError_t pick_kgroup(demag_plan* P, int logn, ToepLaunch& a, int gx, c
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  float best = 1e30f;
+  float best = 1e30f, at_def = 0.f;
   int best_kg = kg;
   cudaError_t err = cudaSuccess;
   for (int c : cands) {
@@ -471,6 +471,7 @@ static cudaError_t pick_kgroup(demag_plan* P, int logn, ToepLaunch& a, int gx, c
     if (err != cudaSuccess) break;
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
+    if (c == kg) at_def = ms;
     if (ms < best) {
       best = ms;
       best_kg = c;
@@ -487,6 +488,7 @@ static cudaError_t pick_kgroup(demag_plan* P, int logn, ToepLaunch& a, int gx, c
   t.key[2] = M;
   t.value = best_kg;
   t.ms = best / 3.f;
+  t.ms_default = at_def / 3.f;
   P->tuned.push_back(t);
   return cudaSuccess;
 }

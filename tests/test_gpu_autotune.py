@@ -1,9 +1,9 @@
 """Autotuned launch shapes and grouped FFT launches.
 
-Tuning changes only how work is split over blocks (nodes per FFT block,
-output-column tile width of the tensor-core GEMMs); every output element is
-computed by the same sequence of operations, so tuned and untuned plans agree
-bit for bit."""
+Tuning changes only how work is split over blocks and scheduled (nodes per FFT
+block; output-column tile width, operand stages and tile order of the
+tensor-core GEMMs); every output element is computed by the same sequence of
+operations, so tuned and untuned plans agree bit for bit."""
 import numpy as np
 import pytest
 
@@ -108,7 +108,47 @@ def test_tile_width_tuning_keeps_results(D, prec):
     entries = [D.demag_autotune_entry(P, i) for i in range(D.demag_autotune_count(P))]
     kind = f"{prec}_tile_width"
     tuned = {e["key"][0]: e for e in entries if e["kind"] == kind}
-    # axis 1 (n = 300, default width 256) and axis 3 (n = 160, default 160): forward and adjoint
+    # folded axis 1 (n = 300, 150 per half, default width 160) and axis 3 (n = 160,
+    # 80 per half, default 80) have narrower candidates: forward and adjoint programs
     assert set(tuned) == {0, 2, 3, 5}
     for e in tuned.values():
         assert e["value"] in (e["key"][1], 128, 64)
+    # every tensor-core program also gets its stage count and tile order
+    stages = {e["key"][0]: e for e in entries if e["kind"] == f"{prec}_stages"}
+    order = {e["key"][0]: e for e in entries if e["kind"] == f"{prec}_tile_order"}
+    assert set(stages) == set(order) == set(range(6))
+    for e in list(stages.values()) + list(order.values()) + list(tuned.values()):
+        assert 0 < e["ms"] <= e["ms_default"]  # the default was a candidate
+    assert all(e["value"] in (0, 4, 3, 2) for e in stages.values())
+    assert all(e["value"] in (0, 1) for e in order.values())
+
+
+def test_tuning_cache_round_trip(D, tmp_path):
+    """Entries saved by a tuned plan are loaded by a new plan of the same grid on the
+    same GPU, which then tunes nothing and gives the same results bit for bit; a plan
+    of another grid loads none of them."""
+    n, h, R = (96, 80, 64), (1 / 96,) * 3, 21
+    m = dev(synth.random_unit_m(n, 31))
+    path = str(tmp_path / "tune.jsonl")
+    P1 = D.demag_build_factors(n, h, R)
+    D.demag_autotune(P1, True)
+    a = torch.empty(n[2], n[1], n[0], device="cuda")
+    D.demag_apply_full(P1, m, a, "bf16x3")
+    count1 = D.demag_autotune_count(P1)
+    assert count1 > 0
+    D.demag_autotune_save(P1, path)
+    P2 = D.demag_build_factors(n, h, R)
+    assert D.demag_autotune_load(P2, path) == count1
+    D.demag_autotune(P2, True)
+    b = torch.empty_like(a)
+    D.demag_apply_full(P2, m, b, "bf16x3")
+    torch.cuda.synchronize()
+    assert D.demag_autotune_count(P2) == count1  # nothing tuned again
+    e1 = sorted((e["kind"], tuple(e["key"]), e["value"]) for e in
+                (D.demag_autotune_entry(P1, i) for i in range(count1)))
+    e2 = sorted((e["kind"], tuple(e["key"]), e["value"]) for e in
+                (D.demag_autotune_entry(P2, i) for i in range(count1)))
+    assert e1 == e2
+    assert torch.equal(a, b)
+    P3 = D.demag_build_factors((96, 80, 65), h, R)
+    assert D.demag_autotune_load(P3, path) == 0
