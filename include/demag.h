@@ -530,8 +530,10 @@ demag_status demag_profile_launch(demag_plan* plan, long long i, int* family, do
  *    use) times, per mode-product stage program, one knob after the other
  *    and keeps each at its fastest value: the output-column tile width
  *    {default, 128, 64} below the default, the operand stages {as many as
- *    fit, 4, 3, 2} and the tile order {every job of a row block in turn, every
- *    row block of a job in turn} (operands as they are, stage timed alone).
+ *    fit, 4, 3, 2}, the tile order {every job of a row block in turn, every
+ *    row block of a job in turn} and, where a 128-row block of the stage lies
+ *    in one outer index, the store boxes {per epilogue warp, one 128-row box
+ *    per chunk} (operands as they are, stage timed alone).
  * No knob changes the arithmetic of an output element: tuned and untuned
  * results agree bit for bit.  The tuning launches write the call's own
  * outputs.  No tuning happens while the stream is being captured.
@@ -539,7 +541,8 @@ demag_status demag_profile_launch(demag_plan* plan, long long i, int* family, do
 demag_status demag_autotune(demag_plan* plan, int enable);
 /* Number of tuned shapes, and entry i of them: kind (0 FFT node group; tensor
  * cores, BF16x3 / TF32x3: 1 / 2 tile width, 3 / 4 operand stages (0 = as many
- * as fit), 5 / 6 tile order), key (FFT: log2 of the complex FFT length, column
+ * as fit), 5 / 6 tile order, 7 / 8 store boxes (1 = 128-row boxes)), key (FFT:
+ * log2 of the complex FFT length, column
  * blocks, M; tensor core: stage program 0..5, default value, 0), the chosen
  * value, its time per launch and the default value's time per launch in ms
  * (0 for an entry read from a cache). */

@@ -142,6 +142,7 @@ struct alignas(128) TcGroup {
   CUtensorMap a_hi, a_lo;              // 3D maps: (K, rows, field)
   CUtensorMap b_hi, b_lo;              // 4D maps: (K, a, half, matrix)
   CUtensorMap o_hi, o_lo;              // 5D output maps (inner, outer, a, half, field) when tma_out
+  CUtensorMap w_hi, w_lo;              // the same with 128-row boxes (o_wide)
   const TcJob* jobs;
   const short2* pairs;                 // (A field, B matrix 2k + type)
   void* out_hi;                        // split: hi plane base; f32: float base
@@ -150,6 +151,8 @@ struct alignas(128) TcGroup {
   long long s_a;                       // output stride of the column index a
   int ldC, n_inner;                    // output row stride and row split (outer, inner)
   int rows, n_a, kblocks, bn, mode, tma_out;
+  int o_wide;                          // one 128-row box per chunk from all epilogue warps (w_hi, w_lo);
+                                       // a launch's groups are either all wide or none (shared staging)
   int hq;                              // folded axis: start of the odd half (K and output columns), else 0
   int pxor;                            // 1 when type 0 factors are the odd ones (derivative factors)
   float alpha;
@@ -255,8 +258,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const __grid_con
   uint64_t* drain = tempty + 2;        // [1]
   uint64_t* sfull = drain + 1;         // [kRing] a tile id is in the ring slot
   uint64_t* sempty = sfull + kRing;    // [kRing] the MMA thread and the 4 epilogue warps read it
-  volatile int* ring = reinterpret_cast<volatile int*>(sempty + kRing);  // [kRing]
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sempty + kRing) + kRing;
+  uint64_t* oready = sempty + kRing;   // [2] wide stores: every epilogue warp staged its rows
+  uint64_t* ofree = oready + 2;        // [2] wide stores: the store that read the buffer has read it
+  volatile int* ring = reinterpret_cast<volatile int*>(ofree + 2);  // [kRing]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(const_cast<int*>(ring) + kRing);
   volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -274,6 +279,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const __grid_con
       ptx::mbar_init(&sempty[i], 1 + kEpiWarps);
     }
     ptx::mbar_init(drain, 1);
+    for (int b = 0; b < 2; ++b) {
+      ptx::mbar_init(&oready[b], kEpiWarps);
+      ptx::mbar_init(&ofree[b], 1);
+    }
     *abort = 0;
     ptx::fence_mbar_init();
   }
@@ -463,7 +472,67 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const __grid_con
       const int n_inner = G.n_inner;
       const int mode = G.mode;
       const float alpha = G.alpha;
-      if (G.tma_out) {
+      if (G.tma_out && G.o_wide) {
+        // The tile's 128 rows lie in one `outer` (n_inner % 128 == 0): the four
+        // warps stage each 32-column chunk together as [column][128 rows] and
+        // one thread stores it as one box per plane (rows of 128 elements, a
+        // quarter of the store requests of per-warp boxes).  Two staging
+        // buffers in turn: `oready` (every warp staged its rows) and `ofree`
+        // (the store that last read the buffer has read it), both bounded.
+        const int r0 = mt * kBM;
+        const int outer0 = r0 / n_inner, inner0 = r0 - outer0 * n_inner;
+        const bool issuer = warp == 2 && lane == 0;
+        bool ok = true;
+        for (int c0 = 0; c0 < bn && ok; c0 += 32) {
+          uint32_t r[32];
+          ptx::tmem_ld32(taddr + (uint32_t)c0, r);
+          ptx::tmem_ld_wait();
+          const uint32_t b = chunk & 1u, par = (chunk >> 1) & 1u;
+          ++chunk;
+          uint8_t* sb = ostage + b * (4 * kOutBuf);
+          if (!ptx::mbar_wait(&ofree[b], par ^ 1u, abort, L.wait_ns)) {
+            tc_fail(abort, L.status);
+            ok = false;
+            break;
+          }
+          const int rr = quad * 32 + lane;
+          if (mode == kOutSplit) {
+            T* sh = reinterpret_cast<T*>(sb);
+            T* sl = sh + 32 * kBM;
+#pragma unroll
+            for (int jj = 0; jj < 32; ++jj) {
+              T hi, lo;
+              F::split(__uint_as_float(r[jj]), hi, lo);
+              sh[jj * kBM + rr] = hi;
+              sl[jj * kBM + rr] = lo;
+            }
+          } else {
+            float* sf = reinterpret_cast<float*>(sb);
+#pragma unroll
+            for (int jj = 0; jj < 32; ++jj) sf[jj * kBM + rr] = alpha * __uint_as_float(r[jj]);
+          }
+          ptx::fence_proxy_async_smem();
+          __syncwarp();
+          if (lane == 0) ptx::mbar_arrive(&oready[b]);
+          if (issuer) {
+            if (!ptx::mbar_wait(&oready[b], par, abort, L.wait_ns)) {
+              tc_fail(abort, L.status);
+              ok = false;
+            } else {
+              ptx::tma_store_5d(&G.w_hi, sb, inner0, outer0, a0 + c0, half, out_field);
+              if (mode == kOutSplit)
+                ptx::tma_store_5d(&G.w_lo, sb + 32 * kBM * sizeof(T), inner0, outer0, a0 + c0, half, out_field);
+              ptx::bulk_commit();
+              ++commits;
+              // the previous chunk's store has read the other buffer: free it
+              ptx::bulk_wait_read<1>();
+              if (chunk >= 2) ptx::mbar_arrive(&ofree[b ^ 1u]);
+            }
+          }
+          __syncwarp();
+        }
+        if (!ok) break;
+      } else if (G.tma_out) {
         // A warp's 32 rows lie in one `outer` (n_inner % 32 == 0), so each
         // 32-column chunk is one TMA box per plane: stage it in shared memory
         // as [column][row] and store it with the async copy engine.
@@ -556,13 +625,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const __grid_con
         epi_signal(L.counters, pend, pend_n, pend_tma, G.tma_out ? commits : 0, lane);
         pend = -1;
       }
-      if (SG.done >= 0) {  // later tiles of the launch read what this tile wrote
+      // later tiles of the launch read what this tile wrote; a wide tile's stores
+      // are all issued by warp 2, which counts them for every epilogue warp
+      const int wgt = G.o_wide ? (warp == 2 ? kEpiWarps : 0) : 1;
+      if (SG.done >= 0 && wgt) {
         if (pend < 0) {
           pend = SG.done;
           pend_n = 0;
           pend_tma = false;
         }
-        ++pend_n;
+        pend_n += wgt;
         pend_tma = pend_tma || G.tma_out != 0;
       }
     }
@@ -1111,17 +1183,17 @@ static bool make_bmap(CUtensorMap* m, void* base, int elem_bytes, uint64_t h, ui
 // 5D map over an output field set: (inner, outer, a, half, field) with the
 // given strides in elements, the column index a limited to the na valid
 // columns of a half (the odd half starts hq columns after the even one);
-// box (32, 1, 32, 1, 1) = one epilogue warp's 32 rows x 32 output columns,
-// no swizzle.
+// box (box_inner, 1, 32, 1, 1) = one epilogue warp's 32 rows (or the four
+// warps' 128 rows) x 32 output columns, no swizzle.
 static bool make_out_map(CUtensorMap* m, void* base, int elem_bytes, uint64_t inner, uint64_t outer, uint64_t na,
                          uint64_t halves, uint64_t hq, uint64_t fields, uint64_t ld, uint64_t s_a,
-                         uint64_t field_elems) {
+                         uint64_t field_elems, uint32_t box_inner = 32) {
   EncodeTiledFn enc = encode_fn();
   if (!enc) return false;
   cuuint64_t dims[5] = {inner, outer, na, halves, fields};
   const uint64_t s_half = (halves > 1 ? hq : na) * s_a;
   cuuint64_t strides[4] = {ld * elem_bytes, s_a * elem_bytes, s_half * elem_bytes, field_elems * elem_bytes};
-  cuuint32_t box[5] = {32, 1, 32, 1, 1};
+  cuuint32_t box[5] = {box_inner, 1, 32, 1, 1};
   cuuint32_t estr[5] = {1, 1, 1, 1, 1};
   const CUtensorMapDataType dt = elem_bytes == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
   CUresult r = enc(m, dt, 5, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -1153,6 +1225,7 @@ struct TcState {
   int part_fields;        // partial fields allocated
   int groups_fwd, groups_adj;  // partial fields used by the forward / adjoint node sum
   int tma[3];             // stage epilogue stores through TMA
+  int wide[3];            // ... one 128-row box per chunk (n_inner % 128 == 0)
   // stage programs: the group descriptors (device) and their job / pair tables
   TcGroup* prog;          // device [kPrograms]
   TcJob* jobs;            // device, all programs
@@ -1342,8 +1415,9 @@ static void set_stage(TcGroup& G, const CUtensorMap& ahi, const CUtensorMap& alo
 static demag_status build_programs(demag_plan* P, TcState* S, const CUtensorMap (&mapX)[2],
                                    const CUtensorMap (&map1)[2], const CUtensorMap (&map2)[2],
                                    const CUtensorMap (&mapB)[3][2], const CUtensorMap (&out1)[2],
-                                   const CUtensorMap (&out2)[2], const CUtensorMap& out3, int bk,
-                                   cudaStream_t st) {
+                                   const CUtensorMap (&out2)[2], const CUtensorMap& out3,
+                                   const CUtensorMap (&wout1)[2], const CUtensorMap (&wout2)[2],
+                                   const CUtensorMap& wout3, int bk, cudaStream_t st) {
   const AxisGeo& g = S->geo;
   const int M = P->M;
   const int x1 = g.ext[0], x2 = g.ext[1], x3 = g.ext[2];
@@ -1436,9 +1510,10 @@ static demag_status build_programs(demag_plan* P, TcState* S, const CUtensorMap 
     const int stage = p % 3;
     if (S->tma[stage]) {
       H[p].tma_out = 1;
-      if (stage == 0) { H[p].o_hi = out1[0]; H[p].o_lo = out1[1]; }
-      if (stage == 1) { H[p].o_hi = out2[0]; H[p].o_lo = out2[1]; }
-      if (stage == 2) H[p].o_hi = out3;
+      H[p].o_wide = 0;  // per-warp boxes by default; the tuner may pick wide ones where S->wide
+      if (stage == 0) { H[p].o_hi = out1[0]; H[p].o_lo = out1[1]; H[p].w_hi = wout1[0]; H[p].w_lo = wout1[1]; }
+      if (stage == 1) { H[p].o_hi = out2[0]; H[p].o_lo = out2[1]; H[p].w_hi = wout2[0]; H[p].w_lo = wout2[1]; }
+      if (stage == 2) { H[p].o_hi = out3; H[p].w_hi = wout3; }
     }
   }
   // job and pair tables
@@ -1549,8 +1624,9 @@ static demag_status set_tile_order(demag_plan* P, TcState* S, int prog, int orde
 }
 
 // Tuned entry kinds of the tensor-core programs, per form (BF16x3, TF32x3):
-// N tile width 1 / 2, operand stages 3 / 4, tile order 5 / 6; key = (stage
-// program, default value, 0).
+// N tile width 1 / 2, operand stages 3 / 4, tile order 5 / 6, store boxes
+// 7 / 8 (per warp or one 128-row box per chunk); key = (stage program,
+// default value, 0).
 static int tune_kind(const TcState* S, int knob) { return 1 + 2 * knob + (S->elem == 2 ? 0 : 1); }
 
 static const demag_plan::Tuned* find_tuned(const demag_plan* P, int kind, int prog) {
@@ -1565,14 +1641,19 @@ static demag_status set_knob(demag_plan* P, TcState* S, int prog, int knob, int 
     S->nst[prog] = v;
     return DEMAG_OK;
   }
-  return set_tile_order(P, S, prog, v);
+  if (knob == 2) return set_tile_order(P, S, prog, v);
+  // store boxes: wide ones only where the stage has them
+  TcGroup& G = S->host_prog[prog];
+  G.o_wide = (v && S->wide[prog % 3]) ? 1 : 0;
+  DEMAG_CUDA(P, cudaMemcpy(S->prog + prog, &G, sizeof(TcGroup), cudaMemcpyHostToDevice));
+  return DEMAG_OK;
 }
 
 // Apply tuned entries already in the plan (a loaded cache) to its programs.
 static demag_status apply_tuned(demag_plan* P, TcState* S) {
   for (int prog = 0; prog < kPrograms; ++prog) {
     if (S->small[prog]) continue;
-    for (int knob = 0; knob < 3; ++knob) {
+    for (int knob = 0; knob < 4; ++knob) {
       const demag_plan::Tuned* t = find_tuned(P, tune_kind(S, knob), prog);
       if (!t) continue;
       if (knob == 0 && !(t->value >= 16 && t->value <= kBN && t->value % 16 == 0)) continue;
@@ -1587,9 +1668,11 @@ static demag_status apply_tuned(demag_plan* P, TcState* S) {
 // candidate, operands as they are in the workspace), one knob after the other,
 // each kept at its fastest value: the output-column tile width (the default:
 // 256, or the column count rounded up to 16; 128 and 64 below it), the number
-// of operand stages (as many as fit, 4, 3, 2) and the tile order (every job of
-// a row block in turn, or every row block of a job).  None of them changes the
-// arithmetic of an output element.
+// of operand stages (as many as fit, 4, 3, 2), the tile order (every job of a
+// row block in turn, or every row block of a job) and, where a 128-row block
+// lies in one outer index, the store boxes (per warp, or one 128-row box per
+// chunk from all four epilogue warps).  None of them changes the arithmetic of
+// an output element.
 template <class F>
 static demag_status tune_programs(demag_plan* P, TcState* S, cudaStream_t st) {
   cudaEvent_t e0, e1;
@@ -1610,7 +1693,7 @@ static demag_status tune_programs(demag_plan* P, TcState* S, cudaStream_t st) {
   };
   for (int prog = 0; prog < kPrograms && s == DEMAG_OK; ++prog) {
     if (S->small[prog]) continue;  // runs on CUDA cores
-    for (int knob = 0; knob < 3 && s == DEMAG_OK; ++knob) {
+    for (int knob = 0; knob < 4 && s == DEMAG_OK; ++knob) {
       if (find_tuned(P, tune_kind(S, knob), prog)) continue;  // chosen before (a loaded cache)
       std::vector<int> cands;
       int def = 0;
@@ -1622,9 +1705,13 @@ static demag_status tune_programs(demag_plan* P, TcState* S, cudaStream_t st) {
       } else if (knob == 1) {
         def = 0;  // as many as fit
         cands = {0, 4, 3, 2};
-      } else {
+      } else if (knob == 2) {
         def = 0;
         cands = {0, 1};
+      } else {
+        def = 0;
+        cands = {0};
+        if (S->wide[prog % 3]) cands.push_back(1);
       }
       if (cands.size() == 1) continue;
       float best = 1e30f, at_def = 0.f;
@@ -1721,7 +1808,10 @@ demag_status tc_prepare(demag_plan* P, demag_precision prec, cudaStream_t st) {
     free_state(S);
     return set_error(P, DEMAG_ENOMEM, "tensor-core workspace allocation failed");
   }
-  CUtensorMap mapB[3][2], mapX[2], map1[2], map2[2], out1[2], out2[2], out3;
+  CUtensorMap mapB[3][2], mapX[2], map1[2], map2[2], out1[2], out2[2], out3, wout1[2], wout2[2], wout3;
+  memset(wout1, 0, sizeof(wout1));
+  memset(wout2, 0, sizeof(wout2));
+  memset(&wout3, 0, sizeof(wout3));
   memset(mapB, 0, sizeof(mapB));
   memset(mapX, 0, sizeof(mapX));
   memset(map1, 0, sizeof(map1));
@@ -1744,23 +1834,31 @@ demag_status tc_prepare(demag_plan* P, demag_precision prec, cudaStream_t st) {
   S->tma[0] = (x2 % 32 == 0) && S->elem == 2;
   S->tma[1] = (x3 % 32 == 0) && S->elem == 2;
   S->tma[2] = (x1 % 32 == 0);
-  for (int h = 0; h < 2; ++h) {
-    if (S->tma[0])
-      ok = ok && make_out_map(&out1[h], S->buf1[h], S->elem, x2, x3, geo.h[0], S->halves[0], geo.hq[0], 3 * M,
-                              S->ld[1], (uint64_t)x3 * S->ld[1], (uint64_t)(x1 * x3) * S->ld[1]);
-    if (S->tma[1])
-      ok = ok && make_out_map(&out2[h], S->buf2[h], S->elem, x3, x1, geo.h[1], S->halves[1], geo.hq[1], 3 * M,
-                              S->ld[2], (uint64_t)x1 * S->ld[2], (uint64_t)(x2 * x1) * S->ld[2]);
+  // a whole 128-row block in one outer index: the four epilogue warps store it together
+  const long long inner_of[3] = {x2, x3, x1};
+  for (int st3 = 0; st3 < 3; ++st3) S->wide[st3] = S->tma[st3] && kEpiWarps == 4 && inner_of[st3] % kBM == 0;
+  for (int w = 0; w < 2; ++w) {  // per-warp boxes, then the wide ones where a stage has them
+    CUtensorMap* o1 = w ? wout1 : out1;
+    CUtensorMap* o2 = w ? wout2 : out2;
+    const uint32_t bi = w ? kBM : 32;
+    for (int h = 0; h < 2; ++h) {
+      if (S->tma[0] && (!w || S->wide[0]))
+        ok = ok && make_out_map(&o1[h], S->buf1[h], S->elem, x2, x3, geo.h[0], S->halves[0], geo.hq[0], 3 * M,
+                                S->ld[1], (uint64_t)x3 * S->ld[1], (uint64_t)(x1 * x3) * S->ld[1], bi);
+      if (S->tma[1] && (!w || S->wide[1]))
+        ok = ok && make_out_map(&o2[h], S->buf2[h], S->elem, x3, x1, geo.h[1], S->halves[1], geo.hq[1], 3 * M,
+                                S->ld[2], (uint64_t)x1 * S->ld[2], (uint64_t)(x2 * x1) * S->ld[2], bi);
+    }
+    if (S->tma[2] && (!w || S->wide[2]))
+      ok = ok && make_out_map(w ? &wout3 : &out3, S->part, 4, x1, x2, geo.h[2], S->halves[2], geo.hq[2],
+                              S->part_fields, x1, (uint64_t)(x2 * x1), (uint64_t)(x1 * x2 * x3), bi);
   }
-  if (S->tma[2])
-    ok = ok && make_out_map(&out3, S->part, 4, x1, x2, geo.h[2], S->halves[2], geo.hq[2], S->part_fields, x1,
-                            (uint64_t)(x2 * x1), (uint64_t)(x1 * x2 * x3));
   if (!ok) {
     free_state(S);
     return set_error(P, DEMAG_ECUDA, "tensor map encoding failed");
   }
   const int bk = kRowBytes / S->elem;
-  demag_status s = build_programs(P, S, mapX, map1, map2, mapB, out1, out2, out3, bk, st);
+  demag_status s = build_programs(P, S, mapX, map1, map2, mapB, out1, out2, out3, wout1, wout2, wout3, bk, st);
   if (s == DEMAG_OK)
     s = prec == DEMAG_TF32X3 ? prepare_form<Tf32Form>(P, S, st) : prepare_form<Bf16Form>(P, S, st);
   if (s == DEMAG_OK) s = apply_tuned(P, S);
@@ -2014,6 +2112,7 @@ demag_status tc_batch_create(demag_plan* const* plans, int count, demag_precisio
       const TcState* S = state(plans[order[i]], prec);
       const int gi = st3 * count + i;
       g[gi] = S->host_prog[kFwd1 + st3];
+      g[gi].o_wide = 0;  // the groups of one launch share the staging: per-warp boxes for all
       if (g[gi].ntiles <= 0) continue;
       TcSeg q = whole_seg(g[gi], gi, acc);
       if (st3 > 0) {

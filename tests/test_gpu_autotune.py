@@ -152,3 +152,28 @@ def test_tuning_cache_round_trip(D, tmp_path):
     assert torch.equal(a, b)
     P3 = D.demag_build_factors((96, 80, 65), h, R)
     assert D.demag_autotune_load(P3, path) == 0
+
+
+def test_store_box_tuning_keeps_results(D):
+    """At 128^3 every stage's 128-row blocks lie in one outer index, so the tuner also
+    times one 128-row store box per chunk against per-warp boxes; whichever it keeps,
+    the results equal the untuned plan's bit for bit (forward and adjoint)."""
+    n, h, R = (128, 128, 128), (1 / 128,) * 3, 11
+    m = dev(synth.random_unit_m(n, 12))
+    out = []
+    for tune in (False, True):
+        P = D.demag_build_factors(n, h, R)
+        if tune:
+            D.demag_autotune(P, True)
+        phi = torch.empty(n[2], n[1], n[0], device="cuda")
+        D.demag_apply_full(P, m, phi, "bf16x3")
+        y = torch.empty(3, n[2], n[1], n[0], device="cuda")
+        D.demag_apply_adjoint(P, phi, y, "bf16x3")
+        torch.cuda.synchronize()
+        D.demag_sync_status(P)
+        out.append((phi, y, P))
+    assert torch.equal(out[0][0], out[1][0]) and torch.equal(out[0][1], out[1][1])
+    P = out[1][2]
+    entries = [D.demag_autotune_entry(P, i) for i in range(D.demag_autotune_count(P))]
+    boxes = {e["key"][0]: e for e in entries if e["kind"] == "bf16x3_store_boxes"}
+    assert set(boxes) == set(range(6)) and all(e["value"] in (0, 1) for e in boxes.values())
