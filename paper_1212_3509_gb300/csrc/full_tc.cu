@@ -486,7 +486,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const __grid_con
         for (int c0 = 0; c0 < bn && ok; c0 += 32) {
           uint32_t r[32];
           ptx::tmem_ld32(taddr + (uint32_t)c0, r);
-          ptx::tmem_ld_wait();
+          ptx::tmem_ld_wait(r);
           const uint32_t b = chunk & 1u, par = (chunk >> 1) & 1u;
           ++chunk;
           uint8_t* sb = ostage + b * (4 * kOutBuf);
@@ -543,7 +543,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const __grid_con
         for (int c0 = 32 * slice; c0 < bn; c0 += 32 * kEpiSlices) {
           uint32_t r[32];
           ptx::tmem_ld32(taddr + (uint32_t)c0, r);
-          ptx::tmem_ld_wait();
+          ptx::tmem_ld_wait(r);
           if (!warp_valid) continue;
           // a warp's buffers are used in turn over its whole chunk sequence
           // (across tiles); before reuse, the store that last read a buffer
@@ -590,7 +590,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const __grid_con
         for (int c0 = 32 * slice; c0 < bn; c0 += 32 * kEpiSlices) {
           uint32_t r[32];
           ptx::tmem_ld32(taddr + (uint32_t)c0, r);
-          ptx::tmem_ld_wait();
+          ptx::tmem_ld_wait(r);
           if (!valid) continue;
           if (mode == kOutSplit) {
             T* hp = reinterpret_cast<T*>(G.out_hi) + rbase + (long long)(a0 + c0) * s_a;
