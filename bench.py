@@ -40,8 +40,8 @@ PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustain
 NCU_TRAFFIC = {
     # the three tcgen05 mode-product stages of one application, BF16x3, R = 41,
     # per cell of the grid (captured at 192^3, folded axes)
-    "tc_gemm_kernel": {"sources": ("full_tc.cu", "tc_ptx.cuh"), "sha": "54a818d77982f21b",
-                       "bytes_per_cell": 5.7324e9 / 192 ** 3},
+    "tc_gemm_kernel": {"sources": ("full_tc.cu", "tc_ptx.cuh"), "sha": "a6dadd13b4003ca1",
+                       "bytes_per_cell": 5.7328e9 / 192 ** 3},
     # the Toeplitz FFT launch of a CP batch, n = 4096, r = 4, R = 61, per application
     "toeplitz_fft_kernel": {"sources": ("structured.cu", "fft.cuh"), "sha": "4fdeeea3a089464e",
                             "bytes_per_app": 549.835e6 / 32},

@@ -93,6 +93,7 @@ _SIGS = {
     "demag_launch_count": (ctypes.c_ulonglong, [_vp]),
     "demag_autotune": (_i, [_vp, _i]),
     "demag_set_wait_limit": (_i, [_vp, ctypes.c_double]),
+    "demag_set_fused": (_i, [_vp, ctypes.c_int]),
     "demag_autotune_count": (_i, [_vp]),
     "demag_autotune_entry": (_i, [_vp, _i, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i),
                                   ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]),
@@ -575,6 +576,10 @@ def demag_sync_status(plan: Plan, stream=None):
 
 def demag_set_wait_limit(plan: Plan, seconds: float):
     _check(lib.demag_set_wait_limit(plan.ptr, float(seconds)), plan.ptr)
+
+
+def demag_set_fused(plan: Plan, enable: bool):
+    _check(lib.demag_set_fused(plan.ptr, 1 if enable else 0), plan.ptr)
 
 
 def demag_autotune(plan: Plan, enable: bool = True):

@@ -155,6 +155,7 @@ struct alignas(128) TcGroup {
                                        // a launch's groups are either all wide or none (shared staging)
   int hq;                              // folded axis: start of the odd half (K and output columns), else 0
   int pxor;                            // 1 when type 0 factors are the odd ones (derivative factors)
+  int a_mn;                            // A read MN-major (BF16): maps (rows, K, field) with 64-row boxes
   float alpha;
   int njobs, m_tiles, n_tiles, ntiles;
 };
@@ -348,8 +349,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const __grid_con
             armed |= 1u << s;
             armed_par = (armed_par & ~(1u << s)) | (ph << s);
             ptx::mbar_arrive_expect_tx(&full[s], bytes);
-            ptx::tma_load_3d(st, &G.a_hi, &full[s], koff + kb * F::kBK, mt * kBM, pr.x);
-            ptx::tma_load_3d(st + kTileA, &G.a_lo, &full[s], koff + kb * F::kBK, mt * kBM, pr.x);
+            if (F::kElem == 2 && G.a_mn) {
+              // rows contiguous, K the outer coordinate: two 64-row boxes per plane
+              const int kc = koff + kb * F::kBK;
+              ptx::tma_load_3d(st, &G.a_hi, &full[s], mt * kBM, kc, pr.x);
+              ptx::tma_load_3d(st + kTileA / 2, &G.a_hi, &full[s], mt * kBM + 64, kc, pr.x);
+              ptx::tma_load_3d(st + kTileA, &G.a_lo, &full[s], mt * kBM, kc, pr.x);
+              ptx::tma_load_3d(st + kTileA + kTileA / 2, &G.a_lo, &full[s], mt * kBM + 64, kc, pr.x);
+            } else {
+              ptx::tma_load_3d(st, &G.a_hi, &full[s], koff + kb * F::kBK, mt * kBM, pr.x);
+              ptx::tma_load_3d(st + kTileA, &G.a_lo, &full[s], koff + kb * F::kBK, mt * kBM, pr.x);
+            }
             ptx::tma_load_4d(st + 2 * kTileA, &G.b_hi, &full[s], kb * F::kBK, nt * G.bn, J.half, pr.y);
             ptx::tma_load_4d(st + 2 * kTileA + btile, &G.b_lo, &full[s], kb * F::kBK, nt * G.bn, J.half, pr.y);
             if (++s == nst) { s = 0; ph ^= 1; }
@@ -376,7 +386,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const __grid_con
         const TileRef tr = tile_coords(L, tile);
         const TcGroup& G = L.groups[tr.g];
         const TcJob J = G.jobs[tr.j];
-        const uint32_t idesc = ptx::instr_desc(F::kFormat, kBM, (uint32_t)G.bn);
+        // an MN-major A tile: 32 K rows of 128 bytes per 64-row box (atoms of 8
+        // rows 1024 bytes apart), the second box kTileA / 2 further
+        const bool amn = F::kElem == 2 && G.a_mn;
+        const uint32_t idesc = ptx::instr_desc(F::kFormat, kBM, (uint32_t)G.bn) | (amn ? ptx::kInstrAMajorMN : 0u);
         const int kblocks = G.kblocks;
         if (!ptx::mbar_wait(&tempty[buf], tph ^ 1, abort, L.wait_ns)) {
           tc_fail(abort, L.status);
@@ -398,8 +411,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const __grid_con
 #pragma unroll
             for (int kk = 0; kk < 2; ++kk) {
               const uint32_t off = kk * 32;  // one MMA consumes 32 bytes of K
-              const uint64_t ah = ptx::smem_desc(st + off, kSBO, kSwizzle64);
-              const uint64_t al = ptx::smem_desc(st + kTileA + off, kSBO, kSwizzle64);
+              const uint64_t ah = amn ? ptx::smem_desc_mn128(st + kk * 2048, kTileA / 2, 1024)
+                                      : ptx::smem_desc(st + off, kSBO, kSwizzle64);
+              const uint64_t al = amn ? ptx::smem_desc_mn128(st + kTileA + kk * 2048, kTileA / 2, 1024)
+                                      : ptx::smem_desc(st + kTileA + off, kSBO, kSwizzle64);
               const uint64_t bh = ptx::smem_desc(st + 2 * kTileA + off, kSBO, kSwizzle64);
               const uint64_t bl = ptx::smem_desc(st + 2 * kTileA + btile + off, kSBO, kSwizzle64);
               F::mma(d, ah, bh, idesc, acc);
@@ -657,6 +672,475 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const __grid_con
     }
     if (threadIdx.x == 0)  // the last loads into every stage: their phase completes when they land
       for (int st = 0; st < nst; ++st)
+        if (armed & (1u << st)) ptx::mbar_wait(&full[st], (armed_par >> st) & 1u, &no_abort, kDrainNs);
+    __syncthreads();
+  }
+  if (warp == 1) ptx::tmem_dealloc(tmem_base, 512);
+}
+
+// ---------------------------------------------------------------- fused mode-1 / mode-2 products
+//
+// On a grid whose axes are all folded, with h1, h2 <= 128 entries per half on
+// the first two (multiples of 32), the mode-1 and mode-2 products of a slab i3
+// run in one persistent kernel and the mode-1 results never leave the SM.  A
+// unit is (slab i3, node k, output half h1o of axis 1).  Its mode-1 products
+// are formed transposed, the factor block being the A operand:
+//     Y_q[a1][i2] = sum_j1 T1_{k,q}[h1o][a1][j1] X_q[i3][i2][off1 + j1],
+// so the accumulator holds one a1 per TMEM lane with i2 along the columns;
+// split into BF16 hi / lo, every 32 columns of it are one K-major k-block of
+// the A operand of the mode-2 product
+//     Z[a1][a2] = sum_i2 Y[a1][i2] T2_{k,type}[h2o][a2][i2],
+// written through shared memory (never to the workspace).  Z is stored as
+// [field][i3][a2][a1] (a1 contiguous, U_k field 2k, V_k field 2k + 1), which
+// the mode-3 stage reads MN-major (TcGroup::a_mn).  Per unit six chunks
+// (component q, input half hh of axis 2) in the order
+//     c     0  1  2  3  4  5
+//     q     0  1  0  1  2  2
+//     hh    0  1  1  0  0  1
+//   target U0 U0 U1 U1 V0 V1  (U_k = Y_1 x2 E + Y_2 x2 F, V_k = Y_3 x2 E; the
+// index is the output half h2o = hh for E, hh ^ 1 for F).  Roles (10 warps):
+//   warp 0      TMA producer: per chunk the mode-1 k-blocks (A: factor block,
+//               128 rows; B: h2 rows of X) and, one chunk behind, the
+//               mode-2 k-blocks (B: factor block of axis 2),
+//   warp 1      MMA issuer: mode-1 of chunk t into one of two 128-column
+//               accumulators, then mode-2 of chunk t - 1 (A from the Y slots)
+//               into one of two 128-column accumulators of the targets,
+//   warps 2..5  mode-1 epilogue: accumulator -> hi / lo -> Y slots (a ring of
+//               k-blocks in shared memory, handed to the MMA by mbarriers),
+//   warps 6..9  mode-2 epilogue: accumulator -> hi / lo -> Z (TMA stores).
+// Every wait is bounded as in tc_gemm_kernel, with the same abort path.
+constexpr int kS12Threads = 320;
+constexpr int kS12Stages = 4;
+constexpr int kS12Stage = 4 * kTileA;             // A hi, A lo (128 rows), B hi, B lo (<= 128 rows)
+constexpr int kS12Slots = 4;
+constexpr int kS12Slot = 2 * kTileA;              // one k-block of Y, hi and lo
+constexpr int kS12Staging = 4 * kOutBufsPerWarp * kOutBuf;
+constexpr int kS12Smem = 1024 + kS12Stages * kS12Stage + kS12Slots * kS12Slot + kS12Staging + kBarBytes;
+static_assert(kS12Smem <= kSmemMax, "fused kernel shared memory");
+
+struct S12Launch {
+  CUtensorMap t1_hi, t1_lo;            // axis-1 factor blocks, 128-row boxes (mode-1 A)
+  CUtensorMap x_hi, x_lo;              // split input, h2-row boxes (mode-1 B)
+  CUtensorMap t2_hi, t2_lo;            // axis-2 factor blocks, h2-row boxes (mode-2 B)
+  CUtensorMap z_hi, z_lo;              // Z [2M ext3][ext2][ext1], 32 x 32 store boxes
+  int M, x2, x3;                       // nodes, extents of axes 2 and 3
+  int h1, h2;                          // entries per half (= start of the odd half) of axes 1, 2
+  int kb1, kb2;                        // k-blocks of the two contractions (h1 / 32, h2 / 32)
+  int units;                           // ext3 * M * 2
+  int* unit_counter;                   // zeroed before the launch
+  int* status;
+  unsigned long long wait_ns;
+};
+
+__device__ __forceinline__ void s12_chunk(int c, int& q, int& hh) {
+  q = c < 4 ? (c & 1) : 2;
+  hh = c < 4 ? (((c >> 1) ^ c) & 1) : (c & 1);
+}
+
+// hi / lo BF16 of two consecutive values, packed (the first in the low half)
+__device__ __forceinline__ void split_pair(float a, float b, uint32_t& hi, uint32_t& lo) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  const float2 hf = __bfloat1622float2(h);
+  const __nv_bfloat162 l = __floats2bfloat162_rn(a - hf.x, b - hf.y);
+  hi = *reinterpret_cast<const uint32_t*>(&h);
+  lo = *reinterpret_cast<const uint32_t*>(&l);
+}
+
+__global__ void __launch_bounds__(kS12Threads, 1) tc_s12_kernel(const __grid_constant__ S12Launch L) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* stages = base;
+  uint8_t* yslots = stages + kS12Stages * kS12Stage;
+  uint8_t* ostage = yslots + kS12Slots * kS12Slot;
+  uint64_t* full = reinterpret_cast<uint64_t*>(ostage + kS12Staging);
+  uint64_t* empty = full + kS12Stages;
+  uint64_t* d1full = empty + kS12Stages;   // [2] mode-1 accumulators
+  uint64_t* d1empty = d1full + 2;
+  uint64_t* yfull = d1empty + 2;           // [kS12Slots]
+  uint64_t* yempty = yfull + kS12Slots;
+  uint64_t* d2full = yempty + kS12Slots;   // [2] mode-2 accumulators
+  uint64_t* d2empty = d2full + 2;
+  uint64_t* sfull = d2empty + 2;           // [kRing] unit ids
+  uint64_t* sempty = sfull + kRing;
+  uint64_t* drain = sempty + kRing;
+  volatile int* ring = reinterpret_cast<volatile int*>(drain + 1);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(const_cast<int*>(ring) + kRing);
+  volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kS12Stages; ++i) {
+      ptx::mbar_init(&full[i], 1);
+      ptx::mbar_init(&empty[i], 1);
+    }
+    for (int i = 0; i < kS12Slots; ++i) {
+      ptx::mbar_init(&yfull[i], 4);
+      ptx::mbar_init(&yempty[i], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      ptx::mbar_init(&d1full[b], 1);
+      ptx::mbar_init(&d1empty[b], 4);
+      ptx::mbar_init(&d2full[b], 1);
+      ptx::mbar_init(&d2empty[b], 4);
+    }
+    for (int i = 0; i < kRing; ++i) {
+      ptx::mbar_init(&sfull[i], 1);
+      ptx::mbar_init(&sempty[i], 9);
+    }
+    ptx::mbar_init(drain, 1);
+    *abort = 0;
+    ptx::fence_mbar_init();
+  }
+  if (warp == 1) {
+    ptx::tmem_alloc(tmem_slot, 512);
+    ptx::tmem_relinquish();
+  }
+  ptx::tc_fence_before();
+  __syncthreads();
+  ptx::tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+  bool issued_mma = false;
+  uint32_t armed = 0, armed_par = 0;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int s = 0;
+      uint32_t ph = 0;
+      int rs = 0;
+      uint32_t rph = 0;
+      bool ok = true;
+      // next operand stage (its previous contents consumed), or null after an abort
+      auto take_stage = [&]() -> uint8_t* {
+        if (!ptx::mbar_wait(&empty[s], ph ^ 1, abort, L.wait_ns)) {
+          tc_fail(abort, L.status);
+          ok = false;
+          return nullptr;
+        }
+        armed |= 1u << s;
+        armed_par = (armed_par & ~(1u << s)) | (ph << s);
+        return stages + s * kS12Stage;
+      };
+      auto next_stage = [&]() {
+        if (++s == kS12Stages) {
+          s = 0;
+          ph ^= 1;
+        }
+      };
+      auto load1 = [&](int u, int c) {
+        int q, hh;
+        s12_chunk(c, q, hh);
+        const int h1o = u & 1, k = (u >> 1) % L.M, i3 = (u >> 1) / L.M;
+        const int type = q == 0 ? 1 : 0;               // F along axis 1 for component 1
+        const int off1 = ((h1o ^ type) & 1) * L.h1;    // input half of axis 1
+        const int row = i3 * L.x2 + hh * L.h2;
+        for (int kb = 0; kb < L.kb1 && ok; ++kb) {
+          uint8_t* st = take_stage();
+          if (!st) break;
+          ptx::mbar_arrive_expect_tx(&full[s], 2 * kTileA + 2 * L.h2 * kRowBytes);
+          ptx::tma_load_4d(st, &L.t1_hi, &full[s], kb * 32, 0, h1o, 2 * k + type);
+          ptx::tma_load_4d(st + kTileA, &L.t1_lo, &full[s], kb * 32, 0, h1o, 2 * k + type);
+          ptx::tma_load_3d(st + 2 * kTileA, &L.x_hi, &full[s], off1 + kb * 32, row, q);
+          ptx::tma_load_3d(st + 3 * kTileA, &L.x_lo, &full[s], off1 + kb * 32, row, q);
+          next_stage();
+        }
+      };
+      auto load2 = [&](int u, int c) {
+        int q, hh;
+        s12_chunk(c, q, hh);
+        const int k = (u >> 1) % L.M;
+        const int type = q == 1 ? 1 : 0;               // F along axis 2 for component 2
+        const int h2o = hh ^ type;
+        for (int kb = 0; kb < L.kb2 && ok; ++kb) {
+          uint8_t* st = take_stage();
+          if (!st) break;
+          ptx::mbar_arrive_expect_tx(&full[s], 2 * L.h2 * kRowBytes);
+          ptx::tma_load_4d(st + 2 * kTileA, &L.t2_hi, &full[s], kb * 32, 0, h2o, 2 * k + type);
+          ptx::tma_load_4d(st + 3 * kTileA, &L.t2_lo, &full[s], kb * 32, 0, h2o, 2 * k + type);
+          next_stage();
+        }
+      };
+      int pu = -1, pc = 0;  // chunk whose mode-2 operands come next
+      while (ok && !*abort) {
+        if (!ptx::mbar_wait(&sempty[rs], rph ^ 1, abort, L.wait_ns)) {
+          tc_fail(abort, L.status);
+          break;
+        }
+        const int u = atomicAdd(L.unit_counter, 1);
+        ring[rs] = u < L.units ? u : -1;
+        ptx::mbar_arrive(&sfull[rs]);
+        if (++rs == kRing) { rs = 0; rph ^= 1; }
+        if (u >= L.units) break;
+        for (int c = 0; c < 6 && ok; ++c) {
+          load1(u, c);
+          if (pu >= 0 && ok) load2(pu, pc);
+          pu = u;
+          pc = c;
+        }
+      }
+      if (ok && !*abort && pu >= 0) load2(pu, pc);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      int s = 0;
+      uint32_t ph = 0;
+      int rs = 0;
+      uint32_t rph = 0;
+      uint32_t t = 0, yc = 0, g = 0;  // mode-1 chunks, Y slots and mode-2 targets issued
+      bool ok = true;
+      const uint32_t idesc = ptx::instr_desc(1, kBM, (uint32_t)L.h2);
+      auto take_full = [&]() -> uint32_t {
+        if (!ptx::mbar_wait(&full[s], ph, abort, L.wait_ns)) {
+          tc_fail(abort, L.status);
+          ok = false;
+          return 0;
+        }
+        ptx::tc_fence_after();
+        return ptx::smem_u32(stages + s * kS12Stage);
+      };
+      auto release_stage = [&]() {
+        ptx::mma_commit(&empty[s]);
+        if (++s == kS12Stages) {
+          s = 0;
+          ph ^= 1;
+        }
+      };
+      auto mma1 = [&]() {
+        const uint32_t b = t & 1;
+        if (!ptx::mbar_wait(&d1empty[b], ((t >> 1) & 1) ^ 1, abort, L.wait_ns)) {
+          tc_fail(abort, L.status);
+          ok = false;
+          return;
+        }
+        ptx::tc_fence_after();
+        const uint32_t d = tmem_base + b * 128;
+        for (int kb = 0; kb < L.kb1 && ok; ++kb) {
+          const uint32_t st = take_full();
+          if (!ok) break;
+#pragma unroll
+          for (int kk = 0; kk < 2; ++kk) {
+            const uint32_t off = kk * 32;
+            const uint64_t ah = ptx::smem_desc(st + off, kSBO, kSwizzle64);
+            const uint64_t al = ptx::smem_desc(st + kTileA + off, kSBO, kSwizzle64);
+            const uint64_t bh = ptx::smem_desc(st + 2 * kTileA + off, kSBO, kSwizzle64);
+            const uint64_t bl = ptx::smem_desc(st + 3 * kTileA + off, kSBO, kSwizzle64);
+            Bf16Form::mma(d, ah, bh, idesc, (kb | kk) ? 1u : 0u);
+            Bf16Form::mma(d, ah, bl, idesc, 1u);
+            Bf16Form::mma(d, al, bh, idesc, 1u);
+          }
+          issued_mma = true;
+          release_stage();
+        }
+        if (!ok) return;
+        ptx::mma_commit(&d1full[b]);
+        ++t;
+      };
+      auto mma2 = [&](int c) {
+        const bool first = c < 4 ? (c & 1) == 0 : true;
+        const bool last = c < 4 ? (c & 1) == 1 : true;
+        const uint32_t b = g & 1;
+        if (first) {
+          if (!ptx::mbar_wait(&d2empty[b], ((g >> 1) & 1) ^ 1, abort, L.wait_ns)) {
+            tc_fail(abort, L.status);
+            ok = false;
+            return;
+          }
+          ptx::tc_fence_after();
+        }
+        const uint32_t d = tmem_base + 256 + b * 128;
+        for (int kb = 0; kb < L.kb2 && ok; ++kb) {
+          const uint32_t ys = yc % kS12Slots;
+          if (!ptx::mbar_wait(&yfull[ys], (yc / kS12Slots) & 1, abort, L.wait_ns)) {
+            tc_fail(abort, L.status);
+            ok = false;
+            break;
+          }
+          const uint32_t st = take_full();
+          if (!ok) break;
+          const uint32_t ya = ptx::smem_u32(yslots + ys * kS12Slot);
+#pragma unroll
+          for (int kk = 0; kk < 2; ++kk) {
+            const uint32_t off = kk * 32;
+            const uint64_t ah = ptx::smem_desc(ya + off, kSBO, kSwizzle64);
+            const uint64_t al = ptx::smem_desc(ya + kTileA + off, kSBO, kSwizzle64);
+            const uint64_t bh = ptx::smem_desc(st + 2 * kTileA + off, kSBO, kSwizzle64);
+            const uint64_t bl = ptx::smem_desc(st + 3 * kTileA + off, kSBO, kSwizzle64);
+            Bf16Form::mma(d, ah, bh, idesc, (first && kb == 0 && kk == 0) ? 0u : 1u);
+            Bf16Form::mma(d, ah, bl, idesc, 1u);
+            Bf16Form::mma(d, al, bh, idesc, 1u);
+          }
+          issued_mma = true;
+          release_stage();
+          ptx::mma_commit(&yempty[ys]);
+          ++yc;
+        }
+        if (!ok) return;
+        if (last) {
+          ptx::mma_commit(&d2full[b]);
+          ++g;
+        }
+      };
+      int pc = -1;  // chunk of the previous unit / this unit whose mode-2 products come next
+      while (ok && !*abort) {
+        if (!ptx::mbar_wait(&sfull[rs], rph, abort, L.wait_ns)) {
+          tc_fail(abort, L.status);
+          break;
+        }
+        const int u = ring[rs];
+        ptx::mbar_arrive(&sempty[rs]);
+        if (++rs == kRing) { rs = 0; rph ^= 1; }
+        if (u < 0) break;
+        for (int c = 0; c < 6 && ok; ++c) {
+          mma1();
+          if (pc >= 0 && ok) mma2(pc);
+          pc = c;
+        }
+      }
+      if (ok && !*abort && pc >= 0) mma2(pc);
+    }
+  } else if (warp < 6) {
+    // mode-1 epilogue: row a1 = quad * 32 + lane of the accumulator; each
+    // 32-column block becomes one k-block of Y: 64-byte rows in the 64-byte
+    // swizzle of the TMA (16-byte chunk c of row r at c ^ ((r >> 1) & 3))
+    const int quad = warp & 3;
+    const int r = quad * 32 + lane;
+    const uint32_t rowoff = (uint32_t)r * 64, sw = (uint32_t)(r >> 1) & 3u;
+    int rs = 0;
+    uint32_t rph = 0;
+    uint32_t t = 0, yc = 0;
+    bool ok = true;
+    while (ok && !*abort) {
+      if (!ptx::mbar_wait(&sfull[rs], rph, abort, L.wait_ns)) {
+        tc_fail(abort, L.status);
+        break;
+      }
+      const int u = ring[rs];
+      __syncwarp();
+      if (lane == 0) ptx::mbar_arrive(&sempty[rs]);
+      if (++rs == kRing) { rs = 0; rph ^= 1; }
+      if (u < 0) break;
+      for (int c = 0; c < 6 && ok; ++c) {
+        const uint32_t b = t & 1;
+        if (!ptx::mbar_wait(&d1full[b], (t >> 1) & 1, abort, L.wait_ns)) {
+          tc_fail(abort, L.status);
+          ok = false;
+          break;
+        }
+        ptx::tc_fence_after();
+        const uint32_t taddr = tmem_base + ((uint32_t)(quad * 32) << 16) + b * 128;
+        for (int kb = 0; kb < L.kb2; ++kb) {
+          uint32_t v[32];
+          ptx::tmem_ld32(taddr + (uint32_t)(kb * 32), v);
+          const uint32_t ys = yc % kS12Slots;
+          if (!ptx::mbar_wait(&yempty[ys], ((yc / kS12Slots) & 1) ^ 1, abort, L.wait_ns)) {
+            ptx::tmem_ld_wait(v);
+            tc_fail(abort, L.status);
+            ok = false;
+            break;
+          }
+          ptx::tmem_ld_wait(v);
+          uint8_t* slot = yslots + ys * kS12Slot;
+#pragma unroll
+          for (int cc = 0; cc < 4; ++cc) {
+            uint32_t hw[4], lw[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+              split_pair(__uint_as_float(v[cc * 8 + 2 * e]), __uint_as_float(v[cc * 8 + 2 * e + 1]), hw[e], lw[e]);
+            const uint32_t o = rowoff + (((uint32_t)cc ^ sw) << 4);
+            *reinterpret_cast<uint4*>(slot + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+            *reinterpret_cast<uint4*>(slot + kTileA + o) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+          }
+          ptx::fence_proxy_async_smem();
+          __syncwarp();
+          if (lane == 0) ptx::mbar_arrive(&yfull[ys]);
+          ++yc;
+        }
+        if (!ok) break;
+        ptx::tc_fence_before();
+        __syncwarp();
+        if (lane == 0) ptx::mbar_arrive(&d1empty[b]);
+        ++t;
+      }
+    }
+  } else {
+    // mode-2 epilogue: rows a1 of the unit's output half, columns a2; each
+    // 32 x 32 chunk staged as [a2][a1] and stored as one box per plane
+    const int quad = warp & 3;
+    uint8_t* stg = ostage + (warp - 6) * (kOutBufsPerWarp * kOutBuf);
+    int rs = 0;
+    uint32_t rph = 0;
+    uint32_t g = 0, chunk = 0;
+    bool ok = true;
+    while (ok && !*abort) {
+      if (!ptx::mbar_wait(&sfull[rs], rph, abort, L.wait_ns)) {
+        tc_fail(abort, L.status);
+        break;
+      }
+      const int u = ring[rs];
+      __syncwarp();
+      if (lane == 0) ptx::mbar_arrive(&sempty[rs]);
+      if (++rs == kRing) { rs = 0; rph ^= 1; }
+      if (u < 0) break;
+      const int h1o = u & 1, k = (u >> 1) % L.M, i3 = (u >> 1) / L.M;
+      const bool valid = quad * 32 < L.h1;  // rows past h1 are zero and not stored
+      for (int j = 0; j < 4 && ok; ++j) {
+        const uint32_t b = g & 1;
+        if (!ptx::mbar_wait(&d2full[b], (g >> 1) & 1, abort, L.wait_ns)) {
+          tc_fail(abort, L.status);
+          ok = false;
+          break;
+        }
+        ptx::tc_fence_after();
+        const uint32_t taddr = tmem_base + ((uint32_t)(quad * 32) << 16) + 256 + b * 128;
+        const int zf = i3 + L.x3 * (2 * k + (j >> 1));
+        const int a1 = h1o * L.h1 + quad * 32;
+        const int a2 = (j & 1) * L.h2;
+        for (int c0 = 0; c0 < L.h2; c0 += 32) {
+          uint32_t v[32];
+          ptx::tmem_ld32(taddr + (uint32_t)c0, v);
+          ptx::tmem_ld_wait(v);
+          if (!valid) continue;
+          uint8_t* sb = stg + (chunk % kOutBufsPerWarp) * kOutBuf;
+          ++chunk;
+          if (lane == 0) ptx::bulk_wait_read<kOutBufsPerWarp - 1>();
+          __syncwarp();
+          __nv_bfloat16* sh = reinterpret_cast<__nv_bfloat16*>(sb);
+          __nv_bfloat16* sl = sh + 32 * 32;
+#pragma unroll
+          for (int jj = 0; jj < 32; ++jj) {
+            __nv_bfloat16 hi, lo;
+            Bf16Form::split(__uint_as_float(v[jj]), hi, lo);
+            sh[jj * 32 + lane] = hi;
+            sl[jj * 32 + lane] = lo;
+          }
+          ptx::fence_proxy_async_smem();
+          __syncwarp();
+          if (lane == 0) {
+            ptx::tma_store_3d(&L.z_hi, sb, a1, a2 + c0, zf);
+            ptx::tma_store_3d(&L.z_lo, sb + 32 * 32 * 2, a1, a2 + c0, zf);
+            ptx::bulk_commit();
+          }
+        }
+        ptx::tc_fence_before();
+        __syncwarp();
+        if (lane == 0) ptx::mbar_arrive(&d2empty[b]);
+        ++g;
+      }
+    }
+    if (lane == 0) ptx::bulk_wait_all();
+  }
+
+  __syncwarp();
+  ptx::tc_fence_before();
+  __syncthreads();
+  ptx::tc_fence_after();
+  if (*abort) {
+    volatile int no_abort = 0;
+    if (warp == 1 && lane == 0 && issued_mma) {
+      ptx::mma_commit(drain);
+      ptx::mbar_wait(drain, 0, &no_abort, kDrainNs);
+    }
+    if (threadIdx.x == 0)
+      for (int st = 0; st < kS12Stages; ++st)
         if (armed & (1u << st)) ptx::mbar_wait(&full[st], (armed_par >> st) & 1u, &no_abort, kDrainNs);
     __syncthreads();
   }
@@ -1201,10 +1685,31 @@ static bool make_out_map(CUtensorMap* m, void* base, int elem_bytes, uint64_t in
   return r == CUDA_SUCCESS;
 }
 
+// 3D BF16 map with explicit strides, box and swizzle (the fused application's
+// Z fields and its operand maps of other box shapes).
+static bool make_map3(CUtensorMap* m, void* base, uint64_t d0, uint64_t d1, uint64_t d2, uint64_t s1_elems,
+                      uint64_t s2_elems, uint32_t b0, uint32_t b1, CUtensorMapSwizzle sw) {
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return false;
+  cuuint64_t dims[3] = {d0, d1, d2};
+  cuuint64_t strides[2] = {s1_elems * 2, s2_elems * 2};
+  cuuint32_t box[3] = {b0, b1, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
 static int round_up(int v, int m) { return (v + m - 1) / m * m; }
 
-// Stage programs of a plan: forward stages 0-2, adjoint stages 3-5.
-enum { kFwd1 = 0, kFwd2, kFwd3, kAdj1, kAdj2, kAdj3, kPrograms };
+// Stage programs of a plan: forward stages 0-2, adjoint stages 3-5, and the
+// mode-3 stage of the fused forward application (A = Z read MN-major).
+enum { kFwd1 = 0, kFwd2, kFwd3, kAdj1, kAdj2, kAdj3, kFwd3Z, kPrograms };
+constexpr int kChain = kFwd3Z;  // programs of the three-stage chains
+
+// axis contracted by stage program p
+static int prog_axis(int p) { return p == kFwd3Z ? 2 : p % 3; }
 
 // Per-plan, per-form tensor-core state.
 struct TcState {
@@ -1236,6 +1741,11 @@ struct TcState {
   TcGroup host_prog[kPrograms];
   bool small[kPrograms];          // program runs on CUDA cores (axis of at most kSmallAxis cells)
   SmallStage small_prog[kPrograms];
+  // fused forward application (tc_s12_kernel, then kFwd3Z): built where the
+  // grid allows it (BF16x3, every axis folded, h1 and h2 multiples of 32 up
+  // to 128); the Z fields live in buf1
+  bool fused;
+  S12Launch s12;
   // analytic stray field: the forward stage programs with the derivative
   // factors of their axis (built on first use)
   bool field_ready;
@@ -1369,7 +1879,7 @@ static short mat(int k, int type) { return (short)(2 * k + type); }
 struct ProgramBuild {
   std::vector<TcJob> jobs;
   std::vector<short2> pairs;
-  int job0[kPrograms], pair0[kPrograms];
+  int job0[kChain], pair0[kChain];
 };
 
 // The segment covering every tile of group `group`, starting at launch tile tile0.
@@ -1417,7 +1927,7 @@ static demag_status build_programs(demag_plan* P, TcState* S, const CUtensorMap 
                                    const CUtensorMap (&mapB)[3][2], const CUtensorMap (&out1)[2],
                                    const CUtensorMap (&out2)[2], const CUtensorMap& out3,
                                    const CUtensorMap (&wout1)[2], const CUtensorMap (&wout2)[2],
-                                   const CUtensorMap& wout3, int bk, cudaStream_t st) {
+                                   const CUtensorMap& wout3, const CUtensorMap (&zA)[2], int bk, cudaStream_t st) {
   const AxisGeo& g = S->geo;
   const int M = P->M;
   const int x1 = g.ext[0], x2 = g.ext[1], x3 = g.ext[2];
@@ -1430,10 +1940,10 @@ static demag_status build_programs(demag_plan* P, TcState* S, const CUtensorMap 
   // one job per output half, all reading the last npairs pairs pushed
   auto add_job = [&](int prog, int npairs, int out_field) {
     const int p0 = (int)b.pairs.size() - b.pair0[prog] - npairs;
-    for (int hf = 0; hf < S->halves[prog % 3]; ++hf) b.jobs.push_back(job(p0, npairs, out_field, hf));
+    for (int hf = 0; hf < S->halves[prog_axis(prog)]; ++hf) b.jobs.push_back(job(p0, npairs, out_field, hf));
   };
   auto add_job_at = [&](int prog, int p0, int npairs, int out_field) {
-    for (int hf = 0; hf < S->halves[prog % 3]; ++hf) b.jobs.push_back(job(p0, npairs, out_field, hf));
+    for (int hf = 0; hf < S->halves[prog_axis(prog)]; ++hf) b.jobs.push_back(job(p0, npairs, out_field, hf));
   };
   // forward mode 1: Y[k][q] = m_q x_1 T_{k,q,1}; rows (i3, i2), contraction i1 -> Y [i1'][i3][i2]
   begin(kFwd1);
@@ -1506,7 +2016,7 @@ static demag_status build_programs(demag_plan* P, TcState* S, const CUtensorMap 
   H[kAdj1] = H[kFwd1];
   H[kAdj2] = H[kFwd2];
   H[kAdj3] = H[kFwd3];
-  for (int p = 0; p < kPrograms; ++p) {
+  for (int p = 0; p < kChain; ++p) {
     const int stage = p % 3;
     if (S->tma[stage]) {
       H[p].tma_out = 1;
@@ -1521,12 +2031,21 @@ static demag_status build_programs(demag_plan* P, TcState* S, const CUtensorMap 
   DEMAG_CUDA(P, cudaMalloc(&S->pairs, sizeof(short2) * b.pairs.size()));
   DEMAG_CUDA(P, cudaMemcpy(S->jobs, b.jobs.data(), sizeof(TcJob) * b.jobs.size(), cudaMemcpyHostToDevice));
   DEMAG_CUDA(P, cudaMemcpy(S->pairs, b.pairs.data(), sizeof(short2) * b.pairs.size(), cudaMemcpyHostToDevice));
-  for (int p = 0; p < kPrograms; ++p) {
-    const int jend = p + 1 < kPrograms ? b.job0[p + 1] : job_end;
+  for (int p = 0; p < kChain; ++p) {
+    const int jend = p + 1 < kChain ? b.job0[p + 1] : job_end;
     H[p].jobs = S->jobs + b.job0[p];
     H[p].pairs = S->pairs + b.pair0[p];
     H[p].njobs = jend - b.job0[p];
     H[p].ntiles = H[p].njobs * H[p].m_tiles * H[p].n_tiles;
+  }
+  // the fused application's mode-3 stage: the forward mode-3 program with Z
+  // ([field][i3][a2][a1]) as its A operand, read MN-major; the same rows
+  // (a2, a1), pairs and output
+  H[kFwd3Z] = H[kFwd3];
+  if (S->fused) {
+    H[kFwd3Z].a_hi = zA[0];
+    H[kFwd3Z].a_lo = zA[1];
+    H[kFwd3Z].a_mn = 1;
   }
   // stages along an axis of at most kSmallAxis cells (never folded) run on CUDA cores
   {
@@ -1534,7 +2053,7 @@ static demag_status build_programs(demag_plan* P, TcState* S, const CUtensorMap 
     const void* in_lo[3] = {S->X[1], S->buf1[1], S->buf2[1]};
     const long long rows_of[3] = {(long long)x3 * x2, (long long)x1 * x3, (long long)x2 * x1};
     for (int p = 0; p < kPrograms; ++p) {
-      const int stage = p % 3;
+      const int stage = prog_axis(p);
       S->small[p] = P->n[stage] <= kSmallAxis;
       if (!S->small[p]) continue;
       SmallStage& Q = S->small_prog[p];
@@ -1592,6 +2111,7 @@ static demag_status prepare_form(demag_plan* P, TcState* S, cudaStream_t st) {
   const unsigned long long bit = 1ull << (dev & 63);
   if (!(attr & bit)) {
     DEMAG_CUDA(P, cudaFuncSetAttribute(tc_gemm_kernel<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax));
+    DEMAG_CUDA(P, cudaFuncSetAttribute(tc_s12_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kS12Smem));
     attr |= bit;
   }
   return DEMAG_OK;
@@ -1603,7 +2123,7 @@ static demag_status run_program(demag_plan* P, TcState* S, int prog, cudaStream_
 // Point stage program `prog` at output-column tile width bn (device copy included).
 static demag_status set_tile_width(demag_plan* P, TcState* S, int prog, int bn) {
   TcGroup& G = S->host_prog[prog];
-  const int axis = prog % 3;
+  const int axis = prog_axis(prog);
   const int M = P->M;
   for (int h = 0; h < 2; ++h)
     if (!make_bmap(h ? &G.b_lo : &G.b_hi, S->B[axis][h], S->elem, S->geo.h[axis], S->halves[axis], 2 * M,
@@ -1644,7 +2164,7 @@ static demag_status set_knob(demag_plan* P, TcState* S, int prog, int knob, int 
   if (knob == 2) return set_tile_order(P, S, prog, v);
   // store boxes: wide ones only where the stage has them
   TcGroup& G = S->host_prog[prog];
-  G.o_wide = (v && S->wide[prog % 3]) ? 1 : 0;
+  G.o_wide = (v && S->wide[prog_axis(prog)]) ? 1 : 0;
   DEMAG_CUDA(P, cudaMemcpy(S->prog + prog, &G, sizeof(TcGroup), cudaMemcpyHostToDevice));
   return DEMAG_OK;
 }
@@ -1652,7 +2172,7 @@ static demag_status set_knob(demag_plan* P, TcState* S, int prog, int knob, int 
 // Apply tuned entries already in the plan (a loaded cache) to its programs.
 static demag_status apply_tuned(demag_plan* P, TcState* S) {
   for (int prog = 0; prog < kPrograms; ++prog) {
-    if (S->small[prog]) continue;
+    if (S->small[prog] || (prog == kFwd3Z && !S->fused)) continue;
     for (int knob = 0; knob < 4; ++knob) {
       const demag_plan::Tuned* t = find_tuned(P, tune_kind(S, knob), prog);
       if (!t) continue;
@@ -1693,6 +2213,7 @@ static demag_status tune_programs(demag_plan* P, TcState* S, cudaStream_t st) {
   };
   for (int prog = 0; prog < kPrograms && s == DEMAG_OK; ++prog) {
     if (S->small[prog]) continue;  // runs on CUDA cores
+    if (prog == kFwd3Z && !S->fused) continue;
     for (int knob = 0; knob < 4 && s == DEMAG_OK; ++knob) {
       if (find_tuned(P, tune_kind(S, knob), prog)) continue;  // chosen before (a loaded cache)
       std::vector<int> cands;
@@ -1711,7 +2232,7 @@ static demag_status tune_programs(demag_plan* P, TcState* S, cudaStream_t st) {
       } else {
         def = 0;
         cands = {0};
-        if (S->wide[prog % 3]) cands.push_back(1);
+        if (S->wide[prog_axis(prog)]) cands.push_back(1);
       }
       if (cands.size() == 1) continue;
       float best = 1e30f, at_def = 0.f;
@@ -1857,8 +2378,41 @@ demag_status tc_prepare(demag_plan* P, demag_precision prec, cudaStream_t st) {
     free_state(S);
     return set_error(P, DEMAG_ECUDA, "tensor map encoding failed");
   }
+  // the fused forward application (mode-1 and mode-2 products in one kernel)
+  CUtensorMap zA[2];
+  memset(zA, 0, sizeof(zA));
+  {
+    const int h1 = geo.h[0], h2 = geo.h[1];
+    S->fused = S->elem == 2 && !P->nonuniform && geo.hq[0] && geo.hq[1] && geo.hq[2] && h1 % 32 == 0 &&
+               h2 % 32 == 0 && h1 <= 128 && h2 <= 128;
+    if (S->fused) {
+      S12Launch& Z = S->s12;
+      for (int h = 0; h < 2 && ok; ++h) {
+        void* zb = S->buf1[h];  // Z [2M][ext3][ext2][ext1] in the stage-1 workspace
+        ok = ok && make_bmap(h ? &Z.t1_lo : &Z.t1_hi, S->B[0][h], 2, h1, 2, 2 * M, S->ldB[0], kBM);
+        ok = ok && make_map(h ? &Z.x_lo : &Z.x_hi, S->X[h], 2, x1, (uint64_t)(x3 * x2), 3, S->ld[0], h2);
+        ok = ok && make_bmap(h ? &Z.t2_lo : &Z.t2_hi, S->B[1][h], 2, h2, 2, 2 * M, S->ldB[1], h2);
+        ok = ok && make_map3(h ? &Z.z_lo : &Z.z_hi, zb, x1, x2, (uint64_t)x3 * 2 * M, x1, x2 * x1, 32, 32,
+                             CU_TENSOR_MAP_SWIZZLE_NONE);
+        ok = ok && make_map3(&zA[h], zb, x2 * x1, x3, 2 * M, x2 * x1, x3 * x2 * x1, 64, 32,
+                             CU_TENSOR_MAP_SWIZZLE_128B);
+      }
+      Z.M = M;
+      Z.x2 = (int)x2;
+      Z.x3 = (int)x3;
+      Z.h1 = h1;
+      Z.h2 = h2;
+      Z.kb1 = h1 / 32;
+      Z.kb2 = h2 / 32;
+      Z.units = (int)x3 * M * 2;
+      if (!ok) {
+        free_state(S);
+        return set_error(P, DEMAG_ECUDA, "tensor map encoding failed");
+      }
+    }
+  }
   const int bk = kRowBytes / S->elem;
-  demag_status s = build_programs(P, S, mapX, map1, map2, mapB, out1, out2, out3, wout1, wout2, wout3, bk, st);
+  demag_status s = build_programs(P, S, mapX, map1, map2, mapB, out1, out2, out3, wout1, wout2, wout3, zA, bk, st);
   if (s == DEMAG_OK)
     s = prec == DEMAG_TF32X3 ? prepare_form<Tf32Form>(P, S, st) : prepare_form<Bf16Form>(P, S, st);
   if (s == DEMAG_OK) s = apply_tuned(P, S);
@@ -2043,10 +2597,31 @@ static demag_status reduce_parts(demag_plan* P, TcState* S, int groups, int nout
   return launch_reduce(P, L, st);
 }
 
+// The mode-1 and mode-2 products of every slab in one launch (Z into buf1).
+static demag_status run_s12(demag_plan* P, TcState* S, cudaStream_t st) {
+  S12Launch L = S->s12;
+  L.unit_counter = S->counter;
+  L.status = S->status;
+  L.wait_ns = P->wait_ns;
+  int sms = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = L.units < sms ? L.units : sms;
+  DEMAG_CUDA(P, cudaMemsetAsync(S->counter, 0, sizeof(int), st));
+  DEMAG_LAUNCH(P, kFamGemmTc, st, tc_s12_kernel<<<grid, kS12Threads, kS12Smem, st>>>(L));
+  DEMAG_LAUNCHED(P, "tc_s12_kernel");
+  return DEMAG_OK;
+}
+
 template <class F>
 static demag_status forward_chain(demag_plan* P, TcState* S, const float* m, float* phi, cudaStream_t st) {
   demag_status s = split_input<F>(P, S, m, 3, st);
-  for (int prog = kFwd1; prog <= kFwd3 && s == DEMAG_OK; ++prog) s = run_program<F>(P, S, prog, st);
+  if (S->fused && P->fused) {
+    if (s == DEMAG_OK) s = run_s12(P, S, st);
+    if (s == DEMAG_OK) s = run_program<F>(P, S, kFwd3Z, st);
+  } else {
+    for (int prog = kFwd1; prog <= kFwd3 && s == DEMAG_OK; ++prog) s = run_program<F>(P, S, prog, st);
+  }
   if (s != DEMAG_OK) return s;
   return reduce_parts(P, S, S->groups_fwd, 1, 1.f, phi, st);
 }

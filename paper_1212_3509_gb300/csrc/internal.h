@@ -84,6 +84,9 @@ struct demag_plan {
 
   // limit of the bounded device-side waits of the tensor-core kernels (ns)
   unsigned long long wait_ns = 2000000000ull;
+  // full-format forward application on tensor cores: 1 fuses the mode-1 and
+  // mode-2 products where the grid allows it, 0 runs the three-stage chain
+  int fused = 1;
 
   // autotuning: when on, launch shapes not yet tuned are timed on first use
   bool autotune = false;

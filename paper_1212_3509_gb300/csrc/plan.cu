@@ -550,6 +550,12 @@ extern "C" demag_status demag_set_wait_limit(demag_plan* plan, double seconds) {
   return DEMAG_OK;
 }
 
+extern "C" demag_status demag_set_fused(demag_plan* plan, int enable) {
+  if (!plan) return set_error(nullptr, DEMAG_EINVAL, "demag_set_fused: plan is NULL");
+  plan->fused = enable != 0;
+  return DEMAG_OK;
+}
+
 extern "C" demag_status demag_autotune(demag_plan* plan, int enable) {
   if (!plan) return set_error(nullptr, DEMAG_EINVAL, "demag_autotune: plan is NULL");
   plan->autotune = enable != 0;

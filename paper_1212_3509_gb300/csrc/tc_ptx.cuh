@@ -95,6 +95,16 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* m, uin
       : "memory");
 }
 
+// 3D tiled store from shared memory (bulk-group completion).  Coordinates are
+// non-negative; elements of the box outside the tensor are not written.
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap* m, const void* src, int c0, int c1, int c2) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%2, %3, %4}], [%1];" ::"l"(
+          reinterpret_cast<uint64_t>(m)),
+      "r"(smem_u32(src)), "r"(c0), "r"(c1), "r"(c2)
+      : "memory");
+}
+
 // 4D tiled store from shared memory (bulk-group completion).  Coordinates are
 // non-negative; elements of the box outside the tensor are not written.
 __device__ __forceinline__ void tma_store_4d(const CUtensorMap* m, const void* src, int c0, int c1, int c2,
@@ -276,11 +286,28 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t sbo_bytes,
   return d;
 }
 
+// The same for an MN-major operand with 128-byte swizzling: atoms of 8 rows
+// of K, each row 128 bytes of consecutive M (or N) elements; the leading byte
+// offset is the stride between atoms along M (or N), the stride byte offset
+// the stride between atoms along K.
+__device__ __forceinline__ uint64_t smem_desc_mn128(uint32_t addr, uint32_t lbo_bytes, uint32_t sbo_bytes) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((lbo_bytes >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo_bytes >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1u << 46;
+  d |= (uint64_t)2u << 61;
+  return d;
+}
+
 // Instruction descriptor: D = FP32, A/B format (1 = BF16, 2 = TF32), both
 // K-major, N >> 3 at bit 17, M >> 4 at bit 24.
 __host__ __device__ constexpr uint32_t instr_desc(uint32_t ab_format, uint32_t M, uint32_t N) {
   return (1u << 4) | (ab_format << 7) | (ab_format << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
 }
+
+// Bit 15 of the instruction descriptor: the A operand is MN-major.
+constexpr uint32_t kInstrAMajorMN = 1u << 15;
 
 }  // namespace ptx
 }  // namespace demag

@@ -76,5 +76,8 @@ def test_null_arguments_are_rejected(lib):
     lib.demag_num_terms.restype = ctypes.c_int
     lib.demag_num_terms.argtypes = [ctypes.c_void_p]
     assert lib.demag_num_terms(None) == -1
+    lib.demag_set_fused.restype = ctypes.c_int
+    lib.demag_set_fused.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    assert lib.demag_set_fused(None, 1) == 1
     lib.demag_plan_destroy.argtypes = [ctypes.c_void_p]
     lib.demag_plan_destroy(None)

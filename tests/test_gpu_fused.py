@@ -1,0 +1,84 @@
+"""Fused mode-1 / mode-2 products (BF16x3) against the FP64 oracle and the three-stage chain.
+
+A grid whose three axes are folded (longer than 16 cells) with ceil(n1 / 2) and
+ceil(n2 / 2) multiples of 32 up to 128 runs its forward application through the
+fused kernel by default; demag_set_fused(plan, False) selects the chain.  Odd
+extents (63, 127, 255) carry the padding cell of the folded layout; third axes
+of 17, 33 or 37 cells pad their halves to 16-byte multiples; h1 = 32 leaves
+three of the four TMEM lane quadrants of the mode-2 tile without rows."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import full as ofull
+from gpu_helpers import assert_close, TOL, dev, host, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+FUSED_SHAPES = [
+    ((64, 64, 20), (1 / 64,) * 3, 41),
+    ((63, 127, 17), (0.02, 0.01, 0.03), 21),
+    ((128, 192, 33), (1.0, 1.0, 1.0), 11),
+    ((255, 64, 24), (1 / 255, 1 / 64, 1 / 24), 11),
+    ((192, 256, 37), (0.5, 0.25, 1.0), 5),
+]
+
+
+@pytest.fixture(scope="module")
+def D():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1212_3509_gb300 as D
+    return D
+
+
+def _apply(D, P, m, fused):
+    n = P.n
+    D.demag_set_fused(P, fused)
+    phi = torch.empty(n[2], n[1], n[0], device="cuda")
+    D.demag_apply_full(P, m, phi, "bf16x3")
+    torch.cuda.synchronize()
+    D.demag_sync_status(P)
+    return host(phi)
+
+
+@pytest.mark.parametrize("n,h,R", FUSED_SHAPES)
+def test_fused_vs_oracle_and_chain(D, n, h, R):
+    m_h = synth.random_unit_m(n, 3509 + sum(n))
+    m = dev(m_h)
+    P = D.demag_build_factors(n, h, R)
+    fused = _apply(D, P, m, True)
+    chain = _apply(D, P, m, False)
+    ref_ = ofull.apply_full(m_h, n, h, R)
+    ef, ec = rel_l2(fused, ref_), rel_l2(chain, ref_)
+    print(f"{n}: fused {ef:.3e} chain {ec:.3e} fused-chain {rel_l2(fused, chain):.3e}")
+    assert_close(fused, ref_, TOL["bf16x3"], "fused")
+    assert_close(chain, ref_, TOL["bf16x3"], "chain")
+    # the same products accumulated in another order
+    assert_close(fused, chain, 2 * TOL["bf16x3"], "fused vs chain")
+
+
+def test_fused_repeated_calls_are_identical(D):
+    n, h, R = (128, 128, 40), (1 / 128,) * 3, 21
+    m = dev(synth.random_unit_m(n, 7))
+    P = D.demag_build_factors(n, h, R)
+    a = _apply(D, P, m, True)
+    b = _apply(D, P, m, True)
+    # every output entry is summed by one CTA in a fixed order
+    assert np.array_equal(a, b)
+
+
+def test_fused_and_chain_interleaved_256(D):
+    """The bench workload: fused, chain and fused again on one plan (the
+    fused kernel's Z fields share the workspace of the chain's stage 1)."""
+    n, h, R = (256, 256, 256), (1 / 256,) * 3, 41
+    m = dev(synth.vortex_m(n, seed=5))
+    P = D.demag_build_factors(n, h, R)
+    f1 = _apply(D, P, m, True)
+    c = _apply(D, P, m, False)
+    f2 = _apply(D, P, m, True)
+    assert np.array_equal(f1, f2)
+    assert_close(f1, c, 2 * TOL["bf16x3"], "fused vs chain at 256^3")
+
