@@ -53,19 +53,43 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
+// The same test, the thread suspended until the phase completes or about
+// `ns` nanoseconds pass (a waiting warp then takes no issue slots from the
+// warps it shares a scheduler with).
+__device__ __forceinline__ bool mbar_try_wait_suspend(uint64_t* bar, uint32_t parity, uint32_t ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(ns)
+      : "memory");
+  return ok != 0;
+}
+
 // Wait for the phase with the given parity to complete.  Gives up after
 // `limit_ns` nanoseconds or when *abort becomes non-zero; returns success.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort,
                                           uint64_t limit_ns) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = globaltimer();
-  for (uint32_t i = 0;; ++i) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if ((i & 63) == 0) {
-      if (*abort) return false;
-      if (globaltimer() - t0 > limit_ns) return false;
-    }
+  for (;;) {
+    if (mbar_try_wait_suspend(bar, parity, 10000)) return true;
+    if (*abort) return false;
+    if (globaltimer() - t0 > limit_ns) return false;
   }
+}
+
+// The same wait by every lane of a converged warp (the roles that issue TMA
+// copies and MMAs run their loops on the whole warp and issue from lane 0: a
+// single-lane loop around these waits issued MMAs measurably slower, ~89
+// against 64 cycles per 128 x 128 x 16 MMA); true when every lane saw the
+// phase complete.
+__device__ __forceinline__ bool mbar_wait_warp(uint64_t* bar, uint32_t parity, volatile int* abort,
+                                               uint64_t limit_ns) {
+  const bool r = mbar_wait(bar, parity, abort, limit_ns);
+  return __all_sync(0xffffffffu, r);
 }
 
 // ---------------------------------------------------------------- TMA
