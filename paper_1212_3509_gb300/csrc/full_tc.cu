@@ -702,56 +702,49 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const __grid_con
 // unit is (slab i3, node k, output half h1o of axis 1).  Its mode-1 products
 // are formed transposed, the factor block being the A operand:
 //     Y_q[a1][i2] = sum_j1 T1_{k,q}[h1o][a1][j1] X_q[i3][i2][off1 + j1],
-// one 128 x 2 h2 tile per component q (both halves of axis 2 in one MMA),
 // so the accumulator holds one a1 per TMEM lane with i2 along the columns;
 // split into BF16 hi / lo, every 32 columns of it are one K-major k-block of
 // the A operand of the mode-2 product
 //     Z[a1][a2] = sum_i2 Y[a1][i2] T2_{k,type}[h2o][a2][i2],
 // handed over in shared memory (never written to the workspace).  Z is stored
 // as [field][i3][a2][a1] (a1 contiguous, U_k field 2k, V_k field 2k + 1),
-// which the mode-3 stage reads MN-major (TcGroup::a_mn).  Per unit three
-// blocks q = 0, 1, 2, each a mode-1 tile and then its two mode-2 chunks
-// (input half hh = 0, 1 of axis 2) into the targets
-//     q = 0: U0 (hh 0), U1 (hh 1)     first contributions (E along axis 2)
-//     q = 1: U1 (hh 0), U0 (hh 1)     last contributions (F: h2o = hh ^ 1)
-//     q = 2: V0 (hh 0), V1 (hh 1)
-// (U_k = Y_1 x2 E + Y_2 x2 F, V_k = Y_3 x2 E; the index is the output half
-// h2o); U0 and V1 accumulate in TMEM buffer A, U1 and V0 in buffer B.
-// Roles (10 warps):
-//   warp 0      TMA producer, in the MMA's order: per block the mode-1
-//               k-blocks (A: factor block, 128 rows; B: the 2 h2 rows of the
-//               slab, hi and lo) and the mode-2 k-blocks (B: factor block of
-//               axis 2) of both chunks,
-//   warp 1      MMA issuer: the mode-1 tile into a 2 h2-column accumulator,
-//               then the two mode-2 chunks (A from the Y slots) into the
-//               128-column accumulators of their targets,
+// which the mode-3 stage reads MN-major (TcGroup::a_mn).  Per unit six chunks
+// (component q, input half hh of axis 2), each a mode-1 tile (128 x h2) and
+// its mode-2 product, in an order that completes one target before the next:
+//     c     0  1  2  3  4  5
+//     q     0  1  0  1  2  2
+//     hh    0  1  1  0  0  1
+//   target U0 U0 U1 U1 V0 V1  (U_k = Y_1 x2 E + Y_2 x2 F, V_k = Y_3 x2 E; the
+// index is the output half h2o = hh for E, hh ^ 1 for F).  Roles (10 warps):
+//   warp 0      TMA producer, in the MMA's order: per chunk the mode-1
+//               k-blocks (A: factor block, 128 rows; B: h2 rows of X) and the
+//               mode-2 k-blocks (B: factor block of axis 2),
+//   warp 1      MMA issuer: the mode-1 tile into the mode-1 accumulator, then
+//               its mode-2 product (A from the Y slots) into the target's,
 //   warps 2..5  mode-1 epilogue: accumulator -> hi / lo -> Y slots (a ring of
 //               k-blocks in shared memory, handed to the MMA by mbarriers),
 //   warps 6..9  mode-2 epilogue: accumulator -> hi / lo -> Z (TMA stores).
-// One mode-1 accumulator leaves no room to run ahead: the MMA waits for the
-// mode-1 epilogue's first Y k-block after each mode-1 tile (the mode-2 chunks
-// of a block follow its own mode-1 tile, so the Y ring never waits for a
-// tile that needs the accumulator back).  tcgen05.commit is issued once per
-// mode-1 k-block and once per two mode-2 k-blocks: a commit between short
-// MMA runs costs throughput (128 x 128 tiles: ~96 against ~76 cycles per MMA
-// with one commit per six MMAs).  Every wait is bounded as in
-// tc_gemm_kernel, with the same abort path.
+// Within a CTA these hand-offs serialise (a mode-1 tile, its conversion, the
+// mode-2 product, the next tile), so a CTA takes half of an SM: 256 TMEM
+// columns (one 128-column accumulator per mode) and ~106 KB of shared memory,
+// and two CTAs share each SM's tensor core, one filling the other's gaps.
+// The roles that issue copies and MMAs run their loops on the whole warp and
+// issue from lane 0 (single-lane loops issued the MMAs measurably slower).
+// Every wait is bounded as in tc_gemm_kernel, with the same abort path.
 constexpr int kS12Threads = 320;
-// Operand ring of 16 KB slots, each one k-block (64-byte rows) of one operand
-// plane pair: a mode-1 k-block takes three (A hi + lo of 128 rows, B hi and B
-// lo of up to 256 rows), a mode-2 k-block one (B hi + lo of up to 128 rows).
-constexpr int kS12Ring = 9;
+constexpr int kS12Ring = 4;                       // operand slots, one k-block of one operand (hi + lo)
 constexpr int kS12RingSlot = 2 * kTileA;
-constexpr int kS12Y = 4;                          // Y slots, one k-block of Y each (hi and lo)
+constexpr int kS12Y = 2;                          // Y slots, one k-block of Y each (hi and lo)
 constexpr int kS12YSlot = 2 * kTileA;
-constexpr int kS12OutBufs = 1;                    // staging buffers per mode-2 epilogue warp
-constexpr int kS12Staging = 4 * kS12OutBufs * kOutBuf;
+constexpr int kS12Plane = 32 * 32 * 2;            // one 32 x 32 BF16 plane: the staging of a mode-2 epilogue warp
+constexpr int kS12Staging = 4 * kS12Plane;
 constexpr int kS12Smem = 1024 + kS12Ring * kS12RingSlot + kS12Y * kS12YSlot + kS12Staging + kBarBytes;
-static_assert(kS12Smem <= kSmemMax, "fused kernel shared memory");
+constexpr int kS12Tmem = 256;                     // columns: mode-1 accumulator at 0, mode-2 at 128
+static_assert(2 * (kS12Smem + 1024) <= 228 * 1024, "two fused CTAs per SM");
 
 struct S12Launch {
   CUtensorMap t1_hi, t1_lo;            // axis-1 factor blocks, 128-row boxes (mode-1 A)
-  CUtensorMap x_hi, x_lo;              // split input, 2 h2-row boxes (mode-1 B)
+  CUtensorMap x_hi, x_lo;              // split input, h2-row boxes (mode-1 B)
   CUtensorMap t2_hi, t2_lo;            // axis-2 factor blocks, h2-row boxes (mode-2 B)
   CUtensorMap z_hi, z_lo;              // Z [2M ext3][ext2][ext1], 32 x 32 store boxes
   int M, x2, x3;                       // nodes, extents of axes 2 (= 2 h2) and 3
@@ -763,6 +756,11 @@ struct S12Launch {
   unsigned long long wait_ns;
 };
 
+__device__ __forceinline__ void s12_chunk(int c, int& q, int& hh) {
+  q = c < 4 ? (c & 1) : 2;
+  hh = c < 4 ? (((c >> 1) ^ c) & 1) : (c & 1);
+}
+
 // hi / lo BF16 of two consecutive values, packed (the first in the low half)
 __device__ __forceinline__ void split_pair(float a, float b, uint32_t& hi, uint32_t& lo) {
   const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
@@ -772,7 +770,7 @@ __device__ __forceinline__ void split_pair(float a, float b, uint32_t& hi, uint3
   lo = *reinterpret_cast<const uint32_t*>(&l);
 }
 
-__global__ void __launch_bounds__(kS12Threads, 1) tc_s12_kernel(const __grid_constant__ S12Launch L) {
+__global__ void __launch_bounds__(kS12Threads, 2) tc_s12_kernel(const __grid_constant__ S12Launch L) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* slots = base;
@@ -780,13 +778,13 @@ __global__ void __launch_bounds__(kS12Threads, 1) tc_s12_kernel(const __grid_con
   uint8_t* ostage = yslots + kS12Y * kS12YSlot;
   uint64_t* full = reinterpret_cast<uint64_t*>(ostage + kS12Staging);
   uint64_t* empty = full + kS12Ring;
-  uint64_t* d1full = empty + kS12Ring;     // [1] the mode-1 accumulator
+  uint64_t* d1full = empty + kS12Ring;     // the mode-1 accumulator
   uint64_t* d1empty = d1full + 1;
   uint64_t* yfull = d1empty + 1;           // [kS12Y]
   uint64_t* yempty = yfull + kS12Y;
-  uint64_t* d2full = yempty + kS12Y;       // [2] the mode-2 accumulators A, B
-  uint64_t* d2empty = d2full + 2;
-  uint64_t* sfull = d2empty + 2;           // [kRing] unit ids
+  uint64_t* d2full = yempty + kS12Y;       // the mode-2 accumulator
+  uint64_t* d2empty = d2full + 1;
+  uint64_t* sfull = d2empty + 1;           // [kRing] unit ids
   uint64_t* sempty = sfull + kRing;
   uint64_t* drain = sempty + kRing;
   volatile int* ring = reinterpret_cast<volatile int*>(drain + 1);
@@ -805,10 +803,8 @@ __global__ void __launch_bounds__(kS12Threads, 1) tc_s12_kernel(const __grid_con
     }
     ptx::mbar_init(d1full, 1);
     ptx::mbar_init(d1empty, 4);
-    for (int b = 0; b < 2; ++b) {
-      ptx::mbar_init(&d2full[b], 1);
-      ptx::mbar_init(&d2empty[b], 4);
-    }
+    ptx::mbar_init(d2full, 1);
+    ptx::mbar_init(d2empty, 4);
     for (int i = 0; i < kRing; ++i) {
       ptx::mbar_init(&sfull[i], 1);
       ptx::mbar_init(&sempty[i], 9);
@@ -818,7 +814,7 @@ __global__ void __launch_bounds__(kS12Threads, 1) tc_s12_kernel(const __grid_con
     ptx::fence_mbar_init();
   }
   if (warp == 1) {
-    ptx::tmem_alloc(tmem_slot, 512);
+    ptx::tmem_alloc(tmem_slot, kS12Tmem);
     ptx::tmem_relinquish();
   }
   ptx::tc_fence_before();
@@ -829,222 +825,213 @@ __global__ void __launch_bounds__(kS12Threads, 1) tc_s12_kernel(const __grid_con
   uint32_t armed = 0, armed_par = 0;
 
   if (warp == 0) {
-    {
-      // the whole warp runs the loop; lane 0 issues the copies
-      const bool leader = lane == 0;
-      int s = 0;
-      uint32_t ph = 0;
-      int rs = 0;
-      uint32_t rph = 0;
-      bool ok = true;
-      // next operand slot (its previous contents consumed), or null after an abort
-      auto take_slot = [&]() -> uint8_t* {
-        if (!ptx::mbar_wait_warp(&empty[s], ph ^ 1, abort, L.wait_ns)) {
-          if (leader) tc_fail(abort, L.status);
-          ok = false;
-          return nullptr;
-        }
-        armed |= 1u << s;
-        armed_par = (armed_par & ~(1u << s)) | (ph << s);
-        return slots + s * kS12RingSlot;
-      };
-      auto next_slot = [&]() {
-        if (++s == kS12Ring) {
-          s = 0;
-          ph ^= 1;
-        }
-      };
-      while (ok && !*abort) {
-        if (!ptx::mbar_wait_warp(&sempty[rs], rph ^ 1, abort, L.wait_ns)) {
-          if (leader) tc_fail(abort, L.status);
-          break;
-        }
-        int u = 0;
-        if (leader) {
-          u = atomicAdd(L.unit_counter, 1);
-          ring[rs] = u < L.units ? u : -1;
-          ptx::mbar_arrive(&sfull[rs]);
-        }
-        u = __shfl_sync(0xffffffffu, u, 0);
-        if (++rs == kRing) { rs = 0; rph ^= 1; }
-        if (u >= L.units) break;
-        const int h1o = u & 1, k = (u >> 1) % L.M, i3 = (u >> 1) / L.M;
-        for (int q = 0; q < 3 && ok; ++q) {
-          // mode 1: factor block of (k, type) and the slab's rows of X_q
-          const int type1 = q == 0 ? 1 : 0;             // F along axis 1 for component 1
-          const int off1 = ((h1o ^ type1) & 1) * L.h1;   // input half of axis 1
-          for (int kb = 0; kb < L.kb1 && ok; ++kb) {
-            uint8_t* a = take_slot();
-            if (!a) break;
-            if (leader) {
-              ptx::mbar_arrive_expect_tx(&full[s], 2 * kTileA);
-              ptx::tma_load_4d(a, &L.t1_hi, &full[s], kb * 32, 0, h1o, 2 * k + type1);
-              ptx::tma_load_4d(a + kTileA, &L.t1_lo, &full[s], kb * 32, 0, h1o, 2 * k + type1);
-            }
-            next_slot();
-            for (int pl = 0; pl < 2 && ok; ++pl) {
-              uint8_t* b = take_slot();
-              if (!b) break;
-              if (leader) {
-                ptx::mbar_arrive_expect_tx(&full[s], L.x2 * kRowBytes);
-                ptx::tma_load_3d(b, pl ? &L.x_lo : &L.x_hi, &full[s], off1 + kb * 32, i3 * L.x2, q);
-              }
-              next_slot();
-            }
+    // the whole warp runs the loop; lane 0 issues the copies
+    const bool leader = lane == 0;
+    int s = 0;
+    uint32_t ph = 0;
+    int rs = 0;
+    uint32_t rph = 0;
+    bool ok = true;
+    // next operand slot (its previous contents consumed), or null after an abort
+    auto take_slot = [&]() -> uint8_t* {
+      if (!ptx::mbar_wait_warp(&empty[s], ph ^ 1, abort, L.wait_ns)) {
+        if (leader) tc_fail(abort, L.status);
+        ok = false;
+        return nullptr;
+      }
+      armed |= 1u << s;
+      armed_par = (armed_par & ~(1u << s)) | (ph << s);
+      return slots + s * kS12RingSlot;
+    };
+    auto next_slot = [&]() {
+      if (++s == kS12Ring) {
+        s = 0;
+        ph ^= 1;
+      }
+    };
+    while (ok && !*abort) {
+      if (!ptx::mbar_wait_warp(&sempty[rs], rph ^ 1, abort, L.wait_ns)) {
+        if (leader) tc_fail(abort, L.status);
+        break;
+      }
+      int u = 0;
+      if (leader) {
+        u = atomicAdd(L.unit_counter, 1);
+        ring[rs] = u < L.units ? u : -1;
+        ptx::mbar_arrive(&sfull[rs]);
+      }
+      u = __shfl_sync(0xffffffffu, u, 0);
+      if (++rs == kRing) { rs = 0; rph ^= 1; }
+      if (u >= L.units) break;
+      const int h1o = u & 1, k = (u >> 1) % L.M, i3 = (u >> 1) / L.M;
+      for (int c = 0; c < 6 && ok; ++c) {
+        int q, hh;
+        s12_chunk(c, q, hh);
+        // mode 1: factor block of (k, type) and h2 rows of X_q (input half hh of axis 2)
+        const int type1 = q == 0 ? 1 : 0;             // F along axis 1 for component 1
+        const int off1 = ((h1o ^ type1) & 1) * L.h1;   // input half of axis 1
+        const int row = i3 * L.x2 + hh * L.h2;
+        for (int kb = 0; kb < L.kb1 && ok; ++kb) {
+          uint8_t* a = take_slot();
+          if (!a) break;
+          if (leader) {
+            ptx::mbar_arrive_expect_tx(&full[s], 2 * kTileA);
+            ptx::tma_load_4d(a, &L.t1_hi, &full[s], kb * 32, 0, h1o, 2 * k + type1);
+            ptx::tma_load_4d(a + kTileA, &L.t1_lo, &full[s], kb * 32, 0, h1o, 2 * k + type1);
           }
-          // mode 2, chunks hh = 0, 1: factor block of (k, type, h2o)
-          const int type2 = q == 1 ? 1 : 0;             // F along axis 2 for component 2
-          for (int hh = 0; hh < 2 && ok; ++hh)
-            for (int kb = 0; kb < L.kb2 && ok; ++kb) {
-              uint8_t* b = take_slot();
-              if (!b) break;
-              if (leader) {
-                ptx::mbar_arrive_expect_tx(&full[s], 2 * L.h2 * kRowBytes);
-                ptx::tma_load_4d(b, &L.t2_hi, &full[s], kb * 32, 0, hh ^ type2, 2 * k + type2);
-                ptx::tma_load_4d(b + kTileA, &L.t2_lo, &full[s], kb * 32, 0, hh ^ type2, 2 * k + type2);
-              }
-              next_slot();
-            }
+          next_slot();
+          uint8_t* b = take_slot();
+          if (!b) break;
+          if (leader) {
+            ptx::mbar_arrive_expect_tx(&full[s], 2 * L.h2 * kRowBytes);
+            ptx::tma_load_3d(b, &L.x_hi, &full[s], off1 + kb * 32, row, q);
+            ptx::tma_load_3d(b + kTileA, &L.x_lo, &full[s], off1 + kb * 32, row, q);
+          }
+          next_slot();
+        }
+        // mode 2: factor block of (k, type, h2o)
+        const int type2 = q == 1 ? 1 : 0;             // F along axis 2 for component 2
+        for (int kb = 0; kb < L.kb2 && ok; ++kb) {
+          uint8_t* b = take_slot();
+          if (!b) break;
+          if (leader) {
+            ptx::mbar_arrive_expect_tx(&full[s], 2 * L.h2 * kRowBytes);
+            ptx::tma_load_4d(b, &L.t2_hi, &full[s], kb * 32, 0, hh ^ type2, 2 * k + type2);
+            ptx::tma_load_4d(b + kTileA, &L.t2_lo, &full[s], kb * 32, 0, hh ^ type2, 2 * k + type2);
+          }
+          next_slot();
         }
       }
     }
   } else if (warp == 1) {
-    {
-      // the whole warp runs the loop; lane 0 issues the MMAs and commits
-      const bool leader = lane == 0;
-      int s = 0;
-      uint32_t ph = 0;
-      int rs = 0;
-      uint32_t rph = 0;
-      uint32_t p = 0, yc = 0;   // mode-1 tiles, Y k-blocks consumed
-      uint32_t n2[2] = {0, 0};  // targets completed per mode-2 accumulator
-      bool ok = true;
-      const uint32_t idesc1 = ptx::instr_desc(1, kBM, (uint32_t)L.x2);
-      const uint32_t idesc2 = ptx::instr_desc(1, kBM, (uint32_t)L.h2);
-      // the next operand slot once its loads have landed (index in `idx`)
-      auto take_full = [&](int& idx) -> uint32_t {
-        if (!ptx::mbar_wait_warp(&full[s], ph, abort, L.wait_ns)) {
+    // the whole warp runs the loop; lane 0 issues the MMAs and commits
+    const bool leader = lane == 0;
+    int s = 0;
+    uint32_t ph = 0;
+    int rs = 0;
+    uint32_t rph = 0;
+    uint32_t t = 0, yc = 0, g = 0;  // mode-1 tiles, Y k-blocks consumed, mode-2 targets completed
+    bool ok = true;
+    const uint32_t idesc = ptx::instr_desc(1, kBM, (uint32_t)L.h2);
+    const uint32_t d1 = tmem_base, d2 = tmem_base + 128;
+    // the next operand slot once its loads have landed (index in `idx`)
+    auto take_full = [&](int& idx) -> uint32_t {
+      if (!ptx::mbar_wait_warp(&full[s], ph, abort, L.wait_ns)) {
+        if (leader) tc_fail(abort, L.status);
+        ok = false;
+        return 0;
+      }
+      ptx::tc_fence_after();
+      idx = s;
+      const uint32_t a = ptx::smem_u32(slots + s * kS12RingSlot);
+      if (++s == kS12Ring) {
+        s = 0;
+        ph ^= 1;
+      }
+      return a;
+    };
+    while (ok && !*abort) {
+      if (!ptx::mbar_wait_warp(&sfull[rs], rph, abort, L.wait_ns)) {
+        if (leader) tc_fail(abort, L.status);
+        break;
+      }
+      const int u = ring[rs];
+      __syncwarp();
+      if (leader) ptx::mbar_arrive(&sempty[rs]);
+      if (++rs == kRing) { rs = 0; rph ^= 1; }
+      if (u < 0) break;
+      for (int c = 0; c < 6 && ok; ++c) {
+        // mode 1 into the mode-1 accumulator, once the previous tile is read out
+        if (!ptx::mbar_wait_warp(d1empty, (t & 1) ^ 1, abort, L.wait_ns)) {
           if (leader) tc_fail(abort, L.status);
           ok = false;
-          return 0;
-        }
-        ptx::tc_fence_after();
-        idx = s;
-        const uint32_t a = ptx::smem_u32(slots + s * kS12RingSlot);
-        if (++s == kS12Ring) {
-          s = 0;
-          ph ^= 1;
-        }
-        return a;
-      };
-      while (ok && !*abort) {
-        if (!ptx::mbar_wait_warp(&sfull[rs], rph, abort, L.wait_ns)) {
-          if (leader) tc_fail(abort, L.status);
           break;
         }
-        const int u = ring[rs];
-        __syncwarp();
-        if (leader) ptx::mbar_arrive(&sempty[rs]);
-        if (++rs == kRing) { rs = 0; rph ^= 1; }
-        if (u < 0) break;
-        for (int q = 0; q < 3 && ok; ++q) {
-          // mode 1 into the 2 h2-column accumulator
-          if (!ptx::mbar_wait_warp(d1empty, (p & 1) ^ 1, abort, L.wait_ns)) {
+        ptx::tc_fence_after();
+        for (int kb = 0; kb < L.kb1 && ok; ++kb) {
+          int ia = 0, ib = 0;
+          const uint32_t sa = take_full(ia);
+          const uint32_t sb = ok ? take_full(ib) : 0;
+          if (!ok) break;
+#pragma unroll
+          for (int kk = 0; kk < 2; ++kk) {
+            const uint32_t off = kk * 32;
+            const uint64_t ah = ptx::smem_desc(sa + off, kSBO, kSwizzle64);
+            const uint64_t al = ptx::smem_desc(sa + kTileA + off, kSBO, kSwizzle64);
+            const uint64_t bh = ptx::smem_desc(sb + off, kSBO, kSwizzle64);
+            const uint64_t bl = ptx::smem_desc(sb + kTileA + off, kSBO, kSwizzle64);
+            if (leader) {
+              Bf16Form::mma(d1, ah, bh, idesc, (kb | kk) ? 1u : 0u);
+              Bf16Form::mma(d1, ah, bl, idesc, 1u);
+              Bf16Form::mma(d1, al, bh, idesc, 1u);
+            }
+          }
+          issued_mma = true;
+          if (leader) {
+            ptx::mma_commit(&empty[ia]);
+            ptx::mma_commit(&empty[ib]);
+          }
+        }
+        if (!ok) break;
+        if (leader) ptx::mma_commit(d1full);
+        ++t;
+        // mode 2 into the target's accumulator
+        const bool first = c < 4 ? (c & 1) == 0 : true;
+        const bool last = c < 4 ? (c & 1) == 1 : true;
+        if (first) {
+          if (!ptx::mbar_wait_warp(d2empty, (g & 1) ^ 1, abort, L.wait_ns)) {
             if (leader) tc_fail(abort, L.status);
             ok = false;
             break;
           }
           ptx::tc_fence_after();
-          for (int kb = 0; kb < L.kb1 && ok; ++kb) {
-            int ia = 0, ib = 0, ic = 0;
-            const uint32_t sa = take_full(ia);
-            const uint32_t sb = ok ? take_full(ib) : 0;
-            const uint32_t sc = ok ? take_full(ic) : 0;
-            if (!ok) break;
-#pragma unroll
-            for (int kk = 0; kk < 2; ++kk) {
-              const uint32_t off = kk * 32;
-              const uint64_t ah = ptx::smem_desc(sa + off, kSBO, kSwizzle64);
-              const uint64_t al = ptx::smem_desc(sa + kTileA + off, kSBO, kSwizzle64);
-              const uint64_t bh = ptx::smem_desc(sb + off, kSBO, kSwizzle64);
-              const uint64_t bl = ptx::smem_desc(sc + off, kSBO, kSwizzle64);
-              if (leader) {
-                Bf16Form::mma(tmem_base, ah, bh, idesc1, (kb | kk) ? 1u : 0u);
-                Bf16Form::mma(tmem_base, ah, bl, idesc1, 1u);
-                Bf16Form::mma(tmem_base, al, bh, idesc1, 1u);
-              }
-            }
-            issued_mma = true;
-            if (leader) {
-              ptx::mma_commit(&empty[ia]);
-              ptx::mma_commit(&empty[ib]);
-              ptx::mma_commit(&empty[ic]);
-            }
+        }
+        int held_b = -1, held_y = -1;  // slots of the previous k-block, released with this one's
+        for (int kb = 0; kb < L.kb2 && ok; ++kb) {
+          const uint32_t ys = yc % kS12Y;
+          if (!ptx::mbar_wait_warp(&yfull[ys], (yc / kS12Y) & 1, abort, L.wait_ns)) {
+            if (leader) tc_fail(abort, L.status);
+            ok = false;
+            break;
           }
+          int ib = 0;
+          const uint32_t sb = take_full(ib);
           if (!ok) break;
-          if (leader) ptx::mma_commit(d1full);
-          ++p;
-          // its two mode-2 chunks
-          for (int hh = 0; hh < 2 && ok; ++hh) {
-            const int x = q == 0 ? hh : (hh ^ 1);       // accumulator of the target
-            const bool first = q != 1, last = q != 0;
-            if (first) {
-              if (!ptx::mbar_wait_warp(&d2empty[x], (n2[x] & 1) ^ 1, abort, L.wait_ns)) {
-                if (leader) tc_fail(abort, L.status);
-                ok = false;
-                break;
-              }
-              ptx::tc_fence_after();
-            }
-            const uint32_t d = tmem_base + 256 + (uint32_t)x * 128;
-            int held_b = -1, held_y = -1;  // slots of the previous k-block, released with this one's
-            for (int kb = 0; kb < L.kb2 && ok; ++kb) {
-              const uint32_t ys = yc % kS12Y;
-              if (!ptx::mbar_wait_warp(&yfull[ys], (yc / kS12Y) & 1, abort, L.wait_ns)) {
-                if (leader) tc_fail(abort, L.status);
-                ok = false;
-                break;
-              }
-              int ib = 0;
-              const uint32_t sb = take_full(ib);
-              if (!ok) break;
-              const uint32_t ya = ptx::smem_u32(yslots + ys * kS12YSlot);
+          const uint32_t ya = ptx::smem_u32(yslots + ys * kS12YSlot);
 #pragma unroll
-              for (int kk = 0; kk < 2; ++kk) {
-                const uint32_t off = kk * 32;
-                const uint64_t ah = ptx::smem_desc(ya + off, kSBO, kSwizzle64);
-                const uint64_t al = ptx::smem_desc(ya + kTileA + off, kSBO, kSwizzle64);
-                const uint64_t bh = ptx::smem_desc(sb + off, kSBO, kSwizzle64);
-                const uint64_t bl = ptx::smem_desc(sb + kTileA + off, kSBO, kSwizzle64);
-                if (leader) {
-                  Bf16Form::mma(d, ah, bh, idesc2, (first && kb == 0 && kk == 0) ? 0u : 1u);
-                  Bf16Form::mma(d, ah, bl, idesc2, 1u);
-                  Bf16Form::mma(d, al, bh, idesc2, 1u);
-                }
-              }
-              issued_mma = true;
-              ++yc;
-              if (held_b < 0 && kb + 1 < L.kb2) {  // release with the next k-block's
-                held_b = ib;
-                held_y = (int)ys;
-                continue;
-              }
-              if (leader) {
-                if (held_b >= 0) {
-                  ptx::mma_commit(&empty[held_b]);
-                  ptx::mma_commit(&yempty[held_y]);
-                }
-                ptx::mma_commit(&empty[ib]);
-                ptx::mma_commit(&yempty[ys]);
-              }
-              held_b = -1;
-            }
-            if (!ok) break;
-            if (last) {
-              if (leader) ptx::mma_commit(&d2full[x]);
-              ++n2[x];
+          for (int kk = 0; kk < 2; ++kk) {
+            const uint32_t off = kk * 32;
+            const uint64_t ah = ptx::smem_desc(ya + off, kSBO, kSwizzle64);
+            const uint64_t al = ptx::smem_desc(ya + kTileA + off, kSBO, kSwizzle64);
+            const uint64_t bh = ptx::smem_desc(sb + off, kSBO, kSwizzle64);
+            const uint64_t bl = ptx::smem_desc(sb + kTileA + off, kSBO, kSwizzle64);
+            if (leader) {
+              Bf16Form::mma(d2, ah, bh, idesc, (first && kb == 0 && kk == 0) ? 0u : 1u);
+              Bf16Form::mma(d2, ah, bl, idesc, 1u);
+              Bf16Form::mma(d2, al, bh, idesc, 1u);
             }
           }
+          issued_mma = true;
+          ++yc;
+          if (held_b < 0 && kb + 1 < L.kb2) {  // release with the next k-block's
+            held_b = ib;
+            held_y = (int)ys;
+            continue;
+          }
+          if (leader) {
+            if (held_b >= 0) {
+              ptx::mma_commit(&empty[held_b]);
+              ptx::mma_commit(&yempty[held_y]);
+            }
+            ptx::mma_commit(&empty[ib]);
+            ptx::mma_commit(&yempty[ys]);
+          }
+          held_b = -1;
+        }
+        if (!ok) break;
+        if (last) {
+          if (leader) ptx::mma_commit(d2full);
+          ++g;
         }
       }
     }
@@ -1056,10 +1043,9 @@ __global__ void __launch_bounds__(kS12Threads, 1) tc_s12_kernel(const __grid_con
     const int r = quad * 32 + lane;
     const uint32_t rowoff = (uint32_t)r * 64, sw = (uint32_t)(r >> 1) & 3u;
     const uint32_t taddr = tmem_base + ((uint32_t)(quad * 32) << 16);
-    const int nkb = 2 * L.kb2;  // k-blocks of Y per mode-1 tile (both halves of axis 2)
     int rs = 0;
     uint32_t rph = 0;
-    uint32_t p = 0, yc = 0;
+    uint32_t t = 0, yc = 0;
     bool ok = true;
     while (ok && !*abort) {
       if (!ptx::mbar_wait(&sfull[rs], rph, abort, L.wait_ns)) {
@@ -1071,14 +1057,14 @@ __global__ void __launch_bounds__(kS12Threads, 1) tc_s12_kernel(const __grid_con
       if (lane == 0) ptx::mbar_arrive(&sempty[rs]);
       if (++rs == kRing) { rs = 0; rph ^= 1; }
       if (u < 0) break;
-      for (int q = 0; q < 3 && ok; ++q) {
-        if (!ptx::mbar_wait(d1full, p & 1, abort, L.wait_ns)) {
+      for (int c = 0; c < 6 && ok; ++c) {
+        if (!ptx::mbar_wait(d1full, t & 1, abort, L.wait_ns)) {
           tc_fail(abort, L.status);
           ok = false;
           break;
         }
         ptx::tc_fence_after();
-        for (int kb = 0; kb < nkb; ++kb) {
+        for (int kb = 0; kb < L.kb2; ++kb) {
           uint32_t v[32];
           ptx::tmem_ld32(taddr + (uint32_t)(kb * 32), v);
           const uint32_t ys = yc % kS12Y;
@@ -1089,7 +1075,7 @@ __global__ void __launch_bounds__(kS12Threads, 1) tc_s12_kernel(const __grid_con
             break;
           }
           ptx::tmem_ld_wait(v);
-          if (kb + 1 == nkb) {  // the accumulator is read: the next mode-1 tile may start
+          if (kb + 1 == L.kb2) {  // the accumulator is read: the next mode-1 tile may start
             ptx::tc_fence_before();
             __syncwarp();
             if (lane == 0) ptx::mbar_arrive(d1empty);
@@ -1110,19 +1096,19 @@ __global__ void __launch_bounds__(kS12Threads, 1) tc_s12_kernel(const __grid_con
           if (lane == 0) ptx::mbar_arrive(&yfull[ys]);
           ++yc;
         }
-        ++p;
+        ++t;
       }
     }
   } else {
     // mode-2 epilogue: rows a1 of the unit's output half, columns a2; each
-    // 32 x 32 chunk staged as [a2][a1] and stored as one box per plane.
-    // Targets in the order they complete: U1, U0 (after q = 1), V0, V1.
+    // 32 x 32 chunk staged as [a2][a1], plane by plane, one box each.
+    // Targets in the order they complete: U0, U1, V0, V1.
     const int quad = warp & 3;
-    uint8_t* stg = ostage + (warp - 6) * (kS12OutBufs * kOutBuf);
+    uint8_t* stg = ostage + (warp - 6) * kS12Plane;
+    const uint32_t taddr = tmem_base + ((uint32_t)(quad * 32) << 16) + 128;
     int rs = 0;
     uint32_t rph = 0;
-    uint32_t n2[2] = {0, 0};
-    uint32_t chunk = 0;
+    uint32_t g = 0;
     bool ok = true;
     while (ok && !*abort) {
       if (!ptx::mbar_wait(&sfull[rs], rph, abort, L.wait_ns)) {
@@ -1137,49 +1123,44 @@ __global__ void __launch_bounds__(kS12Threads, 1) tc_s12_kernel(const __grid_con
       const int h1o = u & 1, k = (u >> 1) % L.M, i3 = (u >> 1) / L.M;
       const bool valid = quad * 32 < L.h1;  // rows past h1 are zero and not stored
       for (int j = 0; j < 4 && ok; ++j) {
-        const int x = (j & 1) ^ 1;                // U1: B, U0: A, V0: B, V1: A
-        const int h2o = j == 0 || j == 3 ? 1 : 0;
-        const int field = 2 * k + (j >> 1);
-        if (!ptx::mbar_wait(&d2full[x], n2[x] & 1, abort, L.wait_ns)) {
+        if (!ptx::mbar_wait(d2full, g & 1, abort, L.wait_ns)) {
           tc_fail(abort, L.status);
           ok = false;
           break;
         }
         ptx::tc_fence_after();
-        const uint32_t taddr = tmem_base + ((uint32_t)(quad * 32) << 16) + 256 + (uint32_t)x * 128;
-        const int zf = i3 + L.x3 * field;
+        const int zf = i3 + L.x3 * (2 * k + (j >> 1));
         const int a1 = h1o * L.h1 + quad * 32;
-        const int a2 = h2o * L.h2;
+        const int a2 = (j & 1) * L.h2;
         for (int c0 = 0; c0 < L.h2; c0 += 32) {
           uint32_t v[32];
           ptx::tmem_ld32(taddr + (uint32_t)c0, v);
           ptx::tmem_ld_wait(v);
           if (!valid) continue;
-          uint8_t* sb = stg + (chunk % kS12OutBufs) * kOutBuf;
-          ++chunk;
-          if (lane == 0) ptx::bulk_wait_read<kS12OutBufs - 1>();
-          __syncwarp();
-          __nv_bfloat16* sh = reinterpret_cast<__nv_bfloat16*>(sb);
-          __nv_bfloat16* sl = sh + 32 * 32;
+          __nv_bfloat16* sp = reinterpret_cast<__nv_bfloat16*>(stg);
 #pragma unroll
-          for (int jj = 0; jj < 32; ++jj) {
-            __nv_bfloat16 hi, lo;
-            Bf16Form::split(__uint_as_float(v[jj]), hi, lo);
-            sh[jj * 32 + lane] = hi;
-            sl[jj * 32 + lane] = lo;
-          }
-          ptx::fence_proxy_async_smem();
-          __syncwarp();
-          if (lane == 0) {
-            ptx::tma_store_3d(&L.z_hi, sb, a1, a2 + c0, zf);
-            ptx::tma_store_3d(&L.z_lo, sb + 32 * 32 * 2, a1, a2 + c0, zf);
-            ptx::bulk_commit();
+          for (int pl = 0; pl < 2; ++pl) {
+            // the previous store has read the buffer
+            if (lane == 0) ptx::bulk_wait_read<0>();
+            __syncwarp();
+#pragma unroll
+            for (int jj = 0; jj < 32; ++jj) {
+              __nv_bfloat16 hi, lo;
+              Bf16Form::split(__uint_as_float(v[jj]), hi, lo);
+              sp[jj * 32 + lane] = pl ? lo : hi;
+            }
+            ptx::fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) {
+              ptx::tma_store_3d(pl ? &L.z_lo : &L.z_hi, stg, a1, a2 + c0, zf);
+              ptx::bulk_commit();
+            }
           }
         }
         ptx::tc_fence_before();
         __syncwarp();
-        if (lane == 0) ptx::mbar_arrive(&d2empty[x]);
-        ++n2[x];
+        if (lane == 0) ptx::mbar_arrive(d2empty);
+        ++g;
       }
     }
     if (lane == 0) ptx::bulk_wait_all();
@@ -1200,7 +1181,7 @@ __global__ void __launch_bounds__(kS12Threads, 1) tc_s12_kernel(const __grid_con
         if (armed & (1u << st)) ptx::mbar_wait(&full[st], (armed_par >> st) & 1u, &no_abort, kDrainNs);
     __syncthreads();
   }
-  if (warp == 1) ptx::tmem_dealloc(tmem_base, 512);
+  if (warp == 1) ptx::tmem_dealloc(tmem_base, kS12Tmem);
 }
 
 // ---------------------------------------------------------------- operand preparation
@@ -2446,7 +2427,7 @@ demag_status tc_prepare(demag_plan* P, demag_precision prec, cudaStream_t st) {
       for (int h = 0; h < 2 && ok; ++h) {
         void* zb = S->buf1[h];  // Z [2M][ext3][ext2][ext1] in the stage-1 workspace
         ok = ok && make_bmap(h ? &Z.t1_lo : &Z.t1_hi, S->B[0][h], 2, h1, 2, 2 * M, S->ldB[0], kBM);
-        ok = ok && make_map(h ? &Z.x_lo : &Z.x_hi, S->X[h], 2, x1, (uint64_t)(x3 * x2), 3, S->ld[0], (uint32_t)x2);
+        ok = ok && make_map(h ? &Z.x_lo : &Z.x_hi, S->X[h], 2, x1, (uint64_t)(x3 * x2), 3, S->ld[0], h2);
         ok = ok && make_bmap(h ? &Z.t2_lo : &Z.t2_hi, S->B[1][h], 2, h2, 2, 2 * M, S->ldB[1], h2);
         ok = ok && make_map3(h ? &Z.z_lo : &Z.z_hi, zb, x1, x2, (uint64_t)x3 * 2 * M, x1, x2 * x1, 32, 32,
                              CU_TENSOR_MAP_SWIZZLE_NONE);
@@ -2662,7 +2643,7 @@ static demag_status run_s12(demag_plan* P, TcState* S, cudaStream_t st) {
   int sms = 0, dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int grid = L.units < sms ? L.units : sms;
+  const int grid = L.units < 2 * sms ? L.units : 2 * sms;  // two CTAs per SM
   DEMAG_CUDA(P, cudaMemsetAsync(S->counter, 0, sizeof(int), st));
   DEMAG_LAUNCH(P, kFamGemmTc, st, tc_s12_kernel<<<grid, kS12Threads, kS12Smem, st>>>(L));
   DEMAG_LAUNCHED(P, "tc_s12_kernel");
