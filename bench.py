@@ -42,6 +42,10 @@ NCU_TRAFFIC = {
     # per cell of the grid (captured at 192^3, folded axes)
     "tc_gemm_kernel": {"sources": ("full_tc.cu", "tc_ptx.cuh"), "sha": "a6dadd13b4003ca1",
                        "bytes_per_cell": 5.7328e9 / 192 ** 3},
+    # the fused schedule: tc_s12_kernel and the mode-3 tc_gemm_kernel launch of
+    # one application, BF16x3, R = 41, per cell (captured at 192^3)
+    "tc_fused": {"sources": ("full_tc.cu", "tc_ptx.cuh"), "sha": "b09a90da9e222444",
+                 "bytes_per_cell": 2.36645e9 / 192 ** 3},
     # the Toeplitz FFT launch of a CP batch, n = 4096, r = 4, R = 61, per application
     "toeplitz_fft_kernel": {"sources": ("structured.cu", "fft.cuh"), "sha": "4fdeeea3a089464e",
                             "bytes_per_app": 549.835e6 / 32},
@@ -296,16 +300,20 @@ def run_ours(args, world, rank, local):
     achieved_tflops = flops_app / (gemm_ms_app * 1e-3) / 1e12
     hbm = peaks.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"])
     hbm_note = f"{peak_src} STREAM copy (HBM)"
+    # two tensor-core launches per application: the fused schedule (mode-1 and
+    # mode-2 products in tc_s12_kernel, mode 3 in tc_gemm_kernel); three: the chain
+    fused_sched = fam == "gemm_tc" and per_app == 2
     if fam == "gemm_tc":
         tpeak = peaks.get("bf16_tflops", PEAKS_FALLBACK["bf16_tflops"])
         if form == "tf32x3":
             tpeak = tpeak / 2.0  # TF32 dense rate is half the BF16 rate
         tpeak_note = f"{peak_src} dense {'bf16' if form == 'bf16x3' else 'tf32 (bf16/2)'} burst"
-        # algorithmic DRAM bytes of the three mode-product stages (folded
-        # layout, the axis extents padded to 2 hq): the split input (3 fields),
-        # the stage-1 intermediates (3M fields, written and read), the stage-2
-        # intermediates (2M fields, written and read), each as a hi and a lo
-        # plane, and the FP32 node-sum partial fields
+        # algorithmic DRAM bytes of the mode-product launches (folded layout,
+        # the axis extents padded to 2 hq): the split input (3 fields), the
+        # stage-1 intermediates (3M fields, written and read; not in the fused
+        # schedule, where they stay on chip), the stage-2 intermediates (2M
+        # fields, written and read), each as a hi and a lo plane, and the FP32
+        # node-sum partial fields
         pair = 4 if form == "bf16x3" else 8
         al = 8 if form == "bf16x3" else 4
         hq = -(-((N1 + 1) // 2) // al) * al
@@ -314,13 +322,17 @@ def run_ours(args, world, rank, local):
         kb3 = -(-((N1 + 1) // 2 if N1 > 16 else N1) // (32 if form == "bf16x3" else 16))
         pp3 = max(1, (400 if form == "bf16x3" else 200) // (kb3 * 6))
         groups = -(-2 * M // pp3)
-        gemm_bytes_app = pair * Nc * (3 + 10 * M) + 4.0 * groups * Nc
+        gemm_bytes_app = pair * Nc * (3 + (4 if fused_sched else 10) * M) + 4.0 * groups * Nc
         achieved_gbs = gemm_bytes_app / (gemm_ms_app * 1e-3) / 1e9
         # the folded chain contracts h = n/2 entries per output (half the dense
         # MACs); the split forms issue 3 tensor-core products per product
         issued_tflops = flops_app_8 / 2.0 * 3.0 / (gemm_ms_app * 1e-3) / 1e12
-        traffic = ncu_traffic("tc_gemm_kernel", N1 ** 3, "bytes_per_cell") if form == "bf16x3" else None
-        roofline = {"kernel": "tc_gemm_kernel (tcgen05 mode products), the three stage launches of one application",
+        traffic = (ncu_traffic("tc_fused" if fused_sched else "tc_gemm_kernel", N1 ** 3, "bytes_per_cell")
+                   if form == "bf16x3" else None)
+        kname = ("tc_s12_kernel (tcgen05 mode-1 and mode-2 products, fused) and tc_gemm_kernel (mode 3 with "
+                 "the node sum), the two launches of one application" if fused_sched else
+                 "tc_gemm_kernel (tcgen05 mode products), the three stage launches of one application")
+        roofline = {"kernel": kname, "schedule": "fused" if fused_sched else "chain",
                     "bound": "tensor", "achieved": achieved_tflops, "peak": tpeak, "unit": "TFLOP/s",
                     "frac": achieved_tflops / tpeak, "traffic": traffic,
                     "peak_source": tpeak_note,

@@ -468,7 +468,7 @@ demag_status demag_sync_status(demag_plan* plan, void* stream);
 demag_status demag_set_wait_limit(demag_plan* plan, double seconds);
 
 /* Schedule of the full-format forward application on tensor cores (BF16x3):
- * enable = 1 (the default) fuses the mode-1 and mode-2 products of Cor. 3
+ * enable = 1 fuses the mode-1 and mode-2 products of Cor. 3
  * into one kernel on grids whose three axes are folded (longer than 16 cells)
  * with ceil(n1 / 2) and ceil(n2 / 2) multiples of 32 up to 128 (n1, n2 of 64,
  * 128, 192 or 256, for example): per slab i3 the mode-1 results are split
@@ -477,7 +477,9 @@ demag_status demag_set_wait_limit(demag_plan* plan, double seconds);
  * layout.  enable = 0 runs the three-stage chain (each mode product's fields
  * in the workspace).  Both give the same values to rounding (the same
  * products, accumulated in another order); other grids and forms always run
- * the chain.  Build-only; no counterpart in the paper. */
+ * the chain.  Without this call the plan takes the autotuner's choice
+ * (demag_autotune, kind 9), else the fused schedule.  Build-only; no
+ * counterpart in the paper. */
 demag_status demag_set_fused(demag_plan* plan, int enable);
 
 /* ---- allocation-free full format (no counterpart in the paper) ---------- */
@@ -546,7 +548,9 @@ demag_status demag_profile_launch(demag_plan* plan, long long i, int* family, do
  *    fit, 4, 3, 2}, the tile order {every job of a row block in turn, every
  *    row block of a job in turn} and, where a 128-row block of the stage lies
  *    in one outer index, the store boxes {per epilogue warp, one 128-row box
- *    per chunk} (operands as they are, stage timed alone).
+ *    per chunk} (operands as they are, stage timed alone); then, where the
+ *    grid has the fused BF16x3 forward schedule (demag_set_fused), that
+ *    schedule's two launches against the three-stage chain.
  * No knob changes the arithmetic of an output element: tuned and untuned
  * results agree bit for bit.  The tuning launches write the call's own
  * outputs.  No tuning happens while the stream is being captured.
@@ -554,9 +558,10 @@ demag_status demag_profile_launch(demag_plan* plan, long long i, int* family, do
 demag_status demag_autotune(demag_plan* plan, int enable);
 /* Number of tuned shapes, and entry i of them: kind (0 FFT node group; tensor
  * cores, BF16x3 / TF32x3: 1 / 2 tile width, 3 / 4 operand stages (0 = as many
- * as fit), 5 / 6 tile order, 7 / 8 store boxes (1 = 128-row boxes)), key (FFT:
- * log2 of the complex FFT length, column
- * blocks, M; tensor core: stage program 0..5, default value, 0), the chosen
+ * as fit), 5 / 6 tile order, 7 / 8 store boxes (1 = 128-row boxes); 9 the
+ * BF16x3 forward schedule (1 fused, 0 chain)), key (FFT: log2 of the complex
+ * FFT length, column blocks, M; tensor core: stage program 0..6 (6: the
+ * mode-3 stage of the fused schedule), default value, 0; schedule: 0, 1, 0), the chosen
  * value, its time per launch and the default value's time per launch in ms
  * (0 for an entry read from a cache). */
 int demag_autotune_count(const demag_plan* plan);

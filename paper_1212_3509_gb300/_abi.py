@@ -592,7 +592,7 @@ def demag_autotune_count(plan: Plan) -> int:
 
 TUNE_KINDS = {0: "fft_node_group", 1: "bf16x3_tile_width", 2: "tf32x3_tile_width", 3: "bf16x3_stages",
               4: "tf32x3_stages", 5: "bf16x3_tile_order", 6: "tf32x3_tile_order", 7: "bf16x3_store_boxes",
-              8: "tf32x3_store_boxes"}
+              8: "tf32x3_store_boxes", 9: "bf16x3_schedule"}
 
 
 def demag_autotune_entry(plan: Plan, i: int) -> dict:

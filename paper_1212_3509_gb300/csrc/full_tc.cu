@@ -1782,6 +1782,7 @@ struct TcState {
   // grid allows it (BF16x3, every axis folded, h1 and h2 multiples of 32 up
   // to 128); the Z fields live in buf1
   bool fused;
+  int sched;              // forward schedule chosen by the tuner (1 fused, 0 chain; 1 untuned)
   S12Launch s12;
   // analytic stray field: the forward stage programs with the derivative
   // factors of their axis (built on first use)
@@ -2156,6 +2157,7 @@ static demag_status prepare_form(demag_plan* P, TcState* S, cudaStream_t st) {
 
 template <class F>
 static demag_status run_program(demag_plan* P, TcState* S, int prog, cudaStream_t st);
+static demag_status run_s12(demag_plan* P, TcState* S, cudaStream_t st);
 
 // Point stage program `prog` at output-column tile width bn (device copy included).
 static demag_status set_tile_width(demag_plan* P, TcState* S, int prog, int bn) {
@@ -2206,8 +2208,14 @@ static demag_status set_knob(demag_plan* P, TcState* S, int prog, int knob, int 
   return DEMAG_OK;
 }
 
+// Tuned entry kind of the forward schedule (BF16x3): 1 fused, 0 chain; key (0, 1, 0).
+constexpr int kTuneSchedule = 9;
+
 // Apply tuned entries already in the plan (a loaded cache) to its programs.
 static demag_status apply_tuned(demag_plan* P, TcState* S) {
+  if (S->fused)
+    for (const demag_plan::Tuned& t : P->tuned)
+      if (t.kind == kTuneSchedule && (t.value == 0 || t.value == 1)) S->sched = t.value;
   for (int prog = 0; prog < kPrograms; ++prog) {
     if (S->small[prog] || (prog == kFwd3Z && !S->fused)) continue;
     for (int knob = 0; knob < 4; ++knob) {
@@ -2236,6 +2244,29 @@ static demag_status tune_programs(demag_plan* P, TcState* S, cudaStream_t st) {
   DEMAG_CUDA(P, cudaEventCreate(&e0));
   DEMAG_CUDA(P, cudaEventCreate(&e1));
   demag_status s = DEMAG_OK;
+  // the stage launches of one forward application (operand split and node-sum
+  // reduction are the same for both schedules and not timed)
+  auto time_sched = [&](int fused, float* ms) -> demag_status {
+    auto once = [&]() -> demag_status {
+      if (fused) {
+        demag_status r = run_s12(P, S, st);
+        return r == DEMAG_OK ? run_program<F>(P, S, kFwd3Z, st) : r;
+      }
+      demag_status r = DEMAG_OK;
+      for (int prog = kFwd1; prog <= kFwd3 && r == DEMAG_OK; ++prog) r = run_program<F>(P, S, prog, st);
+      return r;
+    };
+    demag_status r = once();
+    if (r != DEMAG_OK) return r;
+    DEMAG_CUDA(P, cudaEventRecord(e0, st));
+    for (int i = 0; i < 3 && r == DEMAG_OK; ++i) r = once();
+    DEMAG_CUDA(P, cudaEventRecord(e1, st));
+    DEMAG_CUDA(P, cudaEventSynchronize(e1));
+    if (r != DEMAG_OK) return r;
+    cudaEventElapsedTime(ms, e0, e1);
+    *ms /= 3.f;
+    return DEMAG_OK;
+  };
   auto time_prog = [&](int prog, float* ms) -> demag_status {
     demag_status r = run_program<F>(P, S, prog, st);
     if (r != DEMAG_OK) return r;
@@ -2297,6 +2328,27 @@ static demag_status tune_programs(demag_plan* P, TcState* S, cudaStream_t st) {
         t.ms_default = at_def;
         P->tuned.push_back(t);
       }
+    }
+  }
+  // forward schedule, with every stage program tuned: fused kernel and
+  // mode-3 stage against the three-stage chain
+  bool have_sched = false;
+  for (const demag_plan::Tuned& t : P->tuned) have_sched = have_sched || t.kind == kTuneSchedule;
+  if (s == DEMAG_OK && S->fused && !have_sched) {
+    float mf = 0.f, mc = 0.f;
+    s = time_sched(1, &mf);
+    if (s == DEMAG_OK) s = time_sched(0, &mc);
+    if (s == DEMAG_OK) {
+      S->sched = mc < mf ? 0 : 1;
+      demag_plan::Tuned t;
+      t.kind = kTuneSchedule;
+      t.key[0] = 0;
+      t.key[1] = 1;
+      t.key[2] = 0;
+      t.value = S->sched;
+      t.ms = S->sched ? mf : mc;
+      t.ms_default = mf;
+      P->tuned.push_back(t);
     }
   }
   cudaEventDestroy(e0);
@@ -2422,6 +2474,7 @@ demag_status tc_prepare(demag_plan* P, demag_precision prec, cudaStream_t st) {
     const int h1 = geo.h[0], h2 = geo.h[1];
     S->fused = S->elem == 2 && !P->nonuniform && geo.hq[0] && geo.hq[1] && geo.hq[2] && h1 % 32 == 0 &&
                h2 % 32 == 0 && h1 <= 128 && h2 <= 128;
+    S->sched = 1;
     if (S->fused) {
       S12Launch& Z = S->s12;
       for (int h = 0; h < 2 && ok; ++h) {
@@ -2653,7 +2706,7 @@ static demag_status run_s12(demag_plan* P, TcState* S, cudaStream_t st) {
 template <class F>
 static demag_status forward_chain(demag_plan* P, TcState* S, const float* m, float* phi, cudaStream_t st) {
   demag_status s = split_input<F>(P, S, m, 3, st);
-  if (S->fused && P->fused) {
+  if (S->fused && (P->fused > 0 || (P->fused < 0 && S->sched))) {
     if (s == DEMAG_OK) s = run_s12(P, S, st);
     if (s == DEMAG_OK) s = run_program<F>(P, S, kFwd3Z, st);
   } else {

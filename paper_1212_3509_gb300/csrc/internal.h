@@ -85,14 +85,16 @@ struct demag_plan {
   // limit of the bounded device-side waits of the tensor-core kernels (ns)
   unsigned long long wait_ns = 2000000000ull;
   // full-format forward application on tensor cores: 1 fuses the mode-1 and
-  // mode-2 products where the grid allows it, 0 runs the three-stage chain
-  int fused = 1;
+  // mode-2 products where the grid allows it, 0 runs the three-stage chain,
+  // -1 (default) the tuned choice (fused when nothing was tuned)
+  int fused = -1;
 
   // autotuning: when on, launch shapes not yet tuned are timed on first use
   bool autotune = false;
   struct Tuned {
     int kind;      // 0 FFT nodes per block; tensor cores (BF16x3 / TF32x3): 1 / 2 N tile,
-                   // 3 / 4 operand stages, 5 / 6 tile order
+                   // 3 / 4 operand stages, 5 / 6 tile order, 7 / 8 store boxes;
+                   // 9 forward schedule (BF16x3: 1 fused, 0 chain)
     int key[3];    // FFT: log2 N, column blocks, M; tensor core: stage program, default value, 0
     int value;     // chosen setting
     float ms;      // its time per launch

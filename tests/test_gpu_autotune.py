@@ -163,6 +163,7 @@ def test_store_box_tuning_keeps_results(D):
     out = []
     for tune in (False, True):
         P = D.demag_build_factors(n, h, R)
+        D.demag_set_fused(P, True)  # the same forward schedule in both plans
         if tune:
             D.demag_autotune(P, True)
         phi = torch.empty(n[2], n[1], n[0], device="cuda")
@@ -179,3 +180,27 @@ def test_store_box_tuning_keeps_results(D):
     # programs 0-5 of the chains and 6, the mode-3 stage of the fused forward
     # application (128^3 has it: every axis folded, 64 entries per half)
     assert set(boxes) == set(range(7)) and all(e["value"] in (0, 1) for e in boxes.values())
+
+
+def test_forward_schedule_tuning(D):
+    """On a grid with the fused schedule the tuner times it against the three-stage
+    chain and keeps the faster; the tuned plan's output equals, bit for bit, that of
+    a plan forced to the chosen schedule."""
+    n, h, R = (128, 128, 64), (1 / 128,) * 3, 21
+    m = dev(synth.random_unit_m(n, 41))
+    P = D.demag_build_factors(n, h, R)
+    D.demag_autotune(P, True)
+    a = torch.empty(n[2], n[1], n[0], device="cuda")
+    D.demag_apply_full(P, m, a, "bf16x3")
+    torch.cuda.synchronize()
+    entries = [D.demag_autotune_entry(P, i) for i in range(D.demag_autotune_count(P))]
+    sched = [e for e in entries if e["kind"] == "bf16x3_schedule"]
+    assert len(sched) == 1 and sched[0]["value"] in (0, 1) and sched[0]["key"] == [0, 1, 0]
+    assert 0 < sched[0]["ms"] <= sched[0]["ms_default"]  # ms_default: the fused schedule's time
+    Q = D.demag_build_factors(n, h, R)
+    D.demag_set_fused(Q, bool(sched[0]["value"]))
+    b = torch.empty_like(a)
+    D.demag_apply_full(Q, m, b, "bf16x3")
+    torch.cuda.synchronize()
+    D.demag_sync_status(P)
+    assert torch.equal(a, b)
