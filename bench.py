@@ -40,8 +40,8 @@ PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustain
 NCU_TRAFFIC = {
     # the three tcgen05 mode-product stages of one application, BF16x3, R = 41,
     # per cell of the grid (captured at 192^3, folded axes)
-    "tc_gemm_kernel": {"sources": ("full_tc.cu", "tc_ptx.cuh"), "sha": "a6dadd13b4003ca1",
-                       "bytes_per_cell": 5.7328e9 / 192 ** 3},
+    "tc_gemm_kernel": {"sources": ("full_tc.cu", "tc_ptx.cuh"), "sha": "b09a90da9e222444",
+                       "bytes_per_cell": 5.7316e9 / 192 ** 3},
     # the fused schedule: tc_s12_kernel and the mode-3 tc_gemm_kernel launch of
     # one application, BF16x3, R = 41, per cell (captured at 192^3)
     "tc_fused": {"sources": ("full_tc.cu", "tc_ptx.cuh"), "sha": "b09a90da9e222444",
@@ -91,6 +91,9 @@ def parse():
                     help="skip the uniform-cube energy study (Tucker format, n = 64..4096)")
     ap.add_argument("--no-tune", dest="tune", action="store_false",
                     help="default launch shapes (no autotuning before the timed region; for profiler runs)")
+    ap.add_argument("--schedule", choices=("auto", "fused", "chain"), default="auto",
+                    help="full-format forward schedule on tensor cores: the tuned choice (auto), the fused "
+                         "mode-1/mode-2 kernel, or the three-stage chain")
     ap.add_argument("--cpu-table", action="store_true",
                     help="time the FP64 oracle on every configuration with 1 and with all host threads "
                          "(bounded samples) and print one JSON object; no GPU work")
@@ -252,6 +255,8 @@ def run_ours(args, world, rank, local):
     # (below, or on the first application), before the timed region
     if args.tune:
         D.demag_autotune(P, True)
+    if args.schedule != "auto":
+        D.demag_set_fused(P, args.schedule == "fused")
     if form == "auto":
         form = "fp32"
         for cand in ("bf16x3",):
