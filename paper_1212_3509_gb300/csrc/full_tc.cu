@@ -1253,6 +1253,53 @@ __global__ void __launch_bounds__(128) fold_split_kernel(const __grid_constant__
                    ? (((long long)q * g.ext[2] + b3 * g.hq[2] + j3) * g.ext[1] + b2 * g.hq[1] + j2) * S.ld1
                    : -1;
     }
+    if (F::kElem == 2 && f1 && (g.n[0] & 3) == 0 && (reinterpret_cast<uintptr_t>(S.x) & 7) == 0) {
+      // n1 a multiple of 4 (h1 even): two neighbouring orbits per thread, both
+      // valid or both padding, their cells and their mirror cells each an
+      // aligned float2, the outputs a BF16 pair
+      const int fl[3] = {f1, f2, f3};
+      for (int j1 = 2 * threadIdx.x; j1 < c1; j1 += 2 * blockDim.x) {
+        const bool l1 = j1 < g.h[0];
+        float v[2][8];
+#pragma unroll
+        for (int row = 0; row < 4; ++row) {
+          float2 a = make_float2(0.f, 0.f), b = make_float2(0.f, 0.f);
+          if (src[row] && l1) {
+            a = __ldg(reinterpret_cast<const float2*>(src[row] + j1));
+            b = __ldg(reinterpret_cast<const float2*>(src[row] + 2 * g.h[0] - 2 - j1));
+          }
+          v[0][2 * row] = a.x;      // orbit j1: cell j1, mirror 2h - 1 - j1
+          v[0][2 * row + 1] = b.y;
+          v[1][2 * row] = a.y;      // orbit j1 + 1
+          v[1][2 * row + 1] = b.x;
+        }
+#pragma unroll
+        for (int o = 0; o < 2; ++o)
+#pragma unroll
+          for (int p = 0; p < 3; ++p) {
+            if (!fl[p]) continue;
+            const int bit = 1 << p;
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+              if (!(k & bit)) {
+                const float a = v[o][k], b = v[o][k | bit];
+                v[o][k] = a + b;
+                v[o][k | bit] = a - b;
+              }
+          }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const int b1 = k & 1, row = k >> 1;
+          if (dst[row] < 0) continue;
+          const long long o = dst[row] + b1 * g.hq[0] + j1;
+          uint32_t hw, lw;
+          split_pair(v[0][k], v[1][k], hw, lw);
+          *reinterpret_cast<uint32_t*>(reinterpret_cast<T*>(S.hi) + o) = hw;
+          *reinterpret_cast<uint32_t*>(reinterpret_cast<T*>(S.lo) + o) = lw;
+        }
+      }
+      continue;
+    }
     for (int j1 = threadIdx.x; j1 < c1; j1 += blockDim.x) {
       const bool l1 = j1 < g.h[0];
       const int m1[2] = {j1, 2 * g.h[0] - 1 - j1};
@@ -1380,7 +1427,7 @@ struct Csum {
 // are issued together before they are summed.
 constexpr int kUnfoldBatch = 4;
 
-__global__ void __launch_bounds__(128) unfold_reduce_kernel(const __grid_constant__ UnfoldList L) {
+__global__ void __launch_bounds__(128, 6) unfold_reduce_kernel(const __grid_constant__ UnfoldList L) {
   int item = 0;
   for (long long r = blockIdx.x; r < L.total; r += gridDim.x) {
     while (item + 1 < L.count && r >= L.it[item + 1].begin) ++item;
@@ -1406,6 +1453,58 @@ __global__ void __launch_bounds__(128) unfold_reduce_kernel(const __grid_constan
       dst[k] = (on && m2 < g.n[1] && m3 < g.n[2])
                    ? R.out + (((long long)q * g.n[2] + m3) * g.n[1] + m2) * g.n[0]
                    : nullptr;
+    }
+    if (f1 && (g.n[0] & 3) == 0 && (reinterpret_cast<uintptr_t>(R.out) & 7) == 0) {
+      // n1 a multiple of 4 (h1 even): two neighbouring orbits per thread, each
+      // partial read and each output (and its mirror) written as a float2
+      const int fl[3] = {f1, f2, f3};
+      for (int j1 = 2 * threadIdx.x; j1 < g.h[0]; j1 += 2 * blockDim.x) {
+        Csum a[2][8];
+        for (int gi = 0; gi < R.groups; ++gi) {
+          float2 x[8];
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            const int b1 = k & 1, row = k >> 1;
+            x[k] = src[row] ? __ldg(reinterpret_cast<const float2*>(src[row] + gi * fe + b1 * g.hq[0] + j1))
+                            : make_float2(0.f, 0.f);
+          }
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            a[0][k].add(x[k].x);
+            a[1][k].add(x[k].y);
+          }
+        }
+        float v[2][8];
+#pragma unroll
+        for (int o = 0; o < 2; ++o)
+#pragma unroll
+          for (int k = 0; k < 8; ++k) v[o][k] = a[o][k].value();
+#pragma unroll
+        for (int o = 0; o < 2; ++o)
+#pragma unroll
+          for (int p = 0; p < 3; ++p) {
+            if (!fl[p]) continue;
+            const int bit = 1 << p;
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+              if (!(k & bit)) {
+                const float u = v[o][k], w = v[o][k | bit];
+                v[o][k] = u + w;
+                v[o][k | bit] = u - w;
+              }
+          }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const int b1 = k & 1, row = k >> 1;
+          if (!dst[row]) continue;
+          if (b1 == 0)  // cells j1, j1 + 1
+            *reinterpret_cast<float2*>(dst[row] + j1) = make_float2(R.alpha * v[0][k], R.alpha * v[1][k]);
+          else          // mirror cells 2h - 2 - j1 (of orbit j1 + 1) and 2h - 1 - j1 (of orbit j1)
+            *reinterpret_cast<float2*>(dst[row] + 2 * g.h[0] - 2 - j1) =
+                make_float2(R.alpha * v[1][k], R.alpha * v[0][k]);
+        }
+      }
+      continue;
     }
     for (int j1 = threadIdx.x; j1 < g.h[0]; j1 += blockDim.x) {
       Csum a[8];
