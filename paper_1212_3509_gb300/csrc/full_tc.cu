@@ -986,7 +986,6 @@ __global__ void __launch_bounds__(kS12Threads, 2) tc_s12_kernel(const __grid_con
           }
           ptx::tc_fence_after();
         }
-        int held_b = -1, held_y = -1;  // slots of the previous k-block, released with this one's
         for (int kb = 0; kb < L.kb2 && ok; ++kb) {
           const uint32_t ys = yc % kS12Y;
           if (!ptx::mbar_wait_warp(&yfull[ys], (yc / kS12Y) & 1, abort, L.wait_ns)) {
@@ -1013,20 +1012,13 @@ __global__ void __launch_bounds__(kS12Threads, 2) tc_s12_kernel(const __grid_con
           }
           issued_mma = true;
           ++yc;
-          if (held_b < 0 && kb + 1 < L.kb2) {  // release with the next k-block's
-            held_b = ib;
-            held_y = (int)ys;
-            continue;
-          }
+          // each k-block's slots are released as soon as its MMAs complete
+          // (batching two k-blocks per commit measured 4% slower here: with two
+          // Y slots the mode-1 epilogue then waits for both)
           if (leader) {
-            if (held_b >= 0) {
-              ptx::mma_commit(&empty[held_b]);
-              ptx::mma_commit(&yempty[held_y]);
-            }
             ptx::mma_commit(&empty[ib]);
             ptx::mma_commit(&yempty[ys]);
           }
-          held_b = -1;
         }
         if (!ok) break;
         if (last) {
