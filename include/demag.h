@@ -448,7 +448,9 @@ demag_status demag_energy(demag_plan* plan, const float* m, double* energy, floa
  * relations used for the micromagnetic stray field after Fig. 2), with 1/s for
  * the domain scaling.  Computed by the full-format chains of `prec` with the
  * derivative factors along one axis (the three directions share their first
- * stages: eight stage launches).  m: float [3][n3][n2][n1]; hd: float
+ * stages: eight stage launches; with the fused schedule of demag_set_fused,
+ * one fused launch and one mode-3 launch per direction, the derivative factors
+ * along axis 1, 2 or 3).  m: float [3][n3][n2][n1]; hd: float
  * [3][n3][n2][n1] (overwritten).  Allocates the derivative factors on first
  * use of a precision. */
 demag_status demag_stray_field_exact(demag_plan* plan, const float* m, float* hd, demag_precision prec,
@@ -475,7 +477,8 @@ demag_status demag_set_wait_limit(demag_plan* plan, double seconds);
  * into hi / lo and used as the mode-2 operand in shared memory, never written
  * to the workspace; the mode-3 product reads the mode-2 fields in another
  * layout.  enable = 0 runs the three-stage chain (each mode product's fields
- * in the workspace).  Both give the same values to rounding (the same
+ * in the workspace).  The analytic stray field (demag_stray_field_exact) takes
+ * the same schedule.  Both give the same values to rounding (the same
  * products, accumulated in another order); other grids and forms always run
  * the chain.  Without this call the plan takes the autotuner's choice
  * (demag_autotune, kind 9), else the fused schedule.  Build-only; no

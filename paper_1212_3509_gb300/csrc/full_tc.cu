@@ -750,6 +750,7 @@ struct S12Launch {
   int M, x2, x3;                       // nodes, extents of axes 2 (= 2 h2) and 3
   int h1, h2;                          // entries per half (= start of the odd half) of axes 1, 2
   int kb1, kb2;                        // k-blocks of the two contractions (h1 / 32, h2 / 32)
+  int pxor1, pxor2;                    // 1 when axis 1 / 2 carries derivative factors (dE odd, dF even)
   int units;                           // ext3 * M * 2
   int* unit_counter;                   // zeroed before the launch
   int* status;
@@ -869,7 +870,7 @@ __global__ void __launch_bounds__(kS12Threads, 2) tc_s12_kernel(const __grid_con
         s12_chunk(c, q, hh);
         // mode 1: factor block of (k, type) and h2 rows of X_q (input half hh of axis 2)
         const int type1 = q == 0 ? 1 : 0;             // F along axis 1 for component 1
-        const int off1 = ((h1o ^ type1) & 1) * L.h1;   // input half of axis 1
+        const int off1 = ((h1o ^ type1 ^ L.pxor1) & 1) * L.h1;  // input half of axis 1
         const int row = i3 * L.x2 + hh * L.h2;
         for (int kb = 0; kb < L.kb1 && ok; ++kb) {
           uint8_t* a = take_slot();
@@ -896,8 +897,9 @@ __global__ void __launch_bounds__(kS12Threads, 2) tc_s12_kernel(const __grid_con
           if (!b) break;
           if (leader) {
             ptx::mbar_arrive_expect_tx(&full[s], 2 * L.h2 * kRowBytes);
-            ptx::tma_load_4d(b, &L.t2_hi, &full[s], kb * 32, 0, hh ^ type2, 2 * k + type2);
-            ptx::tma_load_4d(b + kTileA, &L.t2_lo, &full[s], kb * 32, 0, hh ^ type2, 2 * k + type2);
+            // the block of the output half h2o = hh ^ type (^ 1 for derivative factors)
+            ptx::tma_load_4d(b, &L.t2_hi, &full[s], kb * 32, 0, hh ^ type2 ^ L.pxor2, 2 * k + type2);
+            ptx::tma_load_4d(b + kTileA, &L.t2_lo, &full[s], kb * 32, 0, hh ^ type2 ^ L.pxor2, 2 * k + type2);
           }
           next_slot();
         }
@@ -1094,7 +1096,8 @@ __global__ void __launch_bounds__(kS12Threads, 2) tc_s12_kernel(const __grid_con
   } else {
     // mode-2 epilogue: rows a1 of the unit's output half, columns a2; each
     // 32 x 32 chunk staged as [a2][a1], plane by plane, one box each.
-    // Targets in the order they complete: U0, U1, V0, V1.
+    // Targets in the order they complete: U0, U1, V0, V1 (their output halves
+    // swapped when axis 2 carries derivative factors).
     const int quad = warp & 3;
     uint8_t* stg = ostage + (warp - 6) * kS12Plane;
     const uint32_t taddr = tmem_base + ((uint32_t)(quad * 32) << 16) + 128;
@@ -1123,7 +1126,7 @@ __global__ void __launch_bounds__(kS12Threads, 2) tc_s12_kernel(const __grid_con
         ptx::tc_fence_after();
         const int zf = i3 + L.x3 * (2 * k + (j >> 1));
         const int a1 = h1o * L.h1 + quad * 32;
-        const int a2 = (j & 1) * L.h2;
+        const int a2 = ((j & 1) ^ L.pxor2) * L.h2;  // output half of the target
         for (int c0 = 0; c0 < L.h2; c0 += 32) {
           uint32_t v[32];
           ptx::tmem_ld32(taddr + (uint32_t)c0, v);
@@ -1879,10 +1882,12 @@ struct TcState {
   // factors of their axis (built on first use)
   bool field_ready;
   void* Bd[3][2];                 // per axis: hi / lo derivative factors [M][2][n][ld]
-  TcGroup dprog_host[3];
-  TcGroup* dprog;                 // device [3]
-  TcSeg* dseg;                    // device [3]
+  TcGroup dprog_host[4];          // stages 1-3 with derivative factors; 3: the fused schedule's
+                                  // mode-3 stage (Z, MN-major) with derivative factors
+  TcGroup* dprog;                 // device [4]
+  TcSeg* dseg;                    // device [4]
   SmallStage small_dprog[3];
+  S12Launch s12d[2];              // fused launches with derivative factors along axis 1 / axis 2
   size_t bytes;
 };
 
@@ -2248,7 +2253,7 @@ static demag_status prepare_form(demag_plan* P, TcState* S, cudaStream_t st) {
 
 template <class F>
 static demag_status run_program(demag_plan* P, TcState* S, int prog, cudaStream_t st);
-static demag_status run_s12(demag_plan* P, TcState* S, cudaStream_t st);
+static demag_status run_s12(demag_plan* P, TcState* S, const S12Launch& base, cudaStream_t st);
 
 // Point stage program `prog` at output-column tile width bn (device copy included).
 static demag_status set_tile_width(demag_plan* P, TcState* S, int prog, int bn) {
@@ -2340,7 +2345,7 @@ static demag_status tune_programs(demag_plan* P, TcState* S, cudaStream_t st) {
   auto time_sched = [&](int fused, float* ms) -> demag_status {
     auto once = [&]() -> demag_status {
       if (fused) {
-        demag_status r = run_s12(P, S, st);
+        demag_status r = run_s12(P, S, S->s12, st);
         return r == DEMAG_OK ? run_program<F>(P, S, kFwd3Z, st) : r;
       }
       demag_status r = DEMAG_OK;
@@ -2779,8 +2784,8 @@ static demag_status reduce_parts(demag_plan* P, TcState* S, int groups, int nout
 }
 
 // The mode-1 and mode-2 products of every slab in one launch (Z into buf1).
-static demag_status run_s12(demag_plan* P, TcState* S, cudaStream_t st) {
-  S12Launch L = S->s12;
+static demag_status run_s12(demag_plan* P, TcState* S, const S12Launch& base, cudaStream_t st) {
+  S12Launch L = base;
   L.unit_counter = S->counter;
   L.status = S->status;
   L.wait_ns = P->wait_ns;
@@ -2798,7 +2803,7 @@ template <class F>
 static demag_status forward_chain(demag_plan* P, TcState* S, const float* m, float* phi, cudaStream_t st) {
   demag_status s = split_input<F>(P, S, m, 3, st);
   if (S->fused && (P->fused > 0 || (P->fused < 0 && S->sched))) {
-    if (s == DEMAG_OK) s = run_s12(P, S, st);
+    if (s == DEMAG_OK) s = run_s12(P, S, S->s12, st);
     if (s == DEMAG_OK) s = run_program<F>(P, S, kFwd3Z, st);
   } else {
     for (int prog = kFwd1; prog <= kFwd3 && s == DEMAG_OK; ++prog) s = run_program<F>(P, S, prog, st);
@@ -2978,7 +2983,8 @@ static demag_status prepare_field(demag_plan* P, TcState* S, cudaStream_t st) {
                      (typename F::T*)S->Bd[p][0], (typename F::T*)S->Bd[p][1], nullptr, 0, 0));
     DEMAG_LAUNCHED(P, "tc_factor_kernel");
   }
-  TcSeg sg[3];
+  TcSeg sg[4];
+  memset(sg, 0, sizeof(sg));
   for (int st3 = 0; st3 < 3; ++st3) {
     TcGroup& G = S->dprog_host[st3];
     G = S->host_prog[kFwd1 + st3];
@@ -2995,9 +3001,32 @@ static demag_status prepare_field(demag_plan* P, TcState* S, cudaStream_t st) {
     S->small_dprog[st3].fac = nullptr;
     sg[st3] = whole_seg(G, 0, 0);
   }
-  DEMAG_CUDA(P, cudaMalloc(&S->dprog, sizeof(TcGroup) * 3));
+  if (S->fused) {
+    // the fused schedule with derivative factors: the mode-3 stage on Z, and
+    // the fused launches with dT1 (axis 1) or dT2 (axis 2)
+    TcGroup& G = S->dprog_host[3];
+    G = S->host_prog[kFwd3Z];
+    for (int h = 0; h < 2; ++h)
+      if (!make_bmap(h ? &G.b_lo : &G.b_hi, S->Bd[2][h], S->elem, S->geo.h[2], S->halves[2], 2 * M, S->ldB[2],
+                     G.bn))
+        return set_error(P, DEMAG_ECUDA, "tensor map encoding failed");
+    G.pxor = 1;
+    sg[3] = whole_seg(G, 0, 0);
+    const int h1 = S->geo.h[0], h2 = S->geo.h[1];
+    S->s12d[0] = S->s12;
+    S->s12d[1] = S->s12;
+    bool ok = true;
+    for (int h = 0; h < 2; ++h) {
+      ok = ok && make_bmap(h ? &S->s12d[0].t1_lo : &S->s12d[0].t1_hi, S->Bd[0][h], 2, h1, 2, 2 * M, S->ldB[0], kBM);
+      ok = ok && make_bmap(h ? &S->s12d[1].t2_lo : &S->s12d[1].t2_hi, S->Bd[1][h], 2, h2, 2, 2 * M, S->ldB[1], h2);
+    }
+    if (!ok) return set_error(P, DEMAG_ECUDA, "tensor map encoding failed");
+    S->s12d[0].pxor1 = 1;
+    S->s12d[1].pxor2 = 1;
+  }
+  DEMAG_CUDA(P, cudaMalloc(&S->dprog, sizeof(TcGroup) * 4));
   DEMAG_CUDA(P, cudaMalloc(&S->dseg, sizeof(sg)));
-  DEMAG_CUDA(P, cudaMemcpy(S->dprog, S->dprog_host, sizeof(TcGroup) * 3, cudaMemcpyHostToDevice));
+  DEMAG_CUDA(P, cudaMemcpy(S->dprog, S->dprog_host, sizeof(TcGroup) * 4, cudaMemcpyHostToDevice));
   DEMAG_CUDA(P, cudaMemcpy(S->dseg, sg, sizeof(sg), cudaMemcpyHostToDevice));
   S->field_ready = true;
   return DEMAG_OK;
@@ -3005,7 +3034,7 @@ static demag_status prepare_field(demag_plan* P, TcState* S, cudaStream_t st) {
 
 template <class F>
 static demag_status run_deriv(demag_plan* P, TcState* S, int st3, cudaStream_t st) {
-  if (S->small[kFwd1 + st3]) return launch_small<F>(P, S->small_dprog[st3], st);
+  if (st3 < 3 && S->small[kFwd1 + st3]) return launch_small<F>(P, S->small_dprog[st3], st);
   return launch_segs<F>(P, S->dprog + st3, S->dseg + st3, 1, S->dprog_host[st3].ntiles, S->dprog_host[st3].bn,
                         S->counter, nullptr, 0, S->status, st);
 }
@@ -3018,6 +3047,21 @@ static demag_status field_chain(demag_plan* P, TcState* S, const float* m, float
   const long long N = (long long)P->n[0] * P->n[1] * P->n[2];
   demag_status s = prepare_field<F>(P, S, st);
   if (s == DEMAG_OK) s = split_input<F>(P, S, m, 3, st);
+  if (S->fused && (P->fused > 0 || (P->fused < 0 && S->sched))) {
+    // the fused schedule, once per direction (the stage-1 fields are never
+    // stored, so the directions share nothing but the split input): direction
+    // 3 the fused launch and the derivative mode-3 stage, directions 2 and 1
+    // the fused launch with dT2 or dT1 and the mode-3 stage
+    if (s == DEMAG_OK) s = run_s12(P, S, S->s12, st);
+    if (s == DEMAG_OK) s = run_deriv<F>(P, S, 3, st);
+    if (s == DEMAG_OK) s = reduce_parts(P, S, S->groups_fwd, 1, -1.f, hd + 2 * N, st);
+    for (int dir = 1; dir >= 0 && s == DEMAG_OK; --dir) {
+      s = run_s12(P, S, S->s12d[dir], st);
+      if (s == DEMAG_OK) s = run_program<F>(P, S, kFwd3Z, st);
+      if (s == DEMAG_OK) s = reduce_parts(P, S, S->groups_fwd, 1, -1.f, hd + dir * N, st);
+    }
+    return s;
+  }
   // direction 3: stages 1, 2 as for phi, derivative stage 3
   if (s == DEMAG_OK) s = run_program<F>(P, S, kFwd1, st);
   if (s == DEMAG_OK) s = run_program<F>(P, S, kFwd2, st);
