@@ -477,8 +477,10 @@ demag_status demag_set_wait_limit(demag_plan* plan, double seconds);
  * into hi / lo and used as the mode-2 operand in shared memory, never written
  * to the workspace; the mode-3 product reads the mode-2 fields in another
  * layout.  enable = 0 runs the three-stage chain (each mode product's fields
- * in the workspace).  The analytic stray field (demag_stray_field_exact) takes
- * the same schedule.  Both give the same values to rounding (the same
+ * in the workspace).  The adjoint (demag_apply_adjoint, its first two
+ * transposed mode products fused the same way) and the analytic stray field
+ * (demag_stray_field_exact) take the same schedule.  Both give the same values
+ * to rounding (the same
  * products, accumulated in another order); other grids and forms always run
  * the chain.  Without this call the plan takes the autotuner's choice
  * (demag_autotune, kind 9), else the fused schedule.  Build-only; no
@@ -563,8 +565,9 @@ demag_status demag_autotune(demag_plan* plan, int enable);
  * cores, BF16x3 / TF32x3: 1 / 2 tile width, 3 / 4 operand stages (0 = as many
  * as fit), 5 / 6 tile order, 7 / 8 store boxes (1 = 128-row boxes); 9 the
  * BF16x3 forward schedule (1 fused, 0 chain)), key (FFT: log2 of the complex
- * FFT length, column blocks, M; tensor core: stage program 0..6 (6: the
- * mode-3 stage of the fused schedule), default value, 0; schedule: 0, 1, 0), the chosen
+ * FFT length, column blocks, M; tensor core: stage program 0..7 (6, 7: the
+ * mode-3 stages of the fused forward and adjoint schedules), default value, 0;
+ * schedule: 0, 1, 0), the chosen
  * value, its time per launch and the default value's time per launch in ms
  * (0 for an entry read from a cache). */
 int demag_autotune_count(const demag_plan* plan);

@@ -757,9 +757,49 @@ struct S12Launch {
   unsigned long long wait_ns;
 };
 
-__device__ __forceinline__ void s12_chunk(int c, int& q, int& hh) {
-  q = c < 4 ? (c & 1) : 2;
-  hh = c < 4 ? (((c >> 1) ^ c) & 1) : (c & 1);
+// Chunk c of a unit: the field of X read by its mode-1 tile, the factor types
+// along axes 1 and 2, the input half hh of axis 2, and whether it starts /
+// completes its mode-2 target.  Forward: the table above.  Adjoint (the
+// transposed chain, one input field y): Ya = y x1 F (chunks 0, 1), Yb = y x1 E
+// (chunks 2-5, computed twice), targets Za = Ya x2 E (chunks 0, 1), Zb = Yb x2 F
+// (2, 3), Zc = Yb x2 E (4, 5), one chunk each, in chunk order.
+struct S12Chunk {
+  int xf, type1, hh, type2;
+  bool first, last;
+};
+
+template <bool ADJ>
+__device__ __forceinline__ S12Chunk s12_chunk(int c) {
+  S12Chunk r;
+  if (!ADJ) {
+    const int q = c < 4 ? (c & 1) : 2;
+    r.xf = q;
+    r.type1 = q == 0 ? 1 : 0;  // F along axis 1 for component 1
+    r.hh = c < 4 ? (((c >> 1) ^ c) & 1) : (c & 1);
+    r.type2 = q == 1 ? 1 : 0;  // F along axis 2 for component 2
+    r.first = c < 4 ? (c & 1) == 0 : true;
+    r.last = c < 4 ? (c & 1) == 1 : true;
+  } else {
+    r.xf = 0;
+    r.type1 = c < 2 ? 1 : 0;
+    r.hh = c & 1;
+    r.type2 = (c >> 1) == 1 ? 1 : 0;
+    r.first = r.last = true;
+  }
+  return r;
+}
+
+// Mode-2 target j of a unit (in the order they complete): its field within the
+// node (forward U, V; adjoint Za, Zb, Zc) and its output half of axis 2.
+template <bool ADJ>
+__device__ __forceinline__ void s12_target(int j, int pxor2, int& zf, int& h2o) {
+  zf = j >> 1;
+  if (!ADJ) {
+    h2o = (j & 1) ^ pxor2;
+  } else {
+    const S12Chunk ch = s12_chunk<true>(j);
+    h2o = ch.hh ^ ch.type2 ^ pxor2;
+  }
 }
 
 // hi / lo BF16 of two consecutive values, packed (the first in the low half)
@@ -771,7 +811,10 @@ __device__ __forceinline__ void split_pair(float a, float b, uint32_t& hi, uint3
   lo = *reinterpret_cast<const uint32_t*>(&l);
 }
 
+template <bool ADJ>
 __global__ void __launch_bounds__(kS12Threads, 2) tc_s12_kernel(const __grid_constant__ S12Launch L) {
+  constexpr int kTargets = ADJ ? 6 : 4;  // mode-2 targets per unit
+  constexpr int kZf = ADJ ? 3 : 2;       // Z fields per node
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* slots = base;
@@ -866,10 +909,9 @@ __global__ void __launch_bounds__(kS12Threads, 2) tc_s12_kernel(const __grid_con
       if (u >= L.units) break;
       const int h1o = u & 1, k = (u >> 1) % L.M, i3 = (u >> 1) / L.M;
       for (int c = 0; c < 6 && ok; ++c) {
-        int q, hh;
-        s12_chunk(c, q, hh);
+        const S12Chunk ch = s12_chunk<ADJ>(c);
+        const int q = ch.xf, hh = ch.hh, type1 = ch.type1;
         // mode 1: factor block of (k, type) and h2 rows of X_q (input half hh of axis 2)
-        const int type1 = q == 0 ? 1 : 0;             // F along axis 1 for component 1
         const int off1 = ((h1o ^ type1 ^ L.pxor1) & 1) * L.h1;  // input half of axis 1
         const int row = i3 * L.x2 + hh * L.h2;
         for (int kb = 0; kb < L.kb1 && ok; ++kb) {
@@ -891,7 +933,7 @@ __global__ void __launch_bounds__(kS12Threads, 2) tc_s12_kernel(const __grid_con
           next_slot();
         }
         // mode 2: factor block of (k, type, h2o)
-        const int type2 = q == 1 ? 1 : 0;             // F along axis 2 for component 2
+        const int type2 = ch.type2;
         for (int kb = 0; kb < L.kb2 && ok; ++kb) {
           uint8_t* b = take_slot();
           if (!b) break;
@@ -978,8 +1020,8 @@ __global__ void __launch_bounds__(kS12Threads, 2) tc_s12_kernel(const __grid_con
         if (leader) ptx::mma_commit(d1full);
         ++t;
         // mode 2 into the target's accumulator
-        const bool first = c < 4 ? (c & 1) == 0 : true;
-        const bool last = c < 4 ? (c & 1) == 1 : true;
+        const S12Chunk ch = s12_chunk<ADJ>(c);
+        const bool first = ch.first, last = ch.last;
         if (first) {
           if (!ptx::mbar_wait_warp(d2empty, (g & 1) ^ 1, abort, L.wait_ns)) {
             if (leader) tc_fail(abort, L.status);
@@ -1117,16 +1159,18 @@ __global__ void __launch_bounds__(kS12Threads, 2) tc_s12_kernel(const __grid_con
       if (u < 0) break;
       const int h1o = u & 1, k = (u >> 1) % L.M, i3 = (u >> 1) / L.M;
       const bool valid = quad * 32 < L.h1;  // rows past h1 are zero and not stored
-      for (int j = 0; j < 4 && ok; ++j) {
+      for (int j = 0; j < kTargets && ok; ++j) {
         if (!ptx::mbar_wait(d2full, g & 1, abort, L.wait_ns)) {
           tc_fail(abort, L.status);
           ok = false;
           break;
         }
         ptx::tc_fence_after();
-        const int zf = i3 + L.x3 * (2 * k + (j >> 1));
+        int tf, h2o;
+        s12_target<ADJ>(j, L.pxor2, tf, h2o);
+        const int zf = i3 + L.x3 * (kZf * k + tf);
         const int a1 = h1o * L.h1 + quad * 32;
-        const int a2 = ((j & 1) ^ L.pxor2) * L.h2;  // output half of the target
+        const int a2 = h2o * L.h2;  // output half of the target
         for (int c0 = 0; c0 < L.h2; c0 += 32) {
           uint32_t v[32];
           ptx::tmem_ld32(taddr + (uint32_t)c0, v);
@@ -1835,12 +1879,13 @@ static bool make_map3(CUtensorMap* m, void* base, uint64_t d0, uint64_t d1, uint
 static int round_up(int v, int m) { return (v + m - 1) / m * m; }
 
 // Stage programs of a plan: forward stages 0-2, adjoint stages 3-5, and the
-// mode-3 stage of the fused forward application (A = Z read MN-major).
-enum { kFwd1 = 0, kFwd2, kFwd3, kAdj1, kAdj2, kAdj3, kFwd3Z, kPrograms };
+// mode-3 stages of the fused forward and adjoint applications (A = Z read
+// MN-major).
+enum { kFwd1 = 0, kFwd2, kFwd3, kAdj1, kAdj2, kAdj3, kFwd3Z, kAdj3Z, kPrograms };
 constexpr int kChain = kFwd3Z;  // programs of the three-stage chains
 
 // axis contracted by stage program p
-static int prog_axis(int p) { return p == kFwd3Z ? 2 : p % 3; }
+static int prog_axis(int p) { return p >= kChain ? 2 : p % 3; }
 
 // Per-plan, per-form tensor-core state.
 struct TcState {
@@ -1878,6 +1923,7 @@ struct TcState {
   bool fused;
   int sched;              // forward schedule chosen by the tuner (1 fused, 0 chain; 1 untuned)
   S12Launch s12;
+  S12Launch s12a;         // the adjoint's fused launch (Z with 3M fields)
   // analytic stray field: the forward stage programs with the derivative
   // factors of their axis (built on first use)
   bool field_ready;
@@ -2061,7 +2107,8 @@ static demag_status build_programs(demag_plan* P, TcState* S, const CUtensorMap 
                                    const CUtensorMap (&mapB)[3][2], const CUtensorMap (&out1)[2],
                                    const CUtensorMap (&out2)[2], const CUtensorMap& out3,
                                    const CUtensorMap (&wout1)[2], const CUtensorMap (&wout2)[2],
-                                   const CUtensorMap& wout3, const CUtensorMap (&zA)[2], int bk, cudaStream_t st) {
+                                   const CUtensorMap& wout3, const CUtensorMap (&zA)[2],
+                                   const CUtensorMap (&zA3)[2], int bk, cudaStream_t st) {
   const AxisGeo& g = S->geo;
   const int M = P->M;
   const int x1 = g.ext[0], x2 = g.ext[1], x3 = g.ext[2];
@@ -2176,10 +2223,14 @@ static demag_status build_programs(demag_plan* P, TcState* S, const CUtensorMap 
   // ([field][i3][a2][a1]) as its A operand, read MN-major; the same rows
   // (a2, a1), pairs and output
   H[kFwd3Z] = H[kFwd3];
+  H[kAdj3Z] = H[kAdj3];
   if (S->fused) {
     H[kFwd3Z].a_hi = zA[0];
     H[kFwd3Z].a_lo = zA[1];
     H[kFwd3Z].a_mn = 1;
+    H[kAdj3Z].a_hi = zA3[0];  // the adjoint's Z: 3M fields
+    H[kAdj3Z].a_lo = zA3[1];
+    H[kAdj3Z].a_mn = 1;
   }
   // stages along an axis of at most kSmallAxis cells (never folded) run on CUDA cores
   {
@@ -2245,7 +2296,8 @@ static demag_status prepare_form(demag_plan* P, TcState* S, cudaStream_t st) {
   const unsigned long long bit = 1ull << (dev & 63);
   if (!(attr & bit)) {
     DEMAG_CUDA(P, cudaFuncSetAttribute(tc_gemm_kernel<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax));
-    DEMAG_CUDA(P, cudaFuncSetAttribute(tc_s12_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kS12Smem));
+    DEMAG_CUDA(P, cudaFuncSetAttribute(tc_s12_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kS12Smem));
+    DEMAG_CUDA(P, cudaFuncSetAttribute(tc_s12_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kS12Smem));
     attr |= bit;
   }
   return DEMAG_OK;
@@ -2253,7 +2305,7 @@ static demag_status prepare_form(demag_plan* P, TcState* S, cudaStream_t st) {
 
 template <class F>
 static demag_status run_program(demag_plan* P, TcState* S, int prog, cudaStream_t st);
-static demag_status run_s12(demag_plan* P, TcState* S, const S12Launch& base, cudaStream_t st);
+static demag_status run_s12(demag_plan* P, TcState* S, const S12Launch& base, cudaStream_t st, bool adj = false);
 
 // Point stage program `prog` at output-column tile width bn (device copy included).
 static demag_status set_tile_width(demag_plan* P, TcState* S, int prog, int bn) {
@@ -2313,7 +2365,7 @@ static demag_status apply_tuned(demag_plan* P, TcState* S) {
     for (const demag_plan::Tuned& t : P->tuned)
       if (t.kind == kTuneSchedule && (t.value == 0 || t.value == 1)) S->sched = t.value;
   for (int prog = 0; prog < kPrograms; ++prog) {
-    if (S->small[prog] || (prog == kFwd3Z && !S->fused)) continue;
+    if (S->small[prog] || (prog >= kChain && !S->fused)) continue;
     for (int knob = 0; knob < 4; ++knob) {
       const demag_plan::Tuned* t = find_tuned(P, tune_kind(S, knob), prog);
       if (!t) continue;
@@ -2377,7 +2429,7 @@ static demag_status tune_programs(demag_plan* P, TcState* S, cudaStream_t st) {
   };
   for (int prog = 0; prog < kPrograms && s == DEMAG_OK; ++prog) {
     if (S->small[prog]) continue;  // runs on CUDA cores
-    if (prog == kFwd3Z && !S->fused) continue;
+    if (prog >= kChain && !S->fused) continue;
     for (int knob = 0; knob < 4 && s == DEMAG_OK; ++knob) {
       if (find_tuned(P, tune_kind(S, knob), prog)) continue;  // chosen before (a loaded cache)
       std::vector<int> cands;
@@ -2564,8 +2616,9 @@ demag_status tc_prepare(demag_plan* P, demag_precision prec, cudaStream_t st) {
     return set_error(P, DEMAG_ECUDA, "tensor map encoding failed");
   }
   // the fused forward application (mode-1 and mode-2 products in one kernel)
-  CUtensorMap zA[2];
+  CUtensorMap zA[2], zA3[2];
   memset(zA, 0, sizeof(zA));
+  memset(zA3, 0, sizeof(zA3));
   {
     const int h1 = geo.h[0], h2 = geo.h[1];
     S->fused = S->elem == 2 && !P->nonuniform && geo.hq[0] && geo.hq[1] && geo.hq[2] && h1 % 32 == 0 &&
@@ -2582,6 +2635,11 @@ demag_status tc_prepare(demag_plan* P, demag_precision prec, cudaStream_t st) {
                              CU_TENSOR_MAP_SWIZZLE_NONE);
         ok = ok && make_map3(&zA[h], zb, x2 * x1, x3, 2 * M, x2 * x1, x3 * x2 * x1, 64, 32,
                              CU_TENSOR_MAP_SWIZZLE_128B);
+        // the adjoint: 3M Z fields (buf1 holds 3M ext1 ext3 ld2 >= 3M ext3 ext2 ext1 elements)
+        ok = ok && make_map3(h ? &S->s12a.z_lo : &S->s12a.z_hi, zb, x1, x2, (uint64_t)x3 * 3 * M, x1, x2 * x1, 32,
+                             32, CU_TENSOR_MAP_SWIZZLE_NONE);
+        ok = ok && make_map3(&zA3[h], zb, x2 * x1, x3, 3 * M, x2 * x1, x3 * x2 * x1, 64, 32,
+                             CU_TENSOR_MAP_SWIZZLE_128B);
       }
       Z.M = M;
       Z.x2 = (int)x2;
@@ -2591,6 +2649,12 @@ demag_status tc_prepare(demag_plan* P, demag_precision prec, cudaStream_t st) {
       Z.kb1 = h1 / 32;
       Z.kb2 = h2 / 32;
       Z.units = (int)x3 * M * 2;
+      {  // the adjoint's launch: the same operand maps, its own Z store maps
+        const CUtensorMap zh = S->s12a.z_hi, zl = S->s12a.z_lo;
+        S->s12a = Z;
+        S->s12a.z_hi = zh;
+        S->s12a.z_lo = zl;
+      }
       if (!ok) {
         free_state(S);
         return set_error(P, DEMAG_ECUDA, "tensor map encoding failed");
@@ -2598,7 +2662,8 @@ demag_status tc_prepare(demag_plan* P, demag_precision prec, cudaStream_t st) {
     }
   }
   const int bk = kRowBytes / S->elem;
-  demag_status s = build_programs(P, S, mapX, map1, map2, mapB, out1, out2, out3, wout1, wout2, wout3, zA, bk, st);
+  demag_status s =
+      build_programs(P, S, mapX, map1, map2, mapB, out1, out2, out3, wout1, wout2, wout3, zA, zA3, bk, st);
   if (s == DEMAG_OK)
     s = prec == DEMAG_TF32X3 ? prepare_form<Tf32Form>(P, S, st) : prepare_form<Bf16Form>(P, S, st);
   if (s == DEMAG_OK) s = apply_tuned(P, S);
@@ -2784,7 +2849,7 @@ static demag_status reduce_parts(demag_plan* P, TcState* S, int groups, int nout
 }
 
 // The mode-1 and mode-2 products of every slab in one launch (Z into buf1).
-static demag_status run_s12(demag_plan* P, TcState* S, const S12Launch& base, cudaStream_t st) {
+static demag_status run_s12(demag_plan* P, TcState* S, const S12Launch& base, cudaStream_t st, bool adj) {
   S12Launch L = base;
   L.unit_counter = S->counter;
   L.status = S->status;
@@ -2794,7 +2859,10 @@ static demag_status run_s12(demag_plan* P, TcState* S, const S12Launch& base, cu
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int grid = L.units < 2 * sms ? L.units : 2 * sms;  // two CTAs per SM
   DEMAG_CUDA(P, cudaMemsetAsync(S->counter, 0, sizeof(int), st));
-  DEMAG_LAUNCH(P, kFamGemmTc, st, tc_s12_kernel<<<grid, kS12Threads, kS12Smem, st>>>(L));
+  if (adj)
+    DEMAG_LAUNCH(P, kFamGemmTc, st, tc_s12_kernel<true><<<grid, kS12Threads, kS12Smem, st>>>(L));
+  else
+    DEMAG_LAUNCH(P, kFamGemmTc, st, tc_s12_kernel<false><<<grid, kS12Threads, kS12Smem, st>>>(L));
   DEMAG_LAUNCHED(P, "tc_s12_kernel");
   return DEMAG_OK;
 }
@@ -2815,6 +2883,13 @@ static demag_status forward_chain(demag_plan* P, TcState* S, const float* m, flo
 template <class F>
 static demag_status adjoint_chain(demag_plan* P, TcState* S, const float* y, float* g, cudaStream_t st) {
   demag_status s = split_input<F>(P, S, y, 1, st);
+  if (S->fused && (P->fused > 0 || (P->fused < 0 && S->sched))) {
+    // the forward's schedule: the first two transposed mode products fused
+    if (s == DEMAG_OK) s = run_s12(P, S, S->s12a, st, true);
+    if (s == DEMAG_OK) s = run_program<F>(P, S, kAdj3Z, st);
+    if (s != DEMAG_OK) return s;
+    return reduce_parts(P, S, S->groups_adj, 3, -1.f, g, st);
+  }
   for (int prog = kAdj1; prog <= kAdj3 && s == DEMAG_OK; ++prog) s = run_program<F>(P, S, prog, st);
   if (s != DEMAG_OK) return s;
   return reduce_parts(P, S, S->groups_adj, 3, -1.f, g, st);

@@ -177,9 +177,9 @@ def test_store_box_tuning_keeps_results(D):
     P = out[1][2]
     entries = [D.demag_autotune_entry(P, i) for i in range(D.demag_autotune_count(P))]
     boxes = {e["key"][0]: e for e in entries if e["kind"] == "bf16x3_store_boxes"}
-    # programs 0-5 of the chains and 6, the mode-3 stage of the fused forward
-    # application (128^3 has it: every axis folded, 64 entries per half)
-    assert set(boxes) == set(range(7)) and all(e["value"] in (0, 1) for e in boxes.values())
+    # programs 0-5 of the chains and 6, 7, the mode-3 stages of the fused forward
+    # and adjoint applications (128^3 has them: every axis folded, 64 entries per half)
+    assert set(boxes) == set(range(8)) and all(e["value"] in (0, 1) for e in boxes.values())
 
 
 def test_forward_schedule_tuning(D):

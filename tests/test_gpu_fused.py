@@ -107,3 +107,27 @@ def test_fused_stray_field_vs_oracle_and_chain(D, n, h, R):
     assert_close(out[True], ref, TOL["bf16x3"], "fused field")
     assert_close(out[False], ref, TOL["bf16x3"], "chain field")
     assert_close(out[True], out[False], 2 * TOL["bf16x3"], "fused vs chain field")
+
+
+@pytest.mark.parametrize("n,h,R", FUSED_SHAPES[:3])
+def test_fused_adjoint_vs_oracle_and_chain(D, n, h, R):
+    """The adjoint through the fused schedule (the transposed chain's first two
+    mode products in one kernel, Za, Zb, Zc per node read MN-major by the
+    mode-3 stage) against the oracle's explicit transpose and the chain."""
+    rng = np.random.default_rng(5 + sum(n))
+    y_h = rng.standard_normal((n[2], n[1], n[0])).astype(np.float32)
+    y = dev(y_h)
+    out = {}
+    for fused in (True, False):
+        P = D.demag_build_factors(n, h, R)
+        D.demag_set_fused(P, fused)
+        g = torch.empty(3, n[2], n[1], n[0], device="cuda")
+        D.demag_apply_adjoint(P, y, g, "bf16x3")
+        torch.cuda.synchronize()
+        D.demag_sync_status(P)
+        out[fused] = host(g)
+    ref = ofull.apply_adjoint(y_h, n, h, R)
+    print(f"{n}: fused {rel_l2(out[True], ref):.3e} chain {rel_l2(out[False], ref):.3e}")
+    assert_close(out[True], ref, TOL["bf16x3"], "fused adjoint")
+    assert_close(out[False], ref, TOL["bf16x3"], "chain adjoint")
+    assert_close(out[True], out[False], 2 * TOL["bf16x3"], "fused vs chain adjoint")
