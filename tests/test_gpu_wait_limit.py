@@ -28,8 +28,11 @@ def D():
     return D
 
 
-def test_zero_wait_limit_reports_timeout_then_plan_recovers(D):
-    n, h, R = (48, 40, 37), (1 / 48,) * 3, 21  # every axis > 16 cells: all stages on tcgen05
+# every axis > 16 cells: all stages on tcgen05; the second grid takes the fused
+# schedule (its fused kernel's abort path, then the mode-3 stage's)
+@pytest.mark.parametrize("n", [(48, 40, 37), (64, 64, 20)])
+def test_zero_wait_limit_reports_timeout_then_plan_recovers(D, n):
+    h, R = (1 / max(n),) * 3, 21
     m = synth.random_unit_m(n, 1230)
     P = D.demag_build_factors(n, h, R)
     phi = torch.empty(n[2], n[1], n[0], device="cuda")
