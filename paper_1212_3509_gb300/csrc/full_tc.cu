@@ -2041,7 +2041,10 @@ static int grid_blocks(long long count) {
 }
 
 // blocks of a row-wise launch: one row per block, at most 16 blocks per SM
-static int row_blocks(long long rows) { return (int)(rows > 152 * 16 ? 152 * 16 : (rows < 1 ? 1 : rows)); }
+static int row_blocks(long long rows, int per_sm = 16) {
+  const long long cap = 152LL * per_sm;
+  return (int)(rows > cap ? cap : (rows < 1 ? 1 : rows));
+}
 
 static TcJob job(int pair0, int npairs, int out_field, int half) {
   TcJob j;
@@ -2773,7 +2776,16 @@ static void add_split(SplitLists& L, demag_plan* P, TcState* S, const float* x, 
 template <class F>
 static demag_status launch_split(demag_plan* P, const SplitLists& L, cudaStream_t st) {
   if (L.f.count) {
-    DEMAG_LAUNCH(P, kFamSplit, st, fold_split_kernel<F><<<row_blocks(L.f.total), 128, 0, st>>>(L.f));
+    // rows whose first axis takes the paired path (two orbits per thread) need
+    // half the threads: 64-thread blocks, twice as many resident
+    bool pairs = F::kElem == 2;
+    for (int i = 0; i < L.f.count; ++i) {
+      const FoldItem& it = L.f.it[i];
+      pairs = pairs && it.g.hq[0] && (it.g.n[0] & 3) == 0 && (reinterpret_cast<uintptr_t>(it.x) & 7) == 0;
+    }
+    const int threads = pairs ? 64 : 128;
+    DEMAG_LAUNCH(P, kFamSplit, st,
+                 fold_split_kernel<F><<<row_blocks(L.f.total, pairs ? 32 : 16), threads, 0, st>>>(L.f));
     DEMAG_LAUNCHED(P, "fold_split_kernel");
   }
   if (L.p.count) {
@@ -2804,7 +2816,14 @@ struct ReduceLists {
 
 static demag_status launch_reduce(demag_plan* P, const ReduceLists& L, cudaStream_t st) {
   if (L.f.count) {
-    DEMAG_LAUNCH(P, kFamMisc, st, unfold_reduce_kernel<<<row_blocks(L.f.total), 128, 0, st>>>(L.f));
+    bool pairs = true;  // as in the fold: the paired path needs half the threads
+    for (int i = 0; i < L.f.count; ++i) {
+      const UnfoldItem& it = L.f.it[i];
+      pairs = pairs && it.g.hq[0] && (it.g.n[0] & 3) == 0 && (reinterpret_cast<uintptr_t>(it.out) & 7) == 0;
+    }
+    const int threads = pairs ? 64 : 128;
+    DEMAG_LAUNCH(P, kFamMisc, st,
+                 unfold_reduce_kernel<<<row_blocks(L.f.total, pairs ? 24 : 16), threads, 0, st>>>(L.f));
     DEMAG_LAUNCHED(P, "unfold_reduce_kernel");
   }
   if (L.p.count) {

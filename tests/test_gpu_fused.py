@@ -131,3 +131,30 @@ def test_fused_adjoint_vs_oracle_and_chain(D, n, h, R):
     assert_close(out[True], ref, TOL["bf16x3"], "fused adjoint")
     assert_close(out[False], ref, TOL["bf16x3"], "chain adjoint")
     assert_close(out[True], out[False], 2 * TOL["bf16x3"], "fused vs chain adjoint")
+
+
+def test_fused_forward_and_adjoint_graph_capturable(D):
+    """The fused schedule's launches (split, fused kernel, mode-3 stage, node-sum
+    reduction; the same for the adjoint) capture into a CUDA graph and replay to
+    the direct calls' bits."""
+    n, h, R = (128, 64, 40), (1 / 128,) * 3, 21
+    m = dev(synth.random_unit_m(n, 21))
+    P = D.demag_build_factors(n, h, R)
+    D.demag_set_fused(P, True)
+    a = torch.empty(n[2], n[1], n[0], device="cuda")
+    ga = torch.empty(3, n[2], n[1], n[0], device="cuda")
+    D.demag_apply_full(P, m, a, "bf16x3")  # the first calls build the tensor-core state
+    D.demag_apply_adjoint(P, a, ga, "bf16x3")
+    torch.cuda.synchronize()
+    b = torch.zeros_like(a)
+    gb = torch.zeros_like(ga)
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            D.demag_apply_full(P, m, b, "bf16x3", stream=s)
+            D.demag_apply_adjoint(P, b, gb, "bf16x3", stream=s)
+    g.replay()
+    torch.cuda.synchronize()
+    D.demag_sync_status(P)
+    assert torch.equal(a, b) and torch.equal(ga, gb)
