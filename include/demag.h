@@ -472,8 +472,7 @@ demag_status demag_set_wait_limit(demag_plan* plan, double seconds);
 /* Schedule of the full-format forward application on tensor cores (BF16x3):
  * enable = 1 fuses the mode-1 and mode-2 products of Cor. 3
  * into one kernel on grids whose three axes are folded (longer than 16 cells)
- * with ceil(n1 / 2) and ceil(n2 / 2) multiples of 32 up to 128 (n1, n2 of 64,
- * 128, 192 or 256, for example): per slab i3 the mode-1 results are split
+ * with n1 and n2 at most 256: per slab i3 the mode-1 results are split
  * into hi / lo and used as the mode-2 operand in shared memory, never written
  * to the workspace; the mode-3 product reads the mode-2 fields in another
  * layout.  enable = 0 runs the three-stage chain (each mode product's fields
@@ -483,8 +482,9 @@ demag_status demag_set_wait_limit(demag_plan* plan, double seconds);
  * to rounding (the same
  * products, accumulated in another order); other grids and forms always run
  * the chain.  Without this call the plan takes the autotuner's choice
- * (demag_autotune, kind 9), else the fused schedule.  Build-only; no
- * counterpart in the paper. */
+ * (demag_autotune, kind 9), else the fused schedule on grids of at least
+ * 2^20 cells in the folded layout (about 100^3 and up) and the chain on
+ * smaller ones.  Build-only; no counterpart in the paper. */
 demag_status demag_set_fused(demag_plan* plan, int enable);
 
 /* ---- allocation-free full format (no counterpart in the paper) ---------- */

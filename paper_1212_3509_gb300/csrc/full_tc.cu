@@ -697,7 +697,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const __grid_con
 // ---------------------------------------------------------------- fused mode-1 / mode-2 products
 //
 // On a grid whose axes are all folded, with h1, h2 <= 128 entries per half on
-// the first two (multiples of 32), the mode-1 and mode-2 products of a slab i3
+// the first two, the mode-1 and mode-2 products of a slab i3
 // run in one persistent kernel and the mode-1 results never leave the SM.  A
 // unit is (slab i3, node k, output half h1o of axis 1).  Its mode-1 products
 // are formed transposed, the factor block being the A operand:
@@ -708,7 +708,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const __grid_con
 //     Z[a1][a2] = sum_i2 Y[a1][i2] T2_{k,type}[h2o][a2][i2],
 // handed over in shared memory (never written to the workspace).  Z is stored
 // as [field][i3][a2][a1] (a1 contiguous, U_k field 2k, V_k field 2k + 1),
-// which the mode-3 stage reads MN-major (TcGroup::a_mn).  Per unit six chunks
+// which the mode-3 stage reads MN-major (TcGroup::a_mn).  Halves that are not
+// multiples of 32: the contractions run over ceil(h / 32) k-blocks (factor
+// columns past h read as zeros, Y columns past h2 are zeroed), the tiles are
+// n2 = h2 rounded up to 16 wide, and the Z stores are clipped to the h1 x h2
+// valid entries of each half by their tensor map.  Per unit six chunks
 // (component q, input half hh of axis 2), each a mode-1 tile (128 x h2) and
 // its mode-2 product, in an order that completes one target before the next:
 //     c     0  1  2  3  4  5
@@ -744,12 +748,14 @@ static_assert(2 * (kS12Smem + 1024) <= 228 * 1024, "two fused CTAs per SM");
 
 struct S12Launch {
   CUtensorMap t1_hi, t1_lo;            // axis-1 factor blocks, 128-row boxes (mode-1 A)
-  CUtensorMap x_hi, x_lo;              // split input, h2-row boxes (mode-1 B)
-  CUtensorMap t2_hi, t2_lo;            // axis-2 factor blocks, h2-row boxes (mode-2 B)
-  CUtensorMap z_hi, z_lo;              // Z [2M ext3][ext2][ext1], 32 x 32 store boxes
-  int M, x2, x3;                       // nodes, extents of axes 2 (= 2 h2) and 3
-  int h1, h2;                          // entries per half (= start of the odd half) of axes 1, 2
-  int kb1, kb2;                        // k-blocks of the two contractions (h1 / 32, h2 / 32)
+  CUtensorMap x_hi, x_lo;              // split input, n2-row boxes (mode-1 B)
+  CUtensorMap t2_hi, t2_lo;            // axis-2 factor blocks, n2-row boxes (mode-2 B)
+  CUtensorMap z_hi, z_lo;              // Z as (a1 < h1, half, a2 < h2, half, field), 32 x 32 store boxes
+  int M, x2, x3;                       // nodes, extents of axes 2 (= 2 hq2) and 3
+  int h1, h2;                          // valid entries per half of axes 1, 2
+  int hq1, hq2;                        // start of the odd half of axes 1, 2 (h rounded up to 8)
+  int n2;                              // tile width of both products: h2 rounded up to 16
+  int kb1, kb2;                        // k-blocks of the two contractions (ceil(h1 / 32), ceil(h2 / 32))
   int pxor1, pxor2;                    // 1 when axis 1 / 2 carries derivative factors (dE odd, dF even)
   int units;                           // ext3 * M * 2
   int* unit_counter;                   // zeroed before the launch
@@ -912,8 +918,8 @@ __global__ void __launch_bounds__(kS12Threads, 2) tc_s12_kernel(const __grid_con
         const S12Chunk ch = s12_chunk<ADJ>(c);
         const int q = ch.xf, hh = ch.hh, type1 = ch.type1;
         // mode 1: factor block of (k, type) and h2 rows of X_q (input half hh of axis 2)
-        const int off1 = ((h1o ^ type1 ^ L.pxor1) & 1) * L.h1;  // input half of axis 1
-        const int row = i3 * L.x2 + hh * L.h2;
+        const int off1 = ((h1o ^ type1 ^ L.pxor1) & 1) * L.hq1;  // input half of axis 1
+        const int row = i3 * L.x2 + hh * L.hq2;
         for (int kb = 0; kb < L.kb1 && ok; ++kb) {
           uint8_t* a = take_slot();
           if (!a) break;
@@ -926,7 +932,7 @@ __global__ void __launch_bounds__(kS12Threads, 2) tc_s12_kernel(const __grid_con
           uint8_t* b = take_slot();
           if (!b) break;
           if (leader) {
-            ptx::mbar_arrive_expect_tx(&full[s], 2 * L.h2 * kRowBytes);
+            ptx::mbar_arrive_expect_tx(&full[s], 2 * L.n2 * kRowBytes);
             ptx::tma_load_3d(b, &L.x_hi, &full[s], off1 + kb * 32, row, q);
             ptx::tma_load_3d(b + kTileA, &L.x_lo, &full[s], off1 + kb * 32, row, q);
           }
@@ -938,7 +944,7 @@ __global__ void __launch_bounds__(kS12Threads, 2) tc_s12_kernel(const __grid_con
           uint8_t* b = take_slot();
           if (!b) break;
           if (leader) {
-            ptx::mbar_arrive_expect_tx(&full[s], 2 * L.h2 * kRowBytes);
+            ptx::mbar_arrive_expect_tx(&full[s], 2 * L.n2 * kRowBytes);
             // the block of the output half h2o = hh ^ type (^ 1 for derivative factors)
             ptx::tma_load_4d(b, &L.t2_hi, &full[s], kb * 32, 0, hh ^ type2 ^ L.pxor2, 2 * k + type2);
             ptx::tma_load_4d(b + kTileA, &L.t2_lo, &full[s], kb * 32, 0, hh ^ type2 ^ L.pxor2, 2 * k + type2);
@@ -956,7 +962,7 @@ __global__ void __launch_bounds__(kS12Threads, 2) tc_s12_kernel(const __grid_con
     uint32_t rph = 0;
     uint32_t t = 0, yc = 0, g = 0;  // mode-1 tiles, Y k-blocks consumed, mode-2 targets completed
     bool ok = true;
-    const uint32_t idesc = ptx::instr_desc(1, kBM, (uint32_t)L.h2);
+    const uint32_t idesc = ptx::instr_desc(1, kBM, (uint32_t)L.n2);
     const uint32_t d1 = tmem_base, d2 = tmem_base + 128;
     // the next operand slot once its loads have landed (index in `idx`)
     auto take_full = [&](int& idx) -> uint32_t {
@@ -1115,6 +1121,13 @@ __global__ void __launch_bounds__(kS12Threads, 2) tc_s12_kernel(const __grid_con
             ptx::tc_fence_before();
             __syncwarp();
             if (lane == 0) ptx::mbar_arrive(d1empty);
+            // columns i2 >= h2: rows of the next half or never written; zero
+            // them, so that Y holds only finite entries (their factor columns
+            // read as zeros)
+            const int lim = L.h2 - kb * 32;
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+              if (j >= lim) v[j] = 0u;
           }
           uint8_t* slot = yslots + ys * kS12YSlot;
 #pragma unroll
@@ -1169,8 +1182,6 @@ __global__ void __launch_bounds__(kS12Threads, 2) tc_s12_kernel(const __grid_con
         int tf, h2o;
         s12_target<ADJ>(j, L.pxor2, tf, h2o);
         const int zf = i3 + L.x3 * (kZf * k + tf);
-        const int a1 = h1o * L.h1 + quad * 32;
-        const int a2 = h2o * L.h2;  // output half of the target
         for (int c0 = 0; c0 < L.h2; c0 += 32) {
           uint32_t v[32];
           ptx::tmem_ld32(taddr + (uint32_t)c0, v);
@@ -1191,7 +1202,8 @@ __global__ void __launch_bounds__(kS12Threads, 2) tc_s12_kernel(const __grid_con
             ptx::fence_proxy_async_smem();
             __syncwarp();
             if (lane == 0) {
-              ptx::tma_store_3d(pl ? &L.z_lo : &L.z_hi, stg, a1, a2 + c0, zf);
+              // (a1 in the half, output half of axis 1, a2 in the target's half, its half, field)
+              ptx::tma_store_5d(pl ? &L.z_lo : &L.z_hi, stg, quad * 32, h1o, c0, h2o, zf);
               ptx::bulk_commit();
             }
           }
@@ -1918,10 +1930,11 @@ struct TcState {
   bool small[kPrograms];          // program runs on CUDA cores (axis of at most kSmallAxis cells)
   SmallStage small_prog[kPrograms];
   // fused forward application (tc_s12_kernel, then kFwd3Z): built where the
-  // grid allows it (BF16x3, every axis folded, h1 and h2 multiples of 32 up
-  // to 128); the Z fields live in buf1
+  // grid allows it (BF16x3, every axis folded, h1 and h2 at most 128); the Z
+  // fields live in buf1
   bool fused;
-  int sched;              // forward schedule chosen by the tuner (1 fused, 0 chain; 1 untuned)
+  int sched;              // forward schedule (1 fused, 0 chain): the tuner's choice, else sched0
+  int sched0;             // untuned forward schedule: fused on grids of at least 2^20 split cells
   S12Launch s12;
   S12Launch s12a;         // the adjoint's fused launch (Z with 3M fields)
   // analytic stray field: the forward stage programs with the derivative
@@ -2498,7 +2511,7 @@ static demag_status tune_programs(demag_plan* P, TcState* S, cudaStream_t st) {
       t.key[2] = 0;
       t.value = S->sched;
       t.ms = S->sched ? mf : mc;
-      t.ms_default = mf;
+      t.ms_default = S->sched0 ? mf : mc;
       P->tuned.push_back(t);
     }
   }
@@ -2623,24 +2636,30 @@ demag_status tc_prepare(demag_plan* P, demag_precision prec, cudaStream_t st) {
   memset(zA, 0, sizeof(zA));
   memset(zA3, 0, sizeof(zA3));
   {
-    const int h1 = geo.h[0], h2 = geo.h[1];
-    S->fused = S->elem == 2 && !P->nonuniform && geo.hq[0] && geo.hq[1] && geo.hq[2] && h1 % 32 == 0 &&
-               h2 % 32 == 0 && h1 <= 128 && h2 <= 128;
-    S->sched = 1;
+    const int h1 = geo.h[0], h2 = geo.h[1], hq1 = geo.hq[0], hq2 = geo.hq[1];
+    const int n2 = round_up(h2, 16);
+    S->fused = S->elem == 2 && !P->nonuniform && geo.hq[0] && geo.hq[1] && geo.hq[2] && h1 <= 128 && h2 <= 128;
+    // untuned choice (BF16x3, R = 41, CUDA events per application): the chain
+    // is faster on small grids (32^3 0.072 against 0.095 ms, 80^3 0.249 against
+    // 0.274, 96^3 0.325 against 0.329), the fused schedule from 112^3 on
+    // (0.42 against 0.45 ms, 160^3 0.87 against 0.99, 256^3 2.14 against 3.00)
+    S->sched0 = x1 * x2 * x3 >= (1LL << 20) ? 1 : 0;
+    S->sched = S->sched0;
     if (S->fused) {
       S12Launch& Z = S->s12;
       for (int h = 0; h < 2 && ok; ++h) {
         void* zb = S->buf1[h];  // Z [2M][ext3][ext2][ext1] in the stage-1 workspace
         ok = ok && make_bmap(h ? &Z.t1_lo : &Z.t1_hi, S->B[0][h], 2, h1, 2, 2 * M, S->ldB[0], kBM);
-        ok = ok && make_map(h ? &Z.x_lo : &Z.x_hi, S->X[h], 2, x1, (uint64_t)(x3 * x2), 3, S->ld[0], h2);
-        ok = ok && make_bmap(h ? &Z.t2_lo : &Z.t2_hi, S->B[1][h], 2, h2, 2, 2 * M, S->ldB[1], h2);
-        ok = ok && make_map3(h ? &Z.z_lo : &Z.z_hi, zb, x1, x2, (uint64_t)x3 * 2 * M, x1, x2 * x1, 32, 32,
-                             CU_TENSOR_MAP_SWIZZLE_NONE);
+        ok = ok && make_map(h ? &Z.x_lo : &Z.x_hi, S->X[h], 2, x1, (uint64_t)(x3 * x2), 3, S->ld[0], n2);
+        ok = ok && make_bmap(h ? &Z.t2_lo : &Z.t2_hi, S->B[1][h], 2, h2, 2, 2 * M, S->ldB[1], n2);
+        // stores clipped to the valid h1 x h2 entries of each pair of halves
+        ok = ok && make_out_map(h ? &Z.z_lo : &Z.z_hi, zb, 2, h1, 2, h2, 2, hq2, (uint64_t)x3 * 2 * M, hq1, x1,
+                                x2 * x1);
         ok = ok && make_map3(&zA[h], zb, x2 * x1, x3, 2 * M, x2 * x1, x3 * x2 * x1, 64, 32,
                              CU_TENSOR_MAP_SWIZZLE_128B);
         // the adjoint: 3M Z fields (buf1 holds 3M ext1 ext3 ld2 >= 3M ext3 ext2 ext1 elements)
-        ok = ok && make_map3(h ? &S->s12a.z_lo : &S->s12a.z_hi, zb, x1, x2, (uint64_t)x3 * 3 * M, x1, x2 * x1, 32,
-                             32, CU_TENSOR_MAP_SWIZZLE_NONE);
+        ok = ok && make_out_map(h ? &S->s12a.z_lo : &S->s12a.z_hi, zb, 2, h1, 2, h2, 2, hq2, (uint64_t)x3 * 3 * M,
+                                hq1, x1, x2 * x1);
         ok = ok && make_map3(&zA3[h], zb, x2 * x1, x3, 3 * M, x2 * x1, x3 * x2 * x1, 64, 32,
                              CU_TENSOR_MAP_SWIZZLE_128B);
       }
@@ -2649,8 +2668,11 @@ demag_status tc_prepare(demag_plan* P, demag_precision prec, cudaStream_t st) {
       Z.x3 = (int)x3;
       Z.h1 = h1;
       Z.h2 = h2;
-      Z.kb1 = h1 / 32;
-      Z.kb2 = h2 / 32;
+      Z.hq1 = hq1;
+      Z.hq2 = hq2;
+      Z.n2 = n2;
+      Z.kb1 = (h1 + 31) / 32;
+      Z.kb2 = (h2 + 31) / 32;
       Z.units = (int)x3 * M * 2;
       {  // the adjoint's launch: the same operand maps, its own Z store maps
         const CUtensorMap zh = S->s12a.z_hi, zl = S->s12a.z_lo;
@@ -3112,7 +3134,8 @@ static demag_status prepare_field(demag_plan* P, TcState* S, cudaStream_t st) {
     bool ok = true;
     for (int h = 0; h < 2; ++h) {
       ok = ok && make_bmap(h ? &S->s12d[0].t1_lo : &S->s12d[0].t1_hi, S->Bd[0][h], 2, h1, 2, 2 * M, S->ldB[0], kBM);
-      ok = ok && make_bmap(h ? &S->s12d[1].t2_lo : &S->s12d[1].t2_hi, S->Bd[1][h], 2, h2, 2, 2 * M, S->ldB[1], h2);
+      ok = ok && make_bmap(h ? &S->s12d[1].t2_lo : &S->s12d[1].t2_hi, S->Bd[1][h], 2, h2, 2, 2 * M, S->ldB[1],
+                           S->s12.n2);
     }
     if (!ok) return set_error(P, DEMAG_ECUDA, "tensor map encoding failed");
     S->s12d[0].pxor1 = 1;

@@ -1,11 +1,14 @@
 """Fused mode-1 / mode-2 products (BF16x3) against the FP64 oracle and the three-stage chain.
 
 A grid whose three axes are folded (longer than 16 cells) with ceil(n1 / 2) and
-ceil(n2 / 2) multiples of 32 up to 128 runs its forward application through the
-fused kernel by default; demag_set_fused(plan, False) selects the chain.  Odd
-extents (63, 127, 255) carry the padding cell of the folded layout; third axes
-of 17, 33 or 37 cells pad their halves to 16-byte multiples; h1 = 32 leaves
-three of the four TMEM lane quadrants of the mode-2 tile without rows."""
+ceil(n2 / 2) at most 128 runs its forward application through the fused kernel
+by default; demag_set_fused(plan, False) selects the chain.  Odd extents (63,
+127, 255) carry the padding cell of the folded layout; third axes of 17, 33 or
+37 cells pad their halves to 16-byte multiples; h1 = 32 leaves three of the four
+TMEM lane quadrants of the mode-2 tile without rows.  Halves that are not
+multiples of 32 (RAGGED_HALVES) end their contractions inside a k-block, run
+tiles of h2 rounded up to 16, pad each half of axes 1 and 2 to a multiple of 8
+(h 9 -> 16, 19 -> 24, 115 -> 120) and clip the Z stores to the valid entries."""
 import numpy as np
 import pytest
 
@@ -23,6 +26,14 @@ FUSED_SHAPES = [
     ((128, 192, 33), (1.0, 1.0, 1.0), 11),
     ((255, 64, 24), (1 / 255, 1 / 64, 1 / 24), 11),
     ((192, 256, 37), (0.5, 0.25, 1.0), 5),
+]
+
+RAGGED_HALVES = [
+    ((80, 80, 80), (1 / 80,) * 3, 21),                # h 40: k-blocks of 32 + 8, tiles 48 wide
+    ((37, 45, 33), (0.03, 0.02, 0.03), 11),           # h 19, 23 (halves padded to 24), tiles 32 wide
+    ((17, 18, 17), (1 / 17,) * 3, 11),                # h 9 (padded to 16), tiles 16 wide
+    ((160, 100, 21), (0.01, 0.015, 0.05), 11),        # h 80, 50 (odd half at 56), tiles 64 wide
+    ((250, 230, 19), (1 / 250, 1 / 230, 1 / 19), 5),  # h 125, 115 (padded to 128, 120), tiles 128 wide
 ]
 
 
@@ -44,7 +55,7 @@ def _apply(D, P, m, fused):
     return host(phi)
 
 
-@pytest.mark.parametrize("n,h,R", FUSED_SHAPES)
+@pytest.mark.parametrize("n,h,R", FUSED_SHAPES + RAGGED_HALVES)
 def test_fused_vs_oracle_and_chain(D, n, h, R):
     m_h = synth.random_unit_m(n, 3509 + sum(n))
     m = dev(m_h)
@@ -84,7 +95,8 @@ def test_fused_and_chain_interleaved_256(D):
 
 
 
-@pytest.mark.parametrize("n,h,R", [((64, 64, 24), (1 / 64,) * 3, 21), ((128, 64, 19), (0.01, 0.02, 0.03), 11)])
+@pytest.mark.parametrize("n,h,R", [((64, 64, 24), (1 / 64,) * 3, 21), ((128, 64, 19), (0.01, 0.02, 0.03), 11),
+                                   ((75, 43, 30), (0.02, 0.03, 0.01), 11)])
 def test_fused_stray_field_vs_oracle_and_chain(D, n, h, R):
     """The analytic stray field through the fused schedule (one fused launch per
     direction, with derivative factors along axis 1 or 2, and the mode-3 stage on
@@ -109,7 +121,7 @@ def test_fused_stray_field_vs_oracle_and_chain(D, n, h, R):
     assert_close(out[True], out[False], 2 * TOL["bf16x3"], "fused vs chain field")
 
 
-@pytest.mark.parametrize("n,h,R", FUSED_SHAPES[:3])
+@pytest.mark.parametrize("n,h,R", FUSED_SHAPES[:3] + RAGGED_HALVES[:2])
 def test_fused_adjoint_vs_oracle_and_chain(D, n, h, R):
     """The adjoint through the fused schedule (the transposed chain's first two
     mode products in one kernel, Za, Zb, Zc per node read MN-major by the

@@ -66,13 +66,16 @@ def test_split_adjoint_vs_oracle(D, n, h, R, prec):
     assert_close(host(g), ref_, TOL[prec])
 
 
+@pytest.mark.parametrize("fused", [False, True])
 @pytest.mark.parametrize("n", [(40, 24, 16), (64, 32, 96), (96, 64, 32)])
-def test_bf16x3_repeated_calls_are_identical(D, n):
-    # (64, 32, 96) and (96, 64, 32) store every stage through TMA with an odd
-    # number of 32-column chunks per tile
+def test_bf16x3_repeated_calls_are_identical(D, n, fused):
+    # (64, 32, 96) and (96, 64, 32) store every stage of the chain through TMA
+    # with an odd number of 32-column chunks per tile; both take the fused
+    # schedule when asked ((40, 24, 16) has a short axis: the chain only)
     h, R = (0.05,) * 3, 21
     m = dev(synth.random_unit_m(n, 99))
     P = D.demag_build_factors(n, h, R)
+    D.demag_set_fused(P, fused)
     a = torch.empty(n[2], n[1], n[0], device="cuda")
     b = torch.empty_like(a)
     D.demag_apply_full(P, m, a, "bf16x3")
@@ -89,11 +92,13 @@ def test_grouped_batch_equals_single_applies(D, prec):
     bit, what separate calls give on grids whose axes all run on the tensor
     cores: every tile runs the same MMA sequence.  Axes of at most 16 cells run
     on CUDA cores in a single call but as padded tensor-core tiles in the
-    batch, so those grids agree to the split-form tolerance."""
+    batch, so those grids agree to the split-form tolerance.  The batch runs
+    the three-stage chain, so the separate calls are held to it too."""
     cases = [TC_SHAPES[0], TC_SHAPES[1], TC_SHAPES[4], TC_SHAPES[7], TC_SHAPES[8]]
     plans, ms, single = [], [], []
     for i, (n, h, R) in enumerate(cases):
         P = D.demag_build_factors(n, h, R)
+        D.demag_set_fused(P, False)
         m = dev(synth.random_unit_m(n, 4242 + i))
         phi = torch.empty(n[2], n[1], n[0], device="cuda")
         D.demag_apply_full(P, m, phi, prec)

@@ -28,13 +28,15 @@ def D():
     return D
 
 
-# every axis > 16 cells: all stages on tcgen05; the second grid takes the fused
-# schedule (its fused kernel's abort path, then the mode-3 stage's)
-@pytest.mark.parametrize("n", [(48, 40, 37), (64, 64, 20)])
-def test_zero_wait_limit_reports_timeout_then_plan_recovers(D, n):
+# every axis > 16 cells: all stages on tcgen05, through the three-stage chain
+# (its kernel's abort path) or the fused schedule (the fused kernel's abort
+# path, then the mode-3 stage's)
+@pytest.mark.parametrize("n,fused", [((48, 40, 37), False), ((48, 40, 37), True), ((64, 64, 20), True)])
+def test_zero_wait_limit_reports_timeout_then_plan_recovers(D, n, fused):
     h, R = (1 / max(n),) * 3, 21
     m = synth.random_unit_m(n, 1230)
     P = D.demag_build_factors(n, h, R)
+    D.demag_set_fused(P, fused)
     phi = torch.empty(n[2], n[1], n[0], device="cuda")
     D.demag_apply_full(P, dev(m), phi, "bf16x3")  # prepares the tensor-core state
     D.demag_sync_status(P)
