@@ -1166,8 +1166,10 @@ def ncore_implicit(rho, rt):
 
 def run_uneven_batch(args, D, world, local, stream, form):
     """64 full-format grids of mixed shape (cubes 32^3..192^3, 512x512x4 and
-    256x64x8 films), R = 41, one grouped tensor-core launch per mode-product
-    stage, replayed as a CUDA graph; compared with one call per grid."""
+    256x64x8 films), R = 41, replayed as a CUDA graph of four launches (split;
+    the fused mode-1 / mode-2 products of the grids with the fused schedule;
+    one persistent launch over their mode-3 stages and the other grids'
+    three stages; reduction); compared with one call per grid."""
     import numpy as np
     import torch
     import synth
@@ -1186,10 +1188,11 @@ def run_uneven_batch(args, D, world, local, stream, form):
     M = plans[0].M
     flops = sum(2.0 * M * (a * b * c) * (3 * a + 3 * b + 2 * c) for a, b, c in shapes)
 
-    def stage_bytes(a, b, c):  # algorithmic DRAM bytes of one grid's three BF16x3 stages
+    def grid_bytes(a, b, c, fused):  # algorithmic DRAM bytes of one grid's BF16x3 mode products
         pp3 = max(1, 400 // (-(-c // 32) * 6))
-        return 4.0 * a * b * c * (3 + 10 * M) + 4.0 * (-(-2 * M // pp3)) * a * b * c
-    batch_bytes = sum(stage_bytes(*sh) for sh in shapes)
+        return 4.0 * a * b * c * (3 + (4 if fused else 10) * M) + 4.0 * (-(-2 * M // pp3)) * a * b * c
+    sched = [D.demag_forward_schedule(P, form) for P in plans]
+    batch_bytes = sum(grid_bytes(*sh, sc == 1) for sh, sc in zip(shapes, sched))
     G = D.demag_graph_create_batched(plans, ms, phis, form)
     graph_fn = lambda: G.launch(stream)  # noqa: E731
     seq_fn = lambda: [D.demag_apply_full(P, m, f, form) for P, m, f in zip(plans, ms, phis)]  # noqa: E731
@@ -1217,6 +1220,7 @@ def run_uneven_batch(args, D, world, local, stream, form):
             "cells": int(sum(a * b * c for a, b, c in shapes)),
             "shapes": {f"{a}x{b}x{c}": shapes.count((a, b, c)) for a, b, c in sorted(set(shapes))},
             "gpu_launches": int(launches), "graph_kernels": G.kernels, "clocks": clk.summary(),
+            "fused_grids": int(sum(1 for sc in sched if sc == 1)),
             "_check": check, "_shapes": shapes, "_h": hs, "_m": ms_host, "_phi": phis}
 
 

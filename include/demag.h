@@ -487,6 +487,14 @@ demag_status demag_set_wait_limit(demag_plan* plan, double seconds);
  * smaller ones.  Build-only; no counterpart in the paper. */
 demag_status demag_set_fused(demag_plan* plan, int enable);
 
+/* The forward schedule a plan's next full-format application in `prec`
+ * takes: 1 the fused mode-1 / mode-2 kernel, 0 the three-stage chain, -1
+ * when the plan has no tensor-core state for `prec` yet (no application or
+ * demag_reserve_workspace in that form), `prec` is not a tensor-core form,
+ * or plan is NULL.  A query; no error status is set.  Build-only; no
+ * counterpart in the paper. */
+int demag_forward_schedule(const demag_plan* plan, demag_precision prec);
+
 /* ---- allocation-free full format (no counterpart in the paper) ---------- */
 
 /* phi = sum_q P^(q) m^(q) exactly as demag_apply_full with DEMAG_FP32 (same

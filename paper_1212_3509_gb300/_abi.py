@@ -94,6 +94,7 @@ _SIGS = {
     "demag_autotune": (_i, [_vp, _i]),
     "demag_set_wait_limit": (_i, [_vp, ctypes.c_double]),
     "demag_set_fused": (_i, [_vp, ctypes.c_int]),
+    "demag_forward_schedule": (_i, [_vp, ctypes.c_int]),
     "demag_autotune_count": (_i, [_vp]),
     "demag_autotune_entry": (_i, [_vp, _i, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i),
                                   ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]),
@@ -580,6 +581,11 @@ def demag_set_wait_limit(plan: Plan, seconds: float):
 
 def demag_set_fused(plan: Plan, enable: bool):
     _check(lib.demag_set_fused(plan.ptr, 1 if enable else 0), plan.ptr)
+
+
+def demag_forward_schedule(plan: Plan, precision="bf16x3") -> int:
+    """1 fused, 0 three-stage chain, -1 no tensor-core state for `precision` yet."""
+    return lib.demag_forward_schedule(plan.ptr, _prec(precision))
 
 
 def demag_autotune(plan: Plan, enable: bool = True):

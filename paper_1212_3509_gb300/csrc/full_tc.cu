@@ -757,11 +757,24 @@ struct S12Launch {
   int n2;                              // tile width of both products: h2 rounded up to 16
   int kb1, kb2;                        // k-blocks of the two contractions (ceil(h1 / 32), ceil(h2 / 32))
   int pxor1, pxor2;                    // 1 when axis 1 / 2 carries derivative factors (dE odd, dF even)
-  int units;                           // ext3 * M * 2
+  int units;                           // ext3 * M * 2 (batched: all items' units)
   int* unit_counter;                   // zeroed before the launch
   int* status;
   unsigned long long wait_ns;
+  // batched launch (several grids, units numbered item after item): the
+  // geometry and maps above come from items[i], the unit counter, status and
+  // wait limit from the launch; null for a single grid
+  const S12Launch* items;
+  const int* unit0;                    // first unit of each item, [count + 1]
+  int count;
 };
+
+// The launch that a unit of item `it` belongs to.
+template <bool BATCH>
+__device__ __forceinline__ const S12Launch& s12_item(const S12Launch& L, int it) {
+  if constexpr (BATCH) return L.items[it];
+  else return L;
+}
 
 // Chunk c of a unit: the field of X read by its mode-1 tile, the factor types
 // along axes 1 and 2, the input half hh of axis 2, and whether it starts /
@@ -817,7 +830,7 @@ __device__ __forceinline__ void split_pair(float a, float b, uint32_t& hi, uint3
   lo = *reinterpret_cast<const uint32_t*>(&l);
 }
 
-template <bool ADJ>
+template <bool ADJ, bool BATCH>
 __global__ void __launch_bounds__(kS12Threads, 2) tc_s12_kernel(const __grid_constant__ S12Launch L) {
   constexpr int kTargets = ADJ ? 6 : 4;  // mode-2 targets per unit
   constexpr int kZf = ADJ ? 3 : 2;       // Z fields per node
@@ -837,8 +850,9 @@ __global__ void __launch_bounds__(kS12Threads, 2) tc_s12_kernel(const __grid_con
   uint64_t* sfull = d2empty + 1;           // [kRing] unit ids
   uint64_t* sempty = sfull + kRing;
   uint64_t* drain = sempty + kRing;
-  volatile int* ring = reinterpret_cast<volatile int*>(drain + 1);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(const_cast<int*>(ring) + kRing);
+  volatile int* ring = reinterpret_cast<volatile int*>(drain + 1);  // [kRing] unit within its item
+  volatile int* ritem = ring + kRing;                                // [kRing] item of the unit
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(const_cast<int*>(ritem) + kRing);
   volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -881,6 +895,7 @@ __global__ void __launch_bounds__(kS12Threads, 2) tc_s12_kernel(const __grid_con
     uint32_t ph = 0;
     int rs = 0;
     uint32_t rph = 0;
+    int cur = 0;  // item of the last unit taken (batched launch)
     bool ok = true;
     // next operand slot (its previous contents consumed), or null after an abort
     auto take_slot = [&]() -> uint8_t* {
@@ -904,50 +919,60 @@ __global__ void __launch_bounds__(kS12Threads, 2) tc_s12_kernel(const __grid_con
         if (leader) tc_fail(abort, L.status);
         break;
       }
-      int u = 0;
+      int u = 0, it = 0;
       if (leader) {
         u = atomicAdd(L.unit_counter, 1);
-        ring[rs] = u < L.units ? u : -1;
+        if (u >= L.units) {
+          u = -1;
+        } else if (BATCH) {  // this CTA's units only grow: the item cursor only advances
+          while (cur + 1 < L.count && u >= L.unit0[cur + 1]) ++cur;
+          it = cur;
+          u -= L.unit0[cur];
+        }
+        ring[rs] = u;
+        ritem[rs] = it;
         ptx::mbar_arrive(&sfull[rs]);
       }
       u = __shfl_sync(0xffffffffu, u, 0);
+      it = __shfl_sync(0xffffffffu, it, 0);
       if (++rs == kRing) { rs = 0; rph ^= 1; }
-      if (u >= L.units) break;
-      const int h1o = u & 1, k = (u >> 1) % L.M, i3 = (u >> 1) / L.M;
+      if (u < 0) break;
+      const S12Launch& G = s12_item<BATCH>(L, it);
+      const int h1o = u & 1, k = (u >> 1) % G.M, i3 = (u >> 1) / G.M;
       for (int c = 0; c < 6 && ok; ++c) {
         const S12Chunk ch = s12_chunk<ADJ>(c);
         const int q = ch.xf, hh = ch.hh, type1 = ch.type1;
         // mode 1: factor block of (k, type) and h2 rows of X_q (input half hh of axis 2)
-        const int off1 = ((h1o ^ type1 ^ L.pxor1) & 1) * L.hq1;  // input half of axis 1
-        const int row = i3 * L.x2 + hh * L.hq2;
-        for (int kb = 0; kb < L.kb1 && ok; ++kb) {
+        const int off1 = ((h1o ^ type1 ^ G.pxor1) & 1) * G.hq1;  // input half of axis 1
+        const int row = i3 * G.x2 + hh * G.hq2;
+        for (int kb = 0; kb < G.kb1 && ok; ++kb) {
           uint8_t* a = take_slot();
           if (!a) break;
           if (leader) {
             ptx::mbar_arrive_expect_tx(&full[s], 2 * kTileA);
-            ptx::tma_load_4d(a, &L.t1_hi, &full[s], kb * 32, 0, h1o, 2 * k + type1);
-            ptx::tma_load_4d(a + kTileA, &L.t1_lo, &full[s], kb * 32, 0, h1o, 2 * k + type1);
+            ptx::tma_load_4d(a, &G.t1_hi, &full[s], kb * 32, 0, h1o, 2 * k + type1);
+            ptx::tma_load_4d(a + kTileA, &G.t1_lo, &full[s], kb * 32, 0, h1o, 2 * k + type1);
           }
           next_slot();
           uint8_t* b = take_slot();
           if (!b) break;
           if (leader) {
-            ptx::mbar_arrive_expect_tx(&full[s], 2 * L.n2 * kRowBytes);
-            ptx::tma_load_3d(b, &L.x_hi, &full[s], off1 + kb * 32, row, q);
-            ptx::tma_load_3d(b + kTileA, &L.x_lo, &full[s], off1 + kb * 32, row, q);
+            ptx::mbar_arrive_expect_tx(&full[s], 2 * G.n2 * kRowBytes);
+            ptx::tma_load_3d(b, &G.x_hi, &full[s], off1 + kb * 32, row, q);
+            ptx::tma_load_3d(b + kTileA, &G.x_lo, &full[s], off1 + kb * 32, row, q);
           }
           next_slot();
         }
         // mode 2: factor block of (k, type, h2o)
         const int type2 = ch.type2;
-        for (int kb = 0; kb < L.kb2 && ok; ++kb) {
+        for (int kb = 0; kb < G.kb2 && ok; ++kb) {
           uint8_t* b = take_slot();
           if (!b) break;
           if (leader) {
-            ptx::mbar_arrive_expect_tx(&full[s], 2 * L.n2 * kRowBytes);
+            ptx::mbar_arrive_expect_tx(&full[s], 2 * G.n2 * kRowBytes);
             // the block of the output half h2o = hh ^ type (^ 1 for derivative factors)
-            ptx::tma_load_4d(b, &L.t2_hi, &full[s], kb * 32, 0, hh ^ type2 ^ L.pxor2, 2 * k + type2);
-            ptx::tma_load_4d(b + kTileA, &L.t2_lo, &full[s], kb * 32, 0, hh ^ type2 ^ L.pxor2, 2 * k + type2);
+            ptx::tma_load_4d(b, &G.t2_hi, &full[s], kb * 32, 0, hh ^ type2 ^ G.pxor2, 2 * k + type2);
+            ptx::tma_load_4d(b + kTileA, &G.t2_lo, &full[s], kb * 32, 0, hh ^ type2 ^ G.pxor2, 2 * k + type2);
           }
           next_slot();
         }
@@ -962,7 +987,6 @@ __global__ void __launch_bounds__(kS12Threads, 2) tc_s12_kernel(const __grid_con
     uint32_t rph = 0;
     uint32_t t = 0, yc = 0, g = 0;  // mode-1 tiles, Y k-blocks consumed, mode-2 targets completed
     bool ok = true;
-    const uint32_t idesc = ptx::instr_desc(1, kBM, (uint32_t)L.n2);
     const uint32_t d1 = tmem_base, d2 = tmem_base + 128;
     // the next operand slot once its loads have landed (index in `idx`)
     auto take_full = [&](int& idx) -> uint32_t {
@@ -985,11 +1009,14 @@ __global__ void __launch_bounds__(kS12Threads, 2) tc_s12_kernel(const __grid_con
         if (leader) tc_fail(abort, L.status);
         break;
       }
-      const int u = ring[rs];
+      const int u = ring[rs], it = ritem[rs];
       __syncwarp();
       if (leader) ptx::mbar_arrive(&sempty[rs]);
       if (++rs == kRing) { rs = 0; rph ^= 1; }
       if (u < 0) break;
+      const S12Launch& G = s12_item<BATCH>(L, it);
+      const int kb1 = G.kb1, kb2 = G.kb2;
+      const uint32_t idesc = ptx::instr_desc(1, kBM, (uint32_t)G.n2);
       for (int c = 0; c < 6 && ok; ++c) {
         // mode 1 into the mode-1 accumulator, once the previous tile is read out
         if (!ptx::mbar_wait_warp(d1empty, (t & 1) ^ 1, abort, L.wait_ns)) {
@@ -998,7 +1025,7 @@ __global__ void __launch_bounds__(kS12Threads, 2) tc_s12_kernel(const __grid_con
           break;
         }
         ptx::tc_fence_after();
-        for (int kb = 0; kb < L.kb1 && ok; ++kb) {
+        for (int kb = 0; kb < kb1 && ok; ++kb) {
           int ia = 0, ib = 0;
           const uint32_t sa = take_full(ia);
           const uint32_t sb = ok ? take_full(ib) : 0;
@@ -1036,7 +1063,7 @@ __global__ void __launch_bounds__(kS12Threads, 2) tc_s12_kernel(const __grid_con
           }
           ptx::tc_fence_after();
         }
-        for (int kb = 0; kb < L.kb2 && ok; ++kb) {
+        for (int kb = 0; kb < kb2 && ok; ++kb) {
           const uint32_t ys = yc % kS12Y;
           if (!ptx::mbar_wait_warp(&yfull[ys], (yc / kS12Y) & 1, abort, L.wait_ns)) {
             if (leader) tc_fail(abort, L.status);
@@ -1094,11 +1121,13 @@ __global__ void __launch_bounds__(kS12Threads, 2) tc_s12_kernel(const __grid_con
         tc_fail(abort, L.status);
         break;
       }
-      const int u = ring[rs];
+      const int u = ring[rs], it = ritem[rs];
       __syncwarp();
       if (lane == 0) ptx::mbar_arrive(&sempty[rs]);
       if (++rs == kRing) { rs = 0; rph ^= 1; }
       if (u < 0) break;
+      const S12Launch& G = s12_item<BATCH>(L, it);
+      const int kb2 = G.kb2, h2 = G.h2;
       for (int c = 0; c < 6 && ok; ++c) {
         if (!ptx::mbar_wait(d1full, t & 1, abort, L.wait_ns)) {
           tc_fail(abort, L.status);
@@ -1106,7 +1135,7 @@ __global__ void __launch_bounds__(kS12Threads, 2) tc_s12_kernel(const __grid_con
           break;
         }
         ptx::tc_fence_after();
-        for (int kb = 0; kb < L.kb2; ++kb) {
+        for (int kb = 0; kb < kb2; ++kb) {
           uint32_t v[32];
           ptx::tmem_ld32(taddr + (uint32_t)(kb * 32), v);
           const uint32_t ys = yc % kS12Y;
@@ -1117,14 +1146,14 @@ __global__ void __launch_bounds__(kS12Threads, 2) tc_s12_kernel(const __grid_con
             break;
           }
           ptx::tmem_ld_wait(v);
-          if (kb + 1 == L.kb2) {  // the accumulator is read: the next mode-1 tile may start
+          if (kb + 1 == kb2) {  // the accumulator is read: the next mode-1 tile may start
             ptx::tc_fence_before();
             __syncwarp();
             if (lane == 0) ptx::mbar_arrive(d1empty);
             // columns i2 >= h2: rows of the next half or never written; zero
             // them, so that Y holds only finite entries (their factor columns
             // read as zeros)
-            const int lim = L.h2 - kb * 32;
+            const int lim = h2 - kb * 32;
 #pragma unroll
             for (int j = 0; j < 32; ++j)
               if (j >= lim) v[j] = 0u;
@@ -1165,13 +1194,14 @@ __global__ void __launch_bounds__(kS12Threads, 2) tc_s12_kernel(const __grid_con
         tc_fail(abort, L.status);
         break;
       }
-      const int u = ring[rs];
+      const int u = ring[rs], it = ritem[rs];
       __syncwarp();
       if (lane == 0) ptx::mbar_arrive(&sempty[rs]);
       if (++rs == kRing) { rs = 0; rph ^= 1; }
       if (u < 0) break;
-      const int h1o = u & 1, k = (u >> 1) % L.M, i3 = (u >> 1) / L.M;
-      const bool valid = quad * 32 < L.h1;  // rows past h1 are zero and not stored
+      const S12Launch& G = s12_item<BATCH>(L, it);
+      const int h1o = u & 1, k = (u >> 1) % G.M, i3 = (u >> 1) / G.M;
+      const bool valid = quad * 32 < G.h1;  // rows past h1 are zero and not stored
       for (int j = 0; j < kTargets && ok; ++j) {
         if (!ptx::mbar_wait(d2full, g & 1, abort, L.wait_ns)) {
           tc_fail(abort, L.status);
@@ -1180,9 +1210,9 @@ __global__ void __launch_bounds__(kS12Threads, 2) tc_s12_kernel(const __grid_con
         }
         ptx::tc_fence_after();
         int tf, h2o;
-        s12_target<ADJ>(j, L.pxor2, tf, h2o);
-        const int zf = i3 + L.x3 * (kZf * k + tf);
-        for (int c0 = 0; c0 < L.h2; c0 += 32) {
+        s12_target<ADJ>(j, G.pxor2, tf, h2o);
+        const int zf = i3 + G.x3 * (kZf * k + tf);
+        for (int c0 = 0; c0 < G.h2; c0 += 32) {
           uint32_t v[32];
           ptx::tmem_ld32(taddr + (uint32_t)c0, v);
           ptx::tmem_ld_wait(v);
@@ -1203,7 +1233,7 @@ __global__ void __launch_bounds__(kS12Threads, 2) tc_s12_kernel(const __grid_con
             __syncwarp();
             if (lane == 0) {
               // (a1 in the half, output half of axis 1, a2 in the target's half, its half, field)
-              ptx::tma_store_5d(pl ? &L.z_lo : &L.z_hi, stg, quad * 32, h1o, c0, h2o, zf);
+              ptx::tma_store_5d(pl ? &G.z_lo : &G.z_hi, stg, quad * 32, h1o, c0, h2o, zf);
               ptx::bulk_commit();
             }
           }
@@ -1963,6 +1993,10 @@ struct TcBatch {
   int* ctr = nullptr;                  // device [1 + 2 count]: tile counter, then stage-done counters
   int nctr = 0;
   int maxbn = 16;                      // widest N tile of all groups
+  std::vector<char> fused;             // per plan: the fused schedule (part of the cache key)
+  S12Launch* s12items = nullptr;       // device [s12count]: the fused grids' mode-1/mode-2 launches
+  int* s12unit0 = nullptr;             // device [s12count + 1]: first unit of each
+  int s12count = 0, s12units = 0;
 };
 
 struct TcHolder {
@@ -2312,8 +2346,12 @@ static demag_status prepare_form(demag_plan* P, TcState* S, cudaStream_t st) {
   const unsigned long long bit = 1ull << (dev & 63);
   if (!(attr & bit)) {
     DEMAG_CUDA(P, cudaFuncSetAttribute(tc_gemm_kernel<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax));
-    DEMAG_CUDA(P, cudaFuncSetAttribute(tc_s12_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kS12Smem));
-    DEMAG_CUDA(P, cudaFuncSetAttribute(tc_s12_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kS12Smem));
+    DEMAG_CUDA(P, cudaFuncSetAttribute(tc_s12_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       kS12Smem));
+    DEMAG_CUDA(P, cudaFuncSetAttribute(tc_s12_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       kS12Smem));
+    DEMAG_CUDA(P, cudaFuncSetAttribute(tc_s12_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       kS12Smem));
     attr |= bit;
   }
   return DEMAG_OK;
@@ -2895,15 +2933,18 @@ static demag_status run_s12(demag_plan* P, TcState* S, const S12Launch& base, cu
   L.unit_counter = S->counter;
   L.status = S->status;
   L.wait_ns = P->wait_ns;
+  L.items = nullptr;
+  L.unit0 = nullptr;
+  L.count = 1;
   int sms = 0, dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int grid = L.units < 2 * sms ? L.units : 2 * sms;  // two CTAs per SM
   DEMAG_CUDA(P, cudaMemsetAsync(S->counter, 0, sizeof(int), st));
   if (adj)
-    DEMAG_LAUNCH(P, kFamGemmTc, st, tc_s12_kernel<true><<<grid, kS12Threads, kS12Smem, st>>>(L));
+    DEMAG_LAUNCH(P, kFamGemmTc, st, tc_s12_kernel<true, false><<<grid, kS12Threads, kS12Smem, st>>>(L));
   else
-    DEMAG_LAUNCH(P, kFamGemmTc, st, tc_s12_kernel<false><<<grid, kS12Threads, kS12Smem, st>>>(L));
+    DEMAG_LAUNCH(P, kFamGemmTc, st, tc_s12_kernel<false, false><<<grid, kS12Threads, kS12Smem, st>>>(L));
   DEMAG_LAUNCHED(P, "tc_s12_kernel");
   return DEMAG_OK;
 }
@@ -2955,12 +2996,22 @@ void tc_batch_destroy(TcBatch* B) {
   cudaFree(B->groups);
   cudaFree(B->segs);
   cudaFree(B->ctr);
+  cudaFree(B->s12items);
+  cudaFree(B->s12unit0);
   delete B;
 }
 
+// Whether a plan's forward application takes the fused schedule.
+static bool fused_schedule(const demag_plan* P, const TcState* S) {
+  return S->fused && (P->fused > 0 || (P->fused < 0 && S->sched));
+}
+
 // One launch for every forward stage of `plans` (distinct, with their
-// tensor-core state for `prec`): the tiles of stage 1 of all grids, largest
-// grids first, then stage 2, then stage 3.  Stage s of a grid waits for the
+// tensor-core state for `prec`): the tiles of stage 1 of all grids that run
+// the chain, largest grids first, then the mode-3 stages of the grids that run
+// the fused schedule (their mode-1 / mode-2 products ran before, in one
+// tc_s12_kernel launch over all of them, largest first), then stage 2 and
+// stage 3 of the chain grids.  Stage s of a chain grid waits for the
 // completion counter of its stage s - 1 (every epilogue warp of every tile of
 // that stage counts once); in this order the wait is met long before, except
 // for the last grids of a stage.  (Interleaving the stages of different grids
@@ -2983,20 +3034,42 @@ demag_status tc_batch_create(demag_plan* const* plans, int count, demag_precisio
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cells(a) > cells(b); });
   std::vector<TcGroup> g(3 * (size_t)count);
   std::vector<TcSeg> segs;
+  std::vector<S12Launch> items;
+  std::vector<int> unit0(1, 0);
+  B->fused.resize(count);
+  for (int i = 0; i < count; ++i) {
+    const TcState* S = state(plans[i], prec);
+    B->fused[i] = fused_schedule(plans[i], S) ? 1 : 0;
+  }
+  for (int i = 0; i < count; ++i) {
+    const TcState* S = state(plans[order[i]], prec);
+    for (int st3 = 0; st3 < 3; ++st3) {
+      g[st3 * count + i] = S->host_prog[kFwd1 + st3];
+      g[st3 * count + i].o_wide = 0;  // the groups of one launch share the staging: per-warp boxes for all
+    }
+    if (B->fused[order[i]]) {  // slot 0 holds its mode-3 stage on Z
+      g[i] = S->host_prog[kFwd3Z];
+      g[i].o_wide = 0;
+      items.push_back(S->s12);
+      unit0.push_back(unit0.back() + S->s12.units);
+    }
+  }
   int acc = 0;
-  for (int st3 = 0; st3 < 3; ++st3) {
+  // passes: chain stage 1, fused mode-3 stages, chain stages 2 and 3
+  for (int pass = 0; pass < 4; ++pass) {
     for (int i = 0; i < count; ++i) {
+      const bool fz = B->fused[order[i]] != 0;
+      if (fz != (pass == 1)) continue;
       const TcState* S = state(plans[order[i]], prec);
-      const int gi = st3 * count + i;
-      g[gi] = S->host_prog[kFwd1 + st3];
-      g[gi].o_wide = 0;  // the groups of one launch share the staging: per-warp boxes for all
+      const int st3 = pass == 0 ? 0 : pass - 1;
+      const int gi = fz ? i : st3 * count + i;
       if (g[gi].ntiles <= 0) continue;
       TcSeg q = whole_seg(g[gi], gi, acc);
-      if (st3 > 0) {
+      if (!fz && st3 > 0) {
         q.dep = 2 * i + (st3 - 1);
         q.dep_target = kEpiWarps * S->host_prog[kFwd1 + st3 - 1].ntiles;
       }
-      if (st3 < 2) q.done = 2 * i + st3;
+      if (!fz && st3 < 2) q.done = 2 * i + st3;
       segs.push_back(q);
       acc += g[gi].ntiles;
     }
@@ -3005,15 +3078,23 @@ demag_status tc_batch_create(demag_plan* const* plans, int count, demag_precisio
   B->nsegs = (int)segs.size();
   B->total = acc;
   B->nctr = 2 * count;
+  B->s12count = (int)items.size();
+  B->s12units = unit0.back();
   if (cudaMalloc(&B->groups, sizeof(TcGroup) * g.size()) != cudaSuccess ||
       cudaMalloc(&B->segs, sizeof(TcSeg) * (segs.size() ? segs.size() : 1)) != cudaSuccess ||
-      cudaMalloc(&B->ctr, sizeof(int) * (1 + B->nctr)) != cudaSuccess) {
+      cudaMalloc(&B->ctr, sizeof(int) * (1 + B->nctr)) != cudaSuccess ||
+      (B->s12count > 0 && (cudaMalloc(&B->s12items, sizeof(S12Launch) * items.size()) != cudaSuccess ||
+                           cudaMalloc(&B->s12unit0, sizeof(int) * unit0.size()) != cudaSuccess))) {
     tc_batch_destroy(B);
     return set_error(P0, DEMAG_ENOMEM, "grouped launch descriptors: allocation failed");
   }
   cudaError_t e = cudaMemcpy(B->groups, g.data(), sizeof(TcGroup) * g.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess && !segs.empty())
     e = cudaMemcpy(B->segs, segs.data(), sizeof(TcSeg) * segs.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && B->s12count > 0)
+    e = cudaMemcpy(B->s12items, items.data(), sizeof(S12Launch) * items.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && B->s12count > 0)
+    e = cudaMemcpy(B->s12unit0, unit0.data(), sizeof(int) * unit0.size(), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
     tc_batch_destroy(B);
     return cuda_error(P0, e, "grouped launch descriptors");
@@ -3023,9 +3104,10 @@ demag_status tc_batch_create(demag_plan* const* plans, int count, demag_precisio
 }
 
 // Several grids in one call: one split launch over every plan's input, one
-// persistent launch over all stages of all grids, one node-sum reduction
-// launch into every plan's phi (per kMaxItems grids for the element-wise
-// launches).
+// fused mode-1 / mode-2 launch over the grids with the fused schedule, one
+// persistent launch over all remaining stages of all grids, one node-sum
+// reduction launch into every plan's phi (per kMaxItems grids for the
+// element-wise launches).
 template <class F>
 static demag_status batched_chain(const TcBatch* B, const float* const* m, float* const* phi, cudaStream_t st) {
   const demag_precision prec = (demag_precision)B->prec;
@@ -3037,6 +3119,24 @@ static demag_status batched_chain(const TcBatch* B, const float* const* m, float
     for (int i = i0; i < count && i < i0 + kMaxItems; ++i) add_split(L, B->plans[i], state(B->plans[i], prec), m[i], 3);
     demag_status s = launch_split<F>(P0, L, st);
     if (s != DEMAG_OK) return s;
+  }
+  if (B->s12count > 0) {
+    S12Launch L;
+    memset(&L, 0, sizeof(L));
+    L.units = B->s12units;
+    L.unit_counter = B->ctr;  // zeroed again by the persistent launch below
+    L.status = S0->status;
+    L.wait_ns = P0->wait_ns;
+    L.items = B->s12items;
+    L.unit0 = B->s12unit0;
+    L.count = B->s12count;
+    int sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = L.units < 2 * sms ? L.units : 2 * sms;  // two CTAs per SM
+    DEMAG_CUDA(P0, cudaMemsetAsync(B->ctr, 0, sizeof(int), st));
+    DEMAG_LAUNCH(P0, kFamGemmTc, st, tc_s12_kernel<false, true><<<grid, kS12Threads, kS12Smem, st>>>(L));
+    DEMAG_LAUNCHED(P0, "tc_s12_kernel");
   }
   demag_status s = launch_segs<F>(P0, B->groups, B->segs, B->nsegs, B->total, B->maxbn, B->ctr, B->ctr + 1,
                                   B->nctr, S0->status, st);
@@ -3063,7 +3163,9 @@ demag_status tc_forward_batched(demag_plan* const* plans, const float* const* m,
   TcHolder* H = reinterpret_cast<TcHolder*>(plans[0]->tc);
   TcBatch* B = H->cache;
   bool hit = B && B->prec == (int)prec && (int)B->plans.size() == count;
-  for (int i = 0; hit && i < count; ++i) hit = B->plans[i] == plans[i] && B->serials[i] == plans[i]->serial;
+  for (int i = 0; hit && i < count; ++i)
+    hit = B->plans[i] == plans[i] && B->serials[i] == plans[i]->serial &&
+          B->fused[i] == (fused_schedule(plans[i], state(plans[i], prec)) ? 1 : 0);
   if (!hit) {
     tc_batch_destroy(H->cache);
     H->cache = nullptr;
@@ -3220,5 +3322,10 @@ demag_status tc_sync_status(demag_plan* P, cudaStream_t st) {
 }
 
 bool tc_ready(const demag_plan* P, demag_precision prec) { return state(const_cast<demag_plan*>(P), prec) != nullptr; }
+
+int tc_forward_schedule(const demag_plan* P, demag_precision prec) {
+  const TcState* S = state(const_cast<demag_plan*>(P), prec);
+  return S ? (fused_schedule(P, S) ? 1 : 0) : -1;
+}
 
 }  // namespace demag

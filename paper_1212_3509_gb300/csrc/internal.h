@@ -177,6 +177,8 @@ demag_status tc_forward_batched(demag_plan* const* plans, const float* const* m,
 size_t tc_workspace_bytes(const demag_plan* plan, demag_precision prec);
 demag_status tc_sync_status(demag_plan* plan, cudaStream_t st);
 bool tc_ready(const demag_plan* plan, demag_precision prec);
+// forward schedule of a prepared plan: 1 fused, 0 three-stage chain, -1 no tensor-core state
+int tc_forward_schedule(const demag_plan* plan, demag_precision prec);
 void tc_destroy(demag_plan* plan);
 
 // compressed kernels (compress.cu)

@@ -556,6 +556,11 @@ extern "C" demag_status demag_set_fused(demag_plan* plan, int enable) {
   return DEMAG_OK;
 }
 
+extern "C" int demag_forward_schedule(const demag_plan* plan, demag_precision prec) {
+  if (!plan || (prec != DEMAG_BF16X3 && prec != DEMAG_TF32X3)) return -1;
+  return tc_forward_schedule(plan, prec);
+}
+
 extern "C" demag_status demag_autotune(demag_plan* plan, int enable) {
   if (!plan) return set_error(nullptr, DEMAG_EINVAL, "demag_autotune: plan is NULL");
   plan->autotune = enable != 0;

@@ -79,5 +79,8 @@ def test_null_arguments_are_rejected(lib):
     lib.demag_set_fused.restype = ctypes.c_int
     lib.demag_set_fused.argtypes = [ctypes.c_void_p, ctypes.c_int]
     assert lib.demag_set_fused(None, 1) == 1
+    lib.demag_forward_schedule.restype = ctypes.c_int
+    lib.demag_forward_schedule.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    assert lib.demag_forward_schedule(None, 3) == -1
     lib.demag_plan_destroy.argtypes = [ctypes.c_void_p]
     lib.demag_plan_destroy(None)

@@ -71,6 +71,21 @@ def test_fused_vs_oracle_and_chain(D, n, h, R):
     assert_close(fused, chain, 2 * TOL["bf16x3"], "fused vs chain")
 
 
+def test_untuned_schedule_follows_grid_size(D):
+    """Untuned, a grid of at least 2^20 cells in the folded layout takes the fused
+    schedule and a smaller one the chain; demag_set_fused overrides both ways;
+    a grid with a short axis has the chain only."""
+    for n, want in (((96, 96, 96), 0), ((128, 96, 96), 1), ((128, 128, 12), 0)):
+        P = D.demag_build_factors(n, (1 / max(n),) * 3, 11)
+        assert D.demag_forward_schedule(P, "bf16x3") == -1  # no tensor-core state yet
+        D.demag_reserve_workspace(P, "bf16x3")
+        assert D.demag_forward_schedule(P, "bf16x3") == want, n
+        D.demag_set_fused(P, True)
+        assert D.demag_forward_schedule(P, "bf16x3") == (0 if min(n) <= 16 else 1)
+        D.demag_set_fused(P, False)
+        assert D.demag_forward_schedule(P, "bf16x3") == 0
+
+
 def test_fused_repeated_calls_are_identical(D):
     n, h, R = (128, 128, 40), (1 / 128,) * 3, 21
     m = dev(synth.random_unit_m(n, 7))
@@ -170,3 +185,52 @@ def test_fused_forward_and_adjoint_graph_capturable(D):
     torch.cuda.synchronize()
     D.demag_sync_status(P)
     assert torch.equal(a, b) and torch.equal(ga, gb)
+
+
+def test_fused_batch_equals_single_applies(D):
+    """A batch mixing both schedules: one fused mode-1 / mode-2 launch over the
+    grids with the fused schedule (largest first; halves of 40, 64 / 32 and
+    19 / 23 entries), whose mode-3 stages run inside the persistent launch
+    beside the chain grids' three stages.  Every tile runs the MMA sequence of
+    the grid's own call, so each output equals that call bit for bit (a thin
+    film, on CUDA cores in its own call, to the split-form tolerance); the
+    captured graph of the batch replays the same bits."""
+    cases = [((80, 80, 80), (1 / 80,) * 3, 21, True),
+             ((48, 40, 37), (1 / 48,) * 3, 21, False),
+             ((128, 64, 40), (1 / 128,) * 3, 21, True),
+             ((37, 45, 33), (0.03, 0.02, 0.03), 11, True),
+             ((96, 64, 8), (1 / 96,) * 3, 21, True)]   # axis 3 not folded: the chain
+    plans, ms, single = [], [], []
+    for i, (n, h, R, fused) in enumerate(cases):
+        P = D.demag_build_factors(n, h, R)
+        D.demag_set_fused(P, fused)
+        m = dev(synth.random_unit_m(n, 9100 + i))
+        phi = torch.empty(n[2], n[1], n[0], device="cuda")
+        D.demag_apply_full(P, m, phi, "bf16x3")
+        plans.append(P)
+        ms.append(m)
+        single.append(phi)
+    assert [D.demag_forward_schedule(P, "bf16x3") for P in plans] == [1, 0, 1, 1, 0]
+    before = D.demag_launch_count(plans[0])
+    outs = [torch.full_like(p, float("nan")) for p in single]
+    D.demag_apply_full_batched(plans, ms, outs, "bf16x3")
+    torch.cuda.synchronize()
+    for P in plans:
+        D.demag_sync_status(P)
+    # split, fused mode-1 / mode-2 products, persistent launch, reduction
+    assert D.demag_launch_count(plans[0]) - before == 4
+    for (n, _, _, _), got, ref in zip(cases, outs, single):
+        if min(n) > 16:
+            assert torch.equal(got, ref), n
+        else:
+            assert_close(host(got), host(ref), TOL["bf16x3"], n)
+    n, h, R, _ = cases[3]
+    assert_close(host(outs[3]), ofull.apply_full(host(ms[3]), n, h, R), TOL["bf16x3"], "ragged halves in the batch")
+    gouts = [torch.full_like(p, float("nan")) for p in single]
+    G = D.demag_graph_create_batched(plans, ms, gouts, "bf16x3")
+    assert G.kernels == 4
+    G.launch()
+    torch.cuda.synchronize()
+    for got, want in zip(gouts, outs):
+        assert torch.equal(got, want)
+    G.close()
