@@ -722,7 +722,8 @@ def run_fig2(args, D, stream, sizes=(64, 128, 256, 512, 1024, 2048, 4096), tol=1
     import torch
     out = {"tol": tol, "sizes": list(sizes), "R_rule": "smallest M in {64, 128, 256} with sinh(c0 ln M) >= 8 n",
            "rows": [],
-           "work": "demag_apply_tucker + demag_energy_tucker (rank 1); Alg. 2: demag_compress_kernel, "
+           "work": "demag_apply_tucker + demag_energy_tucker (rank 1, FP32 factors); fp64: "
+                   "demag_energy_tucker_fp64 (FP64 Tucker application and energy); Alg. 2: demag_compress_kernel, "
                    "demag_apply_tucker_compressed, demag_recompress_tucker, demag_energy_tucker_phi (R = 129)"}
     ranks = (1, 1, 1)
     for n in sizes:
@@ -744,6 +745,16 @@ def run_fig2(args, D, stream, sizes=(64, 128, 256, 512, 1024, 2048, 4096), tol=1
         ms = time_region(fn, 20, stream)
         e = float(E.item())
         row = {"n": n, "R": R, "energy": e, "rel_err": abs(e - 1.0 / 6.0) * 6.0, "ms_apply_energy": ms}
+        # the same energy with the Tucker application in FP64 (direct Toeplitz sums)
+        core64, V64 = core.double(), V.double()
+
+        def fn64():
+            D.demag_energy_tucker_fp64(P, ranks, core64, V64, E)
+        fn64()
+        torch.cuda.synchronize()
+        ms64 = time_region(fn64, 3, stream)
+        e64 = float(E.item())
+        row["fp64"] = {"energy": e64, "rel_err": abs(e64 - 1.0 / 6.0) * 6.0, "ms_apply_energy": ms64}
         del P
         try:
             P2 = D.demag_build_factors((n, n, n), (1.0 / n,) * 3, 129)
@@ -766,6 +777,20 @@ def run_fig2(args, D, stream, sizes=(64, 128, 256, 512, 1024, 2048, 4096), tol=1
     errs = [r["rel_err"] for r in out["rows"]]
     out["order_per_doubling"] = [math.log2(errs[i] / errs[i + 1]) if errs[i + 1] > 0 else None
                                  for i in range(len(errs) - 1)]
+    e64 = [r["fp64"]["rel_err"] for r in out["rows"]]
+    out["fp64_order_per_doubling"] = [math.log2(e64[i] / e64[i + 1]) if e64[i + 1] > 0 else None
+                                      for i in range(len(e64) - 1)]
+    # the same energies by the FP64 oracle's one-dimensional sums (after the timed work): what
+    # the method gives without the FP32 factors, and how far the GPU values are from it
+    from oracle import energy as oen
+    oerr = []
+    for r in out["rows"]:
+        eo = oen.uniform_cube_energy(r["n"], r["R"])
+        r["oracle_fp64"] = {"energy": eo, "rel_err": abs(eo - 1.0 / 6.0) * 6.0,
+                            "gpu_minus_oracle_rel": (r["energy"] - eo) / eo,
+                            "fp64_minus_oracle_rel": (r["fp64"]["energy"] - eo) / eo}
+        oerr.append(r["oracle_fp64"]["rel_err"])
+    out["oracle_order_per_doubling"] = [math.log2(oerr[i] / oerr[i + 1]) for i in range(len(oerr) - 1)]
     a2 = [r["alg2"].get("rel_err") for r in out["rows"]]
     out["alg2_order_per_doubling"] = [math.log2(a2[i] / a2[i + 1]) if a2[i] and a2[i + 1] else None
                                       for i in range(len(a2) - 1)]

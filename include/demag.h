@@ -426,6 +426,20 @@ demag_status demag_energy_tucker_phi(demag_plan* plan, const int r[3], const flo
                                      const int rho[3], const float* phi_core, const float* phi_U,
                                      double* energy, void* stream);
 
+/* The energy of demag_energy_tucker with the Tucker application done here in
+ * FP64 (the energy study after Alg. 2 on fine grids, where the FP32 factors of
+ * demag_apply_tucker leave the energy about 5e-7 off): every factor
+ * T_{k,q,p} V^(q,p) of Eq. kron_eval_tuck (E off the component's axis, F on
+ * it) is summed directly from the plan's FP64 generators, O(n_p^2) per column,
+ * then the Grams and the core contraction run in FP64.  core double
+ * [3][r3][r2][r1]; V double blocks (q, p) [r_p][n_p]; r[3] in [1, 64]; energy:
+ * one double on the device (overwritten).  Uniform grids with at most 8533
+ * cells per axis (DEMAG_EUNSUPPORTED beyond); device memory for the factors is
+ * taken and returned on the stream (cudaMallocAsync).  No counterpart in the
+ * paper beyond its energy study. */
+demag_status demag_energy_tucker_fp64(demag_plan* plan, const int r[3], const double* core, const double* V,
+                                      double* energy, void* stream);
+
 /* Second-order finite-difference stray field h_d = -D phi: central
  * differences inside, 3-point one-sided at the first and last cell of each
  * axis (two-point for n_p = 2, zero for n_p = 1).

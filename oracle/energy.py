@@ -113,3 +113,53 @@ def energy_tt(G1, G2, G3, n, ranks, h, R: int, c0: float = 2.15) -> float:
     phi = ost.tt_output_to_full(w, o1, o2, o3, ranks)
     m = np.stack([ost.tt_to_full(G1[q], G2[q], G3[q], ranks) for q in range(3)])
     return energy(m, phi, h)
+
+
+def fd_column_sums(n: int, hp: float) -> np.ndarray:
+    """1^T D for the stencils of fd_matrix, in O(n) (no dense matrix)."""
+    cs = np.zeros(n)
+    if n == 1:
+        return cs
+    if n == 2:
+        cs[0], cs[1] = -2.0 / hp, 2.0 / hp
+        return cs
+    cs[0:3] += np.array([-3.0, 4.0, -1.0]) / (2.0 * hp)
+    cs[n - 3:n] += np.array([1.0, -4.0, 3.0]) / (2.0 * hp)
+    i = np.arange(1, n - 1)
+    np.add.at(cs, i - 1, -0.5 / hp)
+    np.add.at(cs, i + 1, 0.5 / hp)
+    return cs
+
+
+def uniform_cube_energy(n: int, R: int, c0: float = 2.15) -> float:
+    """Energy of the unit cube of n^3 cells magnetized along axis 3 (the case of the
+    energy study after Alg. 2), by one-dimensional sums, so n can reach thousands.
+
+    m = e3 is the rank-1 Tucker tensor 1 x 1 x 1 in component 3, so Eq. kron_eval_tuck
+    gives phi = sum_k w_k (E_k 1) x (E_k 1) x (F_k 1) with w_k = c s omega_k (s = 1 on
+    the unit cube; E along axes 1 and 2, F along axis 3, the component's own axis), and
+    the second-order energy E = -1/2 h^3 sum m . h_d = 1/2 h^3 sum_i (D_3 phi)_i
+    factorises into
+        E = 1/2 h^3 sum_k w_k (1^T E_k 1)^2 (1^T D F_k 1),
+    with 1^T E_k 1 = sum_d (n - |d|) E_k[d] and F_k 1 the prefix sums of the generator
+    F_k[d].  Pinned against energy_tucker (the dense route) on small cubes."""
+    from .full import C_POT
+    from .generators import gen_E, gen_F
+    from .quadrature import sinc_nodes
+
+    if R < 5 or R % 2 == 0:
+        raise ValueError("R must be odd and >= 5")
+    M = (R - 1) // 2
+    h = 1.0 / n
+    _, _, tau, omega = sinc_nodes(M, c0)
+    cs = fd_column_sums(n, h)
+    d = np.arange(-(n - 1), n)
+    mult = (n - np.abs(d)).astype(np.float64)
+    i = np.arange(n)
+    total = 0.0
+    for k in range(M):
+        sE = float(mult @ gen_E(tau[k], h, n))
+        prefix = np.concatenate([[0.0], np.cumsum(gen_F(tau[k], h, n))])
+        F1 = prefix[i + n] - prefix[i]  # (F 1)_i = sum_{j < n} F[i - j], generator index i - j + n - 1
+        total += C_POT * omega[k] * sE * sE * float(cs @ F1)
+    return 0.5 * h ** 3 * total

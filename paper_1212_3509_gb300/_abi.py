@@ -85,6 +85,7 @@ _SIGS = {
     "demag_energy_tucker": (_i, [_vp, ctypes.POINTER(_i), _vp, _vp, _vp, _vp, _vp, _vp]),
     "demag_energy_tt": (_i, [_vp, ctypes.POINTER(_i), _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "demag_energy_tucker_phi": (_i, [_vp, ctypes.POINTER(_i), _vp, _vp, ctypes.POINTER(_i), _vp, _vp, _vp, _vp]),
+    "demag_energy_tucker_fp64": (_i, [_vp, ctypes.POINTER(_i), _vp, _vp, _vp, _vp]),
     "demag_stray_field": (_i, [_vp, _vp, _vp, _vp]),
     "demag_stray_field_exact": (_i, [_vp, _vp, _vp, _i, _vp]),
     "demag_energy": (_i, [_vp, _vp, _vp, _vp, _i, _vp]),
@@ -531,6 +532,19 @@ def demag_energy_tucker(plan: Plan, ranks, core, V, out_w, out_V, energy, stream
                                    _ptr(V, 3 * tot, f32, "V"), _ptr(out_w, plan.M * 3, f32, "out_w"),
                                    _ptr(out_V, plan.M * 3 * tot, f32, "out_V"),
                                    _ptr(energy, 1, torch.float64, "energy"), _stream(stream)), plan.ptr)
+
+
+def demag_energy_tucker_fp64(plan: Plan, ranks, core, V, energy, stream=None):
+    """Energy of a Tucker magnetization with its Tucker application in FP64 (core, V, energy:
+    device float64)."""
+    import torch
+    r = (_i * 3)(*[int(v) for v in ranks])
+    tot = sum(int(ranks[p]) * plan.n[p] for p in range(3))
+    f64 = torch.float64
+    _check(lib.demag_energy_tucker_fp64(plan.ptr, r,
+                                        _ptr(core, 3 * int(ranks[0]) * int(ranks[1]) * int(ranks[2]), f64, "core"),
+                                        _ptr(V, 3 * tot, f64, "V"), _ptr(energy, 1, f64, "energy"),
+                                        _stream(stream)), plan.ptr)
 
 
 def demag_energy_tt(plan: Plan, ranks, G1, G2, G3, out_w, oG1, oG2, oG3, energy, stream=None):

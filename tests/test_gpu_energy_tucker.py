@@ -173,3 +173,36 @@ def test_energy_1024_tucker_and_tt_routes_agree(D):
     D.demag_energy_tt(P, t, *G, w, *o, E)
     torch.cuda.synchronize()
     assert abs(E.item() - Et) <= 2e-5 * abs(Et), (E.item(), Et)
+
+
+@pytest.mark.parametrize("n,ranks,R", [((12, 10, 8), (2, 3, 2), 21), ((17, 9, 23), (1, 4, 3), 41),
+                                       ((12, 10, 8), (40, 40, 40), 21)])
+def test_energy_tucker_fp64_vs_oracle(D, n, ranks, R):
+    """The FP64 Tucker application and energy equal the oracle's dense FP64 route to
+    rounding (sums of ~10^3 FP64 terms with some cancellation: 1e-10; the FP32 route is
+    held to 1e-5)."""
+    h = (1.0 / max(n),) * 3
+    core, V = synth.tucker_inputs(n, ranks, 79)
+    P = D.demag_build_factors(n, h, R)
+    E = torch.empty((), dtype=torch.float64, device="cuda")
+    D.demag_energy_tucker_fp64(P, ranks, torch.from_numpy(np.ascontiguousarray(core, dtype=np.float64).ravel()).cuda(),
+                               torch.from_numpy(np.ascontiguousarray(V, dtype=np.float64)).cuda(), E)
+    torch.cuda.synchronize()
+    ref = oe.energy_tucker(core, V, n, ranks, h, R)
+    assert abs(E.item() - ref) <= 1e-10 * abs(ref), (E.item(), ref)
+
+
+@pytest.mark.parametrize("n,R", [(512, 257), (2048, 257)])
+def test_uniform_cube_energy_fp64_vs_oracle_1d_sums(D, n, R):
+    """The energy study's cube (m = e3, rank 1) on fine grids: the FP64 route equals the
+    oracle's one-dimensional FP64 sums to rounding, below the FP32 route's floor."""
+    P = D.demag_build_factors((n, n, n), (1.0 / n,) * 3, R)
+    core = torch.zeros(3, dtype=torch.float64, device="cuda")
+    core[2] = 1.0
+    V = torch.ones(9 * n, dtype=torch.float64, device="cuda")
+    E = torch.empty((), dtype=torch.float64, device="cuda")
+    D.demag_energy_tucker_fp64(P, (1, 1, 1), core, V, E)
+    torch.cuda.synchronize()
+    ref = oe.uniform_cube_energy(n, R)
+    assert abs(E.item() - ref) <= 1e-11 * ref, (E.item(), ref)
+    assert abs(E.item() - 1.0 / 6.0) * 6.0 < 1e-5

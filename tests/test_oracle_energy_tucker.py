@@ -50,3 +50,33 @@ def test_tt_energy_equals_the_full_format_energy():
     m = np.stack([ost.tt_to_full(G1[q], G2[q], G3[q], ranks) for q in range(3)])
     ref = oe.energy_from_m(m, n, h, R)
     assert abs(E - ref) <= 1e-12 * abs(ref)
+
+
+def test_fd_column_sums_match_the_stencil_matrix():
+    for n, hp in ((1, 0.3), (2, 0.5), (3, 0.25), (7, 0.1), (40, 1 / 40)):
+        assert np.allclose(oe.fd_column_sums(n, hp), oe.fd_matrix(n, hp).sum(axis=0), rtol=0, atol=1e-12 / hp)
+
+
+@pytest.mark.parametrize("n,R", [(8, 21), (12, 41), (17, 129)])
+def test_uniform_cube_energy_by_1d_sums_equals_the_tucker_route(n, R):
+    """The factorised energy of the study's cube equals the dense Tucker route."""
+    h = (1.0 / n,) * 3
+    core = np.zeros((3, 1, 1, 1))
+    core[2] = 1.0
+    V = np.ones(3 * 3 * n)
+    ref = oe.energy_tucker(core, V, (n, n, n), (1, 1, 1), h, R)
+    assert abs(oe.uniform_cube_energy(n, R) - ref) <= 1e-12 * abs(ref)
+
+
+def test_uniform_cube_energy_converges_to_one_sixth():
+    """The text after Fig. 2: the relative energy error falls with n, at an order
+    near 1.5 (R large enough that the quadrature error is far below it)."""
+    import json
+    import os
+    facts = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_facts.json")))
+    order = facts["energy_error_order"]["value"]
+    E0 = facts["uniform_cube_energy"]["value"]
+    errs = [abs(oe.uniform_cube_energy(n, 257) - E0) / E0 for n in (64, 128, 256, 512)]
+    orders = [np.log2(errs[i] / errs[i + 1]) for i in range(3)]
+    assert all(abs(o - order) <= 0.3 for o in orders), orders
+    assert errs[-1] < 1e-5
