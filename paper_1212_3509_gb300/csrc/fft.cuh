@@ -35,6 +35,28 @@ template <typename C> __device__ __forceinline__ C cadd(C a, C b) { C r; r.x = a
 template <typename C> __device__ __forceinline__ C csub(C a, C b) { C r; r.x = a.x - b.x; r.y = a.y - b.y; return r; }
 template <typename C> __device__ __forceinline__ C cconj(C a) { a.y = -a.y; return a; }
 
+// FP32 complex add / subtract as one packed instruction on the (re, im) pair
+// (add.rn.f32x2 / sub.rn.f32x2): per component the same correctly rounded
+// result as a scalar add, half the issue slots of the FFT butterflies.
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) {
+  unsigned long long ra, rb, rc;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(ra) : "f"(a.x), "f"(a.y));
+  asm("mov.b64 %0, {%1, %2};" : "=l"(rb) : "f"(b.x), "f"(b.y));
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(rc) : "l"(ra), "l"(rb));
+  float2 r;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(rc));
+  return r;
+}
+__device__ __forceinline__ float2 csub(float2 a, float2 b) {
+  unsigned long long ra, rb, rc;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(ra) : "f"(a.x), "f"(a.y));
+  asm("mov.b64 %0, {%1, %2};" : "=l"(rb) : "f"(b.x), "f"(b.y));
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(rc) : "l"(ra), "l"(rb));
+  float2 r;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(rc));
+  return r;
+}
+
 // exp(-2 pi i j / 16) for j = 0..15 (cos, -sin), exact zeros and ones.
 __device__ __forceinline__ constexpr double w16_re(int j) {
   return j == 0 ? 1.0 : j == 1 ? 0.92387953251128675613 : j == 2 ? 0.70710678118654752440
@@ -79,8 +101,18 @@ template <int R, bool INV, int K, typename C>
 __device__ __forceinline__ void dft_combine(C (&v)[R], C (&e)[R / 2], C (&o)[R / 2]) {
   if constexpr (K < R / 2) {
     C t = rot<R, K, INV>(o[K]);
-    v[K] = cadd(e[K], t);
-    v[K + R / 2] = csub(e[K], t);
+    constexpr int j = (K * (16 / R)) & 15;
+    if constexpr (j == 4 || j == 12) {
+      // +-i: the swap and sign fold into scalar adds (a packed add would need
+      // the swapped pair built first)
+      v[K].x = e[K].x + t.x;
+      v[K].y = e[K].y + t.y;
+      v[K + R / 2].x = e[K].x - t.x;
+      v[K + R / 2].y = e[K].y - t.y;
+    } else {
+      v[K] = cadd(e[K], t);
+      v[K + R / 2] = csub(e[K], t);
+    }
     dft_combine<R, INV, K + 1>(v, e, o);
   }
 }

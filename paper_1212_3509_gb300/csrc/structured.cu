@@ -104,7 +104,13 @@ struct TwN {
 template <int K>
 __device__ __forceinline__ void combine_half16(float2 (&v)[16], float2 (&e)[8], float2 (&o)[8]) {
   if constexpr (K < 8) {
-    v[K] = cadd(e[K], rot<16, K, true>(o[K]));
+    const float2 t = rot<16, K, true>(o[K]);
+    if constexpr (K == 4) {  // +i: folded into scalar adds
+      v[K].x = e[K].x + t.x;
+      v[K].y = e[K].y + t.y;
+    } else {
+      v[K] = cadd(e[K], t);
+    }
     combine_half16<K + 1>(v, e, o);
   }
 }
