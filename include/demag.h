@@ -209,10 +209,15 @@ demag_status demag_energy_field_fft(demag_plan* plan, const float* m, double* en
  * i < count.  Arrays of device pointers live in HOST memory.  Grids may
  * differ in shape; every plan must already have its workspace for `prec`
  * (made by a previous demag_apply_full or demag_reserve_workspace).
- * With DEMAG_TF32X3 / DEMAG_BF16X3 each of the three mode-product stages of
- * all listed grids is ONE persistent tensor-core launch (tiles of every grid
- * drawn from one work counter); a plan listed twice starts a second such
- * group after the first.  Device-side errors of a group are reported on its
+ * With DEMAG_TF32X3 / DEMAG_BF16X3 a group of listed grids runs as one split
+ * launch, one fused mode-1 / mode-2 launch over the grids whose forward
+ * schedule is the fused one (demag_forward_schedule; absent when none is),
+ * ONE persistent tensor-core launch for every remaining mode-product stage of
+ * every grid (tiles of every grid drawn from one work counter, later stages
+ * of a grid waiting for its earlier ones), and one reduction launch; every
+ * tile runs the MMA sequence of the grid's own call, so a grid without short
+ * axes gets the bits of demag_apply_full.  A plan listed twice starts a
+ * second such group after the first.  Device-side errors of a group are reported on its
  * first plan (demag_sync_status).  The grouped descriptors are cached on the
  * first plan for the last list seen; the first call with a new list
  * allocates them. */
