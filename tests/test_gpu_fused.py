@@ -107,6 +107,11 @@ def test_fused_and_chain_interleaved_256(D):
     f2 = _apply(D, P, m, True)
     assert np.array_equal(f1, f2)
     assert_close(f1, c, 2 * TOL["bf16x3"], "fused vs chain at 256^3")
+    # sampled output lines against the oracle: corners, faces and the centre
+    lines = [(0, 0), (255, 255), (128, 0), (0, 128), (128, 128), (37, 201)]
+    ref = ofull.apply_full_lines(host(m), n, h, R, lines)
+    got = np.stack([f1[i3, i2] for i3, i2 in lines])
+    assert_close(got, ref, TOL["bf16x3"], "fused 256^3 sampled lines vs oracle")
 
 
 
