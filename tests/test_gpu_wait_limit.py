@@ -52,6 +52,42 @@ def test_zero_wait_limit_reports_timeout_then_plan_recovers(D, n, fused):
     assert_close(host(phi), ofull.apply_full(m, n, h, R), TOL["bf16x3"])
 
 
+def test_zero_wait_limit_in_a_batch_with_fused_grids(D):
+    """The batched application (one fused mode-1 / mode-2 launch over two fused grids,
+    then the persistent launch with their mode-3 stages and a chain grid's stages)
+    with the first plan's limit at zero: the status on that plan says DEMAG_ETIMEOUT;
+    with the limit restored the same batch gives the single calls' bits."""
+    cases = [((64, 64, 20), True), ((48, 40, 37), False), ((37, 45, 33), True)]
+    plans, ms, single = [], [], []
+    for i, (n, fused) in enumerate(cases):
+        P = D.demag_build_factors(n, (1 / max(n),) * 3, 21)
+        D.demag_set_fused(P, fused)
+        m = dev(synth.random_unit_m(n, 1240 + i))
+        phi = torch.empty(n[2], n[1], n[0], device="cuda")
+        D.demag_apply_full(P, m, phi, "bf16x3")
+        plans.append(P)
+        ms.append(m)
+        single.append(phi)
+    outs = [torch.empty_like(p) for p in single]
+    D.demag_apply_full_batched(plans, ms, outs, "bf16x3")  # builds the grouped descriptors
+    torch.cuda.synchronize()
+    D.demag_sync_status(plans[0])
+    D.demag_set_wait_limit(plans[0], 0.0)
+    D.demag_apply_full_batched(plans, ms, outs, "bf16x3")
+    with pytest.raises(D.DemagError) as ei:
+        D.demag_sync_status(plans[0])
+    assert ei.value.status == 4  # DEMAG_ETIMEOUT
+    D.demag_set_wait_limit(plans[0], 2.0)
+    for o in outs:
+        o.fill_(float("nan"))
+    D.demag_apply_full_batched(plans, ms, outs, "bf16x3")
+    torch.cuda.synchronize()
+    for P in plans:
+        D.demag_sync_status(P)
+    for got, want in zip(outs, single):
+        assert torch.equal(got, want)
+
+
 def test_wait_limit_is_validated(D):
     P = D.demag_build_factors((8, 8, 8), (1 / 8,) * 3, 11)
     for bad in (-1.0, 61.0, float("nan")):
