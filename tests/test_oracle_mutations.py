@@ -222,3 +222,44 @@ def _energy_mutations():
 def test_energy_mutation_is_caught(monkeypatch, name, fn):
     monkeypatch.setattr(ost, name, fn)
     assert _energy_pin_error() > 1e-3
+
+
+def _cube_pin_error(n=12, R=41):
+    """The study's 1D-sum cube energy against the dense Tucker route."""
+    from oracle import energy as oen
+    h = (1.0 / n,) * 3
+    core = np.zeros((3, 1, 1, 1))
+    core[2] = 1.0
+    V = np.ones(9 * n)
+    ref = oen.energy_tucker(core, V, (n, n, n), (1, 1, 1), h, R)
+    return abs(oen.uniform_cube_energy(n, R) - ref) / abs(ref)
+
+
+def test_cube_energy_unmutated_is_exact():
+    assert _cube_pin_error() < 1e-12
+
+
+def _cube_mutations():
+    from oracle import energy as oen
+    orig_cs = oen.fd_column_sums
+
+    def central_only(n, hp):  # the one-sided end stencils replaced by the central one
+        cs = np.zeros(n)
+        i = np.arange(n)
+        np.add.at(cs, np.clip(i - 1, 0, n - 1), -0.5 / hp)
+        np.add.at(cs, np.clip(i + 1, 0, n - 1), 0.5 / hp)
+        return cs
+
+    def halved(n, hp):  # a dropped factor 1/2 h_p -> 1/h_p on one end
+        cs = orig_cs(n, hp)
+        cs[0] *= 2.0
+        return cs
+
+    return [("central_only", central_only), ("halved", halved)]
+
+
+@pytest.mark.parametrize("name,fn", _cube_mutations(), ids=lambda x: x if isinstance(x, str) else "")
+def test_cube_energy_mutation_is_caught(monkeypatch, name, fn):
+    from oracle import energy as oen
+    monkeypatch.setattr(oen, "fd_column_sums", fn)
+    assert _cube_pin_error() > 1e-3
