@@ -34,6 +34,8 @@ RAGGED_HALVES = [
     ((17, 18, 17), (1 / 17,) * 3, 11),                # h 9 (padded to 16), tiles 16 wide
     ((160, 100, 21), (0.01, 0.015, 0.05), 11),        # h 80, 50 (odd half at 56), tiles 64 wide
     ((250, 230, 19), (1 / 250, 1 / 230, 1 / 19), 5),  # h 125, 115 (padded to 128, 120), tiles 128 wide
+    ((17, 256, 300), (0.02, 0.01, 0.005), 5),         # h 9 / 128 (one k-block against four), 304 slabs, M = 2
+    ((256, 17, 33), (0.004, 0.05, 0.03), 5),          # h 128 / 9: 16-wide tiles over four mode-1 k-blocks
 ]
 
 
