@@ -1767,13 +1767,14 @@ struct SmallStage {
   float alpha;
 };
 
+// One block of rows of one job of a stage (the block's threads all run the
+// shared-memory rounds; rows past the stage's count only skip the arithmetic).
 template <class F>
-__global__ void __launch_bounds__(256) small_stage_kernel(const __grid_constant__ SmallStage S) {
+__device__ __forceinline__ void small_stage_block(const SmallStage& S, int job, int rowblock, float* sB) {
   using T = typename F::T;
-  __shared__ float sB[kSmallChunk * kSmallAxis * kSmallAxis];
-  const TcJob J = S.jobs[blockIdx.y];
+  const TcJob J = S.jobs[job];
   const int n = S.n;
-  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  const int row = rowblock * blockDim.x + threadIdx.x;
   const bool valid = row < S.rows;
   float acc[kSmallAxis];
 #pragma unroll
@@ -1828,6 +1829,33 @@ __global__ void __launch_bounds__(256) small_stage_kernel(const __grid_constant_
       reinterpret_cast<float*>(S.out_hi)[rbase + a * S.s_a] = S.alpha * acc[a];
     }
   }
+}
+
+template <class F>
+__global__ void __launch_bounds__(256) small_stage_kernel(const __grid_constant__ SmallStage S) {
+  __shared__ float sB[kSmallChunk * kSmallAxis * kSmallAxis];
+  small_stage_block<F>(S, blockIdx.y, blockIdx.x, sB);
+}
+
+// The thin last stages of several grids in one launch (batched applications):
+// blockIdx.y runs over the jobs of all items, blockIdx.x over row blocks up to
+// the largest item's; blocks past their item's rows leave at once.
+constexpr int kMaxSmallItems = 32;
+struct SmallBatch {
+  SmallStage it[kMaxSmallItems];
+  int job0[kMaxSmallItems + 1];  // first job of each item
+  int count;
+  int rowblocks;                 // of the largest item
+};
+
+template <class F>
+__global__ void __launch_bounds__(256) small_batch_kernel(const __grid_constant__ SmallBatch B) {
+  __shared__ float sB[kSmallChunk * kSmallAxis * kSmallAxis];
+  int i = 0;
+  while (i + 1 < B.count && (int)blockIdx.y >= B.job0[i + 1]) ++i;
+  const SmallStage& S = B.it[i];
+  if ((long long)blockIdx.x * blockDim.x >= S.rows) return;  // uniform over the block
+  small_stage_block<F>(S, (int)blockIdx.y - B.job0[i], blockIdx.x, sB);
 }
 
 // ---------------------------------------------------------------- host side
@@ -1997,6 +2025,7 @@ struct TcBatch {
   S12Launch* s12items = nullptr;       // device [s12count]: the fused grids' mode-1/mode-2 launches
   int* s12unit0 = nullptr;             // device [s12count + 1]: first unit of each
   int s12count = 0, s12units = 0;
+  SmallBatch small;                    // thin last stages run on CUDA cores after the persistent launch
 };
 
 struct TcHolder {
@@ -3036,6 +3065,13 @@ demag_status tc_batch_create(demag_plan* const* plans, int count, demag_precisio
   std::vector<TcSeg> segs;
   std::vector<S12Launch> items;
   std::vector<int> unit0(1, 0);
+  // chain grids whose last stage only is along a thin axis (films n1, n2 > 16 >= n3): that
+  // stage runs on CUDA cores as in a single call, one launch for all of them after the
+  // persistent one (as padded tensor-core tiles it took twice as long); other thin stages
+  // stay in the persistent launch as padded tiles
+  std::vector<char> thin3(count, 0);
+  memset(&B->small, 0, sizeof(B->small));
+  B->small.job0[0] = 0;
   B->fused.resize(count);
   for (int i = 0; i < count; ++i) {
     const TcState* S = state(plans[i], prec);
@@ -3052,6 +3088,14 @@ demag_status tc_batch_create(demag_plan* const* plans, int count, demag_precisio
       g[i].o_wide = 0;
       items.push_back(S->s12);
       unit0.push_back(unit0.back() + S->s12.units);
+    } else if (S->small[kFwd3] && !S->small[kFwd1] && !S->small[kFwd2] && B->small.count < kMaxSmallItems) {
+      SmallBatch& SB = B->small;
+      const SmallStage& Q = S->small_prog[kFwd3];
+      thin3[i] = 1;
+      SB.it[SB.count] = Q;
+      SB.job0[SB.count + 1] = SB.job0[SB.count] + Q.njobs;
+      SB.rowblocks = std::max(SB.rowblocks, (Q.rows + 255) / 256);
+      ++SB.count;
     }
   }
   int acc = 0;
@@ -3062,6 +3106,7 @@ demag_status tc_batch_create(demag_plan* const* plans, int count, demag_precisio
       if (fz != (pass == 1)) continue;
       const TcState* S = state(plans[order[i]], prec);
       const int st3 = pass == 0 ? 0 : pass - 1;
+      if (st3 == 2 && thin3[i]) continue;  // in the CUDA-core launch after this one
       const int gi = fz ? i : st3 * count + i;
       if (g[gi].ntiles <= 0) continue;
       TcSeg q = whole_seg(g[gi], gi, acc);
@@ -3141,6 +3186,11 @@ static demag_status batched_chain(const TcBatch* B, const float* const* m, float
   demag_status s = launch_segs<F>(P0, B->groups, B->segs, B->nsegs, B->total, B->maxbn, B->ctr, B->ctr + 1,
                                   B->nctr, S0->status, st);
   if (s != DEMAG_OK) return s;
+  if (B->small.count > 0) {
+    const dim3 grid((unsigned)B->small.rowblocks, (unsigned)B->small.job0[B->small.count]);
+    DEMAG_LAUNCH(P0, kFamGemmSimt, st, small_batch_kernel<F><<<grid, 256, 0, st>>>(B->small));
+    DEMAG_LAUNCHED(P0, "small_batch_kernel");
+  }
   for (int i0 = 0; i0 < count; i0 += kMaxItems) {
     ReduceLists L;
     for (int i = i0; i < count && i < i0 + kMaxItems; ++i) {

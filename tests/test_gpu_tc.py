@@ -90,10 +90,12 @@ def test_grouped_batch_equals_single_applies(D, prec):
     (TMA-stored and directly stored epilogues mixed, a plan listed twice, later
     stages waiting for earlier ones through completion counters) gives, bit for
     bit, what separate calls give on grids whose axes all run on the tensor
-    cores: every tile runs the same MMA sequence.  Axes of at most 16 cells run
-    on CUDA cores in a single call but as padded tensor-core tiles in the
-    batch, so those grids agree to the split-form tolerance.  The batch runs
-    the three-stage chain, so the separate calls are held to it too."""
+    cores: every tile runs the same MMA sequence.  A thin last axis (at most 16
+    cells) runs on CUDA cores in both, so those grids agree bit for bit too;
+    other thin axes run on CUDA cores in a single call but as padded
+    tensor-core tiles in the batch, so those grids agree to the split-form
+    tolerance.  The batch runs the three-stage chain, so the separate calls are
+    held to it too."""
     cases = [TC_SHAPES[0], TC_SHAPES[1], TC_SHAPES[4], TC_SHAPES[7], TC_SHAPES[8]]
     plans, ms, single = [], [], []
     for i, (n, h, R) in enumerate(cases):
@@ -116,7 +118,7 @@ def test_grouped_batch_equals_single_applies(D, prec):
     for P in plans:
         D.demag_sync_status(P)
     for (n, _, _), got, ref in zip(cases + [cases[0]], outs, single + [ref_extra]):
-        if min(n) > 16:
+        if n[0] > 16 and n[1] > 16:  # a thin last axis runs the single call's CUDA-core stage
             assert torch.equal(got, ref), n
         else:
             assert_close(host(got), host(ref), TOL[prec], n)
