@@ -1191,10 +1191,11 @@ def ncore_implicit(rho, rt):
 
 def run_uneven_batch(args, D, world, local, stream, form):
     """64 full-format grids of mixed shape (cubes 32^3..192^3, 512x512x4 and
-    256x64x8 films), R = 41, replayed as a CUDA graph of four launches (split;
+    256x64x8 films), R = 41, replayed as a CUDA graph of five launches (split;
     the fused mode-1 / mode-2 products of the grids with the fused schedule;
     one persistent launch over their mode-3 stages and the other grids'
-    three stages; reduction); compared with one call per grid."""
+    tensor-core stages; the films' thin last stages on CUDA cores; reduction);
+    compared with one call per grid."""
     import numpy as np
     import torch
     import synth

@@ -214,9 +214,12 @@ demag_status demag_energy_field_fft(demag_plan* plan, const float* m, double* en
  * schedule is the fused one (demag_forward_schedule; absent when none is),
  * ONE persistent tensor-core launch for every remaining mode-product stage of
  * every grid (tiles of every grid drawn from one work counter, later stages
- * of a grid waiting for its earlier ones), and one reduction launch; every
- * tile runs the MMA sequence of the grid's own call, so a grid without short
- * axes gets the bits of demag_apply_full.  A plan listed twice starts a
+ * of a grid waiting for its earlier ones), one CUDA-core launch for the last
+ * stages along a short third axis (at most 16 cells, films), and one
+ * reduction launch; every tile runs the MMA sequence of the grid's own call
+ * and a short last stage the same CUDA-core kernel, so a grid whose first two
+ * axes are longer than 16 cells gets the bits of demag_apply_full (a short
+ * first or second axis runs as padded tensor-core tiles in the batch).  A plan listed twice starts a
  * second such group after the first.  Device-side errors of a group are reported on its
  * first plan (demag_sync_status).  The grouped descriptors are cached on the
  * first plan for the last list seen; the first call with a new list
