@@ -40,12 +40,12 @@ PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustain
 NCU_TRAFFIC = {
     # the three tcgen05 mode-product stages of one application, BF16x3, R = 41,
     # per cell of the grid (captured at 192^3, folded axes)
-    "tc_gemm_kernel": {"sources": ("full_tc.cu", "tc_ptx.cuh"), "sha": "08444307804737c0",
-                       "bytes_per_cell": 5.73276e9 / 192 ** 3},
+    "tc_gemm_kernel": {"sources": ("full_tc.cu", "tc_ptx.cuh"), "sha": "05c5be55af52d644",
+                       "bytes_per_cell": 5.73263e9 / 192 ** 3},
     # the fused schedule: tc_s12_kernel and the mode-3 tc_gemm_kernel launch of
     # one application, BF16x3, R = 41, per cell (captured at 192^3)
-    "tc_fused": {"sources": ("full_tc.cu", "tc_ptx.cuh"), "sha": "08444307804737c0",
-                 "bytes_per_cell": 2.36540e9 / 192 ** 3},
+    "tc_fused": {"sources": ("full_tc.cu", "tc_ptx.cuh"), "sha": "05c5be55af52d644",
+                 "bytes_per_cell": 2.36666e9 / 192 ** 3},
     # the Toeplitz FFT launch of a CP batch, n = 4096, r = 4, R = 61, per application
     "toeplitz_fft_kernel": {"sources": ("structured.cu", "fft.cuh"), "sha": "d08396a13974c222",
                             "bytes_per_app": 550.296e6 / 32},
