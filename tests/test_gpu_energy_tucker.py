@@ -206,3 +206,19 @@ def test_uniform_cube_energy_fp64_vs_oracle_1d_sums(D, n, R):
     ref = oe.uniform_cube_energy(n, R)
     assert abs(E.item() - ref) <= 1e-11 * ref, (E.item(), ref)
     assert abs(E.item() - 1.0 / 6.0) * 6.0 < 1e-5
+
+
+def test_energy_tucker_fp64_rejects_what_it_cannot_do(D):
+    """A graded (non-uniform) grid has no Toeplitz generators and ranks past 64 do not fit the
+    Gram tiles: both are errors before any launch."""
+    edges = [np.concatenate([[0.0], np.cumsum(1.05 ** np.arange(k))]) / 16 for k in (12, 10, 8)]
+    Pn = D.demag_build_factors_nonuniform(edges, 21)
+    core = torch.zeros(3, dtype=torch.float64, device="cuda")
+    V = torch.ones(3 * 30, dtype=torch.float64, device="cuda")
+    E = torch.empty((), dtype=torch.float64, device="cuda")
+    with pytest.raises(D.DemagError):
+        D.demag_energy_tucker_fp64(Pn, (1, 1, 1), core, V, E)
+    P = D.demag_build_factors((12, 10, 8), (1 / 12,) * 3, 21)
+    with pytest.raises(D.DemagError):
+        D.demag_energy_tucker_fp64(P, (65, 1, 1), torch.zeros(3 * 65, dtype=torch.float64, device="cuda"),
+                                   torch.ones(3 * (65 * 12 + 10 + 8), dtype=torch.float64, device="cuda"), E)

@@ -86,6 +86,10 @@ def test_untuned_schedule_follows_grid_size(D):
         assert D.demag_forward_schedule(P, "bf16x3") == (0 if min(n) <= 16 else 1)
         D.demag_set_fused(P, False)
         assert D.demag_forward_schedule(P, "bf16x3") == 0
+        D.demag_set_fused(P, True)
+        D.demag_reserve_workspace(P, "tf32x3")
+        assert D.demag_forward_schedule(P, "tf32x3") == 0  # the fused kernel is BF16x3 only
+        assert D.demag_forward_schedule(P, "fp32") == -1   # not a tensor-core form
 
 
 def test_fused_repeated_calls_are_identical(D):
