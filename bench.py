@@ -296,9 +296,9 @@ def run_ours(args, world, rank, local):
 
     M = P.M
     N1 = args.n
-    # algorithmic work per application (the dense contraction of the survey's
-    # measurement section): 9 mode products of 2 n^4 flop per node; with the
-    # 8-GEMM sharing of the chain 16 n^4 per node
+    # algorithmic work per application (Eq. kron_operator contracted densely by
+    # Eq. modemul): 9 mode products of 2 n^4 flop per node; with the 8-GEMM
+    # sharing of the chain 16 n^4 per node
     flops_app = 18.0 * (N1 ** 4) * M
     flops_app_8 = 16.0 * (N1 ** 4) * M
     gemm_ms_app = gemm_ms / args.steps
