@@ -597,9 +597,10 @@ demag_status demag_autotune(demag_plan* plan, int enable);
  * BF16x3 forward schedule (1 fused, 0 chain)), key (FFT: log2 of the complex
  * FFT length, column blocks, M; tensor core: stage program 0..7 (6, 7: the
  * mode-3 stages of the fused forward and adjoint schedules), default value, 0;
- * schedule: 0, 1, 0), the chosen
- * value, its time per launch and the default value's time per launch in ms
- * (0 for an entry read from a cache). */
+ * schedule: 0, 1, 0, whatever the untuned choice), the chosen value, its time
+ * per launch and the default value's time per launch in ms (for the schedule,
+ * the untuned choice's time: fused from 2^20 folded cells, else the chain; 0
+ * for an entry read from a cache). */
 int demag_autotune_count(const demag_plan* plan);
 demag_status demag_autotune_entry(const demag_plan* plan, int i, int* kind, int key[3], int* value, float* ms,
                                   float* ms_default);
